@@ -1,0 +1,433 @@
+/*
+ * scalp_oracle.c -- plain, slow, FP64 CPU oracle for SCALP
+ * ("Superpixels with Contour Adherence using Linear Path", Giraud, Ta,
+ * Papadakis, ICPR 2018).
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the CPU
+ * baseline leg of bench.py may load this file.  It shares no code, header,
+ * table or helper with the CUDA library; neither includes the other.
+ *
+ * Everything is evaluated in double precision, in the order Algorithm 1 states
+ * it: for each cluster C_k, for each pixel p of the (2r+1)x(2r+1) window
+ * centred on X_k, compute D(p, C_k) (Eq. 3) and relabel p on a strict '<'.
+ * Then update the clusters and, where needed, project their barycenters
+ * (Eq. 4).
+ *
+ * Readings of points the paper leaves open (each is listed in the design doc):
+ *   - CIELab: sRGB (IEC 61966-2-1) -> linear -> XYZ (D65 matrix) -> CIE 1976
+ *     L*a*b*, with the reference white taken as the XYZ image of sRGB white.
+ *   - Grid: r = sqrt(N/K); nx = max(1, round(W/r)), ny = max(1, round(H/r));
+ *     pixel (x, y) starts in cell floor(y*ny/H)*nx + floor(x*nx/W).
+ *   - Window: p is a candidate of C_k iff |x_p - x_k| <= r and |y_p - y_k| <= r,
+ *     tested exactly as K*(n*x_p - Sx)^2 <= N*n^2 in 128-bit integers.
+ *   - Path endpoint: X_k rounded half-up, floor((2*Sx + n) / (2n)), or X_k^*
+ *     when projected.  The path holds both p and the endpoint; it is traced
+ *     from the lexicographically smaller (x, then y) end so it is symmetric.
+ *   - No candidate: the pixel keeps its previous label.  Empty cluster: its
+ *     colour, barycenter and endpoint are kept.
+ *   - Projection is triggered when the label at the rounded barycenter is not
+ *     k; ties in Eq. 4 go to the smallest raster index.
+ *   - Connectivity enforcement (not in the paper) follows a fixed
+ *     component-merging rule, see orc_connectivity().
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+typedef __int128 i128;
+
+/* ------------------------------------------------------------------------ */
+/* CIELab conversion (Sec. II-A: clustering runs in the CIELab space).       */
+/* ------------------------------------------------------------------------ */
+
+static double srgb_channel_to_linear(double c)
+{
+    /* IEC 61966-2-1 transfer function, inverted */
+    if (c <= 0.04045) return c / 12.92;
+    return pow((c + 0.055) / 1.055, 2.4);
+}
+
+static double cie_f(double t)
+{
+    /* CIE 1976 companding: cube root above (6/29)^3, linear segment below */
+    const double d = 6.0 / 29.0;
+    if (t > d * d * d) return cbrt(t);
+    return t / (3.0 * d * d) + 4.0 / 29.0;
+}
+
+static const double M_SRGB_TO_XYZ[3][3] = {
+    {0.4124564, 0.3575761, 0.1804375},
+    {0.2126729, 0.7151522, 0.0721750},
+    {0.0193339, 0.1191920, 0.9503041},
+};
+
+void orc_lab_from_rgb(const uint8_t *rgb, int64_t npix, double *L, double *A, double *B)
+{
+    double white[3];
+    for (int i = 0; i < 3; i++)
+        white[i] = M_SRGB_TO_XYZ[i][0] + M_SRGB_TO_XYZ[i][1] + M_SRGB_TO_XYZ[i][2];
+    for (int64_t p = 0; p < npix; p++) {
+        double lin[3], xyz[3];
+        for (int c = 0; c < 3; c++) lin[c] = srgb_channel_to_linear(rgb[3 * p + c] / 255.0);
+        for (int i = 0; i < 3; i++)
+            xyz[i] = M_SRGB_TO_XYZ[i][0] * lin[0] + M_SRGB_TO_XYZ[i][1] * lin[1] +
+                     M_SRGB_TO_XYZ[i][2] * lin[2];
+        double fx = cie_f(xyz[0] / white[0]);
+        double fy = cie_f(xyz[1] / white[1]);
+        double fz = cie_f(xyz[2] / white[2]);
+        L[p] = 116.0 * fy - 16.0;
+        A[p] = 500.0 * (fx - fy);
+        B[p] = 200.0 * (fy - fz);
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Regular grid (Sec. II-A; Algorithm 1, initialisation).                    */
+/* ------------------------------------------------------------------------ */
+
+void orc_grid_dims(int H, int W, int K, int *nx, int *ny)
+{
+    double N = (double)H * (double)W;
+    double r = sqrt(N / (double)K);
+    int gx = (int)floor((double)W / r + 0.5);
+    int gy = (int)floor((double)H / r + 0.5);
+    if (gx < 1) gx = 1;
+    if (gy < 1) gy = 1;
+    if (gx > W) gx = W;
+    if (gy > H) gy = H;
+    *nx = gx;
+    *ny = gy;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Linear path (Sec. II-B), Bresenham's digital segment between two pixels. */
+/* ------------------------------------------------------------------------ */
+
+/* Writes the path pixels as (x, y) pairs into xy (capacity >= len) and
+ * returns len = max(|dx|, |dy|) + 1.  Step i along the major axis moves the
+ * minor coordinate by round-half-up(i * d_minor / d_major). */
+int orc_path(int px, int py, int ex, int ey, int32_t *xy)
+{
+    int ax, ay, bx, by;
+    if (px < ex || (px == ex && py <= ey)) {
+        ax = px; ay = py; bx = ex; by = ey;
+    } else {
+        ax = ex; ay = ey; bx = px; by = py;
+    }
+    int dx = bx - ax; /* >= 0 by the ordering */
+    int dy = by - ay;
+    int ady = dy < 0 ? -dy : dy;
+    int sy = dy < 0 ? -1 : 1;
+    if (dx >= ady) {
+        int ns = dx;
+        for (int i = 0; i <= ns; i++) {
+            int off = ns == 0 ? 0 : (int)((2LL * i * ady + ns) / (2LL * ns));
+            xy[2 * i] = ax + i;
+            xy[2 * i + 1] = ay + sy * off;
+        }
+        return ns + 1;
+    } else {
+        int ns = ady;
+        for (int i = 0; i <= ns; i++) {
+            int off = (int)((2LL * i * dx + ns) / (2LL * ns));
+            xy[2 * i] = ax + off;
+            xy[2 * i + 1] = ay + sy * i;
+        }
+        return ns + 1;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Solver state.                                                             */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    int32_t H, W, K;      /* image size, requested number of superpixels */
+    int32_t nx, ny, Keff; /* grid; Keff = nx*ny clusters */
+    double m, lambda, sigma, gamma; /* gamma < 0 selects the default 2r */
+    double r;             /* filled by orc_init: sqrt(N/K) */
+    const double *L, *A, *B; /* CIELab planes, N each, row-major */
+    const double *C;         /* contour prior in [0,1], N */
+    int32_t *labels;      /* N */
+    int64_t *n, *sx, *sy; /* Keff: |S_k| and the integer coordinate sums */
+    double *cL, *cA, *cB; /* Keff: mean colour */
+    int32_t *ex, *ey;     /* Keff: path endpoint (rounded or projected X_k) */
+    int64_t orphans;      /* pixels with no candidate in the last assignment */
+    int64_t projections;  /* clusters projected in the last update */
+} orc_ctx;
+
+/* |v - s/n| <= r with r^2 = N/K, i.e. K*(n*v - s)^2 <= N*n^2, exactly. */
+static int in_window(int64_t v, int64_t n, int64_t s, int64_t N, int64_t K)
+{
+    i128 d = (i128)n * v - (i128)s;
+    i128 lhs = (i128)K * d * d;
+    i128 rhs = (i128)N * (i128)n * (i128)n;
+    return lhs <= rhs;
+}
+
+int orc_in_window(int64_t v, int64_t n, int64_t s, int64_t N, int64_t K)
+{
+    return in_window(v, n, s, N, K);
+}
+
+static double dc_at(const orc_ctx *c, int64_t q, int k)
+{
+    double dl = c->L[q] - c->cL[k];
+    double da = c->A[q] - c->cA[k];
+    double db = c->B[q] - c->cB[k];
+    return dl * dl + da * da + db * db;
+}
+
+/* D(p, C_k) of Eq. 3 with the colour term of Eq. 1 and the contour weight of
+ * Eq. 2, all sums over the path P_p^k. */
+double orc_distance(const orc_ctx *c, int px, int py, int k, int32_t *path_len)
+{
+    int64_t W = c->W;
+    int maxlen = (c->W > c->H ? c->W : c->H) + 1;
+    int32_t *xy = (int32_t *)malloc(sizeof(int32_t) * 2 * (size_t)maxlen);
+    int len = orc_path(px, py, c->ex[k], c->ey[k], xy);
+    double sum_dc = 0.0, sum_w = 0.0;
+    for (int i = 0; i < len; i++) {
+        int64_t q = (int64_t)xy[2 * i + 1] * W + xy[2 * i];
+        sum_dc += dc_at(c, q, k);
+        double cq = c->C[q];
+        sum_w += 1.0 - exp(-(cq * cq) / (c->sigma * c->sigma));
+    }
+    free(xy);
+    int64_t p = (int64_t)py * W + px;
+    double dc_path = c->lambda * dc_at(c, p, k) + (1.0 - c->lambda) * sum_dc / len;  /* Eq. 1 */
+    double d_contour = 1.0 + c->gamma / len * sum_w;                                /* Eq. 2 */
+    double xk = (double)c->sx[k] / (double)c->n[k];
+    double yk = (double)c->sy[k] / (double)c->n[k];
+    double ds = (px - xk) * (px - xk) + (py - yk) * (py - yk);
+    if (path_len) *path_len = len;
+    return dc_path * d_contour + ds * (c->m * c->m) / (c->r * c->r); /* Eq. 3 */
+}
+
+/* Eq. 4: X_k^* = argmin over p in S_k of ||X_p - X_k||, evaluated as
+ * (n*x_p - Sx)^2 + (n*y_p - Sy)^2 in 128-bit integers; ties -> smallest raster
+ * index.  Only called for clusters with n > 0 (so S_k is not empty). */
+static void project_center(orc_ctx *c, int k)
+{
+    int64_t N = (int64_t)c->H * c->W;
+    i128 best = -1;
+    int64_t best_p = -1;
+    for (int64_t p = 0; p < N; p++) {
+        if (c->labels[p] != k) continue;
+        int64_t x = p % c->W, y = p / c->W;
+        i128 ddx = (i128)c->n[k] * x - c->sx[k];
+        i128 ddy = (i128)c->n[k] * y - c->sy[k];
+        i128 d2 = ddx * ddx + ddy * ddy;
+        if (best_p < 0 || d2 < best) {
+            best = d2;
+            best_p = p;
+        }
+    }
+    c->ex[k] = (int32_t)(best_p % c->W);
+    c->ey[k] = (int32_t)(best_p / c->W);
+}
+
+/* Algorithm 1, last two steps: recompute [l_k, a_k, b_k, X_k] as means over
+ * S_k, then project X_k when it is not inside S_k. */
+void orc_update(orc_ctx *c)
+{
+    int64_t N = (int64_t)c->H * c->W;
+    int K = c->Keff;
+    int64_t *n = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    int64_t *sx = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    int64_t *sy = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    double *sl = (double *)calloc((size_t)K, sizeof(double));
+    double *sa = (double *)calloc((size_t)K, sizeof(double));
+    double *sb = (double *)calloc((size_t)K, sizeof(double));
+    for (int64_t p = 0; p < N; p++) {
+        int k = c->labels[p];
+        n[k] += 1;
+        sx[k] += p % c->W;
+        sy[k] += p / c->W;
+        sl[k] += c->L[p];
+        sa[k] += c->A[p];
+        sb[k] += c->B[p];
+    }
+    c->projections = 0;
+    for (int k = 0; k < K; k++) {
+        if (n[k] == 0) continue; /* empty cluster: unchanged */
+        c->n[k] = n[k];
+        c->sx[k] = sx[k];
+        c->sy[k] = sy[k];
+        c->cL[k] = sl[k] / (double)n[k];
+        c->cA[k] = sa[k] / (double)n[k];
+        c->cB[k] = sb[k] / (double)n[k];
+        c->ex[k] = (int32_t)((2 * sx[k] + n[k]) / (2 * n[k]));
+        c->ey[k] = (int32_t)((2 * sy[k] + n[k]) / (2 * n[k]));
+        if (c->labels[(int64_t)c->ey[k] * c->W + c->ex[k]] != k) {
+            project_center(c, k);
+            c->projections++;
+        }
+    }
+    free(n); free(sx); free(sy); free(sl); free(sa); free(sb);
+}
+
+/* Algorithm 1 initialisation: clusters from the regular grid, labels = cell. */
+int orc_init(orc_ctx *c)
+{
+    int64_t N = (int64_t)c->H * c->W;
+    if (c->H < 1 || c->W < 1 || c->K < 1 || c->K > N) return -1;
+    c->r = sqrt((double)N / (double)c->K);
+    if (c->gamma < 0) c->gamma = 2.0 * c->r;
+    orc_grid_dims(c->H, c->W, c->K, &c->nx, &c->ny);
+    c->Keff = c->nx * c->ny;
+    for (int64_t p = 0; p < N; p++) {
+        int64_t x = p % c->W, y = p / c->W;
+        int cx = (int)(x * c->nx / c->W);
+        int cy = (int)(y * c->ny / c->H);
+        c->labels[p] = cy * c->nx + cx;
+    }
+    orc_update(c);
+    c->orphans = 0;
+    return 0;
+}
+
+/* Algorithm 1, assignment: d <- inf; for each C_k, for each p of its window,
+ * relabel p when D(p, C_k) < d(p).  Pixels no window reaches keep their label.
+ * dbest (optional, N) receives d(p). */
+int64_t orc_assign(orc_ctx *c, double *dbest)
+{
+    int64_t N = (int64_t)c->H * c->W;
+    double *d = (double *)malloc(sizeof(double) * (size_t)N);
+    for (int64_t p = 0; p < N; p++) d[p] = INFINITY;
+    for (int k = 0; k < c->Keff; k++) {
+        double xk = (double)c->sx[k] / (double)c->n[k];
+        double yk = (double)c->sy[k] / (double)c->n[k];
+        int x0 = (int)floor(xk - c->r) - 1, x1 = (int)ceil(xk + c->r) + 1;
+        int y0 = (int)floor(yk - c->r) - 1, y1 = (int)ceil(yk + c->r) + 1;
+        if (x0 < 0) x0 = 0;
+        if (y0 < 0) y0 = 0;
+        if (x1 > c->W - 1) x1 = c->W - 1;
+        if (y1 > c->H - 1) y1 = c->H - 1;
+        for (int y = y0; y <= y1; y++) {
+            if (!in_window(y, c->n[k], c->sy[k], N, c->K)) continue;
+            for (int x = x0; x <= x1; x++) {
+                if (!in_window(x, c->n[k], c->sx[k], N, c->K)) continue;
+                double D = orc_distance(c, x, y, k, NULL);
+                int64_t p = (int64_t)y * c->W + x;
+                if (D < d[p]) {
+                    d[p] = D;
+                    c->labels[p] = k;
+                }
+            }
+        }
+    }
+    int64_t orphans = 0;
+    for (int64_t p = 0; p < N; p++) {
+        if (d[p] == INFINITY) orphans++;
+        if (dbest) dbest[p] = d[p];
+    }
+    free(d);
+    c->orphans = orphans;
+    return orphans;
+}
+
+int orc_iterate(orc_ctx *c, int iters)
+{
+    for (int it = 0; it < iters; it++) {
+        orc_assign(c, NULL);
+        orc_update(c);
+    }
+    return 0;
+}
+
+/* Label of each listed pixel as the assignment would give it, found by
+ * testing every cluster's window (pixel-centric); used to check single pixels
+ * of large images.  out_label gets the argmin (smallest k on ties, previous
+ * label when no window covers the pixel), out_d its distance (inf if none). */
+void orc_assign_pixels(const orc_ctx *c, const int64_t *pix, int64_t M, int32_t *out_label,
+                       double *out_d)
+{
+    int64_t N = (int64_t)c->H * c->W;
+    for (int64_t i = 0; i < M; i++) {
+        int64_t p = pix[i];
+        int x = (int)(p % c->W), y = (int)(p / c->W);
+        double best = INFINITY;
+        int lab = c->labels[p];
+        for (int k = 0; k < c->Keff; k++) {
+            if (!in_window(x, c->n[k], c->sx[k], N, c->K)) continue;
+            if (!in_window(y, c->n[k], c->sy[k], N, c->K)) continue;
+            double D = orc_distance(c, x, y, k, NULL);
+            if (D < best) {
+                best = D;
+                lab = k;
+            }
+        }
+        out_label[i] = lab;
+        out_d[i] = best;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Connectivity enforcement (not part of the paper).                         */
+/*   1. 4-connected components of equal label; a component's seed is its     */
+/*      smallest raster index.                                               */
+/*   2. A component is small iff its size <= floor(N / (4K)).                */
+/*   3. A small component whose seed s is not pixel 0 is absorbed by the     */
+/*      component holding s-1 (if x(s) > 0) or s-W (otherwise); these have   */
+/*      smaller seeds.  It takes the identity that component ends up with.   */
+/*   4. Surviving components are numbered 0.. in raster order of seeds.      */
+/* ------------------------------------------------------------------------ */
+
+int32_t orc_connectivity(const int32_t *labels, int H, int W, int K, int32_t *out)
+{
+    int64_t N = (int64_t)H * W;
+    int64_t *comp = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);  /* pixel -> component */
+    int64_t *seed = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);  /* component -> seed */
+    int64_t *size = (int64_t *)calloc((size_t)N, sizeof(int64_t));
+    int64_t *stack = (int64_t *)malloc(sizeof(int64_t) * (size_t)N);
+    for (int64_t p = 0; p < N; p++) comp[p] = -1;
+    int64_t ncomp = 0;
+    for (int64_t s = 0; s < N; s++) {
+        if (comp[s] >= 0) continue;
+        int64_t id = ncomp++;
+        seed[id] = s;
+        int64_t top = 0;
+        stack[top++] = s;
+        comp[s] = id;
+        while (top > 0) {
+            int64_t q = stack[--top];
+            size[id]++;
+            int64_t qx = q % W, qy = q / W;
+            int64_t nb[4];
+            int nn = 0;
+            if (qx > 0) nb[nn++] = q - 1;
+            if (qx < W - 1) nb[nn++] = q + 1;
+            if (qy > 0) nb[nn++] = q - W;
+            if (qy < H - 1) nb[nn++] = q + W;
+            for (int j = 0; j < nn; j++) {
+                int64_t t = nb[j];
+                if (comp[t] < 0 && labels[t] == labels[q]) {
+                    comp[t] = id;
+                    stack[top++] = t;
+                }
+            }
+        }
+    }
+    /* Components were discovered in raster order of their seeds, so a
+     * component's absorbing neighbour always has a smaller id. */
+    int64_t T = N / (4 * (int64_t)K);
+    int64_t *final_id = (int64_t *)malloc(sizeof(int64_t) * (size_t)ncomp);
+    int64_t *number = (int64_t *)malloc(sizeof(int64_t) * (size_t)ncomp);
+    int32_t nlab = 0;
+    for (int64_t id = 0; id < ncomp; id++) {
+        int64_t s = seed[id];
+        int small = size[id] <= T && s != 0;
+        if (small) {
+            int64_t nbp = (s % W) > 0 ? s - 1 : s - W;
+            final_id[id] = final_id[comp[nbp]];
+        } else {
+            final_id[id] = id;
+            number[id] = nlab++;
+        }
+    }
+    for (int64_t p = 0; p < N; p++) out[p] = (int32_t)number[final_id[comp[p]]];
+    free(comp); free(seed); free(size); free(stack); free(final_id); free(number);
+    return nlab;
+}

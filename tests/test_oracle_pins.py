@@ -1,0 +1,422 @@
+"""Pins of the FP64 oracle against facts fixed by the paper or by mathematics.
+
+None of these compares the oracle with itself: each checks a closed form, an
+invariant, a special case the paper states, a library routine, published
+colour values, or brute force on tiny inputs.
+"""
+import json
+import math
+import os
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1903_07149_gb300 import synth
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# CIELab (Sec. II-A names CIELab; the conversion itself is the sRGB/CIE
+# standard).  Published L*a*b* of the sRGB primaries under D65.
+# --------------------------------------------------------------------------
+def test_lab_published_values():
+    rgb = np.array([[255, 255, 255], [0, 0, 0], [255, 0, 0], [0, 255, 0], [0, 0, 255]],
+                   np.uint8)
+    L, A, B = oracle.lab_from_rgb(rgb)
+    assert abs(L[0] - 100) < 1e-9 and abs(A[0]) < 1e-9 and abs(B[0]) < 1e-9
+    assert abs(L[1]) < 1e-12 and abs(A[1]) < 1e-12 and abs(B[1]) < 1e-12
+    expected = {2: (53.2408, 80.0925, 67.2032), 3: (87.7347, -86.1827, 83.1793),
+                4: (32.2970, 79.1875, -107.8602)}
+    for i, (l, a, b) in expected.items():
+        assert abs(L[i] - l) < 2e-3 and abs(A[i] - a) < 2e-3 and abs(B[i] - b) < 2e-3
+
+
+def test_lab_gray_axis_and_monotone():
+    v = np.arange(256, dtype=np.uint8)
+    rgb = np.stack([v, v, v], axis=1)
+    L, A, B = oracle.lab_from_rgb(rgb)
+    assert np.all(np.abs(A) < 1e-9) and np.all(np.abs(B) < 1e-9)
+    assert np.all(np.diff(L) > 0)
+    # Low end is the linear segment of both transfer functions:
+    # Y = (v/255)/12.92 and L = 116 * (Y/(3*(6/29)^2) + 4/29) - 16 = (29/3)^3 * Y
+    Y = (1 / 255) / 12.92
+    assert abs(L[1] - (29 / 3) ** 3 * Y) < 1e-9
+
+
+# --------------------------------------------------------------------------
+# Grid (Sec. II-A: blocks of size r = sqrt(N/k)).
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("H,W,K,exp", [(321, 481, 400, (24, 16)), (1080, 1920, 2000, (60, 34)),
+                                       (2160, 3840, 10000, (133, 75)), (64, 96, 24, (6, 4)),
+                                       (5, 5, 25, (5, 5)), (1, 7, 1, (3, 1))])
+def test_grid_dims(H, W, K, exp):
+    assert oracle.grid_dims(H, W, K) == exp
+
+
+# --------------------------------------------------------------------------
+# Linear path (Sec. II-B; Bresenham's digital segment).
+# --------------------------------------------------------------------------
+def _check_path(p, e):
+    pts = oracle.path(p, e)
+    dx, dy = e[0] - p[0], e[1] - p[1]
+    ns = max(abs(dx), abs(dy))
+    assert len(pts) == ns + 1
+    s = {tuple(q) for q in pts}
+    assert len(s) == ns + 1
+    assert tuple(p) in s and tuple(e) in s
+    # 8-connected, one step along the major axis each time
+    steps = np.abs(np.diff(pts, axis=0))
+    if ns:
+        assert np.all(steps.max(axis=1) == 1)
+    # every pixel is a nearest lattice point to the exact segment in its
+    # major-axis column: |minor - exact| <= 1/2
+    if ns:
+        major = 0 if abs(dx) >= abs(dy) else 1
+        for q in pts:
+            t = Fraction(int(q[major] - p[major]), int(e[major] - p[major]))
+            exact = p[1 - major] + t * (e[1 - major] - p[1 - major])
+            assert abs(q[1 - major] - exact) <= Fraction(1, 2)
+    # symmetric: the same set from either end
+    back = {tuple(q) for q in oracle.path(e, p)}
+    assert back == s
+
+
+def test_path_properties_exhaustive_small():
+    for ex in range(-6, 7):
+        for ey in range(-6, 7):
+            _check_path((0, 0), (ex, ey))
+            _check_path((3, 5), (3 + ex, 5 + 2 * ey))
+
+
+def test_path_properties_random():
+    rng = np.random.default_rng(7)
+    for _ in range(300):
+        p = tuple(int(v) for v in rng.integers(0, 80, 2))
+        e = tuple(int(v) for v in rng.integers(0, 80, 2))
+        _check_path(p, e)
+
+
+# --------------------------------------------------------------------------
+# Window test (Algorithm 1: a (2r+1)x(2r+1) window centred on X_k).
+# --------------------------------------------------------------------------
+def test_window_predicate_exact():
+    rng = np.random.default_rng(3)
+    for _ in range(3000):
+        N = int(rng.integers(10, 10_000_000))
+        K = int(rng.integers(1, min(N, 20000) + 1))
+        n = int(rng.integers(1, 5000))
+        s = int(rng.integers(0, n * 4000))
+        xk = Fraction(s, n)
+        r2 = Fraction(N, K)
+        # probe the integers around the window edge
+        r = math.sqrt(N / K)
+        for v in {math.floor(xk - r) - 1, math.floor(xk - r), math.ceil(xk - r),
+                  math.floor(xk + r), math.ceil(xk + r), math.ceil(xk + r) + 1}:
+            assert oracle.in_window(v, n, s, N, K) == ((v - xk) ** 2 <= r2)
+    # huge clusters do not overflow
+    N, K = 8_294_400, 10_000
+    assert oracle.in_window(3839, N, N * 1919 + N // 2, N, K) is False
+    assert oracle.in_window(1919, N, N * 1919 + N // 2, N, K) is True
+
+
+# --------------------------------------------------------------------------
+# Distance, Eq. 1-3, on hand-worked examples.
+# --------------------------------------------------------------------------
+def _golden_solver(g, lam, gamma):
+    lab = tuple(np.array(g[c], dtype=np.float64) for c in ("L", "a", "b"))
+    s = oracle.Solver(lab, np.array(g["C"], dtype=np.float64), g["K"], m=g["m"], lam=lam,
+                      sigma=g["sigma"], gamma=gamma)
+    for c in g["clusters"]:
+        k = c["k"]
+        s.n[k], s.sx[k], s.sy[k] = c["n"], c["sx"], c["sy"]
+        s.cL[k], s.cA[k], s.cB[k] = c["color"]
+        s.ex[k], s.ey[k] = c["endpoint"]
+    return s
+
+
+def test_distance_worked_examples():
+    with open(os.path.join(GOLDEN, "distance_worked_examples.json")) as f:
+        g = json.load(f)
+    for case in g["cases"]:
+        s = _golden_solver(g, case["lambda"], case["gamma"])
+        assert s.r == 2.0
+        c = g["clusters"][case["k"]]
+        pth = oracle.path(tuple(case["p"]), tuple(c["endpoint"]))
+        assert sorted(map(tuple, pth)) == sorted(map(tuple, case["path"]))
+        D, plen = s.distance(case["p"][0], case["p"][1], case["k"])
+        assert plen == len(case["path"])
+        assert abs(D - case["D"]) <= 1e-12 * abs(case["D"]), case["name"]
+
+
+# --------------------------------------------------------------------------
+# Special case stated below Eq. 3: lambda=1, gamma=0 gives SLIC.
+# A plain SLIC, written here with numpy, must give the same labels.
+# --------------------------------------------------------------------------
+def _slic_numpy(L, A, B, K, iters, m):
+    H, W = L.shape
+    N = H * W
+    nx, ny = oracle.grid_dims(H, W, K)
+    ys, xs = np.mgrid[0:H, 0:W]
+    lab = (ys * ny // H) * nx + (xs * nx // W)
+    feats = np.stack([L, A, B], axis=-1)
+
+    def means(lab):
+        Kc = nx * ny
+        cnt = np.bincount(lab.ravel(), minlength=Kc)
+        sx = np.bincount(lab.ravel(), weights=xs.ravel(), minlength=Kc).astype(np.int64)
+        sy = np.bincount(lab.ravel(), weights=ys.ravel(), minlength=Kc).astype(np.int64)
+        col = np.stack([np.bincount(lab.ravel(), weights=feats[..., c].ravel(), minlength=Kc)
+                        for c in range(3)], axis=1)
+        return cnt, sx, sy, col
+
+    n, sx, sy, col = means(lab)
+    col = col / n[:, None]
+    for _ in range(iters):
+        best = np.full((H, W), np.inf)
+        new = lab.copy()
+        for k in range(nx * ny):
+            # window: K*(n*v - S)^2 <= N*n^2 per axis, with Python ints
+            inx = K * (n[k] * xs - sx[k]) ** 2 <= N * n[k] ** 2
+            iny = K * (n[k] * ys - sy[k]) ** 2 <= N * n[k] ** 2
+            win = inx & iny
+            dc = ((feats - col[k]) ** 2).sum(-1)
+            ds = (xs - sx[k] / n[k]) ** 2 + (ys - sy[k] / n[k]) ** 2
+            D = dc + ds * m * m * K / N
+            upd = win & (D < best)
+            best[upd] = D[upd]
+            new[upd] = k
+        lab = new
+        n2, sx2, sy2, col2 = means(lab)
+        keep = n2 > 0
+        n[keep], sx[keep], sy[keep] = n2[keep], sx2[keep], sy2[keep]
+        col[keep] = col2[keep] / n2[keep, None]
+    return lab
+
+
+def test_slic_special_case():
+    rgb, contour, _ = synth.small_image(40, 56, seed=11, n_cells=6)
+    L, A, B = oracle.lab_from_rgb(rgb)
+    K = 14
+    s = oracle.Solver((L, A, B), contour, K, lam=1.0, gamma=0.0)
+    ref = _slic_numpy(L, A, B, K, iters=4, m=10.0)
+    for it in range(4):
+        s.iterate(1)
+    # the two differ only by the order of FP64 roundings in d_s*m^2/r^2;
+    # exact ties are impossible on this noisy image
+    assert np.array_equal(s.labels, ref)
+
+
+# --------------------------------------------------------------------------
+# Constant image, no contour: D = m^2/r^2 * d_s.  With r an integer that
+# divides H and W the grid is a fixed point (cells are the Voronoi regions of
+# their centres under the window test).
+# --------------------------------------------------------------------------
+def test_constant_image_fixed_point():
+    H, W, K = 64, 96, 24  # r = 16, 6 x 4 cells of 16 x 16
+    lab = (np.full((H, W), 50.0), np.full((H, W), 10.0), np.full((H, W), -5.0))
+    s = oracle.Solver(lab, np.zeros((H, W)), K)
+    assert s.r == 16.0 and s.grid == (6, 4)
+    ys, xs = np.mgrid[0:H, 0:W]
+    cells = (ys // 16) * 6 + xs // 16
+    c0 = s.centers().copy()
+    assert np.allclose(c0[:, 0], (np.arange(24) % 6) * 16 + 7.5)
+    assert np.allclose(c0[:, 1], (np.arange(24) // 6) * 16 + 7.5)
+    for _ in range(3):
+        s.iterate(1)
+        assert np.array_equal(s.labels, cells)
+        assert np.array_equal(s.centers(), c0)
+        assert np.allclose(s.colors(), [50.0, 10.0, -5.0])
+        assert s.projections == 0
+
+
+# --------------------------------------------------------------------------
+# Contour wall: a full column with C=1 and a large gamma.  A path that
+# crosses the wall costs far more than one that does not, so no superpixel
+# straddles it (Sec. II-D: the term keeps pixels from clusters behind a
+# contour).
+# --------------------------------------------------------------------------
+def test_contour_wall_not_crossed():
+    H, W, K = 48, 64, 12  # r = 16, 4 x 3 cells
+    rng = np.random.default_rng(5)
+    rgb = rng.integers(90, 166, size=(H, W, 3)).astype(np.uint8)
+    C = np.zeros((H, W))
+    wall = 31  # cells span x in [0,16),[16,32),..; the wall is inside one cell
+    C[:, wall] = 1.0
+    lab = oracle.lab_from_rgb(rgb)
+    s = oracle.Solver(lab, C, K, gamma=1e4)
+    for _ in range(4):
+        s.iterate(1)
+        left = set(np.unique(s.labels[:, :wall]))
+        right = set(np.unique(s.labels[:, wall + 1:]))
+        assert not (left & right)
+    # with gamma=0 the same image does straddle the wall
+    s0 = oracle.Solver(lab, C, K, gamma=0.0)
+    s0.iterate(1)
+    assert set(np.unique(s0.labels[:, :wall])) & set(np.unique(s0.labels[:, wall + 1:]))
+
+
+# --------------------------------------------------------------------------
+# Brute force on tiny images: D is evaluated here, independently, for every
+# (pixel, cluster) pair without a window.  Wherever the global winner's window
+# holds the pixel, the windowed oracle must pick it.
+# --------------------------------------------------------------------------
+def _brute_D(L, A, B, C, st, K, m, lam, sigma, gamma, x, y, k):
+    H, W = L.shape
+    N = H * W
+    pts = oracle.path((x, y), (int(st["ex"][k]), int(st["ey"][k])))
+    col = np.array([st["cL"][k], st["cA"][k], st["cB"][k]])
+
+    def dc(q):
+        return ((np.array([L[q[1], q[0]], A[q[1], q[0]], B[q[1], q[0]]]) - col) ** 2).sum()
+
+    sdc = sum(dc(q) for q in pts)
+    sw = sum(1 - math.exp(-C[q[1], q[0]] ** 2 / sigma ** 2) for q in pts)
+    xk, yk = st["sx"][k] / st["n"][k], st["sy"][k] / st["n"][k]
+    ds = (x - xk) ** 2 + (y - yk) ** 2
+    return (lam * dc((x, y)) + (1 - lam) * sdc / len(pts)) * (1 + gamma * sw / len(pts)) + \
+        ds * m * m / (N / K)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_bruteforce_tiny(seed):
+    H, W, K = 24, 32, 8
+    rgb, C, _ = synth.small_image(H, W, seed=100 + seed, n_cells=5)
+    lab = oracle.lab_from_rgb(rgb)
+    s = oracle.Solver(lab, C, K)
+    s.iterate(2)
+    st = s.state()
+    s.assign()
+    N = H * W
+    checked = 0
+    for y in range(H):
+        for x in range(W):
+            Ds = [_brute_D(*lab, C, st, K, 10.0, 0.5, 0.25, s.gamma, x, y, k)
+                  for k in range(s.Keff)]
+            kbest = int(np.argmin(Ds))
+            if (K * (st["n"][kbest] * x - st["sx"][kbest]) ** 2 <= N * st["n"][kbest] ** 2 and
+                    K * (st["n"][kbest] * y - st["sy"][kbest]) ** 2 <= N * st["n"][kbest] ** 2):
+                assert s.labels[y, x] == kbest
+                checked += 1
+    assert checked > 0.6 * N
+
+
+# --------------------------------------------------------------------------
+# Update (Algorithm 1: means over S_k) against numpy reductions.
+# --------------------------------------------------------------------------
+def test_update_means():
+    rgb, C, _ = synth.small_image(60, 80, seed=21)
+    L, A, B = oracle.lab_from_rgb(rgb)
+    s = oracle.Solver((L, A, B), C, 30)
+    s.iterate(3)
+    lab = s.labels.ravel()
+    ys, xs = np.mgrid[0:60, 0:80]
+    cnt = np.bincount(lab, minlength=s.Keff)
+    nz = cnt > 0
+    assert np.array_equal(s.n[nz], cnt[nz])
+    assert np.array_equal(s.sx[nz], np.bincount(lab, weights=xs.ravel(), minlength=s.Keff)[nz]
+                          .astype(np.int64))
+    assert np.array_equal(s.sy[nz], np.bincount(lab, weights=ys.ravel(), minlength=s.Keff)[nz]
+                          .astype(np.int64))
+    for arr, plane in ((s.cL, L), (s.cA, A), (s.cB, B)):
+        ref = np.bincount(lab, weights=plane.ravel(), minlength=s.Keff)[nz] / cnt[nz]
+        assert np.allclose(arr[nz], ref, rtol=1e-12, atol=1e-12)
+
+
+# --------------------------------------------------------------------------
+# Projection, Eq. 4: a superpixel whose barycenter lies outside it.
+# --------------------------------------------------------------------------
+def test_projection_ring():
+    H, W, K = 30, 30, 4
+    lab = (np.full((H, W), 50.0), np.zeros((H, W)), np.zeros((H, W)))
+    s = oracle.Solver(lab, np.zeros((H, W)), K)
+    ys, xs = np.mgrid[0:H, 0:W]
+    # label 0: a ring around (14.5, 14.5) with a slot, label 1: everything else
+    rr = (xs - 14.5) ** 2 + (ys - 14.5) ** 2
+    ring = (rr >= 49) & (rr <= 100) & ~((xs > 14) & (ys >= 13) & (ys <= 16))
+    labels = np.where(ring, 0, 1).astype(np.int32)
+    s.labels[...] = labels
+    s.update()
+    assert s.projections >= 1
+    n, sx, sy = ring.sum(), xs[ring].sum(), ys[ring].sum()
+    assert s.n[0] == n and s.sx[0] == sx and s.sy[0] == sy
+    ex_r, ey_r = (2 * sx + n) // (2 * n), (2 * sy + n) // (2 * n)
+    assert labels[ey_r, ex_r] != 0
+    d2 = [((Fraction(int(x)) - Fraction(int(sx), int(n))) ** 2 +
+           (Fraction(int(y)) - Fraction(int(sy), int(n))) ** 2, y * W + x)
+          for y, x in zip(ys[ring], xs[ring])]
+    best = min(d2)
+    assert (s.ey[0] * W + s.ex[0]) == best[1]
+    assert labels[s.ey[0], s.ex[0]] == 0
+
+
+# --------------------------------------------------------------------------
+# Connectivity enforcement: scipy's connected-component labelling plus the
+# merge rule written out here, and the invariants the rule guarantees.
+# --------------------------------------------------------------------------
+def _connectivity_scipy(labels, K):
+    from scipy import ndimage
+
+    H, W = labels.shape
+    N = H * W
+    comp = np.full((H, W), -1, np.int64)
+    nxt = 0
+    for v in np.unique(labels):
+        cc, n = ndimage.label(labels == v)  # 4-connectivity by default
+        m = cc > 0
+        comp[m] = cc[m] - 1 + nxt
+        nxt += n
+    flat = comp.ravel()
+    seeds = np.full(nxt, N, np.int64)
+    np.minimum.at(seeds, flat, np.arange(N))
+    sizes = np.bincount(flat, minlength=nxt)
+    T = N // (4 * K)
+    order = np.argsort(seeds)
+    final = {}
+    number = {}
+    for c in order:
+        s = seeds[c]
+        if sizes[c] <= T and s != 0:
+            nb = s - 1 if s % W else s - W
+            final[c] = final[flat[nb]]
+        else:
+            final[c] = c
+            number[c] = len(number)
+    return np.array([number[final[c]] for c in flat], np.int32).reshape(H, W), len(number)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_connectivity_vs_scipy(seed):
+    rng = np.random.default_rng(seed)
+    H, W = int(rng.integers(5, 40)), int(rng.integers(5, 40))
+    base = rng.integers(0, 6, size=(H // 3 + 1, W // 3 + 1))
+    labels = np.kron(base, np.ones((3, 3), int))[:H, :W]
+    noise = rng.uniform(size=(H, W)) < 0.15
+    labels = np.where(noise, rng.integers(0, 6, size=(H, W)), labels).astype(np.int32)
+    K = int(rng.integers(2, 12))
+    out, n = oracle.connectivity(labels, K)
+    ref, nref = _connectivity_scipy(labels, K)
+    assert n == nref
+    assert np.array_equal(out, ref)
+
+
+def test_connectivity_invariants():
+    rgb, C, _ = synth.small_image(90, 120, seed=31)
+    s, out, n = oracle.solve(rgb, C, 60, iters=3)
+    from scipy import ndimage
+
+    H, W = out.shape
+    T = H * W // (4 * 60)
+    assert out.min() == 0 and out.max() == n - 1
+    first = []
+    for v in range(n):
+        m = out == v
+        _, ncc = ndimage.label(m)
+        assert ncc == 1  # every output superpixel is 4-connected
+        idx = np.flatnonzero(m.ravel())
+        first.append(idx[0])
+        if idx[0] != 0:
+            assert m.sum() > T
+    assert first == sorted(first)  # numbered in raster order of their seeds
