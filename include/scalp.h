@@ -1,0 +1,175 @@
+/*
+ * scalp.h -- C ABI of libscalp, a GB300 (sm_103a) implementation of the
+ * iterative clustering of SCALP ("Superpixels with Contour Adherence using
+ * Linear Path", Giraud, Ta, Papadakis, ICPR 2018).
+ *
+ * The problem (Algorithm 1): given an image, a number of superpixels k and a
+ * soft contour prior C in [0,1], output a superpixel decomposition S.  Each
+ * iteration assigns every pixel p to the cluster C_k = [l_k, a_k, b_k, X_k]
+ * minimising D(p, C_k) of Eq. 3 over the clusters whose (2r+1)x(2r+1) window
+ * (r = sqrt(N/k)) holds p, where D combines the CIELab colour distance along
+ * the linear path from p to the barycenter X_k (Eq. 1), the contour prior
+ * along the same path (Eq. 2) and the spatial distance; then it recomputes the
+ * cluster means and projects each barycenter that falls outside its
+ * superpixel onto the nearest pixel of that superpixel (Eq. 4).
+ *
+ * Conventions for every entry point:
+ *   - Return value: SCALP_OK (0) or a negative SCALP_E_* code.  An argument
+ *     error (SCALP_E_ARG) has no side effect.  scalp_last_error() gives text.
+ *   - Device work is enqueued on params->stream (a cudaStream_t; NULL = the
+ *     legacy default stream).  Errors of asynchronous work surface at the next
+ *     call that synchronises (scalp_labels, scalp_clusters, scalp_get_state,
+ *     scalp_debug_paths, scalp_sync).
+ *   - The caller owns every input and output buffer.  Inputs are copied into
+ *     the workspace by scalp_init and never referenced after it returns.
+ *   - The library allocates no device memory: all device buffers are carved
+ *     from params->workspace (caller-allocated, at least
+ *     scalp_workspace_bytes() bytes, 256-byte aligned), which must stay valid
+ *     until scalp_destroy().  The context itself is host memory.
+ *   - Images are row-major, pixel (x, y) at row y, column x, with integer
+ *     coordinates at pixel centres.  Labels are int32, row-major H x W.
+ *   - One context is used by one host thread at a time.
+ */
+#ifndef SCALP_H
+#define SCALP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SCALP_OK 0
+#define SCALP_E_ARG (-1)      /* invalid argument; nothing was done */
+#define SCALP_E_NOMEM (-2)    /* workspace missing or smaller than required */
+#define SCALP_E_CUDA (-3)     /* a CUDA runtime call failed */
+#define SCALP_E_TIMEOUT (-4)  /* a bounded device-side wait gave up */
+#define SCALP_E_STATE (-5)    /* call not valid in the context's state */
+#define SCALP_E_INTERNAL (-6) /* a device-side consistency check failed */
+
+#define SCALP_STORAGE_F32 0   /* Lab + contour planes stored as 4 x fp32 per pixel */
+#define SCALP_STORAGE_F16 1   /* the same planes stored as 4 x fp16 per pixel */
+
+/* Input image: 8-bit sRGB, interleaved R, G, B. */
+typedef struct {
+    int32_t H, W;          /* rows and columns, both >= 1 */
+    const uint8_t *rgb;    /* H rows of W*3 bytes */
+    int64_t rgb_stride;    /* bytes between rows; 0 means 3*W */
+    int32_t on_device;     /* 1: rgb (and the contour) are device pointers */
+} scalp_image;
+
+/* Soft contour prior C (Sec. II-E): fp32 in [0,1], 1 on a contour. */
+typedef struct {
+    const float *data;     /* H rows of W floats; NULL means C = 0 everywhere */
+    int64_t stride;        /* floats between rows; 0 means W */
+} scalp_contour;
+
+/* Parameters of Eq. 1-3; defaults of Sec. III-A3 via scalp_default_params(). */
+typedef struct {
+    float lambda;          /* Eq. 1 weight of the pixel's own colour, in [0,1]; 0.5 */
+    float sigma;           /* Eq. 2 contour scale, > 0; 0.25 */
+    float gamma;           /* Eq. 2 contour weight, >= 0; < 0 selects 2r */
+    int32_t storage;       /* SCALP_STORAGE_F32 or SCALP_STORAGE_F16 */
+    int32_t use_graph;     /* 1: replay each iteration as a CUDA graph (non-NULL stream) */
+    int32_t global_walk;   /* 1: walk every path in global memory (no shared-memory tile) */
+    void *stream;          /* cudaStream_t for all device work */
+    void *workspace;       /* device memory owned by the caller */
+    size_t workspace_bytes;
+} scalp_params;
+
+/* Sizes fixed by scalp_init. */
+typedef struct {
+    int32_t H, W, K;       /* image size and requested number of superpixels */
+    int32_t nx, ny, Keff;  /* regular grid, Keff = nx*ny clusters */
+    double r;              /* sqrt(H*W/K), the grid step and window half-size */
+    double gamma;          /* resolved Eq. 2 weight */
+    int32_t halo;          /* shared-memory halo of the assignment tiles (0: none) */
+    int32_t iterations;    /* iterations run so far */
+} scalp_info;
+
+/* Host view of the solver state: the data one iteration reads.  Arrays are
+ * caller-allocated host memory. */
+typedef struct {
+    int32_t *labels;       /* H*W current labels S */
+    int64_t *n;            /* Keff: |S_k| */
+    int64_t *sx, *sy;      /* Keff: sums of x and y over S_k; X_k = (sx/n, sy/n) */
+    double *color;         /* Keff x 3: mean (l_k, a_k, b_k) */
+    int32_t *endpoint;     /* Keff x 2: path end, X_k rounded half-up or X_k^* (Eq. 4) */
+} scalp_state;
+
+typedef struct scalp_ctx scalp_ctx;
+
+/* Fills *p with lambda=0.5, sigma=0.25, gamma=2r, FP32 storage, graphs on. */
+void scalp_default_params(scalp_params *p);
+
+/* Workspace bytes scalp_init needs for an H x W image and K superpixels
+ * (0 on invalid sizes).  Depends on p->storage only among the parameters. */
+size_t scalp_workspace_bytes(int32_t H, int32_t W, int32_t K, const scalp_params *p);
+
+/* Algorithm 1 initialisation.  Converts the image to CIELab (Sec. II-A),
+ * precomputes the per-pixel contour factor 1 - exp(-C^2/sigma^2) of Eq. 2,
+ * seeds Keff clusters on the regular grid of step r = sqrt(N/K) and labels
+ * every pixel with its grid cell.  K in [1, H*W]; m > 0 is the compactness of
+ * Eq. 3.  On success *out receives a context (free with scalp_destroy). */
+int scalp_init(scalp_ctx **out, const scalp_image *image, const scalp_contour *contour,
+               int32_t K, float m, const scalp_params *params);
+
+/* Reloads a new image and contour of the same H x W into an existing context
+ * and re-initialises the clusters, keeping K, m and the parameters. */
+int scalp_reload(scalp_ctx *ctx, const scalp_image *image, const scalp_contour *contour);
+
+/* Enqueues n >= 0 iterations of Algorithm 1: assignment by Eq. 3 over the
+ * window of each cluster (strict '<' in ascending k, so ties go to the
+ * smallest k; a pixel no window reaches keeps its label), cluster update, and
+ * the projection of Eq. 4.  Asynchronous. */
+int scalp_iterate(scalp_ctx *ctx, int32_t n);
+
+/* Writes the decomposition to out (H*W int32, host or device memory per
+ * out_on_device) and synchronises the stream.  enforce != 0 first applies
+ * the connectivity enforcement (not part of the paper): 4-connected
+ * components of equal label, each component of at most floor(N/(4K)) pixels
+ * merged into the component left of (else above) its first pixel, and the
+ * result numbered 0.. in raster order; *n_labels gets the count.  With
+ * enforce == 0 the cluster labels are returned and *n_labels = Keff. */
+int scalp_labels(scalp_ctx *ctx, int32_t *out, int32_t out_on_device, int32_t enforce,
+                 int32_t *n_labels);
+
+int scalp_get_info(const scalp_ctx *ctx, scalp_info *info);
+
+/* Copies the state to host memory (synchronises). */
+int scalp_get_state(scalp_ctx *ctx, const scalp_state *state);
+
+/* Replaces the state (checkpoint restore, or injecting a state to compute one
+ * assignment from).  Labels must be in [0, Keff), n >= 1, 0 <= sx/n <= W-1,
+ * 0 <= sy/n <= H-1 and endpoints inside the image; otherwise SCALP_E_ARG. */
+int scalp_set_state(scalp_ctx *ctx, const scalp_state *state);
+
+/* Linear paths (Sec. II-B) as the assignment kernel walks them, for checking:
+ * pairs holds M rows (px, py, ex, ey) of host int32; out_len[i] receives
+ * max(|ex-px|, |ey-py|) + 1 and out_xy[i*stride_xy .. ] the (x, y) pixels in
+ * walking order (stride_xy int32 per row, >= 2*out_len[i]).  All host memory;
+ * coordinates must lie in the image. */
+int scalp_debug_paths(scalp_ctx *ctx, const int32_t *pairs, int32_t M, int32_t *out_xy,
+                      int32_t stride_xy, int32_t *out_len);
+
+/* Per-kernel timing of the assignment kernel with CUDA events on the
+ * context's stream.  enable != 0 starts counting (and resets the totals);
+ * *ms and *launches receive the totals so far (synchronises). */
+int scalp_profile(scalp_ctx *ctx, int32_t enable, double *ms, int64_t *launches);
+
+/* Total path samples (sum of |P| over evaluated candidate pairs) of the last
+ * assignment, counted on the device when counting is enabled via
+ * scalp_count_samples(ctx, 1) (adds one atomic per tile; off by default). */
+int scalp_count_samples(scalp_ctx *ctx, int32_t enable, int64_t *samples, int64_t *pairs);
+
+/* Synchronises the context's stream and reports pending device errors. */
+int scalp_sync(scalp_ctx *ctx);
+
+const char *scalp_last_error(const scalp_ctx *ctx);
+void scalp_destroy(scalp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCALP_H */

@@ -1,0 +1,714 @@
+// scalp_api.cu -- the C ABI of libscalp (declared in include/scalp.h):
+// argument checks, workspace carving, the TMA descriptor, CUDA-graph replay
+// of one iteration, state I/O.  All device work is in the kernel files.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/scalp.h"
+#include "scalp_launch.h"
+
+using namespace scalp;
+
+namespace {
+
+thread_local std::string g_last_error;
+
+struct Layout {
+    size_t rgb, contour, plane, labels, parent, size, link, scan, scan_tmp;
+    size_t st_n, st_sx, st_sy, st_col, st_end, cdev, acc, proj;
+    size_t tile_count, tile_off, tile_cursor, tile_list, ctr, nlab, debug;
+    size_t total;
+    long long tile_cap, scan_tmp_len;
+    int n_tx, n_ty, pitch;
+};
+
+constexpr size_t ALIGN = 256;
+constexpr size_t DEBUG_BYTES = 1 << 20;
+
+size_t carve(size_t &cur, size_t bytes)
+{
+    size_t off = (cur + ALIGN - 1) & ~(ALIGN - 1);
+    cur = off + bytes;
+    return off;
+}
+
+bool grid_dims(int H, int W, int K, int &nx, int &ny, double &r)
+{
+    double N = (double)H * (double)W;
+    r = std::sqrt(N / (double)K);
+    long long gx = (long long)std::floor((double)W / r + 0.5);
+    long long gy = (long long)std::floor((double)H / r + 0.5);
+    nx = (int)std::min<long long>(std::max<long long>(gx, 1), W);
+    ny = (int)std::min<long long>(std::max<long long>(gy, 1), H);
+    return true;
+}
+
+bool sizes_ok(int H, int W, int K)
+{
+    if (H < 1 || W < 1 || K < 1) return false;
+    long long N = (long long)H * W;
+    if (N > (1LL << 30)) return false;  // int32 pixel indices with headroom
+    return K <= N;
+}
+
+Layout make_layout(int H, int W, int K, int storage)
+{
+    Layout L{};
+    long long N = (long long)H * W;
+    int nx, ny;
+    double r;
+    grid_dims(H, W, K, nx, ny, r);
+    long long Keff = (long long)nx * ny;
+    L.pitch = (W + 3) & ~3;
+    L.n_tx = (int)ceil_div_ll(W, TILE_X);
+    L.n_ty = (int)ceil_div_ll(H, TILE_Y);
+    long long n_tiles = (long long)L.n_tx * L.n_ty;
+    L.tile_cap = Keff * tiles_per_window(r, TILE_X) * tiles_per_window(r, TILE_Y);
+    L.scan_tmp_len = ccl_scan_tmp_len(N);
+    size_t elem = storage == 0 ? 16 : 8;
+    size_t cur = 0;
+    L.rgb = carve(cur, (size_t)N * 3);
+    L.contour = carve(cur, (size_t)N * 4);
+    L.plane = carve(cur, (size_t)L.pitch * H * elem);
+    L.labels = carve(cur, (size_t)N * 4);
+    L.parent = carve(cur, (size_t)N * 4);
+    L.size = carve(cur, (size_t)N * 4);
+    L.link = carve(cur, (size_t)N * 4);
+    L.scan = carve(cur, (size_t)N * 4);
+    L.scan_tmp = carve(cur, (size_t)L.scan_tmp_len * 4);
+    L.st_n = carve(cur, Keff * 8);
+    L.st_sx = carve(cur, Keff * 8);
+    L.st_sy = carve(cur, Keff * 8);
+    L.st_col = carve(cur, Keff * 16);
+    L.st_end = carve(cur, Keff * 8);
+    L.cdev = carve(cur, Keff * sizeof(ClusterDev));
+    L.acc = carve(cur, Keff * sizeof(ClusterAcc));
+    L.proj = carve(cur, Keff * 4);
+    L.tile_count = carve(cur, n_tiles * 4);
+    L.tile_off = carve(cur, (n_tiles + 1) * 4);
+    L.tile_cursor = carve(cur, n_tiles * 4);
+    L.tile_list = carve(cur, (size_t)L.tile_cap * 4);
+    L.ctr = carve(cur, sizeof(DevCounters));
+    L.nlab = carve(cur, 16);
+    L.debug = carve(cur, DEBUG_BYTES);
+    L.total = (cur + ALIGN - 1) & ~(ALIGN - 1);
+    return L;
+}
+
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
+                                    const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
+                                    const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+PFN_encodeTiled get_encode()
+{
+    static PFN_encodeTiled fn = nullptr;
+    if (!fn) {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_encodeTiled>(p);
+    }
+    return fn;
+}
+
+}  // namespace
+
+struct scalp_ctx {
+    int H, W, K;
+    long long N;
+    float m;
+    scalp_params p;
+    int nx, ny, Keff;
+    double r, gamma;
+    cudaStream_t st;
+    unsigned char *ws;
+    Layout L;
+    SolveArgs a;
+    CclBuffers ccl;
+    CUtensorMap tmap;
+    bool staged;
+    size_t smem;
+    cudaGraphExec_t gexec;
+    bool graph_valid;
+    int graph_n;           // iterations in the captured graph
+    bool graph_prof;       // graph records the profiling events
+    bool profiling;
+    std::vector<cudaEvent_t> ev_pool;  // pairs around each assignment launch
+    int prof_pending;      // event pairs recorded and not yet read
+    double prof_ms;
+    long long prof_launches;
+    int iterations;
+    std::string err;
+};
+
+namespace {
+
+int fail(scalp_ctx *c, int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c) c->err = buf;
+    g_last_error = buf;
+    return code;
+}
+
+int cuda_check(scalp_ctx *c, cudaError_t e, const char *what)
+{
+    if (e == cudaSuccess) return SCALP_OK;
+    return fail(c, SCALP_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+int launch_check(scalp_ctx *c, const char *what) { return cuda_check(c, cudaGetLastError(), what); }
+
+// Reads the device counters after a synchronisation; reports device-side failures.
+int device_status(scalp_ctx *c)
+{
+    DevCounters h;
+    int rc = cuda_check(c, cudaMemcpyAsync(&h, c->a.ctr, sizeof h, cudaMemcpyDeviceToHost, c->st),
+                        "read device counters");
+    if (rc) return rc;
+    rc = cuda_check(c, cudaStreamSynchronize(c->st), "synchronise");
+    if (rc) return rc;
+    if (h.timeout) return fail(c, SCALP_E_TIMEOUT, "a bounded device-side wait gave up");
+    if (h.error) return fail(c, SCALP_E_INTERNAL, "device-side check failed (code %d)", h.error);
+    return SCALP_OK;
+}
+
+int load_inputs(scalp_ctx *c, const scalp_image *img, const scalp_contour *con)
+{
+    const uint8_t *rgb = img->rgb;
+    long long rs = img->rgb_stride ? img->rgb_stride : 3LL * c->W;
+    const float *cp = con ? con->data : nullptr;
+    long long cs = (con && con->stride) ? con->stride : c->W;
+    int rc;
+    if (!img->on_device) {
+        uint8_t *d_rgb = c->ws + c->L.rgb;
+        rc = cuda_check(c, cudaMemcpy2DAsync(d_rgb, 3 * (size_t)c->W, rgb, (size_t)rs, 3 * (size_t)c->W,
+                                             c->H, cudaMemcpyHostToDevice, c->st),
+                        "copy image to device");
+        if (rc) return rc;
+        rgb = d_rgb;
+        rs = 3LL * c->W;
+        if (cp) {
+            float *d_c = reinterpret_cast<float *>(c->ws + c->L.contour);
+            rc = cuda_check(c, cudaMemcpy2DAsync(d_c, 4 * (size_t)c->W, cp, 4 * (size_t)cs,
+                                                 4 * (size_t)c->W, c->H, cudaMemcpyHostToDevice, c->st),
+                            "copy contour to device");
+            if (rc) return rc;
+            cp = d_c;
+            cs = c->W;
+        }
+    }
+    rc = cuda_check(c, cudaMemsetAsync(c->a.acc, 0, sizeof(ClusterAcc) * c->Keff, c->st), "memset");
+    if (rc) return rc;
+    rc = cuda_check(c, cudaMemsetAsync(c->a.tile_count, 0, sizeof(int) * c->L.n_tx * c->L.n_ty, c->st),
+                    "memset");
+    if (rc) return rc;
+    rc = cuda_check(c, cudaMemsetAsync(c->a.ctr, 0, sizeof(DevCounters), c->st), "memset");
+    if (rc) return rc;
+    void *plane = c->ws + c->L.plane;
+    launch_setup(c->a, rgb, rs, cp, cs, c->p.storage, plane, c->st);
+    launch_accumulate(c->a, c->st);
+    launch_finalize(c->a, c->st);
+    launch_project(c->a, 1, c->st);
+    launch_derive(c->a, c->st);
+    c->iterations = 0;
+    return launch_check(c, "initialisation kernels");
+}
+
+int validate_image(const scalp_image *img, const scalp_contour *con, const char **why)
+{
+    if (!img || !img->rgb) { *why = "image or image->rgb is NULL"; return 0; }
+    if (img->rgb_stride != 0 && img->rgb_stride < 3LL * img->W) { *why = "rgb_stride < 3*W"; return 0; }
+    if (con && con->data && con->stride != 0 && con->stride < img->W) { *why = "contour stride < W"; return 0; }
+    return 1;
+}
+
+int ensure_events(scalp_ctx *c, size_t pairs)
+{
+    while (c->ev_pool.size() < 2 * pairs) {
+        cudaEvent_t e;
+        int rc = cuda_check(c, cudaEventCreate(&e), "create event");
+        if (rc) return rc;
+        c->ev_pool.push_back(e);
+    }
+    return SCALP_OK;
+}
+
+// Adds the durations of the recorded assignment launches to the totals.
+int harvest_profile(scalp_ctx *c)
+{
+    if (c->prof_pending == 0) return SCALP_OK;
+    int rc = cuda_check(c, cudaStreamSynchronize(c->st), "synchronise");
+    if (rc) return rc;
+    for (int i = 0; i < c->prof_pending; ++i) {
+        float t = 0.f;
+        rc = cuda_check(c, cudaEventElapsedTime(&t, c->ev_pool[2 * i], c->ev_pool[2 * i + 1]),
+                        "event time");
+        if (rc) return rc;
+        c->prof_ms += t;
+        c->prof_launches += 1;
+    }
+    c->prof_pending = 0;
+    return SCALP_OK;
+}
+
+// One iteration of Algorithm 1; with profiling, event pair `slot` brackets
+// the assignment kernel.
+void enqueue_iteration(scalp_ctx *c, int slot)
+{
+    if (c->profiling) cudaEventRecord(c->ev_pool[2 * slot], c->st);
+    launch_assign(c->a, c->p.storage, c->staged, c->tmap, c->smem, c->st);
+    if (c->profiling) cudaEventRecord(c->ev_pool[2 * slot + 1], c->st);
+    launch_finalize(c->a, c->st);
+    launch_project(c->a, 0, c->st);
+    launch_derive(c->a, c->st);
+}
+
+}  // namespace
+
+extern "C" {
+
+void scalp_default_params(scalp_params *p)
+{
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->lambda = 0.5f;
+    p->sigma = 0.25f;
+    p->gamma = -1.0f;
+    p->storage = SCALP_STORAGE_F32;
+    p->use_graph = 1;
+    p->global_walk = 0;
+}
+
+size_t scalp_workspace_bytes(int32_t H, int32_t W, int32_t K, const scalp_params *p)
+{
+    if (!sizes_ok(H, W, K)) return 0;
+    int storage = p ? p->storage : 0;
+    if (storage != 0 && storage != 1) return 0;
+    return make_layout(H, W, K, storage).total;
+}
+
+int scalp_init(scalp_ctx **out, const scalp_image *image, const scalp_contour *contour, int32_t K,
+               float m, const scalp_params *params)
+{
+    const char *why = nullptr;
+    if (!out) return fail(nullptr, SCALP_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (!params) return fail(nullptr, SCALP_E_ARG, "params is NULL");
+    if (!validate_image(image, contour, &why)) return fail(nullptr, SCALP_E_ARG, "%s", why);
+    if (!sizes_ok(image->H, image->W, K))
+        return fail(nullptr, SCALP_E_ARG, "need H, W >= 1, H*W <= 2^30 and 1 <= K <= H*W");
+    if (!(m > 0.0f) || !std::isfinite(m)) return fail(nullptr, SCALP_E_ARG, "m must be > 0");
+    if (!(params->lambda >= 0.0f && params->lambda <= 1.0f))
+        return fail(nullptr, SCALP_E_ARG, "lambda must be in [0, 1]");
+    if (!(params->sigma > 0.0f) || !std::isfinite(params->sigma))
+        return fail(nullptr, SCALP_E_ARG, "sigma must be > 0");
+    if (!std::isfinite(params->gamma)) return fail(nullptr, SCALP_E_ARG, "gamma must be finite");
+    if (params->storage != 0 && params->storage != 1)
+        return fail(nullptr, SCALP_E_ARG, "storage must be SCALP_STORAGE_F32 or _F16");
+    const int H = image->H, W = image->W;
+    Layout L = make_layout(H, W, K, params->storage);
+    if (!params->workspace || params->workspace_bytes < L.total)
+        return fail(nullptr, SCALP_E_NOMEM, "workspace of %zu bytes needed, %zu given", L.total,
+                    params->workspace ? params->workspace_bytes : (size_t)0);
+    if (reinterpret_cast<uintptr_t>(params->workspace) % ALIGN)
+        return fail(nullptr, SCALP_E_ARG, "workspace must be 256-byte aligned");
+
+    scalp_ctx *c = new (std::nothrow) scalp_ctx();
+    if (!c) return fail(nullptr, SCALP_E_NOMEM, "host allocation failed");
+    c->H = H; c->W = W; c->K = K; c->N = (long long)H * W; c->m = m;
+    c->p = *params;
+    grid_dims(H, W, K, c->nx, c->ny, c->r);
+    c->Keff = c->nx * c->ny;
+    c->gamma = params->gamma < 0 ? 2.0 * c->r : (double)params->gamma;
+    c->st = reinterpret_cast<cudaStream_t>(params->stream);
+    c->ws = reinterpret_cast<unsigned char *>(params->workspace);
+    c->L = L;
+
+    SolveArgs &a = c->a;
+    std::memset(&a, 0, sizeof a);
+    a.H = H; a.W = W; a.K = K; a.Keff = c->Keff; a.nx = c->nx; a.ny = c->ny; a.N = c->N;
+    a.r = c->r;
+    a.lam = params->lambda;
+    a.gamma = (float)c->gamma;
+    a.sigma = params->sigma;
+    a.ms2 = (float)((double)m * (double)m * (double)K / (double)c->N);  // m^2 / r^2
+    a.n_tx = L.n_tx; a.n_ty = L.n_ty;
+    a.pitch = L.pitch;
+    a.plane32 = params->storage == 0 ? reinterpret_cast<const float4 *>(c->ws + L.plane) : nullptr;
+    a.plane16 = params->storage == 1 ? reinterpret_cast<const uint2 *>(c->ws + L.plane) : nullptr;
+    a.labels = reinterpret_cast<int *>(c->ws + L.labels);
+    a.st_n = reinterpret_cast<long long *>(c->ws + L.st_n);
+    a.st_sx = reinterpret_cast<long long *>(c->ws + L.st_sx);
+    a.st_sy = reinterpret_cast<long long *>(c->ws + L.st_sy);
+    a.st_col = reinterpret_cast<float4 *>(c->ws + L.st_col);
+    a.st_end = reinterpret_cast<int2 *>(c->ws + L.st_end);
+    a.cdev = reinterpret_cast<ClusterDev *>(c->ws + L.cdev);
+    a.acc = reinterpret_cast<ClusterAcc *>(c->ws + L.acc);
+    a.proj_list = reinterpret_cast<int *>(c->ws + L.proj);
+    a.tile_count = reinterpret_cast<int *>(c->ws + L.tile_count);
+    a.tile_off = reinterpret_cast<int *>(c->ws + L.tile_off);
+    a.tile_cursor = reinterpret_cast<int *>(c->ws + L.tile_cursor);
+    a.tile_list = reinterpret_cast<int *>(c->ws + L.tile_list);
+    a.tile_cap = L.tile_cap;
+    a.ctr = reinterpret_cast<DevCounters *>(c->ws + L.ctr);
+    c->ccl.parent = reinterpret_cast<int *>(c->ws + L.parent);
+    c->ccl.size = reinterpret_cast<int *>(c->ws + L.size);
+    c->ccl.link = reinterpret_cast<int *>(c->ws + L.link);
+    c->ccl.scan = reinterpret_cast<int *>(c->ws + L.scan);
+    c->ccl.scan_tmp = reinterpret_cast<int *>(c->ws + L.scan_tmp);
+    c->ccl.scan_tmp_len = L.scan_tmp_len;
+
+    // Shared-memory tile: halo round(r) + margin holds every path whose end is
+    // the rounded barycenter of a cluster whose window holds the pixel.
+    int halo = (int)std::floor(c->r + 0.5) + HALO_MARGIN;
+    if (params->storage == 1) halo = (halo + 1) & ~1;  // even start column for 8-byte TMA
+    int BX = TILE_X + 2 * halo, BY = TILE_Y + 2 * halo;
+    size_t smem = assign_smem_bytes(halo, params->storage);
+    c->staged = !params->global_walk && BX <= 256 && BY <= 256 && smem <= 227 * 1024;
+    PFN_encodeTiled enc = c->staged ? get_encode() : nullptr;
+    if (c->staged && !enc) c->staged = false;
+    if (c->staged) {
+        CUresult r;
+        if (params->storage == 0) {
+            cuuint64_t dims[3] = {4, (cuuint64_t)W, (cuuint64_t)H};
+            cuuint64_t strides[2] = {16, (cuuint64_t)L.pitch * 16};
+            cuuint32_t box[3] = {4, (cuuint32_t)BX, (cuuint32_t)BY};
+            cuuint32_t es[3] = {1, 1, 1};
+            r = enc(&c->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->ws + L.plane, dims, strides, box,
+                    es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        } else {
+            cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
+            cuuint64_t strides[1] = {(cuuint64_t)L.pitch * 8};
+            cuuint32_t box[2] = {(cuuint32_t)BX, (cuuint32_t)BY};
+            cuuint32_t es[2] = {1, 1};
+            r = enc(&c->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, c->ws + L.plane, dims, strides, box,
+                    es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        }
+        if (r != CUDA_SUCCESS) c->staged = false;
+    }
+    if (!c->staged) {
+        halo = 0;
+        std::memset(&c->tmap, 0, sizeof c->tmap);
+    }
+    a.halo = halo;
+    c->smem = assign_smem_bytes(halo, params->storage);
+    int rc = cuda_check(c, assign_configure(params->storage, c->staged, c->smem), "configure kernel");
+    if (rc == SCALP_OK) rc = load_inputs(c, image, contour);
+    if (rc != SCALP_OK) {
+        delete c;
+        return rc;
+    }
+    *out = c;
+    return SCALP_OK;
+}
+
+int scalp_reload(scalp_ctx *c, const scalp_image *image, const scalp_contour *contour)
+{
+    const char *why = nullptr;
+    if (!c) return fail(nullptr, SCALP_E_ARG, "ctx is NULL");
+    if (!validate_image(image, contour, &why)) return fail(c, SCALP_E_ARG, "%s", why);
+    if (image->H != c->H || image->W != c->W)
+        return fail(c, SCALP_E_ARG, "reload needs the same image size");
+    return load_inputs(c, image, contour);
+}
+
+int scalp_iterate(scalp_ctx *c, int32_t n)
+{
+    if (!c) return fail(nullptr, SCALP_E_ARG, "ctx is NULL");
+    if (n < 0) return fail(c, SCALP_E_ARG, "n must be >= 0");
+    if (n == 0) return SCALP_OK;
+    int rc;
+    if (c->profiling) {
+        rc = harvest_profile(c);  // the events are about to be re-recorded
+        if (rc) return rc;
+        rc = ensure_events(c, (size_t)n);
+        if (rc) return rc;
+    }
+    const bool graphs = c->p.use_graph && c->st != nullptr;
+    if (graphs && !(c->graph_valid && c->graph_n == n && c->graph_prof == c->profiling)) {
+        if (c->graph_valid) {
+            cudaGraphExecDestroy(c->gexec);
+            c->graph_valid = false;
+        }
+        cudaGraph_t g;
+        rc = cuda_check(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal),
+                        "begin capture");
+        if (rc) return rc;
+        for (int i = 0; i < n; ++i) enqueue_iteration(c, i);
+        cudaError_t le = cudaGetLastError();
+        rc = cuda_check(c, cudaStreamEndCapture(c->st, &g), "end capture");
+        if (rc) return rc;
+        if (le != cudaSuccess) {
+            cudaGraphDestroy(g);
+            return cuda_check(c, le, "capture iterations");
+        }
+        rc = cuda_check(c, cudaGraphInstantiate(&c->gexec, g, 0), "instantiate graph");
+        cudaGraphDestroy(g);
+        if (rc) return rc;
+        c->graph_valid = true;
+        c->graph_n = n;
+        c->graph_prof = c->profiling;
+    }
+    if (graphs) {
+        rc = cuda_check(c, cudaGraphLaunch(c->gexec, c->st), "launch graph");
+        if (rc) return rc;
+    } else {
+        for (int i = 0; i < n; ++i) enqueue_iteration(c, i);
+        rc = launch_check(c, "iteration kernels");
+        if (rc) return rc;
+    }
+    if (c->profiling) c->prof_pending = n;
+    c->iterations += n;
+    return SCALP_OK;
+}
+
+int scalp_labels(scalp_ctx *c, int32_t *out, int32_t out_on_device, int32_t enforce,
+                 int32_t *n_labels)
+{
+    if (!c) return fail(nullptr, SCALP_E_ARG, "ctx is NULL");
+    if (!out) return fail(c, SCALP_E_ARG, "out is NULL");
+    int rc;
+    int nlab = c->Keff;
+    size_t bytes = sizeof(int) * (size_t)c->N;
+    if (enforce) {
+        int *dst = out_on_device ? out : c->ccl.link;  // link is free once resolved
+        int *d_nlab = reinterpret_cast<int *>(c->ws + c->L.nlab);
+        if (out_on_device) {
+            // the output must not alias a buffer the enforcement still reads
+            launch_ccl(c->a.labels, c->H, c->W, c->K, dst, c->ccl, d_nlab, c->a.ctr, c->st);
+        } else {
+            launch_ccl(c->a.labels, c->H, c->W, c->K, dst, c->ccl, d_nlab, c->a.ctr, c->st);
+            rc = cuda_check(c, cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->st),
+                            "copy labels");
+            if (rc) return rc;
+        }
+        rc = launch_check(c, "connectivity kernels");
+        if (rc) return rc;
+        rc = cuda_check(c, cudaMemcpyAsync(&nlab, d_nlab, sizeof(int), cudaMemcpyDeviceToHost, c->st),
+                        "copy label count");
+        if (rc) return rc;
+    } else {
+        rc = cuda_check(c, cudaMemcpyAsync(out, c->a.labels, bytes,
+                                           out_on_device ? cudaMemcpyDeviceToDevice
+                                                         : cudaMemcpyDeviceToHost,
+                                           c->st),
+                        "copy labels");
+        if (rc) return rc;
+    }
+    rc = device_status(c);
+    if (rc) return rc;
+    if (n_labels) *n_labels = nlab;
+    return SCALP_OK;
+}
+
+int scalp_get_info(const scalp_ctx *c, scalp_info *info)
+{
+    if (!c || !info) return fail(nullptr, SCALP_E_ARG, "ctx or info is NULL");
+    info->H = c->H; info->W = c->W; info->K = c->K;
+    info->nx = c->nx; info->ny = c->ny; info->Keff = c->Keff;
+    info->r = c->r; info->gamma = c->gamma;
+    info->halo = c->a.halo;
+    info->iterations = c->iterations;
+    return SCALP_OK;
+}
+
+int scalp_get_state(scalp_ctx *c, const scalp_state *s)
+{
+    if (!c || !s) return fail(nullptr, SCALP_E_ARG, "ctx or state is NULL");
+    if (!s->labels || !s->n || !s->sx || !s->sy || !s->color || !s->endpoint)
+        return fail(c, SCALP_E_ARG, "state arrays must all be given");
+    const size_t K = c->Keff;
+    std::vector<float4> col(K);
+    std::vector<int2> end(K);
+    int rc = 0;
+    rc = rc ? rc : cuda_check(c, cudaMemcpyAsync(s->labels, c->a.labels, 4 * (size_t)c->N,
+                                                 cudaMemcpyDeviceToHost, c->st), "copy state");
+    rc = rc ? rc : cuda_check(c, cudaMemcpyAsync(s->n, c->a.st_n, 8 * K, cudaMemcpyDeviceToHost, c->st), "copy state");
+    rc = rc ? rc : cuda_check(c, cudaMemcpyAsync(s->sx, c->a.st_sx, 8 * K, cudaMemcpyDeviceToHost, c->st), "copy state");
+    rc = rc ? rc : cuda_check(c, cudaMemcpyAsync(s->sy, c->a.st_sy, 8 * K, cudaMemcpyDeviceToHost, c->st), "copy state");
+    rc = rc ? rc : cuda_check(c, cudaMemcpyAsync(col.data(), c->a.st_col, 16 * K, cudaMemcpyDeviceToHost, c->st), "copy state");
+    rc = rc ? rc : cuda_check(c, cudaMemcpyAsync(end.data(), c->a.st_end, 8 * K, cudaMemcpyDeviceToHost, c->st), "copy state");
+    if (rc) return rc;
+    rc = device_status(c);
+    if (rc) return rc;
+    for (size_t k = 0; k < K; ++k) {
+        s->color[3 * k] = col[k].x;
+        s->color[3 * k + 1] = col[k].y;
+        s->color[3 * k + 2] = col[k].z;
+        s->endpoint[2 * k] = end[k].x;
+        s->endpoint[2 * k + 1] = end[k].y;
+    }
+    return SCALP_OK;
+}
+
+int scalp_set_state(scalp_ctx *c, const scalp_state *s)
+{
+    if (!c || !s) return fail(nullptr, SCALP_E_ARG, "ctx or state is NULL");
+    if (!s->labels || !s->n || !s->sx || !s->sy || !s->color || !s->endpoint)
+        return fail(c, SCALP_E_ARG, "state arrays must all be given");
+    const size_t K = c->Keff;
+    for (long long p = 0; p < c->N; ++p)
+        if (s->labels[p] < 0 || s->labels[p] >= c->Keff)
+            return fail(c, SCALP_E_ARG, "label %d at pixel %lld out of range", s->labels[p], p);
+    std::vector<float4> col(K);
+    std::vector<int2> end(K);
+    for (size_t k = 0; k < K; ++k) {
+        long long n = s->n[k];
+        if (n < 1 || n > c->N || s->sx[k] < 0 || s->sy[k] < 0 || s->sx[k] > (long long)(c->W - 1) * n ||
+            s->sy[k] > (long long)(c->H - 1) * n)
+            return fail(c, SCALP_E_ARG, "cluster %zu: bad n / coordinate sums", k);
+        int ex = s->endpoint[2 * k], ey = s->endpoint[2 * k + 1];
+        if (ex < 0 || ex >= c->W || ey < 0 || ey >= c->H)
+            return fail(c, SCALP_E_ARG, "cluster %zu: endpoint outside the image", k);
+        double L = s->color[3 * k], A = s->color[3 * k + 1], B = s->color[3 * k + 2];
+        if (!std::isfinite(L) || !std::isfinite(A) || !std::isfinite(B))
+            return fail(c, SCALP_E_ARG, "cluster %zu: colour not finite", k);
+        col[k] = make_float4((float)L, (float)A, (float)B, 0.f);
+        end[k] = make_int2(ex, ey);
+    }
+    int rc = 0;
+    rc = rc ? rc : cuda_check(c, cudaMemcpyAsync(c->a.labels, s->labels, 4 * (size_t)c->N,
+                                                 cudaMemcpyHostToDevice, c->st), "copy state");
+    rc = rc ? rc : cuda_check(c, cudaMemcpyAsync(c->a.st_n, s->n, 8 * K, cudaMemcpyHostToDevice, c->st), "copy state");
+    rc = rc ? rc : cuda_check(c, cudaMemcpyAsync(c->a.st_sx, s->sx, 8 * K, cudaMemcpyHostToDevice, c->st), "copy state");
+    rc = rc ? rc : cuda_check(c, cudaMemcpyAsync(c->a.st_sy, s->sy, 8 * K, cudaMemcpyHostToDevice, c->st), "copy state");
+    rc = rc ? rc : cuda_check(c, cudaMemcpyAsync(c->a.st_col, col.data(), 16 * K, cudaMemcpyHostToDevice, c->st), "copy state");
+    rc = rc ? rc : cuda_check(c, cudaMemcpyAsync(c->a.st_end, end.data(), 8 * K, cudaMemcpyHostToDevice, c->st), "copy state");
+    rc = rc ? rc : cuda_check(c, cudaMemsetAsync(c->a.acc, 0, sizeof(ClusterAcc) * K, c->st), "memset");
+    if (rc) return rc;
+    launch_derive(c->a, c->st);
+    rc = launch_check(c, "derive kernels");
+    if (rc) return rc;
+    // the host vectors must outlive the copies
+    return device_status(c);
+}
+
+int scalp_debug_paths(scalp_ctx *c, const int32_t *pairs, int32_t M, int32_t *out_xy,
+                      int32_t stride_xy, int32_t *out_len)
+{
+    if (!c) return fail(nullptr, SCALP_E_ARG, "ctx is NULL");
+    if (M < 0 || (M > 0 && (!pairs || !out_xy || !out_len)) || stride_xy < 2)
+        return fail(c, SCALP_E_ARG, "bad debug_paths arguments");
+    for (int i = 0; i < M; ++i) {
+        const int32_t *q = pairs + 4 * (size_t)i;
+        if (q[0] < 0 || q[0] >= c->W || q[2] < 0 || q[2] >= c->W || q[1] < 0 || q[1] >= c->H ||
+            q[3] < 0 || q[3] >= c->H)
+            return fail(c, SCALP_E_ARG, "pair %d outside the image", i);
+    }
+    const size_t per = (size_t)(4 + stride_xy + 1) * 4;
+    const int chunk = (int)std::max<size_t>(1, DEBUG_BYTES / per);
+    if ((size_t)chunk * per > DEBUG_BYTES) return fail(c, SCALP_E_ARG, "stride_xy too large");
+    int *d_pairs = reinterpret_cast<int *>(c->ws + c->L.debug);
+    int *d_xy = d_pairs + 4 * (size_t)chunk;
+    int *d_len = d_xy + (size_t)chunk * stride_xy;
+    for (int b = 0; b < M; b += chunk) {
+        int m = std::min(chunk, M - b);
+        int rc = cuda_check(c, cudaMemcpyAsync(d_pairs, pairs + 4 * (size_t)b, 16 * (size_t)m,
+                                               cudaMemcpyHostToDevice, c->st), "copy pairs");
+        if (rc) return rc;
+        launch_debug_paths(d_pairs, m, d_xy, stride_xy, d_len, c->W, c->st);
+        rc = launch_check(c, "debug kernel");
+        if (rc) return rc;
+        rc = cuda_check(c, cudaMemcpyAsync(out_xy + (size_t)b * stride_xy, d_xy,
+                                           4 * (size_t)m * stride_xy, cudaMemcpyDeviceToHost, c->st),
+                        "copy paths");
+        if (rc) return rc;
+        rc = cuda_check(c, cudaMemcpyAsync(out_len + b, d_len, 4 * (size_t)m, cudaMemcpyDeviceToHost,
+                                           c->st), "copy lengths");
+        if (rc) return rc;
+        rc = cuda_check(c, cudaStreamSynchronize(c->st), "synchronise");
+        if (rc) return rc;
+    }
+    return SCALP_OK;
+}
+
+int scalp_profile(scalp_ctx *c, int32_t enable, double *ms, int64_t *launches)
+{
+    if (!c) return fail(nullptr, SCALP_E_ARG, "ctx is NULL");
+    int rc = harvest_profile(c);
+    if (rc) return rc;
+    if (ms) *ms = c->prof_ms;
+    if (launches) *launches = c->prof_launches;
+    if (enable >= 0) {
+        bool on = enable != 0;
+        if (on) {
+            c->prof_ms = 0;
+            c->prof_launches = 0;
+        }
+        c->profiling = on;
+    }
+    return SCALP_OK;
+}
+
+int scalp_count_samples(scalp_ctx *c, int32_t enable, int64_t *samples, int64_t *pairs)
+{
+    if (!c) return fail(nullptr, SCALP_E_ARG, "ctx is NULL");
+    DevCounters h;
+    int rc = cuda_check(c, cudaMemcpyAsync(&h, c->a.ctr, sizeof h, cudaMemcpyDeviceToHost, c->st),
+                        "read counters");
+    if (rc) return rc;
+    rc = cuda_check(c, cudaStreamSynchronize(c->st), "synchronise");
+    if (rc) return rc;
+    if (samples) *samples = (int64_t)h.samples;
+    if (pairs) *pairs = (int64_t)h.pairs;
+    if (enable >= 0) {
+        int on = enable != 0;
+        if (on) {
+            unsigned long long z[2] = {0, 0};
+            rc = cuda_check(c, cudaMemcpyAsync(&c->a.ctr->samples, z, sizeof z, cudaMemcpyHostToDevice,
+                                               c->st), "reset counters");
+            if (rc) return rc;
+            rc = cuda_check(c, cudaStreamSynchronize(c->st), "synchronise");
+            if (rc) return rc;
+        }
+        if (c->a.count_samples != on) {
+            c->a.count_samples = on;
+            if (c->graph_valid) {
+                cudaGraphExecDestroy(c->gexec);
+                c->graph_valid = false;
+            }
+        }
+    }
+    return SCALP_OK;
+}
+
+int scalp_sync(scalp_ctx *c)
+{
+    if (!c) return fail(nullptr, SCALP_E_ARG, "ctx is NULL");
+    int rc = launch_check(c, "pending launch");
+    if (rc) return rc;
+    return device_status(c);
+}
+
+const char *scalp_last_error(const scalp_ctx *c)
+{
+    if (c) return c->err.c_str();
+    return g_last_error.c_str();
+}
+
+void scalp_destroy(scalp_ctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->st);
+    if (c->graph_valid) cudaGraphExecDestroy(c->gexec);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    delete c;
+}
+
+}  // extern "C"

@@ -1,0 +1,258 @@
+// scalp_internal.cuh -- device data layout and helpers shared by the libscalp
+// kernels (never by the CPU oracle).
+#pragma once
+
+#include <cuda.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace scalp {
+
+// Assignment tile: a CTA labels TILE_X x TILE_Y pixels.  Each warp owns an
+// 8 x 4 block of them (one pixel per lane), so the paths a warp walks
+// together start close to one another and have similar lengths.
+constexpr int TILE_X = 32;
+constexpr int TILE_Y = 16;
+constexpr int ASSIGN_THREADS = TILE_X * TILE_Y;  // 512, one pixel per thread
+constexpr int WARP_BLOCK_X = 8;
+constexpr int WARP_BLOCK_Y = 4;
+// Candidate clusters of one tile kept in shared memory per pass.
+constexpr int MAX_TILE_CANDIDATES = 64;
+// Extra halo beyond round(r) so that endpoints projected by Eq. 4 a pixel or
+// two from the barycenter still walk in shared memory.
+constexpr int HALO_MARGIN = 2;
+// Colour sums are kept as integers: value * 2^COLOR_FRAC_BITS, rounded.
+constexpr int COLOR_FRAC_BITS = 24;
+
+// What the assignment kernel reads about one cluster (48 bytes).
+struct ClusterDev {
+    float L, a, b;           // mean CIELab colour
+    float xk, yk;            // barycenter X_k
+    int ex, ey;              // path endpoint: X_k rounded half-up, or X_k^* (Eq. 4)
+    int xlo, xhi, ylo, yhi;  // window of X_k, clipped to the image (inclusive)
+    int pad;
+};
+static_assert(sizeof(ClusterDev) == 48, "ClusterDev layout");
+
+// Per-cluster integer sums accumulated by one assignment (64 bytes).
+struct ClusterAcc {
+    unsigned long long n, sx, sy;  // count and coordinate sums
+    unsigned long long sL, sa, sb; // two's-complement sums of fixed-point colour
+    unsigned long long pad0, pad1;
+};
+
+// Counters and flags on the device.
+struct DevCounters {
+    int nproj;        // clusters queued for projection in this update
+    int orphans;      // pixels no window reached in the last assignment
+    int error;        // nonzero: a device-side check failed (code below)
+    int timeout;      // nonzero: a bounded wait gave up
+    unsigned long long samples;  // optional: path samples of the last assignment
+    unsigned long long pairs;    // optional: (pixel, cluster) pairs evaluated
+};
+constexpr int ERR_TILE_LIST_OVERFLOW = 1;
+constexpr int ERR_BAD_LABEL = 2;
+constexpr int ERR_CCL_CHAIN = 3;
+
+// Everything the per-iteration kernels need, by value.
+struct SolveArgs {
+    int H, W, K, Keff, nx, ny;
+    long long N;
+    double r;          // sqrt(N/K)
+    float lam, gamma, sigma, ms2;  // ms2 = m^2 / r^2
+    int n_tx, n_ty;    // tiles
+    int halo;          // shared-memory halo (0: global-memory walk)
+    int pitch;         // plane row pitch in pixels (>= W, multiple of 4)
+    int count_samples;
+    const float4 *plane32;   // (L, a, b, w) per pixel, row pitch `pitch` [FP32 storage]
+    const uint2 *plane16;    // the same as 4 x fp16                   [FP16 storage]
+    int *labels;
+    long long *st_n, *st_sx, *st_sy;   // cluster state
+    float4 *st_col;
+    int2 *st_end;
+    ClusterDev *cdev;
+    ClusterAcc *acc;
+    int *proj_list;
+    int *tile_count, *tile_off, *tile_cursor, *tile_list;
+    long long tile_cap;
+    DevCounters *ctr;
+};
+
+__device__ __forceinline__ float4 load_f16x4(const uint2 *p)
+{
+    uint2 u = *p;
+    __half2 lo = *reinterpret_cast<__half2 *>(&u.x);
+    __half2 hi = *reinterpret_cast<__half2 *>(&u.y);
+    float2 a = __half22float2(lo), b = __half22float2(hi);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+template <typename T>
+__device__ __forceinline__ float4 fetch_sample(const T *q);
+template <>
+__device__ __forceinline__ float4 fetch_sample<float4>(const float4 *q) { return *q; }
+template <>
+__device__ __forceinline__ float4 fetch_sample<uint2>(const uint2 *q) { return load_f16x4(q); }
+
+// The linear path of Sec. II-B between pixels p and e, walked from the
+// lexicographically smaller end (x, then y) so the pixel set does not depend
+// on the direction.  With ns = max(|dx|,|dy|) steps along the major axis, step
+// i moves the minor coordinate by floor((2*i*d_minor + ns) / (2*ns)), i.e.
+// i*d_minor/ns rounded half-up: the incremental integer form below keeps
+// e = (2*i*d_minor + ns) mod 2*ns.
+struct PathSetup {
+    int ax, ay;        // start
+    int ns, dmin;      // steps along the major axis, minor extent
+    int major_sgn_y;   // for y-major paths: +1 / -1 direction of y; 0 for x-major
+    int minor_sgn;     // direction of the minor axis (+1/-1)
+    bool xmajor;
+};
+
+__device__ __forceinline__ PathSetup path_setup(int px, int py, int ex, int ey)
+{
+    PathSetup s;
+    int ax, ay, bx, by;
+    if (px < ex || (px == ex && py <= ey)) { ax = px; ay = py; bx = ex; by = ey; }
+    else { ax = ex; ay = ey; bx = px; by = py; }
+    int dx = bx - ax;
+    int dy = by - ay;
+    int ady = dy < 0 ? -dy : dy;
+    int sgy = dy < 0 ? -1 : 1;
+    s.ax = ax; s.ay = ay;
+    if (dx >= ady) { s.xmajor = true; s.ns = dx; s.dmin = ady; s.minor_sgn = sgy; s.major_sgn_y = 0; }
+    else { s.xmajor = false; s.ns = ady; s.dmin = dx; s.minor_sgn = 1; s.major_sgn_y = sgy; }
+    return s;
+}
+
+// Visits the pixels of the path set up by `s` in walking order on a plane
+// with row pitch `pitch` whose element (0,0) is image pixel (ox, oy); `visit`
+// receives a pointer to each sample.  Returns |P| = ns + 1.
+template <typename T, typename Visit>
+__device__ __forceinline__ int walk_path(const T *__restrict__ base, int pitch, int ox, int oy,
+                                         const PathSetup &s, Visit &&visit)
+{
+    int smaj, smin;
+    if (s.xmajor) { smaj = 1; smin = s.minor_sgn * pitch; }
+    else { smaj = s.major_sgn_y * pitch; smin = 1; }
+    const T *q = base + (long long)(s.ay - oy) * pitch + (s.ax - ox);
+    const int two_ns = 2 * s.ns, two_d = 2 * s.dmin;
+    int e = s.ns;
+#pragma unroll 4
+    for (int i = 0; i <= s.ns; ++i) {
+        visit(q);
+        e += two_d;
+        int step = smaj;
+        if (e >= two_ns) { e -= two_ns; step += smin; }
+        q += step;
+    }
+    return s.ns + 1;
+}
+
+// Sums along the path of d_c(q, C_k) (Eq. 1) and of the contour factor w(q)
+// (Eq. 2).  Returns |P|.
+template <typename T>
+__device__ __forceinline__ int path_sums(const T *__restrict__ base, int pitch, int ox, int oy,
+                                         const PathSetup &s, float cL, float ca, float cb,
+                                         float &sum_dc, float &sum_w)
+{
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, bw = 0.f;
+    int len = walk_path(base, pitch, ox, oy, s, [&](const T *q) {
+        float4 v = fetch_sample<T>(q);
+        float dl = v.x - cL, da = v.y - ca, db = v.z - cb;
+        a0 = fmaf(dl, dl, a0);
+        a1 = fmaf(da, da, a1);
+        a2 = fmaf(db, db, a2);
+        bw += v.w;
+    });
+    sum_dc = (a0 + a1) + a2;
+    sum_w = bw;
+    return len;
+}
+
+// Eq. 1-3 assembled from the path sums.
+__device__ __forceinline__ float scalp_distance(float dcp, float sum_dc, float sum_w, int len,
+                                                float lam, float gamma, float ms2, float ds)
+{
+    float inv = 1.0f / (float)len;
+    float dcol = lam * dcp + (1.0f - lam) * (sum_dc * inv);
+    float dcon = 1.0f + gamma * (sum_w * inv);
+    return fmaf(dcol, dcon, ms2 * ds);
+}
+
+// ---------------------------------------------------------------------------
+// Warp-aggregated segmented reduction.  Lanes holding the same key are summed
+// with warp reductions; the group's first lane hands the sums to `sink`.
+// Colour values are fixed point (x 2^24, fits int32 for CIELab of sRGB) and
+// summed as two int32 halves so a 32-lane sum cannot overflow.
+// ---------------------------------------------------------------------------
+template <class Sink>
+__device__ __forceinline__ void warp_aggregate(bool valid, int key, int x, int y, float4 v,
+                                               Sink &&sink)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const float scale = (float)(1 << COLOR_FRAC_BITS);
+    int qL = valid ? __float2int_rn(v.x * scale) : 0;
+    int qa = valid ? __float2int_rn(v.y * scale) : 0;
+    int qb = valid ? __float2int_rn(v.z * scale) : 0;
+    unsigned pending = __ballot_sync(FULL, valid);
+    while (pending) {
+        int leader = __ffs(pending) - 1;
+        int k = __shfl_sync(FULL, key, leader);
+        bool mine = valid && key == k;
+        unsigned grp = __ballot_sync(FULL, mine);
+        long long cnt = __popc(grp);
+        long long sx = __reduce_add_sync(FULL, (unsigned)(mine ? x : 0));
+        long long sy = __reduce_add_sync(FULL, (unsigned)(mine ? y : 0));
+        long long sL = ((long long)__reduce_add_sync(FULL, mine ? (qL >> 12) : 0) << 12) +
+                       (long long)__reduce_add_sync(FULL, (unsigned)(mine ? (qL & 4095) : 0));
+        long long sa = ((long long)__reduce_add_sync(FULL, mine ? (qa >> 12) : 0) << 12) +
+                       (long long)__reduce_add_sync(FULL, (unsigned)(mine ? (qa & 4095) : 0));
+        long long sb = ((long long)__reduce_add_sync(FULL, mine ? (qb >> 12) : 0) << 12) +
+                       (long long)__reduce_add_sync(FULL, (unsigned)(mine ? (qb & 4095) : 0));
+        if (lane == leader) sink(k, cnt, sx, sy, sL, sa, sb);
+        pending &= ~grp;
+    }
+}
+
+__device__ __forceinline__ void acc_add(ClusterAcc *c, long long n, long long sx, long long sy,
+                                        long long sL, long long sa, long long sb)
+{
+    atomicAdd(&c->n, (unsigned long long)n);
+    atomicAdd(&c->sx, (unsigned long long)sx);
+    atomicAdd(&c->sy, (unsigned long long)sy);
+    atomicAdd(&c->sL, (unsigned long long)sL);
+    atomicAdd(&c->sa, (unsigned long long)sa);
+    atomicAdd(&c->sb, (unsigned long long)sb);
+}
+
+// Sum into a tile's shared-memory slot table.
+__device__ __forceinline__ void warp_aggregate_tile(bool valid, int slot, int x, int y, float4 v,
+                                                    ClusterAcc *sacc)
+{
+    warp_aggregate(valid, slot, x, y, v,
+                   [&](int k, long long n, long long sx, long long sy, long long sL, long long sa,
+                       long long sb) { acc_add(&sacc[k], n, sx, sy, sL, sa, sb); });
+}
+
+// Sum straight into the global per-cluster sums.
+__device__ __forceinline__ void warp_aggregate_global(bool valid, int label, int x, int y,
+                                                      float4 v, ClusterAcc *acc)
+{
+    warp_aggregate(valid, label, x, y, v,
+                   [&](int k, long long n, long long sx, long long sy, long long sL, long long sa,
+                       long long sb) { acc_add(&acc[k], n, sx, sy, sL, sa, sb); });
+}
+
+__host__ __device__ inline long long ceil_div_ll(long long a, long long b) { return (a + b - 1) / b; }
+
+// Upper bound on the tiles a window spans along one axis: the window holds at
+// most floor(2r) + 1 consecutive pixels (one more is allowed for rounding of r).
+__host__ __device__ inline int tiles_per_window(double r, int tile)
+{
+    long long len = (long long)(2.0 * r) + 2;
+    return (int)((len + tile - 1) / tile + 1);
+}
+
+}  // namespace scalp

@@ -1,0 +1,375 @@
+// scalp_kernels.cu -- set-up, cluster update, projection and candidate-list
+// kernels of libscalp.  The assignment kernel is in scalp_assign.cu and the
+// connectivity enforcement in scalp_ccl.cu.
+#include <cfloat>
+#include <climits>
+
+#include <algorithm>
+
+#include "scalp_launch.h"
+
+namespace scalp {
+
+// ---------------------------------------------------------------------------
+// Set-up (once per solve): sRGB -> CIELab, contour factor, grid label.
+// CIELab follows the sRGB standard: inverse transfer function, the D65
+// sRGB->XYZ matrix, normalisation by the XYZ of sRGB white (the matrix row
+// sums), then the CIE 1976 L*a*b* companding with the linear segment below
+// (6/29)^3.
+// ---------------------------------------------------------------------------
+__constant__ float c_rgb2xyz[9] = {0.4124564f, 0.3575761f, 0.1804375f,
+                                   0.2126729f, 0.7151522f, 0.0721750f,
+                                   0.0193339f, 0.1191920f, 0.9503041f};
+
+__device__ __forceinline__ float lab_f(float t)
+{
+    const float d3 = (6.0f / 29.0f) * (6.0f / 29.0f) * (6.0f / 29.0f);
+    return t > d3 ? cbrtf(t) : t * (841.0f / 108.0f) + (4.0f / 29.0f);
+}
+
+__global__ void k_setup(SolveArgs a, const uint8_t *__restrict__ rgb, long long rgb_stride,
+                        const float *__restrict__ contour, long long contour_stride, int storage,
+                        void *plane)
+{
+    __shared__ float lin[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
+        double c = i / 255.0;
+        lin[i] = (float)(c <= 0.04045 ? c / 12.92 : pow((c + 0.055) / 1.055, 2.4));
+    }
+    __syncthreads();
+    const float wx = c_rgb2xyz[0] + c_rgb2xyz[1] + c_rgb2xyz[2];
+    const float wy = c_rgb2xyz[3] + c_rgb2xyz[4] + c_rgb2xyz[5];
+    const float wz = c_rgb2xyz[6] + c_rgb2xyz[7] + c_rgb2xyz[8];
+    const float inv_s2 = 1.0f / (a.sigma * a.sigma);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < a.N;
+         p += (long long)gridDim.x * blockDim.x) {
+        int y = (int)(p / a.W), x = (int)(p - (long long)y * a.W);
+        const uint8_t *px = rgb + y * rgb_stride + 3 * (long long)x;
+        float R = lin[px[0]], G = lin[px[1]], B = lin[px[2]];
+        float X = c_rgb2xyz[0] * R + c_rgb2xyz[1] * G + c_rgb2xyz[2] * B;
+        float Y = c_rgb2xyz[3] * R + c_rgb2xyz[4] * G + c_rgb2xyz[5] * B;
+        float Z = c_rgb2xyz[6] * R + c_rgb2xyz[7] * G + c_rgb2xyz[8] * B;
+        float fx = lab_f(X / wx), fy = lab_f(Y / wy), fz = lab_f(Z / wz);
+        float L = 116.0f * fy - 16.0f;
+        float A = 500.0f * (fx - fy);
+        float Bb = 200.0f * (fy - fz);
+        float c = contour ? contour[y * contour_stride + x] : 0.0f;
+        float w = -expm1f(-(c * c) * inv_s2);  // 1 - exp(-C^2/sigma^2), Eq. 2
+        const long long q = (long long)y * a.pitch + x;
+        if (storage == 0) {
+            reinterpret_cast<float4 *>(plane)[q] = make_float4(L, A, Bb, w);
+        } else {
+            __half2 lo = __floats2half2_rn(L, A), hi = __floats2half2_rn(Bb, w);
+            uint2 u;
+            u.x = *reinterpret_cast<unsigned *>(&lo);
+            u.y = *reinterpret_cast<unsigned *>(&hi);
+            reinterpret_cast<uint2 *>(plane)[q] = u;
+        }
+        // Algorithm 1 initialisation: label = cell of the regular grid
+        int cx = (int)((long long)x * a.nx / a.W);
+        int cy = (int)((long long)y * a.ny / a.H);
+        a.labels[p] = cy * a.nx + cx;
+    }
+}
+
+void launch_setup(const SolveArgs &a, const uint8_t *rgb, long long rgb_stride,
+                  const float *contour, long long contour_stride, int storage, void *plane,
+                  cudaStream_t st)
+{
+    int blocks = (int)std::min<long long>(ceil_div_ll(a.N, 256), 152 * 8);
+    k_setup<<<blocks, 256, 0, st>>>(a, rgb, rgb_stride, contour, contour_stride, storage, plane);
+}
+
+template <typename T>
+__global__ void k_accumulate(SolveArgs a, const T *__restrict__ plane)
+{
+    // grid-stride loop with a warp-uniform trip count so that every lane
+    // takes part in the warp reductions
+    long long stride = (long long)gridDim.x * blockDim.x;
+    long long base0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31);
+    for (long long base = base0; base < a.N; base += stride) {
+        long long p = base + (threadIdx.x & 31);
+        bool valid = p < a.N;
+        int lab = valid ? a.labels[p] : 0;
+        int y = valid ? (int)(p / a.W) : 0;
+        int x = valid ? (int)(p - (long long)y * a.W) : 0;
+        float4 v = valid ? fetch_sample<T>(plane + (long long)y * a.pitch + x) : make_float4(0, 0, 0, 0);
+        warp_aggregate(valid, lab, x, y, v,
+                       [&](int k, long long n, long long sx, long long sy, long long sL,
+                           long long sa, long long sb) { acc_add(&a.acc[k], n, sx, sy, sL, sa, sb); });
+    }
+}
+
+void launch_accumulate(const SolveArgs &a, cudaStream_t st)
+{
+    int blocks = (int)std::min<long long>(ceil_div_ll(a.N, 256), 152 * 8);
+    if (a.plane32) k_accumulate<float4><<<blocks, 256, 0, st>>>(a, a.plane32);
+    else k_accumulate<uint2><<<blocks, 256, 0, st>>>(a, a.plane16);
+}
+
+// ---------------------------------------------------------------------------
+// Cluster update (Algorithm 1): means over S_k from the integer sums; an empty
+// cluster keeps its colour, barycenter and endpoint.  The endpoint is X_k
+// rounded half-up; if the pixel there is not labelled k the cluster is queued
+// for the projection of Eq. 4.  The sums are cleared for the next assignment.
+// ---------------------------------------------------------------------------
+__global__ void k_finalize(SolveArgs a)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.Keff) return;
+    ClusterAcc c = a.acc[k];
+    ClusterAcc z = {};
+    a.acc[k] = z;
+    long long n = (long long)c.n;
+    if (n <= 0) return;
+    long long sx = (long long)c.sx, sy = (long long)c.sy;
+    a.st_n[k] = n;
+    a.st_sx[k] = sx;
+    a.st_sy[k] = sy;
+    double den = (double)n * (double)(1 << COLOR_FRAC_BITS);
+    a.st_col[k] = make_float4((float)((double)(long long)c.sL / den),
+                              (float)((double)(long long)c.sa / den),
+                              (float)((double)(long long)c.sb / den), 0.f);
+    int ex = (int)((2 * sx + n) / (2 * n));
+    int ey = (int)((2 * sy + n) / (2 * n));
+    a.st_end[k] = make_int2(ex, ey);
+    if (a.labels[(long long)ey * a.W + ex] != k) {
+        int slot = atomicAdd(&a.ctr->nproj, 1);
+        a.proj_list[slot] = k;
+    }
+}
+
+void launch_finalize(const SolveArgs &a, cudaStream_t st)
+{
+    k_finalize<<<(a.Keff + 255) / 256, 256, 0, st>>>(a);
+}
+
+// ---------------------------------------------------------------------------
+// Projection, Eq. 4: X_k^* = argmin over p in S_k of ||X_p - X_k||, compared
+// exactly as (n*x - Sx)^2 + (n*y - Sy)^2 in 128-bit integers, ties to the
+// smallest raster index.  S_k lies inside the window the last assignment used
+// for cluster k, unless some pixel kept its old label for lack of any
+// candidate; then the whole image is searched.  One CTA per queued cluster.
+// ---------------------------------------------------------------------------
+constexpr int PROJ_THREADS = 256;
+
+__global__ void __launch_bounds__(PROJ_THREADS) k_project(SolveArgs a, int whole_image)
+{
+    __shared__ unsigned long long s_hi[PROJ_THREADS], s_lo[PROJ_THREADS];
+    __shared__ long long s_p[PROJ_THREADS];
+    const int nproj = a.ctr->nproj;
+    const bool all = whole_image || a.ctr->orphans > 0;
+    for (int j = blockIdx.x; j < nproj; j += gridDim.x) {
+        const int k = a.proj_list[j];
+        const long long n = a.st_n[k], sx = a.st_sx[k], sy = a.st_sy[k];
+        int xlo = 0, xhi = a.W - 1, ylo = 0, yhi = a.H - 1;
+        if (!all) {
+            ClusterDev cd = a.cdev[k];
+            xlo = cd.xlo; xhi = cd.xhi; ylo = cd.ylo; yhi = cd.yhi;
+        }
+        const int w = xhi - xlo + 1;
+        const long long area = (long long)w * (yhi - ylo + 1);
+        unsigned __int128 best = ~(unsigned __int128)0;
+        long long bestp = LLONG_MAX;
+        for (long long i = threadIdx.x; i < area; i += PROJ_THREADS) {
+            int y = ylo + (int)(i / w), x = xlo + (int)(i % w);
+            long long p = (long long)y * a.W + x;
+            if (a.labels[p] != k) continue;
+            __int128 dx = (__int128)n * x - sx, dy = (__int128)n * y - sy;
+            unsigned __int128 d2 = (unsigned __int128)(dx * dx) + (unsigned __int128)(dy * dy);
+            if (d2 < best || (d2 == best && p < bestp)) { best = d2; bestp = p; }
+        }
+        s_hi[threadIdx.x] = (unsigned long long)(best >> 64);
+        s_lo[threadIdx.x] = (unsigned long long)best;
+        s_p[threadIdx.x] = bestp;
+        __syncthreads();
+        for (int h = PROJ_THREADS / 2; h > 0; h >>= 1) {
+            if (threadIdx.x < h) {
+                int o = threadIdx.x + h;
+                bool take = s_hi[o] < s_hi[threadIdx.x] ||
+                            (s_hi[o] == s_hi[threadIdx.x] &&
+                             (s_lo[o] < s_lo[threadIdx.x] ||
+                              (s_lo[o] == s_lo[threadIdx.x] && s_p[o] < s_p[threadIdx.x])));
+                if (take) {
+                    s_hi[threadIdx.x] = s_hi[o];
+                    s_lo[threadIdx.x] = s_lo[o];
+                    s_p[threadIdx.x] = s_p[o];
+                }
+            }
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) {
+            long long p = s_p[0];
+            if (p == LLONG_MAX) {
+                atomicExch(&a.ctr->error, ERR_BAD_LABEL);
+            } else {
+                a.st_end[k] = make_int2((int)(p % a.W), (int)(p / a.W));
+            }
+        }
+        __syncthreads();
+    }
+}
+
+void launch_project(const SolveArgs &a, int whole_image, cudaStream_t st)
+{
+    int blocks = std::min(a.Keff, 2 * 152);
+    k_project<<<blocks, PROJ_THREADS, 0, st>>>(a, whole_image);
+}
+
+// ---------------------------------------------------------------------------
+// Windows and per-tile candidate lists.  Pixel p is a candidate of cluster k
+// iff |x_p - x_k| <= r and |y_p - y_k| <= r (the (2r+1)x(2r+1) window of
+// Algorithm 1), i.e. K*(n*x_p - Sx)^2 <= N*n^2 and likewise for y, evaluated
+// exactly.  Each cluster's window becomes an inclusive integer range; every
+// assignment tile overlapping it lists the cluster.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool in_window(long long v, long long n, long long s, long long N,
+                                          long long K)
+{
+    __int128 d = (__int128)n * v - s;
+    unsigned __int128 lhs = (unsigned __int128)K * (unsigned __int128)(d * d);
+    unsigned __int128 rhs = (unsigned __int128)N * (unsigned __int128)n * (unsigned __int128)n;
+    return lhs <= rhs;
+}
+
+__device__ bool window_range(long long n, long long s, long long N, long long K, double r,
+                             int limit, int &lo, int &hi)
+{
+    double c = (double)s / (double)n;
+    long long l = (long long)floor(c - r) - 1, h = (long long)ceil(c + r) + 1;
+    int guard = 0;
+    while (!in_window(l, n, s, N, K) && guard++ < 64) ++l;
+    guard = 0;
+    while (!in_window(h, n, s, N, K) && guard++ < 64) --h;
+    if (!in_window(l, n, s, N, K) || !in_window(h, n, s, N, K)) return false;
+    lo = (int)max(0LL, l);
+    hi = (int)min((long long)limit - 1, h);
+    return true;
+}
+
+__global__ void k_window(SolveArgs a)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.Keff) return;
+    const long long n = a.st_n[k], sx = a.st_sx[k], sy = a.st_sy[k];
+    ClusterDev cd;
+    float4 col = a.st_col[k];
+    int2 e = a.st_end[k];
+    cd.L = col.x; cd.a = col.y; cd.b = col.z;
+    cd.xk = (float)((double)sx / (double)n);
+    cd.yk = (float)((double)sy / (double)n);
+    cd.ex = e.x; cd.ey = e.y;
+    cd.pad = k;
+    bool ok = window_range(n, sx, a.N, a.K, a.r, a.W, cd.xlo, cd.xhi) &&
+              window_range(n, sy, a.N, a.K, a.r, a.H, cd.ylo, cd.yhi);
+    if (!ok) {
+        atomicExch(&a.ctr->error, ERR_BAD_LABEL);
+        cd.xlo = 1; cd.xhi = 0; cd.ylo = 1; cd.yhi = 0;
+    }
+    a.cdev[k] = cd;
+    if (!ok) return;
+    for (int ty = cd.ylo / TILE_Y; ty <= cd.yhi / TILE_Y; ++ty)
+        for (int tx = cd.xlo / TILE_X; tx <= cd.xhi / TILE_X; ++tx)
+            atomicAdd(&a.tile_count[ty * a.n_tx + tx], 1);
+}
+
+// Exclusive scan of the tile counts (one CTA), reset of per-iteration counters.
+constexpr int SCAN1_THREADS = 1024;
+
+__global__ void __launch_bounds__(SCAN1_THREADS) k_scan_tiles(SolveArgs a)
+{
+    __shared__ int s_warp[32];
+    __shared__ int s_carry;
+    const int n = a.n_tx * a.n_ty;
+    if (threadIdx.x == 0) s_carry = 0;
+    __syncthreads();
+    for (int base = 0; base < n; base += SCAN1_THREADS) {
+        int i = base + threadIdx.x;
+        int v = i < n ? a.tile_count[i] : 0;
+        int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+        int incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_warp[wid] = incl;
+        __syncthreads();
+        if (wid == 0) {
+            int w = s_warp[lane];
+            for (int o = 1; o < 32; o <<= 1) {
+                int t = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += t;
+            }
+            s_warp[lane] = w;
+        }
+        __syncthreads();
+        int carry = s_carry;
+        int excl = carry + (wid ? s_warp[wid - 1] : 0) + incl - v;
+        if (i < n) {
+            a.tile_off[i] = excl;
+            a.tile_cursor[i] = excl;
+            a.tile_count[i] = 0;
+        }
+        __syncthreads();
+        if (threadIdx.x == SCAN1_THREADS - 1) s_carry = excl + v;
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        a.tile_off[n] = s_carry;
+        if (s_carry > a.tile_cap) atomicExch(&a.ctr->error, ERR_TILE_LIST_OVERFLOW);
+        a.ctr->nproj = 0;
+        a.ctr->orphans = 0;
+    }
+}
+
+__global__ void k_fill_tiles(SolveArgs a)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.Keff) return;
+    ClusterDev cd = a.cdev[k];
+    if (cd.xlo > cd.xhi) return;
+    for (int ty = cd.ylo / TILE_Y; ty <= cd.yhi / TILE_Y; ++ty)
+        for (int tx = cd.xlo / TILE_X; tx <= cd.xhi / TILE_X; ++tx) {
+            int pos = atomicAdd(&a.tile_cursor[ty * a.n_tx + tx], 1);
+            if (pos < a.tile_cap) a.tile_list[pos] = k;
+        }
+}
+
+void launch_derive(const SolveArgs &a, cudaStream_t st)
+{
+    int blocks = (a.Keff + 255) / 256;
+    k_window<<<blocks, 256, 0, st>>>(a);
+    k_scan_tiles<<<1, SCAN1_THREADS, 0, st>>>(a);
+    k_fill_tiles<<<blocks, 256, 0, st>>>(a);
+}
+
+// ---------------------------------------------------------------------------
+// Debug: the path pixels exactly as the assignment kernel steps through them.
+// ---------------------------------------------------------------------------
+__global__ void k_debug_paths(const int *pairs, int M, int *out_xy, int stride_xy, int *out_len,
+                              int W)
+{
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= M) return;
+    PathSetup s = path_setup(pairs[4 * i], pairs[4 * i + 1], pairs[4 * i + 2], pairs[4 * i + 3]);
+    // the walker only does pointer arithmetic here; nothing is dereferenced
+    const char *base = reinterpret_cast<const char *>(out_xy);
+    int *o = out_xy + (long long)i * stride_xy;
+    int cnt = 0;
+    int len = walk_path(base, W, 0, 0, s, [&](const char *q) {
+        long long off = q - base;
+        int y = (int)(off / W), x = (int)(off - (long long)y * W);
+        if (2 * cnt + 1 < stride_xy) { o[2 * cnt] = x; o[2 * cnt + 1] = y; }
+        ++cnt;
+    });
+    out_len[i] = len;
+}
+
+void launch_debug_paths(const int *pairs, int M, int *out_xy, int stride_xy, int *out_len, int W,
+                        cudaStream_t st)
+{
+    if (M <= 0) return;
+    k_debug_paths<<<(M + 127) / 128, 128, 0, st>>>(pairs, M, out_xy, stride_xy, out_len, W);
+}
+
+}  // namespace scalp

@@ -1,0 +1,40 @@
+// scalp_launch.h -- host-side launchers of the libscalp kernels (internal).
+#pragma once
+
+#include "scalp_internal.cuh"
+
+namespace scalp {
+
+// Per-pixel set-up: CIELab (Sec. II-A), contour factor 1-exp(-C^2/sigma^2)
+// of Eq. 2, grid label.  rgb/contour are device pointers with row strides.
+void launch_setup(const SolveArgs &a, const uint8_t *rgb, long long rgb_stride,
+                  const float *contour, long long contour_stride, int storage,
+                  void *plane, cudaStream_t st);
+// Integer sums of (1, x, y, L, a, b) by label into a.acc (grid initialisation).
+void launch_accumulate(const SolveArgs &a, cudaStream_t st);
+// Cluster update (Algorithm 1) from a.acc, then queue projections (Eq. 4).
+void launch_finalize(const SolveArgs &a, cudaStream_t st);
+// Eq. 4 for the queued clusters; whole_image=1 searches every pixel.
+void launch_project(const SolveArgs &a, int whole_image, cudaStream_t st);
+// Windows, derived cluster table and per-tile candidate lists.
+void launch_derive(const SolveArgs &a, cudaStream_t st);
+// Assignment (Algorithm 1 inner loops, Eq. 1-3).  tmap is used when staged.
+void launch_assign(const SolveArgs &a, int storage, bool staged, const CUtensorMap &tmap,
+                   size_t smem_bytes, cudaStream_t st);
+size_t assign_smem_bytes(int halo, int storage);
+cudaError_t assign_configure(int storage, bool staged, size_t smem_bytes);
+// Debug: record the pixels of M paths.
+void launch_debug_paths(const int *pairs, int M, int *out_xy, int stride_xy, int *out_len,
+                        int W, cudaStream_t st);
+
+// Connectivity enforcement; returns the number of labels through *d_nlab.
+struct CclBuffers {
+    int *parent, *size, *link, *scan;
+    int *scan_tmp;     // block sums for the multi-level scan
+    long long scan_tmp_len;
+};
+long long ccl_scan_tmp_len(long long N);
+void launch_ccl(const int *labels, int H, int W, int K, int *out, const CclBuffers &b,
+                int *d_nlab, DevCounters *ctr, cudaStream_t st);
+
+}  // namespace scalp

@@ -1,0 +1,323 @@
+"""ctypes binding of libscalp (include/scalp.h).
+
+The functions below carry the C names and do argument marshalling only: every
+step of SCALP runs in the CUDA kernels of libscalp.  PyTorch supplies device
+memory (the workspace, inputs and outputs) and streams.  There is no CPU
+fallback: if the library is missing, loading raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libscalp.so")
+
+SCALP_OK = 0
+SCALP_E_ARG = -1
+SCALP_E_NOMEM = -2
+SCALP_E_CUDA = -3
+SCALP_E_TIMEOUT = -4
+SCALP_E_STATE = -5
+SCALP_E_INTERNAL = -6
+STORAGE = {"f32": 0, "f16": 1}
+
+
+class ScalpError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"libscalp error {code}: {msg}")
+        self.code = code
+
+
+class scalp_image(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("rgb", ctypes.c_void_p),
+                ("rgb_stride", ctypes.c_int64), ("on_device", ctypes.c_int32)]
+
+
+class scalp_contour(ctypes.Structure):
+    _fields_ = [("data", ctypes.c_void_p), ("stride", ctypes.c_int64)]
+
+
+class scalp_params(ctypes.Structure):
+    _fields_ = [("lambda_", ctypes.c_float), ("sigma", ctypes.c_float), ("gamma", ctypes.c_float),
+                ("storage", ctypes.c_int32), ("use_graph", ctypes.c_int32),
+                ("global_walk", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
+
+
+class scalp_info(ctypes.Structure):
+    _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("Keff", ctypes.c_int32),
+                ("r", ctypes.c_double), ("gamma", ctypes.c_double), ("halo", ctypes.c_int32),
+                ("iterations", ctypes.c_int32)]
+
+
+class scalp_state(ctypes.Structure):
+    _fields_ = [("labels", ctypes.c_void_p), ("n", ctypes.c_void_p), ("sx", ctypes.c_void_p),
+                ("sy", ctypes.c_void_p), ("color", ctypes.c_void_p), ("endpoint", ctypes.c_void_p)]
+
+
+# Every symbol include/scalp.h declares.
+EXPORTS = (
+    "scalp_default_params", "scalp_workspace_bytes", "scalp_init", "scalp_reload",
+    "scalp_iterate", "scalp_labels", "scalp_get_info", "scalp_get_state", "scalp_set_state",
+    "scalp_debug_paths", "scalp_profile", "scalp_count_samples", "scalp_sync",
+    "scalp_last_error", "scalp_destroy",
+)
+
+_lib = None
+_lock = threading.Lock()
+
+
+def load(path: str = LIB_PATH) -> ctypes.CDLL:
+    """Loads libscalp.so (built by paper_1903_07149_gb300.build); raises if absent."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(path):
+            raise FileNotFoundError(
+                f"{path} is missing: build it with `python -m paper_1903_07149_gb300.build`")
+        L = ctypes.CDLL(path)
+        P, I32, I64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        sig = {
+            "scalp_default_params": (None, [ctypes.POINTER(scalp_params)]),
+            "scalp_workspace_bytes": (ctypes.c_size_t, [I32, I32, I32, ctypes.POINTER(scalp_params)]),
+            "scalp_init": (ctypes.c_int, [ctypes.POINTER(P), ctypes.POINTER(scalp_image),
+                                          ctypes.POINTER(scalp_contour), I32, ctypes.c_float,
+                                          ctypes.POINTER(scalp_params)]),
+            "scalp_reload": (ctypes.c_int, [P, ctypes.POINTER(scalp_image),
+                                            ctypes.POINTER(scalp_contour)]),
+            "scalp_iterate": (ctypes.c_int, [P, I32]),
+            "scalp_labels": (ctypes.c_int, [P, P, I32, I32, ctypes.POINTER(I32)]),
+            "scalp_get_info": (ctypes.c_int, [P, ctypes.POINTER(scalp_info)]),
+            "scalp_get_state": (ctypes.c_int, [P, ctypes.POINTER(scalp_state)]),
+            "scalp_set_state": (ctypes.c_int, [P, ctypes.POINTER(scalp_state)]),
+            "scalp_debug_paths": (ctypes.c_int, [P, P, I32, P, I32, P]),
+            "scalp_profile": (ctypes.c_int, [P, I32, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(I64)]),
+            "scalp_count_samples": (ctypes.c_int, [P, I32, ctypes.POINTER(I64),
+                                                   ctypes.POINTER(I64)]),
+            "scalp_sync": (ctypes.c_int, [P]),
+            "scalp_last_error": (ctypes.c_char_p, [P]),
+            "scalp_destroy": (None, [P]),
+        }
+        for name, (res, args) in sig.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+        return L
+
+
+def _check(rc: int, ctx=None):
+    if rc != SCALP_OK:
+        msg = load().scalp_last_error(ctx).decode(errors="replace")
+        raise ScalpError(rc, msg)
+
+
+# --- C names, argument marshalling only -------------------------------------
+def scalp_default_params() -> scalp_params:
+    p = scalp_params()
+    load().scalp_default_params(ctypes.byref(p))
+    return p
+
+
+def scalp_workspace_bytes(H: int, W: int, K: int, params: scalp_params) -> int:
+    return int(load().scalp_workspace_bytes(H, W, K, ctypes.byref(params)))
+
+
+def scalp_init(image: scalp_image, contour: scalp_contour, K: int, m: float,
+               params: scalp_params) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    _check(load().scalp_init(ctypes.byref(ctx), ctypes.byref(image), ctypes.byref(contour),
+                             int(K), float(m), ctypes.byref(params)))
+    return ctx
+
+
+def scalp_reload(ctx, image: scalp_image, contour: scalp_contour):
+    _check(load().scalp_reload(ctx, ctypes.byref(image), ctypes.byref(contour)), ctx)
+
+
+def scalp_iterate(ctx, n: int):
+    _check(load().scalp_iterate(ctx, int(n)), ctx)
+
+
+def scalp_labels(ctx, out_ptr: int, out_on_device: bool, enforce: bool) -> int:
+    n = ctypes.c_int32()
+    _check(load().scalp_labels(ctx, ctypes.c_void_p(out_ptr), int(out_on_device), int(enforce),
+                               ctypes.byref(n)), ctx)
+    return n.value
+
+
+def scalp_get_info(ctx) -> scalp_info:
+    info = scalp_info()
+    _check(load().scalp_get_info(ctx, ctypes.byref(info)), ctx)
+    return info
+
+
+def scalp_get_state(ctx, state: scalp_state):
+    _check(load().scalp_get_state(ctx, ctypes.byref(state)), ctx)
+
+
+def scalp_set_state(ctx, state: scalp_state):
+    _check(load().scalp_set_state(ctx, ctypes.byref(state)), ctx)
+
+
+def scalp_debug_paths(ctx, pairs: np.ndarray, stride_xy: int):
+    pairs = np.ascontiguousarray(pairs, dtype=np.int32).reshape(-1, 4)
+    M = len(pairs)
+    out_xy = np.full((M, stride_xy), -1, dtype=np.int32)
+    out_len = np.zeros(M, dtype=np.int32)
+    _check(load().scalp_debug_paths(ctx, pairs.ctypes.data, M, out_xy.ctypes.data, stride_xy,
+                                    out_len.ctypes.data), ctx)
+    return out_xy, out_len
+
+
+def scalp_profile(ctx, enable: int):
+    ms = ctypes.c_double()
+    n = ctypes.c_int64()
+    _check(load().scalp_profile(ctx, int(enable), ctypes.byref(ms), ctypes.byref(n)), ctx)
+    return ms.value, n.value
+
+
+def scalp_count_samples(ctx, enable: int):
+    s = ctypes.c_int64()
+    n = ctypes.c_int64()
+    _check(load().scalp_count_samples(ctx, int(enable), ctypes.byref(s), ctypes.byref(n)), ctx)
+    return s.value, n.value
+
+
+def scalp_sync(ctx):
+    _check(load().scalp_sync(ctx), ctx)
+
+
+def scalp_destroy(ctx):
+    load().scalp_destroy(ctx)
+
+
+# --- convenience wrapper over the C calls -------------------------------------
+class Segmenter:
+    """One SCALP solve on the current CUDA device.
+
+    rgb: (H, W, 3) uint8, a CUDA tensor or a host numpy array / CPU tensor.
+    contour: (H, W) float32 in [0,1] on the same side, or None.
+    The workspace is a torch uint8 CUDA tensor owned by this object.
+    """
+
+    def __init__(self, rgb, contour, K: int, m: float = 10.0, lam: float = 0.5,
+                 sigma: float = 0.25, gamma: float = -1.0, storage: str = "f32",
+                 use_graph: bool = True, global_walk: bool = False, stream=None):
+        import torch
+
+        self._torch = torch
+        H, W = int(rgb.shape[0]), int(rgb.shape[1])
+        self.H, self.W, self.K = H, W, int(K)
+        p = scalp_default_params()
+        p.lambda_, p.sigma, p.gamma = lam, sigma, gamma
+        p.storage = STORAGE[storage]
+        p.use_graph = int(use_graph)
+        p.global_walk = int(global_walk)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        p.stream = self.stream.cuda_stream
+        nbytes = scalp_workspace_bytes(H, W, K, p)
+        if nbytes == 0:
+            raise ScalpError(SCALP_E_ARG, "invalid sizes")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        p.workspace = self.workspace.data_ptr()
+        p.workspace_bytes = nbytes
+        self.params = p
+        img, con, self._keep = self._marshal(rgb, contour)
+        self.ctx = scalp_init(img, con, K, m, p)
+        self.info = scalp_get_info(self.ctx)
+
+    def _marshal(self, rgb, contour):
+        torch = self._torch
+        keep = []
+        if isinstance(rgb, torch.Tensor) and rgb.is_cuda:
+            rgb = rgb.contiguous()
+            keep.append(rgb)
+            img = scalp_image(rgb.shape[0], rgb.shape[1], rgb.data_ptr(), 0, 1)
+            con = scalp_contour(None, 0)
+            if contour is not None:
+                c = contour.to(device=rgb.device, dtype=torch.float32).contiguous()
+                keep.append(c)
+                con = scalp_contour(c.data_ptr(), 0)
+        else:
+            a = np.ascontiguousarray(np.asarray(rgb), dtype=np.uint8)
+            keep.append(a)
+            img = scalp_image(a.shape[0], a.shape[1], a.ctypes.data, 0, 0)
+            con = scalp_contour(None, 0)
+            if contour is not None:
+                c = np.ascontiguousarray(np.asarray(contour), dtype=np.float32)
+                keep.append(c)
+                con = scalp_contour(c.ctypes.data, 0)
+        return img, con, keep
+
+    def reload(self, rgb, contour):
+        img, con, self._keep = self._marshal(rgb, contour)
+        scalp_reload(self.ctx, img, con)
+
+    def iterate(self, n: int = 1):
+        scalp_iterate(self.ctx, n)
+
+    def labels(self, enforce: bool = True, out=None):
+        """Labels as a (H, W) int32 array: into `out` (a CUDA tensor or a numpy
+        array) if given, else a new numpy array.  Returns (labels, n_labels)."""
+        torch = self._torch
+        if out is None:
+            out = np.empty((self.H, self.W), dtype=np.int32)
+        if isinstance(out, torch.Tensor):
+            assert out.is_cuda and out.dtype == torch.int32 and out.is_contiguous()
+            n = scalp_labels(self.ctx, out.data_ptr(), True, enforce)
+        else:
+            assert out.dtype == np.int32 and out.flags["C_CONTIGUOUS"]
+            n = scalp_labels(self.ctx, out.ctypes.data, False, enforce)
+        return out, n
+
+    def get_state(self):
+        K = self.info.Keff
+        st = dict(labels=np.empty((self.H, self.W), np.int32), n=np.empty(K, np.int64),
+                  sx=np.empty(K, np.int64), sy=np.empty(K, np.int64),
+                  color=np.empty((K, 3), np.float64), endpoint=np.empty((K, 2), np.int32))
+        scalp_get_state(self.ctx, scalp_state(*(st[k].ctypes.data for k in
+                                                ("labels", "n", "sx", "sy", "color", "endpoint"))))
+        return st
+
+    def set_state(self, st):
+        arrs = dict(labels=np.ascontiguousarray(st["labels"], np.int32),
+                    n=np.ascontiguousarray(st["n"], np.int64),
+                    sx=np.ascontiguousarray(st["sx"], np.int64),
+                    sy=np.ascontiguousarray(st["sy"], np.int64),
+                    color=np.ascontiguousarray(st["color"], np.float64),
+                    endpoint=np.ascontiguousarray(st["endpoint"], np.int32))
+        scalp_set_state(self.ctx, scalp_state(*(arrs[k].ctypes.data for k in
+                                                ("labels", "n", "sx", "sy", "color", "endpoint"))))
+
+    def debug_paths(self, pairs, stride_xy: int | None = None):
+        if stride_xy is None:
+            stride_xy = 2 * (max(self.H, self.W) + 1)
+        return scalp_debug_paths(self.ctx, pairs, stride_xy)
+
+    def profile(self, enable: int):
+        return scalp_profile(self.ctx, enable)
+
+    def count_samples(self, enable: int):
+        return scalp_count_samples(self.ctx, enable)
+
+    def sync(self):
+        scalp_sync(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            scalp_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
