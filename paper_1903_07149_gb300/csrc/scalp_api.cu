@@ -266,12 +266,14 @@ int harvest_profile(scalp_ctx *c)
 }
 
 // One iteration of Algorithm 1; with profiling, event pair `slot` brackets
-// the assignment kernel.
-void enqueue_iteration(scalp_ctx *c, int slot)
+// the assignment kernel.  Under stream capture the records must be external
+// so that they become event-record nodes of the graph.
+void enqueue_iteration(scalp_ctx *c, int slot, bool capturing)
 {
-    if (c->profiling) cudaEventRecord(c->ev_pool[2 * slot], c->st);
+    const unsigned flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
+    if (c->profiling) cudaEventRecordWithFlags(c->ev_pool[2 * slot], c->st, flags);
     launch_assign(c->a, c->p.storage, c->staged, c->tmap, c->smem, c->st);
-    if (c->profiling) cudaEventRecord(c->ev_pool[2 * slot + 1], c->st);
+    if (c->profiling) cudaEventRecordWithFlags(c->ev_pool[2 * slot + 1], c->st, flags);
     launch_finalize(c->a, c->st);
     launch_project(c->a, 0, c->st);
     launch_derive(c->a, c->st);
@@ -450,7 +452,7 @@ int scalp_iterate(scalp_ctx *c, int32_t n)
         rc = cuda_check(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal),
                         "begin capture");
         if (rc) return rc;
-        for (int i = 0; i < n; ++i) enqueue_iteration(c, i);
+        for (int i = 0; i < n; ++i) enqueue_iteration(c, i, true);
         cudaError_t le = cudaGetLastError();
         rc = cuda_check(c, cudaStreamEndCapture(c->st, &g), "end capture");
         if (rc) return rc;
@@ -469,7 +471,7 @@ int scalp_iterate(scalp_ctx *c, int32_t n)
         rc = cuda_check(c, cudaGraphLaunch(c->gexec, c->st), "launch graph");
         if (rc) return rc;
     } else {
-        for (int i = 0; i < n; ++i) enqueue_iteration(c, i);
+        for (int i = 0; i < n; ++i) enqueue_iteration(c, i, false);
         rc = launch_check(c, "iteration kernels");
         if (rc) return rc;
     }

@@ -1,20 +1,33 @@
 // scalp_assign.cu -- the assignment step of SCALP (Algorithm 1, inner loops)
-// restated per pixel, plus the fused partial sums of the cluster update.
+// restated per tile of pixels, plus the fused partial sums of the update.
 //
 // Algorithm 1 loops over clusters and, for each pixel of a cluster's
 // (2r+1)x(2r+1) window, keeps the cluster with the smallest D(p, C_k) (Eq. 3)
-// under a strict '<' in ascending k.  Here each pixel evaluates the same set
-// of clusters (those whose window holds it, taken from its tile's candidate
-// list) and keeps the lexicographically smallest (D, k): the same result,
-// independent of the visiting order.
+// under a strict '<' in ascending k.  Here each pixel evaluates the same set of
+// clusters (those whose window holds it, from its tile's candidate list) and
+// keeps the smallest (D, k) pair: the same result, in any evaluation order.
 //
-// One CTA labels a 32 x 16 tile; each warp an 8 x 4 block, one pixel per lane.
-// Staged variant: the (L, a, b, w) plane of the tile plus a halo of
-// round(r) + 2 pixels is copied into shared memory by one TMA bulk-tensor load
-// (tile mode, zero fill outside the image), so every path to an endpoint
-// within the halo is walked on-chip; a path to a farther endpoint (a
-// projected barycenter, Eq. 4) is walked in global memory with the same code.
-// Unstaged variant (halo does not fit): every path is walked in global memory.
+// One CTA (1024 threads) labels a 32 x 32 tile:
+//   1. One thread issues a TMA bulk-tensor load of the (L, a, b, w) plane of
+//      the tile plus a halo of round(r) + 2 pixels into shared memory (zero
+//      fill outside the image).  Every path to an endpoint inside that region
+//      is walked on-chip; a farther endpoint (a projected barycenter, Eq. 4)
+//      is walked in global memory with the same stepping rule.
+//   2. Meanwhile the tile's candidate clusters are copied to shared memory,
+//      sorted by cluster index.
+//   3. The pixels of the tile inside a candidate's window form a rectangle,
+//      cut into 8 x 4 blocks; each (candidate, block) is one work item, and
+//      warps take items from a shared-memory counter until none are left (no
+//      per-pixel scan of the candidate list, no idle warps at a barrier).
+//   4. Each lane walks its pixel's path to the candidate's endpoint, forms D
+//      (Eq. 1-3) and takes a 64-bit shared-memory atomicMin of (D bits,
+//      candidate slot) for its pixel; slots are in cluster order, so ties go
+//      to the smallest k.
+//   5. Each thread writes its pixel's label, and warp-aggregated integer sums
+//      of (1, x, y, L, a, b) are added per candidate in shared memory, then
+//      once per candidate to the global cluster sums.
+// A tile with more candidates or pairs than shared memory holds evaluates
+// its pixels one by one from the global candidate list instead.
 #include <cfloat>
 #include <climits>
 
@@ -74,22 +87,98 @@ __device__ __forceinline__ void tma_load_region<uint2>(const CUtensorMap *tmap, 
         : "memory");
 }
 
+// One sample of the staged plane, by 32-bit shared-memory byte address.
+template <typename T>
+__device__ __forceinline__ float4 lds_sample(uint32_t addr);
+template <>
+__device__ __forceinline__ float4 lds_sample<float4>(uint32_t addr)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(addr));
+    return v;
+}
+template <>
+__device__ __forceinline__ float4 lds_sample<uint2>(uint32_t addr)
+{
+    uint2 u;
+    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(u.x), "=r"(u.y) : "r"(addr));
+    __half2 lo = *reinterpret_cast<__half2 *>(&u.x);
+    __half2 hi = *reinterpret_cast<__half2 *>(&u.y);
+    float2 a = __half22float2(lo), b = __half22float2(hi);
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
+// Path sums of Eq. 1 and Eq. 2 over the staged region (row pitch BX elements,
+// element (0,0) = image pixel (rx0, ry0)).
+template <typename T>
+__device__ __forceinline__ int path_sums_smem(uint32_t region, int BX, int rx0, int ry0,
+                                              const PathSetup &s, float cL, float ca, float cb,
+                                              float &sum_dc, float &sum_w)
+{
+    int smaj, smin;
+    path_strides(s, BX, smaj, smin);
+    const uint32_t q0 = region + (uint32_t)(((s.ay - ry0) * BX + (s.ax - rx0)) * (int)sizeof(T));
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, bw = 0.f;
+    int len = walk_steps(q0, smaj * (int)sizeof(T), smin * (int)sizeof(T), s, [&](uint32_t q) {
+        float4 v = lds_sample<T>(q);
+        float dl = v.x - cL, da = v.y - ca, db = v.z - cb;
+        a0 = fmaf(dl, dl, a0);
+        a1 = fmaf(da, da, a1);
+        a2 = fmaf(db, db, a2);
+        bw += v.w;
+    });
+    sum_dc = (a0 + a1) + a2;
+    sum_w = bw;
+    return len;
+}
+
 __host__ __device__ inline size_t region_bytes(int halo, int elem)
 {
     size_t bx = TILE_X + 2 * halo, by = TILE_Y + 2 * halo;
     return (bx * by * elem + 127) & ~(size_t)127;
 }
 
+// Shared-memory layout after the staged region; every section starts on a
+// 16-byte boundary (int4 loads, 8-byte atomics and the mbarrier need it).
+constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+struct AssignSmem {
+    static constexpr size_t cand = 0;
+    static constexpr size_t cid = align16(cand + MAX_TILE_CANDIDATES * sizeof(ClusterDev));
+    static constexpr size_t rect = align16(cid + MAX_TILE_CANDIDATES * sizeof(int));
+    static constexpr size_t sacc = align16(rect + MAX_TILE_CANDIDATES * sizeof(int4));
+    static constexpr size_t best = align16(sacc + MAX_TILE_CANDIDATES * sizeof(ClusterAcc));
+    static constexpr size_t first = align16(best + ASSIGN_THREADS * sizeof(unsigned long long));
+    static constexpr size_t misc = align16(first + (MAX_TILE_CANDIDATES + 1) * sizeof(int));
+    static constexpr size_t total = align16(misc + 64);
+};
+static_assert(AssignSmem::cid % 16 == 0 && AssignSmem::rect % 16 == 0 && AssignSmem::sacc % 16 == 0 &&
+                  AssignSmem::best % 16 == 0 && AssignSmem::first % 16 == 0 &&
+                  AssignSmem::misc % 16 == 0 && (AssignSmem::misc + 32) % 8 == 0,
+              "shared-memory sections aligned");
+static_assert(MAX_TILE_CANDIDATES * sizeof(ClusterAcc) == ASSIGN_THREADS * 8,
+              "one thread clears one word of the slot sums");
+static_assert(MAX_TILE_CANDIDATES <= ASSIGN_THREADS && MAX_TILE_CANDIDATES % 32 == 0,
+              "one thread per candidate; the item scan gives each lane a whole number of them");
+
 size_t assign_smem_bytes(int halo, int storage)
 {
     size_t elem = storage == 0 ? 16 : 8;
     size_t r = halo > 0 ? region_bytes(halo, (int)elem) : 0;
-    return r + MAX_TILE_CANDIDATES * sizeof(ClusterDev) + MAX_TILE_CANDIDATES * sizeof(ClusterAcc) +
-           16;
+    return r + AssignSmem::total;
 }
 
 constexpr int MBAR_MAX_POLLS = 1 << 22;
 
+__device__ __forceinline__ unsigned long long pack_best(float D, int slot)
+{
+    // D >= 0, so its IEEE bits order like the value; ties fall to the slot
+    return ((unsigned long long)__float_as_uint(D) << 32) | (unsigned)slot;
+}
+
+// Items: the pixels of a candidate's window that lie in the tile form a
+// rectangle; it is cut into 8 x 4 blocks, one block per warp-sized item.
 template <typename T, bool STAGED>
 __global__ void __launch_bounds__(ASSIGN_THREADS, 1)
     k_assign(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
@@ -100,9 +189,11 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 1)
     const int tile = blockIdx.x;
     const int tx = tile % a.n_tx, ty = tile / a.n_tx;
     const int x0 = tx * TILE_X, y0 = ty * TILE_Y;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int px = x0 + (warp % (TILE_X / WARP_BLOCK_X)) * WARP_BLOCK_X + (lane % WARP_BLOCK_X);
-    const int py = y0 + (warp / (TILE_X / WARP_BLOCK_X)) * WARP_BLOCK_Y + (lane / WARP_BLOCK_X);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int lx = (warp % (TILE_X / WARP_BLOCK_X)) * WARP_BLOCK_X + (lane % WARP_BLOCK_X);
+    const int ly = (warp / (TILE_X / WARP_BLOCK_X)) * WARP_BLOCK_Y + (lane / WARP_BLOCK_X);
+    const int lp = ly * TILE_X + lx;  // this thread's pixel within the tile
+    const int px = x0 + lx, py = y0 + ly;
     const bool valid = px < a.W && py < a.H;
     const long long p = (long long)py * a.W + px;
 
@@ -110,12 +201,18 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 1)
     const int BX = TILE_X + 2 * halo, BY = TILE_Y + 2 * halo;
     const int rx0 = x0 - halo, ry0 = y0 - halo;
     const size_t rbytes = STAGED ? region_bytes(halo, sizeof(T)) : 0;
-    T *region = reinterpret_cast<T *>(smem);
-    ClusterDev *cand = reinterpret_cast<ClusterDev *>(smem + rbytes);
-    ClusterAcc *sacc = reinterpret_cast<ClusterAcc *>(cand + MAX_TILE_CANDIDATES);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sacc + MAX_TILE_CANDIDATES);
+    unsigned char *sm = smem + rbytes;
+    const uint32_t region = smem_u32(smem);
+    ClusterDev *cand = reinterpret_cast<ClusterDev *>(sm + AssignSmem::cand);
+    int *cid = reinterpret_cast<int *>(sm + AssignSmem::cid);
+    int4 *rect = reinterpret_cast<int4 *>(sm + AssignSmem::rect);
+    ClusterAcc *sacc = reinterpret_cast<ClusterAcc *>(sm + AssignSmem::sacc);
+    unsigned long long *best = reinterpret_cast<unsigned long long *>(sm + AssignSmem::best);
+    int *first = reinterpret_cast<int *>(sm + AssignSmem::first);
+    int *misc = reinterpret_cast<int *>(sm + AssignSmem::misc);
+    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + AssignSmem::misc + 32);
 
-    if (STAGED && threadIdx.x == 0) {
+    if (STAGED && tid == 0) {
         uint32_t bar = smem_u32(mbar);
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -125,22 +222,73 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 1)
             "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
             "r"(bytes)
             : "memory");
-        tma_load_region<T>(&tmap, smem_u32(region), bar, rx0, ry0);
+        tma_load_region<T>(&tmap, region, bar, rx0, ry0);
     }
 
     const int off = a.tile_off[tile];
     // the list capacity is a proven bound; the clamp only guards memory if the
     // device-side overflow check (reported as an error) ever fired
     const int cnt = (int)max(0LL, min((long long)a.tile_off[tile + 1], a.tile_cap) - off);
-    for (int i = threadIdx.x; i < MAX_TILE_CANDIDATES * 8; i += ASSIGN_THREADS)
-        reinterpret_cast<unsigned long long *>(sacc)[i] = 0ull;
+    const bool fast = cnt <= MAX_TILE_CANDIDATES;
+
+    // candidates sorted by cluster index (ranks of distinct ids); the id
+    // staging reuses the `best` words before they are initialised
+    int *ids = reinterpret_cast<int *>(best);
+    int myid = INT_MAX;
+    if (fast && tid < cnt) {
+        myid = a.tile_list[off + tid];
+        ids[tid] = myid;
+    }
+    if (tid == 0) misc[1] = 0;  // work counter
+    __syncthreads();
+    int nblk = 0;
+    if (fast && tid < cnt) {
+        int rank = 0;
+        for (int j = 0; j < cnt; ++j) rank += ids[j] < myid;
+        const ClusterDev cd = a.cdev[myid];
+        cid[rank] = myid;
+        cand[rank] = cd;
+        // window x tile (clipped to the image), in 8 x 4 blocks
+        const int xa = max(cd.xlo, x0), xb = min(min(cd.xhi, x0 + TILE_X - 1), a.W - 1);
+        const int ya = max(cd.ylo, y0), yb = min(min(cd.yhi, y0 + TILE_Y - 1), a.H - 1);
+        if (xa <= xb && ya <= yb)
+            nblk = ((xb - xa) / WARP_BLOCK_X + 1) * ((yb - ya) / WARP_BLOCK_Y + 1);
+        rect[rank] = make_int4(xa, ya, xb, yb);
+        first[rank] = nblk;  // block count, turned into a prefix below
+    }
+    __syncthreads();
+    best[tid] = ~0ull;
+    reinterpret_cast<unsigned long long *>(sacc)[tid] = 0ull;
+    if (warp == 0 && fast) {
+        // exclusive prefix of the per-candidate block counts (4 per lane)
+        constexpr int PER = MAX_TILE_CANDIDATES / 32;
+        int v[PER], sum = 0;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int c = lane * PER + i;
+            v[i] = c < cnt ? first[c] : 0;
+            sum += v[i];
+        }
+        int incl = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        int run = incl - sum;
+#pragma unroll
+        for (int i = 0; i < PER; ++i) {
+            const int c = lane * PER + i;
+            if (c < cnt) first[c] = run;
+            run += v[i];
+        }
+        if (lane == 31) first[cnt] = incl;
+    }
 
     bool staged_ok = true;
     if (STAGED) {
-        __syncthreads();  // barrier initialised before anyone polls it
         staged_ok = mbar_wait_bounded(smem_u32(mbar), 0, MBAR_MAX_POLLS);
         if (!staged_ok) {
-            if (threadIdx.x == 0) atomicExch(&a.ctr->timeout, 1);
+            if (tid == 0) atomicExch(&a.ctr->timeout, 1);
             // let the copy land (bounded) before the CTA releases its memory
             mbar_wait_bounded(smem_u32(mbar), 0, MBAR_MAX_POLLS);
         }
@@ -149,58 +297,108 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 1)
 
     float4 own = make_float4(0.f, 0.f, 0.f, 0.f);
     if (valid) {
-        own = STAGED ? fetch_sample<T>(region + (py - ry0) * BX + (px - rx0))
+        own = STAGED ? lds_sample<T>(region + (uint32_t)(((ly + halo) * BX + lx + halo) * (int)sizeof(T)))
                      : fetch_sample<T>(plane + (long long)py * a.pitch + px);
     }
-    float best = FLT_MAX;
-    int bestk = INT_MAX, bestslot = -1;
     unsigned long long my_samples = 0, my_pairs = 0;
+    int bestk = INT_MAX;  // per-pixel path only
 
-    for (int base = 0; base < cnt; base += MAX_TILE_CANDIDATES) {
-        const int nb = min(MAX_TILE_CANDIDATES, cnt - base);
-        __syncthreads();
-        for (int i = threadIdx.x; i < nb; i += ASSIGN_THREADS)
-            cand[i] = a.cdev[a.tile_list[off + base + i]];
-        __syncthreads();
-        if (!valid) continue;
-        for (int c = 0; c < nb; ++c) {
+    if (fast) {
+        const int n_items = first[cnt];
+        while (true) {
+            int item = 0;
+            if (lane == 0) item = atomicAdd(&misc[1], 1);
+            item = __shfl_sync(0xffffffffu, item, 0);
+            if (item >= n_items) break;
+            // the candidate owning this item: last c with first[c] <= item
+            int lo = 0, hi = cnt - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (first[mid] <= item) lo = mid;
+                else hi = mid - 1;
+            }
+            const int c = lo;
+            const int4 rc = rect[c];
+            const int nbx = (rc.z - rc.x) / WARP_BLOCK_X + 1;
+            const int local = item - first[c];
+            const int qx = rc.x + (local % nbx) * WARP_BLOCK_X + (lane % WARP_BLOCK_X);
+            const int qy = rc.y + (local / nbx) * WARP_BLOCK_Y + (lane / WARP_BLOCK_X);
+            if (qx > rc.z || qy > rc.w) continue;
             const ClusterDev cd = cand[c];
-            if (px < cd.xlo || px > cd.xhi || py < cd.ylo || py > cd.yhi) continue;
-            const PathSetup s = path_setup(px, py, cd.ex, cd.ey);
+            const PathSetup s = path_setup(qx, qy, cd.ex, cd.ey);
+            const bool inside = STAGED && cd.ex >= rx0 && cd.ex < rx0 + BX && cd.ey >= ry0 &&
+                                cd.ey < ry0 + BY;
             float sdc, sw;
             int len;
-            bool inside = STAGED && cd.ex >= rx0 && cd.ex < rx0 + BX && cd.ey >= ry0 &&
-                          cd.ey < ry0 + BY;
-            if (inside) len = path_sums<T>(region, BX, rx0, ry0, s, cd.L, cd.a, cd.b, sdc, sw);
-            else len = path_sums<T>(plane, a.pitch, 0, 0, s, cd.L, cd.a, cd.b, sdc, sw);
-            float dl = own.x - cd.L, da = own.y - cd.a, db = own.z - cd.b;
-            float dcp = fmaf(dl, dl, fmaf(da, da, db * db));
-            float ddx = (float)px - cd.xk, ddy = (float)py - cd.yk;
-            float ds = fmaf(ddx, ddx, ddy * ddy);
-            float D = scalp_distance(dcp, sdc, sw, len, a.lam, a.gamma, a.ms2, ds);
-            const int k = cd.pad;
-            if (D < best || (D == best && k < bestk)) {
-                best = D;
+            float4 v;
+            if (inside) {
+                len = path_sums_smem<T>(region, BX, rx0, ry0, s, cd.L, cd.a, cd.b, sdc, sw);
+                v = lds_sample<T>(region + (uint32_t)(((qy - ry0) * BX + (qx - rx0)) * (int)sizeof(T)));
+            } else {
+                len = path_sums<T>(plane, a.pitch, 0, 0, s, cd.L, cd.a, cd.b, sdc, sw);
+                v = fetch_sample<T>(plane + (long long)qy * a.pitch + qx);
+            }
+            const float dl = v.x - cd.L, da = v.y - cd.a, db = v.z - cd.b;
+            const float dcp = fmaf(dl, dl, fmaf(da, da, db * db));
+            const float ddx = (float)qx - cd.xk, ddy = (float)qy - cd.yk;
+            const float ds = fmaf(ddx, ddx, ddy * ddy);
+            const float D = scalp_distance(dcp, sdc, sw, len, a.lam, a.gamma, a.ms2, ds);
+            atomicMin(&best[(qy - y0) * TILE_X + (qx - x0)], pack_best(D, c));
+            my_samples += len;
+            my_pairs += 1;
+        }
+    } else if (valid) {
+        // per-pixel path: every candidate straight from the global list
+        float bestD = FLT_MAX;
+        for (int j = 0; j < cnt; ++j) {
+            const int k = a.tile_list[off + j];
+            const ClusterDev cd = a.cdev[k];
+            if (px < cd.xlo || px > cd.xhi || py < cd.ylo || py > cd.yhi) continue;
+            const PathSetup s = path_setup(px, py, cd.ex, cd.ey);
+            const bool inside = STAGED && cd.ex >= rx0 && cd.ex < rx0 + BX && cd.ey >= ry0 &&
+                                cd.ey < ry0 + BY;
+            float sdc, sw;
+            const int len = inside ? path_sums_smem<T>(region, BX, rx0, ry0, s, cd.L, cd.a, cd.b, sdc, sw)
+                                   : path_sums<T>(plane, a.pitch, 0, 0, s, cd.L, cd.a, cd.b, sdc, sw);
+            const float dl = own.x - cd.L, da = own.y - cd.a, db = own.z - cd.b;
+            const float dcp = fmaf(dl, dl, fmaf(da, da, db * db));
+            const float ddx = (float)px - cd.xk, ddy = (float)py - cd.yk;
+            const float ds = fmaf(ddx, ddx, ddy * ddy);
+            const float D = scalp_distance(dcp, sdc, sw, len, a.lam, a.gamma, a.ms2, ds);
+            if (D < bestD || (D == bestD && k < bestk)) {
+                bestD = D;
                 bestk = k;
-                bestslot = base + c;
             }
             my_samples += len;
             my_pairs += 1;
         }
     }
+    __syncthreads();
 
-    int lab = 0;
+    // labels and the fused partial sums of the cluster update
+    int lab = 0, slot = -1;
+    bool found;
+    if (fast) {
+        const unsigned long long b = best[lp];
+        found = b != ~0ull;
+        if (found) {
+            slot = (int)(b & 0xffffffffu);
+            lab = cid[slot];
+        }
+    } else {
+        found = bestk != INT_MAX;
+        lab = bestk;
+    }
     if (valid) {
-        if (bestk != INT_MAX) {
-            lab = bestk;
+        if (found) {
             a.labels[p] = lab;
         } else {
             lab = a.labels[p];  // no window reaches p: keep its label
             atomicAdd(&a.ctr->orphans, 1);
         }
     }
-    const bool in_slot = valid && bestslot >= 0 && bestslot < MAX_TILE_CANDIDATES;
-    warp_aggregate_tile(in_slot, bestslot, px, py, own, sacc);
+    const bool in_slot = valid && fast && found;
+    warp_aggregate_tile(in_slot, slot, px, py, own, sacc);
     const bool direct = valid && !in_slot;
     if (__any_sync(0xffffffffu, direct)) warp_aggregate_global(direct, lab, px, py, own, a.acc);
     if (a.count_samples) {
@@ -214,17 +412,18 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 1)
         }
     }
     __syncthreads();
-    const int nslots = min(cnt, MAX_TILE_CANDIDATES);
-    for (int s = threadIdx.x; s < nslots; s += ASSIGN_THREADS) {
-        const ClusterAcc c = sacc[s];
-        if (c.n == 0) continue;
-        ClusterAcc *g = &a.acc[a.tile_list[off + s]];
-        atomicAdd(&g->n, c.n);
-        atomicAdd(&g->sx, c.sx);
-        atomicAdd(&g->sy, c.sy);
-        atomicAdd(&g->sL, c.sL);
-        atomicAdd(&g->sa, c.sa);
-        atomicAdd(&g->sb, c.sb);
+    if (fast) {
+        for (int s = tid; s < cnt; s += ASSIGN_THREADS) {
+            const ClusterAcc c = sacc[s];
+            if (c.n == 0) continue;
+            ClusterAcc *g = &a.acc[cid[s]];
+            atomicAdd(&g->n, c.n);
+            atomicAdd(&g->sx, c.sx);
+            atomicAdd(&g->sy, c.sy);
+            atomicAdd(&g->sL, c.sL);
+            atomicAdd(&g->sa, c.sa);
+            atomicAdd(&g->sb, c.sb);
+        }
     }
 }
 

@@ -9,16 +9,17 @@
 
 namespace scalp {
 
-// Assignment tile: a CTA labels TILE_X x TILE_Y pixels.  Each warp owns an
-// 8 x 4 block of them (one pixel per lane), so the paths a warp walks
-// together start close to one another and have similar lengths.
+// Assignment tile: a CTA of 1024 threads labels TILE_X x TILE_Y pixels.  For
+// the reduction each warp owns an 8 x 4 block of them (one pixel per lane), so
+// the labels a warp sums are spatially coherent.
 constexpr int TILE_X = 32;
-constexpr int TILE_Y = 16;
-constexpr int ASSIGN_THREADS = TILE_X * TILE_Y;  // 512, one pixel per thread
+constexpr int TILE_Y = 32;
+constexpr int ASSIGN_THREADS = TILE_X * TILE_Y;  // 1024, one pixel per thread
 constexpr int WARP_BLOCK_X = 8;
 constexpr int WARP_BLOCK_Y = 4;
-// Candidate clusters of one tile kept in shared memory per pass.
-constexpr int MAX_TILE_CANDIDATES = 64;
+// Candidate clusters of one tile held in shared memory.  A tile with more
+// candidates (never seen on the regular grid) takes a slower per-pixel path.
+constexpr int MAX_TILE_CANDIDATES = 128;
 // Extra halo beyond round(r) so that endpoints projected by Eq. 4 a pixel or
 // two from the barycenter still walk in shared memory.
 constexpr int HALO_MARGIN = 2;
@@ -81,7 +82,7 @@ struct SolveArgs {
 
 __device__ __forceinline__ float4 load_f16x4(const uint2 *p)
 {
-    uint2 u = *p;
+    uint2 u = __ldg(p);
     __half2 lo = *reinterpret_cast<__half2 *>(&u.x);
     __half2 hi = *reinterpret_cast<__half2 *>(&u.y);
     float2 a = __half22float2(lo), b = __half22float2(hi);
@@ -90,8 +91,9 @@ __device__ __forceinline__ float4 load_f16x4(const uint2 *p)
 
 template <typename T>
 __device__ __forceinline__ float4 fetch_sample(const T *q);
+// Read-only global loads of one plane sample.
 template <>
-__device__ __forceinline__ float4 fetch_sample<float4>(const float4 *q) { return *q; }
+__device__ __forceinline__ float4 fetch_sample<float4>(const float4 *q) { return __ldg(q); }
 template <>
 __device__ __forceinline__ float4 fetch_sample<uint2>(const uint2 *q) { return load_f16x4(q); }
 
@@ -125,17 +127,14 @@ __device__ __forceinline__ PathSetup path_setup(int px, int py, int ex, int ey)
     return s;
 }
 
-// Visits the pixels of the path set up by `s` in walking order on a plane
-// with row pitch `pitch` whose element (0,0) is image pixel (ox, oy); `visit`
-// receives a pointer to each sample.  Returns |P| = ns + 1.
-template <typename T, typename Visit>
-__device__ __forceinline__ int walk_path(const T *__restrict__ base, int pitch, int ox, int oy,
-                                         const PathSetup &s, Visit &&visit)
+// Steps through the |P| = ns + 1 samples of a path from its start `q`
+// (an address or offset in any unit): each step adds smaj, plus smin when the
+// error term wraps.  `visit` receives every sample address.  This is the one
+// stepping rule every walker (shared memory, global memory, debug) uses.
+template <typename Addr, typename Visit>
+__device__ __forceinline__ int walk_steps(Addr q, int smaj, int smin, const PathSetup &s,
+                                          Visit &&visit)
 {
-    int smaj, smin;
-    if (s.xmajor) { smaj = 1; smin = s.minor_sgn * pitch; }
-    else { smaj = s.major_sgn_y * pitch; smin = 1; }
-    const T *q = base + (long long)(s.ay - oy) * pitch + (s.ax - ox);
     const int two_ns = 2 * s.ns, two_d = 2 * s.dmin;
     int e = s.ns;
 #pragma unroll 4
@@ -147,6 +146,25 @@ __device__ __forceinline__ int walk_path(const T *__restrict__ base, int pitch, 
         q += step;
     }
     return s.ns + 1;
+}
+
+// Element strides of the major and minor steps on a plane with row pitch `pitch`.
+__device__ __forceinline__ void path_strides(const PathSetup &s, int pitch, int &smaj, int &smin)
+{
+    if (s.xmajor) { smaj = 1; smin = s.minor_sgn * pitch; }
+    else { smaj = s.major_sgn_y * pitch; smin = 1; }
+}
+
+// Visits the pixels of the path on a plane with row pitch `pitch` whose
+// element (0,0) is image pixel (ox, oy).  Returns |P|.
+template <typename T, typename Visit>
+__device__ __forceinline__ int walk_path(const T *__restrict__ base, int pitch, int ox, int oy,
+                                         const PathSetup &s, Visit &&visit)
+{
+    int smaj, smin;
+    path_strides(s, pitch, smaj, smin);
+    const T *q = base + (long long)(s.ay - oy) * pitch + (s.ax - ox);
+    return walk_steps(q, smaj, smin, s, visit);
 }
 
 // Sums along the path of d_c(q, C_k) (Eq. 1) and of the contour factor w(q)
