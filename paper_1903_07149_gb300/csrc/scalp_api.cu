@@ -380,17 +380,19 @@ int scalp_init(scalp_ctx **out, const scalp_image *image, const scalp_contour *c
     if (params->storage == 1) halo = (halo + 1) & ~1;  // even start column for 8-byte TMA
     int BX = TILE_X + 2 * halo, BY = TILE_Y + 2 * halo;
     size_t smem = assign_smem_bytes(halo, params->storage);
-    c->staged = !params->global_walk && BX <= 256 && BY <= 256 && smem <= 227 * 1024;
+    const int box_x = params->storage == 0 ? 2 * BX : BX;  // TMA box elements per row
+    c->staged = !params->global_walk && box_x <= 256 && BY <= 256 && smem <= 227 * 1024;
     PFN_encodeTiled enc = c->staged ? get_encode() : nullptr;
     if (c->staged && !enc) c->staged = false;
     if (c->staged) {
         CUresult r;
         if (params->storage == 0) {
-            cuuint64_t dims[3] = {4, (cuuint64_t)W, (cuuint64_t)H};
-            cuuint64_t strides[2] = {16, (cuuint64_t)L.pitch * 16};
-            cuuint32_t box[3] = {4, (cuuint32_t)BX, (cuuint32_t)BY};
-            cuuint32_t es[3] = {1, 1, 1};
-            r = enc(&c->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, c->ws + L.plane, dims, strides, box,
+            // 16-byte pixels as pairs of 8-byte elements: rows of 2*BX elements
+            cuuint64_t dims[2] = {2 * (cuuint64_t)W, (cuuint64_t)H};
+            cuuint64_t strides[1] = {(cuuint64_t)L.pitch * 16};
+            cuuint32_t box[2] = {2 * (cuuint32_t)BX, (cuuint32_t)BY};
+            cuuint32_t es[2] = {1, 1};
+            r = enc(&c->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, c->ws + L.plane, dims, strides, box,
                     es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                     CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         } else {

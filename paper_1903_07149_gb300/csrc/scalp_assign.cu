@@ -7,7 +7,7 @@
 // clusters (those whose window holds it, from its tile's candidate list) and
 // keeps the smallest (D, k) pair: the same result, in any evaluation order.
 //
-// One CTA (1024 threads) labels a 32 x 32 tile:
+// One CTA (1024 threads for FP32 planes, 512 for FP16) labels a 32 x 32 tile:
 //   1. One thread issues a TMA bulk-tensor load of the (L, a, b, w) plane of
 //      the tile plus a halo of round(r) + 2 pixels into shared memory (zero
 //      fill outside the image).  Every path to an endpoint inside that region
@@ -23,9 +23,9 @@
 //      (Eq. 1-3) and takes a 64-bit shared-memory atomicMin of (D bits,
 //      candidate slot) for its pixel; slots are in cluster order, so ties go
 //      to the smallest k.
-//   5. Each thread writes its pixel's label, and warp-aggregated integer sums
-//      of (1, x, y, L, a, b) are added per candidate in shared memory, then
-//      once per candidate to the global cluster sums.
+//   5. Each thread writes its pixel's label; warp-aggregated integer sums of
+//      (1, x, y, L, a, b) per label go to the global cluster sums as
+//      fire-and-forget reductions.
 // A tile with more candidates or pairs than shared memory holds evaluates
 // its pixels one by one from the global candidate list instead.
 #include <cfloat>
@@ -61,16 +61,17 @@ template <typename T>
 __device__ __forceinline__ void tma_load_region(const CUtensorMap *tmap, uint32_t dst, uint32_t bar,
                                                 int rx0, int ry0);
 
-// FP32 planes: 3-D map {4 channels, W, H} of fp32, box {4, BX, BY}.
+// FP32 planes: 2-D map {2W, H} of 8-byte elements (half a pixel each), box
+// {2BX, BY}: long contiguous rows per request; x = 2*rx0 is 16-byte aligned.
 template <>
 __device__ __forceinline__ void tma_load_region<float4>(const CUtensorMap *tmap, uint32_t dst,
                                                         uint32_t bar, int rx0, int ry0)
 {
     asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%2, %3, %4}], [%5];"
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+        "[%0], [%1, {%2, %3}], [%4];"
         :
-        : "r"(dst), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(0), "r"(rx0), "r"(ry0), "r"(bar)
+        : "r"(dst), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(2 * rx0), "r"(ry0), "r"(bar)
         : "memory");
 }
 
@@ -143,24 +144,24 @@ __host__ __device__ inline size_t region_bytes(int halo, int elem)
 // Shared-memory layout after the staged region; every section starts on a
 // 16-byte boundary (int4 loads, 8-byte atomics and the mbarrier need it).
 constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+constexpr int MAX_ITEMS = MAX_TILE_CANDIDATES * MAX_BLOCKS_PER_CANDIDATE;
 struct AssignSmem {
     static constexpr size_t cand = 0;
     static constexpr size_t cid = align16(cand + MAX_TILE_CANDIDATES * sizeof(ClusterDev));
     static constexpr size_t rect = align16(cid + MAX_TILE_CANDIDATES * sizeof(int));
-    static constexpr size_t sacc = align16(rect + MAX_TILE_CANDIDATES * sizeof(int4));
-    static constexpr size_t best = align16(sacc + MAX_TILE_CANDIDATES * sizeof(ClusterAcc));
-    static constexpr size_t first = align16(best + ASSIGN_THREADS * sizeof(unsigned long long));
-    static constexpr size_t misc = align16(first + (MAX_TILE_CANDIDATES + 1) * sizeof(int));
+    static constexpr size_t best = align16(rect + MAX_TILE_CANDIDATES * sizeof(int4));
+    static constexpr size_t first = align16(best + TILE_PIXELS * sizeof(unsigned long long));
+    static constexpr size_t owner = align16(first + (MAX_TILE_CANDIDATES + 1) * sizeof(int));
+    static constexpr size_t misc = align16(owner + MAX_ITEMS);
     static constexpr size_t total = align16(misc + 64);
 };
-static_assert(AssignSmem::cid % 16 == 0 && AssignSmem::rect % 16 == 0 && AssignSmem::sacc % 16 == 0 &&
+static_assert(AssignSmem::cid % 16 == 0 && AssignSmem::rect % 16 == 0 &&
                   AssignSmem::best % 16 == 0 && AssignSmem::first % 16 == 0 &&
-                  AssignSmem::misc % 16 == 0 && (AssignSmem::misc + 32) % 8 == 0,
+                  AssignSmem::owner % 16 == 0 && AssignSmem::misc % 16 == 0 &&
+                  (AssignSmem::misc + 32) % 8 == 0,
               "shared-memory sections aligned");
-static_assert(MAX_TILE_CANDIDATES * sizeof(ClusterAcc) == ASSIGN_THREADS * 8,
-              "one thread clears one word of the slot sums");
-static_assert(MAX_TILE_CANDIDATES <= ASSIGN_THREADS && MAX_TILE_CANDIDATES % 32 == 0,
-              "one thread per candidate; the item scan gives each lane a whole number of them");
+static_assert(MAX_TILE_CANDIDATES <= 256, "item owners are bytes");
+static_assert(MAX_TILE_CANDIDATES % 32 == 0, "the item scan gives each lane whole candidates");
 
 size_t assign_smem_bytes(int halo, int storage)
 {
@@ -168,6 +169,11 @@ size_t assign_smem_bytes(int halo, int storage)
     size_t r = halo > 0 ? region_bytes(halo, (int)elem) : 0;
     return r + AssignSmem::total;
 }
+
+// Threads per CTA: FP32 tiles use one 1024-thread CTA per SM (the staged
+// region fills shared memory); FP16 tiles use 512-thread CTAs, two per SM, so
+// one CTA's set-up and tail overlap the other's walks.
+int assign_threads(int storage) { return storage == 0 ? 1024 : 512; }
 
 constexpr int MBAR_MAX_POLLS = 1 << 22;
 
@@ -179,10 +185,12 @@ __device__ __forceinline__ unsigned long long pack_best(float D, int slot)
 
 // Items: the pixels of a candidate's window that lie in the tile form a
 // rectangle; it is cut into 8 x 4 blocks, one block per warp-sized item.
-template <typename T, bool STAGED>
-__global__ void __launch_bounds__(ASSIGN_THREADS, 1)
+template <typename T, bool STAGED, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS)
     k_assign(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
 {
+    constexpr int PIX_PER_THREAD = TILE_PIXELS / THREADS;
+    constexpr int WARPS = THREADS / 32;
     extern __shared__ __align__(1024) unsigned char smem[];
     const T *__restrict__ plane = reinterpret_cast<const T *>(
         sizeof(T) == 16 ? (const void *)a.plane32 : (const void *)a.plane16);
@@ -190,12 +198,6 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 1)
     const int tx = tile % a.n_tx, ty = tile / a.n_tx;
     const int x0 = tx * TILE_X, y0 = ty * TILE_Y;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int lx = (warp % (TILE_X / WARP_BLOCK_X)) * WARP_BLOCK_X + (lane % WARP_BLOCK_X);
-    const int ly = (warp / (TILE_X / WARP_BLOCK_X)) * WARP_BLOCK_Y + (lane / WARP_BLOCK_X);
-    const int lp = ly * TILE_X + lx;  // this thread's pixel within the tile
-    const int px = x0 + lx, py = y0 + ly;
-    const bool valid = px < a.W && py < a.H;
-    const long long p = (long long)py * a.W + px;
 
     const int halo = STAGED ? a.halo : 0;
     const int BX = TILE_X + 2 * halo, BY = TILE_Y + 2 * halo;
@@ -206,9 +208,9 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 1)
     ClusterDev *cand = reinterpret_cast<ClusterDev *>(sm + AssignSmem::cand);
     int *cid = reinterpret_cast<int *>(sm + AssignSmem::cid);
     int4 *rect = reinterpret_cast<int4 *>(sm + AssignSmem::rect);
-    ClusterAcc *sacc = reinterpret_cast<ClusterAcc *>(sm + AssignSmem::sacc);
     unsigned long long *best = reinterpret_cast<unsigned long long *>(sm + AssignSmem::best);
     int *first = reinterpret_cast<int *>(sm + AssignSmem::first);
+    unsigned char *owner = sm + AssignSmem::owner;
     int *misc = reinterpret_cast<int *>(sm + AssignSmem::misc);
     uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + AssignSmem::misc + 32);
 
@@ -241,7 +243,6 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 1)
     }
     if (tid == 0) misc[1] = 0;  // work counter
     __syncthreads();
-    int nblk = 0;
     if (fast && tid < cnt) {
         int rank = 0;
         for (int j = 0; j < cnt; ++j) rank += ids[j] < myid;
@@ -251,14 +252,16 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 1)
         // window x tile (clipped to the image), in 8 x 4 blocks
         const int xa = max(cd.xlo, x0), xb = min(min(cd.xhi, x0 + TILE_X - 1), a.W - 1);
         const int ya = max(cd.ylo, y0), yb = min(min(cd.yhi, y0 + TILE_Y - 1), a.H - 1);
-        if (xa <= xb && ya <= yb)
-            nblk = ((xb - xa) / WARP_BLOCK_X + 1) * ((yb - ya) / WARP_BLOCK_Y + 1);
-        rect[rank] = make_int4(xa, ya, xb, yb);
-        first[rank] = nblk;  // block count, turned into a prefix below
+        int nbx = 0, nblk = 0;
+        if (xa <= xb && ya <= yb) {
+            nbx = (xb - xa) / WARP_BLOCK_X + 1;
+            nblk = nbx * ((yb - ya) / WARP_BLOCK_Y + 1);
+        }
+        // (x origin, y origin, blocks per row, blocks)
+        rect[rank] = make_int4(xa, ya, nbx, nblk);
     }
     __syncthreads();
-    best[tid] = ~0ull;
-    reinterpret_cast<unsigned long long *>(sacc)[tid] = 0ull;
+    for (int i = tid; i < TILE_PIXELS; i += THREADS) best[i] = ~0ull;
     if (warp == 0 && fast) {
         // exclusive prefix of the per-candidate block counts (4 per lane)
         constexpr int PER = MAX_TILE_CANDIDATES / 32;
@@ -266,7 +269,7 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 1)
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
             const int c = lane * PER + i;
-            v[i] = c < cnt ? first[c] : 0;
+            v[i] = c < cnt ? rect[c].w : 0;
             sum += v[i];
         }
         int incl = sum;
@@ -283,6 +286,11 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 1)
         }
         if (lane == 31) first[cnt] = incl;
     }
+    __syncthreads();
+    if (fast && tid < cnt) {
+        const int f = first[tid], n = rect[tid].w;
+        for (int j = 0; j < n; ++j) owner[f + j] = (unsigned char)tid;
+    }
 
     bool staged_ok = true;
     if (STAGED) {
@@ -295,13 +303,17 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 1)
     }
     if (!__syncthreads_and(staged_ok)) return;
 
-    float4 own = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (valid) {
-        own = STAGED ? lds_sample<T>(region + (uint32_t)(((ly + halo) * BX + lx + halo) * (int)sizeof(T)))
-                     : fetch_sample<T>(plane + (long long)py * a.pitch + px);
-    }
     unsigned long long my_samples = 0, my_pairs = 0;
-    int bestk = INT_MAX;  // per-pixel path only
+    int bestk[PIX_PER_THREAD];  // per-pixel path only
+#pragma unroll
+    for (int j = 0; j < PIX_PER_THREAD; ++j) bestk[j] = INT_MAX;
+
+    // this thread's pixels: block (warp + j*WARPS) of the tile, lane within it
+    auto my_pixel = [&](int j, int &qx, int &qy) {
+        const int blk = warp + j * WARPS;
+        qx = x0 + (blk % (TILE_X / WARP_BLOCK_X)) * WARP_BLOCK_X + (lane % WARP_BLOCK_X);
+        qy = y0 + (blk / (TILE_X / WARP_BLOCK_X)) * WARP_BLOCK_Y + (lane / WARP_BLOCK_X);
+    };
 
     if (fast) {
         const int n_items = first[cnt];
@@ -310,21 +322,16 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 1)
             if (lane == 0) item = atomicAdd(&misc[1], 1);
             item = __shfl_sync(0xffffffffu, item, 0);
             if (item >= n_items) break;
-            // the candidate owning this item: last c with first[c] <= item
-            int lo = 0, hi = cnt - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (first[mid] <= item) lo = mid;
-                else hi = mid - 1;
-            }
-            const int c = lo;
+            const int c = owner[item];
             const int4 rc = rect[c];
-            const int nbx = (rc.z - rc.x) / WARP_BLOCK_X + 1;
             const int local = item - first[c];
-            const int qx = rc.x + (local % nbx) * WARP_BLOCK_X + (lane % WARP_BLOCK_X);
-            const int qy = rc.y + (local / nbx) * WARP_BLOCK_Y + (lane / WARP_BLOCK_X);
-            if (qx > rc.z || qy > rc.w) continue;
+            const int by = local / rc.z, bx = local - by * rc.z;
+            const int qx = rc.x + bx * WARP_BLOCK_X + (lane % WARP_BLOCK_X);
+            const int qy = rc.y + by * WARP_BLOCK_Y + (lane / WARP_BLOCK_X);
             const ClusterDev cd = cand[c];
+            if (qx > cd.xhi || qy > cd.yhi || qx >= x0 + TILE_X || qy >= y0 + TILE_Y ||
+                qx >= a.W || qy >= a.H)
+                continue;
             const PathSetup s = path_setup(qx, qy, cd.ex, cd.ey);
             const bool inside = STAGED && cd.ex >= rx0 && cd.ex < rx0 + BX && cd.ey >= ry0 &&
                                 cd.ey < ry0 + BY;
@@ -347,60 +354,76 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 1)
             my_samples += len;
             my_pairs += 1;
         }
-    } else if (valid) {
+    } else {
         // per-pixel path: every candidate straight from the global list
-        float bestD = FLT_MAX;
-        for (int j = 0; j < cnt; ++j) {
-            const int k = a.tile_list[off + j];
-            const ClusterDev cd = a.cdev[k];
-            if (px < cd.xlo || px > cd.xhi || py < cd.ylo || py > cd.yhi) continue;
-            const PathSetup s = path_setup(px, py, cd.ex, cd.ey);
-            const bool inside = STAGED && cd.ex >= rx0 && cd.ex < rx0 + BX && cd.ey >= ry0 &&
-                                cd.ey < ry0 + BY;
-            float sdc, sw;
-            const int len = inside ? path_sums_smem<T>(region, BX, rx0, ry0, s, cd.L, cd.a, cd.b, sdc, sw)
-                                   : path_sums<T>(plane, a.pitch, 0, 0, s, cd.L, cd.a, cd.b, sdc, sw);
-            const float dl = own.x - cd.L, da = own.y - cd.a, db = own.z - cd.b;
-            const float dcp = fmaf(dl, dl, fmaf(da, da, db * db));
-            const float ddx = (float)px - cd.xk, ddy = (float)py - cd.yk;
-            const float ds = fmaf(ddx, ddx, ddy * ddy);
-            const float D = scalp_distance(dcp, sdc, sw, len, a.lam, a.gamma, a.ms2, ds);
-            if (D < bestD || (D == bestD && k < bestk)) {
-                bestD = D;
-                bestk = k;
+#pragma unroll 1
+        for (int j = 0; j < PIX_PER_THREAD; ++j) {
+            int px, py;
+            my_pixel(j, px, py);
+            if (px >= a.W || py >= a.H) continue;
+            const float4 own = STAGED ? lds_sample<T>(region + (uint32_t)(((py - ry0) * BX + (px - rx0)) * (int)sizeof(T)))
+                                      : fetch_sample<T>(plane + (long long)py * a.pitch + px);
+            float bestD = FLT_MAX;
+            for (int i = 0; i < cnt; ++i) {
+                const int k = a.tile_list[off + i];
+                const ClusterDev cd = a.cdev[k];
+                if (px < cd.xlo || px > cd.xhi || py < cd.ylo || py > cd.yhi) continue;
+                const PathSetup s = path_setup(px, py, cd.ex, cd.ey);
+                const bool inside = STAGED && cd.ex >= rx0 && cd.ex < rx0 + BX && cd.ey >= ry0 &&
+                                    cd.ey < ry0 + BY;
+                float sdc, sw;
+                const int len = inside ? path_sums_smem<T>(region, BX, rx0, ry0, s, cd.L, cd.a, cd.b, sdc, sw)
+                                       : path_sums<T>(plane, a.pitch, 0, 0, s, cd.L, cd.a, cd.b, sdc, sw);
+                const float dl = own.x - cd.L, da = own.y - cd.a, db = own.z - cd.b;
+                const float dcp = fmaf(dl, dl, fmaf(da, da, db * db));
+                const float ddx = (float)px - cd.xk, ddy = (float)py - cd.yk;
+                const float ds = fmaf(ddx, ddx, ddy * ddy);
+                const float D = scalp_distance(dcp, sdc, sw, len, a.lam, a.gamma, a.ms2, ds);
+                if (D < bestD || (D == bestD && k < bestk[j])) {
+                    bestD = D;
+                    bestk[j] = k;
+                }
+                my_samples += len;
+                my_pairs += 1;
             }
-            my_samples += len;
-            my_pairs += 1;
         }
     }
     __syncthreads();
 
     // labels and the fused partial sums of the cluster update
-    int lab = 0, slot = -1;
-    bool found;
-    if (fast) {
-        const unsigned long long b = best[lp];
-        found = b != ~0ull;
-        if (found) {
-            slot = (int)(b & 0xffffffffu);
-            lab = cid[slot];
+#pragma unroll 1
+    for (int j = 0; j < PIX_PER_THREAD; ++j) {
+        int px, py;
+        my_pixel(j, px, py);
+        const bool valid = px < a.W && py < a.H;
+        const long long p = (long long)py * a.W + px;
+        float4 own = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (valid) {
+            own = STAGED ? lds_sample<T>(region + (uint32_t)(((py - ry0) * BX + (px - rx0)) * (int)sizeof(T)))
+                         : fetch_sample<T>(plane + (long long)py * a.pitch + px);
         }
-    } else {
-        found = bestk != INT_MAX;
-        lab = bestk;
-    }
-    if (valid) {
-        if (found) {
-            a.labels[p] = lab;
+        int lab = 0;
+        bool found;
+        if (fast) {
+            const unsigned long long b = best[(py - y0) * TILE_X + (px - x0)];
+            found = b != ~0ull;
+            if (found) lab = cid[(int)(b & 0xffffffffu)];
         } else {
-            lab = a.labels[p];  // no window reaches p: keep its label
-            atomicAdd(&a.ctr->orphans, 1);
+            found = bestk[j] != INT_MAX;
+            lab = bestk[j];
         }
+        if (valid) {
+            if (found) {
+                a.labels[p] = lab;
+            } else {
+                lab = a.labels[p];  // no window reaches p: keep its label
+                atomicAdd(&a.ctr->orphans, 1);
+            }
+        }
+        // warp-aggregated sums straight into the global cluster sums
+        // (fire-and-forget reductions, one set per label group of the warp)
+        warp_aggregate_global(valid, lab, px, py, own, a.acc);
     }
-    const bool in_slot = valid && fast && found;
-    warp_aggregate_tile(in_slot, slot, px, py, own, sacc);
-    const bool direct = valid && !in_slot;
-    if (__any_sync(0xffffffffu, direct)) warp_aggregate_global(direct, lab, px, py, own, a.acc);
     if (a.count_samples) {
         for (int o = 16; o > 0; o >>= 1) {
             my_samples += __shfl_down_sync(0xffffffffu, my_samples, o);
@@ -411,45 +434,33 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, 1)
             atomicAdd(&a.ctr->pairs, my_pairs);
         }
     }
-    __syncthreads();
-    if (fast) {
-        for (int s = tid; s < cnt; s += ASSIGN_THREADS) {
-            const ClusterAcc c = sacc[s];
-            if (c.n == 0) continue;
-            ClusterAcc *g = &a.acc[cid[s]];
-            atomicAdd(&g->n, c.n);
-            atomicAdd(&g->sx, c.sx);
-            atomicAdd(&g->sy, c.sy);
-            atomicAdd(&g->sL, c.sL);
-            atomicAdd(&g->sa, c.sa);
-            atomicAdd(&g->sb, c.sb);
-        }
-    }
 }
 
-template <typename T, bool STAGED>
+template <typename T, bool STAGED, int THREADS>
 static void launch_one(const SolveArgs &a, const CUtensorMap &tmap, size_t smem, cudaStream_t st)
 {
-    k_assign<T, STAGED><<<a.n_tx * a.n_ty, ASSIGN_THREADS, smem, st>>>(a, tmap);
+    k_assign<T, STAGED, THREADS><<<a.n_tx * a.n_ty, THREADS, smem, st>>>(a, tmap);
 }
 
 void launch_assign(const SolveArgs &a, int storage, bool staged, const CUtensorMap &tmap,
                    size_t smem_bytes, cudaStream_t st)
 {
     if (storage == 0) {
-        if (staged) launch_one<float4, true>(a, tmap, smem_bytes, st);
-        else launch_one<float4, false>(a, tmap, smem_bytes, st);
+        if (staged) launch_one<float4, true, 1024>(a, tmap, smem_bytes, st);
+        else launch_one<float4, false, 1024>(a, tmap, smem_bytes, st);
     } else {
-        if (staged) launch_one<uint2, true>(a, tmap, smem_bytes, st);
-        else launch_one<uint2, false>(a, tmap, smem_bytes, st);
+        if (staged) launch_one<uint2, true, 512>(a, tmap, smem_bytes, st);
+        else launch_one<uint2, false, 512>(a, tmap, smem_bytes, st);
     }
 }
 
 cudaError_t assign_configure(int storage, bool staged, size_t smem_bytes)
 {
     const void *f;
-    if (storage == 0) f = staged ? (const void *)k_assign<float4, true> : (const void *)k_assign<float4, false>;
-    else f = staged ? (const void *)k_assign<uint2, true> : (const void *)k_assign<uint2, false>;
+    if (storage == 0)
+        f = staged ? (const void *)k_assign<float4, true, 1024> : (const void *)k_assign<float4, false, 1024>;
+    else
+        f = staged ? (const void *)k_assign<uint2, true, 512> : (const void *)k_assign<uint2, false, 512>;
     return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
 

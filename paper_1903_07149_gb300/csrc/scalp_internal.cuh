@@ -9,14 +9,17 @@
 
 namespace scalp {
 
-// Assignment tile: a CTA of 1024 threads labels TILE_X x TILE_Y pixels.  For
-// the reduction each warp owns an 8 x 4 block of them (one pixel per lane), so
-// the labels a warp sums are spatially coherent.
+// Assignment tile: a CTA labels TILE_X x TILE_Y pixels.  For the reduction a
+// warp takes 8 x 4 blocks of them (one pixel per lane), so the labels a warp
+// sums are spatially coherent.
 constexpr int TILE_X = 32;
 constexpr int TILE_Y = 32;
-constexpr int ASSIGN_THREADS = TILE_X * TILE_Y;  // 1024, one pixel per thread
+constexpr int TILE_PIXELS = TILE_X * TILE_Y;
 constexpr int WARP_BLOCK_X = 8;
 constexpr int WARP_BLOCK_Y = 4;
+// Work items: 8 x 4 blocks of a candidate's window inside the tile, at most
+// (TILE_X/8)*(TILE_Y/4) per candidate.
+constexpr int MAX_BLOCKS_PER_CANDIDATE = (TILE_X / WARP_BLOCK_X) * (TILE_Y / WARP_BLOCK_Y);
 // Candidate clusters of one tile held in shared memory.  A tile with more
 // candidates (never seen on the regular grid) takes a slower per-pixel path.
 constexpr int MAX_TILE_CANDIDATES = 128;
@@ -192,7 +195,7 @@ __device__ __forceinline__ int path_sums(const T *__restrict__ base, int pitch, 
 __device__ __forceinline__ float scalp_distance(float dcp, float sum_dc, float sum_w, int len,
                                                 float lam, float gamma, float ms2, float ds)
 {
-    float inv = 1.0f / (float)len;
+    float inv = __frcp_rn((float)len);  // correctly rounded, as 1.0f / len
     float dcol = lam * dcp + (1.0f - lam) * (sum_dc * inv);
     float dcon = 1.0f + gamma * (sum_w * inv);
     return fmaf(dcol, dcon, ms2 * ds);
