@@ -21,7 +21,7 @@ thread_local std::string g_last_error;
 
 struct Layout {
     size_t rgb, contour, plane, labels, parent, size, link, scan, scan_tmp;
-    size_t st_n, st_sx, st_sy, st_col, st_end, cdev, acc, proj;
+    size_t st_n, st_sx, st_sy, st_col, st_end, cdev, acc, proj, prev_win, lut;
     size_t tile_count, tile_off, tile_cursor, tile_list, ctr, nlab, debug;
     size_t total;
     long long tile_cap, scan_tmp_len;
@@ -90,6 +90,8 @@ Layout make_layout(int H, int W, int K, int storage)
     L.cdev = carve(cur, Keff * sizeof(ClusterDev));
     L.acc = carve(cur, Keff * sizeof(ClusterAcc));
     L.proj = carve(cur, Keff * 4);
+    L.prev_win = carve(cur, Keff * 16);
+    L.lut = carve(cur, 256 * 4);
     L.tile_count = carve(cur, n_tiles * 4);
     L.tile_off = carve(cur, (n_tiles + 1) * 4);
     L.tile_cursor = carve(cur, n_tiles * 4);
@@ -221,9 +223,9 @@ int load_inputs(scalp_ctx *c, const scalp_image *img, const scalp_contour *con)
     void *plane = c->ws + c->L.plane;
     launch_setup(c->a, rgb, rs, cp, cs, c->p.storage, plane, c->st);
     launch_accumulate(c->a, c->st);
-    launch_finalize(c->a, c->st);
+    launch_update(c->a, 1, c->st);
     launch_project(c->a, 1, c->st);
-    launch_derive(c->a, c->st);
+    launch_lists(c->a, c->st);
     c->iterations = 0;
     return launch_check(c, "initialisation kernels");
 }
@@ -274,9 +276,9 @@ void enqueue_iteration(scalp_ctx *c, int slot, bool capturing)
     if (c->profiling) cudaEventRecordWithFlags(c->ev_pool[2 * slot], c->st, flags);
     launch_assign(c->a, c->p.storage, c->staged, c->tmap, c->smem, c->st);
     if (c->profiling) cudaEventRecordWithFlags(c->ev_pool[2 * slot + 1], c->st, flags);
-    launch_finalize(c->a, c->st);
+    launch_update(c->a, 1, c->st);
     launch_project(c->a, 0, c->st);
-    launch_derive(c->a, c->st);
+    launch_lists(c->a, c->st);
 }
 
 }  // namespace
@@ -366,6 +368,10 @@ int scalp_init(scalp_ctx **out, const scalp_image *image, const scalp_contour *c
     a.tile_cursor = reinterpret_cast<int *>(c->ws + L.tile_cursor);
     a.tile_list = reinterpret_cast<int *>(c->ws + L.tile_list);
     a.tile_cap = L.tile_cap;
+    a.tpw_x = tiles_per_window(c->r, TILE_X);
+    a.tpw_y = tiles_per_window(c->r, TILE_Y);
+    a.prev_win = reinterpret_cast<int4 *>(c->ws + L.prev_win);
+    a.lut = reinterpret_cast<float *>(c->ws + L.lut);
     a.ctr = reinterpret_cast<DevCounters *>(c->ws + L.ctr);
     c->ccl.parent = reinterpret_cast<int *>(c->ws + L.parent);
     c->ccl.size = reinterpret_cast<int *>(c->ws + L.size);
@@ -413,6 +419,10 @@ int scalp_init(scalp_ctx **out, const scalp_image *image, const scalp_contour *c
     a.halo = halo;
     c->smem = assign_smem_bytes(halo, params->storage);
     int rc = cuda_check(c, assign_configure(params->storage, c->staged, c->smem), "configure kernel");
+    if (rc == SCALP_OK) {
+        launch_srgb_table(c->a, c->st);
+        rc = launch_check(c, "table kernel");
+    }
     if (rc == SCALP_OK) rc = load_inputs(c, image, contour);
     if (rc != SCALP_OK) {
         delete c;
@@ -596,7 +606,8 @@ int scalp_set_state(scalp_ctx *c, const scalp_state *s)
     rc = rc ? rc : cuda_check(c, cudaMemcpyAsync(c->a.st_end, end.data(), 8 * K, cudaMemcpyHostToDevice, c->st), "copy state");
     rc = rc ? rc : cuda_check(c, cudaMemsetAsync(c->a.acc, 0, sizeof(ClusterAcc) * K, c->st), "memset");
     if (rc) return rc;
-    launch_derive(c->a, c->st);
+    launch_update(c->a, 0, c->st);
+    launch_lists(c->a, c->st);
     rc = launch_check(c, "derive kernels");
     if (rc) return rc;
     // the host vectors must outlive the copies

@@ -4,7 +4,8 @@
 // independent of thread scheduling):
 //   1. 4-connected components of equal label; a component's seed is its
 //      smallest raster index (the root of a union-find forest whose links
-//      always point to smaller indices).
+//      always point to smaller indices), built inside 32 x 32 tiles in shared
+//      memory first and then joined across tile borders.
 //   2. A component is small iff it has at most floor(N / (4K)) pixels.
 //   3. A small component whose seed s is not pixel 0 is absorbed by the
 //      component holding s-1 (if s is not in column 0) or s-W; that component
@@ -53,24 +54,97 @@ __device__ __forceinline__ void unite(int *parent, int a, int b)
     } while (!done);
 }
 
-__global__ void k_ccl_init(int *parent, int *size, long long N)
+// Pass 1: union-find inside each 32 x 32 tile in shared memory.  Tile-local
+// raster order is global raster order, so the local root (smallest local
+// index of a tile-local component) is also its smallest global index; each
+// pixel gets that root's global index as parent.  size[] is cleared.
+constexpr int CCL_TILE = 32;
+
+__device__ __forceinline__ int find_local(const volatile int *sp, int x)
 {
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
-         p += (long long)gridDim.x * blockDim.x) {
-        parent[p] = (int)p;
+    int p = sp[x];
+    while (p != x) {
+        x = p;
+        p = sp[x];
+    }
+    return x;
+}
+
+__device__ __forceinline__ void unite_local(int *sp, int a, int b)
+{
+    bool done;
+    do {
+        a = find_local(sp, a);
+        b = find_local(sp, b);
+        if (b < a) {
+            int old = atomicMin(&sp[a], b);
+            done = old == a;
+            a = old;
+        } else if (a < b) {
+            int old = atomicMin(&sp[b], a);
+            done = old == b;
+            b = old;
+        } else {
+            done = true;
+        }
+    } while (!done);
+}
+
+__global__ void __launch_bounds__(CCL_TILE * CCL_TILE)
+    k_ccl_local(const int *__restrict__ labels, int *parent, int *size, int H, int W, int n_tx)
+{
+    __shared__ int sp[CCL_TILE * CCL_TILE];
+    __shared__ int sl[CCL_TILE * CCL_TILE];
+    __shared__ unsigned srun[CCL_TILE];  // per row: bit x set where a run starts
+    const int t = threadIdx.x;
+    const int lx = t % CCL_TILE, ly = t / CCL_TILE;  // one warp per tile row
+    const int x0 = (blockIdx.x % n_tx) * CCL_TILE, y0 = (blockIdx.x / n_tx) * CCL_TILE;
+    const int x = x0 + lx, y = y0 + ly;
+    const bool valid = x < W && y < H;
+    const long long p = (long long)y * W + x;
+    const int lab = valid ? labels[p] : 0;
+    sl[t] = lab;
+    // runs of equal label along the row: each pixel's head is the last run
+    // start at or before it
+    const int left = __shfl_up_sync(0xffffffffu, lab, 1);
+    const unsigned starts = __ballot_sync(0xffffffffu, lx == 0 || !valid || left != lab);
+    const int head = 31 - __clz(starts & (0xffffffffu >> (31 - lx)));
+    sp[t] = ly * CCL_TILE + head;
+    if (lx == 0) srun[ly] = starts;
+    __syncthreads();
+    // one union per pair of vertically touching runs: at the first pixel of
+    // their overlap, where this pixel or the one above starts a run
+    if (valid && ly > 0 && sl[t - CCL_TILE] == lab &&
+        (((starts >> lx) & 1u) || ((srun[ly - 1] >> lx) & 1u)))
+        unite_local(sp, t, t - CCL_TILE);
+    __syncthreads();
+    if (valid) {
+        const int r = find_local(sp, t);
+        parent[p] = (int)((long long)(y0 + r / CCL_TILE) * W + x0 + r % CCL_TILE);
         size[p] = 0;
     }
 }
 
-__global__ void k_ccl_union(const int *__restrict__ labels, int *parent, int H, int W)
+// Pass 2: unions across tile borders (left edge and top edge of each tile).
+__global__ void k_ccl_border(const int *__restrict__ labels, int *parent, int H, int W, int n_tx,
+                             int n_ty)
 {
-    long long N = (long long)H * W;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
-         p += (long long)gridDim.x * blockDim.x) {
-        int y = (int)(p / W), x = (int)(p - (long long)y * W);
-        int l = labels[p];
-        if (x > 0 && labels[p - 1] == l) unite(parent, (int)p, (int)p - 1);
-        if (y > 0 && labels[p - W] == l) unite(parent, (int)p, (int)(p - W));
+    const long long nv = (long long)(n_tx - 1) * H;  // vertical border pixels
+    const long long nh = (long long)(n_ty - 1) * W;  // horizontal border pixels
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nv + nh;
+         i += (long long)gridDim.x * blockDim.x) {
+        long long p, q;
+        if (i < nv) {
+            const int y = (int)(i / (n_tx - 1)), bx = (int)(i % (n_tx - 1)) + 1;
+            p = (long long)y * W + bx * CCL_TILE;
+            q = p - 1;
+        } else {
+            const long long j = i - nv;
+            const int by = (int)(j / W) + 1, x = (int)(j % W);
+            p = (long long)by * CCL_TILE * W + x;
+            q = p - W;
+        }
+        if (labels[p] == labels[q]) unite(parent, (int)p, (int)q);
     }
 }
 
@@ -215,8 +289,12 @@ void launch_ccl(const int *labels, int H, int W, int K, int *out, const CclBuffe
     const long long N = (long long)H * W;
     const long long T = N / (4LL * K);
     const int blocks = (int)std::min<long long>(ceil_div_ll(N, CCL_THREADS), 152 * 16);
-    k_ccl_init<<<blocks, CCL_THREADS, 0, st>>>(b.parent, b.size, N);
-    k_ccl_union<<<blocks, CCL_THREADS, 0, st>>>(labels, b.parent, H, W);
+    const int n_tx = (W + CCL_TILE - 1) / CCL_TILE, n_ty = (H + CCL_TILE - 1) / CCL_TILE;
+    k_ccl_local<<<n_tx * n_ty, CCL_TILE * CCL_TILE, 0, st>>>(labels, b.parent, b.size, H, W, n_tx);
+    const long long nb = (long long)(n_tx - 1) * H + (long long)(n_ty - 1) * W;
+    if (nb > 0)
+        k_ccl_border<<<(int)std::min<long long>(ceil_div_ll(nb, CCL_THREADS), 152 * 16), CCL_THREADS, 0,
+                       st>>>(labels, b.parent, H, W, n_tx, n_ty);
     k_ccl_flatten_count<<<blocks, CCL_THREADS, 0, st>>>(b.parent, b.size, N);
     k_ccl_link<<<blocks, CCL_THREADS, 0, st>>>(b.parent, b.size, b.link, W, N, T);
     k_ccl_resolve<<<blocks, CCL_THREADS, 0, st>>>(b.parent, b.link, b.size, N, ctr);

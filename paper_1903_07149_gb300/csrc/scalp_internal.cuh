@@ -77,9 +77,12 @@ struct SolveArgs {
     int2 *st_end;
     ClusterDev *cdev;
     ClusterAcc *acc;
+    int4 *prev_win;    // window (xlo, xhi, ylo, yhi) the last assignment used
+    float *lut;        // 256-entry inverse sRGB transfer function
     int *proj_list;
     int *tile_count, *tile_off, *tile_cursor, *tile_list;
     long long tile_cap;
+    int tpw_x, tpw_y;  // bound on the tiles one window spans, per axis
     DevCounters *ctr;
 };
 

@@ -27,15 +27,22 @@ __device__ __forceinline__ float lab_f(float t)
     return t > d3 ? cbrtf(t) : t * (841.0f / 108.0f) + (4.0f / 29.0f);
 }
 
+// Inverse sRGB transfer function for the 256 byte values, in double, once.
+__global__ void k_srgb_table(float *lut)
+{
+    const int i = threadIdx.x;
+    if (i < 256) {
+        const double c = i / 255.0;
+        lut[i] = (float)(c <= 0.04045 ? c / 12.92 : pow((c + 0.055) / 1.055, 2.4));
+    }
+}
+
 __global__ void k_setup(SolveArgs a, const uint8_t *__restrict__ rgb, long long rgb_stride,
                         const float *__restrict__ contour, long long contour_stride, int storage,
                         void *plane)
 {
     __shared__ float lin[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) {
-        double c = i / 255.0;
-        lin[i] = (float)(c <= 0.04045 ? c / 12.92 : pow((c + 0.055) / 1.055, 2.4));
-    }
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) lin[i] = a.lut[i];
     __syncthreads();
     const float wx = c_rgb2xyz[0] + c_rgb2xyz[1] + c_rgb2xyz[2];
     const float wy = c_rgb2xyz[3] + c_rgb2xyz[4] + c_rgb2xyz[5];
@@ -71,6 +78,8 @@ __global__ void k_setup(SolveArgs a, const uint8_t *__restrict__ rgb, long long 
         a.labels[p] = cy * a.nx + cx;
     }
 }
+
+void launch_srgb_table(const SolveArgs &a, cudaStream_t st) { k_srgb_table<<<1, 256, 0, st>>>(a.lut); }
 
 void launch_setup(const SolveArgs &a, const uint8_t *rgb, long long rgb_stride,
                   const float *contour, long long contour_stride, int storage, void *plane,
@@ -108,120 +117,10 @@ void launch_accumulate(const SolveArgs &a, cudaStream_t st)
 }
 
 // ---------------------------------------------------------------------------
-// Cluster update (Algorithm 1): means over S_k from the integer sums; an empty
-// cluster keeps its colour, barycenter and endpoint.  The endpoint is X_k
-// rounded half-up; if the pixel there is not labelled k the cluster is queued
-// for the projection of Eq. 4.  The sums are cleared for the next assignment.
-// ---------------------------------------------------------------------------
-__global__ void k_finalize(SolveArgs a)
-{
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= a.Keff) return;
-    ClusterAcc c = a.acc[k];
-    ClusterAcc z = {};
-    a.acc[k] = z;
-    long long n = (long long)c.n;
-    if (n <= 0) return;
-    long long sx = (long long)c.sx, sy = (long long)c.sy;
-    a.st_n[k] = n;
-    a.st_sx[k] = sx;
-    a.st_sy[k] = sy;
-    double den = (double)n * (double)(1 << COLOR_FRAC_BITS);
-    a.st_col[k] = make_float4((float)((double)(long long)c.sL / den),
-                              (float)((double)(long long)c.sa / den),
-                              (float)((double)(long long)c.sb / den), 0.f);
-    int ex = (int)((2 * sx + n) / (2 * n));
-    int ey = (int)((2 * sy + n) / (2 * n));
-    a.st_end[k] = make_int2(ex, ey);
-    if (a.labels[(long long)ey * a.W + ex] != k) {
-        int slot = atomicAdd(&a.ctr->nproj, 1);
-        a.proj_list[slot] = k;
-    }
-}
-
-void launch_finalize(const SolveArgs &a, cudaStream_t st)
-{
-    k_finalize<<<(a.Keff + 255) / 256, 256, 0, st>>>(a);
-}
-
-// ---------------------------------------------------------------------------
-// Projection, Eq. 4: X_k^* = argmin over p in S_k of ||X_p - X_k||, compared
-// exactly as (n*x - Sx)^2 + (n*y - Sy)^2 in 128-bit integers, ties to the
-// smallest raster index.  S_k lies inside the window the last assignment used
-// for cluster k, unless some pixel kept its old label for lack of any
-// candidate; then the whole image is searched.  One CTA per queued cluster.
-// ---------------------------------------------------------------------------
-constexpr int PROJ_THREADS = 256;
-
-__global__ void __launch_bounds__(PROJ_THREADS) k_project(SolveArgs a, int whole_image)
-{
-    __shared__ unsigned long long s_hi[PROJ_THREADS], s_lo[PROJ_THREADS];
-    __shared__ long long s_p[PROJ_THREADS];
-    const int nproj = a.ctr->nproj;
-    const bool all = whole_image || a.ctr->orphans > 0;
-    for (int j = blockIdx.x; j < nproj; j += gridDim.x) {
-        const int k = a.proj_list[j];
-        const long long n = a.st_n[k], sx = a.st_sx[k], sy = a.st_sy[k];
-        int xlo = 0, xhi = a.W - 1, ylo = 0, yhi = a.H - 1;
-        if (!all) {
-            ClusterDev cd = a.cdev[k];
-            xlo = cd.xlo; xhi = cd.xhi; ylo = cd.ylo; yhi = cd.yhi;
-        }
-        const int w = xhi - xlo + 1;
-        const long long area = (long long)w * (yhi - ylo + 1);
-        unsigned __int128 best = ~(unsigned __int128)0;
-        long long bestp = LLONG_MAX;
-        for (long long i = threadIdx.x; i < area; i += PROJ_THREADS) {
-            int y = ylo + (int)(i / w), x = xlo + (int)(i % w);
-            long long p = (long long)y * a.W + x;
-            if (a.labels[p] != k) continue;
-            __int128 dx = (__int128)n * x - sx, dy = (__int128)n * y - sy;
-            unsigned __int128 d2 = (unsigned __int128)(dx * dx) + (unsigned __int128)(dy * dy);
-            if (d2 < best || (d2 == best && p < bestp)) { best = d2; bestp = p; }
-        }
-        s_hi[threadIdx.x] = (unsigned long long)(best >> 64);
-        s_lo[threadIdx.x] = (unsigned long long)best;
-        s_p[threadIdx.x] = bestp;
-        __syncthreads();
-        for (int h = PROJ_THREADS / 2; h > 0; h >>= 1) {
-            if (threadIdx.x < h) {
-                int o = threadIdx.x + h;
-                bool take = s_hi[o] < s_hi[threadIdx.x] ||
-                            (s_hi[o] == s_hi[threadIdx.x] &&
-                             (s_lo[o] < s_lo[threadIdx.x] ||
-                              (s_lo[o] == s_lo[threadIdx.x] && s_p[o] < s_p[threadIdx.x])));
-                if (take) {
-                    s_hi[threadIdx.x] = s_hi[o];
-                    s_lo[threadIdx.x] = s_lo[o];
-                    s_p[threadIdx.x] = s_p[o];
-                }
-            }
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            long long p = s_p[0];
-            if (p == LLONG_MAX) {
-                atomicExch(&a.ctr->error, ERR_BAD_LABEL);
-            } else {
-                a.st_end[k] = make_int2((int)(p % a.W), (int)(p / a.W));
-            }
-        }
-        __syncthreads();
-    }
-}
-
-void launch_project(const SolveArgs &a, int whole_image, cudaStream_t st)
-{
-    int blocks = std::min(a.Keff, 2 * 152);
-    k_project<<<blocks, PROJ_THREADS, 0, st>>>(a, whole_image);
-}
-
-// ---------------------------------------------------------------------------
-// Windows and per-tile candidate lists.  Pixel p is a candidate of cluster k
-// iff |x_p - x_k| <= r and |y_p - y_k| <= r (the (2r+1)x(2r+1) window of
-// Algorithm 1), i.e. K*(n*x_p - Sx)^2 <= N*n^2 and likewise for y, evaluated
-// exactly.  Each cluster's window becomes an inclusive integer range; every
-// assignment tile overlapping it lists the cluster.
+// Windows.  Pixel p is a candidate of cluster k iff |x_p - x_k| <= r and
+// |y_p - y_k| <= r (the (2r+1)x(2r+1) window of Algorithm 1), i.e.
+// K*(n*x_p - Sx)^2 <= N*n^2 and likewise for y, evaluated exactly; each
+// window becomes an inclusive integer range clipped to the image.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool in_window(long long v, long long n, long long s, long long N,
                                           long long K)
@@ -247,21 +146,56 @@ __device__ bool window_range(long long n, long long s, long long N, long long K,
     return true;
 }
 
-__global__ void k_window(SolveArgs a)
+// ---------------------------------------------------------------------------
+// Cluster update (Algorithm 1) and everything derived from it, one thread per
+// cluster.  With from_acc: the means over S_k from the integer sums (an empty
+// cluster keeps its colour, barycenter and endpoint), the endpoint X_k rounded
+// half-up, and a projection request (Eq. 4) when the pixel there is not
+// labelled k; the sums are cleared for the next assignment.  Then, from the
+// state: the window, the cluster record the assignment reads, and the count
+// of each tile the window overlaps (for the candidate lists).  The window the
+// last assignment used is kept for the projection search.
+// ---------------------------------------------------------------------------
+__global__ void k_update(SolveArgs a, int from_acc)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= a.Keff) return;
+    if (from_acc) {
+        ClusterAcc c = a.acc[k];
+        ClusterAcc z = {};
+        a.acc[k] = z;
+        const long long n = (long long)c.n;
+        if (n > 0) {
+            const long long sx = (long long)c.sx, sy = (long long)c.sy;
+            a.st_n[k] = n;
+            a.st_sx[k] = sx;
+            a.st_sy[k] = sy;
+            const double den = (double)n * (double)(1 << COLOR_FRAC_BITS);
+            a.st_col[k] = make_float4((float)((double)(long long)c.sL / den),
+                                      (float)((double)(long long)c.sa / den),
+                                      (float)((double)(long long)c.sb / den), 0.f);
+            const int ex = (int)((2 * sx + n) / (2 * n));
+            const int ey = (int)((2 * sy + n) / (2 * n));
+            a.st_end[k] = make_int2(ex, ey);
+            if (a.labels[(long long)ey * a.W + ex] != k) {
+                const int slot = atomicAdd(&a.ctr->nproj, 1);
+                a.proj_list[slot] = k;
+            }
+        }
+    }
     const long long n = a.st_n[k], sx = a.st_sx[k], sy = a.st_sy[k];
+    const ClusterDev old = a.cdev[k];
+    a.prev_win[k] = make_int4(old.xlo, old.xhi, old.ylo, old.yhi);
     ClusterDev cd;
-    float4 col = a.st_col[k];
-    int2 e = a.st_end[k];
+    const float4 col = a.st_col[k];
+    const int2 e = a.st_end[k];
     cd.L = col.x; cd.a = col.y; cd.b = col.z;
     cd.xk = (float)((double)sx / (double)n);
     cd.yk = (float)((double)sy / (double)n);
     cd.ex = e.x; cd.ey = e.y;
     cd.pad = k;
-    bool ok = window_range(n, sx, a.N, a.K, a.r, a.W, cd.xlo, cd.xhi) &&
-              window_range(n, sy, a.N, a.K, a.r, a.H, cd.ylo, cd.yhi);
+    const bool ok = window_range(n, sx, a.N, a.K, a.r, a.W, cd.xlo, cd.xhi) &&
+                    window_range(n, sy, a.N, a.K, a.r, a.H, cd.ylo, cd.yhi);
     if (!ok) {
         atomicExch(&a.ctr->error, ERR_BAD_LABEL);
         cd.xlo = 1; cd.xhi = 0; cd.ylo = 1; cd.yhi = 0;
@@ -273,50 +207,170 @@ __global__ void k_window(SolveArgs a)
             atomicAdd(&a.tile_count[ty * a.n_tx + tx], 1);
 }
 
-// Exclusive scan of the tile counts (one CTA), reset of per-iteration counters.
+void launch_update(const SolveArgs &a, int from_acc, cudaStream_t st)
+{
+    // small blocks: one thread per cluster is latency-bound, so spread them
+    k_update<<<(a.Keff + 63) / 64, 64, 0, st>>>(a, from_acc);
+}
+
+// ---------------------------------------------------------------------------
+// Projection, Eq. 4: X_k^* = argmin over p in S_k of ||X_p - X_k||, compared
+// exactly as (n*x - Sx)^2 + (n*y - Sy)^2 in integers (64-bit when the image
+// size bounds them below 2^62, else 128-bit), ties to the smallest raster
+// index.  S_k lies inside the window the last assignment used for cluster k,
+// unless some pixel kept its old label for lack of any candidate; then the
+// whole image is searched.  One CTA per queued cluster; each thread issues
+// PROJ_BATCH label loads before comparing them.
+// ---------------------------------------------------------------------------
+constexpr int PROJ_THREADS = 512;
+constexpr int PROJ_BATCH = 8;
+
+struct ProjBest {
+    unsigned long long hi, lo;
+    long long p;
+};
+
+__device__ __forceinline__ bool proj_less(const ProjBest &u, const ProjBest &v)
+{
+    return u.hi < v.hi || (u.hi == v.hi && (u.lo < v.lo || (u.lo == v.lo && u.p < v.p)));
+}
+
+__device__ __forceinline__ void proj_shfl_min(ProjBest &b)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        ProjBest c;
+        c.hi = __shfl_xor_sync(0xffffffffu, b.hi, o);
+        c.lo = __shfl_xor_sync(0xffffffffu, b.lo, o);
+        c.p = __shfl_xor_sync(0xffffffffu, b.p, o);
+        if (proj_less(c, b)) b = c;
+    }
+}
+
+__global__ void __launch_bounds__(PROJ_THREADS) k_project(SolveArgs a, int whole_image)
+{
+    __shared__ ProjBest s_best[PROJ_THREADS / 32];
+    const int nproj = a.ctr->nproj;
+    const bool all = whole_image || a.ctr->orphans > 0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const double bound = (double)max(a.W, a.H);
+    for (int j = blockIdx.x; j < nproj; j += gridDim.x) {
+        const int k = a.proj_list[j];
+        const long long n = a.st_n[k], sx = a.st_sx[k], sy = a.st_sy[k];
+        int xlo = 0, xhi = a.W - 1, ylo = 0, yhi = a.H - 1;
+        if (!all) {
+            const int4 w4 = a.prev_win[k];
+            xlo = w4.x; xhi = w4.y; ylo = w4.z; yhi = w4.w;
+        }
+        const int w = xhi - xlo + 1;
+        const long long area = (long long)w * (yhi - ylo + 1);
+        const bool small = 2.0 * (n * bound) * (n * bound) < 4.0e18;
+        ProjBest b = {~0ull, ~0ull, LLONG_MAX};
+        for (long long base = 0; base < area; base += (long long)PROJ_THREADS * PROJ_BATCH) {
+            int lab[PROJ_BATCH];
+            long long idx[PROJ_BATCH];
+#pragma unroll
+            for (int u = 0; u < PROJ_BATCH; ++u) {
+                const long long i = base + (long long)u * PROJ_THREADS + tid;
+                lab[u] = -1;
+                idx[u] = -1;
+                if (i < area) {
+                    const int y = ylo + (int)(i / w), x = xlo + (int)(i % w);
+                    idx[u] = (long long)y * a.W + x;
+                    lab[u] = a.labels[idx[u]];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < PROJ_BATCH; ++u) {
+                if (lab[u] != k) continue;
+                const long long p = idx[u];
+                const int y = (int)(p / a.W), x = (int)(p - (long long)y * a.W);
+                ProjBest c;
+                c.p = p;
+                if (small) {
+                    const long long dx = n * x - sx, dy = n * y - sy;
+                    c.hi = 0;
+                    c.lo = (unsigned long long)(dx * dx) + (unsigned long long)(dy * dy);
+                } else {
+                    const __int128 dx = (__int128)n * x - sx, dy = (__int128)n * y - sy;
+                    const unsigned __int128 d2 =
+                        (unsigned __int128)(dx * dx) + (unsigned __int128)(dy * dy);
+                    c.hi = (unsigned long long)(d2 >> 64);
+                    c.lo = (unsigned long long)d2;
+                }
+                if (proj_less(c, b)) b = c;
+            }
+        }
+        proj_shfl_min(b);
+        if (lane == 0) s_best[warp] = b;
+        __syncthreads();
+        if (warp == 0) {
+            b = lane < PROJ_THREADS / 32 ? s_best[lane] : ProjBest{~0ull, ~0ull, LLONG_MAX};
+            proj_shfl_min(b);
+            if (lane == 0) {
+                if (b.p == LLONG_MAX) {
+                    atomicExch(&a.ctr->error, ERR_BAD_LABEL);
+                } else {
+                    const int ex = (int)(b.p % a.W), ey = (int)(b.p / a.W);
+                    a.st_end[k] = make_int2(ex, ey);
+                    a.cdev[k].ex = ex;
+                    a.cdev[k].ey = ey;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+void launch_project(const SolveArgs &a, int whole_image, cudaStream_t st)
+{
+    k_project<<<std::min(a.Keff, 2 * 152), PROJ_THREADS, 0, st>>>(a, whole_image);
+}
+
+// ---------------------------------------------------------------------------
+// Per-tile candidate lists: exclusive scan of the tile counts (one CTA, each
+// thread a contiguous chunk), then one thread per (cluster, tile) slot files
+// the cluster into each tile its window overlaps.  The scan also resets the
+// per-iteration counters.
+// ---------------------------------------------------------------------------
 constexpr int SCAN1_THREADS = 1024;
 
 __global__ void __launch_bounds__(SCAN1_THREADS) k_scan_tiles(SolveArgs a)
 {
     __shared__ int s_warp[32];
-    __shared__ int s_carry;
     const int n = a.n_tx * a.n_ty;
-    if (threadIdx.x == 0) s_carry = 0;
-    __syncthreads();
-    for (int base = 0; base < n; base += SCAN1_THREADS) {
-        int i = base + threadIdx.x;
-        int v = i < n ? a.tile_count[i] : 0;
-        int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-        int incl = v;
-        for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (lane == 31) s_warp[wid] = incl;
-        __syncthreads();
-        if (wid == 0) {
-            int w = s_warp[lane];
-            for (int o = 1; o < 32; o <<= 1) {
-                int t = __shfl_up_sync(0xffffffffu, w, o);
-                if (lane >= o) w += t;
-            }
-            s_warp[lane] = w;
-        }
-        __syncthreads();
-        int carry = s_carry;
-        int excl = carry + (wid ? s_warp[wid - 1] : 0) + incl - v;
-        if (i < n) {
-            a.tile_off[i] = excl;
-            a.tile_cursor[i] = excl;
-            a.tile_count[i] = 0;
-        }
-        __syncthreads();
-        if (threadIdx.x == SCAN1_THREADS - 1) s_carry = excl + v;
-        __syncthreads();
+    const int per = (n + SCAN1_THREADS - 1) / SCAN1_THREADS;
+    const int b = threadIdx.x * per, e = min(n, b + per);
+    int tsum = 0;
+    for (int i = b; i < e; ++i) tsum += a.tile_count[i];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = tsum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
     }
-    if (threadIdx.x == 0) {
-        a.tile_off[n] = s_carry;
-        if (s_carry > a.tile_cap) atomicExch(&a.ctr->error, ERR_TILE_LIST_OVERFLOW);
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int w = s_warp[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    int run = (wid ? s_warp[wid - 1] : 0) + incl - tsum;
+    for (int i = b; i < e; ++i) {
+        const int v = a.tile_count[i];
+        a.tile_off[i] = run;
+        a.tile_cursor[i] = run;
+        a.tile_count[i] = 0;
+        run += v;
+    }
+    if (threadIdx.x == SCAN1_THREADS - 1) {
+        const int total = s_warp[31];
+        a.tile_off[n] = total;
+        if (total > a.tile_cap) atomicExch(&a.ctr->error, ERR_TILE_LIST_OVERFLOW);
         a.ctr->nproj = 0;
         a.ctr->orphans = 0;
     }
@@ -324,23 +378,23 @@ __global__ void __launch_bounds__(SCAN1_THREADS) k_scan_tiles(SolveArgs a)
 
 __global__ void k_fill_tiles(SolveArgs a)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= a.Keff) return;
-    ClusterDev cd = a.cdev[k];
+    const long long slots = (long long)a.tpw_x * a.tpw_y;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)a.Keff * slots) return;
+    const int k = (int)(i / slots), j = (int)(i % slots);
+    const ClusterDev cd = a.cdev[k];
     if (cd.xlo > cd.xhi) return;
-    for (int ty = cd.ylo / TILE_Y; ty <= cd.yhi / TILE_Y; ++ty)
-        for (int tx = cd.xlo / TILE_X; tx <= cd.xhi / TILE_X; ++tx) {
-            int pos = atomicAdd(&a.tile_cursor[ty * a.n_tx + tx], 1);
-            if (pos < a.tile_cap) a.tile_list[pos] = k;
-        }
+    const int tx = cd.xlo / TILE_X + j % a.tpw_x, ty = cd.ylo / TILE_Y + j / a.tpw_x;
+    if (tx > cd.xhi / TILE_X || ty > cd.yhi / TILE_Y) return;
+    const int pos = atomicAdd(&a.tile_cursor[ty * a.n_tx + tx], 1);
+    if (pos < a.tile_cap) a.tile_list[pos] = k;
 }
 
-void launch_derive(const SolveArgs &a, cudaStream_t st)
+void launch_lists(const SolveArgs &a, cudaStream_t st)
 {
-    int blocks = (a.Keff + 255) / 256;
-    k_window<<<blocks, 256, 0, st>>>(a);
     k_scan_tiles<<<1, SCAN1_THREADS, 0, st>>>(a);
-    k_fill_tiles<<<blocks, 256, 0, st>>>(a);
+    const long long slots = (long long)a.Keff * a.tpw_x * a.tpw_y;
+    k_fill_tiles<<<(unsigned)ceil_div_ll(slots, 256), 256, 0, st>>>(a);
 }
 
 // ---------------------------------------------------------------------------

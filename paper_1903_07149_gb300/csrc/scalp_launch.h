@@ -10,14 +10,17 @@ namespace scalp {
 void launch_setup(const SolveArgs &a, const uint8_t *rgb, long long rgb_stride,
                   const float *contour, long long contour_stride, int storage,
                   void *plane, cudaStream_t st);
+// The 256-entry inverse sRGB transfer function (once per context).
+void launch_srgb_table(const SolveArgs &a, cudaStream_t st);
 // Integer sums of (1, x, y, L, a, b) by label into a.acc (grid initialisation).
 void launch_accumulate(const SolveArgs &a, cudaStream_t st);
-// Cluster update (Algorithm 1) from a.acc, then queue projections (Eq. 4).
-void launch_finalize(const SolveArgs &a, cudaStream_t st);
+// Cluster update (Algorithm 1) from a.acc when from_acc (queueing projections,
+// Eq. 4), then windows, the cluster records and the tile counts.
+void launch_update(const SolveArgs &a, int from_acc, cudaStream_t st);
 // Eq. 4 for the queued clusters; whole_image=1 searches every pixel.
 void launch_project(const SolveArgs &a, int whole_image, cudaStream_t st);
-// Windows, derived cluster table and per-tile candidate lists.
-void launch_derive(const SolveArgs &a, cudaStream_t st);
+// Per-tile candidate lists from the tile counts; resets per-iteration counters.
+void launch_lists(const SolveArgs &a, cudaStream_t st);
 // Assignment (Algorithm 1 inner loops, Eq. 1-3).  tmap is used when staged.
 void launch_assign(const SolveArgs &a, int storage, bool staged, const CUtensorMap &tmap,
                    size_t smem_bytes, cudaStream_t st);
