@@ -119,7 +119,17 @@ class Clocks:
                 "samples": len(rows)}
 
 
+# Kernels per step: reload = set-up, sums, update, projection, tile scan, tile
+# fill; each iteration = assignment (with the sums), update, projection, tile
+# scan, tile fill.
+RELOAD_LAUNCHES = 6
+ITER_LAUNCHES = 5
+
+
 def ccl_launches(N: int) -> int:
+    """Connectivity kernels: tile-local, border, flatten, link, resolve, flag,
+    output, plus the multi-level scan (one block pass per level, one add pass
+    per level below the top)."""
     levels, n = 0, N
     while True:
         n = -(-n // 4096)
@@ -342,7 +352,7 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "n_labels": int(n_labels)},
         "clocks": clk, "e2e": e2e,
-        "gpu_launches": args.steps * (7 + 6 * iters + ccl_launches(N)),
+        "gpu_launches": args.steps * (RELOAD_LAUNCHES + ITER_LAUNCHES * iters + ccl_launches(N)),
         "roofline": roofline,
     }
     if not args.no_cpu_baseline and world == 1:

@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
     }
     __syncthreads();
 
-    // labels and the fused partial sums of the cluster update
+    // labels and the warp-aggregated integer sums of the update
 #pragma unroll 1
     for (int j = 0; j < PIX_PER_THREAD; ++j) {
         int px, py;
@@ -398,30 +398,25 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
         const bool valid = px < a.W && py < a.H;
         const long long p = (long long)py * a.W + px;
         float4 own = make_float4(0.f, 0.f, 0.f, 0.f);
+        int lab = -1;
         if (valid) {
             own = STAGED ? lds_sample<T>(region + (uint32_t)(((py - ry0) * BX + (px - rx0)) * (int)sizeof(T)))
                          : fetch_sample<T>(plane + (long long)py * a.pitch + px);
-        }
-        int lab = 0;
-        bool found;
-        if (fast) {
-            const unsigned long long b = best[(py - y0) * TILE_X + (px - x0)];
-            found = b != ~0ull;
-            if (found) lab = cid[(int)(b & 0xffffffffu)];
-        } else {
-            found = bestk[j] != INT_MAX;
-            lab = bestk[j];
-        }
-        if (valid) {
-            if (found) {
+            if (fast) {
+                const unsigned long long b = best[(py - y0) * TILE_X + (px - x0)];
+                if (b != ~0ull) lab = cid[(int)(b & 0xffffffffu)];
+            } else if (bestk[j] != INT_MAX) {
+                lab = bestk[j];
+            }
+            if (lab >= 0) {
                 a.labels[p] = lab;
             } else {
                 lab = a.labels[p];  // no window reaches p: keep its label
                 atomicAdd(&a.ctr->orphans, 1);
             }
         }
-        // warp-aggregated sums straight into the global cluster sums
-        // (fire-and-forget reductions, one set per label group of the warp)
+        // fire-and-forget reductions into the global cluster sums, one set
+        // per label group of the warp
         warp_aggregate_global(valid, lab, px, py, own, a.acc);
     }
     if (a.count_samples) {

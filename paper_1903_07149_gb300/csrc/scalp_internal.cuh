@@ -251,15 +251,6 @@ __device__ __forceinline__ void acc_add(ClusterAcc *c, long long n, long long sx
     atomicAdd(&c->sb, (unsigned long long)sb);
 }
 
-// Sum into a tile's shared-memory slot table.
-__device__ __forceinline__ void warp_aggregate_tile(bool valid, int slot, int x, int y, float4 v,
-                                                    ClusterAcc *sacc)
-{
-    warp_aggregate(valid, slot, x, y, v,
-                   [&](int k, long long n, long long sx, long long sy, long long sL, long long sa,
-                       long long sb) { acc_add(&sacc[k], n, sx, sy, sL, sa, sb); });
-}
-
 // Sum straight into the global per-cluster sums.
 __device__ __forceinline__ void warp_aggregate_global(bool valid, int label, int x, int y,
                                                       float4 v, ClusterAcc *acc)

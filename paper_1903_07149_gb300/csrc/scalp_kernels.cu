@@ -89,29 +89,30 @@ void launch_setup(const SolveArgs &a, const uint8_t *rgb, long long rgb_stride,
     k_setup<<<blocks, 256, 0, st>>>(a, rgb, rgb_stride, contour, contour_stride, storage, plane);
 }
 
+// Integer sums of (1, x, y, L, a, b) per label (the means of the update).
+// Each warp takes 32 consecutive pixels of a row, whose labels are mostly
+// equal, so the warp-aggregated sums need few reductions per warp.
 template <typename T>
-__global__ void k_accumulate(SolveArgs a, const T *__restrict__ plane)
+__global__ void __launch_bounds__(256) k_accumulate(SolveArgs a, const T *__restrict__ plane)
 {
-    // grid-stride loop with a warp-uniform trip count so that every lane
-    // takes part in the warp reductions
-    long long stride = (long long)gridDim.x * blockDim.x;
-    long long base0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31);
+    const long long stride = (long long)gridDim.x * blockDim.x;
+    const long long base0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31);
     for (long long base = base0; base < a.N; base += stride) {
-        long long p = base + (threadIdx.x & 31);
-        bool valid = p < a.N;
-        int lab = valid ? a.labels[p] : 0;
-        int y = valid ? (int)(p / a.W) : 0;
-        int x = valid ? (int)(p - (long long)y * a.W) : 0;
-        float4 v = valid ? fetch_sample<T>(plane + (long long)y * a.pitch + x) : make_float4(0, 0, 0, 0);
-        warp_aggregate(valid, lab, x, y, v,
-                       [&](int k, long long n, long long sx, long long sy, long long sL,
-                           long long sa, long long sb) { acc_add(&a.acc[k], n, sx, sy, sL, sa, sb); });
+        // warp-uniform trip count: every lane takes part in the reductions
+        const long long p = base + (threadIdx.x & 31);
+        const bool valid = p < a.N;
+        const int lab = valid ? a.labels[p] : 0;
+        const int y = valid ? (int)(p / a.W) : 0;
+        const int x = valid ? (int)(p - (long long)y * a.W) : 0;
+        const float4 v = valid ? fetch_sample<T>(plane + (long long)y * a.pitch + x)
+                               : make_float4(0, 0, 0, 0);
+        warp_aggregate_global(valid, lab, x, y, v, a.acc);
     }
 }
 
 void launch_accumulate(const SolveArgs &a, cudaStream_t st)
 {
-    int blocks = (int)std::min<long long>(ceil_div_ll(a.N, 256), 152 * 8);
+    const int blocks = (int)std::min<long long>(ceil_div_ll(a.N, 256), 152 * 16);
     if (a.plane32) k_accumulate<float4><<<blocks, 256, 0, st>>>(a, a.plane32);
     else k_accumulate<uint2><<<blocks, 256, 0, st>>>(a, a.plane16);
 }

@@ -12,7 +12,8 @@ void launch_setup(const SolveArgs &a, const uint8_t *rgb, long long rgb_stride,
                   void *plane, cudaStream_t st);
 // The 256-entry inverse sRGB transfer function (once per context).
 void launch_srgb_table(const SolveArgs &a, cudaStream_t st);
-// Integer sums of (1, x, y, L, a, b) by label into a.acc (grid initialisation).
+// Integer sums of (1, x, y, L, a, b) by label into a.acc (initialisation and
+// every update).
 void launch_accumulate(const SolveArgs &a, cudaStream_t st);
 // Cluster update (Algorithm 1) from a.acc when from_acc (queueing projections,
 // Eq. 4), then windows, the cluster records and the tile counts.
