@@ -144,18 +144,23 @@ __host__ __device__ inline size_t region_bytes(int halo, int elem)
 // Shared-memory layout after the staged region; every section starts on a
 // 16-byte boundary (int4 loads, 8-byte atomics and the mbarrier need it).
 constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
-constexpr int MAX_ITEMS = MAX_TILE_CANDIDATES * MAX_BLOCKS_PER_CANDIDATE;
+constexpr int CELL = 8;  // items are halves of CELL x CELL cells
+constexpr int MAX_ITEMS = MAX_TILE_CANDIDATES * 2 * (TILE_X / CELL) * (TILE_Y / CELL);
+static_assert(TILE_X / CELL <= 4, "the 16-bit reciprocal of the cells per row is exact");
 struct AssignSmem {
     static constexpr size_t cand = 0;
     static constexpr size_t cid = align16(cand + MAX_TILE_CANDIDATES * sizeof(ClusterDev));
     static constexpr size_t rect = align16(cid + MAX_TILE_CANDIDATES * sizeof(int));
-    static constexpr size_t best = align16(rect + MAX_TILE_CANDIDATES * sizeof(int4));
+    static constexpr size_t meta = align16(rect + MAX_TILE_CANDIDATES * sizeof(int4));
+    static constexpr size_t nit = align16(meta + MAX_TILE_CANDIDATES * sizeof(int2));
+    static constexpr size_t best = align16(nit + MAX_TILE_CANDIDATES * sizeof(int));
     static constexpr size_t first = align16(best + TILE_PIXELS * sizeof(unsigned long long));
     static constexpr size_t owner = align16(first + (MAX_TILE_CANDIDATES + 1) * sizeof(int));
     static constexpr size_t misc = align16(owner + MAX_ITEMS);
     static constexpr size_t total = align16(misc + 64);
 };
-static_assert(AssignSmem::cid % 16 == 0 && AssignSmem::rect % 16 == 0 &&
+static_assert(AssignSmem::cid % 16 == 0 && AssignSmem::rect % 16 == 0 && AssignSmem::meta % 16 == 0 &&
+                  AssignSmem::nit % 16 == 0 &&
                   AssignSmem::best % 16 == 0 && AssignSmem::first % 16 == 0 &&
                   AssignSmem::owner % 16 == 0 && AssignSmem::misc % 16 == 0 &&
                   (AssignSmem::misc + 32) % 8 == 0,
@@ -184,7 +189,10 @@ __device__ __forceinline__ unsigned long long pack_best(float D, int slot)
 }
 
 // Items: the pixels of a candidate's window that lie in the tile form a
-// rectangle; it is cut into 8 x 4 blocks, one block per warp-sized item.
+// rectangle; it is cut into 8 x 8 cells and each cell into two warp-sized
+// halves.  A cell whose paths run mostly along x is split into left and right
+// 4 x 8 halves, otherwise into top and bottom 8 x 4 halves, so that the path
+// lengths of a warp's 32 pixels differ by at most about 4.
 template <typename T, bool STAGED, int THREADS>
 __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
     k_assign(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
@@ -208,6 +216,8 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
     ClusterDev *cand = reinterpret_cast<ClusterDev *>(sm + AssignSmem::cand);
     int *cid = reinterpret_cast<int *>(sm + AssignSmem::cid);
     int4 *rect = reinterpret_cast<int4 *>(sm + AssignSmem::rect);
+    int2 *meta = reinterpret_cast<int2 *>(sm + AssignSmem::meta);
+    int *nit = reinterpret_cast<int *>(sm + AssignSmem::nit);
     unsigned long long *best = reinterpret_cast<unsigned long long *>(sm + AssignSmem::best);
     int *first = reinterpret_cast<int *>(sm + AssignSmem::first);
     unsigned char *owner = sm + AssignSmem::owner;
@@ -249,16 +259,20 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
         const ClusterDev cd = a.cdev[myid];
         cid[rank] = myid;
         cand[rank] = cd;
-        // window x tile (clipped to the image), in 8 x 4 blocks
+        // window x tile (clipped to the image), in 8 x 8 cells of two items
         const int xa = max(cd.xlo, x0), xb = min(min(cd.xhi, x0 + TILE_X - 1), a.W - 1);
         const int ya = max(cd.ylo, y0), yb = min(min(cd.yhi, y0 + TILE_Y - 1), a.H - 1);
-        int nbx = 0, nblk = 0;
+        int ncx = 1, nitems = 0;
         if (xa <= xb && ya <= yb) {
-            nbx = (xb - xa) / WARP_BLOCK_X + 1;
-            nblk = nbx * ((yb - ya) / WARP_BLOCK_Y + 1);
+            ncx = (xb - xa) / CELL + 1;
+            nitems = 2 * ncx * ((yb - ya) / CELL + 1);
         }
-        // (x origin, y origin, blocks per row, blocks)
-        rect[rank] = make_int4(xa, ya, nbx, nblk);
+        const bool inside = STAGED && cd.ex >= rx0 && cd.ex < rx0 + BX && cd.ey >= ry0 &&
+                            cd.ey < ry0 + BY;
+        rect[rank] = make_int4(xa, ya, xb, yb);
+        // cells per row, endpoint-in-region flag, 16-bit reciprocal of ncx
+        meta[rank] = make_int2(ncx | ((int)inside << 8), (65536 + ncx - 1) / ncx);
+        nit[rank] = nitems;
     }
     __syncthreads();
     for (int i = tid; i < TILE_PIXELS; i += THREADS) best[i] = ~0ull;
@@ -269,7 +283,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
 #pragma unroll
         for (int i = 0; i < PER; ++i) {
             const int c = lane * PER + i;
-            v[i] = c < cnt ? rect[c].w : 0;
+            v[i] = c < cnt ? nit[c] : 0;
             sum += v[i];
         }
         int incl = sum;
@@ -288,7 +302,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
     }
     __syncthreads();
     if (fast && tid < cnt) {
-        const int f = first[tid], n = rect[tid].w;
+        const int f = first[tid], n = nit[tid];
         for (int j = 0; j < n; ++j) owner[f + j] = (unsigned char)tid;
     }
 
@@ -324,17 +338,20 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
             if (item >= n_items) break;
             const int c = owner[item];
             const int4 rc = rect[c];
+            const int2 mt = meta[c];
             const int local = item - first[c];
-            const int by = local / rc.z, bx = local - by * rc.z;
-            const int qx = rc.x + bx * WARP_BLOCK_X + (lane % WARP_BLOCK_X);
-            const int qy = rc.y + by * WARP_BLOCK_Y + (lane / WARP_BLOCK_X);
+            const int cell = local >> 1, half = local & 1;
+            const int cy = (cell * mt.y) >> 16;  // exact: cell < 2^12, ncx <= 4
+            const int cx = cell - cy * (mt.x & 0xff);
+            const int ox = rc.x + CELL * cx, oy = rc.y + CELL * cy;
             const ClusterDev cd = cand[c];
-            if (qx > cd.xhi || qy > cd.yhi || qx >= x0 + TILE_X || qy >= y0 + TILE_Y ||
-                qx >= a.W || qy >= a.H)
-                continue;
+            // dominant axis of the paths from the cell centre to the endpoint
+            const bool xmaj = abs(2 * (ox - cd.ex) + CELL - 1) > abs(2 * (oy - cd.ey) + CELL - 1);
+            const int qx = xmaj ? ox + 4 * half + (lane & 3) : ox + (lane & 7);
+            const int qy = xmaj ? oy + (lane >> 2) : oy + 4 * half + (lane >> 3);
+            if (qx > rc.z || qy > rc.w) continue;
             const PathSetup s = path_setup(qx, qy, cd.ex, cd.ey);
-            const bool inside = STAGED && cd.ex >= rx0 && cd.ex < rx0 + BX && cd.ey >= ry0 &&
-                                cd.ey < ry0 + BY;
+            const bool inside = (mt.x >> 8) != 0;
             float sdc, sw;
             int len;
             float4 v;
@@ -416,8 +433,8 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
             }
         }
         // fire-and-forget reductions into the global cluster sums, one set
-        // per label group of the warp
-        warp_aggregate_global(valid, lab, px, py, own, a.acc);
+        // per label group of the warp (offsets within the tile)
+        warp_aggregate_global(valid, lab, x0, y0, px - x0, py - y0, own, a.acc);
     }
     if (a.count_samples) {
         for (int o = 16; o > 0; o >>= 1) {

@@ -17,17 +17,15 @@ constexpr int TILE_Y = 32;
 constexpr int TILE_PIXELS = TILE_X * TILE_Y;
 constexpr int WARP_BLOCK_X = 8;
 constexpr int WARP_BLOCK_Y = 4;
-// Work items: 8 x 4 blocks of a candidate's window inside the tile, at most
-// (TILE_X/8)*(TILE_Y/4) per candidate.
-constexpr int MAX_BLOCKS_PER_CANDIDATE = (TILE_X / WARP_BLOCK_X) * (TILE_Y / WARP_BLOCK_Y);
 // Candidate clusters of one tile held in shared memory.  A tile with more
 // candidates (never seen on the regular grid) takes a slower per-pixel path.
 constexpr int MAX_TILE_CANDIDATES = 128;
 // Extra halo beyond round(r) so that endpoints projected by Eq. 4 a pixel or
 // two from the barycenter still walk in shared memory.
 constexpr int HALO_MARGIN = 2;
-// Colour sums are kept as integers: value * 2^COLOR_FRAC_BITS, rounded.
-constexpr int COLOR_FRAC_BITS = 24;
+// Colour sums are kept as integers: value * 2^COLOR_FRAC_BITS, rounded.  CIELab
+// of 8-bit sRGB has |L|, |a|, |b| < 108, so 32 such values sum below 2^31.
+constexpr int COLOR_FRAC_BITS = 19;
 
 // What the assignment kernel reads about one cluster (48 bytes).
 struct ClusterDev {
@@ -210,32 +208,37 @@ __device__ __forceinline__ float scalp_distance(float dcp, float sum_dc, float s
 // Colour values are fixed point (x 2^24, fits int32 for CIELab of sRGB) and
 // summed as two int32 halves so a 32-lane sum cannot overflow.
 // ---------------------------------------------------------------------------
+// Warp-aggregated segmented reduction.  Lanes holding the same key are summed
+// with warp reductions and the group's first lane hands the sums to `sink`.
+// Coordinates come relative to a warp-uniform base (bx, by) with offsets in
+// [0, 31], so both offset sums pack into one 32-bit reduction; colour values
+// are fixed point (x 2^COLOR_FRAC_BITS), small enough that a 32-lane sum fits
+// in 32 bits.
 template <class Sink>
-__device__ __forceinline__ void warp_aggregate(bool valid, int key, int x, int y, float4 v,
-                                               Sink &&sink)
+__device__ __forceinline__ void warp_aggregate(bool valid, int key, int bx, int by, int dx, int dy,
+                                               float4 v, Sink &&sink)
 {
     const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const float scale = (float)(1 << COLOR_FRAC_BITS);
-    int qL = valid ? __float2int_rn(v.x * scale) : 0;
-    int qa = valid ? __float2int_rn(v.y * scale) : 0;
-    int qb = valid ? __float2int_rn(v.z * scale) : 0;
+    const int qL = valid ? __float2int_rn(v.x * scale) : 0;
+    const int qa = valid ? __float2int_rn(v.y * scale) : 0;
+    const int qb = valid ? __float2int_rn(v.z * scale) : 0;
+    const unsigned qxy = valid ? (unsigned)dx | ((unsigned)dy << 16) : 0u;
     unsigned pending = __ballot_sync(FULL, valid);
     while (pending) {
-        int leader = __ffs(pending) - 1;
-        int k = __shfl_sync(FULL, key, leader);
-        bool mine = valid && key == k;
-        unsigned grp = __ballot_sync(FULL, mine);
-        long long cnt = __popc(grp);
-        long long sx = __reduce_add_sync(FULL, (unsigned)(mine ? x : 0));
-        long long sy = __reduce_add_sync(FULL, (unsigned)(mine ? y : 0));
-        long long sL = ((long long)__reduce_add_sync(FULL, mine ? (qL >> 12) : 0) << 12) +
-                       (long long)__reduce_add_sync(FULL, (unsigned)(mine ? (qL & 4095) : 0));
-        long long sa = ((long long)__reduce_add_sync(FULL, mine ? (qa >> 12) : 0) << 12) +
-                       (long long)__reduce_add_sync(FULL, (unsigned)(mine ? (qa & 4095) : 0));
-        long long sb = ((long long)__reduce_add_sync(FULL, mine ? (qb >> 12) : 0) << 12) +
-                       (long long)__reduce_add_sync(FULL, (unsigned)(mine ? (qb & 4095) : 0));
-        if (lane == leader) sink(k, cnt, sx, sy, sL, sa, sb);
+        const int leader = __ffs(pending) - 1;
+        const int k = __shfl_sync(FULL, key, leader);
+        const bool mine = valid && key == k;
+        const unsigned grp = __ballot_sync(FULL, mine);
+        const long long cnt = __popc(grp);
+        const unsigned sxy = __reduce_add_sync(FULL, mine ? qxy : 0u);
+        const long long sL = __reduce_add_sync(FULL, mine ? qL : 0);
+        const long long sa = __reduce_add_sync(FULL, mine ? qa : 0);
+        const long long sb = __reduce_add_sync(FULL, mine ? qb : 0);
+        if (lane == leader)
+            sink(k, cnt, cnt * bx + (long long)(sxy & 0xffffu), cnt * by + (long long)(sxy >> 16), sL,
+                 sa, sb);
         pending &= ~grp;
     }
 }
@@ -252,10 +255,10 @@ __device__ __forceinline__ void acc_add(ClusterAcc *c, long long n, long long sx
 }
 
 // Sum straight into the global per-cluster sums.
-__device__ __forceinline__ void warp_aggregate_global(bool valid, int label, int x, int y,
-                                                      float4 v, ClusterAcc *acc)
+__device__ __forceinline__ void warp_aggregate_global(bool valid, int label, int bx, int by, int dx,
+                                                      int dy, float4 v, ClusterAcc *acc)
 {
-    warp_aggregate(valid, label, x, y, v,
+    warp_aggregate(valid, label, bx, by, dx, dy, v,
                    [&](int k, long long n, long long sx, long long sy, long long sL, long long sa,
                        long long sb) { acc_add(&acc[k], n, sx, sy, sL, sa, sb); });
 }

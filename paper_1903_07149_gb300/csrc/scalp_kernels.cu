@@ -90,23 +90,26 @@ void launch_setup(const SolveArgs &a, const uint8_t *rgb, long long rgb_stride,
 }
 
 // Integer sums of (1, x, y, L, a, b) per label (the means of the update).
-// Each warp takes 32 consecutive pixels of a row, whose labels are mostly
+// Each warp takes a 32-pixel segment of one row, whose labels are mostly
 // equal, so the warp-aggregated sums need few reductions per warp.
 template <typename T>
 __global__ void __launch_bounds__(256) k_accumulate(SolveArgs a, const T *__restrict__ plane)
 {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    const long long base0 = blockIdx.x * (long long)blockDim.x + (threadIdx.x & ~31);
-    for (long long base = base0; base < a.N; base += stride) {
-        // warp-uniform trip count: every lane takes part in the reductions
-        const long long p = base + (threadIdx.x & 31);
-        const bool valid = p < a.N;
+    const long long segs_per_row = (a.W + 31) / 32;
+    const long long n_segs = segs_per_row * a.H;
+    const long long warps = (long long)gridDim.x * (blockDim.x / 32);
+    for (long long seg = blockIdx.x * (long long)(blockDim.x / 32) + (threadIdx.x >> 5); seg < n_segs;
+         seg += warps) {
+        // warp-uniform loop: every lane takes part in the reductions
+        const int y = (int)(seg / segs_per_row);
+        const int bx = (int)(seg % segs_per_row) * 32;
+        const int x = bx + (threadIdx.x & 31);
+        const bool valid = x < a.W;
+        const long long p = (long long)y * a.W + x;
         const int lab = valid ? a.labels[p] : 0;
-        const int y = valid ? (int)(p / a.W) : 0;
-        const int x = valid ? (int)(p - (long long)y * a.W) : 0;
         const float4 v = valid ? fetch_sample<T>(plane + (long long)y * a.pitch + x)
                                : make_float4(0, 0, 0, 0);
-        warp_aggregate_global(valid, lab, x, y, v, a.acc);
+        warp_aggregate_global(valid, lab, bx, y, x - bx, 0, v, a.acc);
     }
 }
 
