@@ -169,6 +169,37 @@ int scalp_sync(scalp_ctx *ctx);
 const char *scalp_last_error(const scalp_ctx *ctx);
 void scalp_destroy(scalp_ctx *ctx);
 
+/* ---- An entry point that allocates nothing (no counterpart in the paper) ----
+ *
+ * For callers that cannot allocate device memory: code running while another
+ * component owns the device memory budget, plugins handed only their input
+ * and output buffers, or hosts where an allocation would synchronise the
+ * device at the wrong moment.  It computes, for each label of a label map,
+ * the mean CIELab colour and barycenter of its pixels (the means of the
+ * cluster update, for a decomposition the caller holds), using no workspace:
+ * its scratch is a fixed file-scope device array of SCALP_STATIC_MAX_LABELS
+ * integer sums plus a 1 KB table, about 4 MB that every GPU loading this
+ * library keeps until the process exits.  No cudaMalloc, cudaFree or other
+ * allocating call is made.
+ *
+ *   rgb       device pointer, H rows of W*3 bytes of 8-bit sRGB
+ *   rgb_stride bytes between rows; 0 means 3*W
+ *   labels    device pointer, H*W int32; labels outside [0, n_labels) are skipped
+ *   n_labels  1 <= n_labels <= SCALP_STATIC_MAX_LABELS, else SCALP_E_ARG
+ *   out       device pointer, n_labels x 6 doubles per label:
+ *             (pixel count, mean L, mean a, mean b, mean x, mean y); zeros if empty
+ *   stream    cudaStream_t the work is enqueued on (asynchronous)
+ *
+ * The first call on each device sets up the scratch (looks up its device
+ * address and fills the table, synchronising that stream once); make that
+ * first call before any stream capture.  Every call shares the one scratch
+ * array and clears the sums it uses, so calls that overlap on the GPU (other
+ * streams, other threads) race and must be serialised by the caller.
+ * Errors: SCALP_E_ARG / SCALP_E_CUDA, text via scalp_last_error(NULL). */
+#define SCALP_STATIC_MAX_LABELS 65536
+int scalp_label_means_static(const uint8_t *rgb, int64_t rgb_stride, const int32_t *labels,
+                             int32_t H, int32_t W, int32_t n_labels, double *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -124,6 +124,11 @@ PFN_encodeTiled get_encode()
 
 }  // namespace
 
+namespace scalp {
+// Sets the text scalp_last_error(NULL) returns on this thread.
+void set_last_error(const char *msg) { g_last_error = msg; }
+}  // namespace scalp
+
 struct scalp_ctx {
     int H, W, K;
     long long N;

@@ -5,6 +5,9 @@
 
 namespace scalp {
 
+// Sets the text scalp_last_error(NULL) returns on this thread.
+void set_last_error(const char *msg);
+
 // Per-pixel set-up: CIELab (Sec. II-A), contour factor 1-exp(-C^2/sigma^2)
 // of Eq. 2, grid label.  rgb/contour are device pointers with row strides.
 void launch_setup(const SolveArgs &a, const uint8_t *rgb, long long rgb_stride,

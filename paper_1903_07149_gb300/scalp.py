@@ -65,7 +65,7 @@ EXPORTS = (
     "scalp_default_params", "scalp_workspace_bytes", "scalp_init", "scalp_reload",
     "scalp_iterate", "scalp_labels", "scalp_get_info", "scalp_get_state", "scalp_set_state",
     "scalp_debug_paths", "scalp_profile", "scalp_count_samples", "scalp_sync",
-    "scalp_last_error", "scalp_destroy",
+    "scalp_last_error", "scalp_destroy", "scalp_label_means_static",
 )
 
 _lib = None
@@ -104,6 +104,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "scalp_sync": (ctypes.c_int, [P]),
             "scalp_last_error": (ctypes.c_char_p, [P]),
             "scalp_destroy": (None, [P]),
+            "scalp_label_means_static": (ctypes.c_int, [P, I64, P, I32, I32, I32, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -197,6 +198,15 @@ def scalp_sync(ctx):
 
 def scalp_destroy(ctx):
     load().scalp_destroy(ctx)
+
+
+def scalp_label_means_static(rgb_ptr: int, rgb_stride: int, labels_ptr: int, H: int, W: int,
+                             n_labels: int, out_ptr: int, stream_ptr: int):
+    """Per-label means with no device allocation (device pointers in and out)."""
+    _check(load().scalp_label_means_static(ctypes.c_void_p(rgb_ptr), int(rgb_stride),
+                                           ctypes.c_void_p(labels_ptr), int(H), int(W),
+                                           int(n_labels), ctypes.c_void_p(out_ptr),
+                                           ctypes.c_void_p(stream_ptr)))
 
 
 # --- convenience wrapper over the C calls -------------------------------------
