@@ -169,6 +169,42 @@ int scalp_sync(scalp_ctx *ctx);
 const char *scalp_last_error(const scalp_ctx *ctx);
 void scalp_destroy(scalp_ctx *ctx);
 
+/* ---- Batches: many images of uneven size and K solved together ----------------
+ *
+ * The paper solves one image at a time; solving many at once is this library's
+ * addition.  Every image gets its own solver state (as scalp_init would give
+ * it) inside one caller-owned workspace of scalp_batch_workspace_bytes()
+ * bytes; each iteration of Algorithm 1 then runs as one launch per kernel for
+ * all images together, and n iterations replay as one CUDA graph (non-NULL
+ * stream, params->use_graph).  Results are identical to solving each image
+ * alone with the same parameters. */
+typedef struct scalp_batch scalp_batch;
+
+size_t scalp_batch_workspace_bytes(int32_t count, const int32_t *H, const int32_t *W,
+                                   const int32_t *K, const scalp_params *params);
+
+/* images[i], contours[i] (contours may be NULL: no prior), K[i], m[i] as for
+ * scalp_init; params->workspace/stream/storage apply to the whole batch. */
+int scalp_batch_init(scalp_batch **out, int32_t count, const scalp_image *images,
+                     const scalp_contour *contours, const int32_t *K, const float *m,
+                     const scalp_params *params);
+
+/* New images and contours of the same sizes; clusters re-initialised. */
+int scalp_batch_reload(scalp_batch *b, const scalp_image *images, const scalp_contour *contours);
+
+/* n iterations for every image (asynchronous). */
+int scalp_batch_iterate(scalp_batch *b, int32_t n);
+
+/* Labels of every image into outs[i] (H_i*W_i int32, host or device memory per
+ * out_on_device), connectivity enforced when enforce != 0; n_labels[i] gets
+ * the count.  Synchronises the stream once. */
+int scalp_batch_labels(scalp_batch *b, int32_t *const *outs, int32_t out_on_device,
+                       int32_t enforce, int32_t *n_labels);
+
+int scalp_batch_get_state(scalp_batch *b, int32_t index, const scalp_state *state);
+int scalp_batch_get_info(const scalp_batch *b, int32_t index, scalp_info *info);
+void scalp_batch_destroy(scalp_batch *b);
+
 /* ---- An entry point that allocates nothing (no counterpart in the paper) ----
  *
  * For callers that cannot allocate device memory: code running while another

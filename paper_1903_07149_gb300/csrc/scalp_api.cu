@@ -5,6 +5,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
+#include <algorithm>
 #include <cstring>
 #include <new>
 #include <string>
@@ -729,6 +730,285 @@ void scalp_destroy(scalp_ctx *c)
     if (c->graph_valid) cudaGraphExecDestroy(c->gexec);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches: many images of uneven size and K solved together.  Each image is an
+// ordinary context carved from the batch workspace; the iteration kernels of
+// all images run as one launch each (tiles, clusters and list slots of all
+// images in one flat index space), and n iterations replay as one CUDA graph.
+// ---------------------------------------------------------------------------
+struct scalp_batch {
+    int count = 0;
+    std::vector<scalp_ctx *> ctx;
+    cudaStream_t st = nullptr;
+    int storage = 0;
+    int use_graph = 1;
+    unsigned char *ws = nullptr;
+    BatchArgs bargs{};
+    int *d_gather = nullptr;     // count label counts + count x DevCounters, gathered
+    int total_tiles = 0, total_clusters = 0, total_fill = 0;
+    size_t smem = 0;
+    cudaGraphExec_t gexec{};
+    bool graph_valid = false;
+    int graph_n = 0;
+};
+
+namespace {
+
+size_t batch_head_bytes(int count)
+{
+    size_t cur = 0;
+    carve(cur, (size_t)count * sizeof(CUtensorMap));
+    carve(cur, (size_t)count * sizeof(SolveArgs));
+    for (int i = 0; i < 3; ++i) carve(cur, (size_t)(count + 1) * sizeof(int));
+    carve(cur, (size_t)count * (sizeof(int) + sizeof(DevCounters)));
+    return (cur + ALIGN - 1) & ~(ALIGN - 1);
+}
+
+int batch_fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t scalp_batch_workspace_bytes(int32_t count, const int32_t *H, const int32_t *W,
+                                   const int32_t *K, const scalp_params *p)
+{
+    if (count < 1 || !H || !W || !K) return 0;
+    size_t total = batch_head_bytes(count);
+    for (int i = 0; i < count; ++i) {
+        const size_t b = scalp_workspace_bytes(H[i], W[i], K[i], p);
+        if (b == 0) return 0;
+        total += (b + ALIGN - 1) & ~(ALIGN - 1);
+    }
+    return total;
+}
+
+void scalp_batch_destroy(scalp_batch *b)
+{
+    if (!b) return;
+    cudaStreamSynchronize(b->st);
+    if (b->graph_valid) cudaGraphExecDestroy(b->gexec);
+    for (scalp_ctx *c : b->ctx) scalp_destroy(c);
+    delete b;
+}
+
+int scalp_batch_init(scalp_batch **out, int32_t count, const scalp_image *images,
+                     const scalp_contour *contours, const int32_t *K, const float *m,
+                     const scalp_params *params)
+{
+    if (!out) return batch_fail(SCALP_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (count < 1 || !images || !K || !m || !params)
+        return batch_fail(SCALP_E_ARG, "need count >= 1 and images, K, m, params");
+    std::vector<int32_t> Hs(count), Ws(count);
+    for (int i = 0; i < count; ++i) {
+        Hs[i] = images[i].H;
+        Ws[i] = images[i].W;
+    }
+    const size_t need = scalp_batch_workspace_bytes(count, Hs.data(), Ws.data(), K, params);
+    if (need == 0) return batch_fail(SCALP_E_ARG, "invalid image size or K in the batch");
+    if (!params->workspace || params->workspace_bytes < need)
+        return batch_fail(SCALP_E_NOMEM, "batch workspace of %zu bytes needed, %zu given", need,
+                          params->workspace ? params->workspace_bytes : (size_t)0);
+    if (reinterpret_cast<uintptr_t>(params->workspace) % ALIGN)
+        return batch_fail(SCALP_E_ARG, "workspace must be 256-byte aligned");
+    scalp_batch *b = new (std::nothrow) scalp_batch();
+    if (!b) return batch_fail(SCALP_E_NOMEM, "host allocation failed");
+    b->count = count;
+    b->st = reinterpret_cast<cudaStream_t>(params->stream);
+    b->storage = params->storage;
+    b->use_graph = params->use_graph;
+    b->ws = reinterpret_cast<unsigned char *>(params->workspace);
+    size_t cur = 0;
+    const size_t o_tmaps = carve(cur, (size_t)count * sizeof(CUtensorMap));
+    const size_t o_args = carve(cur, (size_t)count * sizeof(SolveArgs));
+    const size_t o_tile = carve(cur, (size_t)(count + 1) * sizeof(int));
+    const size_t o_clus = carve(cur, (size_t)(count + 1) * sizeof(int));
+    const size_t o_fill = carve(cur, (size_t)(count + 1) * sizeof(int));
+    const size_t o_gather = carve(cur, (size_t)count * (sizeof(int) + sizeof(DevCounters)));
+    size_t off = batch_head_bytes(count);
+    std::vector<SolveArgs> args(count);
+    std::vector<CUtensorMap> tmaps(count);
+    std::vector<int> tile_base(count + 1, 0), clus_base(count + 1, 0), fill_base(count + 1, 0);
+    for (int i = 0; i < count; ++i) {
+        scalp_params p = *params;
+        p.use_graph = 0;
+        p.workspace = b->ws + off;
+        p.workspace_bytes = scalp_workspace_bytes(Hs[i], Ws[i], K[i], params);
+        off += (p.workspace_bytes + ALIGN - 1) & ~(ALIGN - 1);
+        scalp_ctx *c = nullptr;
+        const int rc = scalp_init(&c, &images[i], contours ? &contours[i] : nullptr, K[i], m[i], &p);
+        if (rc != SCALP_OK) {
+            char msg[512];
+            snprintf(msg, sizeof msg, "image %d: %s", i, g_last_error.c_str());
+            scalp_batch_destroy(b);
+            return batch_fail(rc, "%s", msg);
+        }
+        b->ctx.push_back(c);
+        args[i] = c->a;
+        tmaps[i] = c->tmap;
+        tile_base[i + 1] = tile_base[i] + c->a.n_tx * c->a.n_ty;
+        clus_base[i + 1] = clus_base[i] + c->Keff;
+        fill_base[i + 1] = fill_base[i] + c->Keff * c->a.tpw_x * c->a.tpw_y;
+        b->smem = std::max(b->smem, c->smem);
+    }
+    b->total_tiles = tile_base[count];
+    b->total_clusters = clus_base[count];
+    b->total_fill = fill_base[count];
+    b->bargs.args = reinterpret_cast<const SolveArgs *>(b->ws + o_args);
+    b->bargs.tmaps = reinterpret_cast<const CUtensorMap *>(b->ws + o_tmaps);
+    b->bargs.tile_base = reinterpret_cast<const int *>(b->ws + o_tile);
+    b->bargs.clus_base = reinterpret_cast<const int *>(b->ws + o_clus);
+    b->bargs.fill_base = reinterpret_cast<const int *>(b->ws + o_fill);
+    b->bargs.count = count;
+    b->d_gather = reinterpret_cast<int *>(b->ws + o_gather);
+    cudaError_t e = cudaMemcpyAsync(b->ws + o_tmaps, tmaps.data(), count * sizeof(CUtensorMap),
+                                    cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->ws + o_args, args.data(), count * sizeof(SolveArgs),
+                            cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->ws + o_tile, tile_base.data(), (count + 1) * sizeof(int),
+                            cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->ws + o_clus, clus_base.data(), (count + 1) * sizeof(int),
+                            cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->ws + o_fill, fill_base.data(), (count + 1) * sizeof(int),
+                            cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);  // host vectors go out of scope
+    if (e == cudaSuccess) e = assign_batch_configure(b->storage, b->smem);
+    if (e != cudaSuccess) {
+        scalp_batch_destroy(b);
+        return batch_fail(SCALP_E_CUDA, "batch set-up: %s", cudaGetErrorString(e));
+    }
+    *out = b;
+    return SCALP_OK;
+}
+
+int scalp_batch_reload(scalp_batch *b, const scalp_image *images, const scalp_contour *contours)
+{
+    if (!b || !images) return batch_fail(SCALP_E_ARG, "batch or images is NULL");
+    for (int i = 0; i < b->count; ++i) {
+        const int rc = scalp_reload(b->ctx[i], &images[i], contours ? &contours[i] : nullptr);
+        if (rc != SCALP_OK) return batch_fail(rc, "image %d: %s", i, b->ctx[i]->err.c_str());
+    }
+    return SCALP_OK;
+}
+
+int scalp_batch_iterate(scalp_batch *b, int32_t n)
+{
+    if (!b) return batch_fail(SCALP_E_ARG, "batch is NULL");
+    if (n < 0) return batch_fail(SCALP_E_ARG, "n must be >= 0");
+    if (n == 0) return SCALP_OK;
+    auto enqueue = [&](int iters) {
+        for (int i = 0; i < iters; ++i) {
+            launch_assign_batch(b->bargs, b->storage, b->total_tiles, b->smem, b->st);
+            launch_batch_update(b->bargs, b->total_clusters, b->total_fill, b->st);
+        }
+    };
+    const bool graphs = b->use_graph && b->st != nullptr;
+    cudaError_t e = cudaSuccess;
+    if (graphs && !(b->graph_valid && b->graph_n == n)) {
+        if (b->graph_valid) {
+            cudaGraphExecDestroy(b->gexec);
+            b->graph_valid = false;
+        }
+        cudaGraph_t g;
+        e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
+        if (e != cudaSuccess) return batch_fail(SCALP_E_CUDA, "begin capture: %s", cudaGetErrorString(e));
+        enqueue(n);
+        const cudaError_t le = cudaGetLastError();
+        e = cudaStreamEndCapture(b->st, &g);
+        if (e == cudaSuccess && le != cudaSuccess) {
+            cudaGraphDestroy(g);
+            e = le;
+        }
+        if (e != cudaSuccess) return batch_fail(SCALP_E_CUDA, "capture: %s", cudaGetErrorString(e));
+        e = cudaGraphInstantiate(&b->gexec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return batch_fail(SCALP_E_CUDA, "instantiate: %s", cudaGetErrorString(e));
+        b->graph_valid = true;
+        b->graph_n = n;
+    }
+    if (graphs) {
+        e = cudaGraphLaunch(b->gexec, b->st);
+    } else {
+        enqueue(n);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) return batch_fail(SCALP_E_CUDA, "batch iteration: %s", cudaGetErrorString(e));
+    for (scalp_ctx *c : b->ctx) c->iterations += n;
+    return SCALP_OK;
+}
+
+int scalp_batch_labels(scalp_batch *b, int32_t *const *outs, int32_t out_on_device, int32_t enforce,
+                       int32_t *n_labels)
+{
+    if (!b || !outs) return batch_fail(SCALP_E_ARG, "batch or outs is NULL");
+    for (int i = 0; i < b->count; ++i)
+        if (!outs[i]) return batch_fail(SCALP_E_ARG, "outs[%d] is NULL", i);
+    int *d_nlab = b->d_gather;
+    DevCounters *d_ctr = reinterpret_cast<DevCounters *>(b->d_gather + b->count);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < b->count && e == cudaSuccess; ++i) {
+        scalp_ctx *c = b->ctx[i];
+        const size_t bytes = sizeof(int) * (size_t)c->N;
+        if (enforce) {
+            int *dst = out_on_device ? outs[i] : c->ccl.link;
+            int *c_nlab = reinterpret_cast<int *>(c->ws + c->L.nlab);
+            launch_ccl(c->a.labels, c->H, c->W, c->K, dst, c->ccl, c_nlab, c->a.ctr, b->st);
+            e = cudaGetLastError();
+            if (e == cudaSuccess && !out_on_device)
+                e = cudaMemcpyAsync(outs[i], dst, bytes, cudaMemcpyDeviceToHost, b->st);
+            if (e == cudaSuccess)
+                e = cudaMemcpyAsync(d_nlab + i, c_nlab, sizeof(int), cudaMemcpyDeviceToDevice, b->st);
+        } else {
+            e = cudaMemcpyAsync(outs[i], c->a.labels, bytes,
+                                out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->st);
+        }
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(d_ctr + i, c->a.ctr, sizeof(DevCounters), cudaMemcpyDeviceToDevice, b->st);
+    }
+    if (e != cudaSuccess) return batch_fail(SCALP_E_CUDA, "batch labels: %s", cudaGetErrorString(e));
+    std::vector<int> nlab(b->count);
+    std::vector<DevCounters> ctr(b->count);
+    e = cudaMemcpyAsync(nlab.data(), d_nlab, sizeof(int) * b->count, cudaMemcpyDeviceToHost, b->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(ctr.data(), d_ctr, sizeof(DevCounters) * b->count, cudaMemcpyDeviceToHost, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return batch_fail(SCALP_E_CUDA, "batch labels: %s", cudaGetErrorString(e));
+    for (int i = 0; i < b->count; ++i) {
+        if (ctr[i].timeout) return batch_fail(SCALP_E_TIMEOUT, "image %d: a bounded wait gave up", i);
+        if (ctr[i].error) return batch_fail(SCALP_E_INTERNAL, "image %d: device check failed (%d)", i, ctr[i].error);
+        if (n_labels) n_labels[i] = enforce ? nlab[i] : b->ctx[i]->Keff;
+    }
+    return SCALP_OK;
+}
+
+int scalp_batch_get_state(scalp_batch *b, int32_t index, const scalp_state *state)
+{
+    if (!b || index < 0 || index >= b->count) return batch_fail(SCALP_E_ARG, "bad batch or index");
+    return scalp_get_state(b->ctx[index], state);
+}
+
+int scalp_batch_get_info(const scalp_batch *b, int32_t index, scalp_info *info)
+{
+    if (!b || index < 0 || index >= b->count) return batch_fail(SCALP_E_ARG, "bad batch or index");
+    return scalp_get_info(b->ctx[index], info);
 }
 
 }  // extern "C"

@@ -193,16 +193,16 @@ __device__ __forceinline__ unsigned long long pack_best(float D, int slot)
 // halves.  A cell whose paths run mostly along x is split into left and right
 // 4 x 8 halves, otherwise into top and bottom 8 x 4 halves, so that the path
 // lengths of a warp's 32 pixels differ by at most about 4.
+// One tile of one image (the body shared by the single-image and the batched
+// kernels).  `tmap` is the image's tensor map (kernel parameter or global).
 template <typename T, bool STAGED, int THREADS>
-__global__ void __launch_bounds__(THREADS, 1024 / THREADS)
-    k_assign(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
+__device__ __forceinline__ void assign_tile(const SolveArgs &a, const CUtensorMap *tmap, int tile,
+                                            unsigned char *smem)
 {
     constexpr int PIX_PER_THREAD = TILE_PIXELS / THREADS;
     constexpr int WARPS = THREADS / 32;
-    extern __shared__ __align__(1024) unsigned char smem[];
     const T *__restrict__ plane = reinterpret_cast<const T *>(
         sizeof(T) == 16 ? (const void *)a.plane32 : (const void *)a.plane16);
-    const int tile = blockIdx.x;
     const int tx = tile % a.n_tx, ty = tile / a.n_tx;
     const int x0 = tx * TILE_X, y0 = ty * TILE_Y;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
             "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
             "r"(bytes)
             : "memory");
-        tma_load_region<T>(&tmap, region, bar, rx0, ry0);
+        tma_load_region<T>(tmap, region, bar, rx0, ry0);
     }
 
     const int off = a.tile_off[tile];
@@ -449,6 +449,27 @@ __global__ void __launch_bounds__(THREADS, 1024 / THREADS)
 }
 
 template <typename T, bool STAGED, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS)
+    k_assign(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    assign_tile<T, STAGED, THREADS>(a, &tmap, blockIdx.x, smem);
+}
+
+// All tiles of all images of a batch in one launch: block g is tile
+// g - tile_base[i] of image i, tile_base being the prefix of tile counts.
+template <typename T, int THREADS>
+__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_assign_batch(BatchArgs b)
+{
+    extern __shared__ __align__(1024) unsigned char smem[];
+    const int g = blockIdx.x;
+    const int i = batch_find(b.tile_base, b.count, g);
+    const SolveArgs &a = b.args[i];
+    if (a.halo > 0) assign_tile<T, true, THREADS>(a, &b.tmaps[i], g - b.tile_base[i], smem);
+    else assign_tile<T, false, THREADS>(a, &b.tmaps[i], g - b.tile_base[i], smem);
+}
+
+template <typename T, bool STAGED, int THREADS>
 static void launch_one(const SolveArgs &a, const CUtensorMap &tmap, size_t smem, cudaStream_t st)
 {
     k_assign<T, STAGED, THREADS><<<a.n_tx * a.n_ty, THREADS, smem, st>>>(a, tmap);
@@ -464,6 +485,21 @@ void launch_assign(const SolveArgs &a, int storage, bool staged, const CUtensorM
         if (staged) launch_one<uint2, true, 512>(a, tmap, smem_bytes, st);
         else launch_one<uint2, false, 512>(a, tmap, smem_bytes, st);
     }
+}
+
+void launch_assign_batch(const BatchArgs &b, int storage, int total_tiles, size_t smem_bytes,
+                         cudaStream_t st)
+{
+    if (total_tiles <= 0) return;
+    if (storage == 0) k_assign_batch<float4, 1024><<<total_tiles, 1024, smem_bytes, st>>>(b);
+    else k_assign_batch<uint2, 512><<<total_tiles, 512, smem_bytes, st>>>(b);
+}
+
+cudaError_t assign_batch_configure(int storage, size_t smem_bytes)
+{
+    const void *f = storage == 0 ? (const void *)k_assign_batch<float4, 1024>
+                                 : (const void *)k_assign_batch<uint2, 512>;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
 }
 
 cudaError_t assign_configure(int storage, bool staged, size_t smem_bytes)

@@ -84,6 +84,30 @@ struct SolveArgs {
     DevCounters *ctr;
 };
 
+// A batch: the argument blocks and tensor maps of `count` images in device
+// memory, and prefix sums that map a flat index (tile, cluster, fill slot) to
+// its image.
+struct BatchArgs {
+    const SolveArgs *args;
+    const CUtensorMap *tmaps;
+    const int *tile_base;   // count+1: prefix of n_tx*n_ty
+    const int *clus_base;   // count+1: prefix of Keff
+    const int *fill_base;   // count+1: prefix of Keff*tpw_x*tpw_y
+    int count;
+};
+
+// Image of flat index g: the last i with base[i] <= g (base[0] = 0).
+__device__ __forceinline__ int batch_find(const int *base, int count, int g)
+{
+    int lo = 0, hi = count - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
 __device__ __forceinline__ float4 load_f16x4(const uint2 *p)
 {
     uint2 u = __ldg(p);

@@ -160,10 +160,8 @@ __device__ bool window_range(long long n, long long s, long long N, long long K,
 // of each tile the window overlaps (for the candidate lists).  The window the
 // last assignment used is kept for the projection search.
 // ---------------------------------------------------------------------------
-__global__ void k_update(SolveArgs a, int from_acc)
+__device__ __forceinline__ void update_cluster(const SolveArgs &a, int k, int from_acc)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= a.Keff) return;
     if (from_acc) {
         ClusterAcc c = a.acc[k];
         ClusterAcc z = {};
@@ -211,6 +209,20 @@ __global__ void k_update(SolveArgs a, int from_acc)
             atomicAdd(&a.tile_count[ty * a.n_tx + tx], 1);
 }
 
+__global__ void k_update(SolveArgs a, int from_acc)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < a.Keff) update_cluster(a, k, from_acc);
+}
+
+__global__ void k_update_batch(BatchArgs b, int from_acc)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= b.clus_base[b.count]) return;
+    const int i = batch_find(b.clus_base, b.count, g);
+    update_cluster(b.args[i], g - b.clus_base[i], from_acc);
+}
+
 void launch_update(const SolveArgs &a, int from_acc, cudaStream_t st)
 {
     // small blocks: one thread per cluster is latency-bound, so spread them
@@ -250,14 +262,15 @@ __device__ __forceinline__ void proj_shfl_min(ProjBest &b)
     }
 }
 
-__global__ void __launch_bounds__(PROJ_THREADS) k_project(SolveArgs a, int whole_image)
+// Queue entries j0, j0 + stride, ... of one image, by one CTA.
+__device__ __forceinline__ void project_cta(const SolveArgs &a, int whole_image, int j0, int stride)
 {
     __shared__ ProjBest s_best[PROJ_THREADS / 32];
     const int nproj = a.ctr->nproj;
     const bool all = whole_image || a.ctr->orphans > 0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double bound = (double)max(a.W, a.H);
-    for (int j = blockIdx.x; j < nproj; j += gridDim.x) {
+    for (int j = j0; j < nproj; j += stride) {
         const int k = a.proj_list[j];
         const long long n = a.st_n[k], sx = a.st_sx[k], sy = a.st_sy[k];
         int xlo = 0, xhi = a.W - 1, ylo = 0, yhi = a.H - 1;
@@ -325,6 +338,20 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(SolveArgs a, int whole
     }
 }
 
+__global__ void __launch_bounds__(PROJ_THREADS) k_project(SolveArgs a, int whole_image)
+{
+    project_cta(a, whole_image, blockIdx.x, gridDim.x);
+}
+
+// Batch: PROJ_CTAS_PER_IMAGE CTAs per image.
+constexpr int PROJ_CTAS_PER_IMAGE = 16;
+
+__global__ void __launch_bounds__(PROJ_THREADS) k_project_batch(BatchArgs b, int whole_image)
+{
+    const int i = blockIdx.x / PROJ_CTAS_PER_IMAGE;
+    project_cta(b.args[i], whole_image, blockIdx.x % PROJ_CTAS_PER_IMAGE, PROJ_CTAS_PER_IMAGE);
+}
+
 void launch_project(const SolveArgs &a, int whole_image, cudaStream_t st)
 {
     k_project<<<std::min(a.Keff, 2 * 152), PROJ_THREADS, 0, st>>>(a, whole_image);
@@ -338,7 +365,7 @@ void launch_project(const SolveArgs &a, int whole_image, cudaStream_t st)
 // ---------------------------------------------------------------------------
 constexpr int SCAN1_THREADS = 1024;
 
-__global__ void __launch_bounds__(SCAN1_THREADS) k_scan_tiles(SolveArgs a)
+__device__ __forceinline__ void scan_tiles_cta(const SolveArgs &a)
 {
     __shared__ int s_warp[32];
     const int n = a.n_tx * a.n_ty;
@@ -380,10 +407,16 @@ __global__ void __launch_bounds__(SCAN1_THREADS) k_scan_tiles(SolveArgs a)
     }
 }
 
-__global__ void k_fill_tiles(SolveArgs a)
+__global__ void __launch_bounds__(SCAN1_THREADS) k_scan_tiles(SolveArgs a) { scan_tiles_cta(a); }
+
+__global__ void __launch_bounds__(SCAN1_THREADS) k_scan_tiles_batch(BatchArgs b)
+{
+    scan_tiles_cta(b.args[blockIdx.x]);
+}
+
+__device__ __forceinline__ void fill_slot(const SolveArgs &a, long long i)
 {
     const long long slots = (long long)a.tpw_x * a.tpw_y;
-    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)a.Keff * slots) return;
     const int k = (int)(i / slots), j = (int)(i % slots);
     const ClusterDev cd = a.cdev[k];
@@ -392,6 +425,29 @@ __global__ void k_fill_tiles(SolveArgs a)
     if (tx > cd.xhi / TILE_X || ty > cd.yhi / TILE_Y) return;
     const int pos = atomicAdd(&a.tile_cursor[ty * a.n_tx + tx], 1);
     if (pos < a.tile_cap) a.tile_list[pos] = k;
+}
+
+__global__ void k_fill_tiles(SolveArgs a)
+{
+    fill_slot(a, blockIdx.x * (long long)blockDim.x + threadIdx.x);
+}
+
+__global__ void k_fill_tiles_batch(BatchArgs b)
+{
+    const int g = blockIdx.x * blockDim.x + threadIdx.x;
+    if (g >= b.fill_base[b.count]) return;
+    const int i = batch_find(b.fill_base, b.count, g);
+    fill_slot(b.args[i], g - b.fill_base[i]);
+}
+
+// One iteration's update, projection and list kernels for a whole batch.
+void launch_batch_update(const BatchArgs &b, int total_clusters, int total_fill, cudaStream_t st)
+{
+    if (b.count <= 0) return;
+    k_update_batch<<<(total_clusters + 63) / 64, 64, 0, st>>>(b, 1);
+    k_project_batch<<<b.count * PROJ_CTAS_PER_IMAGE, PROJ_THREADS, 0, st>>>(b, 0);
+    k_scan_tiles_batch<<<b.count, SCAN1_THREADS, 0, st>>>(b);
+    k_fill_tiles_batch<<<(total_fill + 255) / 256, 256, 0, st>>>(b);
 }
 
 void launch_lists(const SolveArgs &a, cudaStream_t st)

@@ -25,6 +25,12 @@ void launch_update(const SolveArgs &a, int from_acc, cudaStream_t st);
 void launch_project(const SolveArgs &a, int whole_image, cudaStream_t st);
 // Per-tile candidate lists from the tile counts; resets per-iteration counters.
 void launch_lists(const SolveArgs &a, cudaStream_t st);
+// Batch: the assignment of every tile of every image in one launch, and one
+// iteration's update, projection and candidate lists for every image.
+void launch_assign_batch(const BatchArgs &b, int storage, int total_tiles, size_t smem_bytes,
+                         cudaStream_t st);
+cudaError_t assign_batch_configure(int storage, size_t smem_bytes);
+void launch_batch_update(const BatchArgs &b, int total_clusters, int total_fill, cudaStream_t st);
 // Assignment (Algorithm 1 inner loops, Eq. 1-3).  tmap is used when staged.
 void launch_assign(const SolveArgs &a, int storage, bool staged, const CUtensorMap &tmap,
                    size_t smem_bytes, cudaStream_t st);

@@ -66,6 +66,8 @@ EXPORTS = (
     "scalp_iterate", "scalp_labels", "scalp_get_info", "scalp_get_state", "scalp_set_state",
     "scalp_debug_paths", "scalp_profile", "scalp_count_samples", "scalp_sync",
     "scalp_last_error", "scalp_destroy", "scalp_label_means_static",
+    "scalp_batch_workspace_bytes", "scalp_batch_init", "scalp_batch_reload", "scalp_batch_iterate",
+    "scalp_batch_labels", "scalp_batch_get_state", "scalp_batch_get_info", "scalp_batch_destroy",
 )
 
 _lib = None
@@ -105,6 +107,15 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "scalp_last_error": (ctypes.c_char_p, [P]),
             "scalp_destroy": (None, [P]),
             "scalp_label_means_static": (ctypes.c_int, [P, I64, P, I32, I32, I32, P, P]),
+            "scalp_batch_workspace_bytes": (ctypes.c_size_t, [I32, P, P, P, ctypes.POINTER(scalp_params)]),
+            "scalp_batch_init": (ctypes.c_int, [ctypes.POINTER(P), I32, P, P, P, P,
+                                                ctypes.POINTER(scalp_params)]),
+            "scalp_batch_reload": (ctypes.c_int, [P, P, P]),
+            "scalp_batch_iterate": (ctypes.c_int, [P, I32]),
+            "scalp_batch_labels": (ctypes.c_int, [P, P, I32, I32, P]),
+            "scalp_batch_get_state": (ctypes.c_int, [P, I32, ctypes.POINTER(scalp_state)]),
+            "scalp_batch_get_info": (ctypes.c_int, [P, I32, ctypes.POINTER(scalp_info)]),
+            "scalp_batch_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -325,6 +336,154 @@ class Segmenter:
         if getattr(self, "ctx", None):
             scalp_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --- batches -----------------------------------------------------------------
+def scalp_batch_workspace_bytes(H, W, K, params: scalp_params) -> int:
+    H = np.ascontiguousarray(H, np.int32); W = np.ascontiguousarray(W, np.int32)
+    K = np.ascontiguousarray(K, np.int32)
+    return int(load().scalp_batch_workspace_bytes(len(H), H.ctypes.data, W.ctypes.data,
+                                                  K.ctypes.data, ctypes.byref(params)))
+
+
+def scalp_batch_init(images, contours, K, m, params: scalp_params) -> ctypes.c_void_p:
+    n = len(images)
+    imgs = (scalp_image * n)(*images)
+    cons = (scalp_contour * n)(*contours) if contours is not None else None
+    K = np.ascontiguousarray(K, np.int32)
+    m = np.ascontiguousarray(m, np.float32)
+    b = ctypes.c_void_p()
+    _check(load().scalp_batch_init(ctypes.byref(b), n, ctypes.cast(imgs, ctypes.c_void_p),
+                                   ctypes.cast(cons, ctypes.c_void_p) if cons is not None else None,
+                                   K.ctypes.data, m.ctypes.data, ctypes.byref(params)))
+    return b
+
+
+def scalp_batch_reload(batch, images, contours):
+    n = len(images)
+    imgs = (scalp_image * n)(*images)
+    cons = (scalp_contour * n)(*contours) if contours is not None else None
+    _check(load().scalp_batch_reload(batch, ctypes.cast(imgs, ctypes.c_void_p),
+                                     ctypes.cast(cons, ctypes.c_void_p) if cons is not None else None))
+
+
+def scalp_batch_iterate(batch, n: int):
+    _check(load().scalp_batch_iterate(batch, int(n)))
+
+
+def scalp_batch_labels(batch, out_ptrs, out_on_device: bool, enforce: bool):
+    n = len(out_ptrs)
+    ptrs = (ctypes.c_void_p * n)(*out_ptrs)
+    nl = np.zeros(n, np.int32)
+    _check(load().scalp_batch_labels(batch, ctypes.cast(ptrs, ctypes.c_void_p), int(out_on_device),
+                                     int(enforce), nl.ctypes.data))
+    return nl
+
+
+def scalp_batch_get_state(batch, index: int, state: scalp_state):
+    _check(load().scalp_batch_get_state(batch, int(index), ctypes.byref(state)))
+
+
+def scalp_batch_get_info(batch, index: int) -> scalp_info:
+    info = scalp_info()
+    _check(load().scalp_batch_get_info(batch, int(index), ctypes.byref(info)))
+    return info
+
+
+def scalp_batch_destroy(batch):
+    load().scalp_batch_destroy(batch)
+
+
+class Batch:
+    """Many SCALP solves of uneven size on the current CUDA device.
+
+    rgbs: list of (H_i, W_i, 3) uint8 CUDA tensors; contours: list of (H_i, W_i)
+    float32 CUDA tensors or None; Ks: list of K_i.
+    """
+
+    def __init__(self, rgbs, contours, Ks, m: float = 10.0, lam: float = 0.5, sigma: float = 0.25,
+                 gamma: float = -1.0, storage: str = "f32", use_graph: bool = True,
+                 global_walk: bool = False, stream=None):
+        import torch
+
+        self._torch = torch
+        self.count = len(rgbs)
+        self.shapes = [(int(r.shape[0]), int(r.shape[1])) for r in rgbs]
+        p = scalp_default_params()
+        p.lambda_, p.sigma, p.gamma = lam, sigma, gamma
+        p.storage = STORAGE[storage]
+        p.use_graph = int(use_graph)
+        p.global_walk = int(global_walk)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        p.stream = self.stream.cuda_stream
+        H = [s[0] for s in self.shapes]
+        W = [s[1] for s in self.shapes]
+        nbytes = scalp_batch_workspace_bytes(H, W, Ks, p)
+        if nbytes == 0:
+            raise ScalpError(SCALP_E_ARG, "invalid batch sizes")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        p.workspace = self.workspace.data_ptr()
+        p.workspace_bytes = nbytes
+        self.params = p
+        imgs, cons, self._keep = self._marshal(rgbs, contours)
+        self.batch = scalp_batch_init(imgs, cons, Ks, [m] * self.count, p)
+        self.infos = [scalp_batch_get_info(self.batch, i) for i in range(self.count)]
+
+    def _marshal(self, rgbs, contours):
+        torch = self._torch
+        keep, imgs, cons = [], [], []
+        for i, r in enumerate(rgbs):
+            r = r.contiguous()
+            keep.append(r)
+            imgs.append(scalp_image(r.shape[0], r.shape[1], r.data_ptr(), 0, 1))
+            c = None if contours is None else contours[i]
+            if c is None:
+                cons.append(scalp_contour(None, 0))
+            else:
+                c = c.to(device=r.device, dtype=torch.float32).contiguous()
+                keep.append(c)
+                cons.append(scalp_contour(c.data_ptr(), 0))
+        return imgs, cons, keep
+
+    def reload(self, rgbs, contours):
+        imgs, cons, self._keep = self._marshal(rgbs, contours)
+        scalp_batch_reload(self.batch, imgs, cons)
+
+    def iterate(self, n: int = 1):
+        scalp_batch_iterate(self.batch, n)
+
+    def labels(self, enforce: bool = True, outs=None):
+        """Labels of every image: into `outs` (CUDA int32 tensors) if given,
+        else new numpy arrays.  Returns (labels list, n_labels array)."""
+        torch = self._torch
+        if outs is None:
+            outs = [np.empty(s, dtype=np.int32) for s in self.shapes]
+        on_dev = isinstance(outs[0], torch.Tensor)
+        ptrs = [o.data_ptr() if on_dev else o.ctypes.data for o in outs]
+        n = scalp_batch_labels(self.batch, ptrs, on_dev, enforce)
+        return outs, n
+
+    def get_state(self, index: int):
+        info = self.infos[index]
+        K = info.Keff
+        st = dict(labels=np.empty((info.H, info.W), np.int32), n=np.empty(K, np.int64),
+                  sx=np.empty(K, np.int64), sy=np.empty(K, np.int64),
+                  color=np.empty((K, 3), np.float64), endpoint=np.empty((K, 2), np.int32))
+        scalp_batch_get_state(self.batch, index, scalp_state(*(st[k].ctypes.data for k in
+                                                               ("labels", "n", "sx", "sy", "color",
+                                                                "endpoint"))))
+        return st
+
+    def close(self):
+        if getattr(self, "batch", None):
+            scalp_batch_destroy(self.batch)
+            self.batch = None
 
     def __del__(self):
         try:
