@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--storage", choices=["f32", "f16"], default="f32")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the FP16-storage and batched forms")
     return ap.parse_args()
 
 
@@ -226,6 +228,95 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def measure_batch(args, storage: str, flush):
+    """The batched form: 64 images of uneven size and K (H~U{240..1080},
+    W~U{320..1920}, grid step S~U[12,30]) solved together, 10 iterations each;
+    one step = reload + 10 batched iterations + connectivity for all images."""
+    import torch
+
+    from paper_1903_07149_gb300 import scalp, synth
+
+    ws = synth.batch_configs()
+    rgbs, cons = synth.batch_images(ws)
+    d_rgb = [torch.from_numpy(r).cuda() for r in rgbs]
+    d_con = [torch.from_numpy(c).cuda() for c in cons]
+    outs = [torch.empty((w.H, w.W), dtype=torch.int32, device="cuda") for w in ws]
+    stream = torch.cuda.Stream()
+    pix = sum(w.H * w.W for w in ws)
+    iters = ws[0].iters
+    with torch.cuda.stream(stream):
+        b = scalp.Batch(d_rgb, d_con, [w.K for w in ws], storage=storage, stream=stream)
+
+        def step():
+            b.reload(d_rgb, d_con)
+            b.iterate(iters)
+            b.labels(enforce=True, outs=outs)
+
+        for _ in range(args.warmup):
+            step()
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            ev0[i].record(stream)
+            step()
+            ev1[i].record(stream)
+        torch.cuda.synchronize()
+        # the iteration loop alone (the batched kernels), for the split
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        b.iterate(iters)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        b.close()
+    total_ms = sum(a.elapsed_time(c) for a, c in zip(ev0, ev1))
+    return {"value": pix * iters * args.steps / (total_ms / 1e3) / 1e6, "unit": UNIT,
+            "ms_per_step": total_ms / args.steps, "images": len(ws), "mpix": pix / 1e6,
+            "iters": iters, "storage": storage,
+            "iterations_only_mpix_iter_s": pix * iters / (t0.elapsed_time(t1) / 1e3) / 1e6,
+            "workload": "64 images, H~U{240..1080}, W~U{320..1920}, S~U[12,30], K=round(HW/S^2)"}
+
+
+def measure_single_form(args, w, rgb, con, storage: str, flush):
+    """Plain single-image solve with the given plane storage (FP16 form)."""
+    import torch
+
+    from paper_1903_07149_gb300 import scalp
+
+    stream = torch.cuda.Stream()
+    d_rgb = torch.from_numpy(rgb).cuda()
+    d_con = torch.from_numpy(con).cuda()
+    out = torch.empty((w.H, w.W), dtype=torch.int32, device="cuda")
+    with torch.cuda.stream(stream):
+        seg = scalp.Segmenter(d_rgb, d_con, w.K, storage=storage, stream=stream)
+
+        def step():
+            seg.reload(d_rgb, d_con)
+            seg.iterate(w.iters)
+            seg.labels(enforce=True, out=out)
+
+        for _ in range(args.warmup):
+            step()
+        seg.profile(1)
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            ev0[i].record(stream)
+            step()
+            ev1[i].record(stream)
+        torch.cuda.synchronize()
+        ms_assign, n_assign = seg.profile(0)
+        seg.close()
+    total_ms = sum(a.elapsed_time(c) for a, c in zip(ev0, ev1))
+    return {"value": w.H * w.W * w.iters * args.steps / (total_ms / 1e3) / 1e6, "unit": UNIT,
+            "ms_per_step": total_ms / args.steps, "storage": storage, "workload": w.name,
+            "assign_ms_per_launch": ms_assign / max(n_assign, 1)}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -355,6 +446,13 @@ def run_ours(args):
         "gpu_launches": args.steps * (RELOAD_LAUNCHES + ITER_LAUNCHES * iters + ccl_launches(N)),
         "roofline": roofline,
     }
+    if not args.no_forms:
+        other = "f16" if args.storage == "f32" else "f32"
+        line["forms"] = {
+            f"single_{other}": measure_single_form(args, w, rgb, con, other, flush),
+            "batched_f16": measure_batch(args, "f16", flush),
+            "batched_f32": measure_batch(args, "f32", flush),
+        }
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline_oracle(w, rgb, con)
     print(json.dumps(line), flush=True)

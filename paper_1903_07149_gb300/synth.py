@@ -21,6 +21,7 @@ __all__ = [
     "voronoi_image",
     "single_image_config",
     "batch_configs",
+    "batch_images",
     "serving_arrivals",
     "WORKLOADS",
 ]
@@ -79,7 +80,7 @@ def _voronoi_cells(H: int, W: int, seeds_xy: np.ndarray) -> np.ndarray:
     tree = cKDTree(seeds_xy)
     ys, xs = np.mgrid[0:H, 0:W]
     pts = np.stack([xs.ravel(), ys.ravel()], axis=1).astype(np.float64)
-    _, idx = tree.query(pts, k=1)
+    _, idx = tree.query(pts, k=1, workers=-1)
     return idx.reshape(H, W).astype(np.int32)
 
 
@@ -159,6 +160,17 @@ def batch_configs(n_images: int = 64, seed: int = 3000):
         n_cells = max(2, int(round(300 * H * W / 2_073_600)))
         out.append(Workload(f"batch{i}_{H}x{W}_k{K}", H, W, K, n_cells, True, 6.0, seed + i))
     return out
+
+
+def batch_images(workloads):
+    """(rgb list, contour list) for a list of workloads (e.g. batch_configs())."""
+    rgbs, cons = [], []
+    for w in workloads:
+        rgb, con, _ = voronoi_image(w.H, w.W, w.n_cells, gradient=w.gradient,
+                                    noise_sigma=w.noise_sigma, seed=w.seed)
+        rgbs.append(rgb)
+        cons.append(con)
+    return rgbs, cons
 
 
 def serving_arrivals(n_requests: int = 2000, rate_hz: float = 500.0, seed: int = 4000):
