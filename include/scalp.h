@@ -205,6 +205,37 @@ int scalp_batch_get_state(scalp_batch *b, int32_t index, const scalp_state *stat
 int scalp_batch_get_info(const scalp_batch *b, int32_t index, scalp_info *info);
 void scalp_batch_destroy(scalp_batch *b);
 
+/* ---- Serving: continuous batching of solves in flight ------------------------
+ *
+ * Not part of the paper.  A server owns a caller-allocated device memory pool
+ * (pool_bytes, 256-byte aligned; the first scalp_server_reserve_bytes(max_slots)
+ * bytes are its own).  scalp_server_submit() admits a request when its solver
+ * state (scalp_workspace_bytes of the image) fits in the pool and fewer than
+ * max_slots requests are in flight, and returns SCALP_E_NOMEM otherwise (nothing
+ * done; retry after a step has freed memory).  Each scalp_server_step() runs one
+ * iteration of Algorithm 1 for every admitted request that still has
+ * iterations to do, all sizes together in one launch per kernel; requests that
+ * finish are retired: connectivity enforcement (if asked) and the copy of their
+ * labels to the caller's host buffer are enqueued.  scalp_server_poll() reports
+ * whether a request's labels have arrived (and then releases its memory).  The
+ * labels equal those of scalp_init + scalp_iterate + scalp_labels on the same
+ * image.  labels_out should be pinned host memory: with pageable memory the copy
+ * synchronises the stream.  One server is driven by one host thread. */
+typedef struct scalp_server scalp_server;
+
+size_t scalp_server_reserve_bytes(int32_t max_slots);
+int scalp_server_create(scalp_server **out, void *pool, size_t pool_bytes, int32_t max_slots,
+                        const scalp_params *params);
+/* image/contour/K/m as scalp_init; iters >= 0; labels_out: H*W int32 host buffer
+ * the caller keeps until poll reports done; *id receives the request id. */
+int scalp_server_submit(scalp_server *s, const scalp_image *image, const scalp_contour *contour,
+                        int32_t K, float m, int32_t iters, int32_t enforce, int32_t *labels_out,
+                        uint64_t *id);
+int scalp_server_step(scalp_server *s, int32_t *n_running);
+int scalp_server_poll(scalp_server *s, uint64_t id, int32_t *done, int32_t *n_labels);
+int scalp_server_stats(const scalp_server *s, int32_t *in_flight, size_t *pool_free_bytes);
+void scalp_server_destroy(scalp_server *s);
+
 /* ---- An entry point that allocates nothing (no counterpart in the paper) ----
  *
  * For callers that cannot allocate device memory: code running while another

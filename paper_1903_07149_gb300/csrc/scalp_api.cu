@@ -735,6 +735,53 @@ void scalp_destroy(scalp_ctx *c)
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
+// Accessors for the serving loop (scalp_server.cu), which keeps one context
+// per request in flight.
+// ---------------------------------------------------------------------------
+namespace scalp {
+
+SolveArgs scalp_ctx_args(const scalp_ctx *c) { return c->a; }
+CUtensorMap scalp_ctx_tmap(const scalp_ctx *c) { return c->tmap; }
+size_t scalp_ctx_smem(const scalp_ctx *c) { return c->smem; }
+void scalp_ctx_count_iteration(scalp_ctx *c) { c->iterations += 1; }
+
+// Enqueues the connectivity enforcement (if enforce) and the copy of the
+// labels to host memory `out`; no synchronisation.
+int scalp_ctx_enqueue_labels(scalp_ctx *c, int32_t *out, int enforce)
+{
+    const size_t bytes = sizeof(int) * (size_t)c->N;
+    const int *src = c->a.labels;
+    if (enforce) {
+        int *d_nlab = reinterpret_cast<int *>(c->ws + c->L.nlab);
+        launch_ccl(c->a.labels, c->H, c->W, c->K, c->ccl.link, c->ccl, d_nlab, c->a.ctr, c->st);
+        src = c->ccl.link;
+    }
+    int rc = launch_check(c, "connectivity kernels");
+    if (rc) return rc;
+    return cuda_check(c, cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToHost, c->st), "copy labels");
+}
+
+// After the enqueued work has completed: the label count and device status.
+int scalp_ctx_finish_labels(scalp_ctx *c, int enforce, int32_t *n_labels)
+{
+    int nlab = c->Keff;
+    if (enforce) {
+        int rc = cuda_check(c, cudaMemcpy(&nlab, c->ws + c->L.nlab, sizeof(int), cudaMemcpyDeviceToHost),
+                            "copy label count");
+        if (rc) return rc;
+    }
+    DevCounters h;
+    int rc = cuda_check(c, cudaMemcpy(&h, c->a.ctr, sizeof h, cudaMemcpyDeviceToHost), "read counters");
+    if (rc) return rc;
+    if (h.timeout) return fail(c, SCALP_E_TIMEOUT, "a bounded device-side wait gave up");
+    if (h.error) return fail(c, SCALP_E_INTERNAL, "device-side check failed (code %d)", h.error);
+    *n_labels = nlab;
+    return SCALP_OK;
+}
+
+}  // namespace scalp
+
+// ---------------------------------------------------------------------------
 // Batches: many images of uneven size and K solved together.  Each image is an
 // ordinary context carved from the batch workspace; the iteration kernels of
 // all images run as one launch each (tiles, clusters and list slots of all

@@ -3,6 +3,8 @@
 
 #include "scalp_internal.cuh"
 
+typedef struct scalp_ctx scalp_ctx;
+
 namespace scalp {
 
 // Sets the text scalp_last_error(NULL) returns on this thread.
@@ -49,5 +51,13 @@ struct CclBuffers {
 long long ccl_scan_tmp_len(long long N);
 void launch_ccl(const int *labels, int H, int W, int K, int *out, const CclBuffers &b,
                 int *d_nlab, DevCounters *ctr, cudaStream_t st);
+
+// Per-context accessors used by the serving loop.
+SolveArgs scalp_ctx_args(const scalp_ctx *c);
+CUtensorMap scalp_ctx_tmap(const scalp_ctx *c);
+size_t scalp_ctx_smem(const scalp_ctx *c);
+void scalp_ctx_count_iteration(scalp_ctx *c);
+int scalp_ctx_enqueue_labels(scalp_ctx *c, int32_t *out, int enforce);
+int scalp_ctx_finish_labels(scalp_ctx *c, int enforce, int32_t *n_labels);
 
 }  // namespace scalp

@@ -1,0 +1,338 @@
+// scalp_server.cu -- continuous batching of many SCALP solves (serving).
+//
+// A server owns a caller-allocated device memory pool.  A request is admitted
+// when its workspace fits in the pool and a slot is free; its state then stays
+// resident until its labels have been delivered.  Each scalp_server_step()
+// runs one iteration of Algorithm 1 for every solve in flight, whatever its
+// size, as one launch per kernel (the batched kernels), so requests admitted
+// while others are running share the device with them.  A solve that has done
+// its iterations is retired: connectivity enforcement and the copy of its
+// labels to the caller's buffer are enqueued, followed by an event that
+// scalp_server_poll() checks.
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <map>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/scalp.h"
+#include "scalp_launch.h"
+
+using namespace scalp;
+
+namespace {
+
+constexpr size_t SALIGN = 256;
+
+size_t salign(size_t x) { return (x + SALIGN - 1) & ~(SALIGN - 1); }
+
+struct Solve {
+    uint64_t id = 0;
+    scalp_ctx *ctx = nullptr;
+    size_t off = 0, bytes = 0;  // its part of the pool
+    int iters_left = 0;
+    int enforce = 1;
+    int32_t *labels_out = nullptr;
+    cudaEvent_t done = nullptr;
+    bool retired = false;
+};
+
+int server_fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    scalp::set_last_error(buf);
+    return code;
+}
+
+size_t head_bytes(int slots)
+{
+    return salign((size_t)slots * sizeof(CUtensorMap)) + salign((size_t)slots * sizeof(SolveArgs)) +
+           3 * salign((size_t)(slots + 1) * sizeof(int));
+}
+
+}  // namespace
+
+struct scalp_server {
+    cudaStream_t st = nullptr;
+    unsigned char *pool = nullptr;
+    size_t pool_bytes = 0;
+    scalp_params params{};
+    int max_slots = 0;
+    std::map<size_t, size_t> free_list;  // offset -> size, coalesced
+    std::vector<Solve *> active;          // admitted, iterating or retired-but-not-polled
+    std::map<uint64_t, Solve *> by_id;
+    uint64_t next_id = 1;
+    bool args_dirty = true;
+    BatchArgs bargs{};
+    int total_tiles = 0, total_clusters = 0, total_fill = 0;
+    size_t smem = 0;
+    std::vector<cudaEvent_t> spare_events;
+};
+
+namespace {
+
+bool pool_alloc(scalp_server *s, size_t bytes, size_t &off)
+{
+    bytes = salign(bytes);
+    for (auto it = s->free_list.begin(); it != s->free_list.end(); ++it) {
+        if (it->second >= bytes) {
+            off = it->first;
+            const size_t rest = it->second - bytes;
+            s->free_list.erase(it);
+            if (rest) s->free_list[off + bytes] = rest;
+            return true;
+        }
+    }
+    return false;
+}
+
+void pool_free(scalp_server *s, size_t off, size_t bytes)
+{
+    bytes = salign(bytes);
+    auto it = s->free_list.emplace(off, bytes).first;
+    auto next = std::next(it);
+    if (next != s->free_list.end() && it->first + it->second == next->first) {
+        it->second += next->second;
+        s->free_list.erase(next);
+    }
+    if (it != s->free_list.begin()) {
+        auto prev = std::prev(it);
+        if (prev->first + prev->second == it->first) {
+            prev->second += it->second;
+            s->free_list.erase(it);
+        }
+    }
+}
+
+// Uploads the argument blocks of the solves still iterating.
+int rebuild_args(scalp_server *s, std::vector<Solve *> &running)
+{
+    const int n = (int)running.size();
+    std::vector<SolveArgs> args(n);
+    std::vector<CUtensorMap> tmaps(n);
+    std::vector<int> tile(n + 1, 0), clus(n + 1, 0), fill(n + 1, 0);
+    size_t smem = 0;
+    for (int i = 0; i < n; ++i) {
+        const scalp_ctx *c = running[i]->ctx;
+        args[i] = scalp_ctx_args(c);
+        tmaps[i] = scalp_ctx_tmap(c);
+        tile[i + 1] = tile[i] + args[i].n_tx * args[i].n_ty;
+        clus[i + 1] = clus[i] + args[i].Keff;
+        fill[i + 1] = fill[i] + args[i].Keff * args[i].tpw_x * args[i].tpw_y;
+        smem = std::max(smem, scalp_ctx_smem(c));
+    }
+    unsigned char *h = s->pool;
+    const size_t o_tmaps = 0;
+    const size_t o_args = o_tmaps + salign((size_t)s->max_slots * sizeof(CUtensorMap));
+    const size_t o_tile = o_args + salign((size_t)s->max_slots * sizeof(SolveArgs));
+    const size_t o_clus = o_tile + salign((size_t)(s->max_slots + 1) * sizeof(int));
+    const size_t o_fill = o_clus + salign((size_t)(s->max_slots + 1) * sizeof(int));
+    cudaError_t e = cudaSuccess;
+    if (n > 0) {
+        e = cudaMemcpyAsync(h + o_tmaps, tmaps.data(), n * sizeof(CUtensorMap), cudaMemcpyHostToDevice, s->st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(h + o_args, args.data(), n * sizeof(SolveArgs), cudaMemcpyHostToDevice, s->st);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h + o_tile, tile.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h + o_clus, clus.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(h + o_fill, fill.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, s->st);
+    // the host vectors are released on return: wait for the copies
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    if (e != cudaSuccess) return server_fail(SCALP_E_CUDA, "server arguments: %s", cudaGetErrorString(e));
+    s->bargs.args = reinterpret_cast<const SolveArgs *>(h + o_args);
+    s->bargs.tmaps = reinterpret_cast<const CUtensorMap *>(h + o_tmaps);
+    s->bargs.tile_base = reinterpret_cast<const int *>(h + o_tile);
+    s->bargs.clus_base = reinterpret_cast<const int *>(h + o_clus);
+    s->bargs.fill_base = reinterpret_cast<const int *>(h + o_fill);
+    s->bargs.count = n;
+    s->total_tiles = tile[n];
+    s->total_clusters = clus[n];
+    s->total_fill = fill[n];
+    s->smem = smem;
+    s->args_dirty = false;
+    return SCALP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t scalp_server_reserve_bytes(int32_t max_slots)
+{
+    return max_slots < 1 ? 0 : head_bytes(max_slots);
+}
+
+int scalp_server_create(scalp_server **out, void *pool, size_t pool_bytes, int32_t max_slots,
+                        const scalp_params *params)
+{
+    if (!out) return server_fail(SCALP_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (!params || !pool || max_slots < 1) return server_fail(SCALP_E_ARG, "need params, pool, max_slots >= 1");
+    if (reinterpret_cast<uintptr_t>(pool) % SALIGN) return server_fail(SCALP_E_ARG, "pool must be 256-byte aligned");
+    const size_t head = head_bytes(max_slots);
+    if (pool_bytes <= head) return server_fail(SCALP_E_NOMEM, "pool smaller than the %zu-byte reserve", head);
+    if (params->storage != 0 && params->storage != 1) return server_fail(SCALP_E_ARG, "bad storage");
+    scalp_server *s = new (std::nothrow) scalp_server();
+    if (!s) return server_fail(SCALP_E_NOMEM, "host allocation failed");
+    s->st = reinterpret_cast<cudaStream_t>(params->stream);
+    s->pool = reinterpret_cast<unsigned char *>(pool);
+    s->pool_bytes = pool_bytes;
+    s->params = *params;
+    s->params.use_graph = 0;
+    s->max_slots = max_slots;
+    s->free_list[head] = (pool_bytes - head) & ~(SALIGN - 1);
+    // the batched assignment may need up to the full shared memory of an SM
+    cudaError_t e = assign_batch_configure(params->storage, 227 * 1024);
+    if (e != cudaSuccess) {
+        delete s;
+        return server_fail(SCALP_E_CUDA, "configure: %s", cudaGetErrorString(e));
+    }
+    *out = s;
+    return SCALP_OK;
+}
+
+int scalp_server_submit(scalp_server *s, const scalp_image *image, const scalp_contour *contour,
+                        int32_t K, float m, int32_t iters, int32_t enforce, int32_t *labels_out,
+                        uint64_t *id)
+{
+    if (!s || !image || !labels_out || !id) return server_fail(SCALP_E_ARG, "null argument");
+    if (iters < 0) return server_fail(SCALP_E_ARG, "iters must be >= 0");
+    if ((int)s->active.size() >= s->max_slots) return server_fail(SCALP_E_NOMEM, "no free slot");
+    const size_t bytes = scalp_workspace_bytes(image->H, image->W, K, &s->params);
+    if (bytes == 0) return server_fail(SCALP_E_ARG, "invalid image size or K");
+    size_t off;
+    if (!pool_alloc(s, bytes, off)) return server_fail(SCALP_E_NOMEM, "pool full");
+    Solve *v = new (std::nothrow) Solve();
+    if (!v) {
+        pool_free(s, off, bytes);
+        return server_fail(SCALP_E_NOMEM, "host allocation failed");
+    }
+    scalp_params p = s->params;
+    p.workspace = s->pool + off;
+    p.workspace_bytes = bytes;
+    int rc = scalp_init(&v->ctx, image, contour, K, m, &p);
+    if (rc != SCALP_OK) {
+        pool_free(s, off, bytes);
+        delete v;
+        return rc;
+    }
+    if (s->spare_events.empty()) {
+        cudaEvent_t e;
+        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            scalp_destroy(v->ctx);
+            pool_free(s, off, bytes);
+            delete v;
+            return server_fail(SCALP_E_CUDA, "event creation failed");
+        }
+        s->spare_events.push_back(e);
+    }
+    v->done = s->spare_events.back();
+    s->spare_events.pop_back();
+    v->id = s->next_id++;
+    v->off = off;
+    v->bytes = bytes;
+    v->iters_left = iters;
+    v->enforce = enforce;
+    v->labels_out = labels_out;
+    s->active.push_back(v);
+    s->by_id[v->id] = v;
+    s->args_dirty = true;
+    *id = v->id;
+    return SCALP_OK;
+}
+
+int scalp_server_step(scalp_server *s, int32_t *n_running)
+{
+    if (!s) return server_fail(SCALP_E_ARG, "server is NULL");
+    std::vector<Solve *> running;
+    for (Solve *v : s->active)
+        if (!v->retired && v->iters_left > 0) running.push_back(v);
+    if (!running.empty()) {
+        if (s->args_dirty || s->bargs.count != (int)running.size()) {
+            const int rc = rebuild_args(s, running);
+            if (rc) return rc;
+        }
+        launch_assign_batch(s->bargs, s->params.storage, s->total_tiles, s->smem, s->st);
+        launch_batch_update(s->bargs, s->total_clusters, s->total_fill, s->st);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return server_fail(SCALP_E_CUDA, "server step: %s", cudaGetErrorString(e));
+        for (Solve *v : running) {
+            --v->iters_left;
+            scalp_ctx_count_iteration(v->ctx);
+        }
+    }
+    // retire the solves whose iterations are done
+    for (Solve *v : s->active) {
+        if (v->retired || v->iters_left > 0) continue;
+        const int rc = scalp_ctx_enqueue_labels(v->ctx, v->labels_out, v->enforce);
+        if (rc) return rc;
+        const cudaError_t e = cudaEventRecord(v->done, s->st);
+        if (e != cudaSuccess) return server_fail(SCALP_E_CUDA, "record: %s", cudaGetErrorString(e));
+        v->retired = true;
+        s->args_dirty = true;
+    }
+    if (n_running) *n_running = (int32_t)running.size();
+    return SCALP_OK;
+}
+
+int scalp_server_poll(scalp_server *s, uint64_t id, int32_t *done, int32_t *n_labels)
+{
+    if (!s || !done) return server_fail(SCALP_E_ARG, "null argument");
+    *done = 0;
+    auto it = s->by_id.find(id);
+    if (it == s->by_id.end()) return server_fail(SCALP_E_ARG, "unknown or already delivered request");
+    Solve *v = it->second;
+    if (!v->retired) return SCALP_OK;
+    const cudaError_t q = cudaEventQuery(v->done);
+    if (q == cudaErrorNotReady) return SCALP_OK;
+    if (q != cudaSuccess) return server_fail(SCALP_E_CUDA, "request %llu: %s", (unsigned long long)id, cudaGetErrorString(q));
+    int32_t nl = 0;
+    int rc = scalp_ctx_finish_labels(v->ctx, v->enforce, &nl);
+    if (rc) return rc;
+    *done = 1;
+    if (n_labels) *n_labels = nl;
+    // release: the state leaves the pool
+    scalp_destroy(v->ctx);
+    pool_free(s, v->off, v->bytes);
+    s->spare_events.push_back(v->done);
+    s->active.erase(std::find(s->active.begin(), s->active.end(), v));
+    s->by_id.erase(it);
+    delete v;
+    return SCALP_OK;
+}
+
+int scalp_server_stats(const scalp_server *s, int32_t *in_flight, size_t *pool_free_bytes)
+{
+    if (!s) return server_fail(SCALP_E_ARG, "server is NULL");
+    if (in_flight) *in_flight = (int32_t)s->active.size();
+    if (pool_free_bytes) {
+        size_t f = 0;
+        for (const auto &kv : s->free_list) f += kv.second;
+        *pool_free_bytes = f;
+    }
+    return SCALP_OK;
+}
+
+void scalp_server_destroy(scalp_server *s)
+{
+    if (!s) return;
+    cudaStreamSynchronize(s->st);
+    for (Solve *v : s->active) {
+        scalp_destroy(v->ctx);
+        cudaEventDestroy(v->done);
+        delete v;
+    }
+    for (cudaEvent_t e : s->spare_events) cudaEventDestroy(e);
+    delete s;
+}
+
+}  // extern "C"

@@ -68,6 +68,8 @@ EXPORTS = (
     "scalp_last_error", "scalp_destroy", "scalp_label_means_static",
     "scalp_batch_workspace_bytes", "scalp_batch_init", "scalp_batch_reload", "scalp_batch_iterate",
     "scalp_batch_labels", "scalp_batch_get_state", "scalp_batch_get_info", "scalp_batch_destroy",
+    "scalp_server_reserve_bytes", "scalp_server_create", "scalp_server_submit", "scalp_server_step",
+    "scalp_server_poll", "scalp_server_stats", "scalp_server_destroy",
 )
 
 _lib = None
@@ -116,6 +118,17 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "scalp_batch_get_state": (ctypes.c_int, [P, I32, ctypes.POINTER(scalp_state)]),
             "scalp_batch_get_info": (ctypes.c_int, [P, I32, ctypes.POINTER(scalp_info)]),
             "scalp_batch_destroy": (None, [P]),
+            "scalp_server_reserve_bytes": (ctypes.c_size_t, [I32]),
+            "scalp_server_create": (ctypes.c_int, [ctypes.POINTER(P), P, ctypes.c_size_t, I32,
+                                                   ctypes.POINTER(scalp_params)]),
+            "scalp_server_submit": (ctypes.c_int, [P, ctypes.POINTER(scalp_image),
+                                                   ctypes.POINTER(scalp_contour), I32, ctypes.c_float,
+                                                   I32, I32, P, ctypes.POINTER(ctypes.c_uint64)]),
+            "scalp_server_step": (ctypes.c_int, [P, ctypes.POINTER(I32)]),
+            "scalp_server_poll": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.POINTER(I32),
+                                                 ctypes.POINTER(I32)]),
+            "scalp_server_stats": (ctypes.c_int, [P, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_size_t)]),
+            "scalp_server_destroy": (None, [P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -484,6 +497,117 @@ class Batch:
         if getattr(self, "batch", None):
             scalp_batch_destroy(self.batch)
             self.batch = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# --- serving -------------------------------------------------------------------
+def scalp_server_reserve_bytes(max_slots: int) -> int:
+    return int(load().scalp_server_reserve_bytes(int(max_slots)))
+
+
+def scalp_server_create(pool_ptr: int, pool_bytes: int, max_slots: int, params: scalp_params):
+    s = ctypes.c_void_p()
+    _check(load().scalp_server_create(ctypes.byref(s), ctypes.c_void_p(pool_ptr), int(pool_bytes),
+                                      int(max_slots), ctypes.byref(params)))
+    return s
+
+
+def scalp_server_submit(server, image: scalp_image, contour: scalp_contour, K: int, m: float,
+                        iters: int, enforce: bool, labels_out_ptr: int):
+    """Request id, or None when the request does not fit now (SCALP_E_NOMEM)."""
+    rid = ctypes.c_uint64()
+    rc = load().scalp_server_submit(server, ctypes.byref(image), ctypes.byref(contour), int(K),
+                                    float(m), int(iters), int(enforce),
+                                    ctypes.c_void_p(labels_out_ptr), ctypes.byref(rid))
+    if rc == SCALP_E_NOMEM:
+        return None
+    _check(rc)
+    return rid.value
+
+
+def scalp_server_step(server) -> int:
+    n = ctypes.c_int32()
+    _check(load().scalp_server_step(server, ctypes.byref(n)))
+    return n.value
+
+
+def scalp_server_poll(server, rid: int):
+    done = ctypes.c_int32()
+    nl = ctypes.c_int32()
+    _check(load().scalp_server_poll(server, ctypes.c_uint64(rid), ctypes.byref(done), ctypes.byref(nl)))
+    return bool(done.value), nl.value
+
+
+def scalp_server_stats(server):
+    n = ctypes.c_int32()
+    f = ctypes.c_size_t()
+    _check(load().scalp_server_stats(server, ctypes.byref(n), ctypes.byref(f)))
+    return n.value, f.value
+
+
+def scalp_server_destroy(server):
+    load().scalp_server_destroy(server)
+
+
+class Server:
+    """Continuous batching of SCALP solves within a device memory budget."""
+
+    def __init__(self, budget_bytes: int, max_slots: int = 1024, storage: str = "f32", m: float = 10.0,
+                 iters: int = 10, enforce: bool = True, stream=None):
+        import torch
+
+        self._torch = torch
+        p = scalp_default_params()
+        p.storage = STORAGE[storage]
+        self.stream = stream if stream is not None else torch.cuda.Stream()
+        p.stream = self.stream.cuda_stream
+        self.params = p
+        self.pool = torch.empty(int(budget_bytes), dtype=torch.uint8, device="cuda")
+        self.server = scalp_server_create(self.pool.data_ptr(), int(budget_bytes), max_slots, p)
+        self.m, self.iters, self.enforce = m, iters, enforce
+        self._keep = {}
+
+    def submit(self, rgb, contour, K: int):
+        """rgb (H, W, 3) uint8 and contour (H, W) float32, CUDA tensors.  Returns
+        (id, pinned host labels tensor) or None when the request must wait."""
+        torch = self._torch
+        rgb = rgb.contiguous()
+        img = scalp_image(rgb.shape[0], rgb.shape[1], rgb.data_ptr(), 0, 1)
+        con = scalp_contour(None, 0)
+        keep = [rgb]
+        if contour is not None:
+            c = contour.contiguous()
+            keep.append(c)
+            con = scalp_contour(c.data_ptr(), 0)
+        out = torch.empty((rgb.shape[0], rgb.shape[1]), dtype=torch.int32).pin_memory()
+        rid = scalp_server_submit(self.server, img, con, K, self.m, self.iters, self.enforce,
+                                  out.data_ptr())
+        if rid is None:
+            return None
+        self._keep[rid] = (keep, out)
+        return rid, out
+
+    def step(self) -> int:
+        return scalp_server_step(self.server)
+
+    def poll(self, rid: int):
+        done, n = scalp_server_poll(self.server, rid)
+        if done:
+            self._keep.pop(rid, None)
+        return done, n
+
+    def stats(self):
+        return scalp_server_stats(self.server)
+
+    def close(self):
+        if getattr(self, "server", None):
+            scalp_server_destroy(self.server)
+            self.server = None
 
     def __del__(self):
         try:

@@ -1,0 +1,73 @@
+"""Serving: requests admitted into a memory-bounded server while others are
+in flight give exactly what each image gives alone."""
+import numpy as np
+import pytest
+
+from paper_1903_07149_gb300 import build as scalp_build
+from paper_1903_07149_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [(150, 230, 120), (97, 131, 40), (240, 320, 400), (33, 47, 1), (100, 140, 2),
+         (64, 96, 24), (181, 263, 300), (300, 420, 500), (120, 160, 90), (211, 97, 60)]
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+
+    assert torch.cuda.is_available()
+    scalp_build.build()
+    from paper_1903_07149_gb300 import scalp
+
+    scalp.load()
+    return scalp
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_serving_mix_equals_alone(S, storage):
+    import torch
+
+    imgs = []
+    for i, (H, W, K) in enumerate(SIZES):
+        rgb, con, _ = synth.small_image(H, W, seed=900 + i, n_cells=max(2, H * W // 3000))
+        imgs.append((torch.from_numpy(rgb).cuda(), torch.from_numpy(con).cuda(), K))
+    p = S.scalp_default_params()
+    p.storage = S.STORAGE[storage]
+    need = [S.scalp_workspace_bytes(H, W, K, p) for H, W, K in SIZES]
+    # room for about three requests at a time: later ones wait for memory
+    budget = S.scalp_server_reserve_bytes(8) + 3 * max(need) + (1 << 20)
+    stream = torch.cuda.Stream()
+    srv = S.Server(budget, max_slots=8, storage=storage, iters=6, stream=stream)
+    pending = list(range(len(SIZES)))
+    inflight, results, waited, steps = {}, {}, 0, 0
+    while pending or inflight:
+        # two new arrivals per step, while memory and slots allow
+        for _ in range(2):
+            if not pending:
+                break
+            i = pending[0]
+            r = srv.submit(*imgs[i])
+            if r is None:
+                waited += 1
+                break
+            pending.pop(0)
+            inflight[r[0]] = (i, r[1])
+        srv.step()
+        steps += 1
+        for rid in list(inflight):
+            done, n = srv.poll(rid)
+            if done:
+                i, out = inflight.pop(rid)
+                results[i] = (out.numpy().copy(), n)
+        assert steps < 500
+    assert waited > 0  # admission was bounded by memory
+    with torch.cuda.stream(stream):
+        for i, (rgb, con, K) in enumerate(imgs):
+            s = S.Segmenter(rgb, con, K, storage=storage, stream=stream)
+            s.iterate(6)
+            ref, nref = s.labels(enforce=True)
+            out, n = results[i]
+            assert n == nref and np.array_equal(out, ref), i
+            s.close()
+    srv.close()
