@@ -50,7 +50,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true",
-                    help="skip the FP16-storage and batched forms")
+                    help="skip the FP16-storage, batched and serving forms")
+    ap.add_argument("--no-serving", action="store_true", help="skip the serving form")
     return ap.parse_args()
 
 
@@ -228,16 +229,15 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def measure_batch(args, storage: str, flush):
+def measure_batch(args, storage: str, flush, batch_imgs):
     """The batched form: 64 images of uneven size and K (H~U{240..1080},
     W~U{320..1920}, grid step S~U[12,30]) solved together, 10 iterations each;
     one step = reload + 10 batched iterations + connectivity for all images."""
     import torch
 
-    from paper_1903_07149_gb300 import scalp, synth
+    from paper_1903_07149_gb300 import scalp
 
-    ws = synth.batch_configs()
-    rgbs, cons = synth.batch_images(ws)
+    ws, rgbs, cons = batch_imgs
     d_rgb = [torch.from_numpy(r).cuda() for r in rgbs]
     d_con = [torch.from_numpy(c).cuda() for c in cons]
     outs = [torch.empty((w.H, w.W), dtype=torch.int32, device="cuda") for w in ws]
@@ -277,6 +277,98 @@ def measure_batch(args, storage: str, flush):
             "iters": iters, "storage": storage,
             "iterations_only_mpix_iter_s": pix * iters / (t0.elapsed_time(t1) / 1e3) / 1e6,
             "workload": "64 images, H~U{240..1080}, W~U{320..1920}, S~U[12,30], K=round(HW/S^2)"}
+
+
+def measure_serving(args, batch_imgs, n_requests: int = 2000, rate_hz: float = 500.0,
+                    budget_gb: float = 40.0, storage: str = "f16"):
+    """The serving form: Poisson arrivals at rate_hz over the batch size mix
+    plus 10% 2160x3840 images, admitted into a server with a device memory
+    budget; each request gets 10 iterations and connectivity enforcement.
+    Latency = delivery of its labels (host, pinned) - arrival.  Compared with
+    serial plain-FP32 solves of the same request stream (first come, first
+    served, one at a time)."""
+    import numpy as np
+    import torch
+
+    from paper_1903_07149_gb300 import scalp, synth
+
+    ws, rgbs, cons = batch_imgs
+    uhd = []
+    for seed in (1002, 1003):
+        w = synth.WORKLOADS["uhd_2160x3840_k10000"]
+        rgb, con, _ = synth.voronoi_image(w.H, w.W, w.n_cells, gradient=True, noise_sigma=6.0, seed=seed)
+        uhd.append((torch.from_numpy(rgb).cuda(), torch.from_numpy(con).cuda(), w.K))
+    small = [(torch.from_numpy(r).cuda(), torch.from_numpy(c).cuda(), w.K)
+             for w, r, c in zip(ws, rgbs, cons)]
+    arrivals, kind = synth.serving_arrivals(n_requests, rate_hz, seed=4000)
+    reqs = [uhd[i % 2] if kind[i] else small[i % len(small)] for i in range(n_requests)]
+    pix = [int(r[0].shape[0]) * int(r[0].shape[1]) for r in reqs]
+    iters = 10
+
+    # warm the pinned-memory cache and the kernels with a few requests
+    stream = torch.cuda.Stream()
+    srv = scalp.Server(int(budget_gb * (1 << 30)), max_slots=1024, storage=storage, iters=iters,
+                       stream=stream)
+    warm = [srv.submit(*reqs[i]) for i in range(8)]
+    while any(not srv.poll(r[0])[0] for r in warm if r):
+        srv.step()
+
+    lat = np.zeros(n_requests)
+    t0 = time.perf_counter()
+    nxt, inflight, queue = 0, {}, []
+    while nxt < n_requests or queue or inflight:
+        now = time.perf_counter() - t0
+        while nxt < n_requests and arrivals[nxt] <= now:
+            queue.append(nxt)
+            nxt += 1
+        while queue:  # admit in arrival order while memory and slots allow
+            r = srv.submit(*reqs[queue[0]])
+            if r is None:
+                break
+            inflight[r[0]] = queue.pop(0)
+        if inflight:
+            srv.step()
+        elif nxt < n_requests:
+            time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
+        for rid in list(inflight):
+            done, _ = srv.poll(rid)
+            if done:
+                i = inflight.pop(rid)
+                lat[i] = time.perf_counter() - t0 - arrivals[i]
+    wall = time.perf_counter() - t0
+    srv.close()
+
+    # serial plain-FP32 solves of the same stream
+    lat_s = np.zeros(n_requests)
+    segs = {}
+    t0 = time.perf_counter()
+    with torch.cuda.stream(stream):
+        for i, (rgb, con, K) in enumerate(reqs):
+            now = time.perf_counter() - t0
+            if arrivals[i] > now:
+                time.sleep(arrivals[i] - now)
+            key = (rgb.data_ptr(), K)
+            if key not in segs:
+                segs[key] = scalp.Segmenter(rgb, con, K, storage="f32", stream=stream)
+            s = segs[key]
+            s.reload(rgb, con)
+            s.iterate(iters)
+            out = torch.empty((rgb.shape[0], rgb.shape[1]), dtype=torch.int32, pin_memory=True)
+            s.labels(enforce=True, out=out.numpy())
+            lat_s[i] = time.perf_counter() - t0 - arrivals[i]
+    wall_s = time.perf_counter() - t0
+    for s in segs.values():
+        s.close()
+    tot = sum(pix) * iters / 1e6
+    return {
+        "requests": n_requests, "rate_hz": rate_hz, "budget_gb": budget_gb, "storage": storage,
+        "mix": "64 sizes of the batch mix + 10% 2160x3840", "iters": iters,
+        "value": tot / wall, "unit": UNIT, "wall_s": wall,
+        "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+        "serial_f32": {"value": tot / wall_s, "unit": UNIT, "wall_s": wall_s,
+                       "p50_ms": float(np.percentile(lat_s, 50) * 1e3),
+                       "p99_ms": float(np.percentile(lat_s, 99) * 1e3)},
+    }
 
 
 def measure_single_form(args, w, rgb, con, storage: str, flush):
@@ -447,12 +539,18 @@ def run_ours(args):
         "roofline": roofline,
     }
     if not args.no_forms:
+        from paper_1903_07149_gb300 import synth
+
         other = "f16" if args.storage == "f32" else "f32"
+        bws = synth.batch_configs()
+        batch_imgs = (bws, *synth.batch_images(bws))
         line["forms"] = {
             f"single_{other}": measure_single_form(args, w, rgb, con, other, flush),
-            "batched_f16": measure_batch(args, "f16", flush),
-            "batched_f32": measure_batch(args, "f32", flush),
+            "batched_f16": measure_batch(args, "f16", flush, batch_imgs),
+            "batched_f32": measure_batch(args, "f32", flush, batch_imgs),
         }
+        if not args.no_serving:
+            line["forms"]["serving"] = measure_serving(args, batch_imgs)
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline_oracle(w, rgb, con)
     print(json.dumps(line), flush=True)
