@@ -129,6 +129,23 @@ RELOAD_LAUNCHES = 6
 ITER_LAUNCHES = 5
 
 
+def rank_max(x: float, device: str = "cuda") -> float:
+    """Max of a per-rank number over all ranks (identity without a process group)."""
+    import torch
+    import torch.distributed as td
+
+    if not (td.is_available() and td.is_initialized()):
+        return x
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    td.all_reduce(t, op=td.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_value(units_per_rank: float, world: int, slowest_ms: float) -> float:
+    """Mpix*iter/s of the whole job: every rank's units over the slowest rank's time."""
+    return world * units_per_rank / (slowest_ms / 1e3) / 1e6
+
+
 def ccl_launches(N: int) -> int:
     """Connectivity kernels: tile-local, border, flatten, link, resolve, flag,
     output, plus the multi-level scan (one block pass per level, one add pass
@@ -463,12 +480,8 @@ def run_ours(args):
         clk = clocks.stop()
         ms_assign, assign_launches = seg.profile(0)
     step_ms = [a.elapsed_time(b) for a, b in zip(ev0, ev1)]
-    total_ms = sum(step_ms)
-    if dist:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        td.all_reduce(t, op=td.ReduceOp.MAX)
-        total_ms = float(t.item())
-    value = world * N * iters * args.steps / (total_ms / 1e3) / 1e6
+    total_ms = rank_max(sum(step_ms))
+    value = whole_job_value(N * iters * args.steps, world, total_ms)
 
     # end to end through the public API: pinned host buffers in, labels out
     e2e = None
@@ -490,11 +503,8 @@ def run_ours(args):
                 seg.iterate(iters)
                 seg.labels(enforce=True, out=a_out)
                 t_e2e += time.perf_counter() - t0
-        if dist:
-            t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-            td.all_reduce(t, op=td.ReduceOp.MAX)
-            t_e2e = float(t.item())
-        e2e = {"value": world * N * iters * args.steps / t_e2e / 1e6, "unit": UNIT,
+        t_e2e = rank_max(t_e2e)
+        e2e = {"value": whole_job_value(N * iters * args.steps, world, t_e2e * 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(rgb.nbytes + con.nbytes),
                "d2h_bytes_per_step": int(w.H * w.W * 4)}
 
