@@ -388,6 +388,48 @@ def measure_serving(args, batch_imgs, n_requests: int = 2000, rate_hz: float = 5
     }
 
 
+def measure_multiscale(args, flush, storage: str = "f32"):
+    """The multi-scale boundary map of Sec. III-A2 on the 321x481 workload: the
+    image solved at 12 scales (K = 6 .. 600, geometric) as one batch, 10
+    iterations, connectivity, then the averaged boundary map."""
+    import torch
+
+    from paper_1903_07149_gb300 import scalp, synth
+
+    w, rgb, con = synth.single_image_config("bsd_321x481_k400")
+    Ks = scalp.multiscale_K()
+    d_rgb, d_con = torch.from_numpy(rgb).cuda(), torch.from_numpy(con).cuda()
+    stream = torch.cuda.Stream()
+    outs = [torch.empty((w.H, w.W), dtype=torch.int32, device="cuda") for _ in Ks]
+    bmap = torch.empty((w.H, w.W), dtype=torch.float32, device="cuda")
+    with torch.cuda.stream(stream):
+        b = scalp.Batch([d_rgb] * len(Ks), [d_con] * len(Ks), Ks, storage=storage, stream=stream)
+
+        def step():
+            b.reload([d_rgb] * len(Ks), [d_con] * len(Ks))
+            b.iterate(w.iters)
+            b.labels(enforce=True, outs=outs)
+            scalp.scalp_boundary_map([o.data_ptr() for o in outs], w.H, w.W, bmap.data_ptr(),
+                                     stream.cuda_stream)
+
+        for _ in range(args.warmup):
+            step()
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        torch.cuda.synchronize()
+        for i in range(args.steps):
+            flush.zero_()
+            ev0[i].record(stream)
+            step()
+            ev1[i].record(stream)
+        torch.cuda.synchronize()
+        b.close()
+    total_ms = sum(a.elapsed_time(c) for a, c in zip(ev0, ev1))
+    return {"value": len(Ks) * w.H * w.W * w.iters * args.steps / (total_ms / 1e3) / 1e6,
+            "unit": UNIT, "ms_per_map": total_ms / args.steps, "scales": Ks,
+            "workload": w.name, "storage": storage}
+
+
 def measure_single_form(args, w, rgb, con, storage: str, flush):
     """Plain single-image solve with the given plane storage (FP16 form)."""
     import torch
@@ -559,6 +601,7 @@ def run_ours(args):
             "batched_f16": measure_batch(args, "f16", flush, batch_imgs),
             "batched_f32": measure_batch(args, "f32", flush, batch_imgs),
         }
+        line["forms"]["multiscale_boundary_map"] = measure_multiscale(args, flush)
         if not args.no_serving:
             line["forms"]["serving"] = measure_serving(args, batch_imgs)
     if not args.no_cpu_baseline and world == 1:

@@ -236,6 +236,18 @@ int scalp_server_poll(scalp_server *s, uint64_t id, int32_t *done, int32_t *n_la
 int scalp_server_stats(const scalp_server *s, int32_t *in_flight, size_t *pool_free_bytes);
 void scalp_server_destroy(scalp_server *s);
 
+/* ---- Multi-scale boundary map (Sec. III-A2) -----------------------------------
+ *
+ * The precision-recall evaluation of the paper averages the boundary maps of
+ * decompositions at several scales (12 scales from 6 to 600 superpixels) into
+ * a boundary confidence map.  labels: host array of `count` device pointers
+ * to H*W int32 label maps (1 <= count <= SCALP_MAX_MAPS); out: device H*W
+ * float.  out[p] = (number of maps in which a 4-neighbour of p has another
+ * label) / count.  Asynchronous on `stream`. */
+#define SCALP_MAX_MAPS 64
+int scalp_boundary_map(const int32_t *const *labels, int32_t count, int32_t H, int32_t W,
+                       float *out, void *stream);
+
 /* ---- An entry point that allocates nothing (no counterpart in the paper) ----
  *
  * For callers that cannot allocate device memory: code running while another

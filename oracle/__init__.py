@@ -82,6 +82,7 @@ def lib():
             L.orc_assign_pixels.argtypes = [ctypes.POINTER(_Ctx), P, ctypes.c_int64, P, P]
             L.orc_connectivity.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
             L.orc_connectivity.restype = ctypes.c_int32
+            L.orc_boundary_map.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
             _lib = L
     return _lib
 
@@ -127,6 +128,21 @@ def connectivity(labels: np.ndarray, K: int):
     out = np.empty_like(labels)
     n = lib().orc_connectivity(_ptr(labels), H, W, K, _ptr(out))
     return out, int(n)
+
+
+def boundary_map(label_maps):
+    """Average boundary indicator of several (H, W) label maps -> float32 (H, W)."""
+    maps = [np.ascontiguousarray(m, dtype=np.int32) for m in label_maps]
+    H, W = maps[0].shape
+    ptrs = (ctypes.c_void_p * len(maps))(*[m.ctypes.data for m in maps])
+    out = np.empty((H, W), np.float32)
+    lib().orc_boundary_map(ctypes.cast(ptrs, ctypes.c_void_p), len(maps), H, W, _ptr(out))
+    return out
+
+
+def multiscale_K(k_min: int = 6, k_max: int = 600, scales: int = 12):
+    """Geometric scale ladder k_min .. k_max (the paper's 12 scales, 6 to 600)."""
+    return [int(round(k_min * (k_max / k_min) ** (i / (scales - 1)))) for i in range(scales)]
 
 
 class Solver:

@@ -431,3 +431,31 @@ int32_t orc_connectivity(const int32_t *labels, int H, int W, int K, int32_t *ou
     free(comp); free(seed); free(size); free(stack); free(final_id); free(number);
     return nlab;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Multi-scale boundary map (Sec. III-A2: boundary maps of decompositions at  */
+/* several scales are averaged into a confidence map).  Pixel p is a boundary */
+/* pixel of a decomposition iff one of its 4-neighbours carries another      */
+/* label; the map is the fraction of the `count` decompositions in which p is */
+/* a boundary pixel: (number of decompositions) / count, in single precision. */
+/* ------------------------------------------------------------------------ */
+
+void orc_boundary_map(const int32_t *const *labels, int count, int H, int W, float *out)
+{
+    for (int y = 0; y < H; y++) {
+        for (int x = 0; x < W; x++) {
+            int64_t p = (int64_t)y * W + x;
+            int hits = 0;
+            for (int i = 0; i < count; i++) {
+                const int32_t *l = labels[i];
+                int b = 0;
+                if (x > 0 && l[p - 1] != l[p]) b = 1;
+                if (x < W - 1 && l[p + 1] != l[p]) b = 1;
+                if (y > 0 && l[p - W] != l[p]) b = 1;
+                if (y < H - 1 && l[p + W] != l[p]) b = 1;
+                hits += b;
+            }
+            out[p] = (float)hits / (float)count;
+        }
+    }
+}

@@ -69,7 +69,7 @@ EXPORTS = (
     "scalp_batch_workspace_bytes", "scalp_batch_init", "scalp_batch_reload", "scalp_batch_iterate",
     "scalp_batch_labels", "scalp_batch_get_state", "scalp_batch_get_info", "scalp_batch_destroy",
     "scalp_server_reserve_bytes", "scalp_server_create", "scalp_server_submit", "scalp_server_step",
-    "scalp_server_poll", "scalp_server_stats", "scalp_server_destroy",
+    "scalp_server_poll", "scalp_server_stats", "scalp_server_destroy", "scalp_boundary_map",
 )
 
 _lib = None
@@ -129,6 +129,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                                  ctypes.POINTER(I32)]),
             "scalp_server_stats": (ctypes.c_int, [P, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_size_t)]),
             "scalp_server_destroy": (None, [P]),
+            "scalp_boundary_map": (ctypes.c_int, [P, I32, I32, I32, P, P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -614,3 +615,37 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+# --- multi-scale boundary map ---------------------------------------------------
+def scalp_boundary_map(label_ptrs, H: int, W: int, out_ptr: int, stream_ptr: int):
+    n = len(label_ptrs)
+    ptrs = (ctypes.c_void_p * n)(*label_ptrs)
+    _check(load().scalp_boundary_map(ctypes.cast(ptrs, ctypes.c_void_p), n, int(H), int(W),
+                                     ctypes.c_void_p(out_ptr), ctypes.c_void_p(stream_ptr)))
+
+
+def multiscale_K(k_min: int = 6, k_max: int = 600, scales: int = 12):
+    """The scale ladder: scales values of K from k_min to k_max, geometric."""
+    return [int(round(k_min * (k_max / k_min) ** (i / (scales - 1)))) for i in range(scales)]
+
+
+def multiscale_boundaries(rgb, contour, Ks, iters: int = 10, storage: str = "f32", stream=None):
+    """Solves one image (CUDA tensors) at every K of Ks as one batch and returns
+    (boundary confidence map (H, W) float32 CUDA tensor, list of label tensors)."""
+    import torch
+
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    H, W = int(rgb.shape[0]), int(rgb.shape[1])
+    b = Batch([rgb] * len(Ks), None if contour is None else [contour] * len(Ks), Ks,
+              storage=storage, stream=stream)
+    try:
+        b.iterate(iters)
+        outs = [torch.empty((H, W), dtype=torch.int32, device="cuda") for _ in Ks]
+        b.labels(enforce=True, outs=outs)
+        bmap = torch.empty((H, W), dtype=torch.float32, device="cuda")
+        scalp_boundary_map([o.data_ptr() for o in outs], H, W, bmap.data_ptr(), stream.cuda_stream)
+        stream.synchronize()
+    finally:
+        b.close()
+    return bmap, outs

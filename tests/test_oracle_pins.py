@@ -420,3 +420,47 @@ def test_connectivity_invariants():
         if idx[0] != 0:
             assert m.sum() > T
     assert first == sorted(first)  # numbered in raster order of their seeds
+
+
+# --------------------------------------------------------------------------
+# Multi-scale boundary map (Sec. III-A2): averaged boundary indicators.
+# --------------------------------------------------------------------------
+def _boundary_numpy(lab):
+    b = np.zeros(lab.shape, bool)
+    dx = lab[:, 1:] != lab[:, :-1]
+    dy = lab[1:, :] != lab[:-1, :]
+    b[:, 1:] |= dx
+    b[:, :-1] |= dx
+    b[1:, :] |= dy
+    b[:-1, :] |= dy
+    return b
+
+
+def test_boundary_map_closed_forms():
+    two = np.zeros((5, 8), np.int32)
+    two[:, 5:] = 1
+    m = oracle.boundary_map([two])
+    expected = np.zeros((5, 8), np.float32)
+    expected[:, 4:6] = 1.0
+    assert np.array_equal(m, expected)
+    checker = (np.add.outer(np.arange(6), np.arange(7)) % 2).astype(np.int32)
+    assert np.all(oracle.boundary_map([checker]) == 1.0)
+    assert np.all(oracle.boundary_map([np.full((4, 4), 3, np.int32)]) == 0.0)
+
+
+def test_boundary_map_vs_numpy_average():
+    rng = np.random.default_rng(4)
+    maps = [np.kron(rng.integers(0, 9, size=(8, 10)), np.ones((4, 5), int)).astype(np.int32)
+            for _ in range(5)]
+    ref = np.mean([_boundary_numpy(m) for m in maps], axis=0).astype(np.float32)
+    got = oracle.boundary_map(maps)
+    assert np.allclose(got, ref, atol=1e-7)
+    counts = np.sum([_boundary_numpy(m) for m in maps], axis=0)
+    assert np.array_equal(got, (counts.astype(np.float32) / np.float32(5)))
+
+
+def test_multiscale_ladder():
+    Ks = oracle.multiscale_K()
+    assert len(Ks) == 12 and Ks[0] == 6 and Ks[-1] == 600
+    ratios = np.array(Ks[1:]) / np.array(Ks[:-1])
+    assert np.all(np.abs(ratios - 100 ** (1 / 11)) < 0.12)  # geometric up to rounding
