@@ -430,6 +430,31 @@ def measure_multiscale(args, flush, storage: str = "f32"):
             "workload": w.name, "storage": storage}
 
 
+def measure_quality(w, rgb, con, cells):
+    """Superpixel metrics (Eq. 5-8) of the HD decomposition against its Voronoi
+    cells, for SCALP's defaults and for the SLIC special case (lambda = 1,
+    gamma = 0, stated below Eq. 3): the ablation of Fig. 4(a) on synthetic
+    ground truth."""
+    import torch
+
+    from paper_1903_07149_gb300 import scalp
+
+    d_rgb, d_con = torch.from_numpy(rgb).cuda(), torch.from_numpy(con).cuda()
+    gt = torch.from_numpy(cells).cuda()
+    res = {}
+    for name, lam, gamma in (("scalp", 0.5, -1.0), ("slic", 1.0, 0.0)):
+        seg = scalp.Segmenter(d_rgb, d_con, w.K, lam=lam, gamma=gamma)
+        seg.iterate(w.iters)
+        out = torch.empty((w.H, w.W), dtype=torch.int32, device="cuda")
+        _, n = seg.labels(enforce=True, out=out)
+        q = scalp.quality_metrics(out, gt)
+        q["n_superpixels"] = int(n)
+        res[name] = q
+        seg.close()
+    res["ground_truth"] = f"the {int(cells.max()) + 1} Voronoi cells of the synthetic image"
+    return res
+
+
 def measure_single_form(args, w, rgb, con, storage: str, flush):
     """Plain single-image solve with the given plane storage (FP16 form)."""
     import torch
@@ -602,6 +627,9 @@ def run_ours(args):
             "batched_f32": measure_batch(args, "f32", flush, batch_imgs),
         }
         line["forms"]["multiscale_boundary_map"] = measure_multiscale(args, flush)
+        _, _, cells = synth.voronoi_image(w.H, w.W, w.n_cells, gradient=w.gradient,
+                                          noise_sigma=w.noise_sigma, seed=w.seed)
+        line["forms"]["quality_eq5_8"] = measure_quality(w, rgb, con, cells)
         if not args.no_serving:
             line["forms"]["serving"] = measure_serving(args, batch_imgs)
     if not args.no_cpu_baseline and world == 1:

@@ -248,6 +248,28 @@ void scalp_server_destroy(scalp_server *s);
 int scalp_boundary_map(const int32_t *const *labels, int32_t count, int32_t H, int32_t W,
                        float *out, void *stream);
 
+/* ---- Superpixel quality metrics (Sec. III-A2, Eq. 5-8) -------------------------
+ *
+ * Scores of a decomposition `labels` (values in [0, n_labels)) against a
+ * ground-truth segmentation `gt` (values in [0, n_gt)), both device H*W int32.
+ * Boundary pixels are pixels with a 4-neighbour of another label.
+ *   br  Eq. 5, boundary recall: ground-truth boundary pixels with a superpixel
+ *       boundary pixel at Euclidean distance < eps (the paper uses eps = 2)
+ *   asa Eq. 6, achievable segmentation accuracy
+ *   ue  Eq. 7, undersegmentation error, sum over segments and the superpixels
+ *       meeting them of |S_k - G_i|, over the pixel count
+ *   co  Eq. 8, compactness, the perimeter |P(S_k)| counted as pixel edges between
+ *       S_k and the rest of the image (image border included)
+ * The workspace (device, scalp_quality_workspace_bytes) is caller-owned; the
+ * call synchronises `stream` and fills *out.  n_labels * n_gt <= 2^28. */
+typedef struct {
+    double br, asa, ue, co;
+} scalp_quality;
+size_t scalp_quality_workspace_bytes(int32_t H, int32_t W, int32_t n_labels, int32_t n_gt);
+int scalp_quality_metrics(const int32_t *labels, int32_t n_labels, const int32_t *gt, int32_t n_gt,
+                          int32_t H, int32_t W, double eps, void *workspace, size_t workspace_bytes,
+                          scalp_quality *out, void *stream);
+
 /* ---- An entry point that allocates nothing (no counterpart in the paper) ----
  *
  * For callers that cannot allocate device memory: code running while another

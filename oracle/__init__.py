@@ -83,6 +83,8 @@ def lib():
             L.orc_connectivity.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
             L.orc_connectivity.restype = ctypes.c_int32
             L.orc_boundary_map.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
+            L.orc_quality.argtypes = [P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_double, P, P, P, P]
             _lib = L
     return _lib
 
@@ -138,6 +140,17 @@ def boundary_map(label_maps):
     out = np.empty((H, W), np.float32)
     lib().orc_boundary_map(ctypes.cast(ptrs, ctypes.c_void_p), len(maps), H, W, _ptr(out))
     return out
+
+
+def quality(labels, gt, eps: float = 2.0):
+    """BR, ASA, UE, CO (Eq. 5-8) of a label map against a ground truth."""
+    labels = np.ascontiguousarray(labels, dtype=np.int32)
+    gt = np.ascontiguousarray(gt, dtype=np.int32)
+    H, W = labels.shape
+    out = [ctypes.c_double() for _ in range(4)]
+    lib().orc_quality(_ptr(labels), int(labels.max()) + 1, _ptr(gt), int(gt.max()) + 1, H, W,
+                      float(eps), *[ctypes.byref(v) for v in out])
+    return dict(zip(("br", "asa", "ue", "co"), (v.value for v in out)))
 
 
 def multiscale_K(k_min: int = 6, k_max: int = 600, scales: int = 12):

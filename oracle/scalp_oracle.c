@@ -459,3 +459,88 @@ void orc_boundary_map(const int32_t *const *labels, int count, int H, int W, flo
         }
     }
 }
+
+/* ------------------------------------------------------------------------ */
+/* Superpixel quality metrics against a ground-truth segmentation, Eq. 5-8.  */
+/* Boundary pixels are pixels with a 4-neighbour of another label.           */
+/*   BR  (Eq. 5): fraction of ground-truth boundary pixels p with a          */
+/*        superpixel boundary pixel q at Euclidean distance ||p-q|| < eps.    */
+/*   ASA (Eq. 6): sum over superpixels of the largest overlap with one        */
+/*        ground-truth segment, over the number of pixels.                    */
+/*   UE  (Eq. 7): sum over segments G_i and superpixels S_k meeting G_i of    */
+/*        |S_k - G_i|, over the number of pixels.                             */
+/*   CO  (Eq. 8): (1/|I|) sum_k 4 pi |S_k|^2 / |P(S_k)|^2, the perimeter      */
+/*        being the number of pixel edges between S_k and the rest of the     */
+/*        image, the image border included.                                   */
+/* Labels in [0, n_labels), ground truth in [0, n_gt).                        */
+/* ------------------------------------------------------------------------ */
+
+static int is_boundary(const int32_t *l, int H, int W, int x, int y)
+{
+    int64_t p = (int64_t)y * W + x;
+    if (x > 0 && l[p - 1] != l[p]) return 1;
+    if (x < W - 1 && l[p + 1] != l[p]) return 1;
+    if (y > 0 && l[p - W] != l[p]) return 1;
+    if (y < H - 1 && l[p + W] != l[p]) return 1;
+    return 0;
+}
+
+void orc_quality(const int32_t *labels, int n_labels, const int32_t *gt, int n_gt, int H, int W,
+                 double eps, double *br, double *asa, double *ue, double *co)
+{
+    int64_t N = (int64_t)H * W;
+    /* Eq. 5 */
+    int r = (int)ceil(eps);
+    int64_t gb = 0, hit = 0;
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            if (!is_boundary(gt, H, W, x, y)) continue;
+            gb++;
+            int found = 0;
+            for (int dy = -r; dy <= r && !found; dy++)
+                for (int dx = -r; dx <= r && !found; dx++) {
+                    int qx = x + dx, qy = y + dy;
+                    if (qx < 0 || qy < 0 || qx >= W || qy >= H) continue;
+                    if (sqrt((double)(dx * dx + dy * dy)) >= eps) continue;
+                    if (is_boundary(labels, H, W, qx, qy)) found = 1;
+                }
+            hit += found;
+        }
+    *br = gb ? (double)hit / (double)gb : 1.0;
+    /* overlaps |S_k n G_i| */
+    int64_t *ov = (int64_t *)calloc((size_t)n_labels * (size_t)n_gt, sizeof(int64_t));
+    int64_t *area = (int64_t *)calloc((size_t)n_labels, sizeof(int64_t));
+    int64_t *perim = (int64_t *)calloc((size_t)n_labels, sizeof(int64_t));
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            int64_t p = (int64_t)y * W + x;
+            int k = labels[p];
+            ov[(int64_t)k * n_gt + gt[p]]++;
+            area[k]++;
+            /* edges to each of the 4 sides: image border or another label */
+            perim[k] += (x == 0 || labels[p - 1] != k) + (x == W - 1 || labels[p + 1] != k) +
+                        (y == 0 || labels[p - W] != k) + (y == H - 1 || labels[p + W] != k);
+        }
+    /* Eq. 6 and Eq. 7 */
+    int64_t asa_num = 0, ue_num = 0;
+    for (int k = 0; k < n_labels; k++) {
+        int64_t best = 0;
+        for (int i = 0; i < n_gt; i++) {
+            int64_t o = ov[(int64_t)k * n_gt + i];
+            if (o > best) best = o;
+            if (o > 0) ue_num += area[k] - o;
+        }
+        asa_num += best;
+    }
+    *asa = (double)asa_num / (double)N;
+    *ue = (double)ue_num / (double)N;
+    /* Eq. 8 */
+    double s = 0.0;
+    for (int k = 0; k < n_labels; k++) {
+        if (area[k] == 0) continue;
+        double a = (double)area[k], pr = (double)perim[k];
+        s += 4.0 * M_PI * a * a / (pr * pr);
+    }
+    *co = s / (double)N;
+    free(ov); free(area); free(perim);
+}

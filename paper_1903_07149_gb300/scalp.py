@@ -55,6 +55,11 @@ class scalp_info(ctypes.Structure):
                 ("iterations", ctypes.c_int32)]
 
 
+class scalp_quality(ctypes.Structure):
+    _fields_ = [("br", ctypes.c_double), ("asa", ctypes.c_double), ("ue", ctypes.c_double),
+                ("co", ctypes.c_double)]
+
+
 class scalp_state(ctypes.Structure):
     _fields_ = [("labels", ctypes.c_void_p), ("n", ctypes.c_void_p), ("sx", ctypes.c_void_p),
                 ("sy", ctypes.c_void_p), ("color", ctypes.c_void_p), ("endpoint", ctypes.c_void_p)]
@@ -70,6 +75,7 @@ EXPORTS = (
     "scalp_batch_labels", "scalp_batch_get_state", "scalp_batch_get_info", "scalp_batch_destroy",
     "scalp_server_reserve_bytes", "scalp_server_create", "scalp_server_submit", "scalp_server_step",
     "scalp_server_poll", "scalp_server_stats", "scalp_server_destroy", "scalp_boundary_map",
+    "scalp_quality_workspace_bytes", "scalp_quality_metrics",
 )
 
 _lib = None
@@ -130,6 +136,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "scalp_server_stats": (ctypes.c_int, [P, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_size_t)]),
             "scalp_server_destroy": (None, [P]),
             "scalp_boundary_map": (ctypes.c_int, [P, I32, I32, I32, P, P]),
+            "scalp_quality_workspace_bytes": (ctypes.c_size_t, [I32, I32, I32, I32]),
+            "scalp_quality_metrics": (ctypes.c_int, [P, I32, P, I32, I32, I32, ctypes.c_double, P,
+                                                     ctypes.c_size_t, ctypes.POINTER(scalp_quality), P]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -649,3 +658,31 @@ def multiscale_boundaries(rgb, contour, Ks, iters: int = 10, storage: str = "f32
     finally:
         b.close()
     return bmap, outs
+
+
+# --- quality metrics ----------------------------------------------------------------
+def scalp_quality_workspace_bytes(H: int, W: int, n_labels: int, n_gt: int) -> int:
+    return int(load().scalp_quality_workspace_bytes(int(H), int(W), int(n_labels), int(n_gt)))
+
+
+def quality_metrics(labels, gt, eps: float = 2.0, stream=None):
+    """BR, ASA, UE, CO (Eq. 5-8) of a CUDA int32 label map against a CUDA int32
+    ground truth, both (H, W).  Returns a dict."""
+    import torch
+
+    stream = stream if stream is not None else torch.cuda.current_stream()
+    H, W = int(labels.shape[0]), int(labels.shape[1])
+    n_labels = int(labels.max().item()) + 1
+    n_gt = int(gt.max().item()) + 1
+    nbytes = scalp_quality_workspace_bytes(H, W, n_labels, n_gt)
+    if nbytes == 0:
+        raise ScalpError(SCALP_E_ARG, "invalid sizes for the quality metrics")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+    q = scalp_quality()
+    lab = labels.contiguous()
+    g = gt.contiguous()
+    _check(load().scalp_quality_metrics(ctypes.c_void_p(lab.data_ptr()), n_labels,
+                                        ctypes.c_void_p(g.data_ptr()), n_gt, H, W, float(eps),
+                                        ctypes.c_void_p(ws.data_ptr()), nbytes, ctypes.byref(q),
+                                        ctypes.c_void_p(stream.cuda_stream)))
+    return {"br": q.br, "asa": q.asa, "ue": q.ue, "co": q.co}

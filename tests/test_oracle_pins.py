@@ -464,3 +464,78 @@ def test_multiscale_ladder():
     assert len(Ks) == 12 and Ks[0] == 6 and Ks[-1] == 600
     ratios = np.array(Ks[1:]) / np.array(Ks[:-1])
     assert np.all(np.abs(ratios - 100 ** (1 / 11)) < 0.12)  # geometric up to rounding
+
+
+# --------------------------------------------------------------------------
+# Quality metrics, Eq. 5-8, against closed forms and an independent numpy /
+# scipy formulation.
+# --------------------------------------------------------------------------
+def test_quality_identity_and_single_superpixel():
+    rng = np.random.default_rng(8)
+    gt = np.kron(rng.integers(0, 6, size=(5, 6)), np.ones((6, 7), int)).astype(np.int32)
+    q = oracle.quality(gt, gt)
+    assert q["br"] == 1.0 and q["asa"] == 1.0 and q["ue"] == 0.0
+    one = np.zeros_like(gt)
+    q = oracle.quality(one, gt)
+    sizes = np.bincount(gt.ravel())
+    sizes = sizes[sizes > 0]
+    N = gt.size
+    assert q["asa"] == sizes.max() / N
+    assert q["ue"] == pytest.approx(len(sizes) * N / N - 1.0)  # sum_i (N - |G_i|) / N
+    assert q["br"] == 0.0
+
+
+def test_compactness_closed_forms():
+    assert oracle.quality(np.zeros((9, 9), np.int32), np.zeros((9, 9), np.int32))["co"] == \
+        pytest.approx(np.pi / 4)
+    n = 13
+    assert oracle.quality(np.zeros((1, n), np.int32), np.zeros((1, n), np.int32))["co"] == \
+        pytest.approx(4 * np.pi * n / (2 * n + 2) ** 2)
+    blocks = np.kron(np.arange(12).reshape(3, 4), np.ones((5, 5), int)).astype(np.int32)
+    assert oracle.quality(blocks, blocks)["co"] == pytest.approx(np.pi / 4)
+
+
+def test_boundary_recall_distance_is_strict():
+    H, W, c = 12, 20, 8
+    gt = np.zeros((H, W), np.int32)
+    gt[:, c:] = 1            # ground-truth boundary pixels: columns c-1 and c
+    s = np.zeros((H, W), np.int32)
+    s[:, c + 2:] = 1         # superpixel boundary pixels: columns c+1 and c+2
+    # column c is at distance 1 (hit); column c-1 at distance 2, not < 2 (miss)
+    assert oracle.quality(s, gt)["br"] == 0.5
+    s1 = np.zeros((H, W), np.int32)
+    s1[:, c + 1:] = 1
+    assert oracle.quality(s1, gt)["br"] == 1.0
+
+
+def _quality_numpy(lab, gt, eps=2.0):
+    from scipy import ndimage
+
+    N = lab.size
+    bs, bg = _boundary_numpy(lab), _boundary_numpy(gt)
+    dist = ndimage.distance_transform_edt(~bs)
+    br = (dist[bg] < eps).mean() if bg.any() else 1.0
+    k, i = lab.ravel(), gt.ravel()
+    ov = np.zeros((k.max() + 1, i.max() + 1), np.int64)
+    np.add.at(ov, (k, i), 1)
+    area = ov.sum(1)
+    asa = ov.max(1).sum() / N
+    ue = ((area[:, None] - ov) * (ov > 0)).sum() / N
+    pad = np.pad(lab, 1, constant_values=-1)
+    edges = np.zeros(k.max() + 1, np.int64)
+    for sl in ((slice(1, -1), slice(0, -2)), (slice(1, -1), slice(2, None)),
+               (slice(0, -2), slice(1, -1)), (slice(2, None), slice(1, -1))):
+        diff = pad[sl] != lab
+        np.add.at(edges, lab[diff], 1)
+    nz = area > 0
+    co = (4 * np.pi * area[nz] ** 2 / edges[nz] ** 2).sum() / N
+    return dict(br=br, asa=asa, ue=ue, co=co)
+
+
+def test_quality_vs_numpy_scipy():
+    rgb, C, cells = synth.small_image(70, 90, seed=41, n_cells=6)
+    s, out, n = oracle.solve(rgb, C, 40, iters=3)
+    got = oracle.quality(out, cells)
+    ref = _quality_numpy(out, cells)
+    for key in ("br", "asa", "ue", "co"):
+        assert got[key] == pytest.approx(ref[key], rel=1e-12, abs=1e-12), key
