@@ -144,9 +144,14 @@ __host__ __device__ inline size_t region_bytes(int halo, int elem)
 // Shared-memory layout after the staged region; every section starts on a
 // 16-byte boundary (int4 loads, 8-byte atomics and the mbarrier need it).
 constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
-constexpr int CELL = 8;  // items are halves of CELL x CELL cells
-constexpr int MAX_ITEMS = MAX_TILE_CANDIDATES * 2 * (TILE_X / CELL) * (TILE_Y / CELL);
-static_assert(TILE_X / CELL <= 4, "the 16-bit reciprocal of the cells per row is exact");
+constexpr int STRIP = 4;  // items run along strips STRIP pixels wide
+constexpr int MAX_ITEMS = MAX_TILE_CANDIDATES * (TILE_PIXELS / 32);
+constexpr int STRIP_RCP_BITS = 20;
+// the strip index j / (STRIP * len) by a STRIP_RCP_BITS-bit reciprocal is exact
+// when the rounding error j / 2^STRIP_RCP_BITS stays below 1 / (STRIP * len)
+static_assert((long long)TILE_PIXELS * STRIP * (TILE_X > TILE_Y ? TILE_X : TILE_Y) <
+                  (1LL << STRIP_RCP_BITS),
+              "exact strip index");
 struct AssignSmem {
     static constexpr size_t cand = 0;
     static constexpr size_t cid = align16(cand + MAX_TILE_CANDIDATES * sizeof(ClusterDev));
@@ -189,10 +194,13 @@ __device__ __forceinline__ unsigned long long pack_best(float D, int slot)
 }
 
 // Items: the pixels of a candidate's window that lie in the tile form a
-// rectangle; it is cut into 8 x 8 cells and each cell into two warp-sized
-// halves.  A cell whose paths run mostly along x is split into left and right
-// 4 x 8 halves, otherwise into top and bottom 8 x 4 halves, so that the path
-// lengths of a warp's 32 pixels differ by at most about 4.
+// rectangle.  When the rectangle lies mostly left or right of the path
+// endpoint (paths mostly along x, |P| set by the column) it is cut into
+// vertical strips STRIP columns wide, otherwise into horizontal strips STRIP
+// rows high.  The strips are read one after the other, each across its width
+// first, and every 32 consecutive pixels of that order form one warp's item.
+// So a warp's pixels lie in a few neighbouring columns (rows), where the path
+// lengths differ little, and only the last item of a rectangle has idle lanes.
 // One tile of one image (the body shared by the single-image and the batched
 // kernels).  `tmap` is the image's tensor map (kernel parameter or global).
 template <typename T, bool STAGED, int THREADS>
@@ -259,20 +267,20 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, const CUtensorMa
         const ClusterDev cd = a.cdev[myid];
         cid[rank] = myid;
         cand[rank] = cd;
-        // window x tile (clipped to the image), in 8 x 8 cells of two items
+        // window x tile (clipped to the image), cut into strips
         const int xa = max(cd.xlo, x0), xb = min(min(cd.xhi, x0 + TILE_X - 1), a.W - 1);
         const int ya = max(cd.ylo, y0), yb = min(min(cd.yhi, y0 + TILE_Y - 1), a.H - 1);
-        int ncx = 1, nitems = 0;
-        if (xa <= xb && ya <= yb) {
-            ncx = (xb - xa) / CELL + 1;
-            nitems = 2 * ncx * ((yb - ya) / CELL + 1);
-        }
+        const int w = max(xb - xa + 1, 0), h = max(yb - ya + 1, 0);
+        const bool vert = abs(xa + xb - 2 * cd.ex) >= abs(ya + yb - 2 * cd.ey);
+        const int slen = max(vert ? h : w, 1);  // pixels along one strip
         const bool inside = STAGED && cd.ex >= rx0 && cd.ex < rx0 + BX && cd.ey >= ry0 &&
                             cd.ey < ry0 + BY;
-        rect[rank] = make_int4(xa, ya, xb, yb);
-        // cells per row, endpoint-in-region flag, 16-bit reciprocal of ncx
-        meta[rank] = make_int2(ncx | ((int)inside << 8), (65536 + ncx - 1) / ncx);
-        nit[rank] = nitems;
+        rect[rank] = make_int4(xa, ya, w, h);
+        // strip direction and endpoint-in-region flags, reciprocal of the
+        // pixels per full strip
+        meta[rank] = make_int2((int)vert | ((int)inside << 1),
+                               ((1 << STRIP_RCP_BITS) + STRIP * slen - 1) / (STRIP * slen));
+        nit[rank] = (w * h + 31) >> 5;
     }
     __syncthreads();
     for (int i = tid; i < TILE_PIXELS; i += THREADS) best[i] = ~0ull;
@@ -339,19 +347,21 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, const CUtensorMa
             const int c = owner[item];
             const int4 rc = rect[c];
             const int2 mt = meta[c];
-            const int local = item - first[c];
-            const int cell = local >> 1, half = local & 1;
-            const int cy = (cell * mt.y) >> 16;  // exact: cell < 2^12, ncx <= 4
-            const int cx = cell - cy * (mt.x & 0xff);
-            const int ox = rc.x + CELL * cx, oy = rc.y + CELL * cy;
+            const int j = ((item - first[c]) << 5) + lane;  // pixel of the rectangle
+            if (j >= rc.z * rc.w) continue;
+            const bool vert = (mt.x & 1) != 0;
+            const int slen = vert ? rc.w : rc.z, across = vert ? rc.z : rc.w;
+            const int strip = (j * mt.y) >> STRIP_RCP_BITS;
+            const int t = j - strip * STRIP * slen;
+            // t / width for a strip 1..4 wide: exact 16-bit reciprocals
+            const int width = min(STRIP, across - strip * STRIP);
+            const int along = (t * (width == 3 ? 21846 : 65536 >> (width >> 1))) >> 16;
+            const int off = strip * STRIP + (t - along * width);
+            const int qx = rc.x + (vert ? off : along);
+            const int qy = rc.y + (vert ? along : off);
             const ClusterDev cd = cand[c];
-            // dominant axis of the paths from the cell centre to the endpoint
-            const bool xmaj = abs(2 * (ox - cd.ex) + CELL - 1) > abs(2 * (oy - cd.ey) + CELL - 1);
-            const int qx = xmaj ? ox + 4 * half + (lane & 3) : ox + (lane & 7);
-            const int qy = xmaj ? oy + (lane >> 2) : oy + 4 * half + (lane >> 3);
-            if (qx > rc.z || qy > rc.w) continue;
             const PathSetup s = path_setup(qx, qy, cd.ex, cd.ey);
-            const bool inside = (mt.x >> 8) != 0;
+            const bool inside = (mt.x >> 1) != 0;
             float sdc, sw;
             int len;
             float4 v;
