@@ -72,7 +72,7 @@ typedef struct {
     float gamma;           /* Eq. 2 contour weight, >= 0; < 0 selects 2r */
     int32_t storage;       /* SCALP_STORAGE_F32 or SCALP_STORAGE_F16 */
     int32_t use_graph;     /* 1: replay each iteration as a CUDA graph (non-NULL stream) */
-    int32_t global_walk;   /* 1: walk every path in global memory (no shared-memory tile) */
+    int32_t global_walk;   /* 1: walk every path on the plane in global memory (no distance maps) */
     void *stream;          /* cudaStream_t for all device work */
     void *workspace;       /* device memory owned by the caller */
     size_t workspace_bytes;
@@ -84,7 +84,8 @@ typedef struct {
     int32_t nx, ny, Keff;  /* regular grid, Keff = nx*ny clusters */
     double r;              /* sqrt(H*W/K), the grid step and window half-size */
     double gamma;          /* resolved Eq. 2 weight */
-    int32_t halo;          /* shared-memory halo of the assignment tiles (0: none) */
+    int32_t map_pairs;     /* shared-memory distance-map capacity of an assignment CTA, in
+                              (d_c, w) pairs (0: every path walks the plane) */
     int32_t iterations;    /* iterations run so far */
 } scalp_info;
 
@@ -158,10 +159,19 @@ int scalp_debug_paths(scalp_ctx *ctx, const int32_t *pairs, int32_t M, int32_t *
  * *ms and *launches receive the totals so far (synchronises). */
 int scalp_profile(scalp_ctx *ctx, int32_t enable, double *ms, int64_t *launches);
 
-/* Total path samples (sum of |P| over evaluated candidate pairs) of the last
- * assignment, counted on the device when counting is enabled via
- * scalp_count_samples(ctx, 1) (adds one atomic per tile; off by default). */
-int scalp_count_samples(scalp_ctx *ctx, int32_t enable, int64_t *samples, int64_t *pairs);
+/* Work of the last assignment, counted on the device while counting is
+ * enabled (scalp_count_samples(ctx, 1, ...) resets and enables, 0 disables,
+ * -1 only reads; a few atomics per tile; off by default):
+ *   samples      sum of |P| over the evaluated (pixel, cluster) pairs
+ *   pairs        evaluated (pixel, cluster) pairs
+ *   map_rects    (tile, cluster) rectangles whose paths walked a shared-memory
+ *                distance map
+ *   plane_rects  (tile, cluster) rectangles whose paths walked the plane in
+ *                global memory (map buffer full, global_walk, or a tile with
+ *                more candidates than shared memory holds)
+ * Any output pointer may be NULL.  Synchronises the stream. */
+int scalp_count_samples(scalp_ctx *ctx, int32_t enable, int64_t *samples, int64_t *pairs,
+                        int64_t *map_rects, int64_t *plane_rects);
 
 /* Synchronises the context's stream and reports pending device errors. */
 int scalp_sync(scalp_ctx *ctx);

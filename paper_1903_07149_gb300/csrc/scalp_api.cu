@@ -104,25 +104,6 @@ Layout make_layout(int H, int W, int K, int storage)
     return L;
 }
 
-typedef CUresult (*PFN_encodeTiled)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *,
-                                    const cuuint64_t *, const cuuint64_t *, const cuuint32_t *,
-                                    const cuuint32_t *, CUtensorMapInterleave, CUtensorMapSwizzle,
-                                    CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-PFN_encodeTiled get_encode()
-{
-    static PFN_encodeTiled fn = nullptr;
-    if (!fn) {
-        void *p = nullptr;
-        cudaDriverEntryPointQueryResult q;
-        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
-                                             &q) == cudaSuccess &&
-            q == cudaDriverEntryPointSuccess)
-            fn = reinterpret_cast<PFN_encodeTiled>(p);
-    }
-    return fn;
-}
-
 }  // namespace
 
 namespace scalp {
@@ -142,8 +123,6 @@ struct scalp_ctx {
     Layout L;
     SolveArgs a;
     CclBuffers ccl;
-    CUtensorMap tmap;
-    bool staged;
     size_t smem;
     cudaGraphExec_t gexec;
     bool graph_valid;
@@ -280,7 +259,7 @@ void enqueue_iteration(scalp_ctx *c, int slot, bool capturing)
 {
     const unsigned flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (c->profiling) cudaEventRecordWithFlags(c->ev_pool[2 * slot], c->st, flags);
-    launch_assign(c->a, c->p.storage, c->staged, c->tmap, c->smem, c->st);
+    launch_assign(c->a, c->p.storage, c->smem, c->st);
     if (c->profiling) cudaEventRecordWithFlags(c->ev_pool[2 * slot + 1], c->st, flags);
     launch_update(c->a, 1, c->st);
     launch_project(c->a, 0, c->st);
@@ -386,45 +365,12 @@ int scalp_init(scalp_ctx **out, const scalp_image *image, const scalp_contour *c
     c->ccl.scan_tmp = reinterpret_cast<int *>(c->ws + L.scan_tmp);
     c->ccl.scan_tmp_len = L.scan_tmp_len;
 
-    // Shared-memory tile: halo round(r) + margin holds every path whose end is
-    // the rounded barycenter of a cluster whose window holds the pixel.
-    int halo = (int)std::floor(c->r + 0.5) + HALO_MARGIN;
-    if (params->storage == 1) halo = (halo + 1) & ~1;  // even start column for 8-byte TMA
-    int BX = TILE_X + 2 * halo, BY = TILE_Y + 2 * halo;
-    size_t smem = assign_smem_bytes(halo, params->storage);
-    const int box_x = params->storage == 0 ? 2 * BX : BX;  // TMA box elements per row
-    c->staged = !params->global_walk && box_x <= 256 && BY <= 256 && smem <= 227 * 1024;
-    PFN_encodeTiled enc = c->staged ? get_encode() : nullptr;
-    if (c->staged && !enc) c->staged = false;
-    if (c->staged) {
-        CUresult r;
-        if (params->storage == 0) {
-            // 16-byte pixels as pairs of 8-byte elements: rows of 2*BX elements
-            cuuint64_t dims[2] = {2 * (cuuint64_t)W, (cuuint64_t)H};
-            cuuint64_t strides[1] = {(cuuint64_t)L.pitch * 16};
-            cuuint32_t box[2] = {2 * (cuuint32_t)BX, (cuuint32_t)BY};
-            cuuint32_t es[2] = {1, 1};
-            r = enc(&c->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, c->ws + L.plane, dims, strides, box,
-                    es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        } else {
-            cuuint64_t dims[2] = {(cuuint64_t)W, (cuuint64_t)H};
-            cuuint64_t strides[1] = {(cuuint64_t)L.pitch * 8};
-            cuuint32_t box[2] = {(cuuint32_t)BX, (cuuint32_t)BY};
-            cuuint32_t es[2] = {1, 1};
-            r = enc(&c->tmap, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 2, c->ws + L.plane, dims, strides, box,
-                    es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-        }
-        if (r != CUDA_SUCCESS) c->staged = false;
-    }
-    if (!c->staged) {
-        halo = 0;
-        std::memset(&c->tmap, 0, sizeof c->tmap);
-    }
-    a.halo = halo;
-    c->smem = assign_smem_bytes(halo, params->storage);
-    int rc = cuda_check(c, assign_configure(params->storage, c->staged, c->smem), "configure kernel");
+    // distance maps of the assignment CTAs (none: every path walks the plane)
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    a.map_cap = params->global_walk ? 0 : assign_map_capacity(dev);
+    c->smem = assign_smem_bytes(a.map_cap);
+    int rc = cuda_check(c, assign_configure(params->storage), "configure kernel");
     if (rc == SCALP_OK) {
         launch_srgb_table(c->a, c->st);
         rc = launch_check(c, "table kernel");
@@ -543,7 +489,7 @@ int scalp_get_info(const scalp_ctx *c, scalp_info *info)
     info->H = c->H; info->W = c->W; info->K = c->K;
     info->nx = c->nx; info->ny = c->ny; info->Keff = c->Keff;
     info->r = c->r; info->gamma = c->gamma;
-    info->halo = c->a.halo;
+    info->map_pairs = c->a.map_cap;
     info->iterations = c->iterations;
     return SCALP_OK;
 }
@@ -677,7 +623,8 @@ int scalp_profile(scalp_ctx *c, int32_t enable, double *ms, int64_t *launches)
     return SCALP_OK;
 }
 
-int scalp_count_samples(scalp_ctx *c, int32_t enable, int64_t *samples, int64_t *pairs)
+int scalp_count_samples(scalp_ctx *c, int32_t enable, int64_t *samples, int64_t *pairs,
+                        int64_t *map_rects, int64_t *plane_rects)
 {
     if (!c) return fail(nullptr, SCALP_E_ARG, "ctx is NULL");
     DevCounters h;
@@ -688,10 +635,13 @@ int scalp_count_samples(scalp_ctx *c, int32_t enable, int64_t *samples, int64_t 
     if (rc) return rc;
     if (samples) *samples = (int64_t)h.samples;
     if (pairs) *pairs = (int64_t)h.pairs;
+    if (map_rects) *map_rects = (int64_t)h.map_rects;
+    if (plane_rects) *plane_rects = (int64_t)h.plane_rects;
     if (enable >= 0) {
         int on = enable != 0;
         if (on) {
-            unsigned long long z[2] = {0, 0};
+            // samples, pairs, map_rects, plane_rects are consecutive
+            unsigned long long z[4] = {0, 0, 0, 0};
             rc = cuda_check(c, cudaMemcpyAsync(&c->a.ctr->samples, z, sizeof z, cudaMemcpyHostToDevice,
                                                c->st), "reset counters");
             if (rc) return rc;
@@ -741,7 +691,6 @@ void scalp_destroy(scalp_ctx *c)
 namespace scalp {
 
 SolveArgs scalp_ctx_args(const scalp_ctx *c) { return c->a; }
-CUtensorMap scalp_ctx_tmap(const scalp_ctx *c) { return c->tmap; }
 size_t scalp_ctx_smem(const scalp_ctx *c) { return c->smem; }
 void scalp_ctx_count_iteration(scalp_ctx *c) { c->iterations += 1; }
 
@@ -808,7 +757,6 @@ namespace {
 size_t batch_head_bytes(int count)
 {
     size_t cur = 0;
-    carve(cur, (size_t)count * sizeof(CUtensorMap));
     carve(cur, (size_t)count * sizeof(SolveArgs));
     for (int i = 0; i < 3; ++i) carve(cur, (size_t)(count + 1) * sizeof(int));
     carve(cur, (size_t)count * (sizeof(int) + sizeof(DevCounters)));
@@ -880,7 +828,6 @@ int scalp_batch_init(scalp_batch **out, int32_t count, const scalp_image *images
     b->use_graph = params->use_graph;
     b->ws = reinterpret_cast<unsigned char *>(params->workspace);
     size_t cur = 0;
-    const size_t o_tmaps = carve(cur, (size_t)count * sizeof(CUtensorMap));
     const size_t o_args = carve(cur, (size_t)count * sizeof(SolveArgs));
     const size_t o_tile = carve(cur, (size_t)(count + 1) * sizeof(int));
     const size_t o_clus = carve(cur, (size_t)(count + 1) * sizeof(int));
@@ -888,7 +835,6 @@ int scalp_batch_init(scalp_batch **out, int32_t count, const scalp_image *images
     const size_t o_gather = carve(cur, (size_t)count * (sizeof(int) + sizeof(DevCounters)));
     size_t off = batch_head_bytes(count);
     std::vector<SolveArgs> args(count);
-    std::vector<CUtensorMap> tmaps(count);
     std::vector<int> tile_base(count + 1, 0), clus_base(count + 1, 0), fill_base(count + 1, 0);
     for (int i = 0; i < count; ++i) {
         scalp_params p = *params;
@@ -906,7 +852,6 @@ int scalp_batch_init(scalp_batch **out, int32_t count, const scalp_image *images
         }
         b->ctx.push_back(c);
         args[i] = c->a;
-        tmaps[i] = c->tmap;
         tile_base[i + 1] = tile_base[i] + c->a.n_tx * c->a.n_ty;
         clus_base[i + 1] = clus_base[i] + c->Keff;
         fill_base[i + 1] = fill_base[i] + c->Keff * c->a.tpw_x * c->a.tpw_y;
@@ -916,17 +861,13 @@ int scalp_batch_init(scalp_batch **out, int32_t count, const scalp_image *images
     b->total_clusters = clus_base[count];
     b->total_fill = fill_base[count];
     b->bargs.args = reinterpret_cast<const SolveArgs *>(b->ws + o_args);
-    b->bargs.tmaps = reinterpret_cast<const CUtensorMap *>(b->ws + o_tmaps);
     b->bargs.tile_base = reinterpret_cast<const int *>(b->ws + o_tile);
     b->bargs.clus_base = reinterpret_cast<const int *>(b->ws + o_clus);
     b->bargs.fill_base = reinterpret_cast<const int *>(b->ws + o_fill);
     b->bargs.count = count;
     b->d_gather = reinterpret_cast<int *>(b->ws + o_gather);
-    cudaError_t e = cudaMemcpyAsync(b->ws + o_tmaps, tmaps.data(), count * sizeof(CUtensorMap),
+    cudaError_t e = cudaMemcpyAsync(b->ws + o_args, args.data(), count * sizeof(SolveArgs),
                                     cudaMemcpyHostToDevice, b->st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->ws + o_args, args.data(), count * sizeof(SolveArgs),
-                            cudaMemcpyHostToDevice, b->st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->ws + o_tile, tile_base.data(), (count + 1) * sizeof(int),
                             cudaMemcpyHostToDevice, b->st);
@@ -937,7 +878,7 @@ int scalp_batch_init(scalp_batch **out, int32_t count, const scalp_image *images
         e = cudaMemcpyAsync(b->ws + o_fill, fill_base.data(), (count + 1) * sizeof(int),
                             cudaMemcpyHostToDevice, b->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);  // host vectors go out of scope
-    if (e == cudaSuccess) e = assign_batch_configure(b->storage, b->smem);
+    if (e == cudaSuccess) e = assign_batch_configure(b->storage);
     if (e != cudaSuccess) {
         scalp_batch_destroy(b);
         return batch_fail(SCALP_E_CUDA, "batch set-up: %s", cudaGetErrorString(e));

@@ -7,27 +7,31 @@
 // clusters (those whose window holds it, from its tile's candidate list) and
 // keeps the smallest (D, k) pair: the same result, in any evaluation order.
 //
-// One CTA (1024 threads for FP32 planes, 512 for FP16) labels a 32 x 32 tile:
-//   1. One thread issues a TMA bulk-tensor load of the (L, a, b, w) plane of
-//      the tile plus a halo of round(r) + 2 pixels into shared memory (zero
-//      fill outside the image).  Every path to an endpoint inside that region
-//      is walked on-chip; a farther endpoint (a projected barycenter, Eq. 4)
-//      is walked in global memory with the same stepping rule.
-//   2. Meanwhile the tile's candidate clusters are copied to shared memory,
-//      sorted by cluster index.
+// One CTA of 512 threads (two per SM) labels a 32 x 32 tile:
+//   1. The tile's candidate clusters are copied to shared memory, sorted by
+//      cluster index.
+//   2. Distance maps.  For a candidate k, every path from a tile pixel in its
+//      window to its endpoint e_k lies in the bounding box of those pixels and
+//      e_k.  Over that box the CTA computes once the colour distance
+//      d_c(q, C_k) of Eq. 1 and the contour factor w(q) of Eq. 2 (an FP32
+//      pair per pixel, read from the (L, a, b, w) plane in global memory).
+//      The boxes of the candidates are packed in candidate order into the map
+//      buffer; a candidate whose box no longer fits walks the plane in global
+//      memory instead, with the same per-sample arithmetic and order.
 //   3. The pixels of the tile inside a candidate's window form a rectangle,
-//      cut into 8 x 4 blocks; each (candidate, block) is one work item, and
-//      warps take items from a shared-memory counter until none are left (no
-//      per-pixel scan of the candidate list, no idle warps at a barrier).
-//   4. Each lane walks its pixel's path to the candidate's endpoint, forms D
-//      (Eq. 1-3) and takes a 64-bit shared-memory atomicMin of (D bits,
-//      candidate slot) for its pixel; slots are in cluster order, so ties go
-//      to the smallest k.
-//   5. Each thread writes its pixel's label; warp-aggregated integer sums of
+//      cut into strips; each 32 consecutive pixels of a candidate are one
+//      work item, and warps take items from a shared-memory counter until
+//      none are left.
+//   4. Each lane walks its pixel's path to the candidate's endpoint (one
+//      8-byte map load and two adds per sample), forms D (Eq. 1-3) and takes
+//      a 64-bit shared-memory atomicMin of (D bits, candidate slot) for its
+//      pixel; slots are in cluster order, so ties go to the smallest k.
+//   5. Each thread writes its pixels' labels; warp-aggregated integer sums of
 //      (1, x, y, L, a, b) per label go to the global cluster sums as
 //      fire-and-forget reductions.
-// A tile with more candidates or pairs than shared memory holds evaluates
-// its pixels one by one from the global candidate list instead.
+// A tile with more candidates than shared memory holds evaluates its pixels
+// one by one from the global candidate list instead.
+#include <algorithm>
 #include <cfloat>
 #include <climits>
 
@@ -40,109 +44,36 @@ __device__ __forceinline__ uint32_t smem_u32(const void *p)
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
 
-// Waits on phase `parity` of an mbarrier for at most `max_polls` polls.
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, int max_polls)
+// One FP32 pair of a distance map, by 32-bit shared-memory byte address.
+__device__ __forceinline__ float2 lds_pair(uint32_t addr)
 {
-    for (int i = 0; i < max_polls; ++i) {
-        uint32_t done;
-        asm volatile(
-            "{\n\t.reg .pred p;\n\t"
-            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-            "selp.u32 %0, 1, 0, p;\n\t}"
-            : "=r"(done)
-            : "r"(bar), "r"(parity)
-            : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-template <typename T>
-__device__ __forceinline__ void tma_load_region(const CUtensorMap *tmap, uint32_t dst, uint32_t bar,
-                                                int rx0, int ry0);
-
-// FP32 planes: 2-D map {2W, H} of 8-byte elements (half a pixel each), box
-// {2BX, BY}: long contiguous rows per request; x = 2*rx0 is 16-byte aligned.
-template <>
-__device__ __forceinline__ void tma_load_region<float4>(const CUtensorMap *tmap, uint32_t dst,
-                                                        uint32_t bar, int rx0, int ry0)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%2, %3}], [%4];"
-        :
-        : "r"(dst), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(2 * rx0), "r"(ry0), "r"(bar)
-        : "memory");
-}
-
-// FP16 planes: 2-D map {W, H} of 8-byte pixels, box {BX, BY}; rx0 is even.
-template <>
-__device__ __forceinline__ void tma_load_region<uint2>(const CUtensorMap *tmap, uint32_t dst,
-                                                       uint32_t bar, int rx0, int ry0)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
-        "[%0], [%1, {%2, %3}], [%4];"
-        :
-        : "r"(dst), "l"(reinterpret_cast<uint64_t>(tmap)), "r"(rx0), "r"(ry0), "r"(bar)
-        : "memory");
-}
-
-// One sample of the staged plane, by 32-bit shared-memory byte address.
-template <typename T>
-__device__ __forceinline__ float4 lds_sample(uint32_t addr);
-template <>
-__device__ __forceinline__ float4 lds_sample<float4>(uint32_t addr)
-{
-    float4 v;
-    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
-                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
-                 : "r"(addr));
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
     return v;
 }
-template <>
-__device__ __forceinline__ float4 lds_sample<uint2>(uint32_t addr)
-{
-    uint2 u;
-    asm volatile("ld.shared.v2.u32 {%0, %1}, [%2];" : "=r"(u.x), "=r"(u.y) : "r"(addr));
-    __half2 lo = *reinterpret_cast<__half2 *>(&u.x);
-    __half2 hi = *reinterpret_cast<__half2 *>(&u.y);
-    float2 a = __half22float2(lo), b = __half22float2(hi);
-    return make_float4(a.x, a.y, b.x, b.y);
-}
 
-// Path sums of Eq. 1 and Eq. 2 over the staged region (row pitch BX elements,
-// element (0,0) = image pixel (rx0, ry0)).
-template <typename T>
-__device__ __forceinline__ int path_sums_smem(uint32_t region, int BX, int rx0, int ry0,
-                                              const PathSetup &s, float cL, float ca, float cb,
-                                              float &sum_dc, float &sum_w)
+// Path sums of Eq. 1 and Eq. 2 over a distance map (row pitch `bw` pairs,
+// pair (0,0) = image pixel (bx0, by0)).  The same samples, in the same order
+// and with the same FP32 additions, as path_sums over the plane.
+__device__ __forceinline__ int path_sums_map(uint32_t map, int bw, int bx0, int by0,
+                                             const PathSetup &s, float &sum_dc, float &sum_w)
 {
     int smaj, smin;
-    path_strides(s, BX, smaj, smin);
-    const uint32_t q0 = region + (uint32_t)(((s.ay - ry0) * BX + (s.ax - rx0)) * (int)sizeof(T));
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, bw = 0.f;
-    int len = walk_steps(q0, smaj * (int)sizeof(T), smin * (int)sizeof(T), s, [&](uint32_t q) {
-        float4 v = lds_sample<T>(q);
-        float dl = v.x - cL, da = v.y - ca, db = v.z - cb;
-        a0 = fmaf(dl, dl, a0);
-        a1 = fmaf(da, da, a1);
-        a2 = fmaf(db, db, a2);
-        bw += v.w;
+    path_strides(s, bw, smaj, smin);
+    const uint32_t q0 = map + (uint32_t)(((s.ay - by0) * bw + (s.ax - bx0)) * 8);
+    float dc = 0.f, w = 0.f;
+    int len = walk_steps(q0, smaj * 8, smin * 8, s, [&](uint32_t q) {
+        const float2 v = lds_pair(q);
+        dc += v.x;
+        w += v.y;
     });
-    sum_dc = (a0 + a1) + a2;
-    sum_w = bw;
+    sum_dc = dc;
+    sum_w = w;
     return len;
 }
 
-__host__ __device__ inline size_t region_bytes(int halo, int elem)
-{
-    size_t bx = TILE_X + 2 * halo, by = TILE_Y + 2 * halo;
-    return (bx * by * elem + 127) & ~(size_t)127;
-}
-
-// Shared-memory layout after the staged region; every section starts on a
-// 16-byte boundary (int4 loads, 8-byte atomics and the mbarrier need it).
+// Shared-memory layout; every section starts on a 16-byte boundary (int4
+// loads and 8-byte atomics need it); the distance maps fill the rest.
 constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
 constexpr int STRIP = 4;  // items run along strips STRIP pixels wide
 constexpr int MAX_ITEMS = MAX_TILE_CANDIDATES * (TILE_PIXELS / 32);
@@ -152,45 +83,92 @@ constexpr int STRIP_RCP_BITS = 20;
 static_assert((long long)TILE_PIXELS * STRIP * (TILE_X > TILE_Y ? TILE_X : TILE_Y) <
                   (1LL << STRIP_RCP_BITS),
               "exact strip index");
+// Per candidate (rank c): three 16-byte records the walk reads,
+//   rec0 = (xa, ya, w | h << 8 | vert << 16, strip reciprocal)  its rectangle
+//   rec1 = (ex, ey, xk bits, yk bits)                           endpoint, X_k
+//   rec2 = (bx0, by0, pitch, map byte offset, or -1: walk the plane)
+// the map box for the build, box = (bx0, by0, pitch, 32-bit reciprocal of
+// the pitch), and the colour C_k, col = (l_k, a_k, b_k, 0).
 struct AssignSmem {
-    static constexpr size_t cand = 0;
-    static constexpr size_t cid = align16(cand + MAX_TILE_CANDIDATES * sizeof(ClusterDev));
-    static constexpr size_t rect = align16(cid + MAX_TILE_CANDIDATES * sizeof(int));
-    static constexpr size_t meta = align16(rect + MAX_TILE_CANDIDATES * sizeof(int4));
-    static constexpr size_t nit = align16(meta + MAX_TILE_CANDIDATES * sizeof(int2));
-    static constexpr size_t best = align16(nit + MAX_TILE_CANDIDATES * sizeof(int));
+    static constexpr size_t rec0 = 0;
+    static constexpr size_t rec1 = align16(rec0 + MAX_TILE_CANDIDATES * sizeof(int4));
+    static constexpr size_t rec2 = align16(rec1 + MAX_TILE_CANDIDATES * sizeof(int4));
+    static constexpr size_t box = align16(rec2 + MAX_TILE_CANDIDATES * sizeof(int4));
+    static constexpr size_t col = align16(box + MAX_TILE_CANDIDATES * sizeof(int4));
+    static constexpr size_t cid = align16(col + MAX_TILE_CANDIDATES * sizeof(float4));
+    static constexpr size_t nit = align16(cid + MAX_TILE_CANDIDATES * sizeof(int));
+    static constexpr size_t area = align16(nit + MAX_TILE_CANDIDATES * sizeof(int));
+    static constexpr size_t best = align16(area + MAX_TILE_CANDIDATES * sizeof(int));
     static constexpr size_t first = align16(best + TILE_PIXELS * sizeof(unsigned long long));
-    static constexpr size_t owner = align16(first + (MAX_TILE_CANDIDATES + 1) * sizeof(int));
+    static constexpr size_t mfirst = align16(first + (MAX_TILE_CANDIDATES + 1) * sizeof(int));
+    static constexpr size_t owner = align16(mfirst + (MAX_TILE_CANDIDATES + 1) * sizeof(int));
     static constexpr size_t misc = align16(owner + MAX_ITEMS);
-    static constexpr size_t total = align16(misc + 64);
+    static constexpr size_t maps = align16(misc + 64);
 };
-static_assert(AssignSmem::cid % 16 == 0 && AssignSmem::rect % 16 == 0 && AssignSmem::meta % 16 == 0 &&
-                  AssignSmem::nit % 16 == 0 &&
-                  AssignSmem::best % 16 == 0 && AssignSmem::first % 16 == 0 &&
+static_assert(AssignSmem::rec1 % 16 == 0 && AssignSmem::rec2 % 16 == 0 && AssignSmem::col % 16 == 0 &&
+                  AssignSmem::cid % 16 == 0 && AssignSmem::nit % 16 == 0 && AssignSmem::box % 16 == 0 &&
+                  AssignSmem::area % 16 == 0 && AssignSmem::best % 16 == 0 &&
+                  AssignSmem::first % 16 == 0 && AssignSmem::mfirst % 16 == 0 &&
                   AssignSmem::owner % 16 == 0 && AssignSmem::misc % 16 == 0 &&
-                  (AssignSmem::misc + 32) % 8 == 0,
+                  AssignSmem::maps % 16 == 0,
               "shared-memory sections aligned");
 static_assert(MAX_TILE_CANDIDATES <= 256, "item owners are bytes");
-static_assert(MAX_TILE_CANDIDATES % 32 == 0, "the item scan gives each lane whole candidates");
+static_assert(MAX_TILE_CANDIDATES % 32 == 0, "the scans give each lane whole candidates");
 
-size_t assign_smem_bytes(int halo, int storage)
+size_t assign_smem_bytes(int map_cap) { return AssignSmem::maps + (size_t)map_cap * sizeof(float2); }
+
+// Map capacity (pairs) when ASSIGN_CTAS_PER_SM CTAs share an SM's shared memory.
+int assign_map_capacity(int device)
 {
-    size_t elem = storage == 0 ? 16 : 8;
-    size_t r = halo > 0 ? region_bytes(halo, (int)elem) : 0;
-    return r + AssignSmem::total;
+    int per_sm = 0, per_cta_max = 0, reserved = 0;
+    if (cudaDeviceGetAttribute(&per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&per_cta_max, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) !=
+            cudaSuccess ||
+        cudaDeviceGetAttribute(&reserved, cudaDevAttrReservedSharedMemoryPerBlock, device) !=
+            cudaSuccess)
+        return 0;
+    long long per_cta = std::min((long long)per_cta_max,
+                                 (long long)per_sm / ASSIGN_CTAS_PER_SM - reserved);
+    per_cta &= ~15LL;
+    const long long cap = (per_cta - (long long)AssignSmem::maps) / (long long)sizeof(float2);
+    return cap > 0 ? (int)cap : 0;
 }
-
-// Threads per CTA: FP32 tiles use one 1024-thread CTA per SM (the staged
-// region fills shared memory); FP16 tiles use 512-thread CTAs, two per SM, so
-// one CTA's set-up and tail overlap the other's walks.
-int assign_threads(int storage) { return storage == 0 ? 1024 : 512; }
-
-constexpr int MBAR_MAX_POLLS = 1 << 22;
 
 __device__ __forceinline__ unsigned long long pack_best(float D, int slot)
 {
     // D >= 0, so its IEEE bits order like the value; ties fall to the slot
     return ((unsigned long long)__float_as_uint(D) << 32) | (unsigned)slot;
+}
+
+// Exclusive prefix of cnt <= MAX_TILE_CANDIDATES counts by one warp: out[c]
+// for c < cnt and the total in out[cnt].  Returns the largest prefix end
+// that stays <= cap (the leading candidates that fit a buffer of cap).
+__device__ __forceinline__ int warp_scan_counts(const int *in, int *out, int cnt, int cap, int lane)
+{
+    constexpr int PER = MAX_TILE_CANDIDATES / 32;
+    int v[PER], sum = 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int c = lane * PER + i;
+        v[i] = c < cnt ? in[c] : 0;
+        sum += v[i];
+    }
+    int incl = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    int run = incl - sum, fit = 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int c = lane * PER + i;
+        if (c < cnt) out[c] = run;
+        run += v[i];
+        if (c < cnt && run <= cap) fit = run;
+    }
+    if (lane == 31) out[cnt] = incl;
+    return (int)__reduce_max_sync(0xffffffffu, (unsigned)fit);
 }
 
 // Items: the pixels of a candidate's window that lie in the tile form a
@@ -202,48 +180,35 @@ __device__ __forceinline__ unsigned long long pack_best(float D, int slot)
 // So a warp's pixels lie in a few neighbouring columns (rows), where the path
 // lengths differ little, and only the last item of a rectangle has idle lanes.
 // One tile of one image (the body shared by the single-image and the batched
-// kernels).  `tmap` is the image's tensor map (kernel parameter or global).
-template <typename T, bool STAGED, int THREADS>
-__device__ __forceinline__ void assign_tile(const SolveArgs &a, const CUtensorMap *tmap, int tile,
-                                            unsigned char *smem)
+// kernels).
+template <typename T>
+__device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsigned char *smem)
 {
+    constexpr int THREADS = ASSIGN_THREADS;
     constexpr int PIX_PER_THREAD = TILE_PIXELS / THREADS;
     constexpr int WARPS = THREADS / 32;
+    constexpr int BUILD_UNROLL = 4;
     const T *__restrict__ plane = reinterpret_cast<const T *>(
         sizeof(T) == 16 ? (const void *)a.plane32 : (const void *)a.plane16);
     const int tx = tile % a.n_tx, ty = tile / a.n_tx;
     const int x0 = tx * TILE_X, y0 = ty * TILE_Y;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    const int halo = STAGED ? a.halo : 0;
-    const int BX = TILE_X + 2 * halo, BY = TILE_Y + 2 * halo;
-    const int rx0 = x0 - halo, ry0 = y0 - halo;
-    const size_t rbytes = STAGED ? region_bytes(halo, sizeof(T)) : 0;
-    unsigned char *sm = smem + rbytes;
-    const uint32_t region = smem_u32(smem);
-    ClusterDev *cand = reinterpret_cast<ClusterDev *>(sm + AssignSmem::cand);
-    int *cid = reinterpret_cast<int *>(sm + AssignSmem::cid);
-    int4 *rect = reinterpret_cast<int4 *>(sm + AssignSmem::rect);
-    int2 *meta = reinterpret_cast<int2 *>(sm + AssignSmem::meta);
-    int *nit = reinterpret_cast<int *>(sm + AssignSmem::nit);
-    unsigned long long *best = reinterpret_cast<unsigned long long *>(sm + AssignSmem::best);
-    int *first = reinterpret_cast<int *>(sm + AssignSmem::first);
-    unsigned char *owner = sm + AssignSmem::owner;
-    int *misc = reinterpret_cast<int *>(sm + AssignSmem::misc);
-    uint64_t *mbar = reinterpret_cast<uint64_t *>(sm + AssignSmem::misc + 32);
-
-    if (STAGED && tid == 0) {
-        uint32_t bar = smem_u32(mbar);
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(bar) : "memory");
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        uint32_t bytes = (uint32_t)(BX * BY * sizeof(T));
-        asm volatile(
-            "{\n\t.reg .b64 st;\n\t"
-            "mbarrier.arrive.expect_tx.shared::cta.b64 st, [%0], %1;\n\t}" ::"r"(bar),
-            "r"(bytes)
-            : "memory");
-        tma_load_region<T>(tmap, region, bar, rx0, ry0);
-    }
+    int4 *rec0 = reinterpret_cast<int4 *>(smem + AssignSmem::rec0);
+    int4 *rec1 = reinterpret_cast<int4 *>(smem + AssignSmem::rec1);
+    int4 *rec2 = reinterpret_cast<int4 *>(smem + AssignSmem::rec2);
+    int4 *box = reinterpret_cast<int4 *>(smem + AssignSmem::box);
+    float4 *col = reinterpret_cast<float4 *>(smem + AssignSmem::col);
+    int *cid = reinterpret_cast<int *>(smem + AssignSmem::cid);
+    int *nit = reinterpret_cast<int *>(smem + AssignSmem::nit);
+    int *area = reinterpret_cast<int *>(smem + AssignSmem::area);
+    unsigned long long *best = reinterpret_cast<unsigned long long *>(smem + AssignSmem::best);
+    int *first = reinterpret_cast<int *>(smem + AssignSmem::first);
+    int *mfirst = reinterpret_cast<int *>(smem + AssignSmem::mfirst);
+    unsigned char *owner = smem + AssignSmem::owner;
+    int *misc = reinterpret_cast<int *>(smem + AssignSmem::misc);
+    float2 *maps = reinterpret_cast<float2 *>(smem + AssignSmem::maps);
+    const uint32_t maps_u32 = smem_u32(maps);
 
     const int off = a.tile_off[tile];
     // the list capacity is a proven bound; the clamp only guards memory if the
@@ -266,64 +231,99 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, const CUtensorMa
         for (int j = 0; j < cnt; ++j) rank += ids[j] < myid;
         const ClusterDev cd = a.cdev[myid];
         cid[rank] = myid;
-        cand[rank] = cd;
         // window x tile (clipped to the image), cut into strips
         const int xa = max(cd.xlo, x0), xb = min(min(cd.xhi, x0 + TILE_X - 1), a.W - 1);
         const int ya = max(cd.ylo, y0), yb = min(min(cd.yhi, y0 + TILE_Y - 1), a.H - 1);
         const int w = max(xb - xa + 1, 0), h = max(yb - ya + 1, 0);
         const bool vert = abs(xa + xb - 2 * cd.ex) >= abs(ya + yb - 2 * cd.ey);
         const int slen = max(vert ? h : w, 1);  // pixels along one strip
-        const bool inside = STAGED && cd.ex >= rx0 && cd.ex < rx0 + BX && cd.ey >= ry0 &&
-                            cd.ey < ry0 + BY;
-        rect[rank] = make_int4(xa, ya, w, h);
-        // strip direction and endpoint-in-region flags, reciprocal of the
-        // pixels per full strip
-        meta[rank] = make_int2((int)vert | ((int)inside << 1),
+        rec0[rank] = make_int4(xa, ya, w | (h << 8) | ((int)vert << 16),
                                ((1 << STRIP_RCP_BITS) + STRIP * slen - 1) / (STRIP * slen));
+        rec1[rank] = make_int4(cd.ex, cd.ey, __float_as_int(cd.xk), __float_as_int(cd.yk));
+        col[rank] = make_float4(cd.L, cd.a, cd.b, 0.f);
         nit[rank] = (w * h + 31) >> 5;
+        // map box: the rectangle and the endpoint (both inside the image).
+        // Rows are padded to a pitch = 4 (mod 8) pairs: the walks of a warp
+        // then spread over the shared-memory banks (neighbouring rows start
+        // 8 banks apart); 32-bit reciprocal of the pitch for the build.
+        int bx0 = 0, by0 = 0, pitch = 1;
+        long long n = 0;
+        if (w > 0 && h > 0) {
+            bx0 = min(xa, cd.ex);
+            by0 = min(ya, cd.ey);
+            const int bw = max(xb, cd.ex) - bx0 + 1;
+            pitch = bw + ((4 - bw) & 7);
+            n = (long long)pitch * (max(yb, cd.ey) - by0 + 1);
+        }
+        const unsigned rcp = (unsigned)((0x100000000ULL + pitch - 1) / pitch);
+        box[rank] = make_int4(bx0, by0, pitch, (int)rcp);
+        // a box larger than the whole buffer never fits: clamp it so that the
+        // prefix sums stay small
+        area[rank] = a.map_cap > 0 ? (int)min(n, (long long)a.map_cap + 1) : 0;
     }
     __syncthreads();
     for (int i = tid; i < TILE_PIXELS; i += THREADS) best[i] = ~0ull;
-    if (warp == 0 && fast) {
-        // exclusive prefix of the per-candidate block counts (4 per lane)
-        constexpr int PER = MAX_TILE_CANDIDATES / 32;
-        int v[PER], sum = 0;
-#pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            const int c = lane * PER + i;
-            v[i] = c < cnt ? nit[c] : 0;
-            sum += v[i];
-        }
-        int incl = sum;
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        int run = incl - sum;
-#pragma unroll
-        for (int i = 0; i < PER; ++i) {
-            const int c = lane * PER + i;
-            if (c < cnt) first[c] = run;
-            run += v[i];
-        }
-        if (lane == 31) first[cnt] = incl;
+    if (warp == 0 && fast) warp_scan_counts(nit, first, cnt, INT_MAX, lane);
+    if (warp == 1 && fast) {
+        const int used = warp_scan_counts(area, mfirst, cnt, a.map_cap, lane);
+        if (lane == 0) misc[2] = used;
     }
     __syncthreads();
-    if (fast && tid < cnt) {
-        const int f = first[tid], n = nit[tid];
-        for (int j = 0; j < n; ++j) owner[f + j] = (unsigned char)tid;
-    }
 
-    bool staged_ok = true;
-    if (STAGED) {
-        staged_ok = mbar_wait_bounded(smem_u32(mbar), 0, MBAR_MAX_POLLS);
-        if (!staged_ok) {
-            if (tid == 0) atomicExch(&a.ctr->timeout, 1);
-            // let the copy land (bounded) before the CTA releases its memory
-            mbar_wait_bounded(smem_u32(mbar), 0, MBAR_MAX_POLLS);
+    // the distance maps of the candidates whose boxes fit: entries [0, used)
+    // hold the leading candidates' boxes back to back, row-major; the
+    // padding columns of a row are left unwritten (no walk reads them)
+    const int used = fast ? misc[2] : 0;
+    if (fast) {
+        if (tid < cnt) {
+            const int f = first[tid], n = nit[tid];
+            for (int j = 0; j < n; ++j) owner[f + j] = (unsigned char)tid;
+            const int4 b = box[tid];
+            const bool mapped = area[tid] > 0 && mfirst[tid + 1] <= used;
+            rec2[tid] = make_int4(b.x, b.y, b.z, mapped ? mfirst[tid] * (int)sizeof(float2) : -1);
+        }
+        int c = -1, c_begin = 0, c_end = 0;  // the current candidate's entries
+        int4 b = make_int4(0, 0, 1, 0);
+        int bw = 1;
+        for (int e0 = tid; e0 < used; e0 += BUILD_UNROLL * THREADS) {
+            float4 v[BUILD_UNROLL];
+            int ec[BUILD_UNROLL];
+#pragma unroll
+            for (int u = 0; u < BUILD_UNROLL; ++u) {
+                const int e = e0 + u * THREADS;
+                ec[u] = -1;
+                if (e < used) {
+                    if (e >= c_end) {
+                        do {
+                            ++c;
+                            c_end = mfirst[c + 1];
+                        } while (e >= c_end);
+                        c_begin = mfirst[c];
+                        b = box[c];
+                        // unpadded width: from the rectangle's right edge and e_k
+                        const int4 r0 = rec0[c];
+                        bw = max(r0.x + (r0.z & 0xff) - 1, rec1[c].x) - b.x + 1;
+                    }
+                    const int le = e - c_begin;
+                    // le * pitch < 2^32, so the 32-bit reciprocal gives the exact row
+                    const int row = b.z > 1 ? (int)__umulhi((unsigned)le, (unsigned)b.w) : le;
+                    const int cx = le - row * b.z;
+                    if (cx < bw) {
+                        v[u] = fetch_sample<T>(plane + (long long)(b.y + row) * a.pitch + (b.x + cx));
+                        ec[u] = c;
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < BUILD_UNROLL; ++u) {
+                if (ec[u] >= 0) {
+                    const float4 ck = col[ec[u]];
+                    maps[e0 + u * THREADS] = make_float2(colour_dist(v[u], ck.x, ck.y, ck.z), v[u].w);
+                }
+            }
         }
     }
-    if (!__syncthreads_and(staged_ok)) return;
+    __syncthreads();
 
     unsigned long long my_samples = 0, my_pairs = 0;
     int bestk[PIX_PER_THREAD];  // per-pixel path only
@@ -345,36 +345,36 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, const CUtensorMa
             item = __shfl_sync(0xffffffffu, item, 0);
             if (item >= n_items) break;
             const int c = owner[item];
-            const int4 rc = rect[c];
-            const int2 mt = meta[c];
+            const int4 r0 = rec0[c];
+            const int rw = r0.z & 0xff, rh = (r0.z >> 8) & 0xff;
             const int j = ((item - first[c]) << 5) + lane;  // pixel of the rectangle
-            if (j >= rc.z * rc.w) continue;
-            const bool vert = (mt.x & 1) != 0;
-            const int slen = vert ? rc.w : rc.z, across = vert ? rc.z : rc.w;
-            const int strip = (j * mt.y) >> STRIP_RCP_BITS;
+            if (j >= rw * rh) continue;
+            const bool vert = (r0.z >> 16) != 0;
+            const int slen = vert ? rh : rw, across = vert ? rw : rh;
+            const int strip = (j * r0.w) >> STRIP_RCP_BITS;
             const int t = j - strip * STRIP * slen;
             // t / width for a strip 1..4 wide: exact 16-bit reciprocals
             const int width = min(STRIP, across - strip * STRIP);
             const int along = (t * (width == 3 ? 21846 : 65536 >> (width >> 1))) >> 16;
-            const int off = strip * STRIP + (t - along * width);
-            const int qx = rc.x + (vert ? off : along);
-            const int qy = rc.y + (vert ? along : off);
-            const ClusterDev cd = cand[c];
-            const PathSetup s = path_setup(qx, qy, cd.ex, cd.ey);
-            const bool inside = (mt.x >> 1) != 0;
-            float sdc, sw;
+            const int offs = strip * STRIP + (t - along * width);
+            const int qx = r0.x + (vert ? offs : along);
+            const int qy = r0.y + (vert ? along : offs);
+            const int4 r1 = rec1[c];
+            const int4 r2 = rec2[c];
+            const PathSetup s = path_setup(qx, qy, r1.x, r1.y);
+            float sdc, sw, dcp;
             int len;
-            float4 v;
-            if (inside) {
-                len = path_sums_smem<T>(region, BX, rx0, ry0, s, cd.L, cd.a, cd.b, sdc, sw);
-                v = lds_sample<T>(region + (uint32_t)(((qy - ry0) * BX + (qx - rx0)) * (int)sizeof(T)));
+            if (r2.w >= 0) {
+                const uint32_t map = maps_u32 + (uint32_t)r2.w;
+                len = path_sums_map(map, r2.z, r2.x, r2.y, s, sdc, sw);
+                dcp = lds_pair(map + (uint32_t)(((qy - r2.y) * r2.z + (qx - r2.x)) * 8)).x;
             } else {
-                len = path_sums<T>(plane, a.pitch, 0, 0, s, cd.L, cd.a, cd.b, sdc, sw);
-                v = fetch_sample<T>(plane + (long long)qy * a.pitch + qx);
+                const float4 ck = col[c];
+                len = path_sums<T>(plane, a.pitch, 0, 0, s, ck.x, ck.y, ck.z, sdc, sw);
+                dcp = colour_dist(fetch_sample<T>(plane + (long long)qy * a.pitch + qx), ck.x, ck.y,
+                                  ck.z);
             }
-            const float dl = v.x - cd.L, da = v.y - cd.a, db = v.z - cd.b;
-            const float dcp = fmaf(dl, dl, fmaf(da, da, db * db));
-            const float ddx = (float)qx - cd.xk, ddy = (float)qy - cd.yk;
+            const float ddx = (float)qx - __int_as_float(r1.z), ddy = (float)qy - __int_as_float(r1.w);
             const float ds = fmaf(ddx, ddx, ddy * ddy);
             const float D = scalp_distance(dcp, sdc, sw, len, a.lam, a.gamma, a.ms2, ds);
             atomicMin(&best[(qy - y0) * TILE_X + (qx - x0)], pack_best(D, c));
@@ -388,21 +388,16 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, const CUtensorMa
             int px, py;
             my_pixel(j, px, py);
             if (px >= a.W || py >= a.H) continue;
-            const float4 own = STAGED ? lds_sample<T>(region + (uint32_t)(((py - ry0) * BX + (px - rx0)) * (int)sizeof(T)))
-                                      : fetch_sample<T>(plane + (long long)py * a.pitch + px);
+            const float4 own = fetch_sample<T>(plane + (long long)py * a.pitch + px);
             float bestD = FLT_MAX;
             for (int i = 0; i < cnt; ++i) {
                 const int k = a.tile_list[off + i];
                 const ClusterDev cd = a.cdev[k];
                 if (px < cd.xlo || px > cd.xhi || py < cd.ylo || py > cd.yhi) continue;
                 const PathSetup s = path_setup(px, py, cd.ex, cd.ey);
-                const bool inside = STAGED && cd.ex >= rx0 && cd.ex < rx0 + BX && cd.ey >= ry0 &&
-                                    cd.ey < ry0 + BY;
                 float sdc, sw;
-                const int len = inside ? path_sums_smem<T>(region, BX, rx0, ry0, s, cd.L, cd.a, cd.b, sdc, sw)
-                                       : path_sums<T>(plane, a.pitch, 0, 0, s, cd.L, cd.a, cd.b, sdc, sw);
-                const float dl = own.x - cd.L, da = own.y - cd.a, db = own.z - cd.b;
-                const float dcp = fmaf(dl, dl, fmaf(da, da, db * db));
+                const int len = path_sums<T>(plane, a.pitch, 0, 0, s, cd.L, cd.a, cd.b, sdc, sw);
+                const float dcp = colour_dist(own, cd.L, cd.a, cd.b);
                 const float ddx = (float)px - cd.xk, ddy = (float)py - cd.yk;
                 const float ds = fmaf(ddx, ddx, ddy * ddy);
                 const float D = scalp_distance(dcp, sdc, sw, len, a.lam, a.gamma, a.ms2, ds);
@@ -427,8 +422,7 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, const CUtensorMa
         float4 own = make_float4(0.f, 0.f, 0.f, 0.f);
         int lab = -1;
         if (valid) {
-            own = STAGED ? lds_sample<T>(region + (uint32_t)(((py - ry0) * BX + (px - rx0)) * (int)sizeof(T)))
-                         : fetch_sample<T>(plane + (long long)py * a.pitch + px);
+            own = fetch_sample<T>(plane + (long long)py * a.pitch + px);
             if (fast) {
                 const unsigned long long b = best[(py - y0) * TILE_X + (px - x0)];
                 if (b != ~0ull) lab = cid[(int)(b & 0xffffffffu)];
@@ -455,71 +449,72 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, const CUtensorMa
             atomicAdd(&a.ctr->samples, my_samples);
             atomicAdd(&a.ctr->pairs, my_pairs);
         }
+        // (candidate, tile) rectangles walked on a map and on the plane
+        if (tid == 0) {
+            unsigned long long on_map = 0, on_plane = 0;
+            for (int c = 0; c < cnt; ++c) {
+                if (fast && nit[c] == 0) continue;
+                if (fast && rec2[c].w >= 0) ++on_map;
+                else ++on_plane;
+            }
+            atomicAdd(&a.ctr->map_rects, on_map);
+            atomicAdd(&a.ctr->plane_rects, on_plane);
+        }
     }
 }
 
-template <typename T, bool STAGED, int THREADS>
-__global__ void __launch_bounds__(THREADS, 1024 / THREADS)
-    k_assign(SolveArgs a, const __grid_constant__ CUtensorMap tmap)
+template <typename T>
+__global__ void __launch_bounds__(ASSIGN_THREADS, ASSIGN_CTAS_PER_SM) k_assign(SolveArgs a)
 {
-    extern __shared__ __align__(1024) unsigned char smem[];
-    assign_tile<T, STAGED, THREADS>(a, &tmap, blockIdx.x, smem);
+    extern __shared__ __align__(16) unsigned char smem[];
+    assign_tile<T>(a, blockIdx.x, smem);
 }
 
 // All tiles of all images of a batch in one launch: block g is tile
 // g - tile_base[i] of image i, tile_base being the prefix of tile counts.
-template <typename T, int THREADS>
-__global__ void __launch_bounds__(THREADS, 1024 / THREADS) k_assign_batch(BatchArgs b)
+template <typename T>
+__global__ void __launch_bounds__(ASSIGN_THREADS, ASSIGN_CTAS_PER_SM) k_assign_batch(BatchArgs b)
 {
-    extern __shared__ __align__(1024) unsigned char smem[];
+    extern __shared__ __align__(16) unsigned char smem[];
     const int g = blockIdx.x;
     const int i = batch_find(b.tile_base, b.count, g);
-    const SolveArgs &a = b.args[i];
-    if (a.halo > 0) assign_tile<T, true, THREADS>(a, &b.tmaps[i], g - b.tile_base[i], smem);
-    else assign_tile<T, false, THREADS>(a, &b.tmaps[i], g - b.tile_base[i], smem);
+    assign_tile<T>(b.args[i], g - b.tile_base[i], smem);
 }
 
-template <typename T, bool STAGED, int THREADS>
-static void launch_one(const SolveArgs &a, const CUtensorMap &tmap, size_t smem, cudaStream_t st)
+void launch_assign(const SolveArgs &a, int storage, size_t smem_bytes, cudaStream_t st)
 {
-    k_assign<T, STAGED, THREADS><<<a.n_tx * a.n_ty, THREADS, smem, st>>>(a, tmap);
-}
-
-void launch_assign(const SolveArgs &a, int storage, bool staged, const CUtensorMap &tmap,
-                   size_t smem_bytes, cudaStream_t st)
-{
-    if (storage == 0) {
-        if (staged) launch_one<float4, true, 1024>(a, tmap, smem_bytes, st);
-        else launch_one<float4, false, 1024>(a, tmap, smem_bytes, st);
-    } else {
-        if (staged) launch_one<uint2, true, 512>(a, tmap, smem_bytes, st);
-        else launch_one<uint2, false, 512>(a, tmap, smem_bytes, st);
-    }
+    const int tiles = a.n_tx * a.n_ty;
+    if (storage == 0) k_assign<float4><<<tiles, ASSIGN_THREADS, smem_bytes, st>>>(a);
+    else k_assign<uint2><<<tiles, ASSIGN_THREADS, smem_bytes, st>>>(a);
 }
 
 void launch_assign_batch(const BatchArgs &b, int storage, int total_tiles, size_t smem_bytes,
                          cudaStream_t st)
 {
     if (total_tiles <= 0) return;
-    if (storage == 0) k_assign_batch<float4, 1024><<<total_tiles, 1024, smem_bytes, st>>>(b);
-    else k_assign_batch<uint2, 512><<<total_tiles, 512, smem_bytes, st>>>(b);
+    if (storage == 0) k_assign_batch<float4><<<total_tiles, ASSIGN_THREADS, smem_bytes, st>>>(b);
+    else k_assign_batch<uint2><<<total_tiles, ASSIGN_THREADS, smem_bytes, st>>>(b);
 }
 
-cudaError_t assign_batch_configure(int storage, size_t smem_bytes)
+// The limit is a property of the kernel, shared by every context on the
+// device: it is always set to the full map buffer, which covers any launch.
+static cudaError_t configure(const void *f)
 {
-    const void *f = storage == 0 ? (const void *)k_assign_batch<float4, 1024>
-                                 : (const void *)k_assign_batch<uint2, 512>;
-    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)assign_smem_bytes(assign_map_capacity(dev)));
 }
 
-cudaError_t assign_configure(int storage, bool staged, size_t smem_bytes)
+cudaError_t assign_batch_configure(int storage)
 {
-    const void *f;
-    if (storage == 0)
-        f = staged ? (const void *)k_assign<float4, true, 1024> : (const void *)k_assign<float4, false, 1024>;
-    else
-        f = staged ? (const void *)k_assign<uint2, true, 512> : (const void *)k_assign<uint2, false, 512>;
-    return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_bytes);
+    return configure(storage == 0 ? (const void *)k_assign_batch<float4> : (const void *)k_assign_batch<uint2>);
+}
+
+cudaError_t assign_configure(int storage)
+{
+    return configure(storage == 0 ? (const void *)k_assign<float4> : (const void *)k_assign<uint2>);
 }
 
 }  // namespace scalp

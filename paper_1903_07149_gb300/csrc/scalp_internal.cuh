@@ -20,9 +20,10 @@ constexpr int WARP_BLOCK_Y = 4;
 // Candidate clusters of one tile held in shared memory.  A tile with more
 // candidates (never seen on the regular grid) takes a slower per-pixel path.
 constexpr int MAX_TILE_CANDIDATES = 128;
-// Extra halo beyond round(r) so that endpoints projected by Eq. 4 a pixel or
-// two from the barycenter still walk in shared memory.
-constexpr int HALO_MARGIN = 2;
+// Assignment CTAs: 512 threads, two per SM (one CTA's set-up, map building
+// and tail overlap the other's path walks).
+constexpr int ASSIGN_THREADS = 512;
+constexpr int ASSIGN_CTAS_PER_SM = 2;
 // Colour sums are kept as integers: value * 2^COLOR_FRAC_BITS, rounded.  CIELab
 // of 8-bit sRGB has |L|, |a|, |b| < 108, so 32 such values sum below 2^31.
 constexpr int COLOR_FRAC_BITS = 19;
@@ -52,6 +53,8 @@ struct DevCounters {
     int timeout;      // nonzero: a bounded wait gave up
     unsigned long long samples;  // optional: path samples of the last assignment
     unsigned long long pairs;    // optional: (pixel, cluster) pairs evaluated
+    unsigned long long map_rects;    // optional: (tile, cluster) rectangles walked on a map
+    unsigned long long plane_rects;  // optional: ... walked on the plane in global memory
 };
 constexpr int ERR_TILE_LIST_OVERFLOW = 1;
 constexpr int ERR_BAD_LABEL = 2;
@@ -64,7 +67,7 @@ struct SolveArgs {
     double r;          // sqrt(N/K)
     float lam, gamma, sigma, ms2;  // ms2 = m^2 / r^2
     int n_tx, n_ty;    // tiles
-    int halo;          // shared-memory halo (0: global-memory walk)
+    int map_cap;       // distance-map pairs per assignment CTA (0: every path on the plane)
     int pitch;         // plane row pitch in pixels (>= W, multiple of 4)
     int count_samples;
     const float4 *plane32;   // (L, a, b, w) per pixel, row pitch `pitch` [FP32 storage]
@@ -84,12 +87,10 @@ struct SolveArgs {
     DevCounters *ctr;
 };
 
-// A batch: the argument blocks and tensor maps of `count` images in device
-// memory, and prefix sums that map a flat index (tile, cluster, fill slot) to
-// its image.
+// A batch: the argument blocks of `count` images in device memory, and prefix
+// sums that map a flat index (tile, cluster, fill slot) to its image.
 struct BatchArgs {
     const SolveArgs *args;
-    const CUtensorMap *tmaps;
     const int *tile_base;   // count+1: prefix of n_tx*n_ty
     const int *clus_base;   // count+1: prefix of Keff
     const int *fill_base;   // count+1: prefix of Keff*tpw_x*tpw_y
@@ -195,24 +196,29 @@ __device__ __forceinline__ int walk_path(const T *__restrict__ base, int pitch, 
     return walk_steps(q, smaj, smin, s, visit);
 }
 
+// Squared CIELab distance d_c(q, C_k) of Eq. 1 between a sample and a
+// cluster colour, in one fixed FP32 order (every walker and map uses it).
+__device__ __forceinline__ float colour_dist(float4 v, float cL, float ca, float cb)
+{
+    const float dl = v.x - cL, da = v.y - ca, db = v.z - cb;
+    return fmaf(dl, dl, fmaf(da, da, db * db));
+}
+
 // Sums along the path of d_c(q, C_k) (Eq. 1) and of the contour factor w(q)
-// (Eq. 2).  Returns |P|.
+// (Eq. 2), in walk order.  Returns |P|.
 template <typename T>
 __device__ __forceinline__ int path_sums(const T *__restrict__ base, int pitch, int ox, int oy,
                                          const PathSetup &s, float cL, float ca, float cb,
                                          float &sum_dc, float &sum_w)
 {
-    float a0 = 0.f, a1 = 0.f, a2 = 0.f, bw = 0.f;
+    float dc = 0.f, w = 0.f;
     int len = walk_path(base, pitch, ox, oy, s, [&](const T *q) {
-        float4 v = fetch_sample<T>(q);
-        float dl = v.x - cL, da = v.y - ca, db = v.z - cb;
-        a0 = fmaf(dl, dl, a0);
-        a1 = fmaf(da, da, a1);
-        a2 = fmaf(db, db, a2);
-        bw += v.w;
+        const float4 v = fetch_sample<T>(q);
+        dc += colour_dist(v, cL, ca, cb);
+        w += v.w;
     });
-    sum_dc = (a0 + a1) + a2;
-    sum_w = bw;
+    sum_dc = dc;
+    sum_w = w;
     return len;
 }
 

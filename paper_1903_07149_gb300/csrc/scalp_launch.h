@@ -31,13 +31,15 @@ void launch_lists(const SolveArgs &a, cudaStream_t st);
 // iteration's update, projection and candidate lists for every image.
 void launch_assign_batch(const BatchArgs &b, int storage, int total_tiles, size_t smem_bytes,
                          cudaStream_t st);
-cudaError_t assign_batch_configure(int storage, size_t smem_bytes);
+cudaError_t assign_batch_configure(int storage);
 void launch_batch_update(const BatchArgs &b, int total_clusters, int total_fill, cudaStream_t st);
-// Assignment (Algorithm 1 inner loops, Eq. 1-3).  tmap is used when staged.
-void launch_assign(const SolveArgs &a, int storage, bool staged, const CUtensorMap &tmap,
-                   size_t smem_bytes, cudaStream_t st);
-size_t assign_smem_bytes(int halo, int storage);
-cudaError_t assign_configure(int storage, bool staged, size_t smem_bytes);
+// Assignment (Algorithm 1 inner loops, Eq. 1-3) with a.map_cap distance-map
+// pairs per CTA; smem_bytes = assign_smem_bytes(a.map_cap).
+void launch_assign(const SolveArgs &a, int storage, size_t smem_bytes, cudaStream_t st);
+size_t assign_smem_bytes(int map_cap);
+// Distance-map pairs that fit when ASSIGN_CTAS_PER_SM assignment CTAs share an SM.
+int assign_map_capacity(int device);
+cudaError_t assign_configure(int storage);
 // Debug: record the pixels of M paths.
 void launch_debug_paths(const int *pairs, int M, int *out_xy, int stride_xy, int *out_len,
                         int W, cudaStream_t st);
@@ -54,7 +56,6 @@ void launch_ccl(const int *labels, int H, int W, int K, int *out, const CclBuffe
 
 // Per-context accessors used by the serving loop.
 SolveArgs scalp_ctx_args(const scalp_ctx *c);
-CUtensorMap scalp_ctx_tmap(const scalp_ctx *c);
 size_t scalp_ctx_smem(const scalp_ctx *c);
 void scalp_ctx_count_iteration(scalp_ctx *c);
 int scalp_ctx_enqueue_labels(scalp_ctx *c, int32_t *out, int enforce);

@@ -52,8 +52,7 @@ int server_fail(int code, const char *fmt, ...)
 
 size_t head_bytes(int slots)
 {
-    return salign((size_t)slots * sizeof(CUtensorMap)) + salign((size_t)slots * sizeof(SolveArgs)) +
-           3 * salign((size_t)(slots + 1) * sizeof(int));
+    return salign((size_t)slots * sizeof(SolveArgs)) + 3 * salign((size_t)(slots + 1) * sizeof(int));
 }
 
 }  // namespace
@@ -115,30 +114,24 @@ int rebuild_args(scalp_server *s, std::vector<Solve *> &running)
 {
     const int n = (int)running.size();
     std::vector<SolveArgs> args(n);
-    std::vector<CUtensorMap> tmaps(n);
     std::vector<int> tile(n + 1, 0), clus(n + 1, 0), fill(n + 1, 0);
     size_t smem = 0;
     for (int i = 0; i < n; ++i) {
         const scalp_ctx *c = running[i]->ctx;
         args[i] = scalp_ctx_args(c);
-        tmaps[i] = scalp_ctx_tmap(c);
         tile[i + 1] = tile[i] + args[i].n_tx * args[i].n_ty;
         clus[i + 1] = clus[i] + args[i].Keff;
         fill[i + 1] = fill[i] + args[i].Keff * args[i].tpw_x * args[i].tpw_y;
         smem = std::max(smem, scalp_ctx_smem(c));
     }
     unsigned char *h = s->pool;
-    const size_t o_tmaps = 0;
-    const size_t o_args = o_tmaps + salign((size_t)s->max_slots * sizeof(CUtensorMap));
+    const size_t o_args = 0;
     const size_t o_tile = o_args + salign((size_t)s->max_slots * sizeof(SolveArgs));
     const size_t o_clus = o_tile + salign((size_t)(s->max_slots + 1) * sizeof(int));
     const size_t o_fill = o_clus + salign((size_t)(s->max_slots + 1) * sizeof(int));
     cudaError_t e = cudaSuccess;
-    if (n > 0) {
-        e = cudaMemcpyAsync(h + o_tmaps, tmaps.data(), n * sizeof(CUtensorMap), cudaMemcpyHostToDevice, s->st);
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(h + o_args, args.data(), n * sizeof(SolveArgs), cudaMemcpyHostToDevice, s->st);
-    }
+    if (n > 0)
+        e = cudaMemcpyAsync(h + o_args, args.data(), n * sizeof(SolveArgs), cudaMemcpyHostToDevice, s->st);
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(h + o_tile, tile.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, s->st);
     if (e == cudaSuccess)
@@ -149,7 +142,6 @@ int rebuild_args(scalp_server *s, std::vector<Solve *> &running)
     if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
     if (e != cudaSuccess) return server_fail(SCALP_E_CUDA, "server arguments: %s", cudaGetErrorString(e));
     s->bargs.args = reinterpret_cast<const SolveArgs *>(h + o_args);
-    s->bargs.tmaps = reinterpret_cast<const CUtensorMap *>(h + o_tmaps);
     s->bargs.tile_base = reinterpret_cast<const int *>(h + o_tile);
     s->bargs.clus_base = reinterpret_cast<const int *>(h + o_clus);
     s->bargs.fill_base = reinterpret_cast<const int *>(h + o_fill);
@@ -191,7 +183,7 @@ int scalp_server_create(scalp_server **out, void *pool, size_t pool_bytes, int32
     s->max_slots = max_slots;
     s->free_list[head] = (pool_bytes - head) & ~(SALIGN - 1);
     // the batched assignment may need up to the full shared memory of an SM
-    cudaError_t e = assign_batch_configure(params->storage, 227 * 1024);
+    cudaError_t e = assign_batch_configure(params->storage);
     if (e != cudaSuccess) {
         delete s;
         return server_fail(SCALP_E_CUDA, "configure: %s", cudaGetErrorString(e));

@@ -51,7 +51,7 @@ class scalp_params(ctypes.Structure):
 class scalp_info(ctypes.Structure):
     _fields_ = [("H", ctypes.c_int32), ("W", ctypes.c_int32), ("K", ctypes.c_int32),
                 ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("Keff", ctypes.c_int32),
-                ("r", ctypes.c_double), ("gamma", ctypes.c_double), ("halo", ctypes.c_int32),
+                ("r", ctypes.c_double), ("gamma", ctypes.c_double), ("map_pairs", ctypes.c_int32),
                 ("iterations", ctypes.c_int32)]
 
 
@@ -110,6 +110,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "scalp_profile": (ctypes.c_int, [P, I32, ctypes.POINTER(ctypes.c_double),
                                              ctypes.POINTER(I64)]),
             "scalp_count_samples": (ctypes.c_int, [P, I32, ctypes.POINTER(I64),
+                                                   ctypes.POINTER(I64), ctypes.POINTER(I64),
                                                    ctypes.POINTER(I64)]),
             "scalp_sync": (ctypes.c_int, [P]),
             "scalp_last_error": (ctypes.c_char_p, [P]),
@@ -219,11 +220,13 @@ def scalp_profile(ctx, enable: int):
     return ms.value, n.value
 
 
-def scalp_count_samples(ctx, enable: int):
-    s = ctypes.c_int64()
-    n = ctypes.c_int64()
-    _check(load().scalp_count_samples(ctx, int(enable), ctypes.byref(s), ctypes.byref(n)), ctx)
-    return s.value, n.value
+def scalp_count_samples(ctx, enable: int, rects: bool = False):
+    """(samples, pairs) of the last assignment, plus (map_rects, plane_rects)
+    when rects; enable 1 resets and counts, 0 stops, -1 only reads."""
+    v = [ctypes.c_int64() for _ in range(4)]
+    _check(load().scalp_count_samples(ctx, int(enable), *(ctypes.byref(x) for x in v)), ctx)
+    out = tuple(x.value for x in v)
+    return out if rects else out[:2]
 
 
 def scalp_sync(ctx):
@@ -349,8 +352,8 @@ class Segmenter:
     def profile(self, enable: int):
         return scalp_profile(self.ctx, enable)
 
-    def count_samples(self, enable: int):
-        return scalp_count_samples(self.ctx, enable)
+    def count_samples(self, enable: int, rects: bool = False):
+        return scalp_count_samples(self.ctx, enable, rects)
 
     def sync(self):
         scalp_sync(self.ctx)

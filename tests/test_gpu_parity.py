@@ -101,7 +101,7 @@ def test_init_matches_oracle(S):
     seg.close()
 
 
-@pytest.mark.parametrize("variant", ["staged", "global"])
+@pytest.mark.parametrize("variant", ["maps", "plane"])
 @pytest.mark.parametrize("t", [0, 3])
 def test_one_step_parity(S, variant, t):
     H, W, K = 150, 230, 120  # ragged: 230 = 7*32+6 columns, 150 = 9*16+6 rows
@@ -109,13 +109,19 @@ def test_one_step_parity(S, variant, t):
     orc = oracle.Solver(oracle.lab_from_rgb(rgb), con, K)
     orc.iterate(t)
     st = orc.state()
-    seg = make_seg(S, rgb, con, K, global_walk=(variant == "global"))
-    if variant == "staged":
-        assert seg.info.halo > 0
+    seg = make_seg(S, rgb, con, K, global_walk=(variant == "plane"))
+    if variant == "maps":
+        assert seg.info.map_pairs > 0
     else:
-        assert seg.info.halo == 0
+        assert seg.info.map_pairs == 0
     seg.set_state(to_gpu_state(st))
+    seg.count_samples(1)
     seg.iterate(1)
+    _, _, on_map, on_plane = seg.count_samples(0, rects=True)
+    if variant == "maps":
+        assert on_map > 0 and on_plane == 0, (on_map, on_plane)
+    else:
+        assert on_map == 0 and on_plane > 0, (on_map, on_plane)
     g = seg.get_state()
     orc.assign()
     check_one_step(orc, g["labels"], orc.labels, st)
@@ -135,16 +141,27 @@ def test_one_step_parity(S, variant, t):
     seg.close()
 
 
-def test_staged_equals_global(S):
-    H, W, K = 200, 300, 150
+@pytest.mark.parametrize("H,W,K", [(200, 300, 150), (240, 320, 6)])
+def test_maps_equal_plane_walk(S, H, W, K):
+    """Paths walked on the shared-memory distance maps and on the plane in
+    global memory give bit-identical labels.  With K = 6 (r = 113) some map
+    boxes overflow the map buffer, so one launch mixes both walks."""
     rgb, con, _ = synth.small_image(H, W, seed=4)
     a = make_seg(S, rgb, con, K)
     b = make_seg(S, rgb, con, K, global_walk=True)
+    a.count_samples(1)
     a.iterate(5)
+    _, _, on_map, on_plane = a.count_samples(0, rects=True)
+    assert on_map > 0
+    if K == 6:
+        assert on_plane > 0
     b.iterate(5)
     la, _ = a.labels(enforce=False)
     lb, _ = b.labels(enforce=False)
     assert np.array_equal(la, lb)
+    sa, sb = a.get_state(), b.get_state()
+    for k in ("n", "sx", "sy", "color", "endpoint"):
+        assert np.array_equal(sa[k], sb[k]), k
     a.close(); b.close()
 
 
@@ -307,7 +324,7 @@ def test_set_state_rejects_bad_state(S):
 
 def test_full_size_hd_one_step(S):
     """1080x1920, K=2000, in the launch configuration the benchmark times
-    (staged FP32 tiles, CUDA-graph replay on a side stream): one assignment
+    (FP32 planes, distance maps, CUDA-graph replay on a side stream): one assignment
     from the oracle's state after one iteration, every pixel compared."""
     import torch
 
@@ -319,7 +336,7 @@ def test_full_size_hd_one_step(S):
     with torch.cuda.stream(stream):
         seg = S.Segmenter(torch.from_numpy(rgb).cuda(), torch.from_numpy(con).cuda(), w.K,
                           stream=stream)
-        assert seg.info.halo > 0
+        assert seg.info.map_pairs > 0
         seg.set_state(to_gpu_state(st))
         seg.iterate(1)
         g = seg.get_state()
@@ -360,7 +377,7 @@ def test_f16_one_step_parity(S):
     orc.iterate(2)
     st = orc.state()
     seg = make_seg(S, rgb, con, K, storage="f16")
-    assert seg.info.halo > 0
+    assert seg.info.map_pairs > 0
     seg.set_state(to_gpu_state(st))
     seg.iterate(1)
     g = seg.get_state()
@@ -374,7 +391,7 @@ def test_f16_one_step_parity(S):
     seg.close()
 
 
-def test_f16_staged_equals_global(S):
+def test_f16_maps_equal_plane_walk(S):
     H, W, K = 200, 300, 150
     rgb, con, _ = synth.small_image(H, W, seed=13)
     a = make_seg(S, rgb, con, K, storage="f16")
