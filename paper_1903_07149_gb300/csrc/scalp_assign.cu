@@ -286,7 +286,7 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
         int4 b = make_int4(0, 0, 1, 0);
         int bw = 1;
         for (int e0 = tid; e0 < used; e0 += BUILD_UNROLL * THREADS) {
-            float4 v[BUILD_UNROLL];
+            T v[BUILD_UNROLL];  // raw samples: all loads issue before any use
             int ec[BUILD_UNROLL];
 #pragma unroll
             for (int u = 0; u < BUILD_UNROLL; ++u) {
@@ -309,7 +309,7 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
                     const int row = b.z > 1 ? (int)__umulhi((unsigned)le, (unsigned)b.w) : le;
                     const int cx = le - row * b.z;
                     if (cx < bw) {
-                        v[u] = fetch_sample<T>(plane + (long long)(b.y + row) * a.pitch + (b.x + cx));
+                        v[u] = __ldg(plane + (long long)(b.y + row) * a.pitch + (b.x + cx));
                         ec[u] = c;
                     }
                 }
@@ -318,14 +318,15 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
             for (int u = 0; u < BUILD_UNROLL; ++u) {
                 if (ec[u] >= 0) {
                     const float4 ck = col[ec[u]];
-                    maps[e0 + u * THREADS] = make_float2(colour_dist(v[u], ck.x, ck.y, ck.z), v[u].w);
+                    const float4 q = sample_value(v[u]);
+                    maps[e0 + u * THREADS] = make_float2(colour_dist(q, ck.x, ck.y, ck.z), q.w);
                 }
             }
         }
     }
     __syncthreads();
 
-    unsigned long long my_samples = 0, my_pairs = 0;
+    unsigned my_samples = 0, my_pairs = 0;  // per thread: far below 2^32
     int bestk[PIX_PER_THREAD];  // per-pixel path only
 #pragma unroll
     for (int j = 0; j < PIX_PER_THREAD; ++j) bestk[j] = INT_MAX;
@@ -446,8 +447,8 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
             my_pairs += __shfl_down_sync(0xffffffffu, my_pairs, o);
         }
         if (lane == 0) {
-            atomicAdd(&a.ctr->samples, my_samples);
-            atomicAdd(&a.ctr->pairs, my_pairs);
+            atomicAdd(&a.ctr->samples, (unsigned long long)my_samples);
+            atomicAdd(&a.ctr->pairs, (unsigned long long)my_pairs);
         }
         // (candidate, tile) rectangles walked on a map and on the plane
         if (tid == 0) {

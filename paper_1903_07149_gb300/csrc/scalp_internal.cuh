@@ -109,22 +109,19 @@ __device__ __forceinline__ int batch_find(const int *base, int count, int g)
     return lo;
 }
 
-__device__ __forceinline__ float4 load_f16x4(const uint2 *p)
+// A plane sample as stored (float4, or 4 x fp16 in a uint2) and as FP32.
+__device__ __forceinline__ float4 sample_value(float4 v) { return v; }
+__device__ __forceinline__ float4 sample_value(uint2 u)
 {
-    uint2 u = __ldg(p);
     __half2 lo = *reinterpret_cast<__half2 *>(&u.x);
     __half2 hi = *reinterpret_cast<__half2 *>(&u.y);
     float2 a = __half22float2(lo), b = __half22float2(hi);
     return make_float4(a.x, a.y, b.x, b.y);
 }
 
+// Read-only global load of one plane sample, as FP32.
 template <typename T>
-__device__ __forceinline__ float4 fetch_sample(const T *q);
-// Read-only global loads of one plane sample.
-template <>
-__device__ __forceinline__ float4 fetch_sample<float4>(const float4 *q) { return __ldg(q); }
-template <>
-__device__ __forceinline__ float4 fetch_sample<uint2>(const uint2 *q) { return load_f16x4(q); }
+__device__ __forceinline__ float4 fetch_sample(const T *q) { return sample_value(__ldg(q)); }
 
 // The linear path of Sec. II-B between pixels p and e, walked from the
 // lexicographically smaller end (x, then y) so the pixel set does not depend
