@@ -122,11 +122,23 @@ class Clocks:
                 "samples": len(rows)}
 
 
-# Kernels per step: reload = set-up, sums, update, projection, tile scan, tile
-# fill; each iteration = assignment (with the sums), update, projection, tile
-# scan, tile fill.
-RELOAD_LAUNCHES = 6
-ITER_LAUNCHES = 5
+# Kernels per step: reload = set-up, sums, update, projection, candidate lists;
+# each iteration = assignment (with the sums), update, projection, candidate
+# lists.  The lists are one kernel up to 12,287 tiles, else a scan and a fill.
+FALLBACK_HBM_GBS = 6800.0
+
+
+def list_launches(H: int, W: int) -> int:
+    tiles = -(-H // 32) * -(-W // 32)
+    return 1 if tiles <= 12287 else 2
+
+
+def reload_launches(H: int, W: int) -> int:
+    return 4 + list_launches(H, W)
+
+
+def iter_launches(H: int, W: int) -> int:
+    return 3 + list_launches(H, W)
 
 
 def rank_max(x: float, device: str = "cuda") -> float:
@@ -455,6 +467,61 @@ def measure_quality(w, rgb, con, cells):
     return res
 
 
+def measure_prior(args, w, rgb, con, cells, flush):
+    """The contour prior computed from the image on the GPU (Sec. II-E takes any
+    soft prior): its throughput on the workload's image, and the superpixel
+    metrics of SCALP driven by it, by the workload's own prior and by none
+    (C = 0): the influence of the prior (Fig. 4(b)) on synthetic ground truth."""
+    import torch
+
+    from paper_1903_07149_gb300 import scalp
+
+    d_rgb = torch.from_numpy(rgb).cuda()
+    out = torch.empty((w.H, w.W), dtype=torch.float32, device="cuda")
+    stream = torch.cuda.Stream()
+    n_iter = max(args.steps, 5)
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            scalp.gradient_prior(d_rgb, out, stream=stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2 * n_iter)]
+        torch.cuda.synchronize()
+        for i in range(n_iter):
+            flush.zero_()
+            ev[2 * i].record(stream)
+            scalp.gradient_prior(d_rgb, out, stream=stream)
+            ev[2 * i + 1].record(stream)
+        torch.cuda.synchronize()
+    ms = sum(ev[2 * i].elapsed_time(ev[2 * i + 1]) for i in range(n_iter)) / n_iter
+    # algorithmic bytes: rgb read (3 B) and the prior written (4 B) by the first
+    # pass, read and written again (8 B) by the normalisation
+    bytes_px = 15
+    peaks = measured_peaks() or {}
+    hbm = peaks.get("hbm_gbs")
+    source = "measured (MEASURED_PEAKS.json)"
+    if not hbm:
+        hbm, source = FALLBACK_HBM_GBS, "fallback 6.8 TB/s (no measured peaks file)"
+    gbs = w.H * w.W * bytes_px / (ms / 1e3) / 1e9
+    res = {"workload": w.name, "ms": ms, "Mpix_per_s": w.H * w.W / (ms / 1e3) / 1e6,
+           "launches": 2, "roofline": {"bound": "hbm", "achieved": gbs, "unit": "GB/s",
+                                        "peak": hbm, "frac": gbs / hbm, "peak_source": source,
+                                        "bytes_per_pixel": bytes_px}}
+    gt = torch.from_numpy(cells).cuda()
+    d_con = torch.from_numpy(con).cuda()
+    quality = {}
+    for name, contour, prior in (("gradient_prior", None, "gradient"), ("input_prior", d_con, "input"),
+                                 ("no_prior", None, "input")):
+        seg = scalp.Segmenter(d_rgb, contour, w.K, prior=prior)
+        seg.iterate(w.iters)
+        lab = torch.empty((w.H, w.W), dtype=torch.int32, device="cuda")
+        _, n = seg.labels(enforce=True, out=lab)
+        q = scalp.quality_metrics(lab, gt)
+        q["n_superpixels"] = int(n)
+        quality[name] = q
+        seg.close()
+    res["quality"] = quality
+    return res
+
+
 def measure_single_form(args, w, rgb, con, storage: str, flush):
     """Plain single-image solve with the given plane storage (FP16 form)."""
     import torch
@@ -612,7 +679,8 @@ def run_ours(args):
                    "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
                    "n_labels": int(n_labels)},
         "clocks": clk, "e2e": e2e,
-        "gpu_launches": args.steps * (RELOAD_LAUNCHES + ITER_LAUNCHES * iters + ccl_launches(N)),
+        "gpu_launches": args.steps * (reload_launches(w.H, w.W) + iter_launches(w.H, w.W) * iters
+                                      + ccl_launches(N)),
         "roofline": roofline,
     }
     if not args.no_forms:
@@ -630,6 +698,7 @@ def run_ours(args):
         _, _, cells = synth.voronoi_image(w.H, w.W, w.n_cells, gradient=w.gradient,
                                           noise_sigma=w.noise_sigma, seed=w.seed)
         line["forms"]["quality_eq5_8"] = measure_quality(w, rgb, con, cells)
+        line["forms"]["gradient_prior"] = measure_prior(args, w, rgb, con, cells, flush)
         if not args.no_serving:
             line["forms"]["serving"] = measure_serving(args, batch_imgs)
     if not args.no_cpu_baseline and world == 1:

@@ -51,6 +51,9 @@ extern "C" {
 #define SCALP_STORAGE_F32 0   /* Lab + contour planes stored as 4 x fp32 per pixel */
 #define SCALP_STORAGE_F16 1   /* the same planes stored as 4 x fp16 per pixel */
 
+#define SCALP_PRIOR_INPUT 0     /* the contour prior is the scalp_contour argument */
+#define SCALP_PRIOR_GRADIENT 1  /* computed on the GPU from the image: scalp_gradient_prior */
+
 /* Input image: 8-bit sRGB, interleaved R, G, B. */
 typedef struct {
     int32_t H, W;          /* rows and columns, both >= 1 */
@@ -73,6 +76,8 @@ typedef struct {
     int32_t storage;       /* SCALP_STORAGE_F32 or SCALP_STORAGE_F16 */
     int32_t use_graph;     /* 1: replay each iteration as a CUDA graph (non-NULL stream) */
     int32_t global_walk;   /* 1: walk every path on the plane in global memory (no distance maps) */
+    int32_t prior;         /* SCALP_PRIOR_INPUT (default) or SCALP_PRIOR_GRADIENT; with the
+                              latter the contour argument must be NULL or have NULL data */
     void *stream;          /* cudaStream_t for all device work */
     void *workspace;       /* device memory owned by the caller */
     size_t workspace_bytes;
@@ -214,6 +219,31 @@ int scalp_batch_labels(scalp_batch *b, int32_t *const *outs, int32_t out_on_devi
 int scalp_batch_get_state(scalp_batch *b, int32_t index, const scalp_state *state);
 int scalp_batch_get_info(const scalp_batch *b, int32_t index, scalp_info *info);
 void scalp_batch_destroy(scalp_batch *b);
+
+/* ---- Contour prior from the image ----------------------------------------
+ * Sec. II-E lets SCALP take any soft contour prior with values in [0, 1] (or a
+ * binary one) from any contour detector.  The detectors the paper uses need
+ * trained models, so this library offers one computed from the image alone:
+ * the magnitude of the CIELab gradient divided by its maximum over the image
+ * (0 everywhere for a flat image).  Per channel and axis the derivative is
+ * the central difference (f[i+1] - f[i-1]) / 2, the one-sided difference at
+ * the first and last pixel, and 0 along an axis of length 1; the magnitude is
+ * the Euclidean norm of the six derivatives (FP32).
+ *
+ * image: H x W sRGB (host or device, image->on_device).  out: H rows of
+ * out_stride floats (0 means W), host or device memory (out_on_device).  The
+ * work runs on `stream`; with host output the call synchronises it.  The
+ * workspace (device memory, 256-byte aligned, owned by the caller) must hold
+ * scalp_gradient_prior_workspace_bytes(...) bytes; it stages host data.
+ * Errors: SCALP_E_ARG for NULL pointers or bad sizes and strides,
+ * SCALP_E_NOMEM for a small workspace, SCALP_E_CUDA for a failed CUDA call.
+ * The same prior is used inside scalp_init when params->prior is
+ * SCALP_PRIOR_GRADIENT. */
+size_t scalp_gradient_prior_workspace_bytes(int32_t H, int32_t W, int32_t image_on_device,
+                                            int32_t out_on_device);
+int scalp_gradient_prior(const scalp_image *image, float *out, int64_t out_stride,
+                         int32_t out_on_device, void *stream, void *workspace,
+                         size_t workspace_bytes);
 
 /* ---- Serving: continuous batching of solves in flight ------------------------
  *

@@ -85,6 +85,7 @@ def lib():
             L.orc_boundary_map.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
             L.orc_quality.argtypes = [P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, P, P, P, P]
+            L.orc_gradient_prior.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, P]
             _lib = L
     return _lib
 
@@ -151,6 +152,16 @@ def quality(labels, gt, eps: float = 2.0):
     lib().orc_quality(_ptr(labels), int(labels.max()) + 1, _ptr(gt), int(gt.max()) + 1, H, W,
                       float(eps), *[ctypes.byref(v) for v in out])
     return dict(zip(("br", "asa", "ue", "co"), (v.value for v in out)))
+
+
+def gradient_prior(lab):
+    """Contour prior from the image: CIELab gradient magnitude / its maximum.
+    ``lab`` = (L, a, b) float64 (H, W) planes, e.g. from lab_from_rgb."""
+    L, A, B = (np.ascontiguousarray(x, dtype=np.float64) for x in lab)
+    H, W = L.shape
+    out = np.empty((H, W))
+    lib().orc_gradient_prior(_ptr(L), _ptr(A), _ptr(B), H, W, _ptr(out))
+    return out
 
 
 def multiscale_K(k_min: int = 6, k_max: int = 600, scales: int = 12):

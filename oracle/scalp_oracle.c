@@ -544,3 +544,42 @@ void orc_quality(const int32_t *labels, int n_labels, const int32_t *gt, int n_g
     *co = s / (double)N;
     free(ov); free(area); free(perim);
 }
+
+/* ------------------------------------------------------------------------ */
+/* A contour prior computed from the image itself.  Sec. II-E lets SCALP take
+ * any soft prior with values in [0, 1] (or a binary one) from any contour
+ * detector; the detector the paper uses needs trained models.  Reading used
+ * here: the magnitude of the CIELab gradient, divided by its maximum over the
+ * image (all zero when the image is flat).  Per channel and axis the
+ * derivative is the central difference (f[i+1] - f[i-1]) / 2 inside the image,
+ * the one-sided difference f[1] - f[0] or f[n-1] - f[n-2] at the two ends, and
+ * 0 along an axis of length 1.  The magnitude is the Euclidean norm of the six
+ * derivatives. */
+static double axis_derivative(const double *f, int64_t stride, int i, int n)
+{
+    if (n < 2) return 0.0;
+    if (i == 0) return f[stride] - f[0];
+    if (i == n - 1) return f[0] - f[-stride];
+    return (f[stride] - f[-stride]) / 2.0;
+}
+
+void orc_gradient_prior(const double *L, const double *A, const double *B, int H, int W,
+                        double *out)
+{
+    const double *ch[3] = {L, A, B};
+    double gmax = 0.0;
+    for (int y = 0; y < H; y++)
+        for (int x = 0; x < W; x++) {
+            int64_t p = (int64_t)y * W + x;
+            double s = 0.0;
+            for (int c = 0; c < 3; c++) {
+                double gx = axis_derivative(ch[c] + p, 1, x, W);
+                double gy = axis_derivative(ch[c] + p, W, y, H);
+                s += gx * gx + gy * gy;
+            }
+            out[p] = sqrt(s);
+            if (out[p] > gmax) gmax = out[p];
+        }
+    int64_t N = (int64_t)H * W;
+    for (int64_t p = 0; p < N; p++) out[p] = gmax > 0.0 ? out[p] / gmax : 0.0;
+}

@@ -173,6 +173,15 @@ int device_status(scalp_ctx *c)
     return SCALP_OK;
 }
 
+// Tile counts and list cursors start at zero before an update (the
+// assignment kernel re-zeroes each tile's pair after reading its list).
+int zero_tile_counts(scalp_ctx *c)
+{
+    const size_t bytes = sizeof(int) * (size_t)c->L.n_tx * c->L.n_ty;
+    int rc = cuda_check(c, cudaMemsetAsync(c->a.tile_count, 0, bytes, c->st), "memset");
+    return rc ? rc : cuda_check(c, cudaMemsetAsync(c->a.tile_cursor, 0, bytes, c->st), "memset");
+}
+
 int load_inputs(scalp_ctx *c, const scalp_image *img, const scalp_contour *con)
 {
     const uint8_t *rgb = img->rgb;
@@ -200,11 +209,17 @@ int load_inputs(scalp_ctx *c, const scalp_image *img, const scalp_contour *con)
     }
     rc = cuda_check(c, cudaMemsetAsync(c->a.acc, 0, sizeof(ClusterAcc) * c->Keff, c->st), "memset");
     if (rc) return rc;
-    rc = cuda_check(c, cudaMemsetAsync(c->a.tile_count, 0, sizeof(int) * c->L.n_tx * c->L.n_ty, c->st),
-                    "memset");
+    rc = zero_tile_counts(c);
     if (rc) return rc;
     rc = cuda_check(c, cudaMemsetAsync(c->a.ctr, 0, sizeof(DevCounters), c->st), "memset");
     if (rc) return rc;
+    if (c->p.prior == SCALP_PRIOR_GRADIENT) {
+        // the prior computed from the image, into the contour staging area
+        float *d_c = reinterpret_cast<float *>(c->ws + c->L.contour);
+        launch_gradient_prior(rgb, rs, c->H, c->W, c->a.lut, d_c, c->W, &c->a.ctr->prior_max, c->st);
+        cp = d_c;
+        cs = c->W;
+    }
     void *plane = c->ws + c->L.plane;
     launch_setup(c->a, rgb, rs, cp, cs, c->p.storage, plane, c->st);
     launch_accumulate(c->a, c->st);
@@ -218,6 +233,7 @@ int load_inputs(scalp_ctx *c, const scalp_image *img, const scalp_contour *con)
 int validate_image(const scalp_image *img, const scalp_contour *con, const char **why)
 {
     if (!img || !img->rgb) { *why = "image or image->rgb is NULL"; return 0; }
+    if (img->H < 1 || img->W < 1) { *why = "image size must be at least 1 x 1"; return 0; }
     if (img->rgb_stride != 0 && img->rgb_stride < 3LL * img->W) { *why = "rgb_stride < 3*W"; return 0; }
     if (con && con->data && con->stride != 0 && con->stride < img->W) { *why = "contour stride < W"; return 0; }
     return 1;
@@ -298,6 +314,10 @@ int scalp_init(scalp_ctx **out, const scalp_image *image, const scalp_contour *c
     *out = nullptr;
     if (!params) return fail(nullptr, SCALP_E_ARG, "params is NULL");
     if (!validate_image(image, contour, &why)) return fail(nullptr, SCALP_E_ARG, "%s", why);
+    if (params->prior != SCALP_PRIOR_INPUT && params->prior != SCALP_PRIOR_GRADIENT)
+        return fail(nullptr, SCALP_E_ARG, "params->prior must be SCALP_PRIOR_INPUT or SCALP_PRIOR_GRADIENT");
+    if (params->prior == SCALP_PRIOR_GRADIENT && contour && contour->data)
+        return fail(nullptr, SCALP_E_ARG, "a contour was given with SCALP_PRIOR_GRADIENT");
     if (!sizes_ok(image->H, image->W, K))
         return fail(nullptr, SCALP_E_ARG, "need H, W >= 1, H*W <= 2^30 and 1 <= K <= H*W");
     if (!(m > 0.0f) || !std::isfinite(m)) return fail(nullptr, SCALP_E_ARG, "m must be > 0");
@@ -389,6 +409,8 @@ int scalp_reload(scalp_ctx *c, const scalp_image *image, const scalp_contour *co
     const char *why = nullptr;
     if (!c) return fail(nullptr, SCALP_E_ARG, "ctx is NULL");
     if (!validate_image(image, contour, &why)) return fail(c, SCALP_E_ARG, "%s", why);
+    if (c->p.prior == SCALP_PRIOR_GRADIENT && contour && contour->data)
+        return fail(c, SCALP_E_ARG, "a contour was given with SCALP_PRIOR_GRADIENT");
     if (image->H != c->H || image->W != c->W)
         return fail(c, SCALP_E_ARG, "reload needs the same image size");
     return load_inputs(c, image, contour);
@@ -557,6 +579,7 @@ int scalp_set_state(scalp_ctx *c, const scalp_state *s)
     rc = rc ? rc : cuda_check(c, cudaMemcpyAsync(c->a.st_col, col.data(), 16 * K, cudaMemcpyHostToDevice, c->st), "copy state");
     rc = rc ? rc : cuda_check(c, cudaMemcpyAsync(c->a.st_end, end.data(), 8 * K, cudaMemcpyHostToDevice, c->st), "copy state");
     rc = rc ? rc : cuda_check(c, cudaMemsetAsync(c->a.acc, 0, sizeof(ClusterAcc) * K, c->st), "memset");
+    rc = rc ? rc : zero_tile_counts(c);
     if (rc) return rc;
     launch_update(c->a, 0, c->st);
     launch_lists(c->a, c->st);
@@ -680,6 +703,69 @@ void scalp_destroy(scalp_ctx *c)
     if (c->graph_valid) cudaGraphExecDestroy(c->gexec);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
+}
+
+
+size_t scalp_gradient_prior_workspace_bytes(int32_t H, int32_t W, int32_t image_on_device,
+                                            int32_t out_on_device)
+{
+    if (H < 1 || W < 1 || (long long)H * W > (1LL << 30)) return 0;
+    const size_t N = (size_t)H * W;
+    size_t cur = 0;
+    carve(cur, 256 * sizeof(float) + 16);  // transfer-function table, maximum
+    if (!image_on_device) carve(cur, 3 * N);
+    if (!out_on_device) carve(cur, 4 * N);
+    return (cur + ALIGN - 1) & ~(ALIGN - 1);
+}
+
+int scalp_gradient_prior(const scalp_image *image, float *out, int64_t out_stride,
+                         int32_t out_on_device, void *stream, void *workspace,
+                         size_t workspace_bytes)
+{
+    const char *why = nullptr;
+    if (!validate_image(image, nullptr, &why)) return fail(nullptr, SCALP_E_ARG, "%s", why);
+    if (!out) return fail(nullptr, SCALP_E_ARG, "out is NULL");
+    const int H = image->H, W = image->W;
+    if (out_stride == 0) out_stride = W;
+    if (out_stride < W) return fail(nullptr, SCALP_E_ARG, "out_stride < W");
+    const size_t need = scalp_gradient_prior_workspace_bytes(H, W, image->on_device, out_on_device);
+    if (need == 0) return fail(nullptr, SCALP_E_ARG, "invalid image size");
+    if (!workspace || workspace_bytes < need)
+        return fail(nullptr, SCALP_E_NOMEM, "gradient prior workspace of %zu bytes needed", need);
+    if (reinterpret_cast<uintptr_t>(workspace) % ALIGN)
+        return fail(nullptr, SCALP_E_ARG, "workspace must be 256-byte aligned");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    unsigned char *ws = reinterpret_cast<unsigned char *>(workspace);
+    const size_t N = (size_t)H * W;
+    size_t cur = 0;
+    const size_t o_lut = carve(cur, 256 * sizeof(float) + 16);
+    const size_t o_rgb = image->on_device ? 0 : carve(cur, 3 * N);
+    const size_t o_out = out_on_device ? 0 : carve(cur, 4 * N);
+    float *lut = reinterpret_cast<float *>(ws + o_lut);
+    unsigned *gmax = reinterpret_cast<unsigned *>(ws + o_lut + 256 * sizeof(float));
+    const uint8_t *rgb = image->rgb;
+    long long rs = image->rgb_stride ? image->rgb_stride : 3LL * W;
+    cudaError_t e = cudaSuccess;
+    if (!image->on_device) {
+        e = cudaMemcpy2DAsync(ws + o_rgb, 3 * (size_t)W, rgb, (size_t)rs, 3 * (size_t)W, H,
+                              cudaMemcpyHostToDevice, st);
+        rgb = ws + o_rgb;
+        rs = 3LL * W;
+    }
+    float *d_out = out_on_device ? out : reinterpret_cast<float *>(ws + o_out);
+    const long long d_stride = out_on_device ? out_stride : W;
+    if (e == cudaSuccess) {
+        launch_srgb_table(lut, st);
+        launch_gradient_prior(rgb, rs, H, W, lut, d_out, d_stride, gmax, st);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess && !out_on_device) {
+        e = cudaMemcpy2DAsync(out, (size_t)out_stride * 4, d_out, 4 * (size_t)W, 4 * (size_t)W, H,
+                              cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    }
+    if (e != cudaSuccess) return fail(nullptr, SCALP_E_CUDA, "gradient prior: %s", cudaGetErrorString(e));
+    return SCALP_OK;
 }
 
 }  // extern "C"

@@ -215,6 +215,10 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
     // device-side overflow check (reported as an error) ever fired
     const int cnt = (int)max(0LL, min((long long)a.tile_off[tile + 1], a.tile_cap) - off);
     const bool fast = cnt <= MAX_TILE_CANDIDATES;
+    if (tid == 0) {  // this tile's list is read: ready the counts for the next update
+        a.tile_count[tile] = 0;
+        a.tile_cursor[tile] = 0;
+    }
 
     // candidates sorted by cluster index (ranks of distinct ids); the id
     // staging reuses the `best` words before they are initialised

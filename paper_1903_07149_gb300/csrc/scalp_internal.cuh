@@ -55,6 +55,7 @@ struct DevCounters {
     unsigned long long pairs;    // optional: (pixel, cluster) pairs evaluated
     unsigned long long map_rects;    // optional: (tile, cluster) rectangles walked on a map
     unsigned long long plane_rects;  // optional: ... walked on the plane in global memory
+    unsigned prior_max;  // scratch: maximum of the gradient prior (float bits)
 };
 constexpr int ERR_TILE_LIST_OVERFLOW = 1;
 constexpr int ERR_BAD_LABEL = 2;

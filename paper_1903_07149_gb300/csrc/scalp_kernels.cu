@@ -37,6 +37,20 @@ __global__ void k_srgb_table(float *lut)
     }
 }
 
+// CIELab of one sRGB pixel; lin = the 256-entry inverse transfer function.
+__device__ __forceinline__ float3 srgb_to_lab(const float *lin, const uint8_t *px)
+{
+    const float wx = c_rgb2xyz[0] + c_rgb2xyz[1] + c_rgb2xyz[2];
+    const float wy = c_rgb2xyz[3] + c_rgb2xyz[4] + c_rgb2xyz[5];
+    const float wz = c_rgb2xyz[6] + c_rgb2xyz[7] + c_rgb2xyz[8];
+    float R = lin[px[0]], G = lin[px[1]], B = lin[px[2]];
+    float X = c_rgb2xyz[0] * R + c_rgb2xyz[1] * G + c_rgb2xyz[2] * B;
+    float Y = c_rgb2xyz[3] * R + c_rgb2xyz[4] * G + c_rgb2xyz[5] * B;
+    float Z = c_rgb2xyz[6] * R + c_rgb2xyz[7] * G + c_rgb2xyz[8] * B;
+    float fx = lab_f(X / wx), fy = lab_f(Y / wy), fz = lab_f(Z / wz);
+    return make_float3(116.0f * fy - 16.0f, 500.0f * (fx - fy), 200.0f * (fy - fz));
+}
+
 __global__ void k_setup(SolveArgs a, const uint8_t *__restrict__ rgb, long long rgb_stride,
                         const float *__restrict__ contour, long long contour_stride, int storage,
                         void *plane)
@@ -44,22 +58,12 @@ __global__ void k_setup(SolveArgs a, const uint8_t *__restrict__ rgb, long long 
     __shared__ float lin[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) lin[i] = a.lut[i];
     __syncthreads();
-    const float wx = c_rgb2xyz[0] + c_rgb2xyz[1] + c_rgb2xyz[2];
-    const float wy = c_rgb2xyz[3] + c_rgb2xyz[4] + c_rgb2xyz[5];
-    const float wz = c_rgb2xyz[6] + c_rgb2xyz[7] + c_rgb2xyz[8];
     const float inv_s2 = 1.0f / (a.sigma * a.sigma);
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < a.N;
          p += (long long)gridDim.x * blockDim.x) {
         int y = (int)(p / a.W), x = (int)(p - (long long)y * a.W);
-        const uint8_t *px = rgb + y * rgb_stride + 3 * (long long)x;
-        float R = lin[px[0]], G = lin[px[1]], B = lin[px[2]];
-        float X = c_rgb2xyz[0] * R + c_rgb2xyz[1] * G + c_rgb2xyz[2] * B;
-        float Y = c_rgb2xyz[3] * R + c_rgb2xyz[4] * G + c_rgb2xyz[5] * B;
-        float Z = c_rgb2xyz[6] * R + c_rgb2xyz[7] * G + c_rgb2xyz[8] * B;
-        float fx = lab_f(X / wx), fy = lab_f(Y / wy), fz = lab_f(Z / wz);
-        float L = 116.0f * fy - 16.0f;
-        float A = 500.0f * (fx - fy);
-        float Bb = 200.0f * (fy - fz);
+        const float3 lab = srgb_to_lab(lin, rgb + y * rgb_stride + 3 * (long long)x);
+        const float L = lab.x, A = lab.y, Bb = lab.z;
         float c = contour ? contour[y * contour_stride + x] : 0.0f;
         float w = -expm1f(-(c * c) * inv_s2);  // 1 - exp(-C^2/sigma^2), Eq. 2
         const long long q = (long long)y * a.pitch + x;
@@ -80,6 +84,92 @@ __global__ void k_setup(SolveArgs a, const uint8_t *__restrict__ rgb, long long 
 }
 
 void launch_srgb_table(const SolveArgs &a, cudaStream_t st) { k_srgb_table<<<1, 256, 0, st>>>(a.lut); }
+void launch_srgb_table(float *lut, cudaStream_t st) { k_srgb_table<<<1, 256, 0, st>>>(lut); }
+
+// ---------------------------------------------------------------------------
+// Contour prior from the image (Sec. II-E takes any soft prior in [0, 1]):
+// the CIELab gradient magnitude over its maximum.  Per channel and axis the
+// derivative is the central difference / 2 inside, one-sided at the ends, 0
+// along an axis of length 1; the magnitude is the norm of the six.  A CTA
+// converts its tile plus a one-pixel ring (coordinates clamped; the ring is
+// only read where the derivative uses it) into shared memory, writes the
+// magnitudes and raises the global maximum (float bits order like the
+// values for g >= 0); a second pass divides by it.
+// ---------------------------------------------------------------------------
+constexpr int PRIOR_TX = 32, PRIOR_TY = 8;
+
+__device__ __forceinline__ float axis_derivative(float fm, float f0, float fp, int i, int n)
+{
+    if (n < 2) return 0.0f;
+    if (i == 0) return fp - f0;
+    if (i == n - 1) return f0 - fm;
+    return (fp - fm) * 0.5f;
+}
+
+__global__ void __launch_bounds__(PRIOR_TX * PRIOR_TY)
+    k_prior_gradient(const uint8_t *__restrict__ rgb, long long rgb_stride, int H, int W,
+                     const float *__restrict__ lut, float *out, long long out_stride, unsigned *gmax)
+{
+    __shared__ float lin[256];
+    __shared__ float s_lab[3][PRIOR_TY + 2][PRIOR_TX + 2];
+    __shared__ unsigned s_max;
+    const int tid = threadIdx.x;
+    for (int i = tid; i < 256; i += blockDim.x) lin[i] = lut[i];
+    if (tid == 0) s_max = 0u;
+    __syncthreads();
+    const int x0 = blockIdx.x * PRIOR_TX, y0 = blockIdx.y * PRIOR_TY;
+    for (int i = tid; i < (PRIOR_TX + 2) * (PRIOR_TY + 2); i += blockDim.x) {
+        const int hx = i % (PRIOR_TX + 2), hy = i / (PRIOR_TX + 2);
+        const int x = min(max(x0 - 1 + hx, 0), W - 1), y = min(max(y0 - 1 + hy, 0), H - 1);
+        const float3 lab = srgb_to_lab(lin, rgb + y * rgb_stride + 3 * (long long)x);
+        s_lab[0][hy][hx] = lab.x;
+        s_lab[1][hy][hx] = lab.y;
+        s_lab[2][hy][hx] = lab.z;
+    }
+    __syncthreads();
+    const int tx = tid % PRIOR_TX, ty = tid / PRIOR_TX;
+    const int x = x0 + tx, y = y0 + ty;
+    float g = 0.0f;
+    if (x < W && y < H) {
+        float s = 0.0f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float gx = axis_derivative(s_lab[c][ty + 1][tx], s_lab[c][ty + 1][tx + 1],
+                                             s_lab[c][ty + 1][tx + 2], x, W);
+            const float gy = axis_derivative(s_lab[c][ty][tx + 1], s_lab[c][ty + 1][tx + 1],
+                                             s_lab[c][ty + 2][tx + 1], y, H);
+            s += gx * gx + gy * gy;
+        }
+        g = sqrtf(s);
+        out[y * out_stride + x] = g;
+    }
+    const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(g));
+    if ((tid & 31) == 0) atomicMax(&s_max, m);
+    __syncthreads();
+    if (tid == 0) atomicMax(gmax, s_max);
+}
+
+__global__ void k_prior_normalise(float *out, long long out_stride, int H, int W, const unsigned *gmax)
+{
+    const float m = __uint_as_float(*gmax);
+    const long long N = (long long)H * W;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(p / W), x = (int)(p - (long long)y * W);
+        float &v = out[y * out_stride + x];
+        v = m > 0.0f ? v / m : 0.0f;
+    }
+}
+
+void launch_gradient_prior(const uint8_t *rgb, long long rgb_stride, int H, int W, const float *lut,
+                           float *out, long long out_stride, unsigned *gmax, cudaStream_t st)
+{
+    cudaMemsetAsync(gmax, 0, sizeof(unsigned), st);
+    const dim3 grid((unsigned)ceil_div_ll(W, PRIOR_TX), (unsigned)ceil_div_ll(H, PRIOR_TY));
+    k_prior_gradient<<<grid, PRIOR_TX * PRIOR_TY, 0, st>>>(rgb, rgb_stride, H, W, lut, out, out_stride, gmax);
+    const long long N = (long long)H * W;
+    k_prior_normalise<<<(unsigned)std::min(ceil_div_ll(N, 256), 152LL * 16), 256, 0, st>>>(out, out_stride, H, W, gmax);
+}
 
 void launch_setup(const SolveArgs &a, const uint8_t *rgb, long long rgb_stride,
                   const float *contour, long long contour_stride, int storage, void *plane,
@@ -148,6 +238,76 @@ __device__ bool window_range(long long n, long long s, long long N, long long K,
     lo = (int)max(0LL, l);
     hi = (int)min((long long)limit - 1, h);
     return true;
+}
+
+// ---------------------------------------------------------------------------
+// Projection, Eq. 4: X_k^* = argmin over p in S_k of ||X_p - X_k||, compared
+// exactly as (n*x - Sx)^2 + (n*y - Sy)^2 in integers (64-bit when the image
+// size bounds them below 2^62, else 128-bit), ties to the smallest raster
+// index.  Searches issue PROJ_BATCH label loads per thread before comparing
+// them.
+// ---------------------------------------------------------------------------
+constexpr int PROJ_THREADS = 512;
+constexpr int PROJ_BATCH = 8;
+
+struct ProjBest {
+    unsigned long long hi, lo;
+    long long p;
+};
+
+__device__ __forceinline__ bool proj_less(const ProjBest &u, const ProjBest &v)
+{
+    return u.hi < v.hi || (u.hi == v.hi && (u.lo < v.lo || (u.lo == v.lo && u.p < v.p)));
+}
+
+__device__ __forceinline__ void proj_shfl_min(ProjBest &b)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        ProjBest c;
+        c.hi = __shfl_xor_sync(0xffffffffu, b.hi, o);
+        c.lo = __shfl_xor_sync(0xffffffffu, b.lo, o);
+        c.p = __shfl_xor_sync(0xffffffffu, b.p, o);
+        if (proj_less(c, b)) b = c;
+    }
+}
+
+
+// Row of index i in rows of w pixels: i / w by a 32-bit reciprocal
+// (rcp = ceil(2^32 / w), exact while i * w < 2^32; the caller checks), else by
+// a 64-bit division.
+struct RowDiv {
+    long long w;
+    unsigned rcp;
+    bool fast;
+    __device__ __forceinline__ RowDiv(long long w_, long long area) : w(w_)
+    {
+        fast = w_ > 1 && (unsigned long long)area * (unsigned long long)w_ < (1ULL << 32);
+        rcp = fast ? (unsigned)((0x100000000ULL + w_ - 1) / w_) : 0u;
+    }
+    __device__ __forceinline__ long long row(long long i) const
+    {
+        if (w == 1) return i;
+        return fast ? (long long)__umulhi((unsigned)i, rcp) : i / w;
+    }
+};
+
+// Candidate p (raster index, pixel (x, y)) for X_k^* of cluster (n, sx, sy).
+__device__ __forceinline__ ProjBest proj_candidate(long long p, int x, int y, long long n,
+                                                   long long sx, long long sy, bool small)
+{
+    ProjBest c;
+    c.p = p;
+    if (small) {
+        const long long dx = n * x - sx, dy = n * y - sy;
+        c.hi = 0;
+        c.lo = (unsigned long long)(dx * dx) + (unsigned long long)(dy * dy);
+    } else {
+        const __int128 dx = (__int128)n * x - sx, dy = (__int128)n * y - sy;
+        const unsigned __int128 d2 = (unsigned __int128)(dx * dx) + (unsigned __int128)(dy * dy);
+        c.hi = (unsigned long long)(d2 >> 64);
+        c.lo = (unsigned long long)d2;
+    }
+    return c;
 }
 
 // ---------------------------------------------------------------------------
@@ -229,40 +389,10 @@ void launch_update(const SolveArgs &a, int from_acc, cudaStream_t st)
     k_update<<<(a.Keff + 63) / 64, 64, 0, st>>>(a, from_acc);
 }
 
-// ---------------------------------------------------------------------------
-// Projection, Eq. 4: X_k^* = argmin over p in S_k of ||X_p - X_k||, compared
-// exactly as (n*x - Sx)^2 + (n*y - Sy)^2 in integers (64-bit when the image
-// size bounds them below 2^62, else 128-bit), ties to the smallest raster
-// index.  S_k lies inside the window the last assignment used for cluster k,
-// unless some pixel kept its old label for lack of any candidate; then the
-// whole image is searched.  One CTA per queued cluster; each thread issues
-// PROJ_BATCH label loads before comparing them.
-// ---------------------------------------------------------------------------
-constexpr int PROJ_THREADS = 512;
-constexpr int PROJ_BATCH = 8;
-
-struct ProjBest {
-    unsigned long long hi, lo;
-    long long p;
-};
-
-__device__ __forceinline__ bool proj_less(const ProjBest &u, const ProjBest &v)
-{
-    return u.hi < v.hi || (u.hi == v.hi && (u.lo < v.lo || (u.lo == v.lo && u.p < v.p)));
-}
-
-__device__ __forceinline__ void proj_shfl_min(ProjBest &b)
-{
-    for (int o = 16; o > 0; o >>= 1) {
-        ProjBest c;
-        c.hi = __shfl_xor_sync(0xffffffffu, b.hi, o);
-        c.lo = __shfl_xor_sync(0xffffffffu, b.lo, o);
-        c.p = __shfl_xor_sync(0xffffffffu, b.p, o);
-        if (proj_less(c, b)) b = c;
-    }
-}
-
-// Queue entries j0, j0 + stride, ... of one image, by one CTA.
+// Queued projections: S_k lies inside the window the last assignment used for
+// cluster k, unless some pixel kept its old label for lack of any candidate;
+// then (or with whole_image, at set-up) the whole image is searched.  One CTA
+// per queued cluster.  Queue entries j0, j0 + stride, ... of one image.
 __device__ __forceinline__ void project_cta(const SolveArgs &a, int whole_image, int j0, int stride)
 {
     __shared__ ProjBest s_best[PROJ_THREADS / 32];
@@ -280,6 +410,7 @@ __device__ __forceinline__ void project_cta(const SolveArgs &a, int whole_image,
         }
         const int w = xhi - xlo + 1;
         const long long area = (long long)w * (yhi - ylo + 1);
+        const RowDiv div(w, area);
         const bool small = 2.0 * (n * bound) * (n * bound) < 4.0e18;
         ProjBest b = {~0ull, ~0ull, LLONG_MAX};
         for (long long base = 0; base < area; base += (long long)PROJ_THREADS * PROJ_BATCH) {
@@ -291,7 +422,8 @@ __device__ __forceinline__ void project_cta(const SolveArgs &a, int whole_image,
                 lab[u] = -1;
                 idx[u] = -1;
                 if (i < area) {
-                    const int y = ylo + (int)(i / w), x = xlo + (int)(i % w);
+                    const long long r = div.row(i);
+                    const int y = ylo + (int)r, x = xlo + (int)(i - r * w);
                     idx[u] = (long long)y * a.W + x;
                     lab[u] = a.labels[idx[u]];
                 }
@@ -301,19 +433,7 @@ __device__ __forceinline__ void project_cta(const SolveArgs &a, int whole_image,
                 if (lab[u] != k) continue;
                 const long long p = idx[u];
                 const int y = (int)(p / a.W), x = (int)(p - (long long)y * a.W);
-                ProjBest c;
-                c.p = p;
-                if (small) {
-                    const long long dx = n * x - sx, dy = n * y - sy;
-                    c.hi = 0;
-                    c.lo = (unsigned long long)(dx * dx) + (unsigned long long)(dy * dy);
-                } else {
-                    const __int128 dx = (__int128)n * x - sx, dy = (__int128)n * y - sy;
-                    const unsigned __int128 d2 =
-                        (unsigned __int128)(dx * dx) + (unsigned __int128)(dy * dy);
-                    c.hi = (unsigned long long)(d2 >> 64);
-                    c.lo = (unsigned long long)d2;
-                }
+                const ProjBest c = proj_candidate(p, x, y, n, sx, sy, small);
                 if (proj_less(c, b)) b = c;
             }
         }
@@ -358,21 +478,21 @@ void launch_project(const SolveArgs &a, int whole_image, cudaStream_t st)
 }
 
 // ---------------------------------------------------------------------------
-// Per-tile candidate lists: exclusive scan of the tile counts (one CTA, each
-// thread a contiguous chunk), then one thread per (cluster, tile) slot files
-// the cluster into each tile its window overlaps.  The scan also resets the
-// per-iteration counters.
+// Per-tile candidate lists: exclusive scan of the tile counts, then one thread
+// per (cluster, tile) slot files the cluster into each tile its window
+// overlaps, at tile_off[t] + (a per-tile cursor).  The assignment CTA of tile
+// t zeroes tile_count[t] and tile_cursor[t] once it has read its list (set-up
+// and set_state zero them on the host side).  The CTA that writes tile_off
+// also resets the per-iteration counters.
 // ---------------------------------------------------------------------------
-constexpr int SCAN1_THREADS = 1024;
-
-__device__ __forceinline__ void scan_tiles_cta(const SolveArgs &a)
+// Exclusive scan of in[0, n) into out[0, n] (out[n] = total) by one CTA of
+// `threads` threads, each a contiguous chunk; s_warp holds 32 ints.
+__device__ __forceinline__ void cta_scan(const int *in, int *out, int n, int threads, int *s_warp)
 {
-    __shared__ int s_warp[32];
-    const int n = a.n_tx * a.n_ty;
-    const int per = (n + SCAN1_THREADS - 1) / SCAN1_THREADS;
+    const int per = (n + threads - 1) / threads;
     const int b = threadIdx.x * per, e = min(n, b + per);
     int tsum = 0;
-    for (int i = b; i < e; ++i) tsum += a.tile_count[i];
+    for (int i = b; i < e; ++i) tsum += in[i];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     int incl = tsum;
     for (int o = 1; o < 32; o <<= 1) {
@@ -382,7 +502,7 @@ __device__ __forceinline__ void scan_tiles_cta(const SolveArgs &a)
     if (lane == 31) s_warp[wid] = incl;
     __syncthreads();
     if (wid == 0) {
-        int w = s_warp[lane];
+        int w = lane < threads / 32 ? s_warp[lane] : 0;
         for (int o = 1; o < 32; o <<= 1) {
             const int t = __shfl_up_sync(0xffffffffu, w, o);
             if (lane >= o) w += t;
@@ -392,16 +512,35 @@ __device__ __forceinline__ void scan_tiles_cta(const SolveArgs &a)
     __syncthreads();
     int run = (wid ? s_warp[wid - 1] : 0) + incl - tsum;
     for (int i = b; i < e; ++i) {
-        const int v = a.tile_count[i];
-        a.tile_off[i] = run;
-        a.tile_cursor[i] = run;
-        a.tile_count[i] = 0;
+        const int v = in[i];
+        out[i] = run;
         run += v;
     }
-    if (threadIdx.x == SCAN1_THREADS - 1) {
-        const int total = s_warp[31];
-        a.tile_off[n] = total;
-        if (total > a.tile_cap) atomicExch(&a.ctr->error, ERR_TILE_LIST_OVERFLOW);
+    if (threadIdx.x == threads - 1) out[n] = s_warp[31];
+    __syncthreads();
+}
+
+// tile_off from the counts, the overflow check and the counter resets.
+__device__ __forceinline__ void publish_offsets(const SolveArgs &a, const int *off)
+{
+    const int n = a.n_tx * a.n_ty;
+    for (int i = threadIdx.x; i <= n; i += blockDim.x) a.tile_off[i] = off[i];
+    if (threadIdx.x == 0) {
+        if (off[n] > a.tile_cap) atomicExch(&a.ctr->error, ERR_TILE_LIST_OVERFLOW);
+        a.ctr->nproj = 0;
+        a.ctr->orphans = 0;
+    }
+}
+
+constexpr int SCAN1_THREADS = 1024;
+
+__device__ __forceinline__ void scan_tiles_cta(const SolveArgs &a)
+{
+    __shared__ int s_warp[32];
+    cta_scan(a.tile_count, a.tile_off, a.n_tx * a.n_ty, SCAN1_THREADS, s_warp);
+    if (threadIdx.x == 0) {
+        const int n = a.n_tx * a.n_ty;
+        if (a.tile_off[n] > a.tile_cap) atomicExch(&a.ctr->error, ERR_TILE_LIST_OVERFLOW);
         a.ctr->nproj = 0;
         a.ctr->orphans = 0;
     }
@@ -423,8 +562,38 @@ __device__ __forceinline__ void fill_slot(const SolveArgs &a, long long i)
     if (cd.xlo > cd.xhi) return;
     const int tx = cd.xlo / TILE_X + j % a.tpw_x, ty = cd.ylo / TILE_Y + j / a.tpw_x;
     if (tx > cd.xhi / TILE_X || ty > cd.yhi / TILE_Y) return;
-    const int pos = atomicAdd(&a.tile_cursor[ty * a.n_tx + tx], 1);
+    const int t = ty * a.n_tx + tx;
+    const int pos = a.tile_off[t] + atomicAdd(&a.tile_cursor[t], 1);
     if (pos < a.tile_cap) a.tile_list[pos] = k;
+}
+
+// Scan and fill in one launch: every CTA scans the counts into shared memory
+// (LISTS_MAX_TILES bounds them), CTA 0 publishes the offsets, and the CTAs
+// fill the slots grid-stride with offsets from their own copy.
+constexpr int LISTS_THREADS = 256;
+constexpr int LISTS_MAX_TILES = 12287;  // (n + 1) ints of shared memory <= 48 KB
+
+__global__ void __launch_bounds__(LISTS_THREADS) k_lists(SolveArgs a)
+{
+    extern __shared__ int s_off[];
+    __shared__ int s_warp[32];
+    const int n = a.n_tx * a.n_ty;
+    cta_scan(a.tile_count, s_off, n, LISTS_THREADS, s_warp);
+    if (blockIdx.x == 0) publish_offsets(a, s_off);
+    const long long slots = (long long)a.Keff * a.tpw_x * a.tpw_y;
+    const int tpw = a.tpw_x * a.tpw_y;
+    for (long long i = blockIdx.x * (long long)LISTS_THREADS + threadIdx.x; i < slots;
+         i += (long long)gridDim.x * LISTS_THREADS) {
+        const int k = slots < (1LL << 32) ? (int)((unsigned)i / (unsigned)tpw) : (int)(i / tpw);
+        const int j = (int)(i - (long long)k * tpw);
+        const ClusterDev cd = a.cdev[k];
+        if (cd.xlo > cd.xhi) continue;
+        const int tx = cd.xlo / TILE_X + j % a.tpw_x, ty = cd.ylo / TILE_Y + j / a.tpw_x;
+        if (tx > cd.xhi / TILE_X || ty > cd.yhi / TILE_Y) continue;
+        const int t = ty * a.n_tx + tx;
+        const int pos = s_off[t] + atomicAdd(&a.tile_cursor[t], 1);
+        if (pos < a.tile_cap) a.tile_list[pos] = k;
+    }
 }
 
 __global__ void k_fill_tiles(SolveArgs a)
@@ -452,9 +621,15 @@ void launch_batch_update(const BatchArgs &b, int total_clusters, int total_fill,
 
 void launch_lists(const SolveArgs &a, cudaStream_t st)
 {
-    k_scan_tiles<<<1, SCAN1_THREADS, 0, st>>>(a);
+    const int n = a.n_tx * a.n_ty;
     const long long slots = (long long)a.Keff * a.tpw_x * a.tpw_y;
-    k_fill_tiles<<<(unsigned)ceil_div_ll(slots, 256), 256, 0, st>>>(a);
+    if (n <= LISTS_MAX_TILES) {
+        const long long blocks = std::min(ceil_div_ll(slots, LISTS_THREADS), 2LL * 152);
+        k_lists<<<(unsigned)std::max(blocks, 1LL), LISTS_THREADS, (size_t)(n + 1) * sizeof(int), st>>>(a);
+    } else {
+        k_scan_tiles<<<1, SCAN1_THREADS, 0, st>>>(a);
+        k_fill_tiles<<<(unsigned)ceil_div_ll(slots, 256), 256, 0, st>>>(a);
+    }
 }
 
 // ---------------------------------------------------------------------------

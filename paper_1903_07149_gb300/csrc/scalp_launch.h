@@ -17,11 +17,18 @@ void launch_setup(const SolveArgs &a, const uint8_t *rgb, long long rgb_stride,
                   void *plane, cudaStream_t st);
 // The 256-entry inverse sRGB transfer function (once per context).
 void launch_srgb_table(const SolveArgs &a, cudaStream_t st);
+void launch_srgb_table(float *lut, cudaStream_t st);
+// Contour prior from the image (CIELab gradient magnitude / its maximum) into
+// out (H rows of out_stride floats); lut = the transfer-function table, gmax
+// one word of scratch.  rgb and out are device pointers.
+void launch_gradient_prior(const uint8_t *rgb, long long rgb_stride, int H, int W, const float *lut,
+                           float *out, long long out_stride, unsigned *gmax, cudaStream_t st);
 // Integer sums of (1, x, y, L, a, b) by label into a.acc (initialisation and
 // every update).
 void launch_accumulate(const SolveArgs &a, cudaStream_t st);
 // Cluster update (Algorithm 1) from a.acc when from_acc (queueing projections,
-// Eq. 4), then windows, the cluster records and the tile counts.
+// Eq. 4), then windows, the cluster records and the tile counts.  The tile
+// counts and list cursors must be zero on entry.
 void launch_update(const SolveArgs &a, int from_acc, cudaStream_t st);
 // Eq. 4 for the queued clusters; whole_image=1 searches every pixel.
 void launch_project(const SolveArgs &a, int whole_image, cudaStream_t st);

@@ -24,6 +24,7 @@ SCALP_E_TIMEOUT = -4
 SCALP_E_STATE = -5
 SCALP_E_INTERNAL = -6
 STORAGE = {"f32": 0, "f16": 1}
+PRIOR = {"input": 0, "gradient": 1}
 
 
 class ScalpError(RuntimeError):
@@ -44,7 +45,7 @@ class scalp_contour(ctypes.Structure):
 class scalp_params(ctypes.Structure):
     _fields_ = [("lambda_", ctypes.c_float), ("sigma", ctypes.c_float), ("gamma", ctypes.c_float),
                 ("storage", ctypes.c_int32), ("use_graph", ctypes.c_int32),
-                ("global_walk", ctypes.c_int32), ("stream", ctypes.c_void_p),
+                ("global_walk", ctypes.c_int32), ("prior", ctypes.c_int32), ("stream", ctypes.c_void_p),
                 ("workspace", ctypes.c_void_p), ("workspace_bytes", ctypes.c_size_t)]
 
 
@@ -76,6 +77,7 @@ EXPORTS = (
     "scalp_server_reserve_bytes", "scalp_server_create", "scalp_server_submit", "scalp_server_step",
     "scalp_server_poll", "scalp_server_stats", "scalp_server_destroy", "scalp_boundary_map",
     "scalp_quality_workspace_bytes", "scalp_quality_metrics",
+    "scalp_gradient_prior_workspace_bytes", "scalp_gradient_prior",
 )
 
 _lib = None
@@ -138,6 +140,9 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "scalp_server_destroy": (None, [P]),
             "scalp_boundary_map": (ctypes.c_int, [P, I32, I32, I32, P, P]),
             "scalp_quality_workspace_bytes": (ctypes.c_size_t, [I32, I32, I32, I32]),
+            "scalp_gradient_prior_workspace_bytes": (ctypes.c_size_t, [I32, I32, I32, I32]),
+            "scalp_gradient_prior": (ctypes.c_int, [ctypes.POINTER(scalp_image), P, I64, I32, P, P,
+                                                    ctypes.c_size_t]),
             "scalp_quality_metrics": (ctypes.c_int, [P, I32, P, I32, I32, I32, ctypes.c_double, P,
                                                      ctypes.c_size_t, ctypes.POINTER(scalp_quality), P]),
         }
@@ -257,7 +262,8 @@ class Segmenter:
 
     def __init__(self, rgb, contour, K: int, m: float = 10.0, lam: float = 0.5,
                  sigma: float = 0.25, gamma: float = -1.0, storage: str = "f32",
-                 use_graph: bool = True, global_walk: bool = False, stream=None):
+                 use_graph: bool = True, global_walk: bool = False, stream=None,
+                 prior: str = "input"):
         import torch
 
         self._torch = torch
@@ -268,6 +274,7 @@ class Segmenter:
         p.storage = STORAGE[storage]
         p.use_graph = int(use_graph)
         p.global_walk = int(global_walk)
+        p.prior = PRIOR[prior]
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         p.stream = self.stream.cuda_stream
         nbytes = scalp_workspace_bytes(H, W, K, p)
@@ -435,7 +442,7 @@ class Batch:
 
     def __init__(self, rgbs, contours, Ks, m: float = 10.0, lam: float = 0.5, sigma: float = 0.25,
                  gamma: float = -1.0, storage: str = "f32", use_graph: bool = True,
-                 global_walk: bool = False, stream=None):
+                 global_walk: bool = False, stream=None, prior: str = "input"):
         import torch
 
         self._torch = torch
@@ -446,6 +453,7 @@ class Batch:
         p.storage = STORAGE[storage]
         p.use_graph = int(use_graph)
         p.global_walk = int(global_walk)
+        p.prior = PRIOR[prior]
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         p.stream = self.stream.cuda_stream
         H = [s[0] for s in self.shapes]
@@ -666,6 +674,31 @@ def multiscale_boundaries(rgb, contour, Ks, iters: int = 10, storage: str = "f32
 # --- quality metrics ----------------------------------------------------------------
 def scalp_quality_workspace_bytes(H: int, W: int, n_labels: int, n_gt: int) -> int:
     return int(load().scalp_quality_workspace_bytes(int(H), int(W), int(n_labels), int(n_gt)))
+
+
+def gradient_prior(rgb, out=None, stream=None):
+    """Contour prior from the image on the GPU (scalp_gradient_prior): the
+    CIELab gradient magnitude over its maximum, (H, W) float32 in [0, 1].
+
+    rgb: (H, W, 3) uint8 CUDA tensor; out: optional (H, W) float32 CUDA tensor.
+    Returns the output tensor (work enqueued on `stream`, not synchronised)."""
+    import torch
+
+    rgb = rgb.contiguous()
+    H, W = int(rgb.shape[0]), int(rgb.shape[1])
+    if out is None:
+        out = torch.empty((H, W), dtype=torch.float32, device=rgb.device)
+    st = stream if stream is not None else torch.cuda.current_stream()
+    L = load()
+    nbytes = L.scalp_gradient_prior_workspace_bytes(H, W, 1, 1)
+    if nbytes == 0:
+        raise ScalpError(SCALP_E_ARG, "invalid sizes")
+    ws = torch.empty(nbytes, dtype=torch.uint8, device=rgb.device)
+    img = scalp_image(H, W, rgb.data_ptr(), 0, 1)
+    _check(L.scalp_gradient_prior(ctypes.byref(img), out.data_ptr(), out.stride(0), 1,
+                                  st.cuda_stream, ws.data_ptr(), nbytes), None)
+    out._scalp_keep = (rgb, ws)  # the enqueued kernels read both
+    return out
 
 
 def quality_metrics(labels, gt, eps: float = 2.0, stream=None):

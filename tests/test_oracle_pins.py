@@ -539,3 +539,55 @@ def test_quality_vs_numpy_scipy():
     ref = _quality_numpy(out, cells)
     for key in ("br", "asa", "ue", "co"):
         assert got[key] == pytest.approx(ref[key], rel=1e-12, abs=1e-12), key
+
+
+# --------------------------------------------------------------------------
+# Contour prior computed from the image (Sec. II-E allows any soft prior):
+# the CIELab gradient magnitude over its maximum.
+# --------------------------------------------------------------------------
+def _gradient_prior_numpy(lab):
+    """The same prior through numpy.gradient (central differences inside,
+    one-sided at the ends), an independent implementation."""
+    g2 = np.zeros(lab[0].shape)
+    for f in lab:
+        for axis in (0, 1):
+            if f.shape[axis] > 1:
+                g2 += np.gradient(f, axis=axis) ** 2
+    g = np.sqrt(g2)
+    return g / g.max() if g.max() > 0 else g
+
+
+@pytest.mark.parametrize("shape", [(9, 13), (1, 11), (12, 1), (2, 2), (31, 17)])
+def test_gradient_prior_vs_numpy(shape):
+    rng = np.random.default_rng(sum(shape))
+    lab = tuple(rng.normal(scale=20.0, size=shape) for _ in range(3))
+    got = oracle.gradient_prior(lab)
+    assert np.allclose(got, _gradient_prior_numpy(lab), rtol=1e-12, atol=1e-12)
+
+
+def test_gradient_prior_linear_ramp_is_one():
+    # a plane linear in x and y has the same gradient everywhere, the borders
+    # included (one-sided differences of a linear function are its slope)
+    ys, xs = np.mgrid[0:7, 0:10].astype(np.float64)
+    lab = (3.0 * xs + 4.0 * ys, np.zeros((7, 10)), -2.0 * xs)
+    assert np.allclose(oracle.gradient_prior(lab), 1.0, rtol=0, atol=1e-15)
+
+
+def test_gradient_prior_step_and_flat():
+    c1, c2 = (30, 200, 90), (220, 40, 10)
+    rgb = np.zeros((6, 10, 3), np.uint8)
+    rgb[:, :5] = c1
+    rgb[:, 5:] = c2
+    C = oracle.gradient_prior(oracle.lab_from_rgb(rgb))
+    want = np.zeros((6, 10))
+    want[:, 4:6] = 1.0  # the two columns whose central difference spans the step
+    assert np.array_equal(C, want)
+    # a step after the first column: the one-sided difference there is twice
+    # the central one next to it
+    rgb[:, 1:] = c2
+    rgb[:, :1] = c1
+    C = oracle.gradient_prior(oracle.lab_from_rgb(rgb))
+    assert np.allclose(C[:, 0], 1.0, atol=1e-15) and np.allclose(C[:, 1], 0.5, atol=1e-15)
+    assert np.all(C[:, 2:] == 0)
+    flat = np.full((5, 8, 3), 77, np.uint8)
+    assert np.all(oracle.gradient_prior(oracle.lab_from_rgb(flat)) == 0)
