@@ -57,6 +57,24 @@ class _Ctx(ctypes.Structure):
     ]
 
 
+class _VCtx(ctypes.Structure):
+    _fields_ = [
+        ("T", ctypes.c_int32), ("H", ctypes.c_int32), ("W", ctypes.c_int32), ("K", ctypes.c_int32),
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nt", ctypes.c_int32),
+        ("Keff", ctypes.c_int32),
+        ("m", ctypes.c_double), ("lam", ctypes.c_double), ("sigma", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("r", ctypes.c_double), ("r2", ctypes.c_double),
+        ("L", ctypes.c_void_p), ("A", ctypes.c_void_p), ("B", ctypes.c_void_p),
+        ("C", ctypes.c_void_p),
+        ("labels", ctypes.c_void_p),
+        ("n", ctypes.c_void_p), ("sx", ctypes.c_void_p), ("sy", ctypes.c_void_p),
+        ("st", ctypes.c_void_p),
+        ("cL", ctypes.c_void_p), ("cA", ctypes.c_void_p), ("cB", ctypes.c_void_p),
+        ("ex", ctypes.c_void_p), ("ey", ctypes.c_void_p), ("et", ctypes.c_void_p),
+        ("orphans", ctypes.c_int64), ("projections", ctypes.c_int64),
+    ]
+
+
 def lib():
     global _lib
     with _lock:
@@ -86,6 +104,19 @@ def lib():
             L.orc_quality.argtypes = [P, ctypes.c_int, P, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_double, P, P, P, P]
             L.orc_gradient_prior.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, P]
+            L.orc_vgrid_dims.argtypes = [ctypes.c_int] * 4 + [P, P, P, P]
+            L.orc_vpath.argtypes = [ctypes.c_int] * 6 + [P]
+            L.orc_vpath.restype = ctypes.c_int
+            L.orc_vin_window.argtypes = [ctypes.c_int64] * 3 + [ctypes.c_double]
+            L.orc_vin_window.restype = ctypes.c_int
+            L.orc_vdistance.argtypes = [ctypes.POINTER(_VCtx)] + [ctypes.c_int] * 4 + [P]
+            L.orc_vdistance.restype = ctypes.c_double
+            L.orc_vupdate.argtypes = [ctypes.POINTER(_VCtx)]
+            L.orc_vinit.argtypes = [ctypes.POINTER(_VCtx)]
+            L.orc_vinit.restype = ctypes.c_int
+            L.orc_vassign.argtypes = [ctypes.POINTER(_VCtx), P]
+            L.orc_vassign.restype = ctypes.c_int64
+            L.orc_viterate.argtypes = [ctypes.POINTER(_VCtx), ctypes.c_int]
             _lib = L
     return _lib
 
@@ -283,3 +314,114 @@ def solve(rgb: np.ndarray, contour: np.ndarray, K: int, iters: int = 10, m: floa
         out, n = connectivity(s.labels, K)
         return s, out, n
     return s, s.labels.copy(), int(s.Keff)
+
+
+# ---------------------------------------------------------------------------
+# Supervoxels: SCALP on a (T, H, W) volume (the extension the paper's
+# conclusion names), stepped by the C oracle.
+# ---------------------------------------------------------------------------
+def vgrid_dims(T: int, H: int, W: int, K: int):
+    """(nx, ny, nt, r) of the 3-D grid, r = cbrt(N/K)."""
+    v = [ctypes.c_int() for _ in range(3)]
+    r = ctypes.c_double()
+    lib().orc_vgrid_dims(T, H, W, K, *(ctypes.byref(x) for x in v), ctypes.byref(r))
+    return v[0].value, v[1].value, v[2].value, r.value
+
+
+def vpath(p, e):
+    """Voxels (x, y, t) of the 3-D linear path between p and e, as an (n, 3) array."""
+    n = max(abs(p[i] - e[i]) for i in range(3)) + 1
+    xyz = np.empty(3 * n, dtype=np.int32)
+    m = lib().orc_vpath(*(int(v) for v in p), *(int(v) for v in e), _ptr(xyz))
+    assert m == n
+    return xyz.reshape(n, 3)
+
+
+def vin_window(v: int, n: int, s: int, r2: float) -> bool:
+    return bool(lib().orc_vin_window(v, n, s, r2))
+
+
+class VSolver:
+    """One supervoxel solve.  ``lab`` = (L, a, b) float64 (T, H, W) volumes,
+    ``contour`` float (T, H, W) in [0, 1]."""
+
+    def __init__(self, lab, contour, K: int, m: float = 10.0, lam: float = 0.5,
+                 sigma: float = 0.25, gamma: float = -1.0):
+        L, A, B = (np.ascontiguousarray(x, dtype=np.float64) for x in lab)
+        self.T, self.H, self.W = L.shape
+        self.N = L.size
+        self.K = int(K)
+        self.L, self.A, self.B = L, A, B
+        self.C = np.ascontiguousarray(contour, dtype=np.float64)
+        nx, ny, nt, _ = vgrid_dims(self.T, self.H, self.W, self.K)
+        Keff = nx * ny * nt
+        self.labels = np.zeros((self.T, self.H, self.W), dtype=np.int32)
+        for name in ("n", "sx", "sy", "st"):
+            setattr(self, name, np.zeros(Keff, np.int64))
+        for name in ("cL", "cA", "cB"):
+            setattr(self, name, np.zeros(Keff))
+        for name in ("ex", "ey", "et"):
+            setattr(self, name, np.zeros(Keff, np.int32))
+        c = _VCtx()
+        c.T, c.H, c.W, c.K = self.T, self.H, self.W, self.K
+        c.m, c.lam, c.sigma, c.gamma = m, lam, sigma, gamma
+        for name in ("L", "A", "B", "C", "labels", "n", "sx", "sy", "st", "cL", "cA", "cB",
+                     "ex", "ey", "et"):
+            setattr(c, name, _ptr(getattr(self, name)))
+        self._c = c
+        if lib().orc_vinit(ctypes.byref(c)) != 0:
+            raise ValueError("invalid supervoxel arguments")
+        assert c.Keff == Keff
+
+    @property
+    def r(self) -> float:
+        return self._c.r
+
+    @property
+    def r2(self) -> float:
+        return self._c.r2
+
+    @property
+    def gamma(self) -> float:
+        return self._c.gamma
+
+    @property
+    def Keff(self) -> int:
+        return self._c.Keff
+
+    @property
+    def grid(self):
+        return self._c.nx, self._c.ny, self._c.nt
+
+    @property
+    def orphans(self) -> int:
+        return self._c.orphans
+
+    @property
+    def projections(self) -> int:
+        return self._c.projections
+
+    def state(self):
+        return {k: getattr(self, k).copy() for k in
+                ("labels", "n", "sx", "sy", "st", "cL", "cA", "cB", "ex", "ey", "et")}
+
+    def set_state(self, st):
+        for k, v in st.items():
+            getattr(self, k)[...] = v
+
+    def assign(self, return_d: bool = False):
+        d = np.empty((self.T, self.H, self.W)) if return_d else None
+        lib().orc_vassign(ctypes.byref(self._c), _ptr(d) if return_d else None)
+        return d
+
+    def update(self):
+        lib().orc_vupdate(ctypes.byref(self._c))
+
+    def iterate(self, iters: int = 1):
+        lib().orc_viterate(ctypes.byref(self._c), int(iters))
+
+    def distance(self, x: int, y: int, t: int, k: int):
+        n = ctypes.c_int32()
+        D = lib().orc_vdistance(ctypes.byref(self._c), int(x), int(y), int(t), int(k),
+                                ctypes.byref(n))
+        return D, n.value

@@ -583,3 +583,253 @@ void orc_gradient_prior(const double *L, const double *A, const double *B, int H
     int64_t N = (int64_t)H * W;
     for (int64_t p = 0; p < N; p++) out[p] = gmax > 0.0 ? out[p] / gmax : 0.0;
 }
+
+/* ======================================================================== */
+/* Supervoxels: SCALP on a video volume (the extension the paper's           */
+/* conclusion names as future work).  Readings, each the 2-D rule taken      */
+/* axis by axis (listed in the design doc):                                       */
+/*   - volume T frames x H x W, voxel (x, y, t) at index (t*H + y)*W + x;    */
+/*   - r = cbrt(N/K) (host C library); grid nx = max(1, round(W/r)),         */
+/*     ny = max(1, round(H/r)), nt = max(1, round(T/r)); voxel starts in     */
+/*     cell floor(t*nt/T)*ny*nx + floor(y*ny/H)*nx + floor(x*nx/W);          */
+/*   - window: |v - s/n| <= r per axis, decided as d*d <= (n*n)*r2 in double */
+/*     with d = n*v - s exact, r2 = r*r, each product rounded once;          */
+/*   - path: 3-D digital segment, traced from the lexicographically smaller  */
+/*     end (x, then y, then t); the major axis is the one with the largest   */
+/*     |delta| (ties: x, then y, then t); step i moves each other axis by    */
+/*     round-half-up(i*|delta_j|/ns); |P| = ns + 1;                          */
+/*   - D as Eq. 3 with the squared 3-D distance; projection (Eq. 4) in exact */
+/*     integers, ties to the smallest voxel index; no connectivity step.     */
+/* ======================================================================== */
+typedef struct {
+    int32_t T, H, W, K;
+    int32_t nx, ny, nt, Keff;
+    double m, lambda, sigma, gamma; /* gamma < 0 selects 2r */
+    double r, r2;                   /* filled by orc_vinit */
+    const double *L, *A, *B, *C;    /* N each */
+    int32_t *labels;                /* N */
+    int64_t *n, *sx, *sy, *st;      /* Keff */
+    double *cL, *cA, *cB;           /* Keff */
+    int32_t *ex, *ey, *et;          /* Keff: path endpoint */
+    int64_t orphans, projections;
+} orc_vctx;
+
+void orc_vgrid_dims(int T, int H, int W, int K, int *nx, int *ny, int *nt, double *r)
+{
+    double N = (double)T * (double)H * (double)W;
+    double rr = cbrt(N / (double)K);
+    int d[3] = {W, H, T}, g[3];
+    for (int i = 0; i < 3; i++) {
+        g[i] = (int)floor((double)d[i] / rr + 0.5);
+        if (g[i] < 1) g[i] = 1;
+        if (g[i] > d[i]) g[i] = d[i];
+    }
+    *nx = g[0];
+    *ny = g[1];
+    *nt = g[2];
+    *r = rr;
+}
+
+int orc_vpath(int px, int py, int pt, int ex, int ey, int et, int32_t *xyz)
+{
+    int p[3] = {px, py, pt}, e[3] = {ex, ey, et}, a[3], b[3];
+    int p_first = px < ex || (px == ex && (py < ey || (py == ey && pt <= et)));
+    for (int j = 0; j < 3; j++) {
+        a[j] = p_first ? p[j] : e[j];
+        b[j] = p_first ? e[j] : p[j];
+    }
+    int ad[3], sg[3], major = 0;
+    for (int j = 0; j < 3; j++) {
+        int d = b[j] - a[j];
+        ad[j] = d < 0 ? -d : d;
+        sg[j] = d < 0 ? -1 : 1;
+        if (ad[j] > ad[major]) major = j;
+    }
+    int ns = ad[major];
+    for (int i = 0; i <= ns; i++)
+        for (int j = 0; j < 3; j++) {
+            int off = j == major ? i : (ns ? (2 * i * ad[j] + ns) / (2 * ns) : 0);
+            xyz[3 * i + j] = a[j] + sg[j] * off;
+        }
+    return ns + 1;
+}
+
+static int vin_window(int64_t v, int64_t n, int64_t s, double r2)
+{
+    double d = (double)(n * v - s);
+    double nn = (double)n * (double)n;
+    return d * d <= nn * r2;
+}
+
+int orc_vin_window(int64_t v, int64_t n, int64_t s, double r2) { return vin_window(v, n, s, r2); }
+
+static double vdc_at(const orc_vctx *c, int64_t q, int k)
+{
+    double dl = c->L[q] - c->cL[k];
+    double da = c->A[q] - c->cA[k];
+    double db = c->B[q] - c->cB[k];
+    return dl * dl + da * da + db * db;
+}
+
+double orc_vdistance(const orc_vctx *c, int x, int y, int t, int k, int32_t *path_len)
+{
+    int64_t W = c->W, H = c->H;
+    int maxd = c->W > c->H ? c->W : c->H;
+    if (c->T > maxd) maxd = c->T;
+    int32_t *xyz = (int32_t *)malloc(sizeof(int32_t) * 3 * (size_t)(maxd + 1));
+    int len = orc_vpath(x, y, t, c->ex[k], c->ey[k], c->et[k], xyz);
+    double sum_dc = 0.0, sum_w = 0.0;
+    for (int i = 0; i < len; i++) {
+        int64_t q = ((int64_t)xyz[3 * i + 2] * H + xyz[3 * i + 1]) * W + xyz[3 * i];
+        sum_dc += vdc_at(c, q, k);
+        double cq = c->C[q];
+        sum_w += 1.0 - exp(-(cq * cq) / (c->sigma * c->sigma));
+    }
+    free(xyz);
+    int64_t p = ((int64_t)t * H + y) * W + x;
+    double dc_path = c->lambda * vdc_at(c, p, k) + (1.0 - c->lambda) * sum_dc / len; /* Eq. 1 */
+    double d_contour = 1.0 + c->gamma / len * sum_w;                               /* Eq. 2 */
+    double xk = (double)c->sx[k] / (double)c->n[k];
+    double yk = (double)c->sy[k] / (double)c->n[k];
+    double tk = (double)c->st[k] / (double)c->n[k];
+    double ds = (x - xk) * (x - xk) + (y - yk) * (y - yk) + (t - tk) * (t - tk);
+    if (path_len) *path_len = len;
+    return dc_path * d_contour + ds * (c->m * c->m) / (c->r * c->r); /* Eq. 3 */
+}
+
+static void vproject_center(orc_vctx *c, int k)
+{
+    int64_t N = (int64_t)c->T * c->H * c->W, HW = (int64_t)c->H * c->W;
+    i128 best = -1;
+    int64_t best_p = -1;
+    for (int64_t p = 0; p < N; p++) {
+        if (c->labels[p] != k) continue;
+        int64_t t = p / HW, y = (p % HW) / c->W, x = p % c->W;
+        i128 dx = (i128)c->n[k] * x - c->sx[k];
+        i128 dy = (i128)c->n[k] * y - c->sy[k];
+        i128 dt = (i128)c->n[k] * t - c->st[k];
+        i128 d2 = dx * dx + dy * dy + dt * dt;
+        if (best_p < 0 || d2 < best) {
+            best = d2;
+            best_p = p;
+        }
+    }
+    c->ex[k] = (int32_t)(best_p % c->W);
+    c->ey[k] = (int32_t)((best_p % HW) / c->W);
+    c->et[k] = (int32_t)(best_p / HW);
+}
+
+void orc_vupdate(orc_vctx *c)
+{
+    int64_t N = (int64_t)c->T * c->H * c->W, HW = (int64_t)c->H * c->W;
+    int K = c->Keff;
+    int64_t *n = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    int64_t *sx = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    int64_t *sy = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    int64_t *st = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    double *sl = (double *)calloc((size_t)K, sizeof(double));
+    double *sa = (double *)calloc((size_t)K, sizeof(double));
+    double *sb = (double *)calloc((size_t)K, sizeof(double));
+    for (int64_t p = 0; p < N; p++) {
+        int k = c->labels[p];
+        n[k] += 1;
+        sx[k] += p % c->W;
+        sy[k] += (p % HW) / c->W;
+        st[k] += p / HW;
+        sl[k] += c->L[p];
+        sa[k] += c->A[p];
+        sb[k] += c->B[p];
+    }
+    c->projections = 0;
+    for (int k = 0; k < K; k++) {
+        if (n[k] == 0) continue; /* empty cluster: unchanged */
+        c->n[k] = n[k];
+        c->sx[k] = sx[k];
+        c->sy[k] = sy[k];
+        c->st[k] = st[k];
+        c->cL[k] = sl[k] / (double)n[k];
+        c->cA[k] = sa[k] / (double)n[k];
+        c->cB[k] = sb[k] / (double)n[k];
+        c->ex[k] = (int32_t)((2 * sx[k] + n[k]) / (2 * n[k]));
+        c->ey[k] = (int32_t)((2 * sy[k] + n[k]) / (2 * n[k]));
+        c->et[k] = (int32_t)((2 * st[k] + n[k]) / (2 * n[k]));
+        if (c->labels[((int64_t)c->et[k] * c->H + c->ey[k]) * c->W + c->ex[k]] != k) {
+            vproject_center(c, k);
+            c->projections++;
+        }
+    }
+    free(n); free(sx); free(sy); free(st); free(sl); free(sa); free(sb);
+}
+
+int orc_vinit(orc_vctx *c)
+{
+    int64_t N = (int64_t)c->T * c->H * c->W, HW = (int64_t)c->H * c->W;
+    if (c->T < 1 || c->H < 1 || c->W < 1 || c->K < 1 || c->K > N) return -1;
+    orc_vgrid_dims(c->T, c->H, c->W, c->K, &c->nx, &c->ny, &c->nt, &c->r);
+    c->r2 = c->r * c->r;
+    if (c->gamma < 0) c->gamma = 2.0 * c->r;
+    c->Keff = c->nx * c->ny * c->nt;
+    for (int64_t p = 0; p < N; p++) {
+        int64_t t = p / HW, y = (p % HW) / c->W, x = p % c->W;
+        int cx = (int)(x * c->nx / c->W);
+        int cy = (int)(y * c->ny / c->H);
+        int ct = (int)(t * c->nt / c->T);
+        c->labels[p] = (ct * c->ny + cy) * c->nx + cx;
+    }
+    orc_vupdate(c);
+    c->orphans = 0;
+    return 0;
+}
+
+/* Window bounds along one axis: every v in [lo, hi] of [0, lim) passes. */
+static void vwindow(int64_t n, int64_t s, double r, double r2, int lim, int *lo, int *hi)
+{
+    double c = (double)s / (double)n;
+    int a = (int)floor(c - r) - 1, b = (int)ceil(c + r) + 1;
+    if (a < 0) a = 0;
+    if (b > lim - 1) b = lim - 1;
+    while (a <= b && !vin_window(a, n, s, r2)) a++;
+    while (b >= a && !vin_window(b, n, s, r2)) b--;
+    *lo = a;
+    *hi = b;
+}
+
+int64_t orc_vassign(orc_vctx *c, double *dbest)
+{
+    int64_t N = (int64_t)c->T * c->H * c->W;
+    double *d = (double *)malloc(sizeof(double) * (size_t)N);
+    for (int64_t p = 0; p < N; p++) d[p] = INFINITY;
+    for (int k = 0; k < c->Keff; k++) {
+        int x0, x1, y0, y1, t0, t1;
+        vwindow(c->n[k], c->sx[k], c->r, c->r2, c->W, &x0, &x1);
+        vwindow(c->n[k], c->sy[k], c->r, c->r2, c->H, &y0, &y1);
+        vwindow(c->n[k], c->st[k], c->r, c->r2, c->T, &t0, &t1);
+        for (int t = t0; t <= t1; t++)
+            for (int y = y0; y <= y1; y++)
+                for (int x = x0; x <= x1; x++) {
+                    double D = orc_vdistance(c, x, y, t, k, NULL);
+                    int64_t p = ((int64_t)t * c->H + y) * c->W + x;
+                    if (D < d[p]) {
+                        d[p] = D;
+                        c->labels[p] = k;
+                    }
+                }
+    }
+    int64_t orphans = 0;
+    for (int64_t p = 0; p < N; p++) {
+        if (d[p] == INFINITY) orphans++;
+        if (dbest) dbest[p] = d[p];
+    }
+    free(d);
+    c->orphans = orphans;
+    return orphans;
+}
+
+int orc_viterate(orc_vctx *c, int iters)
+{
+    for (int it = 0; it < iters; it++) {
+        orc_vassign(c, NULL);
+        orc_vupdate(c);
+    }
+    return 0;
+}

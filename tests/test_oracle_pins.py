@@ -591,3 +591,153 @@ def test_gradient_prior_step_and_flat():
     assert np.all(C[:, 2:] == 0)
     flat = np.full((5, 8, 3), 77, np.uint8)
     assert np.all(oracle.gradient_prior(oracle.lab_from_rgb(flat)) == 0)
+
+
+# --------------------------------------------------------------------------
+# Supervoxels (SCALP on (T, H, W) volumes; the readings are the 2-D ones taken
+# axis by axis).
+# --------------------------------------------------------------------------
+def test_vpath_properties():
+    from fractions import Fraction
+
+    rng = np.random.default_rng(5)
+    pts = rng.integers(0, 9, size=(600, 6))
+    pts = np.concatenate([pts, [[3, 3, 3, 3, 3, 3], [0, 0, 0, 8, 8, 8], [0, 8, 0, 8, 0, 8],
+                                [2, 5, 1, 6, 1, 3]]])
+    for q in pts:
+        p, e = tuple(int(v) for v in q[:3]), tuple(int(v) for v in q[3:])
+        P = oracle.vpath(p, e)
+        d = [abs(e[j] - p[j]) for j in range(3)]
+        ns = max(d)
+        assert len(P) == ns + 1
+        # traced from the lexicographically smaller end (x, then y, then t)
+        a, b = (p, e) if p <= e else (e, p)
+        assert tuple(P[0]) == a and tuple(P[-1]) == b
+        # symmetric: the other direction gives the same voxel sequence
+        assert np.array_equal(oracle.vpath(e, p), P)
+        major = int(np.argmax(d))  # the first largest |delta|: x, then y, then t
+        for i, v in enumerate(P):
+            for j in range(3):
+                sgn = 1 if b[j] >= a[j] else -1
+                off = sgn * (int(v[j]) - a[j])
+                if j == major:
+                    assert off == i
+                else:
+                    # the nearest integer to the exact segment point, half up
+                    exact = Fraction(i * d[j], ns) if ns else Fraction(0)
+                    assert off == int((exact + Fraction(1, 2)).__floor__())
+
+
+def test_vpath_reduces_to_2d_path():
+    rng = np.random.default_rng(6)
+    for _ in range(300):
+        x0, y0, x1, y1, t = (int(v) for v in rng.integers(0, 12, 5))
+        P3 = oracle.vpath((x0, y0, t), (x1, y1, t))
+        P2 = oracle.path((x0, y0), (x1, y1))
+        assert np.array_equal(P3[:, :2], P2) and np.all(P3[:, 2] == t)
+
+
+def test_vconstant_volume_fixed_point():
+    # 16^3 voxels, K = 64: r = 4, a 4x4x4 grid of 4^3 cells; a constant image
+    # with no contour leaves only the spatial term, and the grid is a fixed point
+    T = H = W = 16
+    rgb = np.full((T, H, W, 3), 120, np.uint8)
+    s = oracle.VSolver(oracle.lab_from_rgb(rgb), np.zeros((T, H, W)), 64)
+    assert s.r == 4.0 and s.grid == (4, 4, 4)
+    cells = s.labels.copy()
+    n0, sx0 = s.n.copy(), s.sx.copy()
+    s.iterate(3)
+    assert np.array_equal(s.labels, cells) and np.array_equal(s.n, n0) and np.array_equal(s.sx, sx0)
+    assert s.projections == 0
+
+
+def _vwindow_mask(s, k, T, H, W):
+    """Voxels of cluster k's window, by the per-axis reading (double, as stated)."""
+    def axis(v, n, sv):
+        d = (n * v - sv).astype(np.float64)
+        return d * d <= (float(n) * float(n)) * s.r2
+    t, y, x = np.arange(T), np.arange(H), np.arange(W)
+    n = int(s.n[k])
+    return (axis(t, n, int(s.st[k]))[:, None, None] & axis(y, n, int(s.sy[k]))[None, :, None]
+            & axis(x, n, int(s.sx[k]))[None, None, :])
+
+
+def test_vslic_special_case():
+    # lambda = 1, gamma = 0: D = d_c(p, C_k) + m^2/r^2 d_s, a plain 3-D SLIC
+    # assignment, computed here in numpy over every cluster whose window holds p
+    rng = np.random.default_rng(7)
+    T, H, W = 4, 14, 18
+    rgb = rng.integers(0, 256, (T, H, W, 3), dtype=np.uint8)
+    lab = oracle.lab_from_rgb(rgb)
+    s = oracle.VSolver(lab, rng.uniform(size=(T, H, W)), 10, lam=1.0, gamma=0.0)
+    s.iterate(1)
+    st = s.state()
+    s.assign()
+    tt, yy, xx = np.meshgrid(np.arange(T), np.arange(H), np.arange(W), indexing="ij")
+    best = np.full((T, H, W), np.inf)
+    lab_ref = st["labels"].copy()
+    for k in range(s.Keff):
+        if st["n"][k] == 0:
+            continue
+        m = _vwindow_mask(s, k, T, H, W)
+        n = st["n"][k]
+        dc = ((lab[0] - st["cL"][k]) ** 2 + (lab[1] - st["cA"][k]) ** 2 + (lab[2] - st["cB"][k]) ** 2)
+        ds = (xx - st["sx"][k] / n) ** 2 + (yy - st["sy"][k] / n) ** 2 + (tt - st["st"][k] / n) ** 2
+        D = dc + (10.0 ** 2 / s.r ** 2) * ds
+        take = m & (D < best)
+        best[take] = D[take]
+        lab_ref[take] = k
+    assert np.array_equal(s.labels, lab_ref)
+
+
+def test_vbruteforce_tiny():
+    rng = np.random.default_rng(8)
+    T, H, W = 3, 8, 10
+    rgb = rng.integers(0, 256, (T, H, W, 3), dtype=np.uint8)
+    s = oracle.VSolver(oracle.lab_from_rgb(rgb), rng.uniform(size=(T, H, W)), 8)
+    s.iterate(2)
+    st = s.state()
+    s.assign()
+    for t in range(T):
+        for y in range(H):
+            for x in range(W):
+                best, kb = np.inf, int(st["labels"][t, y, x])
+                for k in range(s.Keff):
+                    if st["n"][k] == 0 or not _vwindow_mask(s, k, T, H, W)[t, y, x]:
+                        continue
+                    D, _ = s.distance(x, y, t, k)
+                    if D < best:
+                        best, kb = D, k
+                assert s.labels[t, y, x] == kb
+
+
+def test_vupdate_and_projection():
+    rng = np.random.default_rng(9)
+    T, H, W = 5, 12, 16
+    rgb = rng.integers(0, 256, (T, H, W, 3), dtype=np.uint8)
+    lab = oracle.lab_from_rgb(rgb)
+    s = oracle.VSolver(lab, np.zeros((T, H, W)), 12)
+    # a label map where cluster 0 is a hollow box: its barycenter lies outside it
+    labels = np.ones((T, H, W), np.int32)
+    labels[:, 2:10, 3:13] = 0
+    labels[1:4, 4:8, 5:11] = 2
+    st = s.state()
+    st["labels"] = labels
+    s.set_state(st)
+    s.update()
+    tt, yy, xx = np.meshgrid(np.arange(T), np.arange(H), np.arange(W), indexing="ij")
+    for k in range(3):
+        m = labels == k
+        n = int(m.sum())
+        assert s.n[k] == n and s.sx[k] == xx[m].sum() and s.sy[k] == yy[m].sum()
+        assert s.st[k] == tt[m].sum()
+        assert s.cL[k] == pytest.approx(lab[0][m].mean(), rel=1e-12, abs=1e-12)
+        sx, sy, stt = int(xx[m].sum()), int(yy[m].sum()), int(tt[m].sum())
+        e = ((2 * sx + n) // (2 * n), (2 * sy + n) // (2 * n), (2 * stt + n) // (2 * n))
+        if labels[e[2], e[1], e[0]] != k:
+            # Eq. 4 by brute force in exact integers, ties to the smallest index
+            d2 = [((n * x - sx) ** 2 + (n * y - sy) ** 2 + (n * t - stt) ** 2, (t * H + y) * W + x, (x, y, t))
+                  for t, y, x in zip(tt[m], yy[m], xx[m])]
+            e = min(d2)[2]
+        assert (s.ex[k], s.ey[k], s.et[k]) == tuple(int(v) for v in e), k
+    assert s.projections >= 1
