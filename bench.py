@@ -522,6 +522,64 @@ def measure_prior(args, w, rgb, con, cells, flush):
     return res
 
 
+def measure_voxel(args, flush):
+    """Supervoxels on a synthetic video volume (moving Voronoi cells): whole
+    solves (set-up + 10 iterations, labels in device memory), Mvox*iter/s, and
+    the assignment's work against the FP32 lane peak as in the 2-D line."""
+    import torch
+
+    from paper_1903_07149_gb300 import scalp, synth
+
+    name = "video_32x240x320_k2000"
+    T, H, W, K, n_cells, seed = synth.VIDEO_WORKLOADS[name]
+    rgb, con, _ = synth.voronoi_video(T, H, W, n_cells, seed=seed)
+    d_rgb, d_con = torch.from_numpy(rgb).cuda(), torch.from_numpy(con).cuda()
+    out = torch.empty((T, H, W), dtype=torch.int32, device="cuda")
+    iters = 10
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        def step():
+            seg = scalp.VoxelSegmenter(d_rgb, d_con, K, stream=stream)
+            seg.iterate(iters)
+            seg.labels(out=out)
+            return seg
+
+        for _ in range(max(args.warmup, 1)):
+            step().close()
+        n_steps = max(args.steps // 2, 2)
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(n_steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(n_steps)]
+        torch.cuda.synchronize()
+        for i in range(n_steps):
+            flush.zero_()
+            ev0[i].record(stream)
+            step().close()
+            ev1[i].record(stream)
+        torch.cuda.synchronize()
+        # work of one iteration, counted on the device, and the iteration time
+        seg = step()
+        seg.count_samples(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        seg.iterate(1)
+        e1.record(stream)
+        samples, pairs = seg.count_samples(0)
+        torch.cuda.synchronize()
+        it_ms = e0.elapsed_time(e1)
+        keff = seg.Keff
+        seg.close()
+    ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)) / n_steps
+    N = T * H * W
+    flops = FLOPS_PER_SAMPLE * samples + FLOPS_PER_PAIR * pairs
+    peak = SMS * FP32_LANES_PER_SM * FALLBACK_SM_MHZ * 1e6 / 1e12
+    return {"workload": name, "T": T, "H": H, "W": W, "K": K, "Keff": keff, "iters": iters,
+            "value": N * iters / (ms / 1e3) / 1e6, "unit": "Mvox*iter/s", "ms_per_solve": ms,
+            "iteration_ms": it_ms, "samples_per_iteration": samples, "pairs_per_iteration": pairs,
+            "roofline": {"bound": "alu", "achieved": flops / (it_ms / 1e3) / 1e12, "unit": "TFLOP/s",
+                         "peak": peak, "frac": flops / (it_ms / 1e3) / 1e12 / peak,
+                         "note": "whole iteration (all four kernels) timed; FP32 lanes at 2070 MHz"}}
+
+
 def measure_single_form(args, w, rgb, con, storage: str, flush):
     """Plain single-image solve with the given plane storage (FP16 form)."""
     import torch
@@ -699,6 +757,7 @@ def run_ours(args):
                                           noise_sigma=w.noise_sigma, seed=w.seed)
         line["forms"]["quality_eq5_8"] = measure_quality(w, rgb, con, cells)
         line["forms"]["gradient_prior"] = measure_prior(args, w, rgb, con, cells, flush)
+        line["forms"]["supervoxels"] = measure_voxel(args, flush)
         if not args.no_serving:
             line["forms"]["serving"] = measure_serving(args, batch_imgs)
     if not args.no_cpu_baseline and world == 1:

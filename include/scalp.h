@@ -245,6 +245,60 @@ int scalp_gradient_prior(const scalp_image *image, float *out, int64_t out_strid
                          int32_t out_on_device, void *stream, void *workspace,
                          size_t workspace_bytes);
 
+/* ---- Supervoxels --------------------------------------------------------
+ * SCALP on a video volume, the extension the paper's conclusion names as
+ * future work.  Every rule is the 2-D one taken axis by axis: r = cbrt(N/K)
+ * (N = T*H*W voxels) and a 3-D regular grid of step r; cluster k's candidates
+ * are the voxels with |v - v_k| <= r on each axis, decided as
+ * d*d <= (n*n)*r^2 in double with d = n*v - S_v exact; the linear path is the
+ * 3-D digital segment traced from the lexicographically smaller end
+ * (x, then y, then t), the axis with the largest |delta| stepping by one and
+ * each other axis by round-half-up(i*|delta_j|/|delta_major|); D is Eq. 3
+ * with the squared 3-D distance; projection (Eq. 4) in exact integers, ties
+ * to the smallest voxel index.  There is no connectivity step.  FP32 planes
+ * and the input prior only (params->storage and params->prior otherwise give
+ * SCALP_E_ARG); params->use_graph and global_walk are ignored.  Voxel
+ * (x, y, t) is element (t*H + y)*W + x of every volume. */
+typedef struct {
+    int32_t T, H, W;          /* frames, rows, columns, each >= 1, T*H*W <= 2^30 */
+    const uint8_t *rgb;       /* T*H*W*3 sRGB bytes, contiguous */
+    const float *contour;     /* T*H*W prior values in [0, 1], or NULL for 0 */
+    int32_t on_device;        /* 1 if rgb and contour are device pointers */
+} scalp_volume;
+
+typedef struct {
+    int32_t T, H, W, K;
+    int32_t nx, ny, nt, Keff; /* the 3-D grid, Keff = nx*ny*nt clusters */
+    double r;                 /* cbrt(N/K) */
+    double gamma;             /* resolved Eq. 2 weight */
+    int32_t iterations;
+} scalp_voxel_info;
+
+typedef struct {
+    int32_t *labels;          /* N */
+    int64_t *n, *sx, *sy, *st;/* Keff: |S_k| and the coordinate sums */
+    double *color;            /* Keff x 3 */
+    int32_t *endpoint;        /* Keff x 3: (x, y, t) path end */
+} scalp_voxel_state;
+
+typedef struct scalp_vctx scalp_vctx;
+
+size_t scalp_voxel_workspace_bytes(int32_t T, int32_t H, int32_t W, int32_t K,
+                                   const scalp_params *params);
+/* Set-up and grid initialisation (synchronises the stream). */
+int scalp_voxel_init(scalp_vctx **out, const scalp_volume *volume, int32_t K, float m,
+                     const scalp_params *params);
+int scalp_voxel_iterate(scalp_vctx *ctx, int32_t n);
+/* Labels (N int32) to host or device memory; synchronises and reports device
+ * errors. */
+int scalp_voxel_labels(scalp_vctx *ctx, int32_t *out, int32_t out_on_device);
+int scalp_voxel_get_info(const scalp_vctx *ctx, scalp_voxel_info *info);
+int scalp_voxel_get_state(scalp_vctx *ctx, const scalp_voxel_state *state);
+int scalp_voxel_set_state(scalp_vctx *ctx, const scalp_voxel_state *state);
+/* As scalp_count_samples, for the supervoxel assignment. */
+int scalp_voxel_count_samples(scalp_vctx *ctx, int32_t enable, int64_t *samples, int64_t *pairs);
+void scalp_voxel_destroy(scalp_vctx *ctx);
+
 /* ---- Serving: continuous batching of solves in flight ------------------------
  *
  * Not part of the paper.  A server owns a caller-allocated device memory pool

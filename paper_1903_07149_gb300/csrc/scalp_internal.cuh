@@ -28,6 +28,34 @@ constexpr int ASSIGN_CTAS_PER_SM = 2;
 // of 8-bit sRGB has |L|, |a|, |b| < 108, so 32 such values sum below 2^31.
 constexpr int COLOR_FRAC_BITS = 19;
 
+// sRGB -> CIELab (Sec. II-A): the sRGB inverse transfer function (a 256-entry
+// table `lin`), the D65 sRGB->XYZ matrix, normalisation by the XYZ of sRGB
+// white (the matrix row sums), then CIE 1976 companding with the linear
+// segment below (6/29)^3.
+static __constant__ float c_rgb2xyz[9] = {0.4124564f, 0.3575761f, 0.1804375f,
+                                   0.2126729f, 0.7151522f, 0.0721750f,
+                                   0.0193339f, 0.1191920f, 0.9503041f};
+
+__device__ __forceinline__ float lab_f(float t)
+{
+    const float d3 = (6.0f / 29.0f) * (6.0f / 29.0f) * (6.0f / 29.0f);
+    return t > d3 ? cbrtf(t) : t * (841.0f / 108.0f) + (4.0f / 29.0f);
+}
+
+// CIELab of one sRGB pixel; lin = the 256-entry inverse transfer function.
+__device__ __forceinline__ float3 srgb_to_lab(const float *lin, const uint8_t *px)
+{
+    const float wx = c_rgb2xyz[0] + c_rgb2xyz[1] + c_rgb2xyz[2];
+    const float wy = c_rgb2xyz[3] + c_rgb2xyz[4] + c_rgb2xyz[5];
+    const float wz = c_rgb2xyz[6] + c_rgb2xyz[7] + c_rgb2xyz[8];
+    float R = lin[px[0]], G = lin[px[1]], B = lin[px[2]];
+    float X = c_rgb2xyz[0] * R + c_rgb2xyz[1] * G + c_rgb2xyz[2] * B;
+    float Y = c_rgb2xyz[3] * R + c_rgb2xyz[4] * G + c_rgb2xyz[5] * B;
+    float Z = c_rgb2xyz[6] * R + c_rgb2xyz[7] * G + c_rgb2xyz[8] * B;
+    float fx = lab_f(X / wx), fy = lab_f(Y / wy), fz = lab_f(Z / wz);
+    return make_float3(116.0f * fy - 16.0f, 500.0f * (fx - fy), 200.0f * (fy - fz));
+}
+
 // What the assignment kernel reads about one cluster (48 bytes).
 struct ClusterDev {
     float L, a, b;           // mean CIELab colour

@@ -17,16 +17,6 @@ namespace scalp {
 // sums), then the CIE 1976 L*a*b* companding with the linear segment below
 // (6/29)^3.
 // ---------------------------------------------------------------------------
-__constant__ float c_rgb2xyz[9] = {0.4124564f, 0.3575761f, 0.1804375f,
-                                   0.2126729f, 0.7151522f, 0.0721750f,
-                                   0.0193339f, 0.1191920f, 0.9503041f};
-
-__device__ __forceinline__ float lab_f(float t)
-{
-    const float d3 = (6.0f / 29.0f) * (6.0f / 29.0f) * (6.0f / 29.0f);
-    return t > d3 ? cbrtf(t) : t * (841.0f / 108.0f) + (4.0f / 29.0f);
-}
-
 // Inverse sRGB transfer function for the 256 byte values, in double, once.
 __global__ void k_srgb_table(float *lut)
 {
@@ -35,20 +25,6 @@ __global__ void k_srgb_table(float *lut)
         const double c = i / 255.0;
         lut[i] = (float)(c <= 0.04045 ? c / 12.92 : pow((c + 0.055) / 1.055, 2.4));
     }
-}
-
-// CIELab of one sRGB pixel; lin = the 256-entry inverse transfer function.
-__device__ __forceinline__ float3 srgb_to_lab(const float *lin, const uint8_t *px)
-{
-    const float wx = c_rgb2xyz[0] + c_rgb2xyz[1] + c_rgb2xyz[2];
-    const float wy = c_rgb2xyz[3] + c_rgb2xyz[4] + c_rgb2xyz[5];
-    const float wz = c_rgb2xyz[6] + c_rgb2xyz[7] + c_rgb2xyz[8];
-    float R = lin[px[0]], G = lin[px[1]], B = lin[px[2]];
-    float X = c_rgb2xyz[0] * R + c_rgb2xyz[1] * G + c_rgb2xyz[2] * B;
-    float Y = c_rgb2xyz[3] * R + c_rgb2xyz[4] * G + c_rgb2xyz[5] * B;
-    float Z = c_rgb2xyz[6] * R + c_rgb2xyz[7] * G + c_rgb2xyz[8] * B;
-    float fx = lab_f(X / wx), fy = lab_f(Y / wy), fz = lab_f(Z / wz);
-    return make_float3(116.0f * fy - 16.0f, 500.0f * (fx - fy), 200.0f * (fy - fz));
 }
 
 __global__ void k_setup(SolveArgs a, const uint8_t *__restrict__ rgb, long long rgb_stride,

@@ -1,0 +1,884 @@
+// scalp_voxel.cu -- supervoxels: SCALP on a video volume (T frames x H x W),
+// the extension the paper's conclusion names as future work.  Each rule is the
+// 2-D one taken axis by axis:
+//   * r = cbrt(N/K) (computed on the host); a 3-D regular grid of step r;
+//   * candidates of cluster k: |v - s_v/n| <= r on each axis, decided as
+//     d*d <= (n*n)*r^2 in double with d = n*v - s_v exact (each product
+//     rounded once), kept as integer bounds per axis;
+//   * the linear path is a 3-D digital segment traced from the
+//     lexicographically smaller end (x, then y, then t); the axis with the
+//     largest |delta| (ties: x, y, t) steps by one, each other axis by
+//     round-half-up(i*|delta_j|/ns);
+//   * D is Eq. 3 with the squared 3-D distance, the colour and contour terms of
+//     Eq. 1-2 along the path;
+//   * update and projection (Eq. 4) as in 2-D, with the voxel index as the
+//     tie-break; there is no connectivity step.
+//
+// One iteration is four kernels: assignment (one 512-thread CTA per 16x8x4
+// tile, one voxel per thread, paths walked in global memory, warp-aggregated
+// integer sums), update (one thread per cluster), projection (one CTA per
+// queued cluster), candidate lists (count scan, then slot fill).
+#include <algorithm>
+#include <cfloat>
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "scalp_launch.h"
+#include "../../include/scalp.h"
+
+namespace scalp {
+namespace {
+
+constexpr int VTX = 16, VTY = 8, VTT = 4;  // voxel tile
+constexpr int VTILE = VTX * VTY * VTT;     // 512 voxels, one per thread
+constexpr int VMAX_CAND = 256;             // candidates of a tile in shared memory
+constexpr int VPROJ_THREADS = 512;
+
+struct VoxCluster {  // 64 bytes: what the assignment reads about cluster k
+    float L, a, b;
+    float xk, yk, tk;
+    int ex, ey, et;
+    int xlo, xhi, ylo, yhi, tlo, thi;
+    int pad;
+};
+static_assert(sizeof(VoxCluster) == 64, "VoxCluster layout");
+
+struct VoxAcc {  // 64 bytes: integer sums of one assignment
+    unsigned long long n, sx, sy, st, sL, sa, sb, pad;
+};
+
+struct VoxArgs {
+    int T, H, W, K, Keff, nx, ny, nt;
+    long long N, HW;
+    double r, r2;
+    float lam, gamma, ms2;
+    int n_tx, n_ty, n_tt;
+    int tpw_x, tpw_y, tpw_t;  // bound on the tiles one window spans, per axis
+    long long tile_cap;
+    int count_samples;
+    const float4 *plane;      // (L, a, b, w) per voxel
+    int *labels;
+    long long *st_n, *st_sx, *st_sy, *st_st;
+    float4 *st_col;
+    int4 *st_end;             // (ex, ey, et, 0)
+    VoxCluster *cdev;
+    VoxAcc *acc;
+    int *prev_win;            // 6 ints per cluster: the window the last assignment used
+    int *proj_list;
+    int *tile_count, *tile_off, *tile_cursor, *tile_list;
+    DevCounters *ctr;
+    float *lut;
+};
+
+// ---------------------------------------------------------------------------
+// Windows: exact integer n*v - s, then d*d <= (n*n)*r^2 in double, each
+// product rounded once (__dmul_rn: no contraction).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool vin_window(long long v, long long n, long long s, double r2)
+{
+    const double d = (double)(n * v - s);
+    return __dmul_rn(d, d) <= __dmul_rn(__dmul_rn((double)n, (double)n), r2);
+}
+
+__device__ __forceinline__ void vwindow(long long n, long long s, double r, double r2, int lim, int &lo,
+                                        int &hi)
+{
+    const double c = (double)s / (double)n;
+    int a = (int)floor(c - r) - 1, b = (int)ceil(c + r) + 1;
+    a = max(a, 0);
+    b = min(b, lim - 1);
+    while (a <= b && !vin_window(a, n, s, r2)) ++a;
+    while (b >= a && !vin_window(b, n, s, r2)) --b;
+    lo = a;
+    hi = b;
+}
+
+// ---------------------------------------------------------------------------
+// Set-up: CIELab, contour factor, grid label.
+// ---------------------------------------------------------------------------
+__global__ void k_vsetup(VoxArgs a, const uint8_t *__restrict__ rgb, const float *__restrict__ contour,
+                         float sigma, float4 *plane)
+{
+    __shared__ float lin[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) lin[i] = a.lut[i];
+    __syncthreads();
+    const float inv_s2 = 1.0f / (sigma * sigma);
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < a.N;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int t = (int)(p / a.HW);
+        const long long q = p - (long long)t * a.HW;
+        const int y = (int)(q / a.W), x = (int)(q - (long long)y * a.W);
+        const float3 lab = srgb_to_lab(lin, rgb + 3 * p);
+        const float c = contour ? contour[p] : 0.0f;
+        plane[p] = make_float4(lab.x, lab.y, lab.z, -expm1f(-(c * c) * inv_s2));
+        const int cx = (int)((long long)x * a.nx / a.W);
+        const int cy = (int)((long long)y * a.ny / a.H);
+        const int ct = (int)((long long)t * a.nt / a.T);
+        a.labels[p] = (ct * a.ny + cy) * a.nx + cx;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Integer sums of (1, x, y, t, L, a, b) per label; colour fixed point
+// 2^COLOR_FRAC_BITS.  A warp's 32 voxels share a frame and lie within 32
+// columns and 2 rows of a base, so the three offsets pack into one 32-bit
+// warp sum (10 bits each).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void vaggregate(const VoxArgs &a, bool valid, int lab, int bx, int by, int bt,
+                                           int dx, int dy, int dt, float4 v)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31;
+    const float scale = (float)(1 << COLOR_FRAC_BITS);
+    const int qL = valid ? __float2int_rn(v.x * scale) : 0;
+    const int qa = valid ? __float2int_rn(v.y * scale) : 0;
+    const int qb = valid ? __float2int_rn(v.z * scale) : 0;
+    const unsigned qc = valid ? (unsigned)dx | ((unsigned)dy << 10) | ((unsigned)dt << 20) : 0u;
+    unsigned pending = __ballot_sync(FULL, valid);
+    while (pending) {
+        const int leader = __ffs(pending) - 1;
+        const int k = __shfl_sync(FULL, lab, leader);
+        const bool mine = valid && lab == k;
+        const unsigned grp = __ballot_sync(FULL, mine);
+        const long long cnt = __popc(grp);
+        const unsigned sc = __reduce_add_sync(FULL, mine ? qc : 0u);
+        const long long sL = (int)__reduce_add_sync(FULL, mine ? (unsigned)qL : 0u);
+        const long long sa = (int)__reduce_add_sync(FULL, mine ? (unsigned)qa : 0u);
+        const long long sb = (int)__reduce_add_sync(FULL, mine ? (unsigned)qb : 0u);
+        if (lane == leader) {
+            VoxAcc *c = &a.acc[k];
+            atomicAdd(&c->n, (unsigned long long)cnt);
+            atomicAdd(&c->sx, (unsigned long long)(cnt * bx + (long long)(sc & 0x3ffu)));
+            atomicAdd(&c->sy, (unsigned long long)(cnt * by + (long long)((sc >> 10) & 0x3ffu)));
+            atomicAdd(&c->st, (unsigned long long)(cnt * bt + (long long)(sc >> 20)));
+            atomicAdd(&c->sL, (unsigned long long)sL);
+            atomicAdd(&c->sa, (unsigned long long)sa);
+            atomicAdd(&c->sb, (unsigned long long)sb);
+        }
+        pending &= ~grp;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_vaccumulate(VoxArgs a)
+{
+    // 32-voxel row segments
+    const long long segs_per_row = (a.W + 31) / 32;
+    const long long n_segs = segs_per_row * a.H * a.T;
+    const long long warps = (long long)gridDim.x * (blockDim.x / 32);
+    const int lane = threadIdx.x & 31;
+    for (long long s = blockIdx.x * (long long)(blockDim.x / 32) + (threadIdx.x >> 5); s < n_segs; s += warps) {
+        const long long row = s / segs_per_row;
+        const int x0 = (int)(s - row * segs_per_row) * 32;
+        const int t = (int)(row / a.H), y = (int)(row - (long long)t * a.H);
+        const int x = x0 + lane;
+        const bool valid = x < a.W;
+        const long long p = ((long long)t * a.H + y) * a.W + x;
+        const float4 v = valid ? __ldg(a.plane + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+        const int lab = valid ? a.labels[p] : -1;
+        vaggregate(a, valid, lab, x0, y, t, lane, 0, 0, v);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Update: means, endpoint, projection request, window, record, tile counts.
+// ---------------------------------------------------------------------------
+__global__ void k_vupdate(VoxArgs a, int from_acc)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= a.Keff) return;
+    if (from_acc) {
+        const VoxAcc c = a.acc[k];
+        a.acc[k] = VoxAcc{};
+        const long long n = (long long)c.n;
+        if (n > 0) {
+            const long long sx = (long long)c.sx, sy = (long long)c.sy, st = (long long)c.st;
+            a.st_n[k] = n;
+            a.st_sx[k] = sx;
+            a.st_sy[k] = sy;
+            a.st_st[k] = st;
+            const double den = (double)n * (double)(1 << COLOR_FRAC_BITS);
+            a.st_col[k] = make_float4((float)((double)(long long)c.sL / den),
+                                      (float)((double)(long long)c.sa / den),
+                                      (float)((double)(long long)c.sb / den), 0.f);
+            const int ex = (int)((2 * sx + n) / (2 * n));
+            const int ey = (int)((2 * sy + n) / (2 * n));
+            const int et = (int)((2 * st + n) / (2 * n));
+            a.st_end[k] = make_int4(ex, ey, et, 0);
+            if (a.labels[((long long)et * a.H + ey) * a.W + ex] != k)
+                a.proj_list[atomicAdd(&a.ctr->nproj, 1)] = k;
+        }
+    }
+    const long long n = a.st_n[k], sx = a.st_sx[k], sy = a.st_sy[k], st = a.st_st[k];
+    const VoxCluster old = a.cdev[k];
+    int *pw = a.prev_win + 6 * (long long)k;
+    pw[0] = old.xlo; pw[1] = old.xhi; pw[2] = old.ylo; pw[3] = old.yhi; pw[4] = old.tlo; pw[5] = old.thi;
+    VoxCluster cd;
+    const float4 col = a.st_col[k];
+    const int4 e = a.st_end[k];
+    cd.L = col.x; cd.a = col.y; cd.b = col.z;
+    cd.xk = (float)((double)sx / (double)n);
+    cd.yk = (float)((double)sy / (double)n);
+    cd.tk = (float)((double)st / (double)n);
+    cd.ex = e.x; cd.ey = e.y; cd.et = e.z;
+    cd.pad = k;
+    vwindow(n, sx, a.r, a.r2, a.W, cd.xlo, cd.xhi);
+    vwindow(n, sy, a.r, a.r2, a.H, cd.ylo, cd.yhi);
+    vwindow(n, st, a.r, a.r2, a.T, cd.tlo, cd.thi);
+    a.cdev[k] = cd;
+    if (cd.xlo > cd.xhi || cd.ylo > cd.yhi || cd.tlo > cd.thi) return;
+    for (int tt = cd.tlo / VTT; tt <= cd.thi / VTT; ++tt)
+        for (int ty = cd.ylo / VTY; ty <= cd.yhi / VTY; ++ty)
+            for (int tx = cd.xlo / VTX; tx <= cd.xhi / VTX; ++tx)
+                atomicAdd(&a.tile_count[(tt * a.n_ty + ty) * a.n_tx + tx], 1);
+}
+
+// ---------------------------------------------------------------------------
+// Projection (Eq. 4) of the queued clusters: argmin over the voxels labelled
+// k of (n*x - Sx)^2 + (n*y - Sy)^2 + (n*t - St)^2 in 128-bit integers, ties
+// to the smallest voxel index; searched over the window the last assignment
+// used (it holds S_k) unless some voxel kept its label for lack of a
+// candidate, or at set-up: then over the whole volume.
+// ---------------------------------------------------------------------------
+struct VBest {
+    unsigned long long hi, lo;
+    long long p;
+};
+
+__device__ __forceinline__ bool vless(const VBest &u, const VBest &v)
+{
+    return u.hi < v.hi || (u.hi == v.hi && (u.lo < v.lo || (u.lo == v.lo && u.p < v.p)));
+}
+
+__device__ __forceinline__ void vshfl_min(VBest &b)
+{
+    for (int o = 16; o > 0; o >>= 1) {
+        VBest c;
+        c.hi = __shfl_xor_sync(0xffffffffu, b.hi, o);
+        c.lo = __shfl_xor_sync(0xffffffffu, b.lo, o);
+        c.p = __shfl_xor_sync(0xffffffffu, b.p, o);
+        if (vless(c, b)) b = c;
+    }
+}
+
+__global__ void __launch_bounds__(VPROJ_THREADS) k_vproject(VoxArgs a, int whole)
+{
+    __shared__ VBest s_best[VPROJ_THREADS / 32];
+    const int nproj = a.ctr->nproj;
+    const bool all = whole || a.ctr->orphans > 0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    for (int j = blockIdx.x; j < nproj; j += gridDim.x) {
+        const int k = a.proj_list[j];
+        const long long n = a.st_n[k], sx = a.st_sx[k], sy = a.st_sy[k], st = a.st_st[k];
+        int xlo = 0, xhi = a.W - 1, ylo = 0, yhi = a.H - 1, tlo = 0, thi = a.T - 1;
+        if (!all) {
+            const int *pw = a.prev_win + 6 * (long long)k;
+            xlo = pw[0]; xhi = pw[1]; ylo = pw[2]; yhi = pw[3]; tlo = pw[4]; thi = pw[5];
+        }
+        const long long w = xhi - xlo + 1, h = yhi - ylo + 1;
+        const long long vol = max(0LL, w) * max(0LL, h) * max(0LL, (long long)(thi - tlo + 1));
+        VBest b = {~0ull, ~0ull, LLONG_MAX};
+        for (long long i = tid; i < vol; i += VPROJ_THREADS) {
+            const long long plane_i = i / w;
+            const int x = xlo + (int)(i - plane_i * w);
+            const int t = tlo + (int)(plane_i / h), y = ylo + (int)(plane_i - (plane_i / h) * h);
+            const long long p = ((long long)t * a.H + y) * a.W + x;
+            if (a.labels[p] != k) continue;
+            const __int128 dx = (__int128)n * x - sx, dy = (__int128)n * y - sy, dt = (__int128)n * t - st;
+            const unsigned __int128 d2 = (unsigned __int128)(dx * dx) + (unsigned __int128)(dy * dy) +
+                                         (unsigned __int128)(dt * dt);
+            const VBest c = {(unsigned long long)(d2 >> 64), (unsigned long long)d2, p};
+            if (vless(c, b)) b = c;
+        }
+        vshfl_min(b);
+        if (lane == 0) s_best[warp] = b;
+        __syncthreads();
+        if (warp == 0) {
+            b = lane < VPROJ_THREADS / 32 ? s_best[lane] : VBest{~0ull, ~0ull, LLONG_MAX};
+            vshfl_min(b);
+            if (lane == 0) {
+                if (b.p == LLONG_MAX) {
+                    atomicExch(&a.ctr->error, ERR_BAD_LABEL);
+                } else {
+                    const int t = (int)(b.p / a.HW);
+                    const long long q = b.p - (long long)t * a.HW;
+                    const int y = (int)(q / a.W), x = (int)(q - (long long)y * a.W);
+                    a.st_end[k] = make_int4(x, y, t, 0);
+                    a.cdev[k].ex = x;
+                    a.cdev[k].ey = y;
+                    a.cdev[k].et = t;
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Candidate lists: exclusive scan of the tile counts (one CTA), then one
+// thread per (cluster, tile slot).
+// ---------------------------------------------------------------------------
+constexpr int VSCAN_THREADS = 1024;
+
+__global__ void __launch_bounds__(VSCAN_THREADS) k_vscan(VoxArgs a)
+{
+    __shared__ int s_warp[32];
+    const int n = a.n_tx * a.n_ty * a.n_tt;
+    const int per = (n + VSCAN_THREADS - 1) / VSCAN_THREADS;
+    const int b = threadIdx.x * per, e = min(n, b + per);
+    int tsum = 0;
+    for (int i = b; i < e; ++i) tsum += a.tile_count[i];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = tsum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int v = s_warp[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, v, o);
+            if (lane >= o) v += t;
+        }
+        s_warp[lane] = v;
+    }
+    __syncthreads();
+    int run = (wid ? s_warp[wid - 1] : 0) + incl - tsum;
+    for (int i = b; i < e; ++i) {
+        const int v = a.tile_count[i];
+        a.tile_off[i] = run;
+        a.tile_cursor[i] = 0;
+        a.tile_count[i] = 0;
+        run += v;
+    }
+    if (threadIdx.x == VSCAN_THREADS - 1) {
+        a.tile_off[n] = s_warp[31];
+        if (s_warp[31] > a.tile_cap) atomicExch(&a.ctr->error, ERR_TILE_LIST_OVERFLOW);
+        a.ctr->nproj = 0;
+        a.ctr->orphans = 0;
+    }
+}
+
+__global__ void k_vfill(VoxArgs a)
+{
+    const long long slots = (long long)a.tpw_x * a.tpw_y * a.tpw_t;
+    const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (i >= (long long)a.Keff * slots) return;
+    const int k = (int)(i / slots);
+    int j = (int)(i - (long long)k * slots);
+    const VoxCluster cd = a.cdev[k];
+    if (cd.xlo > cd.xhi || cd.ylo > cd.yhi || cd.tlo > cd.thi) return;
+    const int jx = j % a.tpw_x;
+    j /= a.tpw_x;
+    const int jy = j % a.tpw_y, jt = j / a.tpw_y;
+    const int tx = cd.xlo / VTX + jx, ty = cd.ylo / VTY + jy, tt = cd.tlo / VTT + jt;
+    if (tx > cd.xhi / VTX || ty > cd.yhi / VTY || tt > cd.thi / VTT) return;
+    const int tile = (tt * a.n_ty + ty) * a.n_tx + tx;
+    const int pos = a.tile_off[tile] + atomicAdd(&a.tile_cursor[tile], 1);
+    if (pos < a.tile_cap) a.tile_list[pos] = k;
+}
+
+// ---------------------------------------------------------------------------
+// Assignment: one voxel per thread, every candidate of the tile whose window
+// holds it, the smallest (D, k).  The path sums follow the 3-D stepping rule
+// in walk order, FP32.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int vpath_sums(const float4 *__restrict__ plane, int W, long long HW, int px,
+                                          int py, int pt, int ex, int ey, int et, float cL, float ca,
+                                          float cb, float &sum_dc, float &sum_w)
+{
+    const bool p_first = px < ex || (px == ex && (py < ey || (py == ey && pt <= et)));
+    const int ax = p_first ? px : ex, ay = p_first ? py : ey, at = p_first ? pt : et;
+    const int dx = (p_first ? ex : px) - ax, dy = (p_first ? ey : py) - ay, dt = (p_first ? et : pt) - at;
+    const int adx = abs(dx), ady = abs(dy), adt = abs(dt);
+    // strides (elements) of the three axes with their signs; the major axis
+    // is the first largest |delta|
+    const long long sxs = dx < 0 ? -1 : 1, sys = dy < 0 ? -(long long)W : (long long)W,
+                    sts = dt < 0 ? -HW : HW;
+    int ns, d1, d2;
+    long long smaj, s1, s2;
+    if (adx >= ady && adx >= adt) { ns = adx; smaj = sxs; d1 = ady; s1 = sys; d2 = adt; s2 = sts; }
+    else if (ady >= adt) { ns = ady; smaj = sys; d1 = adx; s1 = sxs; d2 = adt; s2 = sts; }
+    else { ns = adt; smaj = sts; d1 = adx; s1 = sxs; d2 = ady; s2 = sys; }
+    const float4 *q = plane + ((long long)at * HW + (long long)ay * W + ax);
+    const int two_ns = 2 * ns, two_d1 = 2 * d1, two_d2 = 2 * d2;
+    int e1 = ns, e2 = ns;
+    float dc = 0.f, w = 0.f;
+    for (int i = 0; i <= ns; ++i) {
+        const float4 v = __ldg(q);
+        dc += colour_dist(v, cL, ca, cb);
+        w += v.w;
+        e1 += two_d1;
+        e2 += two_d2;
+        long long step = smaj;
+        if (e1 >= two_ns) { e1 -= two_ns; step += s1; }
+        if (e2 >= two_ns) { e2 -= two_ns; step += s2; }
+        q += step;
+    }
+    sum_dc = dc;
+    sum_w = w;
+    return ns + 1;
+}
+
+__global__ void __launch_bounds__(VTILE) k_vassign(VoxArgs a)
+{
+    __shared__ VoxCluster cand[VMAX_CAND];
+    __shared__ int s_ids[VMAX_CAND];
+    const int tile = blockIdx.x;
+    const int tx = tile % a.n_tx, ty = (tile / a.n_tx) % a.n_ty, tt = tile / (a.n_tx * a.n_ty);
+    const int tid = threadIdx.x;
+    const int lx = tid % VTX, ly = (tid / VTX) % VTY, lt = tid / (VTX * VTY);
+    const int x = tx * VTX + lx, y = ty * VTY + ly, t = tt * VTT + lt;
+    const bool valid = x < a.W && y < a.H && t < a.T;
+    const int off = a.tile_off[tile];
+    const int cnt = (int)max(0LL, min((long long)a.tile_off[tile + 1], a.tile_cap) - off);
+    const long long p = ((long long)t * a.H + y) * a.W + x;
+    const float4 own = valid ? __ldg(a.plane + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+    float bestD = FLT_MAX;
+    int bestk = INT_MAX;
+    unsigned my_samples = 0, my_pairs = 0;
+    for (int c0 = 0; c0 < cnt; c0 += VMAX_CAND) {
+        const int m = min(VMAX_CAND, cnt - c0);
+        __syncthreads();
+        if (tid < m) {
+            const int k = a.tile_list[off + c0 + tid];
+            s_ids[tid] = k;
+            cand[tid] = a.cdev[k];
+        }
+        __syncthreads();
+        if (!valid) continue;
+        for (int i = 0; i < m; ++i) {
+            const VoxCluster &cd = cand[i];
+            if (x < cd.xlo || x > cd.xhi || y < cd.ylo || y > cd.yhi || t < cd.tlo || t > cd.thi) continue;
+            float sdc, sw;
+            const int len = vpath_sums(a.plane, a.W, a.HW, x, y, t, cd.ex, cd.ey, cd.et, cd.L, cd.a, cd.b,
+                                       sdc, sw);
+            const float dcp = colour_dist(own, cd.L, cd.a, cd.b);
+            const float ddx = (float)x - cd.xk, ddy = (float)y - cd.yk, ddt = (float)t - cd.tk;
+            const float ds = fmaf(ddx, ddx, fmaf(ddy, ddy, ddt * ddt));
+            const float D = scalp_distance(dcp, sdc, sw, len, a.lam, a.gamma, a.ms2, ds);
+            const int k = s_ids[i];
+            if (D < bestD || (D == bestD && k < bestk)) {
+                bestD = D;
+                bestk = k;
+            }
+            my_samples += len;
+            my_pairs += 1;
+        }
+    }
+    int lab = -1;
+    if (valid) {
+        if (bestk != INT_MAX) {
+            lab = bestk;
+            a.labels[p] = lab;
+        } else {
+            lab = a.labels[p];  // no window reaches the voxel: keep its label
+            atomicAdd(&a.ctr->orphans, 1);
+        }
+    }
+    // a warp = 32 voxels of one frame: 16 columns x 2 rows
+    const int bx = tx * VTX, by = ty * VTY + (ly & ~1), bt = t;
+    vaggregate(a, valid, lab, bx, by, bt, lx, ly & 1, 0, own);
+    if (a.count_samples) {
+        for (int o = 16; o > 0; o >>= 1) {
+            my_samples += __shfl_down_sync(0xffffffffu, my_samples, o);
+            my_pairs += __shfl_down_sync(0xffffffffu, my_pairs, o);
+        }
+        if ((tid & 31) == 0) {
+            atomicAdd(&a.ctr->samples, (unsigned long long)my_samples);
+            atomicAdd(&a.ctr->pairs, (unsigned long long)my_pairs);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------
+constexpr size_t VALIGN = 256;
+
+size_t vcarve(size_t &cur, size_t bytes)
+{
+    const size_t at = (cur + VALIGN - 1) & ~(VALIGN - 1);
+    cur = at + bytes;
+    return at;
+}
+
+struct VLayout {
+    size_t rgb, contour, plane, labels, st_n, st_sx, st_sy, st_st, st_col, st_end, cdev, acc, prev_win,
+        proj, lut, tile_count, tile_off, tile_cursor, tile_list, ctr, total;
+    long long tile_cap;
+    int n_tx, n_ty, n_tt, tpw_x, tpw_y, tpw_t;
+};
+
+// Tiles one window can span along an axis: the window holds at most
+// floor(2r) + 1 consecutive voxels (one more allowed for rounding).
+int vtiles_per_window(double r, int tile)
+{
+    const long long len = (long long)(2.0 * r) + 2;
+    return (int)((len + tile - 1) / tile + 1);
+}
+
+bool vsizes_ok(int T, int H, int W, int K)
+{
+    if (T < 1 || H < 1 || W < 1 || K < 1) return false;
+    const long long N = (long long)T * H * W;
+    if (N > (1LL << 30) || W > 65535 || H > 65535 || T > 65535) return false;
+    return K <= N;
+}
+
+void vgrid(int T, int H, int W, int K, int &nx, int &ny, int &nt, double &r)
+{
+    const double N = (double)T * (double)H * (double)W;
+    r = std::cbrt(N / (double)K);
+    const int d[3] = {W, H, T};
+    int g[3];
+    for (int i = 0; i < 3; ++i) {
+        g[i] = (int)std::floor((double)d[i] / r + 0.5);
+        g[i] = std::max(1, std::min(g[i], d[i]));
+    }
+    nx = g[0];
+    ny = g[1];
+    nt = g[2];
+}
+
+VLayout vmake_layout(int T, int H, int W, int K)
+{
+    VLayout L{};
+    const size_t N = (size_t)T * H * W;
+    int nx, ny, nt;
+    double r;
+    vgrid(T, H, W, K, nx, ny, nt, r);
+    const size_t Keff = (size_t)nx * ny * nt;
+    L.n_tx = (W + VTX - 1) / VTX;
+    L.n_ty = (H + VTY - 1) / VTY;
+    L.n_tt = (T + VTT - 1) / VTT;
+    L.tpw_x = std::min(vtiles_per_window(r, VTX), L.n_tx);
+    L.tpw_y = std::min(vtiles_per_window(r, VTY), L.n_ty);
+    L.tpw_t = std::min(vtiles_per_window(r, VTT), L.n_tt);
+    L.tile_cap = (long long)Keff * L.tpw_x * L.tpw_y * L.tpw_t;
+    const size_t n_tiles = (size_t)L.n_tx * L.n_ty * L.n_tt;
+    size_t cur = 0;
+    L.rgb = vcarve(cur, 3 * N);
+    L.contour = vcarve(cur, 4 * N);
+    L.plane = vcarve(cur, 16 * N);
+    L.labels = vcarve(cur, 4 * N);
+    L.st_n = vcarve(cur, 8 * Keff);
+    L.st_sx = vcarve(cur, 8 * Keff);
+    L.st_sy = vcarve(cur, 8 * Keff);
+    L.st_st = vcarve(cur, 8 * Keff);
+    L.st_col = vcarve(cur, 16 * Keff);
+    L.st_end = vcarve(cur, 16 * Keff);
+    L.cdev = vcarve(cur, sizeof(VoxCluster) * Keff);
+    L.acc = vcarve(cur, sizeof(VoxAcc) * Keff);
+    L.prev_win = vcarve(cur, 24 * Keff);
+    L.proj = vcarve(cur, 4 * Keff);
+    L.lut = vcarve(cur, 256 * 4);
+    L.tile_count = vcarve(cur, 4 * n_tiles);
+    L.tile_off = vcarve(cur, 4 * (n_tiles + 1));
+    L.tile_cursor = vcarve(cur, 4 * n_tiles);
+    L.tile_list = vcarve(cur, 4 * (size_t)L.tile_cap);
+    L.ctr = vcarve(cur, sizeof(DevCounters));
+    L.total = (cur + VALIGN - 1) & ~(VALIGN - 1);
+    return L;
+}
+
+}  // namespace
+}  // namespace scalp
+
+using namespace scalp;
+
+struct scalp_vctx {
+    int T, H, W, K;
+    long long N;
+    int nx, ny, nt, Keff;
+    double r, gamma;
+    float m;
+    cudaStream_t st;
+    unsigned char *ws;
+    VLayout L;
+    VoxArgs a;
+    int iterations;
+};
+
+namespace {
+
+thread_local std::string g_verr;
+
+int vfail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_verr = buf;
+    scalp::set_last_error(buf);
+    return code;
+}
+
+int vcheck(cudaError_t e, const char *what)
+{
+    return e == cudaSuccess ? SCALP_OK : vfail(SCALP_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+void venqueue_lists(scalp_vctx *c)
+{
+    k_vscan<<<1, VSCAN_THREADS, 0, c->st>>>(c->a);
+    const long long slots = (long long)c->Keff * c->a.tpw_x * c->a.tpw_y * c->a.tpw_t;
+    k_vfill<<<(unsigned)((slots + 255) / 256), 256, 0, c->st>>>(c->a);
+}
+
+void venqueue_update(scalp_vctx *c, int from_acc, int whole)
+{
+    k_vupdate<<<(c->Keff + 63) / 64, 64, 0, c->st>>>(c->a, from_acc);
+    if (from_acc) k_vproject<<<std::min(c->Keff, 2 * 152), VPROJ_THREADS, 0, c->st>>>(c->a, whole);
+    venqueue_lists(c);
+}
+
+int vdevice_status(scalp_vctx *c)
+{
+    int rc = vcheck(cudaStreamSynchronize(c->st), "synchronise");
+    if (rc) return rc;
+    DevCounters h;
+    rc = vcheck(cudaMemcpy(&h, c->a.ctr, sizeof h, cudaMemcpyDeviceToHost), "read counters");
+    if (rc) return rc;
+    if (h.error) return vfail(SCALP_E_INTERNAL, "device-side check failed (code %d)", h.error);
+    return SCALP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t scalp_voxel_workspace_bytes(int32_t T, int32_t H, int32_t W, int32_t K, const scalp_params *params)
+{
+    (void)params;
+    if (!vsizes_ok(T, H, W, K)) return 0;
+    return vmake_layout(T, H, W, K).total;
+}
+
+int scalp_voxel_init(scalp_vctx **out, const scalp_volume *vol, int32_t K, float m,
+                     const scalp_params *params)
+{
+    if (!out) return vfail(SCALP_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (!vol || !vol->rgb || !params) return vfail(SCALP_E_ARG, "volume, volume->rgb and params are required");
+    if (!vsizes_ok(vol->T, vol->H, vol->W, K)) return vfail(SCALP_E_ARG, "invalid volume size or K");
+    if (!(m > 0.0f)) return vfail(SCALP_E_ARG, "m must be > 0");
+    if (params->storage != SCALP_STORAGE_F32) return vfail(SCALP_E_ARG, "supervoxels take FP32 planes only");
+    if (params->prior != SCALP_PRIOR_INPUT) return vfail(SCALP_E_ARG, "supervoxels take the input prior only");
+    if (!(params->sigma > 0.0f) || params->lambda < 0.0f || params->lambda > 1.0f)
+        return vfail(SCALP_E_ARG, "need sigma > 0 and lambda in [0, 1]");
+    const size_t need = scalp_voxel_workspace_bytes(vol->T, vol->H, vol->W, K, params);
+    if (!params->workspace || params->workspace_bytes < need)
+        return vfail(SCALP_E_NOMEM, "supervoxel workspace of %zu bytes needed", need);
+    if (reinterpret_cast<uintptr_t>(params->workspace) % VALIGN)
+        return vfail(SCALP_E_ARG, "workspace must be 256-byte aligned");
+    scalp_vctx *c = new (std::nothrow) scalp_vctx();
+    if (!c) return vfail(SCALP_E_NOMEM, "host allocation failed");
+    c->T = vol->T; c->H = vol->H; c->W = vol->W; c->K = K; c->m = m;
+    c->N = (long long)vol->T * vol->H * vol->W;
+    vgrid(c->T, c->H, c->W, K, c->nx, c->ny, c->nt, c->r);
+    c->Keff = c->nx * c->ny * c->nt;
+    c->gamma = params->gamma < 0.0f ? 2.0 * c->r : (double)params->gamma;
+    c->st = reinterpret_cast<cudaStream_t>(params->stream);
+    c->ws = reinterpret_cast<unsigned char *>(params->workspace);
+    c->L = vmake_layout(c->T, c->H, c->W, K);
+    const VLayout &L = c->L;
+    VoxArgs &a = c->a;
+    a = VoxArgs{};
+    a.T = c->T; a.H = c->H; a.W = c->W; a.K = K; a.Keff = c->Keff;
+    a.nx = c->nx; a.ny = c->ny; a.nt = c->nt;
+    a.N = c->N; a.HW = (long long)c->H * c->W;
+    a.r = c->r; a.r2 = c->r * c->r;
+    a.lam = params->lambda;
+    a.gamma = (float)c->gamma;
+    a.ms2 = (float)((double)m * (double)m / (c->r * c->r));
+    a.n_tx = L.n_tx; a.n_ty = L.n_ty; a.n_tt = L.n_tt;
+    a.tpw_x = L.tpw_x; a.tpw_y = L.tpw_y; a.tpw_t = L.tpw_t;
+    a.tile_cap = L.tile_cap;
+    a.plane = reinterpret_cast<const float4 *>(c->ws + L.plane);
+    a.labels = reinterpret_cast<int *>(c->ws + L.labels);
+    a.st_n = reinterpret_cast<long long *>(c->ws + L.st_n);
+    a.st_sx = reinterpret_cast<long long *>(c->ws + L.st_sx);
+    a.st_sy = reinterpret_cast<long long *>(c->ws + L.st_sy);
+    a.st_st = reinterpret_cast<long long *>(c->ws + L.st_st);
+    a.st_col = reinterpret_cast<float4 *>(c->ws + L.st_col);
+    a.st_end = reinterpret_cast<int4 *>(c->ws + L.st_end);
+    a.cdev = reinterpret_cast<VoxCluster *>(c->ws + L.cdev);
+    a.acc = reinterpret_cast<VoxAcc *>(c->ws + L.acc);
+    a.prev_win = reinterpret_cast<int *>(c->ws + L.prev_win);
+    a.proj_list = reinterpret_cast<int *>(c->ws + L.proj);
+    a.tile_count = reinterpret_cast<int *>(c->ws + L.tile_count);
+    a.tile_off = reinterpret_cast<int *>(c->ws + L.tile_off);
+    a.tile_cursor = reinterpret_cast<int *>(c->ws + L.tile_cursor);
+    a.tile_list = reinterpret_cast<int *>(c->ws + L.tile_list);
+    a.ctr = reinterpret_cast<DevCounters *>(c->ws + L.ctr);
+    a.lut = reinterpret_cast<float *>(c->ws + L.lut);
+    const uint8_t *rgb = vol->rgb;
+    const float *con = vol->contour;
+    const size_t N = (size_t)c->N;
+    int rc = SCALP_OK;
+    if (!vol->on_device) {
+        rc = vcheck(cudaMemcpyAsync(c->ws + L.rgb, rgb, 3 * N, cudaMemcpyHostToDevice, c->st), "copy volume");
+        rgb = c->ws + L.rgb;
+        if (!rc && con) {
+            rc = vcheck(cudaMemcpyAsync(c->ws + L.contour, con, 4 * N, cudaMemcpyHostToDevice, c->st),
+                        "copy contour");
+            con = reinterpret_cast<const float *>(c->ws + L.contour);
+        }
+    }
+    const size_t n_tiles = (size_t)L.n_tx * L.n_ty * L.n_tt;
+    if (!rc) rc = vcheck(cudaMemsetAsync(a.acc, 0, sizeof(VoxAcc) * c->Keff, c->st), "memset");
+    if (!rc) rc = vcheck(cudaMemsetAsync(a.tile_count, 0, 4 * n_tiles, c->st), "memset");
+    if (!rc) rc = vcheck(cudaMemsetAsync(a.cdev, 0, sizeof(VoxCluster) * c->Keff, c->st), "memset");
+    if (!rc) rc = vcheck(cudaMemsetAsync(a.ctr, 0, sizeof(DevCounters), c->st), "memset");
+    if (rc) {
+        delete c;
+        return rc;
+    }
+    launch_srgb_table(a.lut, c->st);
+    const int blocks = (int)std::min<long long>((c->N + 255) / 256, 152 * 8);
+    k_vsetup<<<blocks, 256, 0, c->st>>>(a, rgb, con, params->sigma, reinterpret_cast<float4 *>(c->ws + L.plane));
+    k_vaccumulate<<<152 * 8, 256, 0, c->st>>>(a);
+    venqueue_update(c, 1, 1);
+    rc = vcheck(cudaGetLastError(), "initialisation kernels");
+    if (!rc) rc = vcheck(cudaStreamSynchronize(c->st), "initialisation");  // host staging is released
+    if (rc) {
+        delete c;
+        return rc;
+    }
+    c->iterations = 0;
+    *out = c;
+    return SCALP_OK;
+}
+
+int scalp_voxel_iterate(scalp_vctx *c, int32_t n)
+{
+    if (!c || n < 0) return vfail(SCALP_E_ARG, "ctx is NULL or n < 0");
+    for (int i = 0; i < n; ++i) {
+        const unsigned tiles = (unsigned)(c->a.n_tx * c->a.n_ty * c->a.n_tt);
+        k_vassign<<<tiles, VTILE, 0, c->st>>>(c->a);
+        venqueue_update(c, 1, 0);
+        ++c->iterations;
+    }
+    return vcheck(cudaGetLastError(), "iteration kernels");
+}
+
+int scalp_voxel_labels(scalp_vctx *c, int32_t *out, int32_t out_on_device)
+{
+    if (!c || !out) return vfail(SCALP_E_ARG, "ctx or out is NULL");
+    int rc = vcheck(cudaMemcpyAsync(out, c->a.labels, 4 * (size_t)c->N,
+                                    out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st),
+                    "copy labels");
+    return rc ? rc : vdevice_status(c);
+}
+
+int scalp_voxel_get_info(const scalp_vctx *c, scalp_voxel_info *info)
+{
+    if (!c || !info) return vfail(SCALP_E_ARG, "ctx or info is NULL");
+    info->T = c->T; info->H = c->H; info->W = c->W; info->K = c->K;
+    info->nx = c->nx; info->ny = c->ny; info->nt = c->nt; info->Keff = c->Keff;
+    info->r = c->r; info->gamma = c->gamma;
+    info->iterations = c->iterations;
+    return SCALP_OK;
+}
+
+int scalp_voxel_get_state(scalp_vctx *c, const scalp_voxel_state *s)
+{
+    if (!c || !s || !s->labels || !s->n || !s->sx || !s->sy || !s->st || !s->color || !s->endpoint)
+        return vfail(SCALP_E_ARG, "ctx and every state array are required");
+    const size_t K = (size_t)c->Keff;
+    std::vector<float4> col(K);
+    std::vector<int4> end(K);
+    int rc = vcheck(cudaStreamSynchronize(c->st), "synchronise");
+    if (!rc) rc = vcheck(cudaMemcpy(s->labels, c->a.labels, 4 * (size_t)c->N, cudaMemcpyDeviceToHost), "copy");
+    if (!rc) rc = vcheck(cudaMemcpy(s->n, c->a.st_n, 8 * K, cudaMemcpyDeviceToHost), "copy");
+    if (!rc) rc = vcheck(cudaMemcpy(s->sx, c->a.st_sx, 8 * K, cudaMemcpyDeviceToHost), "copy");
+    if (!rc) rc = vcheck(cudaMemcpy(s->sy, c->a.st_sy, 8 * K, cudaMemcpyDeviceToHost), "copy");
+    if (!rc) rc = vcheck(cudaMemcpy(s->st, c->a.st_st, 8 * K, cudaMemcpyDeviceToHost), "copy");
+    if (!rc) rc = vcheck(cudaMemcpy(col.data(), c->a.st_col, 16 * K, cudaMemcpyDeviceToHost), "copy");
+    if (!rc) rc = vcheck(cudaMemcpy(end.data(), c->a.st_end, 16 * K, cudaMemcpyDeviceToHost), "copy");
+    if (rc) return rc;
+    for (size_t k = 0; k < K; ++k) {
+        s->color[3 * k] = col[k].x;
+        s->color[3 * k + 1] = col[k].y;
+        s->color[3 * k + 2] = col[k].z;
+        s->endpoint[3 * k] = end[k].x;
+        s->endpoint[3 * k + 1] = end[k].y;
+        s->endpoint[3 * k + 2] = end[k].z;
+    }
+    return vdevice_status(c);
+}
+
+int scalp_voxel_set_state(scalp_vctx *c, const scalp_voxel_state *s)
+{
+    if (!c || !s || !s->labels || !s->n || !s->sx || !s->sy || !s->st || !s->color || !s->endpoint)
+        return vfail(SCALP_E_ARG, "ctx and every state array are required");
+    const size_t K = (size_t)c->Keff;
+    for (size_t k = 0; k < K; ++k) {
+        if (s->n[k] < 1) return vfail(SCALP_E_ARG, "cluster %zu has n < 1", k);
+        const int32_t *e = s->endpoint + 3 * k;
+        if (e[0] < 0 || e[0] >= c->W || e[1] < 0 || e[1] >= c->H || e[2] < 0 || e[2] >= c->T)
+            return vfail(SCALP_E_ARG, "endpoint of cluster %zu is outside the volume", k);
+    }
+    for (long long p = 0; p < c->N; ++p)
+        if (s->labels[p] < 0 || s->labels[p] >= c->Keff) return vfail(SCALP_E_ARG, "label out of range");
+    std::vector<float4> col(K);
+    std::vector<int4> end(K);
+    for (size_t k = 0; k < K; ++k) {
+        col[k] = make_float4((float)s->color[3 * k], (float)s->color[3 * k + 1], (float)s->color[3 * k + 2], 0.f);
+        end[k] = make_int4(s->endpoint[3 * k], s->endpoint[3 * k + 1], s->endpoint[3 * k + 2], 0);
+    }
+    const size_t n_tiles = (size_t)c->L.n_tx * c->L.n_ty * c->L.n_tt;
+    int rc = vcheck(cudaStreamSynchronize(c->st), "synchronise");
+    if (!rc) rc = vcheck(cudaMemcpy(c->a.labels, s->labels, 4 * (size_t)c->N, cudaMemcpyHostToDevice), "copy");
+    if (!rc) rc = vcheck(cudaMemcpy(c->a.st_n, s->n, 8 * K, cudaMemcpyHostToDevice), "copy");
+    if (!rc) rc = vcheck(cudaMemcpy(c->a.st_sx, s->sx, 8 * K, cudaMemcpyHostToDevice), "copy");
+    if (!rc) rc = vcheck(cudaMemcpy(c->a.st_sy, s->sy, 8 * K, cudaMemcpyHostToDevice), "copy");
+    if (!rc) rc = vcheck(cudaMemcpy(c->a.st_st, s->st, 8 * K, cudaMemcpyHostToDevice), "copy");
+    if (!rc) rc = vcheck(cudaMemcpy(c->a.st_col, col.data(), 16 * K, cudaMemcpyHostToDevice), "copy");
+    if (!rc) rc = vcheck(cudaMemcpy(c->a.st_end, end.data(), 16 * K, cudaMemcpyHostToDevice), "copy");
+    if (!rc) rc = vcheck(cudaMemset(c->a.acc, 0, sizeof(VoxAcc) * K), "memset");
+    if (!rc) rc = vcheck(cudaMemset(c->a.tile_count, 0, 4 * n_tiles), "memset");
+    if (rc) return rc;
+    venqueue_update(c, 0, 0);
+    rc = vcheck(cudaGetLastError(), "derive kernels");
+    return rc ? rc : vdevice_status(c);
+}
+
+int scalp_voxel_count_samples(scalp_vctx *c, int32_t enable, int64_t *samples, int64_t *pairs)
+{
+    if (!c) return vfail(SCALP_E_ARG, "ctx is NULL");
+    int rc = vcheck(cudaStreamSynchronize(c->st), "synchronise");
+    DevCounters h;
+    if (!rc) rc = vcheck(cudaMemcpy(&h, c->a.ctr, sizeof h, cudaMemcpyDeviceToHost), "read counters");
+    if (rc) return rc;
+    if (samples) *samples = (int64_t)h.samples;
+    if (pairs) *pairs = (int64_t)h.pairs;
+    if (enable >= 0) {
+        if (enable) {
+            unsigned long long z[2] = {0, 0};
+            rc = vcheck(cudaMemcpy(&c->a.ctr->samples, z, sizeof z, cudaMemcpyHostToDevice), "reset counters");
+            if (rc) return rc;
+        }
+        c->a.count_samples = enable != 0;
+    }
+    return SCALP_OK;
+}
+
+void scalp_voxel_destroy(scalp_vctx *c)
+{
+    if (!c) return;
+    cudaStreamSynchronize(c->st);
+    delete c;
+}
+
+}  // extern "C"

@@ -61,6 +61,24 @@ class scalp_quality(ctypes.Structure):
                 ("co", ctypes.c_double)]
 
 
+class scalp_volume(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int32), ("H", ctypes.c_int32), ("W", ctypes.c_int32),
+                ("rgb", ctypes.c_void_p), ("contour", ctypes.c_void_p), ("on_device", ctypes.c_int32)]
+
+
+class scalp_voxel_info(ctypes.Structure):
+    _fields_ = [("T", ctypes.c_int32), ("H", ctypes.c_int32), ("W", ctypes.c_int32), ("K", ctypes.c_int32),
+                ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nt", ctypes.c_int32),
+                ("Keff", ctypes.c_int32), ("r", ctypes.c_double), ("gamma", ctypes.c_double),
+                ("iterations", ctypes.c_int32)]
+
+
+class scalp_voxel_state(ctypes.Structure):
+    _fields_ = [("labels", ctypes.c_void_p), ("n", ctypes.c_void_p), ("sx", ctypes.c_void_p),
+                ("sy", ctypes.c_void_p), ("st", ctypes.c_void_p), ("color", ctypes.c_void_p),
+                ("endpoint", ctypes.c_void_p)]
+
+
 class scalp_state(ctypes.Structure):
     _fields_ = [("labels", ctypes.c_void_p), ("n", ctypes.c_void_p), ("sx", ctypes.c_void_p),
                 ("sy", ctypes.c_void_p), ("color", ctypes.c_void_p), ("endpoint", ctypes.c_void_p)]
@@ -78,6 +96,9 @@ EXPORTS = (
     "scalp_server_poll", "scalp_server_stats", "scalp_server_destroy", "scalp_boundary_map",
     "scalp_quality_workspace_bytes", "scalp_quality_metrics",
     "scalp_gradient_prior_workspace_bytes", "scalp_gradient_prior",
+    "scalp_voxel_workspace_bytes", "scalp_voxel_init", "scalp_voxel_iterate", "scalp_voxel_labels",
+    "scalp_voxel_get_info", "scalp_voxel_get_state", "scalp_voxel_set_state",
+    "scalp_voxel_count_samples", "scalp_voxel_destroy",
 )
 
 _lib = None
@@ -141,6 +162,16 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "scalp_boundary_map": (ctypes.c_int, [P, I32, I32, I32, P, P]),
             "scalp_quality_workspace_bytes": (ctypes.c_size_t, [I32, I32, I32, I32]),
             "scalp_gradient_prior_workspace_bytes": (ctypes.c_size_t, [I32, I32, I32, I32]),
+            "scalp_voxel_workspace_bytes": (ctypes.c_size_t, [I32, I32, I32, I32, ctypes.POINTER(scalp_params)]),
+            "scalp_voxel_init": (ctypes.c_int, [ctypes.POINTER(P), ctypes.POINTER(scalp_volume), I32,
+                                                ctypes.c_float, ctypes.POINTER(scalp_params)]),
+            "scalp_voxel_iterate": (ctypes.c_int, [P, I32]),
+            "scalp_voxel_labels": (ctypes.c_int, [P, P, I32]),
+            "scalp_voxel_get_info": (ctypes.c_int, [P, ctypes.POINTER(scalp_voxel_info)]),
+            "scalp_voxel_get_state": (ctypes.c_int, [P, ctypes.POINTER(scalp_voxel_state)]),
+            "scalp_voxel_set_state": (ctypes.c_int, [P, ctypes.POINTER(scalp_voxel_state)]),
+            "scalp_voxel_count_samples": (ctypes.c_int, [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+            "scalp_voxel_destroy": (None, [P]),
             "scalp_gradient_prior": (ctypes.c_int, [ctypes.POINTER(scalp_image), P, I64, I32, P, P,
                                                     ctypes.c_size_t]),
             "scalp_quality_metrics": (ctypes.c_int, [P, I32, P, I32, I32, I32, ctypes.c_double, P,
@@ -722,3 +753,92 @@ def quality_metrics(labels, gt, eps: float = 2.0, stream=None):
                                         ctypes.c_void_p(ws.data_ptr()), nbytes, ctypes.byref(q),
                                         ctypes.c_void_p(stream.cuda_stream)))
     return {"br": q.br, "asa": q.asa, "ue": q.ue, "co": q.co}
+
+
+class VoxelSegmenter:
+    """Supervoxels (SCALP on a (T, H, W) video volume) on the current CUDA device.
+
+    rgb: (T, H, W, 3) uint8 CUDA tensor; contour: (T, H, W) float32 CUDA tensor
+    in [0, 1], or None.  The workspace is a torch CUDA tensor owned here.
+    """
+
+    def __init__(self, rgb, contour, K: int, m: float = 10.0, lam: float = 0.5,
+                 sigma: float = 0.25, gamma: float = -1.0, stream=None):
+        import torch
+
+        self._torch = torch
+        T, H, W = (int(v) for v in rgb.shape[:3])
+        self.T, self.H, self.W, self.K = T, H, W, int(K)
+        p = scalp_default_params()
+        p.lambda_, p.sigma, p.gamma = lam, sigma, gamma
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        p.stream = self.stream.cuda_stream
+        L = load()
+        nbytes = L.scalp_voxel_workspace_bytes(T, H, W, int(K), ctypes.byref(p))
+        if nbytes == 0:
+            raise ScalpError(SCALP_E_ARG, "invalid sizes")
+        self.workspace = torch.empty(nbytes, dtype=torch.uint8, device="cuda")
+        p.workspace, p.workspace_bytes = self.workspace.data_ptr(), nbytes
+        rgb = rgb.contiguous()
+        con = contour.to(device=rgb.device, dtype=torch.float32).contiguous() if contour is not None else None
+        vol = scalp_volume(T, H, W, rgb.data_ptr(), con.data_ptr() if con is not None else None, 1)
+        ctx = ctypes.c_void_p()
+        _check(L.scalp_voxel_init(ctypes.byref(ctx), ctypes.byref(vol), int(K), float(m), ctypes.byref(p)))
+        self.ctx = ctx
+        info = scalp_voxel_info()
+        _check(L.scalp_voxel_get_info(self.ctx, ctypes.byref(info)))
+        self.info = info
+
+    @property
+    def Keff(self) -> int:
+        return self.info.Keff
+
+    def iterate(self, n: int = 1):
+        _check(load().scalp_voxel_iterate(self.ctx, int(n)))
+
+    def labels(self, out=None):
+        """(T, H, W) int32 labels: into `out` (a CUDA tensor) if given, else a numpy array."""
+        if out is not None:
+            _check(load().scalp_voxel_labels(self.ctx, out.data_ptr(), 1))
+            return out
+        a = np.empty((self.T, self.H, self.W), np.int32)
+        _check(load().scalp_voxel_labels(self.ctx, a.ctypes.data, 0))
+        return a
+
+    def _state_arrays(self):
+        K = self.Keff
+        return dict(labels=np.empty((self.T, self.H, self.W), np.int32), n=np.empty(K, np.int64),
+                    sx=np.empty(K, np.int64), sy=np.empty(K, np.int64), st=np.empty(K, np.int64),
+                    color=np.empty((K, 3), np.float64), endpoint=np.empty((K, 3), np.int32))
+
+    @staticmethod
+    def _struct(d):
+        return scalp_voxel_state(*(np.ascontiguousarray(d[k]).ctypes.data for k in
+                                   ("labels", "n", "sx", "sy", "st", "color", "endpoint")))
+
+    def get_state(self):
+        d = self._state_arrays()
+        s = self._struct(d)
+        _check(load().scalp_voxel_get_state(self.ctx, ctypes.byref(s)))
+        return d
+
+    def set_state(self, d):
+        d = {k: np.ascontiguousarray(v, dtype=self._state_arrays()[k].dtype) for k, v in d.items()}
+        s = self._struct(d)
+        _check(load().scalp_voxel_set_state(self.ctx, ctypes.byref(s)))
+
+    def count_samples(self, enable: int):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().scalp_voxel_count_samples(self.ctx, int(enable), ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            load().scalp_voxel_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

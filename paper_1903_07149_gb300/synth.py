@@ -23,7 +23,9 @@ __all__ = [
     "batch_configs",
     "batch_images",
     "serving_arrivals",
+    "voronoi_video",
     "WORKLOADS",
+    "VIDEO_WORKLOADS",
 ]
 
 
@@ -179,3 +181,54 @@ def serving_arrivals(n_requests: int = 2000, rate_hz: float = 500.0, seed: int =
     gaps = rng.exponential(1.0 / rate_hz, size=n_requests)
     kind = (rng.uniform(size=n_requests) < 0.10).astype(np.int32)
     return np.cumsum(gaps), kind
+
+
+# Video volumes for the supervoxel form: (T, H, W, K, n_cells, seed).
+VIDEO_WORKLOADS = {
+    "video_32x240x320_k2000": (32, 240, 320, 2000, 40, 5000),
+}
+
+
+def voronoi_video(T: int, H: int, W: int, n_cells: int, *, seed: int, noise_sigma: float = 6.0,
+                  contour_noise: float = 0.05):
+    """Return (rgb uint8 TxHxWx3, contour float32 TxHxW in [0,1], cells int32 TxHxW).
+
+    Moving Voronoi cells: seeds uniform in [0,W)x[0,H) drift with a velocity
+    uniform in [-1.5, 1.5] pixels per frame (reflected at the borders); every
+    voxel takes its frame's nearest seed.  Colours as the gradient images of
+    voronoi_image (base U[40,215]^3 plus a per-cell linear ramp), then Gaussian
+    noise.  The contour of each frame is its cell boundary, blurred, normalised
+    and noised as in voronoi_image."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    pos = np.stack([rng.uniform(0, W, n_cells), rng.uniform(0, H, n_cells)], axis=1)
+    vel = rng.uniform(-1.5, 1.5, size=(n_cells, 2))
+    base = rng.uniform(40, 215, size=(n_cells, 3))
+    G = rng.uniform(-40, 40, size=(n_cells, 3, 2))
+    R = np.sqrt(H * W / n_cells)
+    ys, xs = np.mgrid[0:H, 0:W].astype(np.float64)
+    rgb = np.empty((T, H, W, 3), np.uint8)
+    contour = np.empty((T, H, W), np.float32)
+    cells = np.empty((T, H, W), np.int32)
+    for t in range(T):
+        p = pos + vel * t
+        for j, lim in ((0, W), (1, H)):  # reflect into [0, lim)
+            period = 2.0 * lim
+            q = np.mod(p[:, j], period)
+            p[:, j] = np.where(q < lim, q, period - q - 1e-9)
+        c = _voronoi_cells(H, W, p)
+        col = base[c] + G[c, :, 0] * ((xs - p[c, 0]) / R)[..., None] + G[c, :, 1] * ((ys - p[c, 1]) / R)[..., None]
+        col = col + rng.normal(0.0, noise_sigma, size=col.shape)
+        rgb[t] = np.clip(np.rint(col), 0, 255).astype(np.uint8)
+        edge = np.zeros((H, W))
+        dx = c[:, 1:] != c[:, :-1]
+        dy = c[1:, :] != c[:-1, :]
+        edge[:, 1:][dx] = 1.0
+        edge[:, :-1][dx] = 1.0
+        edge[1:, :][dy] = 1.0
+        edge[:-1, :][dy] = 1.0
+        b = _blur_reflect(edge, 1.0, 3)
+        if b.max() > 0:
+            b = b / b.max()
+        contour[t] = np.clip(b + rng.uniform(0.0, contour_noise, size=(H, W)), 0.0, 1.0)
+        cells[t] = c
+    return rgb, contour, cells

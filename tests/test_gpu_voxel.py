@@ -1,0 +1,140 @@
+"""Supervoxels (SCALP on video volumes) on the GPU against the FP64 oracle.
+
+Tolerances follow the 2-D FP32 path: one assignment from the same oracle
+state agrees on >= 99.9% of voxels, and every disagreement is a near-tie
+(relative gap < 1e-5 by the oracle's own FP64 distances): the path sums hold
+at most 2r + 2 FP32 terms as in 2-D.  Windows, paths, counts, coordinate
+sums and endpoints are exact."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1903_07149_gb300 import build as scalp_build
+from paper_1903_07149_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+AGREE = 0.999
+NEAR_TIE = 1e-5
+COLOR_RTOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+
+    assert torch.cuda.is_available()
+    scalp_build.build()
+    from paper_1903_07149_gb300 import scalp
+
+    scalp.load()
+    return scalp
+
+
+def _volume(T, H, W, seed, n_cells=6):
+    rgb, con, cells = synth.voronoi_video(T, H, W, n_cells, seed=seed)
+    return rgb, con, cells
+
+
+def _to_gpu_state(st):
+    return dict(labels=st["labels"], n=st["n"], sx=st["sx"], sy=st["sy"], st=st["st"],
+                color=np.stack([st["cL"], st["cA"], st["cB"]], axis=1),
+                endpoint=np.stack([st["ex"], st["ey"], st["et"]], axis=1))
+
+
+def _seg(S, rgb, con, K, **kw):
+    import torch
+
+    return S.VoxelSegmenter(torch.from_numpy(rgb).cuda(),
+                            torch.from_numpy(con).cuda() if con is not None else None, K, **kw)
+
+
+@pytest.mark.parametrize("T,H,W,K,t", [(6, 37, 53, 40, 0), (6, 37, 53, 40, 2), (9, 20, 35, 12, 1),
+                                       (1, 30, 41, 8, 1)])
+def test_voxel_one_step_parity(S, T, H, W, K, t):
+    rgb, con, _ = _volume(T, H, W, seed=T * 100 + H)
+    orc = oracle.VSolver(oracle.lab_from_rgb(rgb), con, K)
+    orc.iterate(t)
+    st = orc.state()
+    seg = _seg(S, rgb, con, K)
+    assert seg.info.Keff == orc.Keff and seg.info.r == orc.r
+    seg.set_state(_to_gpu_state(st))
+    seg.iterate(1)
+    g = seg.get_state()
+    orc.assign()
+    diff = np.argwhere(g["labels"] != orc.labels)
+    for tt, y, x in diff:
+        kg, ko = int(g["labels"][tt, y, x]), int(orc.labels[tt, y, x])
+        Dg, _ = orc.distance(x, y, tt, kg)
+        Do, _ = orc.distance(x, y, tt, ko)
+        assert (Dg - Do) / max(Do, 1e-12) < NEAR_TIE, (x, y, tt, kg, ko, Dg, Do)
+    assert len(diff) <= (1 - AGREE) * orc.N + 1e-9, len(diff)
+    # update: exact sums and endpoints for clusters with the same voxel set
+    lab_o = orc.labels.copy()
+    orc.update()
+    bad = np.unique(np.concatenate([g["labels"][g["labels"] != lab_o], lab_o[g["labels"] != lab_o]]))
+    same = np.setdiff1d(np.arange(orc.Keff), bad)
+    for k in ("n", "sx", "sy", "st"):
+        assert np.array_equal(g[k][same], getattr(orc, k)[same]), k
+    assert np.array_equal(g["endpoint"][same], np.stack([orc.ex, orc.ey, orc.et], axis=1)[same])
+    ref = np.stack([orc.cL, orc.cA, orc.cB], axis=1)[same]
+    assert np.all(np.abs(g["color"][same] - ref) <= COLOR_RTOL * np.maximum(np.abs(ref), 1))
+    seg.close()
+
+
+def test_voxel_initial_state_exact(S):
+    rgb, con, _ = _volume(7, 26, 45, seed=3)
+    orc = oracle.VSolver(oracle.lab_from_rgb(rgb), con, 30)
+    seg = _seg(S, rgb, con, 30)
+    g = seg.get_state()
+    assert np.array_equal(g["labels"], orc.labels)
+    for k in ("n", "sx", "sy", "st"):
+        assert np.array_equal(g[k], getattr(orc, k)), k
+    assert np.array_equal(g["endpoint"], np.stack([orc.ex, orc.ey, orc.et], axis=1))
+    seg.close()
+
+
+def test_voxel_constant_volume_fixed_point(S):
+    rgb = np.full((16, 16, 16, 3), 120, np.uint8)
+    seg = _seg(S, rgb, None, 64)
+    assert seg.info.r == 4.0 and (seg.info.nx, seg.info.ny, seg.info.nt) == (4, 4, 4)
+    cells = seg.labels()
+    seg.iterate(3)
+    assert np.array_equal(seg.labels(), cells)
+    seg.close()
+
+
+def test_voxel_end_to_end_agreement(S):
+    T, H, W, K = 8, 48, 64, 60
+    rgb, con, _ = _volume(T, H, W, seed=21)
+    orc = oracle.VSolver(oracle.lab_from_rgb(rgb), con, K)
+    orc.iterate(5)
+    seg = _seg(S, rgb, con, K)
+    seg.iterate(5)
+    agree = (seg.labels() == orc.labels).mean()
+    print(f"supervoxels, 5 iterations, voxel agreement with the FP64 oracle: {agree:.5f}")
+    assert agree >= 0.99, agree
+    seg.close()
+
+
+def test_voxel_state_round_trip_and_errors(S):
+    import torch
+
+    rgb, con, _ = _volume(5, 20, 33, seed=4)
+    seg = _seg(S, rgb, con, 10)
+    seg.iterate(2)
+    st = seg.get_state()
+    seg.iterate(2)
+    a = seg.labels()
+    seg.set_state(st)
+    seg.iterate(2)
+    assert np.array_equal(seg.labels(), a)
+    bad = dict(st)
+    bad["endpoint"] = st["endpoint"].copy()
+    bad["endpoint"][0, 2] = 99
+    with pytest.raises(S.ScalpError):
+        seg.set_state(bad)
+    seg.close()
+    t = torch.from_numpy(rgb).cuda()
+    with pytest.raises(S.ScalpError):
+        S.VoxelSegmenter(t, None, 0)
