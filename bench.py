@@ -158,17 +158,10 @@ def whole_job_value(units_per_rank: float, world: int, slowest_ms: float) -> flo
     return world * units_per_rank / (slowest_ms / 1e3) / 1e6
 
 
-def ccl_launches(N: int) -> int:
-    """Connectivity kernels: tile-local, border, flatten, link, resolve, flag,
-    output, plus the multi-level scan (one block pass per level, one add pass
-    per level below the top)."""
-    levels, n = 0, N
-    while True:
-        n = -(-n // 4096)
-        levels += 1
-        if n <= 1:
-            break
-    return 7 + levels + (levels - 1)
+def ccl_launches(H: int, W: int) -> int:
+    """Connectivity kernels: tile-local, border (when there is more than one
+    tile), flatten/count, link, resolve/count, chunk scan, numbering, output."""
+    return 7 + (1 if H > 32 or W > 32 else 0)
 
 
 def kernel_hash() -> str:
@@ -738,7 +731,7 @@ def run_ours(args):
                    "n_labels": int(n_labels)},
         "clocks": clk, "e2e": e2e,
         "gpu_launches": args.steps * (reload_launches(w.H, w.W) + iter_launches(w.H, w.W) * iters
-                                      + ccl_launches(N)),
+                                      + ccl_launches(w.H, w.W)),
         "roofline": roofline,
     }
     if not args.no_forms:

@@ -12,7 +12,8 @@
 //      has a smaller seed, so the absorption links form a forest.  A small
 //      component takes the identity of its first non-small ancestor (or the
 //      component of pixel 0).
-//   4. The surviving components are numbered 0.. in raster order of seeds.
+//   4. The surviving components are numbered 0.. in raster order of seeds
+//      (per 4096-pixel chunk: a count, a scan of the counts, the ranks).
 #include <algorithm>
 
 #include "scalp_launch.h"
@@ -148,13 +149,26 @@ __global__ void k_ccl_border(const int *__restrict__ labels, int *parent, int H,
     }
 }
 
+// Roots and component sizes; the lanes of a warp (32 consecutive pixels, most
+// of them in one component) add their counts once per distinct root.
 __global__ void k_ccl_flatten_count(int *parent, int *size, long long N)
 {
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
-         p += (long long)gridDim.x * blockDim.x) {
-        int r = find_root(parent, (int)p);
-        parent[p] = r;
-        atomicAdd(&size[r], 1);
+    const int lane = threadIdx.x & 31;
+    const long long warps = (long long)gridDim.x * (blockDim.x / 32);
+    for (long long w = blockIdx.x * (long long)(blockDim.x / 32) + (threadIdx.x >> 5); w * 32 < N;
+         w += warps) {
+        const long long p = w * 32 + lane;
+        const bool valid = p < N;
+        int r = -1;
+        if (valid) {
+            r = find_root(parent, (int)p);
+            parent[p] = r;
+        }
+        const unsigned act = __ballot_sync(0xffffffffu, valid);
+        if (valid) {
+            const unsigned grp = __match_any_sync(act, r);
+            if (lane == __ffs(grp) - 1) atomicAdd(&size[r], __popc(grp));
+        }
     }
 }
 
@@ -170,17 +184,39 @@ __global__ void k_ccl_link(const int *__restrict__ parent, const int *__restrict
     }
 }
 
-// final[s] = first non-small ancestor of seed s; written over size[].
-__global__ void k_ccl_resolve(const int *__restrict__ parent, const int *__restrict__ link,
-                              int *final_id, long long N, DevCounters *ctr)
+// Numbering works on chunks of CCL_CHUNK pixels, one CTA each.
+constexpr int CCL_CHUNK = 4096;
+constexpr int CCL_CHUNK_THREADS = 256;
+constexpr int CCL_PER = CCL_CHUNK / CCL_CHUNK_THREADS;  // consecutive pixels per thread
+
+// Sum of v over the CTA (all threads receive it); s_warp holds 32 ints.
+__device__ __forceinline__ int cta_sum(int v, int *s_warp)
 {
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
-         s += (long long)gridDim.x * blockDim.x) {
-        if (parent[s] != s) continue;
+    v = __reduce_add_sync(0xffffffffu, (unsigned)v);
+    if ((threadIdx.x & 31) == 0) s_warp[threadIdx.x >> 5] = v;
+    __syncthreads();
+    int t = (int)(threadIdx.x & 31) < (int)(blockDim.x >> 5) ? s_warp[threadIdx.x & 31] : 0;
+    t = __reduce_add_sync(0xffffffffu, (unsigned)t);
+    __syncthreads();
+    return t;
+}
+
+// final[s] = first non-small ancestor of seed s (written over size[]), and
+// per chunk the number of surviving components (seeds with final[s] == s).
+__global__ void __launch_bounds__(CCL_CHUNK_THREADS)
+    k_ccl_resolve_count(const int *__restrict__ parent, const int *__restrict__ link, int *final_id,
+                        long long N, DevCounters *ctr, int *chunk_count)
+{
+    __shared__ int s_warp[32];
+    const long long base = blockIdx.x * (long long)CCL_CHUNK;
+    int cnt = 0;
+    for (int i = threadIdx.x; i < CCL_CHUNK; i += CCL_CHUNK_THREADS) {
+        const long long s = base + i;
+        if (s >= N || parent[s] != s) continue;
         int f = (int)s;
         long long guard = 0;
         while (true) {
-            int nf = link[f];
+            const int nf = link[f];
             if (nf == f) break;
             f = nf;
             if (++guard > N) {
@@ -189,15 +225,87 @@ __global__ void k_ccl_resolve(const int *__restrict__ parent, const int *__restr
             }
         }
         final_id[s] = f;
+        cnt += f == s;
     }
+    cnt = cta_sum(cnt, s_warp);
+    if (threadIdx.x == 0) chunk_count[blockIdx.x] = cnt;
 }
 
-__global__ void k_ccl_flag(const int *__restrict__ parent, const int *__restrict__ final_id,
-                           int *flag, long long N)
+// Exclusive scan of the chunk counts by one CTA (each thread a contiguous
+// run); *total receives the number of labels.
+constexpr int CCL_SCAN_THREADS = 1024;
+
+__global__ void __launch_bounds__(CCL_SCAN_THREADS) k_ccl_chunk_scan(int *counts, long long n, int *total)
 {
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
-         p += (long long)gridDim.x * blockDim.x)
-        flag[p] = (parent[p] == p && final_id[p] == p) ? 1 : 0;
+    __shared__ int s_warp[32];
+    const long long per = (n + CCL_SCAN_THREADS - 1) / CCL_SCAN_THREADS;
+    const long long b = threadIdx.x * per, e = min(n, b + per);
+    int tsum = 0;
+    for (long long i = b; i < e; ++i) tsum += counts[i];
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = tsum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int w = s_warp[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    int run = (wid ? s_warp[wid - 1] : 0) + incl - tsum;
+    for (long long i = b; i < e; ++i) {
+        const int v = counts[i];
+        counts[i] = run;
+        run += v;
+    }
+    if (threadIdx.x == CCL_SCAN_THREADS - 1) *total = s_warp[31];
+}
+
+// number[s] for each surviving seed s: its rank in raster order (the chunk's
+// offset plus the rank inside the chunk); only seeds are written.
+__global__ void __launch_bounds__(CCL_CHUNK_THREADS)
+    k_ccl_number(const int *__restrict__ parent, const int *__restrict__ final_id,
+                 const int *__restrict__ chunk_off, int *number, long long N)
+{
+    __shared__ int s_warp[32];
+    const long long base = blockIdx.x * (long long)CCL_CHUNK + (long long)threadIdx.x * CCL_PER;
+    unsigned flags = 0;
+#pragma unroll
+    for (int i = 0; i < CCL_PER; ++i) {
+        const long long s = base + i;
+        if (s < N && parent[s] == s && final_id[s] == s) flags |= 1u << i;
+    }
+    const int mine = __popc(flags);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    int incl = mine;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) s_warp[wid] = incl;
+    __syncthreads();
+    if (wid == 0) {
+        int w = lane < CCL_CHUNK_THREADS / 32 ? s_warp[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    int rank = chunk_off[blockIdx.x] + (wid ? s_warp[wid - 1] : 0) + incl - mine;
+    while (flags) {
+        const int i = __ffs(flags) - 1;
+        number[base + i] = rank++;
+        flags &= flags - 1;
+    }
 }
 
 __global__ void k_ccl_out(const int *__restrict__ parent, const int *__restrict__ final_id,
@@ -208,80 +316,7 @@ __global__ void k_ccl_out(const int *__restrict__ parent, const int *__restrict_
         out[p] = number[final_id[parent[p]]];
 }
 
-// ---------------------------------------------------------------------------
-// Exclusive scan of int32 in place: blocks of 4096, then the block sums.
-// ---------------------------------------------------------------------------
-constexpr int SCAN_THREADS = 1024;
-constexpr int SCAN_ITEMS = 4;
-constexpr int SCAN_CHUNK = SCAN_THREADS * SCAN_ITEMS;
-
-__global__ void __launch_bounds__(SCAN_THREADS) k_scan_block(int *data, long long n, int *sums)
-{
-    __shared__ int s_warp[32];
-    const long long base = blockIdx.x * (long long)SCAN_CHUNK + threadIdx.x * SCAN_ITEMS;
-    int v[SCAN_ITEMS];
-    int tsum = 0;
-#pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; ++i) {
-        v[i] = base + i < n ? data[base + i] : 0;
-        tsum += v[i];
-    }
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int incl = tsum;
-    for (int o = 1; o < 32; o <<= 1) {
-        int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) s_warp[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-        int w = s_warp[lane];
-        for (int o = 1; o < 32; o <<= 1) {
-            int t = __shfl_up_sync(0xffffffffu, w, o);
-            if (lane >= o) w += t;
-        }
-        s_warp[lane] = w;
-    }
-    __syncthreads();
-    int run = (wid ? s_warp[wid - 1] : 0) + incl - tsum;
-#pragma unroll
-    for (int i = 0; i < SCAN_ITEMS; ++i) {
-        if (base + i < n) data[base + i] = run;
-        run += v[i];
-    }
-    if (threadIdx.x == SCAN_THREADS - 1) sums[blockIdx.x] = run;
-}
-
-__global__ void k_scan_add(int *data, long long n, const int *__restrict__ sums)
-{
-    const long long base = blockIdx.x * (long long)SCAN_CHUNK;
-    const int add = sums[blockIdx.x];
-    for (int i = threadIdx.x; i < SCAN_CHUNK; i += blockDim.x)
-        if (base + i < n) data[base + i] += add;
-}
-
-long long ccl_scan_tmp_len(long long N)
-{
-    long long len = 0, n = N;
-    do {
-        n = ceil_div_ll(n, SCAN_CHUNK);
-        len += n + 64;
-    } while (n > 1);
-    return len + 64;
-}
-
-// After the call, *total holds the sum of the n inputs.
-static void scan_exclusive(int *data, long long n, int *tmp, int *total, cudaStream_t st)
-{
-    long long nb = ceil_div_ll(n, SCAN_CHUNK);
-    k_scan_block<<<(unsigned)nb, SCAN_THREADS, 0, st>>>(data, n, tmp);
-    if (nb == 1) {
-        cudaMemcpyAsync(total, tmp, sizeof(int), cudaMemcpyDeviceToDevice, st);
-        return;
-    }
-    scan_exclusive(tmp, nb, tmp + nb + 64, total, st);
-    k_scan_add<<<(unsigned)nb, 256, 0, st>>>(data, n, tmp);
-}
+long long ccl_scan_tmp_len(long long N) { return ceil_div_ll(N, CCL_CHUNK) + 64; }
 
 void launch_ccl(const int *labels, int H, int W, int K, int *out, const CclBuffers &b, int *d_nlab,
                 DevCounters *ctr, cudaStream_t st)
@@ -297,9 +332,11 @@ void launch_ccl(const int *labels, int H, int W, int K, int *out, const CclBuffe
                        st>>>(labels, b.parent, H, W, n_tx, n_ty);
     k_ccl_flatten_count<<<blocks, CCL_THREADS, 0, st>>>(b.parent, b.size, N);
     k_ccl_link<<<blocks, CCL_THREADS, 0, st>>>(b.parent, b.size, b.link, W, N, T);
-    k_ccl_resolve<<<blocks, CCL_THREADS, 0, st>>>(b.parent, b.link, b.size, N, ctr);
-    k_ccl_flag<<<blocks, CCL_THREADS, 0, st>>>(b.parent, b.size, b.scan, N);
-    scan_exclusive(b.scan, N, b.scan_tmp, d_nlab, st);
+    const long long chunks = ceil_div_ll(N, CCL_CHUNK);
+    k_ccl_resolve_count<<<(unsigned)chunks, CCL_CHUNK_THREADS, 0, st>>>(b.parent, b.link, b.size, N, ctr,
+                                                                        b.scan_tmp);
+    k_ccl_chunk_scan<<<1, CCL_SCAN_THREADS, 0, st>>>(b.scan_tmp, chunks, d_nlab);
+    k_ccl_number<<<(unsigned)chunks, CCL_CHUNK_THREADS, 0, st>>>(b.parent, b.size, b.scan_tmp, b.scan, N);
     k_ccl_out<<<blocks, CCL_THREADS, 0, st>>>(b.parent, b.size, b.scan, out, N);
 }
 
