@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP16-storage, batched and serving forms")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving form")
+    ap.add_argument("--only-form", choices=["gradient_prior", "supervoxels"],
+                    help="diagnostics: run only this form and print its result (not the benchmark line)")
     return ap.parse_args()
 
 
@@ -761,8 +763,29 @@ def run_ours(args):
         td.destroy_process_group()
 
 
+def run_form(args):
+    import torch
+
+    from paper_1903_07149_gb300 import build as scalp_build
+    from paper_1903_07149_gb300 import synth
+
+    scalp_build.build()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    if args.only_form == "supervoxels":
+        res = measure_voxel(args, flush)
+    else:
+        w, rgb, con = synth.single_image_config(args.workload)
+        _, _, cells = synth.voronoi_image(w.H, w.W, w.n_cells, gradient=w.gradient,
+                                          noise_sigma=w.noise_sigma, seed=w.seed)
+        res = measure_prior(args, w, rgb, con, cells, flush)
+    print(json.dumps({"form": args.only_form, "result": res}))
+
+
 def main():
     args = parse()
+    if args.only_form:
+        run_form(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

@@ -56,12 +56,6 @@ __global__ void k_static_table(StaticScratch *s)
     }
 }
 
-__device__ __forceinline__ float static_lab_f(float t)
-{
-    const float d3 = (6.0f / 29.0f) * (6.0f / 29.0f) * (6.0f / 29.0f);
-    return t > d3 ? cbrtf(t) : t * (841.0f / 108.0f) + (4.0f / 29.0f);
-}
-
 // CIELab of 8-bit sRGB (the set-up kernel's conversion), then warp-aggregated
 // integer sums per label into the static scratch.  Labels outside
 // [0, n_labels) are skipped.
@@ -72,9 +66,6 @@ __global__ void __launch_bounds__(256)
     __shared__ float lin[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) lin[i] = s->lut[i];
     __syncthreads();
-    const float m[9] = {0.4124564f, 0.3575761f, 0.1804375f, 0.2126729f, 0.7151522f,
-                        0.0721750f, 0.0193339f, 0.1191920f, 0.9503041f};
-    const float wx = m[0] + m[1] + m[2], wy = m[3] + m[4] + m[5], wz = m[6] + m[7] + m[8];
     const long long segs_per_row = (W + 31) / 32;
     const long long n_segs = segs_per_row * H;
     const long long warps = (long long)gridDim.x * (blockDim.x / 32);
@@ -89,13 +80,8 @@ __global__ void __launch_bounds__(256)
         if (valid) {
             lab = labels[(long long)y * W + x];
             valid = lab >= 0 && lab < n_labels;
-            const uint8_t *px = rgb + y * rgb_stride + 3 * (long long)x;
-            const float R = lin[px[0]], G = lin[px[1]], B = lin[px[2]];
-            const float X = m[0] * R + m[1] * G + m[2] * B;
-            const float Y = m[3] * R + m[4] * G + m[5] * B;
-            const float Z = m[6] * R + m[7] * G + m[8] * B;
-            const float fx = static_lab_f(X / wx), fy = static_lab_f(Y / wy), fz = static_lab_f(Z / wz);
-            v = make_float4(116.0f * fy - 16.0f, 500.0f * (fx - fy), 200.0f * (fy - fz), 0.f);
+            const float3 lab = srgb_to_lab(lin, rgb + y * rgb_stride + 3 * (long long)x);
+            v = make_float4(lab.x, lab.y, lab.z, 0.f);
         }
         warp_aggregate_global(valid, valid ? lab : 0, bx, y, x - bx, 0, v, s->sums);
     }

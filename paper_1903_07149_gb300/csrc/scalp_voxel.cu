@@ -411,6 +411,7 @@ __device__ __forceinline__ int vpath_sums(const float4 *__restrict__ plane, int 
     const int two_ns = 2 * ns, two_d1 = 2 * d1, two_d2 = 2 * d2;
     int e1 = ns, e2 = ns;
     float dc = 0.f, w = 0.f;
+#pragma unroll 4
     for (int i = 0; i <= ns; ++i) {
         const float4 v = __ldg(q);
         dc += colour_dist(v, cL, ca, cb);

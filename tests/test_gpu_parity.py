@@ -349,6 +349,40 @@ def test_full_size_hd_one_step(S):
     seg.close()
 
 
+def test_full_size_uhd_sampled(S):
+    """2160x3840, K=10000 (the largest single-image workload): the GPU's
+    initial grid state equals the oracle's bit for bit; then one GPU
+    assignment from it, checked on 20,000 sampled pixels against the oracle's
+    pixel-by-pixel evaluation of the same state (near-tie rule as above)."""
+    import torch
+
+    w, rgb, con = synth.single_image_config("uhd_2160x3840_k10000")
+    orc = oracle.Solver(oracle.lab_from_rgb(rgb), con, w.K)
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        seg = S.Segmenter(torch.from_numpy(rgb).cuda(), torch.from_numpy(con).cuda(), w.K,
+                          stream=stream)
+        g0 = seg.get_state()
+        assert np.array_equal(g0["labels"], orc.labels)
+        for k in ("n", "sx", "sy"):
+            assert np.array_equal(g0[k], getattr(orc, k)), k
+        assert np.array_equal(g0["endpoint"], orc.endpoints())
+        seg.iterate(1)
+        g = seg.get_state()
+    rng = np.random.default_rng(77)
+    pix = rng.choice(orc.N, size=20000, replace=False)
+    lab, _ = orc.assign_pixels(pix)
+    got = g["labels"].ravel()[pix]
+    diff = np.nonzero(got != lab)[0]
+    for i in diff:
+        y, x = divmod(int(pix[i]), w.W)
+        Dg, _ = orc.distance(x, y, int(got[i]))
+        Do, _ = orc.distance(x, y, int(lab[i]))
+        assert (Dg - Do) / max(Do, 1e-12) < NEAR_TIE, (x, y, int(got[i]), int(lab[i]), Dg, Do)
+    assert len(diff) <= (1 - AGREE) * len(pix), len(diff)
+    seg.close()
+
+
 # --------------------------------------------------------------------------
 # FP16 storage of the (L, a, b, w) planes.
 #
