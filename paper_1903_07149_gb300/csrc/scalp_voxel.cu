@@ -428,36 +428,146 @@ __device__ __forceinline__ int vpath_sums(const float4 *__restrict__ plane, int 
     return ns + 1;
 }
 
+// Work items: the voxels of the tile inside candidate c's window form a box
+// (x fastest, then y, then t: a warp's paths then start in neighbouring
+// columns, so their global-memory samples share cache lines; ordering by the
+// paths' dominant axis instead was measured slower); every 32 consecutive
+// voxels of it are one warp's item.  Lanes walk their voxel's path and take a 64-bit shared-memory
+// atomicMin of (D bits, candidate slot); slots follow the cluster index, so
+// ties go to the smallest k.  A tile with more than VITEM_CAND candidates
+// evaluates voxel by voxel over the global list instead.
+constexpr int VITEM_CAND = 128;
+constexpr int VMAX_ITEMS = VITEM_CAND * (VTILE / 32);
+
+__device__ __forceinline__ unsigned long long vpack_best(float D, int slot)
+{
+    return ((unsigned long long)__float_as_uint(D) << 32) | (unsigned)slot;  // D >= 0
+}
+
 __global__ void __launch_bounds__(VTILE) k_vassign(VoxArgs a)
 {
-    __shared__ VoxCluster cand[VMAX_CAND];
-    __shared__ int s_ids[VMAX_CAND];
+    __shared__ VoxCluster cand[VITEM_CAND];
+    __shared__ int4 s_box[VITEM_CAND];     // (xa, ya, ta, w | h << 8 | d << 16)
+    __shared__ int2 s_rcp[VITEM_CAND];     // 16-bit reciprocals of w and h
+    __shared__ int s_ids[VITEM_CAND];
+    __shared__ int s_nit[VITEM_CAND];
+    __shared__ int s_first[VITEM_CAND + 1];
+    __shared__ unsigned char s_owner[VMAX_ITEMS];
+    __shared__ unsigned long long s_best[VTILE];
+    __shared__ int s_counter;
     const int tile = blockIdx.x;
     const int tx = tile % a.n_tx, ty = (tile / a.n_tx) % a.n_ty, tt = tile / (a.n_tx * a.n_ty);
-    const int tid = threadIdx.x;
+    const int x0 = tx * VTX, y0 = ty * VTY, t0 = tt * VTT;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int lx = tid % VTX, ly = (tid / VTX) % VTY, lt = tid / (VTX * VTY);
-    const int x = tx * VTX + lx, y = ty * VTY + ly, t = tt * VTT + lt;
+    const int x = x0 + lx, y = y0 + ly, t = t0 + lt;
     const bool valid = x < a.W && y < a.H && t < a.T;
     const int off = a.tile_off[tile];
     const int cnt = (int)max(0LL, min((long long)a.tile_off[tile + 1], a.tile_cap) - off);
+    const bool fast = cnt <= VITEM_CAND;
     const long long p = ((long long)t * a.H + y) * a.W + x;
-    const float4 own = valid ? __ldg(a.plane + p) : make_float4(0.f, 0.f, 0.f, 0.f);
-    float bestD = FLT_MAX;
-    int bestk = INT_MAX;
     unsigned my_samples = 0, my_pairs = 0;
-    for (int c0 = 0; c0 < cnt; c0 += VMAX_CAND) {
-        const int m = min(VMAX_CAND, cnt - c0);
+    int lab = -1;
+
+    if (fast) {
+        // candidates sorted by cluster index (ranks of distinct ids)
+        int myid = INT_MAX;
+        if (tid < cnt) {
+            myid = a.tile_list[off + tid];
+            s_ids[tid] = myid;
+        }
+        s_best[tid] = ~0ull;
+        if (tid == 0) s_counter = 0;
         __syncthreads();
-        if (tid < m) {
-            const int k = a.tile_list[off + c0 + tid];
-            s_ids[tid] = k;
-            cand[tid] = a.cdev[k];
+        if (tid < cnt) {
+            int rank = 0;
+            for (int j = 0; j < cnt; ++j) rank += s_ids[j] < myid;
+            const VoxCluster cd = a.cdev[myid];
+            cand[rank] = cd;
+            const int xa = max(cd.xlo, x0), xb = min(min(cd.xhi, x0 + VTX - 1), a.W - 1);
+            const int ya = max(cd.ylo, y0), yb = min(min(cd.yhi, y0 + VTY - 1), a.H - 1);
+            const int ta = max(cd.tlo, t0), tb = min(min(cd.thi, t0 + VTT - 1), a.T - 1);
+            const int w = max(xb - xa + 1, 0), h = max(yb - ya + 1, 0), d = max(tb - ta + 1, 0);
+            s_box[rank] = make_int4(xa, ya, ta, w | (h << 8) | (d << 16));
+            s_rcp[rank] = make_int2((65536 + max(w, 1) - 1) / max(w, 1), (65536 + max(h, 1) - 1) / max(h, 1));
+            s_nit[rank] = (w * h * d + 31) >> 5;
         }
         __syncthreads();
-        if (!valid) continue;
-        for (int i = 0; i < m; ++i) {
-            const VoxCluster &cd = cand[i];
-            if (x < cd.xlo || x > cd.xhi || y < cd.ylo || y > cd.yhi || t < cd.tlo || t > cd.thi) continue;
+        if (tid < 32) {  // exclusive prefix of the item counts
+            constexpr int PER = VITEM_CAND / 32;
+            int v[PER], sum = 0;
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int c = lane * PER + i;
+                v[i] = c < cnt ? s_nit[c] : 0;
+                sum += v[i];
+            }
+            int incl = sum;
+            for (int o = 1; o < 32; o <<= 1) {
+                const int u = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += u;
+            }
+            int run = incl - sum;
+#pragma unroll
+            for (int i = 0; i < PER; ++i) {
+                const int c = lane * PER + i;
+                if (c < cnt) s_first[c] = run;
+                run += v[i];
+            }
+            if (lane == 31) s_first[cnt] = incl;
+        }
+        __syncthreads();
+        if (tid < cnt) {
+            const int f = s_first[tid], n = s_nit[tid];
+            for (int j = 0; j < n; ++j) s_owner[f + j] = (unsigned char)tid;
+        }
+        __syncthreads();
+        const int n_items = s_first[cnt];
+        while (true) {
+            int item = 0;
+            if (lane == 0) item = atomicAdd(&s_counter, 1);
+            item = __shfl_sync(0xffffffffu, item, 0);
+            if (item >= n_items) break;
+            const int c = s_owner[item];
+            const int4 b = s_box[c];
+            const int w = b.w & 0xff, h = (b.w >> 8) & 0xff, d = b.w >> 16;
+            const int j = ((item - s_first[c]) << 5) + lane;
+            if (j >= w * h * d) continue;
+            const int2 r = s_rcp[c];
+            // exact: j < 512 and w, h <= 16, so the 16-bit reciprocals give floor
+            const int q = (j * r.x) >> 16;  // j / w
+            const int qx = b.x + (j - q * w);
+            const int qt = (q * r.y) >> 16;  // q / h
+            const int qy = b.y + (q - qt * h);
+            const int qtt = b.z + qt;
+            const VoxCluster &cd = cand[c];
+            float sdc, sw;
+            const int len = vpath_sums(a.plane, a.W, a.HW, qx, qy, qtt, cd.ex, cd.ey, cd.et, cd.L, cd.a, cd.b,
+                                       sdc, sw);
+            const float4 v = __ldg(a.plane + ((long long)qtt * a.H + qy) * a.W + qx);
+            const float dcp = colour_dist(v, cd.L, cd.a, cd.b);
+            const float ddx = (float)qx - cd.xk, ddy = (float)qy - cd.yk, ddt = (float)qtt - cd.tk;
+            const float ds = fmaf(ddx, ddx, fmaf(ddy, ddy, ddt * ddt));
+            const float D = scalp_distance(dcp, sdc, sw, len, a.lam, a.gamma, a.ms2, ds);
+            atomicMin(&s_best[((qtt - t0) * VTY + (qy - y0)) * VTX + (qx - x0)], vpack_best(D, c));
+            my_samples += len;
+            my_pairs += 1;
+        }
+        __syncthreads();
+        if (valid) {
+            const unsigned long long bb = s_best[tid];
+            // slot -> cluster index (the record's pad field holds k)
+            if (bb != ~0ull) lab = cand[(int)(bb & 0xffffffffu)].pad;
+        }
+    } else {
+        const float4 own = valid ? __ldg(a.plane + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+        float bestD = FLT_MAX;
+        int bestk = INT_MAX;
+        for (int i = 0; i < cnt; ++i) {
+            const int k = a.tile_list[off + i];
+            const VoxCluster cd = a.cdev[k];
+            if (!valid || x < cd.xlo || x > cd.xhi || y < cd.ylo || y > cd.yhi || t < cd.tlo || t > cd.thi)
+                continue;
             float sdc, sw;
             const int len = vpath_sums(a.plane, a.W, a.HW, x, y, t, cd.ex, cd.ey, cd.et, cd.L, cd.a, cd.b,
                                        sdc, sw);
@@ -465,7 +575,6 @@ __global__ void __launch_bounds__(VTILE) k_vassign(VoxArgs a)
             const float ddx = (float)x - cd.xk, ddy = (float)y - cd.yk, ddt = (float)t - cd.tk;
             const float ds = fmaf(ddx, ddx, fmaf(ddy, ddy, ddt * ddt));
             const float D = scalp_distance(dcp, sdc, sw, len, a.lam, a.gamma, a.ms2, ds);
-            const int k = s_ids[i];
             if (D < bestD || (D == bestD && k < bestk)) {
                 bestD = D;
                 bestk = k;
@@ -473,11 +582,10 @@ __global__ void __launch_bounds__(VTILE) k_vassign(VoxArgs a)
             my_samples += len;
             my_pairs += 1;
         }
+        if (bestk != INT_MAX) lab = bestk;
     }
-    int lab = -1;
     if (valid) {
-        if (bestk != INT_MAX) {
-            lab = bestk;
+        if (lab >= 0) {
             a.labels[p] = lab;
         } else {
             lab = a.labels[p];  // no window reaches the voxel: keep its label
@@ -485,14 +593,15 @@ __global__ void __launch_bounds__(VTILE) k_vassign(VoxArgs a)
         }
     }
     // a warp = 32 voxels of one frame: 16 columns x 2 rows
-    const int bx = tx * VTX, by = ty * VTY + (ly & ~1), bt = t;
+    const float4 own = valid ? __ldg(a.plane + p) : make_float4(0.f, 0.f, 0.f, 0.f);
+    const int bx = x0, by = y0 + (ly & ~1), bt = t;
     vaggregate(a, valid, lab, bx, by, bt, lx, ly & 1, 0, own);
     if (a.count_samples) {
         for (int o = 16; o > 0; o >>= 1) {
             my_samples += __shfl_down_sync(0xffffffffu, my_samples, o);
             my_pairs += __shfl_down_sync(0xffffffffu, my_pairs, o);
         }
-        if ((tid & 31) == 0) {
+        if (lane == 0) {
             atomicAdd(&a.ctr->samples, (unsigned long long)my_samples);
             atomicAdd(&a.ctr->pairs, (unsigned long long)my_pairs);
         }
