@@ -275,11 +275,14 @@ void enqueue_iteration(scalp_ctx *c, int slot, bool capturing)
 {
     const unsigned flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
     if (c->profiling) cudaEventRecordWithFlags(c->ev_pool[2 * slot], c->st, flags);
-    launch_assign(c->a, c->p.storage, c->smem, c->st);
+    // programmatic launches overlap each kernel's placement with the drain of
+    // the one before (not across the profiling event records)
+    const bool pdl = !c->profiling;
+    launch_assign(c->a, c->p.storage, c->smem, c->st, pdl);
     if (c->profiling) cudaEventRecordWithFlags(c->ev_pool[2 * slot + 1], c->st, flags);
-    launch_update(c->a, 1, c->st);
-    launch_project(c->a, 0, c->st);
-    launch_lists(c->a, c->st);
+    launch_update(c->a, 1, c->st, pdl);
+    launch_project(c->a, 0, c->st, pdl);
+    launch_lists(c->a, c->st, pdl);
 }
 
 }  // namespace

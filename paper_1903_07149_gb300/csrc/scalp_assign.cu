@@ -471,6 +471,8 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
 template <typename T>
 __global__ void __launch_bounds__(ASSIGN_THREADS, ASSIGN_CTAS_PER_SM) k_assign(SolveArgs a)
 {
+    pdl_wait();
+    pdl_release();
     extern __shared__ __align__(16) unsigned char smem[];
     assign_tile<T>(a, blockIdx.x, smem);
 }
@@ -486,11 +488,11 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, ASSIGN_CTAS_PER_SM) k_assign_b
     assign_tile<T>(b.args[i], g - b.tile_base[i], smem);
 }
 
-void launch_assign(const SolveArgs &a, int storage, size_t smem_bytes, cudaStream_t st)
+void launch_assign(const SolveArgs &a, int storage, size_t smem_bytes, cudaStream_t st, bool pdl)
 {
-    const int tiles = a.n_tx * a.n_ty;
-    if (storage == 0) k_assign<float4><<<tiles, ASSIGN_THREADS, smem_bytes, st>>>(a);
-    else k_assign<uint2><<<tiles, ASSIGN_THREADS, smem_bytes, st>>>(a);
+    const dim3 grid(a.n_tx * a.n_ty), block(ASSIGN_THREADS);
+    if (storage == 0) pdl_launch(pdl, k_assign<float4>, grid, block, smem_bytes, st, a);
+    else pdl_launch(pdl, k_assign<uint2>, grid, block, smem_bytes, st, a);
 }
 
 void launch_assign_batch(const BatchArgs &b, int storage, int total_tiles, size_t smem_bytes,

@@ -56,6 +56,15 @@ __device__ __forceinline__ float3 srgb_to_lab(const float *lin, const uint8_t *p
     return make_float3(116.0f * fy - 16.0f, 500.0f * (fx - fy), 200.0f * (fy - fz));
 }
 
+// Programmatic dependent launch: a kernel launched with pdl_launch() may be
+// placed on the GPU while its predecessor in the stream is still draining.
+// It calls pdl_wait() before it reads anything the predecessor wrote (the wait
+// returns once the predecessor has completed and its writes are visible), and
+// pdl_release() to let its own successor be placed early.  Both are no-ops
+// for a kernel launched the ordinary way.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_release() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // What the assignment kernel reads about one cluster (48 bytes).
 struct ClusterDev {
     float L, a, b;           // mean CIELab colour

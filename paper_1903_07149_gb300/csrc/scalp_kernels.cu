@@ -347,6 +347,8 @@ __device__ __forceinline__ void update_cluster(const SolveArgs &a, int k, int fr
 
 __global__ void k_update(SolveArgs a, int from_acc)
 {
+    pdl_wait();
+    pdl_release();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k < a.Keff) update_cluster(a, k, from_acc);
 }
@@ -359,10 +361,10 @@ __global__ void k_update_batch(BatchArgs b, int from_acc)
     update_cluster(b.args[i], g - b.clus_base[i], from_acc);
 }
 
-void launch_update(const SolveArgs &a, int from_acc, cudaStream_t st)
+void launch_update(const SolveArgs &a, int from_acc, cudaStream_t st, bool pdl)
 {
     // small blocks: one thread per cluster is latency-bound, so spread them
-    k_update<<<(a.Keff + 63) / 64, 64, 0, st>>>(a, from_acc);
+    pdl_launch(pdl, k_update, dim3((a.Keff + 63) / 64), dim3(64), 0, st, a, from_acc);
 }
 
 // Queued projections: S_k lies inside the window the last assignment used for
@@ -436,6 +438,8 @@ __device__ __forceinline__ void project_cta(const SolveArgs &a, int whole_image,
 
 __global__ void __launch_bounds__(PROJ_THREADS) k_project(SolveArgs a, int whole_image)
 {
+    pdl_wait();
+    pdl_release();
     project_cta(a, whole_image, blockIdx.x, gridDim.x);
 }
 
@@ -448,9 +452,9 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project_batch(BatchArgs b, int
     project_cta(b.args[i], whole_image, blockIdx.x % PROJ_CTAS_PER_IMAGE, PROJ_CTAS_PER_IMAGE);
 }
 
-void launch_project(const SolveArgs &a, int whole_image, cudaStream_t st)
+void launch_project(const SolveArgs &a, int whole_image, cudaStream_t st, bool pdl)
 {
-    k_project<<<std::min(a.Keff, 2 * 152), PROJ_THREADS, 0, st>>>(a, whole_image);
+    pdl_launch(pdl, k_project, dim3(std::min(a.Keff, 2 * 152)), dim3(PROJ_THREADS), 0, st, a, whole_image);
 }
 
 // ---------------------------------------------------------------------------
@@ -551,6 +555,8 @@ constexpr int LISTS_MAX_TILES = 12287;  // (n + 1) ints of shared memory <= 48 K
 
 __global__ void __launch_bounds__(LISTS_THREADS) k_lists(SolveArgs a)
 {
+    pdl_wait();
+    pdl_release();
     extern __shared__ int s_off[];
     __shared__ int s_warp[32];
     const int n = a.n_tx * a.n_ty;
@@ -595,13 +601,14 @@ void launch_batch_update(const BatchArgs &b, int total_clusters, int total_fill,
     k_fill_tiles_batch<<<(total_fill + 255) / 256, 256, 0, st>>>(b);
 }
 
-void launch_lists(const SolveArgs &a, cudaStream_t st)
+void launch_lists(const SolveArgs &a, cudaStream_t st, bool pdl)
 {
     const int n = a.n_tx * a.n_ty;
     const long long slots = (long long)a.Keff * a.tpw_x * a.tpw_y;
     if (n <= LISTS_MAX_TILES) {
         const long long blocks = std::min(ceil_div_ll(slots, LISTS_THREADS), 2LL * 152);
-        k_lists<<<(unsigned)std::max(blocks, 1LL), LISTS_THREADS, (size_t)(n + 1) * sizeof(int), st>>>(a);
+        pdl_launch(pdl, k_lists, dim3((unsigned)std::max(blocks, 1LL)), dim3(LISTS_THREADS),
+                   (size_t)(n + 1) * sizeof(int), st, a);
     } else {
         k_scan_tiles<<<1, SCAN1_THREADS, 0, st>>>(a);
         k_fill_tiles<<<(unsigned)ceil_div_ll(slots, 256), 256, 0, st>>>(a);

@@ -5,7 +5,28 @@
 
 typedef struct scalp_ctx scalp_ctx;
 
+#include <utility>
+
 namespace scalp {
+
+// Launch with programmatic stream serialization (see pdl_wait/pdl_release):
+// with pdl false it is an ordinary launch.
+template <typename... Params, typename... Args>
+cudaError_t pdl_launch(bool pdl, void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem,
+                       cudaStream_t st, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 
 // Sets the text scalp_last_error(NULL) returns on this thread.
 void set_last_error(const char *msg);
@@ -29,11 +50,11 @@ void launch_accumulate(const SolveArgs &a, cudaStream_t st);
 // Cluster update (Algorithm 1) from a.acc when from_acc (queueing projections,
 // Eq. 4), then windows, the cluster records and the tile counts.  The tile
 // counts and list cursors must be zero on entry.
-void launch_update(const SolveArgs &a, int from_acc, cudaStream_t st);
+void launch_update(const SolveArgs &a, int from_acc, cudaStream_t st, bool pdl = false);
 // Eq. 4 for the queued clusters; whole_image=1 searches every pixel.
-void launch_project(const SolveArgs &a, int whole_image, cudaStream_t st);
+void launch_project(const SolveArgs &a, int whole_image, cudaStream_t st, bool pdl = false);
 // Per-tile candidate lists from the tile counts; resets per-iteration counters.
-void launch_lists(const SolveArgs &a, cudaStream_t st);
+void launch_lists(const SolveArgs &a, cudaStream_t st, bool pdl = false);
 // Batch: the assignment of every tile of every image in one launch, and one
 // iteration's update, projection and candidate lists for every image.
 void launch_assign_batch(const BatchArgs &b, int storage, int total_tiles, size_t smem_bytes,
@@ -42,7 +63,7 @@ cudaError_t assign_batch_configure(int storage);
 void launch_batch_update(const BatchArgs &b, int total_clusters, int total_fill, cudaStream_t st);
 // Assignment (Algorithm 1 inner loops, Eq. 1-3) with a.map_cap distance-map
 // pairs per CTA; smem_bytes = assign_smem_bytes(a.map_cap).
-void launch_assign(const SolveArgs &a, int storage, size_t smem_bytes, cudaStream_t st);
+void launch_assign(const SolveArgs &a, int storage, size_t smem_bytes, cudaStream_t st, bool pdl = false);
 size_t assign_smem_bytes(int map_cap);
 // Distance-map pairs that fit when ASSIGN_CTAS_PER_SM assignment CTAs share an SM.
 int assign_map_capacity(int device);

@@ -37,7 +37,6 @@ namespace {
 
 constexpr int VTX = 16, VTY = 8, VTT = 4;  // voxel tile
 constexpr int VTILE = VTX * VTY * VTT;     // 512 voxels, one per thread
-constexpr int VMAX_CAND = 256;             // candidates of a tile in shared memory
 constexpr int VPROJ_THREADS = 512;
 
 struct VoxCluster {  // 64 bytes: what the assignment reads about cluster k
