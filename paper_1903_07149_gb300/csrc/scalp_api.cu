@@ -993,8 +993,8 @@ int scalp_batch_iterate(scalp_batch *b, int32_t n)
     if (n == 0) return SCALP_OK;
     auto enqueue = [&](int iters) {
         for (int i = 0; i < iters; ++i) {
-            launch_assign_batch(b->bargs, b->storage, b->total_tiles, b->smem, b->st);
-            launch_batch_update(b->bargs, b->total_clusters, b->total_fill, b->st);
+            launch_assign_batch(b->bargs, b->storage, b->total_tiles, b->smem, b->st, true);
+            launch_batch_update(b->bargs, b->total_clusters, b->total_fill, b->st, true);
         }
     };
     const bool graphs = b->use_graph && b->st != nullptr;

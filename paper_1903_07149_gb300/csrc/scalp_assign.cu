@@ -482,6 +482,8 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, ASSIGN_CTAS_PER_SM) k_assign(S
 template <typename T>
 __global__ void __launch_bounds__(ASSIGN_THREADS, ASSIGN_CTAS_PER_SM) k_assign_batch(BatchArgs b)
 {
+    pdl_wait();
+    pdl_release();
     extern __shared__ __align__(16) unsigned char smem[];
     const int g = blockIdx.x;
     const int i = batch_find(b.tile_base, b.count, g);
@@ -496,11 +498,12 @@ void launch_assign(const SolveArgs &a, int storage, size_t smem_bytes, cudaStrea
 }
 
 void launch_assign_batch(const BatchArgs &b, int storage, int total_tiles, size_t smem_bytes,
-                         cudaStream_t st)
+                         cudaStream_t st, bool pdl)
 {
     if (total_tiles <= 0) return;
-    if (storage == 0) k_assign_batch<float4><<<total_tiles, ASSIGN_THREADS, smem_bytes, st>>>(b);
-    else k_assign_batch<uint2><<<total_tiles, ASSIGN_THREADS, smem_bytes, st>>>(b);
+    const dim3 grid(total_tiles), block(ASSIGN_THREADS);
+    if (storage == 0) pdl_launch(pdl, k_assign_batch<float4>, grid, block, smem_bytes, st, b);
+    else pdl_launch(pdl, k_assign_batch<uint2>, grid, block, smem_bytes, st, b);
 }
 
 // The limit is a property of the kernel, shared by every context on the

@@ -355,6 +355,8 @@ __global__ void k_update(SolveArgs a, int from_acc)
 
 __global__ void k_update_batch(BatchArgs b, int from_acc)
 {
+    pdl_wait();
+    pdl_release();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= b.clus_base[b.count]) return;
     const int i = batch_find(b.clus_base, b.count, g);
@@ -448,6 +450,8 @@ constexpr int PROJ_CTAS_PER_IMAGE = 16;
 
 __global__ void __launch_bounds__(PROJ_THREADS) k_project_batch(BatchArgs b, int whole_image)
 {
+    pdl_wait();
+    pdl_release();
     const int i = blockIdx.x / PROJ_CTAS_PER_IMAGE;
     project_cta(b.args[i], whole_image, blockIdx.x % PROJ_CTAS_PER_IMAGE, PROJ_CTAS_PER_IMAGE);
 }
@@ -530,6 +534,8 @@ __global__ void __launch_bounds__(SCAN1_THREADS) k_scan_tiles(SolveArgs a) { sca
 
 __global__ void __launch_bounds__(SCAN1_THREADS) k_scan_tiles_batch(BatchArgs b)
 {
+    pdl_wait();
+    pdl_release();
     scan_tiles_cta(b.args[blockIdx.x]);
 }
 
@@ -585,6 +591,8 @@ __global__ void k_fill_tiles(SolveArgs a)
 
 __global__ void k_fill_tiles_batch(BatchArgs b)
 {
+    pdl_wait();
+    pdl_release();
     const int g = blockIdx.x * blockDim.x + threadIdx.x;
     if (g >= b.fill_base[b.count]) return;
     const int i = batch_find(b.fill_base, b.count, g);
@@ -592,13 +600,13 @@ __global__ void k_fill_tiles_batch(BatchArgs b)
 }
 
 // One iteration's update, projection and list kernels for a whole batch.
-void launch_batch_update(const BatchArgs &b, int total_clusters, int total_fill, cudaStream_t st)
+void launch_batch_update(const BatchArgs &b, int total_clusters, int total_fill, cudaStream_t st, bool pdl)
 {
     if (b.count <= 0) return;
-    k_update_batch<<<(total_clusters + 63) / 64, 64, 0, st>>>(b, 1);
-    k_project_batch<<<b.count * PROJ_CTAS_PER_IMAGE, PROJ_THREADS, 0, st>>>(b, 0);
-    k_scan_tiles_batch<<<b.count, SCAN1_THREADS, 0, st>>>(b);
-    k_fill_tiles_batch<<<(total_fill + 255) / 256, 256, 0, st>>>(b);
+    pdl_launch(pdl, k_update_batch, dim3((total_clusters + 63) / 64), dim3(64), 0, st, b, 1);
+    pdl_launch(pdl, k_project_batch, dim3(b.count * PROJ_CTAS_PER_IMAGE), dim3(PROJ_THREADS), 0, st, b, 0);
+    pdl_launch(pdl, k_scan_tiles_batch, dim3(b.count), dim3(SCAN1_THREADS), 0, st, b);
+    pdl_launch(pdl, k_fill_tiles_batch, dim3((total_fill + 255) / 256), dim3(256), 0, st, b);
 }
 
 void launch_lists(const SolveArgs &a, cudaStream_t st, bool pdl)

@@ -58,9 +58,10 @@ void launch_lists(const SolveArgs &a, cudaStream_t st, bool pdl = false);
 // Batch: the assignment of every tile of every image in one launch, and one
 // iteration's update, projection and candidate lists for every image.
 void launch_assign_batch(const BatchArgs &b, int storage, int total_tiles, size_t smem_bytes,
-                         cudaStream_t st);
+                         cudaStream_t st, bool pdl = false);
 cudaError_t assign_batch_configure(int storage);
-void launch_batch_update(const BatchArgs &b, int total_clusters, int total_fill, cudaStream_t st);
+void launch_batch_update(const BatchArgs &b, int total_clusters, int total_fill, cudaStream_t st,
+                         bool pdl = false);
 // Assignment (Algorithm 1 inner loops, Eq. 1-3) with a.map_cap distance-map
 // pairs per CTA; smem_bytes = assign_smem_bytes(a.map_cap).
 void launch_assign(const SolveArgs &a, int storage, size_t smem_bytes, cudaStream_t st, bool pdl = false);

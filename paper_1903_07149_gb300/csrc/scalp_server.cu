@@ -253,8 +253,8 @@ int scalp_server_step(scalp_server *s, int32_t *n_running)
             const int rc = rebuild_args(s, running);
             if (rc) return rc;
         }
-        launch_assign_batch(s->bargs, s->params.storage, s->total_tiles, s->smem, s->st);
-        launch_batch_update(s->bargs, s->total_clusters, s->total_fill, s->st);
+        launch_assign_batch(s->bargs, s->params.storage, s->total_tiles, s->smem, s->st, true);
+        launch_batch_update(s->bargs, s->total_clusters, s->total_fill, s->st, true);
         const cudaError_t e = cudaGetLastError();
         if (e != cudaSuccess) return server_fail(SCALP_E_CUDA, "server step: %s", cudaGetErrorString(e));
         for (Solve *v : running) {
