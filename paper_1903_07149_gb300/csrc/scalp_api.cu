@@ -1,5 +1,5 @@
 // scalp_api.cu -- the C ABI of libscalp (declared in include/scalp.h):
-// argument checks, workspace carving, the TMA descriptor, CUDA-graph replay
+// argument checks, workspace carving, kernel configuration, CUDA-graph replay
 // of one iteration, state I/O.  All device work is in the kernel files.
 #include <cmath>
 #include <cstdarg>
