@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP16-storage, batched and serving forms")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving form")
-    ap.add_argument("--only-form", choices=["gradient_prior", "supervoxels"],
+    ap.add_argument("--only-form", choices=["gradient_prior", "supervoxels", "serving"],
                     help="diagnostics: run only this form and print its result (not the benchmark line)")
     return ap.parse_args()
 
@@ -333,9 +333,10 @@ def measure_serving(args, batch_imgs, n_requests: int = 2000, rate_hz: float = 5
     stream = torch.cuda.Stream()
     srv = scalp.Server(int(budget_gb * (1 << 30)), max_slots=1024, storage=storage, iters=iters,
                        stream=stream)
-    warm = [srv.submit(*reqs[i]) for i in range(8)]
-    while any(not srv.poll(r[0])[0] for r in warm if r):
+    warm = {r[0] for r in (srv.submit(*reqs[i]) for i in range(8)) if r}
+    while warm:
         srv.step()
+        warm = {rid for rid in warm if not srv.poll(rid)[0]}
 
     lat = np.zeros(n_requests)
     t0 = time.perf_counter()
@@ -784,6 +785,9 @@ def run_form(args):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     if args.only_form == "supervoxels":
         res = measure_voxel(args, flush)
+    elif args.only_form == "serving":
+        bws = synth.batch_configs()
+        res = measure_serving(args, (bws, *synth.batch_images(bws)))
     else:
         w, rgb, con = synth.single_image_config(args.workload)
         _, _, cells = synth.voronoi_image(w.H, w.W, w.n_cells, gradient=w.gradient,

@@ -314,7 +314,11 @@ void scalp_voxel_destroy(scalp_vctx *ctx);
  * whether a request's labels have arrived (and then releases its memory).  The
  * labels equal those of scalp_init + scalp_iterate + scalp_labels on the same
  * image.  labels_out should be pinned host memory: with pageable memory the copy
- * synchronises the stream.  One server is driven by one host thread. */
+ * synchronises the stream.  No call waits for the stream to drain: a step waits
+ * only for the step eight argument uploads back (the argument blocks form a
+ * ring in the reserve), and a request's status travels with its labels.
+ * scalp_server_destroy() synchronises the stream.  One server is driven by one
+ * host thread. */
 typedef struct scalp_server scalp_server;
 
 size_t scalp_server_reserve_bytes(int32_t max_slots);

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstdlib>
 #include <algorithm>
+#include <cstddef>
 #include <cstring>
 #include <new>
 #include <string>
@@ -783,38 +784,55 @@ SolveArgs scalp_ctx_args(const scalp_ctx *c) { return c->a; }
 size_t scalp_ctx_smem(const scalp_ctx *c) { return c->smem; }
 void scalp_ctx_count_iteration(scalp_ctx *c) { c->iterations += 1; }
 
-// Enqueues the connectivity enforcement (if enforce) and the copy of the
-// labels to host memory `out`; no synchronisation.
-int scalp_ctx_enqueue_labels(scalp_ctx *c, int32_t *out, int enforce)
+// Enqueues the connectivity enforcement (if enforce), the copy of the labels
+// to host memory `out` and the copy of the solve's status (label count and the
+// device-side error flags) to pinned host memory `status`; no synchronisation.
+int scalp_ctx_enqueue_labels(scalp_ctx *c, int32_t *out, int enforce, CtxStatus *status)
 {
     const size_t bytes = sizeof(int) * (size_t)c->N;
     const int *src = c->a.labels;
+    const int *d_nlab = reinterpret_cast<const int *>(c->ws + c->L.nlab);
     if (enforce) {
-        int *d_nlab = reinterpret_cast<int *>(c->ws + c->L.nlab);
-        launch_ccl(c->a.labels, c->H, c->W, c->K, c->ccl.link, c->ccl, d_nlab, c->a.ctr, c->st);
+        launch_ccl(c->a.labels, c->H, c->W, c->K, c->ccl.link, c->ccl, const_cast<int *>(d_nlab),
+                   c->a.ctr, c->st);
         src = c->ccl.link;
     }
     int rc = launch_check(c, "connectivity kernels");
     if (rc) return rc;
-    return cuda_check(c, cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToHost, c->st), "copy labels");
-}
-
-// After the enqueued work has completed: the label count and device status.
-int scalp_ctx_finish_labels(scalp_ctx *c, int enforce, int32_t *n_labels)
-{
-    int nlab = c->Keff;
+    rc = cuda_check(c, cudaMemcpyAsync(out, src, bytes, cudaMemcpyDeviceToHost, c->st), "copy labels");
+    if (rc) return rc;
+    status->n_labels = c->Keff;
     if (enforce) {
-        int rc = cuda_check(c, cudaMemcpy(&nlab, c->ws + c->L.nlab, sizeof(int), cudaMemcpyDeviceToHost),
-                            "copy label count");
+        rc = cuda_check(c, cudaMemcpyAsync(&status->n_labels, d_nlab, sizeof(int), cudaMemcpyDeviceToHost, c->st),
+                        "copy label count");
         if (rc) return rc;
     }
-    DevCounters h;
-    int rc = cuda_check(c, cudaMemcpy(&h, c->a.ctr, sizeof h, cudaMemcpyDeviceToHost), "read counters");
-    if (rc) return rc;
-    if (h.timeout) return fail(c, SCALP_E_TIMEOUT, "a bounded device-side wait gave up");
-    if (h.error) return fail(c, SCALP_E_INTERNAL, "device-side check failed (code %d)", h.error);
-    *n_labels = nlab;
+    return cuda_check(c, cudaMemcpyAsync(&status->error, &c->a.ctr->error, 2 * sizeof(int),
+                                         cudaMemcpyDeviceToHost, c->st),
+                      "copy status");
+}
+
+static_assert(offsetof(DevCounters, timeout) == offsetof(DevCounters, error) + sizeof(int) &&
+                  offsetof(CtxStatus, timeout) == offsetof(CtxStatus, error) + sizeof(int),
+              "the two flags are copied as one block");
+
+// After the enqueued work has completed: the label count and device status.
+int scalp_ctx_finish_labels(scalp_ctx *c, const CtxStatus *status, int32_t *n_labels)
+{
+    if (status->timeout) return fail(c, SCALP_E_TIMEOUT, "a bounded device-side wait gave up");
+    if (status->error) return fail(c, SCALP_E_INTERNAL, "device-side check failed (code %d)", status->error);
+    *n_labels = status->n_labels;
     return SCALP_OK;
+}
+
+// Frees a context's host state without synchronising: the caller has seen
+// every piece of enqueued work that uses it complete (no graph, no events).
+void scalp_ctx_release(scalp_ctx *c)
+{
+    if (!c) return;
+    if (c->graph_valid) cudaGraphExecDestroy(c->gexec);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    delete c;
 }
 
 }  // namespace scalp

@@ -87,7 +87,14 @@ void launch_ccl(const int *labels, int H, int W, int K, int *out, const CclBuffe
 SolveArgs scalp_ctx_args(const scalp_ctx *c);
 size_t scalp_ctx_smem(const scalp_ctx *c);
 void scalp_ctx_count_iteration(scalp_ctx *c);
-int scalp_ctx_enqueue_labels(scalp_ctx *c, int32_t *out, int enforce);
-int scalp_ctx_finish_labels(scalp_ctx *c, int enforce, int32_t *n_labels);
+// status of a delivered solve, copied to pinned host memory behind its labels
+struct CtxStatus {
+    int error, timeout;  // the device-side flags (DevCounters order)
+    int n_labels;
+    int pad;
+};
+int scalp_ctx_enqueue_labels(scalp_ctx *c, int32_t *out, int enforce, CtxStatus *status);
+int scalp_ctx_finish_labels(scalp_ctx *c, const CtxStatus *status, int32_t *n_labels);
+void scalp_ctx_release(scalp_ctx *c);
 
 }  // namespace scalp

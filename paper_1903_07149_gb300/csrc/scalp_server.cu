@@ -9,6 +9,11 @@
 // its iterations is retired: connectivity enforcement and the copy of its
 // labels to the caller's buffer are enqueued, followed by an event that
 // scalp_server_poll() checks.
+//
+// The host never drains the stream while serving: the per-step argument
+// blocks live in a ring of ARG_RING device blocks, each staged from pinned
+// host memory and reused only after the event behind the last step that read
+// it; a delivered solve's status arrives in pinned memory with its labels.
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
@@ -25,6 +30,7 @@ using namespace scalp;
 namespace {
 
 constexpr size_t SALIGN = 256;
+constexpr int ARG_RING = 8;  // argument blocks in flight
 
 size_t salign(size_t x) { return (x + SALIGN - 1) & ~(SALIGN - 1); }
 
@@ -36,6 +42,7 @@ struct Solve {
     int enforce = 1;
     int32_t *labels_out = nullptr;
     cudaEvent_t done = nullptr;
+    int status_slot = -1;  // its entry in the pinned status array
     bool retired = false;
 };
 
@@ -50,10 +57,14 @@ int server_fail(int code, const char *fmt, ...)
     return code;
 }
 
-size_t head_bytes(int slots)
+// one argument block: the solves' SolveArgs, then their tile, cluster and
+// list-slot prefix sums
+size_t block_bytes(int slots)
 {
     return salign((size_t)slots * sizeof(SolveArgs)) + 3 * salign((size_t)(slots + 1) * sizeof(int));
 }
+
+size_t head_bytes(int slots) { return ARG_RING * block_bytes(slots); }
 
 }  // namespace
 
@@ -72,6 +83,12 @@ struct scalp_server {
     int total_tiles = 0, total_clusters = 0, total_fill = 0;
     size_t smem = 0;
     std::vector<cudaEvent_t> spare_events;
+    unsigned char *stage = nullptr;  // pinned: ARG_RING argument blocks
+    CtxStatus *status = nullptr;     // pinned: max_slots status entries
+    std::vector<int> free_status;
+    cudaEvent_t ring_ev[ARG_RING] = {};
+    bool ring_live[ARG_RING] = {};
+    int ring_next = 0, ring_cur = 0;
 };
 
 namespace {
@@ -109,12 +126,29 @@ void pool_free(scalp_server *s, size_t off, size_t bytes)
     }
 }
 
-// Uploads the argument blocks of the solves still iterating.
+// Uploads the argument block of the solves still iterating into the next ring
+// slot (compact: offsets follow the count n).
 int rebuild_args(scalp_server *s, std::vector<Solve *> &running)
 {
     const int n = (int)running.size();
-    std::vector<SolveArgs> args(n);
-    std::vector<int> tile(n + 1, 0), clus(n + 1, 0), fill(n + 1, 0);
+    const int slot = s->ring_next;
+    s->ring_next = (slot + 1) % ARG_RING;
+    if (s->ring_live[slot]) {  // a step in flight may still read this slot
+        const cudaError_t w = cudaEventSynchronize(s->ring_ev[slot]);
+        if (w != cudaSuccess) return server_fail(SCALP_E_CUDA, "argument ring: %s", cudaGetErrorString(w));
+        s->ring_live[slot] = false;
+    }
+    const size_t blk = block_bytes(s->max_slots);
+    unsigned char *h = s->stage + slot * blk;
+    unsigned char *d = s->pool + slot * blk;
+    const size_t o_tile = salign((size_t)n * sizeof(SolveArgs));
+    const size_t o_clus = o_tile + salign((size_t)(n + 1) * sizeof(int));
+    const size_t o_fill = o_clus + salign((size_t)(n + 1) * sizeof(int));
+    SolveArgs *args = reinterpret_cast<SolveArgs *>(h);
+    int *tile = reinterpret_cast<int *>(h + o_tile);
+    int *clus = reinterpret_cast<int *>(h + o_clus);
+    int *fill = reinterpret_cast<int *>(h + o_fill);
+    tile[0] = clus[0] = fill[0] = 0;
     size_t smem = 0;
     for (int i = 0; i < n; ++i) {
         const scalp_ctx *c = running[i]->ctx;
@@ -124,27 +158,15 @@ int rebuild_args(scalp_server *s, std::vector<Solve *> &running)
         fill[i + 1] = fill[i] + args[i].Keff * args[i].tpw_x * args[i].tpw_y;
         smem = std::max(smem, scalp_ctx_smem(c));
     }
-    unsigned char *h = s->pool;
-    const size_t o_args = 0;
-    const size_t o_tile = o_args + salign((size_t)s->max_slots * sizeof(SolveArgs));
-    const size_t o_clus = o_tile + salign((size_t)(s->max_slots + 1) * sizeof(int));
-    const size_t o_fill = o_clus + salign((size_t)(s->max_slots + 1) * sizeof(int));
-    cudaError_t e = cudaSuccess;
-    if (n > 0)
-        e = cudaMemcpyAsync(h + o_args, args.data(), n * sizeof(SolveArgs), cudaMemcpyHostToDevice, s->st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h + o_tile, tile.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, s->st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h + o_clus, clus.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, s->st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(h + o_fill, fill.data(), (n + 1) * sizeof(int), cudaMemcpyHostToDevice, s->st);
-    // the host vectors are released on return: wait for the copies
-    if (e == cudaSuccess) e = cudaStreamSynchronize(s->st);
+    cudaError_t e = cudaMemcpyAsync(d, h, o_fill + (size_t)(n + 1) * sizeof(int), cudaMemcpyHostToDevice, s->st);
+    if (e == cudaSuccess) e = cudaEventRecord(s->ring_ev[slot], s->st);
     if (e != cudaSuccess) return server_fail(SCALP_E_CUDA, "server arguments: %s", cudaGetErrorString(e));
-    s->bargs.args = reinterpret_cast<const SolveArgs *>(h + o_args);
-    s->bargs.tile_base = reinterpret_cast<const int *>(h + o_tile);
-    s->bargs.clus_base = reinterpret_cast<const int *>(h + o_clus);
-    s->bargs.fill_base = reinterpret_cast<const int *>(h + o_fill);
+    s->ring_live[slot] = true;
+    s->ring_cur = slot;
+    s->bargs.args = reinterpret_cast<const SolveArgs *>(d);
+    s->bargs.tile_base = reinterpret_cast<const int *>(d + o_tile);
+    s->bargs.clus_base = reinterpret_cast<const int *>(d + o_clus);
+    s->bargs.fill_base = reinterpret_cast<const int *>(d + o_fill);
     s->bargs.count = n;
     s->total_tiles = tile[n];
     s->total_clusters = clus[n];
@@ -152,6 +174,14 @@ int rebuild_args(scalp_server *s, std::vector<Solve *> &running)
     s->smem = smem;
     s->args_dirty = false;
     return SCALP_OK;
+}
+
+void free_host(scalp_server *s)
+{
+    for (cudaEvent_t e : s->ring_ev)
+        if (e) cudaEventDestroy(e);
+    if (s->stage) cudaFreeHost(s->stage);
+    delete s;
 }
 
 }  // namespace
@@ -184,10 +214,18 @@ int scalp_server_create(scalp_server **out, void *pool, size_t pool_bytes, int32
     s->free_list[head] = (pool_bytes - head) & ~(SALIGN - 1);
     // the batched assignment may need up to the full shared memory of an SM
     cudaError_t e = assign_batch_configure(params->storage);
+    const size_t ring = ARG_RING * block_bytes(max_slots);
+    if (e == cudaSuccess)
+        e = cudaHostAlloc(reinterpret_cast<void **>(&s->stage), ring + (size_t)max_slots * sizeof(CtxStatus),
+                          cudaHostAllocDefault);
+    for (int i = 0; i < ARG_RING && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&s->ring_ev[i], cudaEventDisableTiming);
     if (e != cudaSuccess) {
-        delete s;
-        return server_fail(SCALP_E_CUDA, "configure: %s", cudaGetErrorString(e));
+        free_host(s);
+        return server_fail(SCALP_E_CUDA, "server setup: %s", cudaGetErrorString(e));
     }
+    s->status = reinterpret_cast<CtxStatus *>(s->stage + ring);
+    for (int i = max_slots - 1; i >= 0; --i) s->free_status.push_back(i);
     *out = s;
     return SCALP_OK;
 }
@@ -229,6 +267,8 @@ int scalp_server_submit(scalp_server *s, const scalp_image *image, const scalp_c
     }
     v->done = s->spare_events.back();
     s->spare_events.pop_back();
+    v->status_slot = s->free_status.back();
+    s->free_status.pop_back();
     v->id = s->next_id++;
     v->off = off;
     v->bytes = bytes;
@@ -255,7 +295,9 @@ int scalp_server_step(scalp_server *s, int32_t *n_running)
         }
         launch_assign_batch(s->bargs, s->params.storage, s->total_tiles, s->smem, s->st, true);
         launch_batch_update(s->bargs, s->total_clusters, s->total_fill, s->st, true);
-        const cudaError_t e = cudaGetLastError();
+        cudaError_t e = cudaGetLastError();
+        // the argument slot stays live until this step has run
+        if (e == cudaSuccess) e = cudaEventRecord(s->ring_ev[s->ring_cur], s->st);
         if (e != cudaSuccess) return server_fail(SCALP_E_CUDA, "server step: %s", cudaGetErrorString(e));
         for (Solve *v : running) {
             --v->iters_left;
@@ -265,7 +307,7 @@ int scalp_server_step(scalp_server *s, int32_t *n_running)
     // retire the solves whose iterations are done
     for (Solve *v : s->active) {
         if (v->retired || v->iters_left > 0) continue;
-        const int rc = scalp_ctx_enqueue_labels(v->ctx, v->labels_out, v->enforce);
+        const int rc = scalp_ctx_enqueue_labels(v->ctx, v->labels_out, v->enforce, &s->status[v->status_slot]);
         if (rc) return rc;
         const cudaError_t e = cudaEventRecord(v->done, s->st);
         if (e != cudaSuccess) return server_fail(SCALP_E_CUDA, "record: %s", cudaGetErrorString(e));
@@ -288,13 +330,15 @@ int scalp_server_poll(scalp_server *s, uint64_t id, int32_t *done, int32_t *n_la
     if (q == cudaErrorNotReady) return SCALP_OK;
     if (q != cudaSuccess) return server_fail(SCALP_E_CUDA, "request %llu: %s", (unsigned long long)id, cudaGetErrorString(q));
     int32_t nl = 0;
-    int rc = scalp_ctx_finish_labels(v->ctx, v->enforce, &nl);
+    int rc = scalp_ctx_finish_labels(v->ctx, &s->status[v->status_slot], &nl);
     if (rc) return rc;
     *done = 1;
     if (n_labels) *n_labels = nl;
-    // release: the state leaves the pool
-    scalp_destroy(v->ctx);
+    // release: the state leaves the pool.  Its done event covers every step
+    // that read it (later argument blocks leave it out), so no stream wait.
+    scalp_ctx_release(v->ctx);
     pool_free(s, v->off, v->bytes);
+    s->free_status.push_back(v->status_slot);
     s->spare_events.push_back(v->done);
     s->active.erase(std::find(s->active.begin(), s->active.end(), v));
     s->by_id.erase(it);
@@ -319,12 +363,12 @@ void scalp_server_destroy(scalp_server *s)
     if (!s) return;
     cudaStreamSynchronize(s->st);
     for (Solve *v : s->active) {
-        scalp_destroy(v->ctx);
+        scalp_ctx_release(v->ctx);
         cudaEventDestroy(v->done);
         delete v;
     }
     for (cudaEvent_t e : s->spare_events) cudaEventDestroy(e);
-    delete s;
+    free_host(s);
 }
 
 }  // extern "C"

@@ -636,7 +636,7 @@ class Server:
             c = contour.contiguous()
             keep.append(c)
             con = scalp_contour(c.data_ptr(), 0)
-        out = torch.empty((rgb.shape[0], rgb.shape[1]), dtype=torch.int32).pin_memory()
+        out = torch.empty((rgb.shape[0], rgb.shape[1]), dtype=torch.int32, pin_memory=True)
         rid = scalp_server_submit(self.server, img, con, K, self.m, self.iters, self.enforce,
                                   out.data_ptr())
         if rid is None:
