@@ -154,8 +154,11 @@ int scalp_set_state(scalp_ctx *ctx, const scalp_state *state);
 /* Linear paths (Sec. II-B) as the assignment kernel walks them, for checking:
  * pairs holds M rows (px, py, ex, ey) of host int32; out_len[i] receives
  * max(|ex-px|, |ey-py|) + 1 and out_xy[i*stride_xy .. ] the (x, y) pixels in
- * walking order (stride_xy int32 per row, >= 2*out_len[i]).  All host memory;
- * coordinates must lie in the image. */
+ * walking order (as many as stride_xy int32 per row hold; 2*out_len[i] for
+ * the whole path).  The kernels step along a path in two equivalent forms (an
+ * error term; a 32-bit fixed-point slope for paths of at most 512 steps): both
+ * are walked, and out_len[i] = -1 reports a path on which they disagree.  All
+ * host memory; coordinates must lie in the image. */
 int scalp_debug_paths(scalp_ctx *ctx, const int32_t *pairs, int32_t M, int32_t *out_xy,
                       int32_t stride_xy, int32_t *out_len);
 

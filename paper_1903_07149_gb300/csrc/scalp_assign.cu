@@ -62,11 +62,16 @@ __device__ __forceinline__ int path_sums_map(uint32_t map, int bw, int bx0, int 
     path_strides(s, bw, smaj, smin);
     const uint32_t q0 = map + (uint32_t)(((s.ay - by0) * bw + (s.ax - bx0)) * 8);
     float dc = 0.f, w = 0.f;
-    int len = walk_steps(q0, smaj * 8, smin * 8, s, [&](uint32_t q) {
+    const auto visit = [&](uint32_t q) {
         const float2 v = lds_pair(q);
         dc += v.x;
         w += v.y;
-    });
+    };
+    // the fixed-point form of the steps (fewer instructions per sample)
+    // covers every path of up to FIXED_STEP_MAX_NS steps
+    const int len = s.ns <= FIXED_STEP_MAX_NS
+                        ? walk_with<FixedPointStep>(q0, smaj * 8, smin * 8, s, visit)
+                        : walk_with<ErrorTermStep>(q0, smaj * 8, smin * 8, s, visit);
     sum_dc = dc;
     sum_w = w;
     return len;

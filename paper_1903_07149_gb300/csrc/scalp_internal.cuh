@@ -191,25 +191,87 @@ __device__ __forceinline__ PathSetup path_setup(int px, int py, int ex, int ey)
     return s;
 }
 
+// The stepping rule of every path (Sec. II-B): after sample i the walk has
+// taken m_i = floor(1/2 + i dmin / ns) minor steps.  Two forms give the same
+// steps (a debugging entry point walks both in lockstep):
+//
+// Error term: e starts at ns and grows by 2 dmin per step; a minor step is
+// taken (and 2 ns removed) when e reaches 2 ns, so e = ns + 2 i dmin - 2 ns m_i.
+struct ErrorTermStep {
+    int e, two_d, two_ns, smaj, sboth;
+    __device__ __forceinline__ ErrorTermStep(const PathSetup &s, int smaj_, int smin_)
+        : e(s.ns), two_d(2 * s.dmin), two_ns(2 * s.ns), smaj(smaj_), sboth(smaj_ + smin_) {}
+    __device__ __forceinline__ int next()
+    {
+        e += two_d;
+        if (e >= two_ns) {
+            e -= two_ns;
+            return sboth;
+        }
+        return smaj;
+    }
+};
+
+// Fixed point: a 32-bit accumulator starts at 2^31 and adds S per step; its
+// carry is the minor step.  With S = dmin 2^32 / ns + eps, the carry count
+// after i steps is floor(1/2 + i dmin / ns + i eps / 2^32).  For 0 < eps <=
+// FIXED_STEP_EPS and ns <= FIXED_STEP_MAX_NS the excess i eps / 2^32 stays
+// below 1 / (2 ns), the least distance from 1/2 + i dmin / ns up to the next
+// integer when it is not one, so the count is m_i.  dmin = ns (exact slope
+// 2^32) takes S = 2^32 - 1: the count is i + floor((2^31 - i) / 2^32) = i.
+constexpr int FIXED_STEP_MAX_NS = 512;
+constexpr uint32_t FIXED_STEP_EPS = 4610;
+static_assert((double)FIXED_STEP_EPS * FIXED_STEP_MAX_NS * FIXED_STEP_MAX_NS < 2147483648.0,
+              "i eps / 2^32 < 1 / (2 ns) for every i <= ns <= FIXED_STEP_MAX_NS");
+
+// S for 0 <= dmin <= ns <= FIXED_STEP_MAX_NS.  The estimate dmin / ns * 2^32
+// from the approximate reciprocal (at most 4 ulp: relative error below 2^-21,
+// so within 2304 of the exact slope, itself below 2^32 - 2^23 when dmin < ns)
+// is raised by 2305: then 0 < S - dmin 2^32 / ns < 4610 = FIXED_STEP_EPS.
+__device__ __forceinline__ uint32_t fixed_step_slope(int dmin, int ns)
+{
+    if (dmin >= ns) return 0xffffffffu;  // also ns = 0: one sample, no step
+    float inv;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"((float)ns));
+    const float f = (float)dmin * inv * 4294967296.0f;
+    return __float2uint_rz(f) + (FIXED_STEP_EPS / 2);
+}
+static_assert(FIXED_STEP_EPS / 2 == 2305, "the raise covers a 4-ulp reciprocal");
+
+struct FixedPointStep {
+    uint32_t acc, S;
+    int smaj, sboth;
+    __device__ __forceinline__ FixedPointStep(const PathSetup &s, int smaj_, int smin_)
+        : acc(0x80000000u), S(fixed_step_slope(s.dmin, s.ns)), smaj(smaj_), sboth(smaj_ + smin_) {}
+    __device__ __forceinline__ int next()
+    {
+        const uint32_t na = acc + S;
+        const bool carry = na < acc;
+        acc = na;
+        return carry ? sboth : smaj;
+    }
+};
+
 // Steps through the |P| = ns + 1 samples of a path from its start `q`
-// (an address or offset in any unit): each step adds smaj, plus smin when the
-// error term wraps.  `visit` receives every sample address.  This is the one
-// stepping rule every walker (shared memory, global memory, debug) uses.
+// (an address or offset in any unit): each step adds smaj, plus smin on a
+// minor step.  `visit` receives every sample address.
+template <typename Step, typename Addr, typename Visit>
+__device__ __forceinline__ int walk_with(Addr q, int smaj, int smin, const PathSetup &s, Visit &&visit)
+{
+    Step st(s, smaj, smin);
+#pragma unroll 4
+    for (int i = 0; i <= s.ns; ++i) {
+        visit(q);
+        q += st.next();
+    }
+    return s.ns + 1;
+}
+
 template <typename Addr, typename Visit>
 __device__ __forceinline__ int walk_steps(Addr q, int smaj, int smin, const PathSetup &s,
                                           Visit &&visit)
 {
-    const int two_ns = 2 * s.ns, two_d = 2 * s.dmin;
-    int e = s.ns;
-#pragma unroll 4
-    for (int i = 0; i <= s.ns; ++i) {
-        visit(q);
-        e += two_d;
-        int step = smaj;
-        if (e >= two_ns) { e -= two_ns; step += smin; }
-        q += step;
-    }
-    return s.ns + 1;
+    return walk_with<ErrorTermStep>(q, smaj, smin, s, visit);
 }
 
 // Element strides of the major and minor steps on a plane with row pitch `pitch`.

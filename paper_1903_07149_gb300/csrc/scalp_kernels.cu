@@ -626,23 +626,36 @@ void launch_lists(const SolveArgs &a, cudaStream_t st, bool pdl)
 // ---------------------------------------------------------------------------
 // Debug: the path pixels exactly as the assignment kernel steps through them.
 // ---------------------------------------------------------------------------
+// One path per thread, pixels in walking order.  The error-term steps give
+// the pixels; paths short enough for the fixed-point form are walked with it
+// in lockstep, and a disagreement on any sample reports length -1.
 __global__ void k_debug_paths(const int *pairs, int M, int *out_xy, int stride_xy, int *out_len,
                               int W)
 {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= M) return;
-    PathSetup s = path_setup(pairs[4 * i], pairs[4 * i + 1], pairs[4 * i + 2], pairs[4 * i + 3]);
-    // the walker only does pointer arithmetic here; nothing is dereferenced
-    const char *base = reinterpret_cast<const char *>(out_xy);
+    const PathSetup s = path_setup(pairs[4 * i], pairs[4 * i + 1], pairs[4 * i + 2], pairs[4 * i + 3]);
+    int smaj, smin;
+    path_strides(s, W, smaj, smin);
+    // offsets in the image, row pitch W (nothing is dereferenced)
+    const long long start = (long long)s.ay * W + s.ax;
+    long long qe = start, qf = start;
+    ErrorTermStep e(s, smaj, smin);
+    FixedPointStep f(s, smaj, smin);
+    const bool check = s.ns <= FIXED_STEP_MAX_NS;
+    bool same = true;
     int *o = out_xy + (long long)i * stride_xy;
-    int cnt = 0;
-    int len = walk_path(base, W, 0, 0, s, [&](const char *q) {
-        long long off = q - base;
-        int y = (int)(off / W), x = (int)(off - (long long)y * W);
-        if (2 * cnt + 1 < stride_xy) { o[2 * cnt] = x; o[2 * cnt + 1] = y; }
-        ++cnt;
-    });
-    out_len[i] = len;
+    for (int k = 0; k <= s.ns; ++k) {
+        if (2 * k + 1 < stride_xy) {
+            const int y = (int)(qe / W);
+            o[2 * k] = (int)(qe - (long long)y * W);
+            o[2 * k + 1] = y;
+        }
+        same = same && (!check || qf == qe);
+        qe += e.next();
+        if (check) qf += f.next();
+    }
+    out_len[i] = same ? s.ns + 1 : -1;
 }
 
 void launch_debug_paths(const int *pairs, int M, int *out_xy, int stride_xy, int *out_len, int W,

@@ -87,6 +87,30 @@ def test_paths_bit_exact(S):
     seg.close()
 
 
+def test_path_step_forms_agree_exhaustively(S):
+    """Every path of up to 512 steps, in all eight octants and both end
+    orders: the kernel's fixed-point steps equal its error-term steps (the
+    debug kernel walks both in lockstep and reports -1 on a difference)."""
+    n = 513
+    rgb = np.zeros((n, n, 3), np.uint8)
+    con = np.zeros((n, n), np.float32)
+    seg = make_seg(S, rgb, con, 4)
+    ns, d = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    keep = d <= ns
+    ns, d = ns[keep], d[keep]
+    z = np.zeros_like(ns)
+    rows = []
+    for a, b in (((z, z), (ns, d)), ((z, d), (ns, z)), ((z, z), (d, ns)), ((z, ns), (d, z))):
+        rows.append(np.stack([a[0], a[1], b[0], b[1]], axis=1))  # from the left end
+        rows.append(np.stack([b[0], b[1], a[0], a[1]], axis=1))  # from the right end
+    pairs = np.concatenate(rows).astype(np.int32)
+    xy, ln = seg.debug_paths(pairs, stride_xy=2)
+    want = np.maximum(np.abs(pairs[:, 2] - pairs[:, 0]), np.abs(pairs[:, 3] - pairs[:, 1])) + 1
+    bad = np.flatnonzero(ln != want)
+    assert bad.size == 0, pairs[bad[:5]]
+    seg.close()
+
+
 def test_init_matches_oracle(S):
     H, W, K = 150, 230, 120
     rgb, con, _ = synth.small_image(H, W, seed=2)
