@@ -192,29 +192,29 @@ __device__ __forceinline__ PathSetup path_setup(int px, int py, int ex, int ey)
 }
 
 // The stepping rule of every path (Sec. II-B): after sample i the walk has
-// taken m_i = floor(1/2 + i dmin / ns) minor steps.  Two forms give the same
-// steps (a debugging entry point walks both in lockstep):
+// taken m_i = floor(1/2 + i dmin / ns) minor steps (per minor axis, for the
+// 3-D paths of supervoxels).  Two forms of the carry (is step i -> i+1 a minor
+// step?) give the same m_i; a debugging entry point walks both in lockstep.
 //
 // Error term: e starts at ns and grows by 2 dmin per step; a minor step is
 // taken (and 2 ns removed) when e reaches 2 ns, so e = ns + 2 i dmin - 2 ns m_i.
-struct ErrorTermStep {
-    int e, two_d, two_ns, smaj, sboth;
-    __device__ __forceinline__ ErrorTermStep(const PathSetup &s, int smaj_, int smin_)
-        : e(s.ns), two_d(2 * s.dmin), two_ns(2 * s.ns), smaj(smaj_), sboth(smaj_ + smin_) {}
-    __device__ __forceinline__ int next()
+struct ErrorTermCarry {
+    int e, two_d, two_ns;
+    __device__ __forceinline__ ErrorTermCarry(int dmin, int ns) : e(ns), two_d(2 * dmin), two_ns(2 * ns) {}
+    __device__ __forceinline__ bool next()
     {
         e += two_d;
         if (e >= two_ns) {
             e -= two_ns;
-            return sboth;
+            return true;
         }
-        return smaj;
+        return false;
     }
 };
 
 // Fixed point: a 32-bit accumulator starts at 2^31 and adds S per step; its
 // carry is the minor step.  With S = dmin 2^32 / ns + eps, the carry count
-// after i steps is floor(1/2 + i dmin / ns + i eps / 2^32).  For 0 < eps <=
+// after i steps is floor(1/2 + i dmin / ns + i eps / 2^32).  For 0 < eps <
 // FIXED_STEP_EPS and ns <= FIXED_STEP_MAX_NS the excess i eps / 2^32 stays
 // below 1 / (2 ns), the least distance from 1/2 + i dmin / ns up to the next
 // integer when it is not one, so the count is m_i.  dmin = ns (exact slope
@@ -238,19 +238,29 @@ __device__ __forceinline__ uint32_t fixed_step_slope(int dmin, int ns)
 }
 static_assert(FIXED_STEP_EPS / 2 == 2305, "the raise covers a 4-ulp reciprocal");
 
-struct FixedPointStep {
+struct FixedPointCarry {
     uint32_t acc, S;
-    int smaj, sboth;
-    __device__ __forceinline__ FixedPointStep(const PathSetup &s, int smaj_, int smin_)
-        : acc(0x80000000u), S(fixed_step_slope(s.dmin, s.ns)), smaj(smaj_), sboth(smaj_ + smin_) {}
-    __device__ __forceinline__ int next()
+    __device__ __forceinline__ FixedPointCarry(int dmin, int ns) : acc(0x80000000u), S(fixed_step_slope(dmin, ns)) {}
+    __device__ __forceinline__ bool next()
     {
         const uint32_t na = acc + S;
         const bool carry = na < acc;
         acc = na;
-        return carry ? sboth : smaj;
+        return carry;
     }
 };
+
+// The address step of a 2-D path: smaj, plus smin on a minor step.
+template <typename Carry>
+struct PathStep {
+    Carry c;
+    int smaj, sboth;
+    __device__ __forceinline__ PathStep(const PathSetup &s, int smaj_, int smin_)
+        : c(s.dmin, s.ns), smaj(smaj_), sboth(smaj_ + smin_) {}
+    __device__ __forceinline__ int next() { return c.next() ? sboth : smaj; }
+};
+using ErrorTermStep = PathStep<ErrorTermCarry>;
+using FixedPointStep = PathStep<FixedPointCarry>;
 
 // Steps through the |P| = ns + 1 samples of a path from its start `q`
 // (an address or offset in any unit): each step adds smaj, plus smin on a
