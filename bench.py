@@ -682,30 +682,57 @@ def run_ours(args):
     total_ms = rank_max(sum(step_ms))
     value = whole_job_value(N * iters * args.steps, world, total_ms)
 
-    # end to end through the public API: pinned host buffers in, labels out
+    # end to end through the public API: pinned host buffers in, labels out.
+    # Two solves in flight, as a throughput user would run them: each host
+    # thread drives one context on its own stream (the library's blocking
+    # calls release the interpreter lock), so one step's copies overlap the
+    # other's kernels.  Every step uploads its inputs, flushes L2 and reads
+    # its labels back inside the timed region.
     e2e = None
     if not args.no_e2e:
+        import threading
+
         h_rgb = torch.from_numpy(rgb).pin_memory()
         h_con = torch.from_numpy(con).pin_memory()
-        h_out = torch.empty((w.H, w.W), dtype=torch.int32).pin_memory()
-        a_rgb, a_con, a_out = h_rgb.numpy(), h_con.numpy(), h_out.numpy()
-        with torch.cuda.stream(stream):
-            seg.reload(a_rgb, a_con)
-            seg.iterate(iters)
-            seg.labels(enforce=True, out=a_out)
-            t_e2e = 0.0
-            for _ in range(args.steps):
-                flush.zero_()
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                seg.reload(a_rgb, a_con)
-                seg.iterate(iters)
-                seg.labels(enforce=True, out=a_out)
-                t_e2e += time.perf_counter() - t0
-        t_e2e = rank_max(t_e2e)
+        a_rgb, a_con = h_rgb.numpy(), h_con.numpy()
+        streams = [stream, torch.cuda.Stream()]
+        segs = [seg, scalp.Segmenter(d_rgb, d_con, w.K, storage=args.storage, stream=streams[1])]
+        outs = [torch.empty((w.H, w.W), dtype=torch.int32, pin_memory=True).numpy() for _ in range(2)]
+        flushes = [flush, torch.empty_like(flush)]
+        errors = []
+
+        def run(j, n):
+            try:
+                torch.cuda.set_device(local)
+                with torch.cuda.stream(streams[j]):
+                    for _ in range(n):
+                        flushes[j].zero_()
+                        segs[j].reload(a_rgb, a_con)
+                        segs[j].iterate(iters)
+                        segs[j].labels(enforce=True, out=outs[j])
+            except Exception as exc:  # reported after the join
+                errors.append(exc)
+
+        for j in range(2):
+            run(j, 1)
+        torch.cuda.synchronize()
+        if dist:
+            td.barrier()
+        t0 = time.perf_counter()
+        threads = [threading.Thread(target=run, args=(j, (args.steps + 1 - j) // 2)) for j in range(2)]
+        for t in threads:
+            t.start()
+        for t in threads:
+            t.join()
+        torch.cuda.synchronize()
+        t_e2e = rank_max(time.perf_counter() - t0)
+        if errors:
+            raise errors[0]
+        segs[1].close()
         e2e = {"value": whole_job_value(N * iters * args.steps, world, t_e2e * 1e3), "unit": UNIT,
                "h2d_bytes_per_step": int(rgb.nbytes + con.nbytes),
-               "d2h_bytes_per_step": int(w.H * w.W * 4)}
+               "d2h_bytes_per_step": int(w.H * w.W * 4),
+               "pipeline": "two contexts on two streams, one host thread each"}
 
     if rank != 0:
         if dist:
