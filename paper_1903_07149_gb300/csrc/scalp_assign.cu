@@ -106,7 +106,8 @@ struct AssignSmem {
     static constexpr size_t best = align16(area + MAX_TILE_CANDIDATES * sizeof(int));
     static constexpr size_t first = align16(best + TILE_PIXELS * sizeof(unsigned long long));
     static constexpr size_t mfirst = align16(first + (MAX_TILE_CANDIDATES + 1) * sizeof(int));
-    static constexpr size_t owner = align16(mfirst + (MAX_TILE_CANDIDATES + 1) * sizeof(int));
+    static constexpr size_t cfirst = align16(mfirst + (MAX_TILE_CANDIDATES + 1) * sizeof(int));
+    static constexpr size_t owner = align16(cfirst + (MAX_TILE_CANDIDATES + 1) * sizeof(int));
     static constexpr size_t misc = align16(owner + MAX_ITEMS);
     static constexpr size_t maps = align16(misc + 64);
 };
@@ -114,6 +115,7 @@ static_assert(AssignSmem::rec1 % 16 == 0 && AssignSmem::rec2 % 16 == 0 && Assign
                   AssignSmem::cid % 16 == 0 && AssignSmem::nit % 16 == 0 && AssignSmem::box % 16 == 0 &&
                   AssignSmem::area % 16 == 0 && AssignSmem::best % 16 == 0 &&
                   AssignSmem::first % 16 == 0 && AssignSmem::mfirst % 16 == 0 &&
+                  AssignSmem::cfirst % 16 == 0 &&
                   AssignSmem::owner % 16 == 0 && AssignSmem::misc % 16 == 0 &&
                   AssignSmem::maps % 16 == 0,
               "shared-memory sections aligned");
@@ -146,17 +148,18 @@ __device__ __forceinline__ unsigned long long pack_best(float D, int slot)
     return ((unsigned long long)__float_as_uint(D) << 32) | (unsigned)slot;
 }
 
-// Exclusive prefix of cnt <= MAX_TILE_CANDIDATES counts by one warp: out[c]
-// for c < cnt and the total in out[cnt].  Returns the largest prefix end
-// that stays <= cap (the leading candidates that fit a buffer of cap).
-__device__ __forceinline__ int warp_scan_counts(const int *in, int *out, int cnt, int cap, int lane)
+// Exclusive prefix of cnt <= MAX_TILE_CANDIDATES counts in(c) by one warp:
+// out[c] for c < cnt and the total in out[cnt].  Returns the largest prefix
+// end that stays <= cap (the leading candidates that fit a buffer of cap).
+template <typename In>
+__device__ __forceinline__ int warp_scan_counts(In in, int *out, int cnt, int cap, int lane)
 {
     constexpr int PER = MAX_TILE_CANDIDATES / 32;
     int v[PER], sum = 0;
 #pragma unroll
     for (int i = 0; i < PER; ++i) {
         const int c = lane * PER + i;
-        v[i] = c < cnt ? in[c] : 0;
+        v[i] = c < cnt ? in(c) : 0;
         sum += v[i];
     }
     int incl = sum;
@@ -193,6 +196,7 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
     constexpr int PIX_PER_THREAD = TILE_PIXELS / THREADS;
     constexpr int WARPS = THREADS / 32;
     constexpr int BUILD_UNROLL = 4;
+    constexpr int BUILD_CHUNK = BUILD_UNROLL * 32;  // map entries per warp task
     const T *__restrict__ plane = reinterpret_cast<const T *>(
         sizeof(T) == 16 ? (const void *)a.plane32 : (const void *)a.plane16);
     const int tx = tile % a.n_tx, ty = tile / a.n_tx;
@@ -210,6 +214,7 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
     unsigned long long *best = reinterpret_cast<unsigned long long *>(smem + AssignSmem::best);
     int *first = reinterpret_cast<int *>(smem + AssignSmem::first);
     int *mfirst = reinterpret_cast<int *>(smem + AssignSmem::mfirst);
+    int *cfirst = reinterpret_cast<int *>(smem + AssignSmem::cfirst);
     unsigned char *owner = smem + AssignSmem::owner;
     int *misc = reinterpret_cast<int *>(smem + AssignSmem::misc);
     float2 *maps = reinterpret_cast<float2 *>(smem + AssignSmem::maps);
@@ -272,10 +277,18 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
     }
     __syncthreads();
     for (int i = tid; i < TILE_PIXELS; i += THREADS) best[i] = ~0ull;
-    if (warp == 0 && fast) warp_scan_counts(nit, first, cnt, INT_MAX, lane);
+    if (warp == 0 && fast) warp_scan_counts([&](int c) { return nit[c]; }, first, cnt, INT_MAX, lane);
     if (warp == 1 && fast) {
-        const int used = warp_scan_counts(area, mfirst, cnt, a.map_cap, lane);
+        const int used = warp_scan_counts([&](int c) { return area[c]; }, mfirst, cnt, a.map_cap, lane);
         if (lane == 0) misc[2] = used;
+        __syncwarp();
+        // the map build's chunks: BUILD_CHUNK entries of one candidate each
+        warp_scan_counts(
+            [&](int c) {
+                const int n = mfirst[c + 1] - mfirst[c];
+                return area[c] > 0 && mfirst[c + 1] <= used ? (n + BUILD_CHUNK - 1) / BUILD_CHUNK : 0;
+            },
+            cfirst, cnt, INT_MAX, lane);
     }
     __syncthreads();
 
@@ -291,44 +304,36 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
             const bool mapped = area[tid] > 0 && mfirst[tid + 1] <= used;
             rec2[tid] = make_int4(b.x, b.y, b.z, mapped ? mfirst[tid] * (int)sizeof(float2) : -1);
         }
-        int c = -1, c_begin = 0, c_end = 0;  // the current candidate's entries
-        int4 b = make_int4(0, 0, 1, 0);
-        int bw = 1;
-        for (int e0 = tid; e0 < used; e0 += BUILD_UNROLL * THREADS) {
+        // warps take the chunks in turn; within one the candidate is uniform
+        // and the lanes read consecutive entries (coalesced plane rows)
+        const int n_chunks = cfirst[cnt];
+        int c = 0;
+        for (int g = warp; g < n_chunks; g += WARPS) {
+            while (g >= cfirst[c + 1]) ++c;
+            const int4 b = box[c];
+            // unpadded width: from the rectangle's right edge and e_k
+            const int4 r0 = rec0[c];
+            const int bw = max(r0.x + (r0.z & 0xff) - 1, rec1[c].x) - b.x + 1;
+            const float4 ck = col[c];
+            const int m0 = mfirst[c];
+            const int n_le = mfirst[c + 1] - m0;
+            const int le0 = (g - cfirst[c]) * BUILD_CHUNK + lane;
             T v[BUILD_UNROLL];  // raw samples: all loads issue before any use
-            int ec[BUILD_UNROLL];
+            bool ok[BUILD_UNROLL];
 #pragma unroll
             for (int u = 0; u < BUILD_UNROLL; ++u) {
-                const int e = e0 + u * THREADS;
-                ec[u] = -1;
-                if (e < used) {
-                    if (e >= c_end) {
-                        do {
-                            ++c;
-                            c_end = mfirst[c + 1];
-                        } while (e >= c_end);
-                        c_begin = mfirst[c];
-                        b = box[c];
-                        // unpadded width: from the rectangle's right edge and e_k
-                        const int4 r0 = rec0[c];
-                        bw = max(r0.x + (r0.z & 0xff) - 1, rec1[c].x) - b.x + 1;
-                    }
-                    const int le = e - c_begin;
-                    // le * pitch < 2^32, so the 32-bit reciprocal gives the exact row
-                    const int row = b.z > 1 ? (int)__umulhi((unsigned)le, (unsigned)b.w) : le;
-                    const int cx = le - row * b.z;
-                    if (cx < bw) {
-                        v[u] = __ldg(plane + (long long)(b.y + row) * a.pitch + (b.x + cx));
-                        ec[u] = c;
-                    }
-                }
+                const int le = le0 + u * 32;
+                // le * pitch < 2^32, so the 32-bit reciprocal gives the exact row
+                const int row = b.z > 1 ? (int)__umulhi((unsigned)le, (unsigned)b.w) : le;
+                const int cx = le - row * b.z;
+                ok[u] = le < n_le && cx < bw;
+                if (ok[u]) v[u] = __ldg(plane + (long long)(b.y + row) * a.pitch + (b.x + cx));
             }
 #pragma unroll
             for (int u = 0; u < BUILD_UNROLL; ++u) {
-                if (ec[u] >= 0) {
-                    const float4 ck = col[ec[u]];
+                if (ok[u]) {
                     const float4 q = sample_value(v[u]);
-                    maps[e0 + u * THREADS] = make_float2(colour_dist(q, ck.x, ck.y, ck.z), q.w);
+                    maps[m0 + le0 + u * 32] = make_float2(colour_dist(q, ck.x, ck.y, ck.z), q.w);
                 }
             }
         }
