@@ -179,6 +179,56 @@ __device__ __forceinline__ int warp_scan_counts(In in, int *out, int cnt, int ca
     return (int)__reduce_max_sync(0xffffffffu, (unsigned)fit);
 }
 
+// The map layout by one warp: mfirst = exclusive prefix of the box areas
+// (cnt + 1 entries); the leading candidates whose boxes end within cap get a
+// map, of CHUNK-entry chunks whose prefix goes to cfirst (cnt + 1 entries;
+// none for the others).  Returns the map entries used.
+template <int CHUNK>
+__device__ __forceinline__ int warp_scan_maps(const int *area, int *mfirst, int *cfirst, int cnt, int cap,
+                                              int lane)
+{
+    constexpr int PER = MAX_TILE_CANDIDATES / 32;
+    int v[PER], ch[PER], sum = 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int c = lane * PER + i;
+        v[i] = c < cnt ? area[c] : 0;
+        sum += v[i];
+    }
+    int incl = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    // a box fits when its prefix end is within cap (the ends only grow)
+    int run = incl - sum, fit = 0, csum = 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int c = lane * PER + i;
+        if (c < cnt) mfirst[c] = run;
+        run += v[i];
+        const bool mapped = c < cnt && v[i] > 0 && run <= cap;
+        if (c < cnt && run <= cap) fit = run;
+        ch[i] = mapped ? (v[i] + CHUNK - 1) / CHUNK : 0;
+        csum += ch[i];
+    }
+    if (lane == 31) mfirst[cnt] = incl;
+    int cincl = csum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, cincl, o);
+        if (lane >= o) cincl += t;
+    }
+    int crun = cincl - csum;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int c = lane * PER + i;
+        if (c < cnt) cfirst[c] = crun;
+        crun += ch[i];
+    }
+    if (lane == 31) cfirst[cnt] = cincl;
+    return (int)__reduce_max_sync(0xffffffffu, (unsigned)fit);
+}
+
 // Items: the pixels of a candidate's window that lie in the tile form a
 // rectangle.  When the rectangle lies mostly left or right of the path
 // endpoint (paths mostly along x, |P| set by the column) it is cut into
@@ -234,16 +284,17 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
     // staging reuses the `best` words before they are initialised
     int *ids = reinterpret_cast<int *>(best);
     int myid = INT_MAX;
+    ClusterDev cd;  // this thread's candidate: its load overlaps the barrier
     if (fast && tid < cnt) {
         myid = a.tile_list[off + tid];
         ids[tid] = myid;
+        cd = a.cdev[myid];
     }
     if (tid == 0) misc[1] = 0;  // work counter
     __syncthreads();
     if (fast && tid < cnt) {
         int rank = 0;
         for (int j = 0; j < cnt; ++j) rank += ids[j] < myid;
-        const ClusterDev cd = a.cdev[myid];
         cid[rank] = myid;
         // window x tile (clipped to the image), cut into strips
         const int xa = max(cd.xlo, x0), xb = min(min(cd.xhi, x0 + TILE_X - 1), a.W - 1);
@@ -269,7 +320,9 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
             pitch = bw + ((4 - bw) & 7);
             n = (long long)pitch * (max(yb, cd.ey) - by0 + 1);
         }
-        const unsigned rcp = (unsigned)((0x100000000ULL + pitch - 1) / pitch);
+        // ceil(2^32 / pitch) = floor((2^32 - 1) / pitch) + 1 for pitch >= 2
+        // (an empty box has pitch 1 and no map)
+        const unsigned rcp = pitch > 1 ? 0xffffffffu / (unsigned)pitch + 1u : 0u;
         box[rank] = make_int4(bx0, by0, pitch, (int)rcp);
         // a box larger than the whole buffer never fits: clamp it so that the
         // prefix sums stay small
@@ -279,16 +332,8 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
     for (int i = tid; i < TILE_PIXELS; i += THREADS) best[i] = ~0ull;
     if (warp == 0 && fast) warp_scan_counts([&](int c) { return nit[c]; }, first, cnt, INT_MAX, lane);
     if (warp == 1 && fast) {
-        const int used = warp_scan_counts([&](int c) { return area[c]; }, mfirst, cnt, a.map_cap, lane);
+        const int used = warp_scan_maps<BUILD_CHUNK>(area, mfirst, cfirst, cnt, a.map_cap, lane);
         if (lane == 0) misc[2] = used;
-        __syncwarp();
-        // the map build's chunks: BUILD_CHUNK entries of one candidate each
-        warp_scan_counts(
-            [&](int c) {
-                const int n = mfirst[c + 1] - mfirst[c];
-                return area[c] > 0 && mfirst[c + 1] <= used ? (n + BUILD_CHUNK - 1) / BUILD_CHUNK : 0;
-            },
-            cfirst, cnt, INT_MAX, lane);
     }
     __syncthreads();
 
@@ -318,22 +363,28 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
             const int m0 = mfirst[c];
             const int n_le = mfirst[c + 1] - m0;
             const int le0 = (g - cfirst[c]) * BUILD_CHUNK + lane;
+            // the box's first pixel; offsets within the box fit 32 bits: a
+            // box of at most map_cap pairs has row < min(H, map_cap / 4) and
+            // the plane pitch is at most W + 3, so row * pitch + column < 2^31
+            const T *__restrict__ pbox = plane + (long long)b.y * a.pitch + b.x;
+            float2 *mrow = maps + (m0 + le0);
             T v[BUILD_UNROLL];  // raw samples: all loads issue before any use
             bool ok[BUILD_UNROLL];
 #pragma unroll
             for (int u = 0; u < BUILD_UNROLL; ++u) {
                 const int le = le0 + u * 32;
-                // le * pitch < 2^32, so the 32-bit reciprocal gives the exact row
-                const int row = b.z > 1 ? (int)__umulhi((unsigned)le, (unsigned)b.w) : le;
+                // a mapped box has pitch >= 4 and le * pitch < 2^32, so the
+                // 32-bit reciprocal gives the exact row
+                const int row = (int)__umulhi((unsigned)le, (unsigned)b.w);
                 const int cx = le - row * b.z;
                 ok[u] = le < n_le && cx < bw;
-                if (ok[u]) v[u] = __ldg(plane + (long long)(b.y + row) * a.pitch + (b.x + cx));
+                if (ok[u]) v[u] = __ldg(pbox + (row * a.pitch + cx));
             }
 #pragma unroll
             for (int u = 0; u < BUILD_UNROLL; ++u) {
                 if (ok[u]) {
                     const float4 q = sample_value(v[u]);
-                    maps[m0 + le0 + u * 32] = make_float2(colour_dist(q, ck.x, ck.y, ck.z), q.w);
+                    mrow[u * 32] = make_float2(colour_dist(q, ck.x, ck.y, ck.z), q.w);
                 }
             }
         }
@@ -427,17 +478,25 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
     }
     __syncthreads();
 
-    // labels and the warp-aggregated integer sums of the update
-#pragma unroll 1
+    // labels and the warp-aggregated integer sums of the update; the
+    // pixels' own samples are all requested first
+    float4 owns[PIX_PER_THREAD];
+#pragma unroll
+    for (int j = 0; j < PIX_PER_THREAD; ++j) {
+        int px, py;
+        my_pixel(j, px, py);
+        owns[j] = px < a.W && py < a.H ? fetch_sample<T>(plane + (long long)py * a.pitch + px)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
     for (int j = 0; j < PIX_PER_THREAD; ++j) {
         int px, py;
         my_pixel(j, px, py);
         const bool valid = px < a.W && py < a.H;
         const long long p = (long long)py * a.W + px;
-        float4 own = make_float4(0.f, 0.f, 0.f, 0.f);
+        const float4 own = owns[j];
         int lab = -1;
         if (valid) {
-            own = fetch_sample<T>(plane + (long long)py * a.pitch + px);
             if (fast) {
                 const unsigned long long b = best[(py - y0) * TILE_X + (px - x0)];
                 if (b != ~0ull) lab = cid[(int)(b & 0xffffffffu)];

@@ -341,11 +341,6 @@ __device__ __forceinline__ float scalp_distance(float dcp, float sum_dc, float s
 
 // ---------------------------------------------------------------------------
 // Warp-aggregated segmented reduction.  Lanes holding the same key are summed
-// with warp reductions; the group's first lane hands the sums to `sink`.
-// Colour values are fixed point (x 2^24, fits int32 for CIELab of sRGB) and
-// summed as two int32 halves so a 32-lane sum cannot overflow.
-// ---------------------------------------------------------------------------
-// Warp-aggregated segmented reduction.  Lanes holding the same key are summed
 // with warp reductions and the group's first lane hands the sums to `sink`.
 // Coordinates come relative to a warp-uniform base (bx, by) with offsets in
 // [0, 31], so both offset sums pack into one 32-bit reduction; colour values
