@@ -23,7 +23,7 @@ thread_local std::string g_last_error;
 
 struct Layout {
     size_t rgb, contour, plane, labels, parent, size, link, scan, scan_tmp;
-    size_t st_n, st_sx, st_sy, st_col, st_end, cdev, acc, proj, prev_win, lut;
+    size_t st_n, st_sx, st_sy, st_col, st_end, cdev, acc, proj, prev_win;
     size_t tile_count, tile_off, tile_cursor, tile_list, ctr, nlab, debug;
     size_t total;
     long long tile_cap, scan_tmp_len;
@@ -93,7 +93,6 @@ Layout make_layout(int H, int W, int K, int storage)
     L.acc = carve(cur, Keff * sizeof(ClusterAcc));
     L.proj = carve(cur, Keff * 4);
     L.prev_win = carve(cur, Keff * 16);
-    L.lut = carve(cur, 256 * 4);
     L.tile_count = carve(cur, n_tiles * 4);
     L.tile_off = carve(cur, (n_tiles + 1) * 4);
     L.tile_cursor = carve(cur, n_tiles * 4);
@@ -380,7 +379,6 @@ int scalp_init(scalp_ctx **out, const scalp_image *image, const scalp_contour *c
     a.tpw_x = tiles_per_window(c->r, TILE_X);
     a.tpw_y = tiles_per_window(c->r, TILE_Y);
     a.prev_win = reinterpret_cast<int4 *>(c->ws + L.prev_win);
-    a.lut = reinterpret_cast<float *>(c->ws + L.lut);
     a.ctr = reinterpret_cast<DevCounters *>(c->ws + L.ctr);
     c->ccl.parent = reinterpret_cast<int *>(c->ws + L.parent);
     c->ccl.size = reinterpret_cast<int *>(c->ws + L.size);
@@ -395,10 +393,7 @@ int scalp_init(scalp_ctx **out, const scalp_image *image, const scalp_contour *c
     a.map_cap = params->global_walk ? 0 : assign_map_capacity(dev);
     c->smem = assign_smem_bytes(a.map_cap);
     int rc = cuda_check(c, assign_configure(params->storage), "configure kernel");
-    if (rc == SCALP_OK) {
-        launch_srgb_table(c->a, c->st);
-        rc = launch_check(c, "table kernel");
-    }
+    if (rc == SCALP_OK) rc = cuda_check(c, srgb_table(&a.lut, c->st), "transfer-function table");
     if (rc == SCALP_OK) rc = load_inputs(c, image, contour);
     if (rc != SCALP_OK) {
         delete c;
@@ -716,7 +711,7 @@ size_t scalp_gradient_prior_workspace_bytes(int32_t H, int32_t W, int32_t image_
     if (H < 1 || W < 1 || (long long)H * W > (1LL << 30)) return 0;
     const size_t N = (size_t)H * W;
     size_t cur = 0;
-    carve(cur, 256 * sizeof(float) + 16);  // transfer-function table, maximum
+    carve(cur, 16);  // the running maximum
     if (!image_on_device) carve(cur, 3 * N);
     if (!out_on_device) carve(cur, 4 * N);
     return (cur + ALIGN - 1) & ~(ALIGN - 1);
@@ -742,15 +737,15 @@ int scalp_gradient_prior(const scalp_image *image, float *out, int64_t out_strid
     unsigned char *ws = reinterpret_cast<unsigned char *>(workspace);
     const size_t N = (size_t)H * W;
     size_t cur = 0;
-    const size_t o_lut = carve(cur, 256 * sizeof(float) + 16);
+    const size_t o_max = carve(cur, 16);
     const size_t o_rgb = image->on_device ? 0 : carve(cur, 3 * N);
     const size_t o_out = out_on_device ? 0 : carve(cur, 4 * N);
-    float *lut = reinterpret_cast<float *>(ws + o_lut);
-    unsigned *gmax = reinterpret_cast<unsigned *>(ws + o_lut + 256 * sizeof(float));
+    unsigned *gmax = reinterpret_cast<unsigned *>(ws + o_max);
+    const float *lut = nullptr;
     const uint8_t *rgb = image->rgb;
     long long rs = image->rgb_stride ? image->rgb_stride : 3LL * W;
-    cudaError_t e = cudaSuccess;
-    if (!image->on_device) {
+    cudaError_t e = srgb_table(&lut, st);
+    if (e == cudaSuccess && !image->on_device) {
         e = cudaMemcpy2DAsync(ws + o_rgb, 3 * (size_t)W, rgb, (size_t)rs, 3 * (size_t)W, H,
                               cudaMemcpyHostToDevice, st);
         rgb = ws + o_rgb;
@@ -759,7 +754,6 @@ int scalp_gradient_prior(const scalp_image *image, float *out, int64_t out_strid
     float *d_out = out_on_device ? out : reinterpret_cast<float *>(ws + o_out);
     const long long d_stride = out_on_device ? out_stride : W;
     if (e == cudaSuccess) {
-        launch_srgb_table(lut, st);
         launch_gradient_prior(rgb, rs, H, W, lut, d_out, d_stride, gmax, st);
         e = cudaGetLastError();
     }

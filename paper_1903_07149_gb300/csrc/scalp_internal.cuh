@@ -117,7 +117,7 @@ struct SolveArgs {
     ClusterDev *cdev;
     ClusterAcc *acc;
     int4 *prev_win;    // window (xlo, xhi, ylo, yhi) the last assignment used
-    float *lut;        // 256-entry inverse sRGB transfer function
+    const float *lut;  // 256-entry inverse sRGB transfer function
     int *proj_list;
     int *tile_count, *tile_off, *tile_cursor, *tile_list;
     long long tile_cap;

@@ -5,6 +5,7 @@
 #include <climits>
 
 #include <algorithm>
+#include <mutex>
 
 #include "scalp_launch.h"
 
@@ -17,14 +18,44 @@ namespace scalp {
 // sums), then the CIE 1976 L*a*b* companding with the linear segment below
 // (6/29)^3.
 // ---------------------------------------------------------------------------
-// Inverse sRGB transfer function for the 256 byte values, in double, once.
+// Inverse sRGB transfer function for the 256 byte values, in double.  It is
+// a constant of the method: built once per device into static device memory
+// (spread over SRGB_TABLE_CTAS CTAs, FP64 being slow on one SM).
+constexpr int SRGB_TABLE_CTAS = 8;
+static __device__ float g_srgb_lut[256];
+
 __global__ void k_srgb_table(float *lut)
 {
-    const int i = threadIdx.x;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < 256) {
         const double c = i / 255.0;
         lut[i] = (float)(c <= 0.04045 ? c / 12.92 : pow((c + 0.055) / 1.055, 2.4));
     }
+}
+
+cudaError_t srgb_table(const float **table, cudaStream_t st)
+{
+    constexpr int MAX_DEVICES = 64;
+    static std::mutex mu;
+    static const float *ready[MAX_DEVICES] = {};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= MAX_DEVICES) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!ready[dev]) {
+        void *p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_srgb_lut);
+        if (e == cudaSuccess) {
+            k_srgb_table<<<SRGB_TABLE_CTAS, 256 / SRGB_TABLE_CTAS, 0, st>>>(static_cast<float *>(p));
+            e = cudaGetLastError();
+        }
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+        if (e != cudaSuccess) return e;
+        ready[dev] = static_cast<const float *>(p);
+    }
+    *table = ready[dev];
+    return cudaSuccess;
 }
 
 __global__ void k_setup(SolveArgs a, const uint8_t *__restrict__ rgb, long long rgb_stride,
@@ -37,7 +68,8 @@ __global__ void k_setup(SolveArgs a, const uint8_t *__restrict__ rgb, long long 
     const float inv_s2 = 1.0f / (a.sigma * a.sigma);
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < a.N;
          p += (long long)gridDim.x * blockDim.x) {
-        int y = (int)(p / a.W), x = (int)(p - (long long)y * a.W);
+        // N <= 2^30: 32-bit division
+        const int y = (int)((unsigned)p / (unsigned)a.W), x = (int)p - y * a.W;
         const float3 lab = srgb_to_lab(lin, rgb + y * rgb_stride + 3 * (long long)x);
         const float L = lab.x, A = lab.y, Bb = lab.z;
         float c = contour ? contour[y * contour_stride + x] : 0.0f;
@@ -59,8 +91,6 @@ __global__ void k_setup(SolveArgs a, const uint8_t *__restrict__ rgb, long long 
     }
 }
 
-void launch_srgb_table(const SolveArgs &a, cudaStream_t st) { k_srgb_table<<<1, 256, 0, st>>>(a.lut); }
-void launch_srgb_table(float *lut, cudaStream_t st) { k_srgb_table<<<1, 256, 0, st>>>(lut); }
 
 // ---------------------------------------------------------------------------
 // Contour prior from the image (Sec. II-E takes any soft prior in [0, 1]):
@@ -72,7 +102,8 @@ void launch_srgb_table(float *lut, cudaStream_t st) { k_srgb_table<<<1, 256, 0, 
 // magnitudes and raises the global maximum (float bits order like the
 // values for g >= 0); a second pass divides by it.
 // ---------------------------------------------------------------------------
-constexpr int PRIOR_TX = 32, PRIOR_TY = 8;
+constexpr int PRIOR_TX = 32, PRIOR_TY = 32;  // pixels per CTA
+constexpr int PRIOR_THREADS = 256;            // PRIOR_TX x 8: four rows per thread
 
 __device__ __forceinline__ float axis_derivative(float fm, float f0, float fp, int i, int n)
 {
@@ -82,19 +113,21 @@ __device__ __forceinline__ float axis_derivative(float fm, float f0, float fp, i
     return (fp - fm) * 0.5f;
 }
 
-__global__ void __launch_bounds__(PRIOR_TX * PRIOR_TY)
+__global__ void __launch_bounds__(PRIOR_THREADS)
     k_prior_gradient(const uint8_t *__restrict__ rgb, long long rgb_stride, int H, int W,
                      const float *__restrict__ lut, float *out, long long out_stride, unsigned *gmax)
 {
+    pdl_wait();  // the table and the cleared maximum
+    pdl_release();
     __shared__ float lin[256];
     __shared__ float s_lab[3][PRIOR_TY + 2][PRIOR_TX + 2];
     __shared__ unsigned s_max;
     const int tid = threadIdx.x;
-    for (int i = tid; i < 256; i += blockDim.x) lin[i] = lut[i];
+    for (int i = tid; i < 256; i += PRIOR_THREADS) lin[i] = lut[i];
     if (tid == 0) s_max = 0u;
     __syncthreads();
     const int x0 = blockIdx.x * PRIOR_TX, y0 = blockIdx.y * PRIOR_TY;
-    for (int i = tid; i < (PRIOR_TX + 2) * (PRIOR_TY + 2); i += blockDim.x) {
+    for (int i = tid; i < (PRIOR_TX + 2) * (PRIOR_TY + 2); i += PRIOR_THREADS) {
         const int hx = i % (PRIOR_TX + 2), hy = i / (PRIOR_TX + 2);
         const int x = min(max(x0 - 1 + hx, 0), W - 1), y = min(max(y0 - 1 + hy, 0), H - 1);
         const float3 lab = srgb_to_lab(lin, rgb + y * rgb_stride + 3 * (long long)x);
@@ -103,48 +136,60 @@ __global__ void __launch_bounds__(PRIOR_TX * PRIOR_TY)
         s_lab[2][hy][hx] = lab.z;
     }
     __syncthreads();
-    const int tx = tid % PRIOR_TX, ty = tid / PRIOR_TX;
-    const int x = x0 + tx, y = y0 + ty;
-    float g = 0.0f;
-    if (x < W && y < H) {
-        float s = 0.0f;
+    const int tx = tid % PRIOR_TX;
+    float gm = 0.0f;
 #pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            const float gx = axis_derivative(s_lab[c][ty + 1][tx], s_lab[c][ty + 1][tx + 1],
-                                             s_lab[c][ty + 1][tx + 2], x, W);
-            const float gy = axis_derivative(s_lab[c][ty][tx + 1], s_lab[c][ty + 1][tx + 1],
-                                             s_lab[c][ty + 2][tx + 1], y, H);
-            s += gx * gx + gy * gy;
+    for (int ty = tid / PRIOR_TX; ty < PRIOR_TY; ty += PRIOR_THREADS / PRIOR_TX) {
+        const int x = x0 + tx, y = y0 + ty;
+        if (x < W && y < H) {
+            float s2 = 0.0f;
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float gx = axis_derivative(s_lab[c][ty + 1][tx], s_lab[c][ty + 1][tx + 1],
+                                                 s_lab[c][ty + 1][tx + 2], x, W);
+                const float gy = axis_derivative(s_lab[c][ty][tx + 1], s_lab[c][ty + 1][tx + 1],
+                                                 s_lab[c][ty + 2][tx + 1], y, H);
+                s2 += gx * gx + gy * gy;
+            }
+            const float g = sqrtf(s2);
+            out[y * out_stride + x] = g;
+            gm = fmaxf(gm, g);
         }
-        g = sqrtf(s);
-        out[y * out_stride + x] = g;
     }
-    const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(g));
+    const unsigned m = __reduce_max_sync(0xffffffffu, __float_as_uint(gm));
     if ((tid & 31) == 0) atomicMax(&s_max, m);
     __syncthreads();
     if (tid == 0) atomicMax(gmax, s_max);
 }
 
-__global__ void k_prior_normalise(float *out, long long out_stride, int H, int W, const unsigned *gmax)
+// The same tiles, four rows per thread.
+__global__ void __launch_bounds__(PRIOR_THREADS)
+    k_prior_normalise(float *out, long long out_stride, int H, int W, const unsigned *gmax)
 {
+    pdl_wait();  // every magnitude and the final maximum
     const float m = __uint_as_float(*gmax);
-    const long long N = (long long)H * W;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
-         p += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(p / W), x = (int)(p - (long long)y * W);
-        float &v = out[y * out_stride + x];
-        v = m > 0.0f ? v / m : 0.0f;
+    const int x = blockIdx.x * PRIOR_TX + threadIdx.x % PRIOR_TX;
+#pragma unroll
+    for (int ty = threadIdx.x / PRIOR_TX; ty < PRIOR_TY; ty += PRIOR_THREADS / PRIOR_TX) {
+        const int y = blockIdx.y * PRIOR_TY + ty;
+        if (x < W && y < H) {
+            float &v = out[y * out_stride + x];
+            v = m > 0.0f ? v / m : 0.0f;
+        }
     }
 }
 
+// The normalisation is a programmatic launch (it waits for the gradient pass
+// before its first read).
 void launch_gradient_prior(const uint8_t *rgb, long long rgb_stride, int H, int W, const float *lut,
                            float *out, long long out_stride, unsigned *gmax, cudaStream_t st)
 {
     cudaMemsetAsync(gmax, 0, sizeof(unsigned), st);
     const dim3 grid((unsigned)ceil_div_ll(W, PRIOR_TX), (unsigned)ceil_div_ll(H, PRIOR_TY));
-    k_prior_gradient<<<grid, PRIOR_TX * PRIOR_TY, 0, st>>>(rgb, rgb_stride, H, W, lut, out, out_stride, gmax);
-    const long long N = (long long)H * W;
-    k_prior_normalise<<<(unsigned)std::min(ceil_div_ll(N, 256), 152LL * 16), 256, 0, st>>>(out, out_stride, H, W, gmax);
+    pdl_launch(false, k_prior_gradient, grid, dim3(PRIOR_THREADS), 0, st, rgb, rgb_stride, H, W, lut,
+               out, out_stride, gmax);
+    pdl_launch(true, k_prior_normalise, grid, dim3(PRIOR_THREADS), 0, st, out, out_stride, H, W,
+               (const unsigned *)gmax);
 }
 
 void launch_setup(const SolveArgs &a, const uint8_t *rgb, long long rgb_stride,
@@ -412,7 +457,8 @@ __device__ __forceinline__ void project_cta(const SolveArgs &a, int whole_image,
             for (int u = 0; u < PROJ_BATCH; ++u) {
                 if (lab[u] != k) continue;
                 const long long p = idx[u];
-                const int y = (int)(p / a.W), x = (int)(p - (long long)y * a.W);
+                const long long r = div.row(base + (long long)u * PROJ_THREADS + tid);
+                const int y = ylo + (int)r, x = xlo + (int)(base + (long long)u * PROJ_THREADS + tid - r * w);
                 const ProjBest c = proj_candidate(p, x, y, n, sx, sy, small);
                 if (proj_less(c, b)) b = c;
             }

@@ -36,9 +36,9 @@ void set_last_error(const char *msg);
 void launch_setup(const SolveArgs &a, const uint8_t *rgb, long long rgb_stride,
                   const float *contour, long long contour_stride, int storage,
                   void *plane, cudaStream_t st);
-// The 256-entry inverse sRGB transfer function (once per context).
-void launch_srgb_table(const SolveArgs &a, cudaStream_t st);
-void launch_srgb_table(float *lut, cudaStream_t st);
+// The 256-entry inverse sRGB transfer function of the current device, built
+// on the first request (which synchronises `st` once) in static device memory.
+cudaError_t srgb_table(const float **table, cudaStream_t st);
 // Contour prior from the image (CIELab gradient magnitude / its maximum) into
 // out (H rows of out_stride floats); lut = the transfer-function table, gmax
 // one word of scratch.  rgb and out are device pointers.

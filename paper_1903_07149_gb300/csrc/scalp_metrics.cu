@@ -30,7 +30,7 @@ __global__ void k_boundary_map(MapPtrs m, int count, int H, int W, float *__rest
     const long long N = (long long)H * W;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
          p += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(p / W), x = (int)(p - (long long)y * W);
+        const int y = (int)((unsigned)p / (unsigned)W), x = (int)p - y * W;  // N <= 2^30
         int hits = 0;
         for (int i = 0; i < count; ++i) {
             const int *__restrict__ l = m.p[i];
@@ -110,7 +110,7 @@ __global__ void k_quality_pixels(const int *__restrict__ lab, const int *__restr
     const int r = (int)ceil(eps);
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
          p += (long long)gridDim.x * blockDim.x) {
-        const int y = (int)(p / W), x = (int)(p - (long long)y * W);
+        const int y = (int)((unsigned)p / (unsigned)W), x = (int)p - y * W;  // N <= 2^30
         const int k = lab[p];
         atomicAdd(&w.ov[(long long)k * n_gt + gt[p]], 1);
         atomicAdd(&w.area[k], 1ull);

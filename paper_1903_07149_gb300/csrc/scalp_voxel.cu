@@ -72,7 +72,7 @@ struct VoxArgs {
     int *proj_list;
     int *tile_count, *tile_off, *tile_cursor, *tile_list;
     DevCounters *ctr;
-    float *lut;
+    const float *lut;
 };
 
 // ---------------------------------------------------------------------------
@@ -621,7 +621,7 @@ size_t vcarve(size_t &cur, size_t bytes)
 
 struct VLayout {
     size_t rgb, contour, plane, labels, st_n, st_sx, st_sy, st_st, st_col, st_end, cdev, acc, prev_win,
-        proj, lut, tile_count, tile_off, tile_cursor, tile_list, ctr, total;
+        proj, tile_count, tile_off, tile_cursor, tile_list, ctr, total;
     long long tile_cap;
     int n_tx, n_ty, n_tt, tpw_x, tpw_y, tpw_t;
 };
@@ -688,7 +688,6 @@ VLayout vmake_layout(int T, int H, int W, int K)
     L.acc = vcarve(cur, sizeof(VoxAcc) * Keff);
     L.prev_win = vcarve(cur, 24 * Keff);
     L.proj = vcarve(cur, 4 * Keff);
-    L.lut = vcarve(cur, 256 * 4);
     L.tile_count = vcarve(cur, 4 * n_tiles);
     L.tile_off = vcarve(cur, 4 * (n_tiles + 1));
     L.tile_cursor = vcarve(cur, 4 * n_tiles);
@@ -830,7 +829,6 @@ int scalp_voxel_init(scalp_vctx **out, const scalp_volume *vol, int32_t K, float
     a.tile_cursor = reinterpret_cast<int *>(c->ws + L.tile_cursor);
     a.tile_list = reinterpret_cast<int *>(c->ws + L.tile_list);
     a.ctr = reinterpret_cast<DevCounters *>(c->ws + L.ctr);
-    a.lut = reinterpret_cast<float *>(c->ws + L.lut);
     const uint8_t *rgb = vol->rgb;
     const float *con = vol->contour;
     const size_t N = (size_t)c->N;
@@ -849,11 +847,11 @@ int scalp_voxel_init(scalp_vctx **out, const scalp_volume *vol, int32_t K, float
     if (!rc) rc = vcheck(cudaMemsetAsync(a.tile_count, 0, 4 * n_tiles, c->st), "memset");
     if (!rc) rc = vcheck(cudaMemsetAsync(a.cdev, 0, sizeof(VoxCluster) * c->Keff, c->st), "memset");
     if (!rc) rc = vcheck(cudaMemsetAsync(a.ctr, 0, sizeof(DevCounters), c->st), "memset");
+    if (!rc) rc = vcheck(srgb_table(&a.lut, c->st), "transfer-function table");
     if (rc) {
         delete c;
         return rc;
     }
-    launch_srgb_table(a.lut, c->st);
     const int blocks = (int)std::min<long long>((c->N + 255) / 256, 152 * 8);
     k_vsetup<<<blocks, 256, 0, c->st>>>(a, rgb, con, params->sigma, reinterpret_cast<float4 *>(c->ws + L.plane));
     k_vaccumulate<<<152 * 8, 256, 0, c->st>>>(a);
