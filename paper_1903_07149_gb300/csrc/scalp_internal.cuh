@@ -333,7 +333,10 @@ __device__ __forceinline__ int path_sums(const T *__restrict__ base, int pitch, 
 __device__ __forceinline__ float scalp_distance(float dcp, float sum_dc, float sum_w, int len,
                                                 float lam, float gamma, float ms2, float ds)
 {
-    float inv = __frcp_rn((float)len);  // correctly rounded, as 1.0f / len
+    // 1 / |P| from the hardware reciprocal (relative error below 2^-22: far
+    // inside the FP32 rounding of the sums); every walker shares this code
+    float inv;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(inv) : "f"((float)len));
     float dcol = lam * dcp + (1.0f - lam) * (sum_dc * inv);
     float dcon = 1.0f + gamma * (sum_w * inv);
     return fmaf(dcol, dcon, ms2 * ds);
