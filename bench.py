@@ -52,7 +52,7 @@ def parse():
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the FP16-storage, batched and serving forms")
     ap.add_argument("--no-serving", action="store_true", help="skip the serving form")
-    ap.add_argument("--only-form", choices=["gradient_prior", "supervoxels", "serving"],
+    ap.add_argument("--only-form", choices=["gradient_prior", "supervoxels", "serving", "batched"],
                     help="diagnostics: run only this form and print its result (not the benchmark line)")
     return ap.parse_args()
 
@@ -815,6 +815,11 @@ def run_form(args):
     elif args.only_form == "serving":
         bws = synth.batch_configs()
         res = measure_serving(args, (bws, *synth.batch_images(bws)))
+    elif args.only_form == "batched":
+        bws = synth.batch_configs()
+        imgs = (bws, *synth.batch_images(bws))
+        res = {st: measure_batch(args, st, flush, imgs) for st in ("f16", "f32")}
+        res["multiscale"] = measure_multiscale(args, flush)
     else:
         w, rgb, con = synth.single_image_config(args.workload)
         _, _, cells = synth.voronoi_image(w.H, w.W, w.n_cells, gradient=w.gradient,

@@ -215,7 +215,10 @@ int scalp_batch_iterate(scalp_batch *b, int32_t n);
 
 /* Labels of every image into outs[i] (H_i*W_i int32, host or device memory per
  * out_on_device), connectivity enforced when enforce != 0; n_labels[i] gets
- * the count.  Synchronises the stream once. */
+ * the count.  Synchronises the stream once.  The per-image work of this call
+ * and of scalp_batch_reload runs on streams of the batch's own, forked from
+ * and joined back to params->stream; host outputs should be pinned for their
+ * copies to overlap. */
 int scalp_batch_labels(scalp_batch *b, int32_t *const *outs, int32_t out_on_device,
                        int32_t enforce, int32_t *n_labels);
 

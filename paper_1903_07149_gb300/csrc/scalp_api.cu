@@ -851,9 +851,49 @@ struct scalp_batch {
     cudaGraphExec_t gexec{};
     bool graph_valid = false;
     int graph_n = 0;
+    // the per-image work of a reload or of the labels (set-up, connectivity,
+    // copies) fans out over BATCH_STREAMS streams: images are independent, and
+    // their small kernels would otherwise run one after another
+    static constexpr int BATCH_STREAMS = 8;
+    cudaStream_t sub[BATCH_STREAMS] = {};
+    cudaEvent_t fork = nullptr, join[BATCH_STREAMS] = {};
 };
 
 namespace {
+
+// Runs per_image(i) for every image with the image's context bound to one of
+// the batch's streams; the batch stream forks to them and joins them after.
+template <typename F>
+cudaError_t batch_fan_out(scalp_batch *b, F &&per_image)
+{
+    cudaError_t e = cudaSuccess;
+    if (!b->fork) {
+        e = cudaEventCreateWithFlags(&b->fork, cudaEventDisableTiming);
+        for (int s = 0; s < scalp_batch::BATCH_STREAMS && e == cudaSuccess; ++s) {
+            e = cudaStreamCreateWithFlags(&b->sub[s], cudaStreamNonBlocking);
+            if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join[s], cudaEventDisableTiming);
+        }
+        if (e != cudaSuccess) return e;
+    }
+    const int n_sub = std::min(b->count, scalp_batch::BATCH_STREAMS);
+    e = cudaEventRecord(b->fork, b->st);
+    for (int s = 0; s < n_sub && e == cudaSuccess; ++s) e = cudaStreamWaitEvent(b->sub[s], b->fork, 0);
+    int rc = SCALP_OK;
+    for (int i = 0; i < b->count && e == cudaSuccess && rc == SCALP_OK; ++i) {
+        scalp_ctx *c = b->ctx[i];
+        c->st = b->sub[i % n_sub];
+        rc = per_image(i);
+        c->st = b->st;
+    }
+    // join whatever was enqueued, also after a failure
+    for (int s = 0; s < n_sub; ++s) {
+        const cudaError_t r = cudaEventRecord(b->join[s], b->sub[s]);
+        const cudaError_t w = r == cudaSuccess ? cudaStreamWaitEvent(b->st, b->join[s], 0) : r;
+        if (e == cudaSuccess) e = w;
+    }
+    if (e == cudaSuccess && rc != SCALP_OK) e = cudaErrorUnknown;
+    return e;
+}
 
 size_t batch_head_bytes(int count)
 {
@@ -896,6 +936,14 @@ void scalp_batch_destroy(scalp_batch *b)
 {
     if (!b) return;
     cudaStreamSynchronize(b->st);
+    for (int s = 0; s < scalp_batch::BATCH_STREAMS; ++s) {
+        if (b->sub[s]) {
+            cudaStreamSynchronize(b->sub[s]);
+            cudaStreamDestroy(b->sub[s]);
+        }
+        if (b->join[s]) cudaEventDestroy(b->join[s]);
+    }
+    if (b->fork) cudaEventDestroy(b->fork);
     if (b->graph_valid) cudaGraphExecDestroy(b->gexec);
     for (scalp_ctx *c : b->ctx) scalp_destroy(c);
     delete b;
@@ -991,10 +1039,17 @@ int scalp_batch_init(scalp_batch **out, int32_t count, const scalp_image *images
 int scalp_batch_reload(scalp_batch *b, const scalp_image *images, const scalp_contour *contours)
 {
     if (!b || !images) return batch_fail(SCALP_E_ARG, "batch or images is NULL");
-    for (int i = 0; i < b->count; ++i) {
+    int bad = -1, bad_rc = SCALP_OK;
+    const cudaError_t e = batch_fan_out(b, [&](int i) {
         const int rc = scalp_reload(b->ctx[i], &images[i], contours ? &contours[i] : nullptr);
-        if (rc != SCALP_OK) return batch_fail(rc, "image %d: %s", i, b->ctx[i]->err.c_str());
-    }
+        if (rc != SCALP_OK) {
+            bad = i;
+            bad_rc = rc;
+        }
+        return rc;
+    });
+    if (bad >= 0) return batch_fail(bad_rc, "image %d: %s", bad, b->ctx[bad]->err.c_str());
+    if (e != cudaSuccess) return batch_fail(SCALP_E_CUDA, "batch reload: %s", cudaGetErrorString(e));
     return SCALP_OK;
 }
 
@@ -1052,26 +1107,30 @@ int scalp_batch_labels(scalp_batch *b, int32_t *const *outs, int32_t out_on_devi
         if (!outs[i]) return batch_fail(SCALP_E_ARG, "outs[%d] is NULL", i);
     int *d_nlab = b->d_gather;
     DevCounters *d_ctr = reinterpret_cast<DevCounters *>(b->d_gather + b->count);
-    cudaError_t e = cudaSuccess;
-    for (int i = 0; i < b->count && e == cudaSuccess; ++i) {
+    cudaError_t ce = cudaSuccess;
+    cudaError_t e = batch_fan_out(b, [&](int i) {
         scalp_ctx *c = b->ctx[i];
         const size_t bytes = sizeof(int) * (size_t)c->N;
+        cudaError_t r = cudaSuccess;
         if (enforce) {
             int *dst = out_on_device ? outs[i] : c->ccl.link;
             int *c_nlab = reinterpret_cast<int *>(c->ws + c->L.nlab);
-            launch_ccl(c->a.labels, c->H, c->W, c->K, dst, c->ccl, c_nlab, c->a.ctr, b->st);
-            e = cudaGetLastError();
-            if (e == cudaSuccess && !out_on_device)
-                e = cudaMemcpyAsync(outs[i], dst, bytes, cudaMemcpyDeviceToHost, b->st);
-            if (e == cudaSuccess)
-                e = cudaMemcpyAsync(d_nlab + i, c_nlab, sizeof(int), cudaMemcpyDeviceToDevice, b->st);
+            launch_ccl(c->a.labels, c->H, c->W, c->K, dst, c->ccl, c_nlab, c->a.ctr, c->st);
+            r = cudaGetLastError();
+            if (r == cudaSuccess && !out_on_device)
+                r = cudaMemcpyAsync(outs[i], dst, bytes, cudaMemcpyDeviceToHost, c->st);
+            if (r == cudaSuccess)
+                r = cudaMemcpyAsync(d_nlab + i, c_nlab, sizeof(int), cudaMemcpyDeviceToDevice, c->st);
         } else {
-            e = cudaMemcpyAsync(outs[i], c->a.labels, bytes,
-                                out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, b->st);
+            r = cudaMemcpyAsync(outs[i], c->a.labels, bytes,
+                                out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st);
         }
-        if (e == cudaSuccess)
-            e = cudaMemcpyAsync(d_ctr + i, c->a.ctr, sizeof(DevCounters), cudaMemcpyDeviceToDevice, b->st);
-    }
+        if (r == cudaSuccess)
+            r = cudaMemcpyAsync(d_ctr + i, c->a.ctr, sizeof(DevCounters), cudaMemcpyDeviceToDevice, c->st);
+        ce = r;
+        return r == cudaSuccess ? SCALP_OK : SCALP_E_CUDA;
+    });
+    if (ce != cudaSuccess) e = ce;
     if (e != cudaSuccess) return batch_fail(SCALP_E_CUDA, "batch labels: %s", cudaGetErrorString(e));
     std::vector<int> nlab(b->count);
     std::vector<DevCounters> ctr(b->count);
