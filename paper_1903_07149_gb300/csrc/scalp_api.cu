@@ -775,6 +775,7 @@ int scalp_gradient_prior(const scalp_image *image, float *out, int64_t out_strid
 namespace scalp {
 
 SolveArgs scalp_ctx_args(const scalp_ctx *c) { return c->a; }
+void scalp_ctx_set_stream(scalp_ctx *c, cudaStream_t st) { c->st = st; }
 size_t scalp_ctx_smem(const scalp_ctx *c) { return c->smem; }
 void scalp_ctx_count_iteration(scalp_ctx *c) { c->iterations += 1; }
 

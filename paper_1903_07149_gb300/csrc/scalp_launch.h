@@ -85,6 +85,7 @@ void launch_ccl(const int *labels, int H, int W, int K, int *out, const CclBuffe
 
 // Per-context accessors used by the serving loop.
 SolveArgs scalp_ctx_args(const scalp_ctx *c);
+void scalp_ctx_set_stream(scalp_ctx *c, cudaStream_t st);  // where its own work goes
 size_t scalp_ctx_smem(const scalp_ctx *c);
 void scalp_ctx_count_iteration(scalp_ctx *c);
 // status of a delivered solve, copied to pinned host memory behind its labels

@@ -14,6 +14,10 @@
 // blocks live in a ring of ARG_RING device blocks, each staged from pinned
 // host memory and reused only after the event behind the last step that read
 // it; a delivered solve's status arrives in pinned memory with its labels.
+// A request's own work runs beside the steps, on SIDE_STREAMS streams of the
+// server: its set-up (the step that first includes it waits for its `ready`
+// event) and its retirement (forked from the step stream after its last step;
+// later steps do not read it, so they need not wait).
 #include <algorithm>
 #include <cstdarg>
 #include <cstdio>
@@ -30,7 +34,8 @@ using namespace scalp;
 namespace {
 
 constexpr size_t SALIGN = 256;
-constexpr int ARG_RING = 8;  // argument blocks in flight
+constexpr int ARG_RING = 8;      // argument blocks in flight
+constexpr int SIDE_STREAMS = 4;  // for the requests' set-up and retirement
 
 size_t salign(size_t x) { return (x + SALIGN - 1) & ~(SALIGN - 1); }
 
@@ -42,7 +47,9 @@ struct Solve {
     int enforce = 1;
     int32_t *labels_out = nullptr;
     cudaEvent_t done = nullptr;
-    int status_slot = -1;  // its entry in the pinned status array
+    cudaEvent_t ready = nullptr;  // its set-up has run
+    int status_slot = -1;         // its entry in the pinned status array
+    bool joined = false;          // the step stream has waited for `ready`
     bool retired = false;
 };
 
@@ -89,6 +96,9 @@ struct scalp_server {
     cudaEvent_t ring_ev[ARG_RING] = {};
     bool ring_live[ARG_RING] = {};
     int ring_next = 0, ring_cur = 0;
+    cudaStream_t side[SIDE_STREAMS] = {};
+    cudaEvent_t step_ev = nullptr;  // the step stream's position, for forks
+    int side_next = 0;
 };
 
 namespace {
@@ -176,8 +186,27 @@ int rebuild_args(scalp_server *s, std::vector<Solve *> &running)
     return SCALP_OK;
 }
 
+cudaError_t spare_event(scalp_server *s, cudaEvent_t &ev)
+{
+    if (s->spare_events.empty()) {
+        cudaEvent_t e;
+        const cudaError_t r = cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        if (r != cudaSuccess) return r;
+        s->spare_events.push_back(e);
+    }
+    ev = s->spare_events.back();
+    s->spare_events.pop_back();
+    return cudaSuccess;
+}
+
 void free_host(scalp_server *s)
 {
+    for (cudaStream_t t : s->side)
+        if (t) {
+            cudaStreamSynchronize(t);
+            cudaStreamDestroy(t);
+        }
+    if (s->step_ev) cudaEventDestroy(s->step_ev);
     for (cudaEvent_t e : s->ring_ev)
         if (e) cudaEventDestroy(e);
     if (s->stage) cudaFreeHost(s->stage);
@@ -220,6 +249,9 @@ int scalp_server_create(scalp_server **out, void *pool, size_t pool_bytes, int32
                           cudaHostAllocDefault);
     for (int i = 0; i < ARG_RING && e == cudaSuccess; ++i)
         e = cudaEventCreateWithFlags(&s->ring_ev[i], cudaEventDisableTiming);
+    for (int i = 0; i < SIDE_STREAMS && e == cudaSuccess; ++i)
+        e = cudaStreamCreateWithFlags(&s->side[i], cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->step_ev, cudaEventDisableTiming);
     if (e != cudaSuccess) {
         free_host(s);
         return server_fail(SCALP_E_CUDA, "server setup: %s", cudaGetErrorString(e));
@@ -246,27 +278,30 @@ int scalp_server_submit(scalp_server *s, const scalp_image *image, const scalp_c
         pool_free(s, off, bytes);
         return server_fail(SCALP_E_NOMEM, "host allocation failed");
     }
+    // the region's previous owner was delivered, so no enqueued work uses it:
+    // the set-up runs on a side stream right away
     scalp_params p = s->params;
     p.workspace = s->pool + off;
     p.workspace_bytes = bytes;
+    cudaStream_t side = s->side[s->side_next++ % SIDE_STREAMS];
+    p.stream = side;
     int rc = scalp_init(&v->ctx, image, contour, K, m, &p);
     if (rc != SCALP_OK) {
         pool_free(s, off, bytes);
         delete v;
         return rc;
     }
-    if (s->spare_events.empty()) {
-        cudaEvent_t e;
-        if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
-            scalp_destroy(v->ctx);
-            pool_free(s, off, bytes);
-            delete v;
-            return server_fail(SCALP_E_CUDA, "event creation failed");
-        }
-        s->spare_events.push_back(e);
+    cudaError_t e = spare_event(s, v->done);
+    if (e == cudaSuccess) e = spare_event(s, v->ready);
+    if (e == cudaSuccess) e = cudaEventRecord(v->ready, side);
+    if (e != cudaSuccess) {
+        scalp_destroy(v->ctx);
+        if (v->done) s->spare_events.push_back(v->done);
+        if (v->ready) s->spare_events.push_back(v->ready);
+        pool_free(s, off, bytes);
+        delete v;
+        return server_fail(SCALP_E_CUDA, "request set-up: %s", cudaGetErrorString(e));
     }
-    v->done = s->spare_events.back();
-    s->spare_events.pop_back();
     v->status_slot = s->free_status.back();
     s->free_status.pop_back();
     v->id = s->next_id++;
@@ -293,6 +328,12 @@ int scalp_server_step(scalp_server *s, int32_t *n_running)
             const int rc = rebuild_args(s, running);
             if (rc) return rc;
         }
+        for (Solve *v : running) {  // new requests: their set-up first
+            if (v->joined) continue;
+            const cudaError_t w = cudaStreamWaitEvent(s->st, v->ready, 0);
+            if (w != cudaSuccess) return server_fail(SCALP_E_CUDA, "join: %s", cudaGetErrorString(w));
+            v->joined = true;
+        }
         launch_assign_batch(s->bargs, s->params.storage, s->total_tiles, s->smem, s->st, true);
         launch_batch_update(s->bargs, s->total_clusters, s->total_fill, s->st, true);
         cudaError_t e = cudaGetLastError();
@@ -304,12 +345,25 @@ int scalp_server_step(scalp_server *s, int32_t *n_running)
             scalp_ctx_count_iteration(v->ctx);
         }
     }
-    // retire the solves whose iterations are done
+    // retire the solves whose iterations are done: connectivity and copies on
+    // a side stream, after the steps so far (and the set-up, for a request
+    // that never ran one)
+    bool forked = false;
     for (Solve *v : s->active) {
         if (v->retired || v->iters_left > 0) continue;
+        cudaError_t e = cudaSuccess;
+        if (!forked) {
+            e = cudaEventRecord(s->step_ev, s->st);
+            forked = true;
+        }
+        cudaStream_t side = s->side[s->side_next++ % SIDE_STREAMS];
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side, s->step_ev, 0);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(side, v->ready, 0);
+        if (e != cudaSuccess) return server_fail(SCALP_E_CUDA, "retire: %s", cudaGetErrorString(e));
+        scalp_ctx_set_stream(v->ctx, side);
         const int rc = scalp_ctx_enqueue_labels(v->ctx, v->labels_out, v->enforce, &s->status[v->status_slot]);
         if (rc) return rc;
-        const cudaError_t e = cudaEventRecord(v->done, s->st);
+        e = cudaEventRecord(v->done, side);
         if (e != cudaSuccess) return server_fail(SCALP_E_CUDA, "record: %s", cudaGetErrorString(e));
         v->retired = true;
         s->args_dirty = true;
@@ -339,6 +393,7 @@ int scalp_server_poll(scalp_server *s, uint64_t id, int32_t *done, int32_t *n_la
     scalp_ctx_release(v->ctx);
     pool_free(s, v->off, v->bytes);
     s->free_status.push_back(v->status_slot);
+    s->spare_events.push_back(v->ready);
     s->spare_events.push_back(v->done);
     s->active.erase(std::find(s->active.begin(), s->active.end(), v));
     s->by_id.erase(it);
@@ -362,9 +417,12 @@ void scalp_server_destroy(scalp_server *s)
 {
     if (!s) return;
     cudaStreamSynchronize(s->st);
+    for (cudaStream_t t : s->side)  // retirements still in flight
+        if (t) cudaStreamSynchronize(t);
     for (Solve *v : s->active) {
         scalp_ctx_release(v->ctx);
         cudaEventDestroy(v->done);
+        cudaEventDestroy(v->ready);
         delete v;
     }
     for (cudaEvent_t e : s->spare_events) cudaEventDestroy(e);
