@@ -168,11 +168,14 @@ def test_one_step_parity(S, variant, t):
     seg.close()
 
 
-@pytest.mark.parametrize("H,W,K", [(200, 300, 150), (240, 320, 6)])
+@pytest.mark.parametrize("H,W,K", [(200, 300, 150), (240, 320, 6), (6, 131072, 2)])
 def test_maps_equal_plane_walk(S, H, W, K):
     """Paths walked on the shared-memory distance maps and on the plane in
     global memory give bit-identical labels.  With K = 6 (r = 113) some map
-    boxes overflow the map buffer, so one launch mixes both walks."""
+    boxes overflow the map buffer, so one launch mixes both walks.  On a
+    6 x 131072 strip with K = 2 (r = 627) the boxes are at most 6 rows high
+    and fit, while paths reach ~600 steps: map walks beyond 512 steps take
+    the error-term steps instead of the fixed-point ones."""
     rgb, con, _ = synth.small_image(H, W, seed=4)
     a = make_seg(S, rgb, con, K)
     b = make_seg(S, rgb, con, K, global_walk=True)
