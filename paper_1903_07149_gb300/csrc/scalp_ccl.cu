@@ -91,38 +91,61 @@ __device__ __forceinline__ void unite_local(int *sp, int a, int b)
     } while (!done);
 }
 
-__global__ void __launch_bounds__(CCL_TILE * CCL_TILE)
+// 256 threads: each warp takes four rows of the tile (all loads first), so
+// eight tiles of an SM are in flight.  size[] is cleared at local roots only:
+// a component's seed is the local root of its tile part, and no other entry
+// of size[] is read.
+constexpr int CCL_LOCAL_THREADS = 256;
+constexpr int CCL_ROWS = CCL_TILE / (CCL_LOCAL_THREADS / 32);  // rows per warp
+
+__global__ void __launch_bounds__(CCL_LOCAL_THREADS)
     k_ccl_local(const int *__restrict__ labels, int *parent, int *size, int H, int W, int n_tx)
 {
     __shared__ int sp[CCL_TILE * CCL_TILE];
     __shared__ int sl[CCL_TILE * CCL_TILE];
     __shared__ unsigned srun[CCL_TILE];  // per row: bit x set where a run starts
-    const int t = threadIdx.x;
-    const int lx = t % CCL_TILE, ly = t / CCL_TILE;  // one warp per tile row
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int x0 = (blockIdx.x % n_tx) * CCL_TILE, y0 = (blockIdx.x / n_tx) * CCL_TILE;
-    const int x = x0 + lx, y = y0 + ly;
-    const bool valid = x < W && y < H;
-    const long long p = (long long)y * W + x;
-    const int lab = valid ? labels[p] : 0;
-    sl[t] = lab;
-    // runs of equal label along the row: each pixel's head is the last run
+    const int x = x0 + lane;
+    int lab[CCL_ROWS];
+    bool valid[CCL_ROWS];
+#pragma unroll
+    for (int r = 0; r < CCL_ROWS; ++r) {
+        const int y = y0 + warp + r * (CCL_LOCAL_THREADS / 32);
+        valid[r] = x < W && y < H;
+        lab[r] = valid[r] ? labels[(long long)y * W + x] : 0;
+    }
+    // runs of equal label along each row: a pixel's head is the last run
     // start at or before it
-    const int left = __shfl_up_sync(0xffffffffu, lab, 1);
-    const unsigned starts = __ballot_sync(0xffffffffu, lx == 0 || !valid || left != lab);
-    const int head = 31 - __clz(starts & (0xffffffffu >> (31 - lx)));
-    sp[t] = ly * CCL_TILE + head;
-    if (lx == 0) srun[ly] = starts;
+#pragma unroll
+    for (int r = 0; r < CCL_ROWS; ++r) {
+        const int ly = warp + r * (CCL_LOCAL_THREADS / 32), t = ly * CCL_TILE + lane;
+        sl[t] = lab[r];
+        const int left = __shfl_up_sync(0xffffffffu, lab[r], 1);
+        const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || !valid[r] || left != lab[r]);
+        const int head = 31 - __clz(starts & (0xffffffffu >> (31 - lane)));
+        sp[t] = ly * CCL_TILE + head;
+        if (lane == 0) srun[ly] = starts;
+    }
     __syncthreads();
     // one union per pair of vertically touching runs: at the first pixel of
     // their overlap, where this pixel or the one above starts a run
-    if (valid && ly > 0 && sl[t - CCL_TILE] == lab &&
-        (((starts >> lx) & 1u) || ((srun[ly - 1] >> lx) & 1u)))
-        unite_local(sp, t, t - CCL_TILE);
+#pragma unroll
+    for (int r = 0; r < CCL_ROWS; ++r) {
+        const int ly = warp + r * (CCL_LOCAL_THREADS / 32), t = ly * CCL_TILE + lane;
+        if (valid[r] && ly > 0 && sl[t - CCL_TILE] == lab[r] &&
+            (((srun[ly] >> lane) & 1u) || ((srun[ly - 1] >> lane) & 1u)))
+            unite_local(sp, t, t - CCL_TILE);
+    }
     __syncthreads();
-    if (valid) {
-        const int r = find_local(sp, t);
-        parent[p] = (int)((long long)(y0 + r / CCL_TILE) * W + x0 + r % CCL_TILE);
-        size[p] = 0;
+#pragma unroll
+    for (int r = 0; r < CCL_ROWS; ++r) {
+        const int ly = warp + r * (CCL_LOCAL_THREADS / 32), t = ly * CCL_TILE + lane;
+        if (!valid[r]) continue;
+        const long long p = (long long)(y0 + ly) * W + x;
+        const int root = find_local(sp, t);
+        parent[p] = (int)((long long)(y0 + root / CCL_TILE) * W + x0 + root % CCL_TILE);
+        if (root == t) size[p] = 0;
     }
 }
 
@@ -179,7 +202,7 @@ __global__ void k_ccl_link(const int *__restrict__ parent, const int *__restrict
          s += (long long)gridDim.x * blockDim.x) {
         if (parent[s] != s) continue;
         bool small = size[s] <= T && s != 0;
-        long long nb = (s % W) > 0 ? s - 1 : s - W;
+        long long nb = ((int)s % W) > 0 ? s - 1 : s - W;  // N <= 2^30
         link[s] = small ? parent[nb] : (int)s;
     }
 }
@@ -208,11 +231,16 @@ __global__ void __launch_bounds__(CCL_CHUNK_THREADS)
                         long long N, DevCounters *ctr, int *chunk_count)
 {
     __shared__ int s_warp[32];
-    const long long base = blockIdx.x * (long long)CCL_CHUNK;
+    // CCL_PER consecutive pixels per thread, their parents loaded first
+    const long long base = blockIdx.x * (long long)CCL_CHUNK + (long long)threadIdx.x * CCL_PER;
+    int par[CCL_PER];
+#pragma unroll
+    for (int i = 0; i < CCL_PER; ++i) par[i] = base + i < N ? parent[base + i] : -1;
     int cnt = 0;
-    for (int i = threadIdx.x; i < CCL_CHUNK; i += CCL_CHUNK_THREADS) {
+#pragma unroll
+    for (int i = 0; i < CCL_PER; ++i) {
         const long long s = base + i;
-        if (s >= N || parent[s] != s) continue;
+        if (par[i] != s) continue;
         int f = (int)s;
         long long guard = 0;
         while (true) {
@@ -325,7 +353,7 @@ void launch_ccl(const int *labels, int H, int W, int K, int *out, const CclBuffe
     const long long T = N / (4LL * K);
     const int blocks = (int)std::min<long long>(ceil_div_ll(N, CCL_THREADS), 152 * 16);
     const int n_tx = (W + CCL_TILE - 1) / CCL_TILE, n_ty = (H + CCL_TILE - 1) / CCL_TILE;
-    k_ccl_local<<<n_tx * n_ty, CCL_TILE * CCL_TILE, 0, st>>>(labels, b.parent, b.size, H, W, n_tx);
+    k_ccl_local<<<n_tx * n_ty, CCL_LOCAL_THREADS, 0, st>>>(labels, b.parent, b.size, H, W, n_tx);
     const long long nb = (long long)(n_tx - 1) * H + (long long)(n_ty - 1) * W;
     if (nb > 0)
         k_ccl_border<<<(int)std::min<long long>(ceil_div_ll(nb, CCL_THREADS), 152 * 16), CCL_THREADS, 0,
