@@ -101,6 +101,8 @@ constexpr int CCL_ROWS = CCL_TILE / (CCL_LOCAL_THREADS / 32);  // rows per warp
 __global__ void __launch_bounds__(CCL_LOCAL_THREADS)
     k_ccl_local(const int *__restrict__ labels, int *parent, int *size, int H, int W, int n_tx)
 {
+    pdl_wait();  // the previous pass (or the labels) complete
+    pdl_release();
     __shared__ int sp[CCL_TILE * CCL_TILE];
     __shared__ int sl[CCL_TILE * CCL_TILE];
     __shared__ unsigned srun[CCL_TILE];  // per row: bit x set where a run starts
@@ -153,6 +155,8 @@ __global__ void __launch_bounds__(CCL_LOCAL_THREADS)
 __global__ void k_ccl_border(const int *__restrict__ labels, int *parent, int H, int W, int n_tx,
                              int n_ty)
 {
+    pdl_wait();  // the previous pass (or the labels) complete
+    pdl_release();
     const long long nv = (long long)(n_tx - 1) * H;  // vertical border pixels
     const long long nh = (long long)(n_ty - 1) * W;  // horizontal border pixels
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nv + nh;
@@ -176,6 +180,8 @@ __global__ void k_ccl_border(const int *__restrict__ labels, int *parent, int H,
 // of them in one component) add their counts once per distinct root.
 __global__ void k_ccl_flatten_count(int *parent, int *size, long long N)
 {
+    pdl_wait();  // the previous pass (or the labels) complete
+    pdl_release();
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (blockDim.x / 32);
     for (long long w = blockIdx.x * (long long)(blockDim.x / 32) + (threadIdx.x >> 5); w * 32 < N;
@@ -198,6 +204,8 @@ __global__ void k_ccl_flatten_count(int *parent, int *size, long long N)
 __global__ void k_ccl_link(const int *__restrict__ parent, const int *__restrict__ size, int *link,
                            int W, long long N, long long T)
 {
+    pdl_wait();  // the previous pass (or the labels) complete
+    pdl_release();
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
          s += (long long)gridDim.x * blockDim.x) {
         if (parent[s] != s) continue;
@@ -230,6 +238,8 @@ __global__ void __launch_bounds__(CCL_CHUNK_THREADS)
     k_ccl_resolve_count(const int *__restrict__ parent, const int *__restrict__ link, int *final_id,
                         long long N, DevCounters *ctr, int *chunk_count)
 {
+    pdl_wait();  // the previous pass (or the labels) complete
+    pdl_release();
     __shared__ int s_warp[32];
     // CCL_PER consecutive pixels per thread, their parents loaded first
     const long long base = blockIdx.x * (long long)CCL_CHUNK + (long long)threadIdx.x * CCL_PER;
@@ -265,6 +275,8 @@ constexpr int CCL_SCAN_THREADS = 1024;
 
 __global__ void __launch_bounds__(CCL_SCAN_THREADS) k_ccl_chunk_scan(int *counts, long long n, int *total)
 {
+    pdl_wait();  // the previous pass (or the labels) complete
+    pdl_release();
     __shared__ int s_warp[32];
     const long long per = (n + CCL_SCAN_THREADS - 1) / CCL_SCAN_THREADS;
     const long long b = threadIdx.x * per, e = min(n, b + per);
@@ -302,6 +314,8 @@ __global__ void __launch_bounds__(CCL_CHUNK_THREADS)
     k_ccl_number(const int *__restrict__ parent, const int *__restrict__ final_id,
                  const int *__restrict__ chunk_off, int *number, long long N)
 {
+    pdl_wait();  // the previous pass (or the labels) complete
+    pdl_release();
     __shared__ int s_warp[32];
     const long long base = blockIdx.x * (long long)CCL_CHUNK + (long long)threadIdx.x * CCL_PER;
     unsigned flags = 0;
@@ -339,6 +353,8 @@ __global__ void __launch_bounds__(CCL_CHUNK_THREADS)
 __global__ void k_ccl_out(const int *__restrict__ parent, const int *__restrict__ final_id,
                           const int *__restrict__ number, int *out, long long N)
 {
+    pdl_wait();  // the previous pass (or the labels) complete
+    pdl_release();
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
          p += (long long)gridDim.x * blockDim.x)
         out[p] = number[final_id[parent[p]]];
@@ -353,19 +369,25 @@ void launch_ccl(const int *labels, int H, int W, int K, int *out, const CclBuffe
     const long long T = N / (4LL * K);
     const int blocks = (int)std::min<long long>(ceil_div_ll(N, CCL_THREADS), 152 * 16);
     const int n_tx = (W + CCL_TILE - 1) / CCL_TILE, n_ty = (H + CCL_TILE - 1) / CCL_TILE;
-    k_ccl_local<<<n_tx * n_ty, CCL_LOCAL_THREADS, 0, st>>>(labels, b.parent, b.size, H, W, n_tx);
+    // eight passes, each a programmatic launch: its CTAs are placed while the
+    // previous pass drains and wait for it before their first read
+    pdl_launch(true, k_ccl_local, dim3(n_tx * n_ty), dim3(CCL_LOCAL_THREADS), 0, st, labels, b.parent, b.size,
+               H, W, n_tx);
     const long long nb = (long long)(n_tx - 1) * H + (long long)(n_ty - 1) * W;
     if (nb > 0)
-        k_ccl_border<<<(int)std::min<long long>(ceil_div_ll(nb, CCL_THREADS), 152 * 16), CCL_THREADS, 0,
-                       st>>>(labels, b.parent, H, W, n_tx, n_ty);
-    k_ccl_flatten_count<<<blocks, CCL_THREADS, 0, st>>>(b.parent, b.size, N);
-    k_ccl_link<<<blocks, CCL_THREADS, 0, st>>>(b.parent, b.size, b.link, W, N, T);
+        pdl_launch(true, k_ccl_border, dim3((unsigned)std::min<long long>(ceil_div_ll(nb, CCL_THREADS), 152 * 16)),
+                   dim3(CCL_THREADS), 0, st, labels, b.parent, H, W, n_tx, n_ty);
+    pdl_launch(true, k_ccl_flatten_count, dim3(blocks), dim3(CCL_THREADS), 0, st, b.parent, b.size, N);
+    pdl_launch(true, k_ccl_link, dim3(blocks), dim3(CCL_THREADS), 0, st, (const int *)b.parent,
+               (const int *)b.size, b.link, W, N, T);
     const long long chunks = ceil_div_ll(N, CCL_CHUNK);
-    k_ccl_resolve_count<<<(unsigned)chunks, CCL_CHUNK_THREADS, 0, st>>>(b.parent, b.link, b.size, N, ctr,
-                                                                        b.scan_tmp);
-    k_ccl_chunk_scan<<<1, CCL_SCAN_THREADS, 0, st>>>(b.scan_tmp, chunks, d_nlab);
-    k_ccl_number<<<(unsigned)chunks, CCL_CHUNK_THREADS, 0, st>>>(b.parent, b.size, b.scan_tmp, b.scan, N);
-    k_ccl_out<<<blocks, CCL_THREADS, 0, st>>>(b.parent, b.size, b.scan, out, N);
+    pdl_launch(true, k_ccl_resolve_count, dim3((unsigned)chunks), dim3(CCL_CHUNK_THREADS), 0, st,
+               (const int *)b.parent, (const int *)b.link, b.size, N, ctr, b.scan_tmp);
+    pdl_launch(true, k_ccl_chunk_scan, dim3(1), dim3(CCL_SCAN_THREADS), 0, st, b.scan_tmp, chunks, d_nlab);
+    pdl_launch(true, k_ccl_number, dim3((unsigned)chunks), dim3(CCL_CHUNK_THREADS), 0, st, (const int *)b.parent,
+               (const int *)b.size, (const int *)b.scan_tmp, b.scan, N);
+    pdl_launch(true, k_ccl_out, dim3(blocks), dim3(CCL_THREADS), 0, st, (const int *)b.parent,
+               (const int *)b.size, (const int *)b.scan, out, N);
 }
 
 }  // namespace scalp
