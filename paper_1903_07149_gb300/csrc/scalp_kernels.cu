@@ -62,6 +62,7 @@ __global__ void k_setup(SolveArgs a, const uint8_t *__restrict__ rgb, long long 
                         const float *__restrict__ contour, long long contour_stride, int storage,
                         void *plane)
 {
+    pdl_release();  // launched after memsets: nothing to wait for
     __shared__ float lin[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) lin[i] = a.lut[i];
     __syncthreads();
@@ -206,6 +207,8 @@ void launch_setup(const SolveArgs &a, const uint8_t *rgb, long long rgb_stride,
 template <typename T>
 __global__ void __launch_bounds__(256) k_accumulate(SolveArgs a, const T *__restrict__ plane)
 {
+    pdl_wait();  // the plane and the grid labels
+    pdl_release();
     const long long segs_per_row = (a.W + 31) / 32;
     const long long n_segs = segs_per_row * a.H;
     const long long warps = (long long)gridDim.x * (blockDim.x / 32);
@@ -224,11 +227,11 @@ __global__ void __launch_bounds__(256) k_accumulate(SolveArgs a, const T *__rest
     }
 }
 
-void launch_accumulate(const SolveArgs &a, cudaStream_t st)
+void launch_accumulate(const SolveArgs &a, cudaStream_t st, bool pdl)
 {
     const int blocks = (int)std::min<long long>(ceil_div_ll(a.N, 256), 152 * 16);
-    if (a.plane32) k_accumulate<float4><<<blocks, 256, 0, st>>>(a, a.plane32);
-    else k_accumulate<uint2><<<blocks, 256, 0, st>>>(a, a.plane16);
+    if (a.plane32) pdl_launch(pdl, k_accumulate<float4>, dim3(blocks), dim3(256), 0, st, a, a.plane32);
+    else pdl_launch(pdl, k_accumulate<uint2>, dim3(blocks), dim3(256), 0, st, a, a.plane16);
 }
 
 // ---------------------------------------------------------------------------

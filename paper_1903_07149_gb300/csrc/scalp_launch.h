@@ -46,7 +46,7 @@ void launch_gradient_prior(const uint8_t *rgb, long long rgb_stride, int H, int 
                            float *out, long long out_stride, unsigned *gmax, cudaStream_t st);
 // Integer sums of (1, x, y, L, a, b) by label into a.acc (initialisation and
 // every update).
-void launch_accumulate(const SolveArgs &a, cudaStream_t st);
+void launch_accumulate(const SolveArgs &a, cudaStream_t st, bool pdl = false);
 // Cluster update (Algorithm 1) from a.acc when from_acc (queueing projections,
 // Eq. 4), then windows, the cluster records and the tile counts.  The tile
 // counts and list cursors must be zero on entry.
