@@ -119,6 +119,7 @@ __global__ void __launch_bounds__(CCL_LOCAL_THREADS)
     }
     // runs of equal label along each row: a pixel's head is the last run
     // start at or before it
+    bool is_head[CCL_ROWS];
 #pragma unroll
     for (int r = 0; r < CCL_ROWS; ++r) {
         const int ly = warp + r * (CCL_LOCAL_THREADS / 32), t = ly * CCL_TILE + lane;
@@ -127,6 +128,7 @@ __global__ void __launch_bounds__(CCL_LOCAL_THREADS)
         const unsigned starts = __ballot_sync(0xffffffffu, lane == 0 || !valid[r] || left != lab[r]);
         const int head = 31 - __clz(starts & (0xffffffffu >> (31 - lane)));
         sp[t] = ly * CCL_TILE + head;
+        is_head[r] = head == lane;
         if (lane == 0) srun[ly] = starts;
     }
     __syncthreads();
@@ -140,12 +142,21 @@ __global__ void __launch_bounds__(CCL_LOCAL_THREADS)
             unite_local(sp, t, t - CCL_TILE);
     }
     __syncthreads();
+    // each run head finds its root once and stores it (other finds passing
+    // through it meanwhile still reach the same root); a pixel is then two
+    // lookups from its root: pixel -> head -> root
+#pragma unroll
+    for (int r = 0; r < CCL_ROWS; ++r) {
+        const int t = (warp + r * (CCL_LOCAL_THREADS / 32)) * CCL_TILE + lane;
+        if (valid[r] && is_head[r]) sp[t] = find_local(sp, t);
+    }
+    __syncthreads();
 #pragma unroll
     for (int r = 0; r < CCL_ROWS; ++r) {
         const int ly = warp + r * (CCL_LOCAL_THREADS / 32), t = ly * CCL_TILE + lane;
         if (!valid[r]) continue;
         const long long p = (long long)(y0 + ly) * W + x;
-        const int root = find_local(sp, t);
+        const int root = sp[sp[t]];
         parent[p] = (int)((long long)(y0 + root / CCL_TILE) * W + x0 + root % CCL_TILE);
         if (root == t) size[p] = 0;
     }
