@@ -346,35 +346,39 @@ __device__ __forceinline__ ProjBest proj_candidate(long long p, int x, int y, lo
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ void update_cluster(const SolveArgs &a, int k, int from_acc)
 {
+    // every load that does not depend on another is issued first: the
+    // previous window, the state (kept when the cluster received no pixel)
+    // and the sums; the new state then stays in registers
+    const ClusterDev old = a.cdev[k];
+    long long n = a.st_n[k], sx = a.st_sx[k], sy = a.st_sy[k];
+    float4 col = a.st_col[k];
+    int2 e = a.st_end[k];
+    bool check_projection = false;
+    int label_at_end = k;
     if (from_acc) {
-        ClusterAcc c = a.acc[k];
-        ClusterAcc z = {};
-        a.acc[k] = z;
-        const long long n = (long long)c.n;
-        if (n > 0) {
-            const long long sx = (long long)c.sx, sy = (long long)c.sy;
+        const ClusterAcc c = a.acc[k];
+        a.acc[k] = ClusterAcc{};
+        if (c.n > 0) {
+            n = (long long)c.n;
+            sx = (long long)c.sx;
+            sy = (long long)c.sy;
             a.st_n[k] = n;
             a.st_sx[k] = sx;
             a.st_sy[k] = sy;
             const double den = (double)n * (double)(1 << COLOR_FRAC_BITS);
-            a.st_col[k] = make_float4((float)((double)(long long)c.sL / den),
-                                      (float)((double)(long long)c.sa / den),
-                                      (float)((double)(long long)c.sb / den), 0.f);
-            const int ex = (int)((2 * sx + n) / (2 * n));
-            const int ey = (int)((2 * sy + n) / (2 * n));
-            a.st_end[k] = make_int2(ex, ey);
-            if (a.labels[(long long)ey * a.W + ex] != k) {
-                const int slot = atomicAdd(&a.ctr->nproj, 1);
-                a.proj_list[slot] = k;
-            }
+            col = make_float4((float)((double)(long long)c.sL / den), (float)((double)(long long)c.sa / den),
+                              (float)((double)(long long)c.sb / den), 0.f);
+            a.st_col[k] = col;
+            e = make_int2((int)((2 * sx + n) / (2 * n)), (int)((2 * sy + n) / (2 * n)));
+            a.st_end[k] = e;
+            // Eq. 4 is needed when the endpoint's pixel is not in S_k; the
+            // label is read now and used last
+            label_at_end = a.labels[(long long)e.y * a.W + e.x];
+            check_projection = true;
         }
     }
-    const long long n = a.st_n[k], sx = a.st_sx[k], sy = a.st_sy[k];
-    const ClusterDev old = a.cdev[k];
     a.prev_win[k] = make_int4(old.xlo, old.xhi, old.ylo, old.yhi);
     ClusterDev cd;
-    const float4 col = a.st_col[k];
-    const int2 e = a.st_end[k];
     cd.L = col.x; cd.a = col.y; cd.b = col.z;
     cd.xk = (float)((double)sx / (double)n);
     cd.yk = (float)((double)sy / (double)n);
@@ -387,10 +391,15 @@ __device__ __forceinline__ void update_cluster(const SolveArgs &a, int k, int fr
         cd.xlo = 1; cd.xhi = 0; cd.ylo = 1; cd.yhi = 0;
     }
     a.cdev[k] = cd;
-    if (!ok) return;
-    for (int ty = cd.ylo / TILE_Y; ty <= cd.yhi / TILE_Y; ++ty)
-        for (int tx = cd.xlo / TILE_X; tx <= cd.xhi / TILE_X; ++tx)
-            atomicAdd(&a.tile_count[ty * a.n_tx + tx], 1);
+    if (ok) {
+        for (int ty = cd.ylo / TILE_Y; ty <= cd.yhi / TILE_Y; ++ty)
+            for (int tx = cd.xlo / TILE_X; tx <= cd.xhi / TILE_X; ++tx)
+                atomicAdd(&a.tile_count[ty * a.n_tx + tx], 1);
+    }
+    if (check_projection && label_at_end != k) {
+        const int slot = atomicAdd(&a.ctr->nproj, 1);
+        a.proj_list[slot] = k;
+    }
 }
 
 __global__ void k_update(SolveArgs a, int from_acc)
