@@ -398,26 +398,26 @@ __device__ __forceinline__ int vpath_sums(const float4 *__restrict__ plane, int 
     const int dx = (p_first ? ex : px) - ax, dy = (p_first ? ey : py) - ay, dt = (p_first ? et : pt) - at;
     const int adx = abs(dx), ady = abs(dy), adt = abs(dt);
     // strides (elements) of the three axes with their signs; the major axis
-    // is the first largest |delta|
-    const long long sxs = dx < 0 ? -1 : 1, sys = dy < 0 ? -(long long)W : (long long)W,
-                    sts = dt < 0 ? -HW : HW;
-    int ns, d1, d2;
-    long long smaj, s1, s2;
+    // is the first largest |delta|.  A volume holds at most 2^30 voxels, so
+    // offsets and strides are 32-bit.
+    const int hw = (int)HW;
+    const int sxs = dx < 0 ? -1 : 1, sys = dy < 0 ? -W : W, sts = dt < 0 ? -hw : hw;
+    int ns, d1, d2, smaj, s1, s2;
     if (adx >= ady && adx >= adt) { ns = adx; smaj = sxs; d1 = ady; s1 = sys; d2 = adt; s2 = sts; }
     else if (ady >= adt) { ns = ady; smaj = sys; d1 = adx; s1 = sxs; d2 = adt; s2 = sts; }
     else { ns = adt; smaj = sts; d1 = adx; s1 = sxs; d2 = ady; s2 = sys; }
-    const float4 *q = plane + ((long long)at * HW + (long long)ay * W + ax);
+    int q = at * hw + ay * W + ax;
     const int two_ns = 2 * ns, two_d1 = 2 * d1, two_d2 = 2 * d2;
     int e1 = ns, e2 = ns;
     float dc = 0.f, w = 0.f;
 #pragma unroll 4
     for (int i = 0; i <= ns; ++i) {
-        const float4 v = __ldg(q);
+        const float4 v = __ldg(plane + q);
         dc += colour_dist(v, cL, ca, cb);
         w += v.w;
         e1 += two_d1;
         e2 += two_d2;
-        long long step = smaj;
+        int step = smaj;
         if (e1 >= two_ns) { e1 -= two_ns; step += s1; }
         if (e2 >= two_ns) { e2 -= two_ns; step += s2; }
         q += step;
