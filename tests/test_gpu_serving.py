@@ -73,3 +73,44 @@ def test_serving_mix_equals_alone(S, storage):
             assert n == nref and np.array_equal(out, ref), i
             s.close()
     srv.close()
+
+
+def test_serving_zero_iterations(S):
+    """Requests with no iterations never join a step: each is retired by the
+    next step call, and its delivery must wait for its own set-up (on a side
+    stream).  Their labels equal solves with no iterations."""
+    import torch
+
+    sizes = SIZES[:5]
+    imgs = []
+    for i, (H, W, K) in enumerate(sizes):
+        rgb, con, _ = synth.small_image(H, W, seed=950 + i, n_cells=max(2, H * W // 3000))
+        imgs.append((torch.from_numpy(rgb).cuda(), torch.from_numpy(con).cuda(), K))
+    p = S.scalp_default_params()
+    need = [S.scalp_workspace_bytes(H, W, K, p) for H, W, K in sizes]
+    budget = S.scalp_server_reserve_bytes(8) + sum(need) + (1 << 20)
+    stream = torch.cuda.Stream()
+    srv = S.Server(budget, max_slots=8, storage="f32", iters=0, stream=stream)
+    inflight = {}
+    for i, im in enumerate(imgs):
+        r = srv.submit(*im)
+        assert r is not None
+        inflight[r[0]] = (i, r[1])
+    assert srv.step() == 0  # nothing to iterate; all retire
+    results = {}
+    t_end = time.monotonic() + 60.0
+    while inflight:
+        for rid in list(inflight):
+            done, n = srv.poll(rid)
+            if done:
+                i, out = inflight.pop(rid)
+                results[i] = (out.numpy().copy(), n)
+        assert time.monotonic() < t_end
+    with torch.cuda.stream(stream):
+        for i, (rgb, con, K) in enumerate(imgs):
+            s = S.Segmenter(rgb, con, K, storage="f32", stream=stream)
+            ref, nref = s.labels(enforce=True)
+            out, n = results[i]
+            assert n == nref and np.array_equal(out, ref), i
+            s.close()
+    srv.close()
