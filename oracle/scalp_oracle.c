@@ -13,7 +13,7 @@
  * Then update the clusters and, where needed, project their barycenters
  * (Eq. 4).
  *
- * Readings of points the paper leaves open (each is listed in the design doc):
+ * Readings of points the paper leaves open:
  *   - CIELab: sRGB (IEC 61966-2-1) -> linear -> XYZ (D65 matrix) -> CIE 1976
  *     L*a*b*, with the reference white taken as the XYZ image of sRGB white.
  *   - Grid: r = sqrt(N/K); nx = max(1, round(W/r)), ny = max(1, round(H/r));
@@ -587,7 +587,7 @@ void orc_gradient_prior(const double *L, const double *A, const double *B, int H
 /* ======================================================================== */
 /* Supervoxels: SCALP on a video volume (the extension the paper's           */
 /* conclusion names as future work).  Readings, each the 2-D rule taken      */
-/* axis by axis (listed in the design doc):                                       */
+/* axis by axis:                                                             */
 /*   - volume T frames x H x W, voxel (x, y, t) at index (t*H + y)*W + x;    */
 /*   - r = cbrt(N/K) (host C library); grid nx = max(1, round(W/r)),         */
 /*     ny = max(1, round(H/r)), nt = max(1, round(T/r)); voxel starts in     */

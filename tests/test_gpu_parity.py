@@ -1,6 +1,9 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 oracle.
 
-Tolerances (written here, derived in the design doc):
+Tolerances (the 1e-5 bound: FP32 CIELab values are good to ~1e-7 relative,
+a path sum of <= 2r+1 ~ 65 FP32 terms to ~4e-6 relative, and Eq. 2-3 add a
+few ulps, so a flip between candidates whose exact distances differ by more
+than 1e-5 relative cannot come from rounding):
   * path pixel sets, initial grid sums, endpoints, connectivity: bit-exact;
   * per-pixel labels of one assignment from the same state: >= 99.9% equal, and
     every disagreement a near-tie, (D(p,k_gpu) - D(p,k_oracle)) / D(p,k_oracle)
