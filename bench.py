@@ -304,13 +304,23 @@ def measure_batch(args, storage: str, flush, batch_imgs):
 
 
 def measure_serving(args, batch_imgs, n_requests: int = 2000, rate_hz: float = 500.0,
-                    budget_gb: float = 40.0, storage: str = "f16"):
+                    budget_gb: float = 40.0, storage: str = "f16", step_mpix: float = 4.0,
+                    split_mpix: float = 4.0):
     """The serving form: Poisson arrivals at rate_hz over the batch size mix
-    plus 10% 2160x3840 images, admitted into a server with a device memory
+    plus 10% 2160x3840 images, admitted into servers with a device memory
     budget; each request gets 10 iterations and connectivity enforcement.
-    Latency = delivery of its labels (host, pinned) - arrival.  Compared with
-    serial plain-FP32 solves of the same request stream (first come, first
-    served, one at a time)."""
+    With split_mpix > 0 two servers share the GPU: requests of at most
+    split_mpix Mpix go to one on a high-priority stream, larger ones to one on
+    a low-priority stream, each driven by its own host thread (the library's
+    blocking calls release the interpreter lock), so long steps of large
+    images neither share a step with small requests nor hold up their
+    admission.  step_mpix > 0 sets each server's step budget (least remaining
+    work first).  Latency = delivery of its labels (host, pinned) - arrival.
+    Compared with serial plain-FP32 solves of the same request stream (first
+    come, first served, one at a time)."""
+    import collections
+    import threading
+
     import numpy as np
     import torch
 
@@ -328,40 +338,77 @@ def measure_serving(args, batch_imgs, n_requests: int = 2000, rate_hz: float = 5
     reqs = [uhd[i % 2] if kind[i] else small[i % len(small)] for i in range(n_requests)]
     pix = [int(r[0].shape[0]) * int(r[0].shape[1]) for r in reqs]
     iters = 10
+    device = torch.cuda.current_device()
 
-    # warm the pinned-memory cache and the kernels with a few requests
-    stream = torch.cuda.Stream()
-    srv = scalp.Server(int(budget_gb * (1 << 30)), max_slots=1024, storage=storage, iters=iters,
-                       stream=stream)
-    warm = {r[0] for r in (srv.submit(*reqs[i]) for i in range(8)) if r}
-    while warm:
-        srv.step()
-        warm = {rid for rid in warm if not srv.poll(rid)[0]}
+    # lanes: (server, stream, queue); a request goes to the first lane whose
+    # size bound holds it
+    if split_mpix > 0:
+        specs = [(split_mpix * 1e6, -5, 0.25), (float("inf"), 0, 0.75)]  # bound, priority, pool share
+    else:
+        specs = [(float("inf"), 0, 1.0)]
+    lanes = []
+    for bound, prio, share in specs:
+        st = torch.cuda.Stream(priority=prio)
+        srv = scalp.Server(int(budget_gb * share * (1 << 30)), max_slots=1024, storage=storage, iters=iters,
+                           stream=st, step_pixels=int(step_mpix * 1e6))
+        lanes.append((bound, srv, st, collections.deque()))
+
+    def lane_of(i):
+        return next(k for k, l in enumerate(lanes) if pix[i] <= l[0])
+
+    # warm the pinned-memory cache and the kernels with a few requests per lane
+    for k, (_, srv, _, _) in enumerate(lanes):
+        mine = [i for i in range(n_requests) if lane_of(i) == k][:8]
+        warm = {r[0] for r in (srv.submit(*reqs[i]) for i in mine) if r}
+        while warm:
+            srv.step()
+            warm = {rid for rid in warm if not srv.poll(rid)[0]}
+    torch.cuda.synchronize()
 
     lat = np.zeros(n_requests)
+    finished = threading.Event()
+    errors = []
     t0 = time.perf_counter()
-    nxt, inflight, queue = 0, {}, []
-    while nxt < n_requests or queue or inflight:
-        now = time.perf_counter() - t0
-        while nxt < n_requests and arrivals[nxt] <= now:
-            queue.append(nxt)
-            nxt += 1
-        while queue:  # admit in arrival order while memory and slots allow
-            r = srv.submit(*reqs[queue[0]])
-            if r is None:
-                break
-            inflight[r[0]] = queue.pop(0)
-        if inflight:
-            srv.step()
-        elif nxt < n_requests:
-            time.sleep(max(0.0, arrivals[nxt] - (time.perf_counter() - t0)))
-        for rid in list(inflight):
-            done, _ = srv.poll(rid)
-            if done:
-                i = inflight.pop(rid)
-                lat[i] = time.perf_counter() - t0 - arrivals[i]
+
+    def drive(srv, queue):
+        try:
+            torch.cuda.set_device(device)
+            inflight = {}
+            while not (finished.is_set() and not queue and not inflight):
+                while queue:  # admit in arrival order while memory and slots allow
+                    r = srv.submit(*reqs[queue[0]])
+                    if r is None:
+                        break
+                    inflight[r[0]] = queue.popleft()
+                if inflight:
+                    srv.step()
+                else:
+                    time.sleep(20e-6)
+                for rid in list(inflight):
+                    done, _ = srv.poll(rid)
+                    if done:
+                        i = inflight.pop(rid)
+                        lat[i] = time.perf_counter() - t0 - arrivals[i]
+        except Exception as exc:  # reported after the join
+            errors.append(exc)
+
+    threads = [threading.Thread(target=drive, args=(srv, q)) for _, srv, _, q in lanes]
+    for t in threads:
+        t.start()
+    for i in range(n_requests):  # dispatch at the arrival times
+        wait = arrivals[i] - (time.perf_counter() - t0)
+        if wait > 0:
+            time.sleep(wait)
+        lanes[lane_of(i)][3].append(i)
+    finished.set()
+    for t in threads:
+        t.join()
     wall = time.perf_counter() - t0
-    srv.close()
+    if errors:
+        raise errors[0]
+    for _, srv, _, _ in lanes:
+        srv.close()
+    stream = lanes[0][2]
 
     # serial plain-FP32 solves of the same stream
     lat_s = np.zeros(n_requests)
@@ -387,6 +434,10 @@ def measure_serving(args, batch_imgs, n_requests: int = 2000, rate_hz: float = 5
     tot = sum(pix) * iters / 1e6
     return {
         "requests": n_requests, "rate_hz": rate_hz, "budget_gb": budget_gb, "storage": storage,
+        "step": (f"least remaining work first, at most {step_mpix:g} Mpix per step" if step_mpix
+                 else "every request in flight each step"),
+        "lanes": (f"requests <= {split_mpix:g} Mpix on a high-priority server, larger ones on a "
+                  "low-priority one, one host thread each" if split_mpix else "one server"),
         "mix": "64 sizes of the batch mix + 10% 2160x3840", "iters": iters,
         "value": tot / wall, "unit": UNIT, "wall_s": wall,
         "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
@@ -814,7 +865,10 @@ def run_form(args):
         res = measure_voxel(args, flush)
     elif args.only_form == "serving":
         bws = synth.batch_configs()
-        res = measure_serving(args, (bws, *synth.batch_images(bws)))
+        imgs = (bws, *synth.batch_images(bws))
+        res = {"one_server": measure_serving(args, imgs, step_mpix=0.0, split_mpix=0.0),
+               "two_lanes": measure_serving(args, imgs, step_mpix=0.0, split_mpix=4.0),
+               "two_lanes_step_budget": measure_serving(args, imgs)}
     elif args.only_form == "batched":
         bws = synth.batch_configs()
         imgs = (bws, *synth.batch_images(bws))

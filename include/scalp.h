@@ -321,8 +321,10 @@ void scalp_voxel_destroy(scalp_vctx *ctx);
  * labels equal those of scalp_init + scalp_iterate + scalp_labels on the same
  * image.  labels_out should be pinned host memory: with pageable memory the copy
  * synchronises the stream.  No call waits for the stream to drain: a step waits
- * only for the step eight argument uploads back (the argument blocks form a
- * ring in the reserve), and a request's status travels with its labels.
+ * only for the step two launches back (so a request admitted between steps
+ * joins within two steps) and for the step eight argument uploads back (the
+ * argument blocks form a ring in the reserve); a request's status travels
+ * with its labels.
  * scalp_server_destroy() synchronises the stream.  One server is driven by one
  * host thread. */
 typedef struct scalp_server scalp_server;
@@ -336,6 +338,12 @@ int scalp_server_submit(scalp_server *s, const scalp_image *image, const scalp_c
                         int32_t K, float m, int32_t iters, int32_t enforce, int32_t *labels_out,
                         uint64_t *id);
 int scalp_server_step(scalp_server *s, int32_t *n_running);
+/* Optional step budget: with max_pixels > 0 a step iterates only the requests
+ * with the least remaining work (pixels x iterations left, ties to the
+ * earlier request) whose pixels sum to at most max_pixels (always at least
+ * one); the others wait for a later step.  0 (the default) iterates every
+ * request in flight.  *n_running of scalp_server_step counts those iterated. */
+int scalp_server_set_step_budget(scalp_server *s, int64_t max_pixels);
 int scalp_server_poll(scalp_server *s, uint64_t id, int32_t *done, int32_t *n_labels);
 int scalp_server_stats(const scalp_server *s, int32_t *in_flight, size_t *pool_free_bytes);
 void scalp_server_destroy(scalp_server *s);

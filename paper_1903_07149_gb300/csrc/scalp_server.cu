@@ -36,6 +36,7 @@ namespace {
 constexpr size_t SALIGN = 256;
 constexpr int ARG_RING = 8;      // argument blocks in flight
 constexpr int SIDE_STREAMS = 4;  // for the requests' set-up and retirement
+constexpr int STEPS_AHEAD = 2;   // steps enqueued beyond the one the GPU runs
 
 size_t salign(size_t x) { return (x + SALIGN - 1) & ~(SALIGN - 1); }
 
@@ -44,6 +45,7 @@ struct Solve {
     scalp_ctx *ctx = nullptr;
     size_t off = 0, bytes = 0;  // its part of the pool
     int iters_left = 0;
+    long long pixels = 0;  // H * W
     int enforce = 1;
     int32_t *labels_out = nullptr;
     cudaEvent_t done = nullptr;
@@ -99,6 +101,11 @@ struct scalp_server {
     cudaStream_t side[SIDE_STREAMS] = {};
     cudaEvent_t step_ev = nullptr;  // the step stream's position, for forks
     int side_next = 0;
+    long long step_pixels = 0;      // 0: every request iterates each step
+    std::vector<uint64_t> arg_ids;  // the requests of the current argument block
+    cudaEvent_t step_done[STEPS_AHEAD] = {};
+    bool step_live[STEPS_AHEAD] = {};
+    int step_next = 0;
 };
 
 namespace {
@@ -207,6 +214,8 @@ void free_host(scalp_server *s)
             cudaStreamDestroy(t);
         }
     if (s->step_ev) cudaEventDestroy(s->step_ev);
+    for (cudaEvent_t e : s->step_done)
+        if (e) cudaEventDestroy(e);
     for (cudaEvent_t e : s->ring_ev)
         if (e) cudaEventDestroy(e);
     if (s->stage) cudaFreeHost(s->stage);
@@ -249,9 +258,14 @@ int scalp_server_create(scalp_server **out, void *pool, size_t pool_bytes, int32
                           cudaHostAllocDefault);
     for (int i = 0; i < ARG_RING && e == cudaSuccess; ++i)
         e = cudaEventCreateWithFlags(&s->ring_ev[i], cudaEventDisableTiming);
+    // side streams share the priority of the server's stream
+    int prio = 0;
+    if (e == cudaSuccess && s->st) e = cudaStreamGetPriority(s->st, &prio);
     for (int i = 0; i < SIDE_STREAMS && e == cudaSuccess; ++i)
-        e = cudaStreamCreateWithFlags(&s->side[i], cudaStreamNonBlocking);
+        e = cudaStreamCreateWithPriority(&s->side[i], cudaStreamNonBlocking, prio);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&s->step_ev, cudaEventDisableTiming);
+    for (int i = 0; i < STEPS_AHEAD && e == cudaSuccess; ++i)
+        e = cudaEventCreateWithFlags(&s->step_done[i], cudaEventDisableTiming);
     if (e != cudaSuccess) {
         free_host(s);
         return server_fail(SCALP_E_CUDA, "server setup: %s", cudaGetErrorString(e));
@@ -308,6 +322,7 @@ int scalp_server_submit(scalp_server *s, const scalp_image *image, const scalp_c
     v->off = off;
     v->bytes = bytes;
     v->iters_left = iters;
+    v->pixels = (long long)image->H * image->W;
     v->enforce = enforce;
     v->labels_out = labels_out;
     s->active.push_back(v);
@@ -320,13 +335,38 @@ int scalp_server_submit(scalp_server *s, const scalp_image *image, const scalp_c
 int scalp_server_step(scalp_server *s, int32_t *n_running)
 {
     if (!s) return server_fail(SCALP_E_ARG, "server is NULL");
-    std::vector<Solve *> running;
+    std::vector<Solve *> running;  // admission (id) order
     for (Solve *v : s->active)
         if (!v->retired && v->iters_left > 0) running.push_back(v);
+    if (s->step_pixels > 0 && running.size() > 1) {
+        // least remaining work first (pixels x iterations left, then id), as
+        // many as the budget holds, at least one; back in id order after
+        std::stable_sort(running.begin(), running.end(), [](const Solve *u, const Solve *v) {
+            return u->pixels * u->iters_left < v->pixels * v->iters_left;
+        });
+        size_t take = 1;
+        long long sum = running[0]->pixels;
+        while (take < running.size() && sum + running[take]->pixels <= s->step_pixels)
+            sum += running[take++]->pixels;
+        running.resize(take);
+        std::sort(running.begin(), running.end(), [](const Solve *u, const Solve *v) { return u->id < v->id; });
+    }
     if (!running.empty()) {
-        if (s->args_dirty || s->bargs.count != (int)running.size()) {
+        // bounded run-ahead: wait for the step STEPS_AHEAD launches back, so a
+        // request admitted now joins within that many steps instead of
+        // queueing behind every step the host could enqueue
+        const int slot = s->step_next;
+        if (s->step_live[slot]) {
+            const cudaError_t w = cudaEventSynchronize(s->step_done[slot]);
+            if (w != cudaSuccess) return server_fail(SCALP_E_CUDA, "step wait: %s", cudaGetErrorString(w));
+            s->step_live[slot] = false;
+        }
+        std::vector<uint64_t> ids(running.size());
+        for (size_t i = 0; i < running.size(); ++i) ids[i] = running[i]->id;
+        if (s->args_dirty || ids != s->arg_ids) {
             const int rc = rebuild_args(s, running);
             if (rc) return rc;
+            s->arg_ids.swap(ids);
         }
         for (Solve *v : running) {  // new requests: their set-up first
             if (v->joined) continue;
@@ -339,6 +379,11 @@ int scalp_server_step(scalp_server *s, int32_t *n_running)
         cudaError_t e = cudaGetLastError();
         // the argument slot stays live until this step has run
         if (e == cudaSuccess) e = cudaEventRecord(s->ring_ev[s->ring_cur], s->st);
+        if (e == cudaSuccess) e = cudaEventRecord(s->step_done[slot], s->st);
+        if (e == cudaSuccess) {
+            s->step_live[slot] = true;
+            s->step_next = (slot + 1) % STEPS_AHEAD;
+        }
         if (e != cudaSuccess) return server_fail(SCALP_E_CUDA, "server step: %s", cudaGetErrorString(e));
         for (Solve *v : running) {
             --v->iters_left;
@@ -369,6 +414,13 @@ int scalp_server_step(scalp_server *s, int32_t *n_running)
         s->args_dirty = true;
     }
     if (n_running) *n_running = (int32_t)running.size();
+    return SCALP_OK;
+}
+
+int scalp_server_set_step_budget(scalp_server *s, int64_t max_pixels)
+{
+    if (!s || max_pixels < 0) return server_fail(SCALP_E_ARG, "need a server and max_pixels >= 0");
+    s->step_pixels = max_pixels;
     return SCALP_OK;
 }
 

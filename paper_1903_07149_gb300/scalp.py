@@ -94,6 +94,7 @@ EXPORTS = (
     "scalp_batch_labels", "scalp_batch_get_state", "scalp_batch_get_info", "scalp_batch_destroy",
     "scalp_server_reserve_bytes", "scalp_server_create", "scalp_server_submit", "scalp_server_step",
     "scalp_server_poll", "scalp_server_stats", "scalp_server_destroy", "scalp_boundary_map",
+    "scalp_server_set_step_budget",
     "scalp_quality_workspace_bytes", "scalp_quality_metrics",
     "scalp_gradient_prior_workspace_bytes", "scalp_gradient_prior",
     "scalp_voxel_workspace_bytes", "scalp_voxel_init", "scalp_voxel_iterate", "scalp_voxel_labels",
@@ -155,6 +156,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
                                                    ctypes.POINTER(scalp_contour), I32, ctypes.c_float,
                                                    I32, I32, P, ctypes.POINTER(ctypes.c_uint64)]),
             "scalp_server_step": (ctypes.c_int, [P, ctypes.POINTER(I32)]),
+            "scalp_server_set_step_budget": (ctypes.c_int, [P, I64]),
             "scalp_server_poll": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.POINTER(I32),
                                                  ctypes.POINTER(I32)]),
             "scalp_server_stats": (ctypes.c_int, [P, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_size_t)]),
@@ -610,7 +612,9 @@ class Server:
     """Continuous batching of SCALP solves within a device memory budget."""
 
     def __init__(self, budget_bytes: int, max_slots: int = 1024, storage: str = "f32", m: float = 10.0,
-                 iters: int = 10, enforce: bool = True, stream=None):
+                 iters: int = 10, enforce: bool = True, stream=None, step_pixels: int = 0):
+        """step_pixels > 0: each step iterates the requests with the least
+        remaining work within that many pixels (scalp_server_set_step_budget)."""
         import torch
 
         self._torch = torch
@@ -621,6 +625,8 @@ class Server:
         self.params = p
         self.pool = torch.empty(int(budget_bytes), dtype=torch.uint8, device="cuda")
         self.server = scalp_server_create(self.pool.data_ptr(), int(budget_bytes), max_slots, p)
+        if step_pixels:
+            _check(load().scalp_server_set_step_budget(self.server, int(step_pixels)))
         self.m, self.iters, self.enforce = m, iters, enforce
         self._keep = {}
 

@@ -26,8 +26,10 @@ def S():
     return scalp
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16"])
-def test_serving_mix_equals_alone(S, storage):
+@pytest.mark.parametrize("storage,step_pixels", [("f32", 0), ("f16", 0), ("f32", 60000)])
+def test_serving_mix_equals_alone(S, storage, step_pixels):
+    """step_pixels > 0: each step iterates only the least remaining work
+    within the budget; every request still gets all its iterations."""
     import torch
 
     imgs = []
@@ -40,7 +42,7 @@ def test_serving_mix_equals_alone(S, storage):
     # room for about three requests at a time: later ones wait for memory
     budget = S.scalp_server_reserve_bytes(8) + 3 * max(need) + (1 << 20)
     stream = torch.cuda.Stream()
-    srv = S.Server(budget, max_slots=8, storage=storage, iters=6, stream=stream)
+    srv = S.Server(budget, max_slots=8, storage=storage, iters=6, stream=stream, step_pixels=step_pixels)
     pending = list(range(len(SIZES)))
     inflight, results, waited, steps = {}, {}, 0, 0
     t_end = time.monotonic() + 120.0  # the host runs ahead: idle steps spin
