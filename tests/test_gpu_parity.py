@@ -171,6 +171,48 @@ def test_one_step_parity(S, variant, t):
     seg.close()
 
 
+def _random_case(seed):
+    """A seeded shape: sides from 1 to ~260 (thin and ragged ones included),
+    K log-uniform from 1 to min(N, 900), 0 or 2 oracle iterations first."""
+    rng = np.random.default_rng(7000 + seed)
+    H = int(rng.choice([1, 2, 3, rng.integers(4, 64), rng.integers(64, 200)]))
+    W = int(rng.choice([1, 5, rng.integers(6, 64), rng.integers(64, 260)]))
+    if H * W < 4:
+        H, W = H + 3, W + 3
+    K = int(np.clip(round(np.exp(rng.uniform(0.0, np.log(min(H * W, 900))))), 1, H * W))
+    return H, W, K, int(rng.choice([0, 2])), bool(seed % 2)
+
+
+@pytest.mark.parametrize("seed", range(32))
+def test_random_shapes_one_step(S, seed):
+    """One assignment and update from the oracle's state on seeded random
+    shapes and K (tiles, windows and boxes of every raggedness), walking the
+    maps or, for odd seeds, the plane: labels within the near-tie rule,
+    counts, sums and endpoints exact for clusters whose pixel set agrees."""
+    H, W, K, t, plane = _random_case(seed)
+    rgb, con, _ = synth.small_image(H, W, seed=7100 + seed, n_cells=max(2, H * W // 900))
+    orc = oracle.Solver(oracle.lab_from_rgb(rgb), con, K)
+    orc.iterate(t)
+    st = orc.state()
+    seg = make_seg(S, rgb, con, K, global_walk=plane)
+    seg.set_state(to_gpu_state(st))
+    seg.iterate(1)
+    g = seg.get_state()
+    orc.assign()
+    check_one_step(orc, g["labels"], orc.labels, st)
+    orc_lab = orc.labels.copy()
+    orc.update()
+    bad = np.unique(np.concatenate([g["labels"][g["labels"] != orc_lab],
+                                    orc_lab[g["labels"] != orc_lab]]))
+    same = np.setdiff1d(np.arange(orc.Keff), bad)
+    for k in ("n", "sx", "sy"):
+        assert np.array_equal(g[k][same], getattr(orc, k)[same]), (k, H, W, K)
+    assert np.array_equal(g["endpoint"][same], orc.endpoints()[same]), (H, W, K)
+    ref = orc.colors()[same]
+    assert np.all(np.abs(g["color"][same] - ref) <= COLOR_RTOL * np.maximum(np.abs(ref), 1))
+    seg.close()
+
+
 @pytest.mark.parametrize("H,W,K", [(200, 300, 150), (240, 320, 6), (6, 131072, 2)])
 def test_maps_equal_plane_walk(S, H, W, K):
     """Paths walked on the shared-memory distance maps and on the plane in
