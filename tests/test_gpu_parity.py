@@ -281,6 +281,33 @@ def test_connectivity_bit_exact(S):
     seg.close()
 
 
+@pytest.mark.parametrize("seed", range(12))
+def test_random_shapes_connectivity(S, seed):
+    """Connectivity enforcement bit-exact against the oracle on seeded random
+    shapes (tile-ragged, thin, tiny) with block label maps plus noise."""
+    rng = np.random.default_rng(7300 + seed)
+    H = int(rng.choice([1, 2, rng.integers(3, 40), rng.integers(40, 300)]))
+    W = int(rng.choice([1, 3, rng.integers(4, 40), rng.integers(40, 300)]))
+    if H * W < 4:
+        H, W = H + 3, W + 3
+    K = int(rng.integers(1, min(H * W, 400) + 1))
+    rgb, con, _ = synth.small_image(H, W, seed=7400 + seed, n_cells=max(2, H * W // 900))
+    orc = oracle.Solver(oracle.lab_from_rgb(rgb), con, K)
+    st = orc.state()
+    blk = int(rng.integers(1, 12))
+    base = rng.integers(0, orc.Keff, size=(H // blk + 1, W // blk + 1))
+    lab = np.kron(base, np.ones((blk, blk), int))[:H, :W]
+    noise = rng.uniform(size=lab.shape) < rng.uniform(0.0, 0.2)
+    lab = np.where(noise, rng.integers(0, orc.Keff, size=lab.shape), lab).astype(np.int32)
+    st["labels"] = lab
+    seg = make_seg(S, rgb, con, K)
+    seg.set_state(to_gpu_state(st))
+    out, n = seg.labels(enforce=True)
+    ref, nref = oracle.connectivity(lab, K)
+    assert n == nref and np.array_equal(out, ref), (H, W, K, blk)
+    seg.close()
+
+
 def test_checkpoint_resume_bit_identical(S):
     H, W, K = 180, 260, 140
     rgb, con, _ = synth.small_image(H, W, seed=5)
