@@ -82,6 +82,44 @@ def test_voxel_one_step_parity(S, T, H, W, K, t):
     seg.close()
 
 
+@pytest.mark.parametrize("seed", range(12))
+def test_voxel_random_shapes_one_step(S, seed):
+    """One assignment and update against the oracle on seeded random volume
+    shapes and K (single frames, thin and ragged tiles): every disagreement a
+    near-tie, sums and endpoints exact where a cluster's voxel set agrees."""
+    rng = np.random.default_rng(7500 + seed)
+    T = int(rng.integers(1, 11))
+    H = int(rng.choice([2, rng.integers(3, 17), rng.integers(17, 48)]))
+    W = int(rng.choice([3, rng.integers(4, 33), rng.integers(33, 70)]))
+    K = int(rng.integers(1, min(T * H * W, 150) + 1))
+    t = int(rng.integers(0, 2))
+    rgb, con, _ = _volume(T, H, W, seed=7600 + seed, n_cells=int(rng.integers(2, 9)))
+    orc = oracle.VSolver(oracle.lab_from_rgb(rgb), con, K)
+    orc.iterate(t)
+    st = orc.state()
+    seg = _seg(S, rgb, con, K)
+    assert seg.info.Keff == orc.Keff
+    seg.set_state(_to_gpu_state(st))
+    seg.iterate(1)
+    g = seg.get_state()
+    orc.assign()
+    diff = np.argwhere(g["labels"] != orc.labels)
+    for tt, y, x in diff:
+        kg, ko = int(g["labels"][tt, y, x]), int(orc.labels[tt, y, x])
+        Dg, _ = orc.distance(x, y, tt, kg)
+        Do, _ = orc.distance(x, y, tt, ko)
+        assert (Dg - Do) / max(Do, 1e-12) < NEAR_TIE, (T, H, W, K, x, y, tt, kg, ko, Dg, Do)
+    assert len(diff) <= max((1 - AGREE) * orc.N, 2), (len(diff), T, H, W, K)
+    lab_o = orc.labels.copy()
+    orc.update()
+    bad = np.unique(np.concatenate([g["labels"][g["labels"] != lab_o], lab_o[g["labels"] != lab_o]]))
+    same = np.setdiff1d(np.arange(orc.Keff), bad)
+    for k in ("n", "sx", "sy", "st"):
+        assert np.array_equal(g[k][same], getattr(orc, k)[same]), (k, T, H, W, K)
+    assert np.array_equal(g["endpoint"][same], np.stack([orc.ex, orc.ey, orc.et], axis=1)[same])
+    seg.close()
+
+
 def test_voxel_initial_state_exact(S):
     rgb, con, _ = _volume(7, 26, 45, seed=3)
     orc = oracle.VSolver(oracle.lab_from_rgb(rgb), con, 30)
