@@ -230,6 +230,24 @@ __global__ void k_ccl_link(const int *__restrict__ parent, const int *__restrict
 constexpr int CCL_CHUNK = 4096;
 constexpr int CCL_CHUNK_THREADS = 256;
 constexpr int CCL_PER = CCL_CHUNK / CCL_CHUNK_THREADS;  // consecutive pixels per thread
+static_assert(CCL_PER % 4 == 0, "runs are read as int4");
+
+// The CCL_PER values of a thread's run from `base` (a multiple of CCL_PER; the
+// buffers are 256-byte aligned) as 16-byte loads; -1 past N.
+__device__ __forceinline__ void load_run(const int *__restrict__ a, long long base, long long N, int (&v)[CCL_PER])
+{
+    if (base + CCL_PER <= N) {
+        const int4 *a4 = reinterpret_cast<const int4 *>(a + base);
+#pragma unroll
+        for (int i = 0; i < CCL_PER / 4; ++i) {
+            const int4 q = a4[i];
+            v[4 * i] = q.x; v[4 * i + 1] = q.y; v[4 * i + 2] = q.z; v[4 * i + 3] = q.w;
+        }
+    } else {
+#pragma unroll
+        for (int i = 0; i < CCL_PER; ++i) v[i] = base + i < N ? a[base + i] : -1;
+    }
+}
 
 // Sum of v over the CTA (all threads receive it); s_warp holds 32 ints.
 __device__ __forceinline__ int cta_sum(int v, int *s_warp)
@@ -255,8 +273,7 @@ __global__ void __launch_bounds__(CCL_CHUNK_THREADS)
     // CCL_PER consecutive pixels per thread, their parents loaded first
     const long long base = blockIdx.x * (long long)CCL_CHUNK + (long long)threadIdx.x * CCL_PER;
     int par[CCL_PER];
-#pragma unroll
-    for (int i = 0; i < CCL_PER; ++i) par[i] = base + i < N ? parent[base + i] : -1;
+    load_run(parent, base, N, par);
     int cnt = 0;
 #pragma unroll
     for (int i = 0; i < CCL_PER; ++i) {
@@ -329,11 +346,13 @@ __global__ void __launch_bounds__(CCL_CHUNK_THREADS)
     pdl_release();
     __shared__ int s_warp[32];
     const long long base = blockIdx.x * (long long)CCL_CHUNK + (long long)threadIdx.x * CCL_PER;
+    int par[CCL_PER];
+    load_run(parent, base, N, par);
     unsigned flags = 0;
 #pragma unroll
     for (int i = 0; i < CCL_PER; ++i) {
         const long long s = base + i;
-        if (s < N && parent[s] == s && final_id[s] == s) flags |= 1u << i;
+        if (par[i] == s && final_id[s] == s) flags |= 1u << i;
     }
     const int mine = __popc(flags);
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
