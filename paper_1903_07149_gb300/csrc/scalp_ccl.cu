@@ -15,6 +15,7 @@
 //   4. The surviving components are numbered 0.. in raster order of seeds
 //      (per 4096-pixel chunk: a count, a scan of the counts, the ranks).
 #include <algorithm>
+#include <cstdint>
 
 #include "scalp_launch.h"
 
@@ -212,17 +213,33 @@ __global__ void k_ccl_flatten_count(int *parent, int *size, long long N)
     }
 }
 
+// Four consecutive pixels per thread (one 16-byte load of their parents; the
+// buffers are 256-byte aligned).
 __global__ void k_ccl_link(const int *__restrict__ parent, const int *__restrict__ size, int *link,
                            int W, long long N, long long T)
 {
     pdl_wait();  // the previous pass (or the labels) complete
     pdl_release();
-    for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < N;
-         s += (long long)gridDim.x * blockDim.x) {
-        if (parent[s] != s) continue;
-        bool small = size[s] <= T && s != 0;
-        long long nb = ((int)s % W) > 0 ? s - 1 : s - W;  // N <= 2^30
-        link[s] = small ? parent[nb] : (int)s;
+    const long long quads = (N + 3) / 4;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < quads;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long s0 = 4 * g;
+        int pv[4];
+        if (s0 + 4 <= N) {
+            const int4 q = reinterpret_cast<const int4 *>(parent)[g];
+            pv[0] = q.x; pv[1] = q.y; pv[2] = q.z; pv[3] = q.w;
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i) pv[i] = s0 + i < N ? parent[s0 + i] : -1;
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const long long s = s0 + i;
+            if (pv[i] != s) continue;
+            const bool small = size[s] <= T && s != 0;
+            const long long nb = ((int)s % W) > 0 ? s - 1 : s - W;  // N <= 2^30
+            link[s] = small ? parent[nb] : (int)s;
+        }
     }
 }
 
@@ -380,14 +397,31 @@ __global__ void __launch_bounds__(CCL_CHUNK_THREADS)
     }
 }
 
+// Four consecutive pixels per thread; the output is written as one 16-byte
+// store when the caller's buffer is 16-byte aligned.
 __global__ void k_ccl_out(const int *__restrict__ parent, const int *__restrict__ final_id,
                           const int *__restrict__ number, int *out, long long N)
 {
     pdl_wait();  // the previous pass (or the labels) complete
     pdl_release();
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
-         p += (long long)gridDim.x * blockDim.x)
-        out[p] = number[final_id[parent[p]]];
+    const bool vec_out = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
+    const long long quads = (N + 3) / 4;
+    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < quads;
+         g += (long long)gridDim.x * blockDim.x) {
+        const long long s0 = 4 * g;
+        if (s0 + 4 <= N) {
+            const int4 q = reinterpret_cast<const int4 *>(parent)[g];
+            const int4 o = make_int4(number[final_id[q.x]], number[final_id[q.y]], number[final_id[q.z]],
+                                     number[final_id[q.w]]);
+            if (vec_out) {
+                reinterpret_cast<int4 *>(out)[g] = o;
+            } else {
+                out[s0] = o.x; out[s0 + 1] = o.y; out[s0 + 2] = o.z; out[s0 + 3] = o.w;
+            }
+        } else {
+            for (long long p = s0; p < N; ++p) out[p] = number[final_id[parent[p]]];
+        }
+    }
 }
 
 long long ccl_scan_tmp_len(long long N) { return ceil_div_ll(N, CCL_CHUNK) + 64; }
@@ -398,6 +432,7 @@ void launch_ccl(const int *labels, int H, int W, int K, int *out, const CclBuffe
     const long long N = (long long)H * W;
     const long long T = N / (4LL * K);
     const int blocks = (int)std::min<long long>(ceil_div_ll(N, CCL_THREADS), 152 * 16);
+    const int qblocks = (int)std::min<long long>(ceil_div_ll((N + 3) / 4, CCL_THREADS), 152 * 16);
     const int n_tx = (W + CCL_TILE - 1) / CCL_TILE, n_ty = (H + CCL_TILE - 1) / CCL_TILE;
     // eight passes, each a programmatic launch: its CTAs are placed while the
     // previous pass drains and wait for it before their first read
@@ -408,7 +443,7 @@ void launch_ccl(const int *labels, int H, int W, int K, int *out, const CclBuffe
         pdl_launch(true, k_ccl_border, dim3((unsigned)std::min<long long>(ceil_div_ll(nb, CCL_THREADS), 152 * 16)),
                    dim3(CCL_THREADS), 0, st, labels, b.parent, H, W, n_tx, n_ty);
     pdl_launch(true, k_ccl_flatten_count, dim3(blocks), dim3(CCL_THREADS), 0, st, b.parent, b.size, N);
-    pdl_launch(true, k_ccl_link, dim3(blocks), dim3(CCL_THREADS), 0, st, (const int *)b.parent,
+    pdl_launch(true, k_ccl_link, dim3(qblocks), dim3(CCL_THREADS), 0, st, (const int *)b.parent,
                (const int *)b.size, b.link, W, N, T);
     const long long chunks = ceil_div_ll(N, CCL_CHUNK);
     pdl_launch(true, k_ccl_resolve_count, dim3((unsigned)chunks), dim3(CCL_CHUNK_THREADS), 0, st,
@@ -416,7 +451,7 @@ void launch_ccl(const int *labels, int H, int W, int K, int *out, const CclBuffe
     pdl_launch(true, k_ccl_chunk_scan, dim3(1), dim3(CCL_SCAN_THREADS), 0, st, b.scan_tmp, chunks, d_nlab);
     pdl_launch(true, k_ccl_number, dim3((unsigned)chunks), dim3(CCL_CHUNK_THREADS), 0, st, (const int *)b.parent,
                (const int *)b.size, (const int *)b.scan_tmp, b.scan, N);
-    pdl_launch(true, k_ccl_out, dim3(blocks), dim3(CCL_THREADS), 0, st, (const int *)b.parent,
+    pdl_launch(true, k_ccl_out, dim3(qblocks), dim3(CCL_THREADS), 0, st, (const int *)b.parent,
                (const int *)b.size, (const int *)b.scan, out, N);
 }
 
