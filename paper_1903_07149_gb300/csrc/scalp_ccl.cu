@@ -62,12 +62,19 @@ __device__ __forceinline__ void unite(int *parent, int a, int b)
 // pixel gets that root's global index as parent.  size[] is cleared.
 constexpr int CCL_TILE = 32;
 
-__device__ __forceinline__ int find_local(const volatile int *sp, int x)
+// The root of x, halving the path on the way with atomicMin: links always
+// point to smaller indices and a root is the least index of its tree, so a
+// pointer only ever moves toward the root and concurrent finds, unions and
+// the heads' final root writes cannot undo one another.
+__device__ __forceinline__ int find_local(int *sp, int x)
 {
-    int p = sp[x];
+    volatile int *v = sp;
+    int p = v[x];
     while (p != x) {
+        const int gp = v[p];
+        if (gp != p) atomicMin(&sp[x], gp);
         x = p;
-        p = sp[x];
+        p = gp;
     }
     return x;
 }
@@ -143,9 +150,9 @@ __global__ void __launch_bounds__(CCL_LOCAL_THREADS)
             unite_local(sp, t, t - CCL_TILE);
     }
     __syncthreads();
-    // each run head finds its root once and stores it (other finds passing
-    // through it meanwhile still reach the same root); a pixel is then two
-    // lookups from its root: pixel -> head -> root
+    // each run head finds its root once and stores it (finds passing through
+    // it meanwhile still reach the same root); a pixel is then two lookups
+    // from its root: pixel -> head -> root
 #pragma unroll
     for (int r = 0; r < CCL_ROWS; ++r) {
         const int t = (warp + r * (CCL_LOCAL_THREADS / 32)) * CCL_TILE + lane;
