@@ -341,8 +341,11 @@ int scalp_server_step(scalp_server *s, int32_t *n_running);
 /* Optional step budget: with max_pixels > 0 a step iterates only the requests
  * with the least remaining work (pixels x iterations left, ties to the
  * earlier request) whose pixels sum to at most max_pixels (always at least
- * one); the others wait for a later step.  0 (the default) iterates every
- * request in flight.  *n_running of scalp_server_step counts those iterated. */
+ * one); the others wait for a later step.  Under a steady stream of smaller
+ * requests a large one can wait indefinitely: route large requests to a
+ * server of their own (e.g. on a lower-priority stream) where that matters.
+ * 0 (the default) iterates every request in flight.  *n_running of
+ * scalp_server_step counts those iterated. */
 int scalp_server_set_step_budget(scalp_server *s, int64_t max_pixels);
 int scalp_server_poll(scalp_server *s, uint64_t id, int32_t *done, int32_t *n_labels);
 int scalp_server_stats(const scalp_server *s, int32_t *in_flight, size_t *pool_free_bytes);
