@@ -116,3 +116,68 @@ def test_serving_zero_iterations(S):
             assert n == nref and np.array_equal(out, ref), i
             s.close()
     srv.close()
+
+
+def test_two_servers_two_threads(S):
+    """Two servers on streams of different priority, each driven by its own
+    host thread (the serving benchmark's configuration), with step budgets:
+    every delivered request equals the image solved alone."""
+    import threading
+
+    import torch
+
+    imgs = []
+    for i, (H, W, K) in enumerate(SIZES):
+        rgb, con, _ = synth.small_image(H, W, seed=980 + i, n_cells=max(2, H * W // 3000))
+        imgs.append((torch.from_numpy(rgb).cuda(), torch.from_numpy(con).cuda(), K))
+    p = S.scalp_default_params()
+    p.storage = S.STORAGE["f16"]
+    need = [S.scalp_workspace_bytes(H, W, K, p) for H, W, K in SIZES]
+    split = 40000  # pixels: smaller requests to the high-priority server
+    device = torch.cuda.current_device()
+    lanes = []
+    for prio, mine in ((-5, [i for i, (H, W, _) in enumerate(SIZES) if H * W <= split]),
+                       (0, [i for i, (H, W, _) in enumerate(SIZES) if H * W > split])):
+        st = torch.cuda.Stream(priority=prio)
+        budget = S.scalp_server_reserve_bytes(8) + sum(need[i] for i in mine) + (1 << 20)
+        srv = S.Server(budget, max_slots=8, storage="f16", iters=5, stream=st, step_pixels=30000)
+        lanes.append((srv, mine))
+    results, errors = {}, []
+
+    def drive(srv, mine):
+        try:
+            torch.cuda.set_device(device)
+            inflight = {}
+            for i in mine:
+                r = srv.submit(*imgs[i])
+                assert r is not None
+                inflight[r[0]] = (i, r[1])
+            t_end = time.monotonic() + 60.0
+            while inflight:
+                srv.step()
+                for rid in list(inflight):
+                    done, n = srv.poll(rid)
+                    if done:
+                        i, out = inflight.pop(rid)
+                        results[i] = (out.numpy().copy(), n)
+                assert time.monotonic() < t_end
+        except Exception as exc:
+            errors.append(exc)
+
+    threads = [threading.Thread(target=drive, args=lane) for lane in lanes]
+    for t in threads:
+        t.start()
+    for t in threads:
+        t.join()
+    assert not errors, errors
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        for i, (rgb, con, K) in enumerate(imgs):
+            s = S.Segmenter(rgb, con, K, storage="f16", stream=stream)
+            s.iterate(5)
+            ref, nref = s.labels(enforce=True)
+            out, n = results[i]
+            assert n == nref and np.array_equal(out, ref), i
+            s.close()
+    for srv, _ in lanes:
+        srv.close()
