@@ -124,7 +124,8 @@ class Clocks:
                 "samples": len(rows)}
 
 
-# Kernels per step: reload = set-up, sums, update, projection, candidate lists;
+# Kernels per step: reload = set-up (with the grid clusters' sums), update,
+# projection, candidate lists;
 # each iteration = assignment (with the sums), update, projection, candidate
 # lists.  The lists are one kernel up to 12,287 tiles, else a scan and a fill.
 FALLBACK_HBM_GBS = 6800.0
@@ -136,7 +137,7 @@ def list_launches(H: int, W: int) -> int:
 
 
 def reload_launches(H: int, W: int) -> int:
-    return 4 + list_launches(H, W)
+    return 3 + list_launches(H, W)
 
 
 def iter_launches(H: int, W: int) -> int:

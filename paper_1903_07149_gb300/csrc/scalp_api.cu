@@ -221,10 +221,10 @@ int load_inputs(scalp_ctx *c, const scalp_image *img, const scalp_contour *con)
         cs = c->W;
     }
     void *plane = c->ws + c->L.plane;
-    // set-up, then the initial update, projection and lists as programmatic
-    // launches (each waits for its predecessor before its first read)
+    // set-up (with the grid clusters' sums), then the initial update,
+    // projection and lists as programmatic launches (each waits for its
+    // predecessor before its first read)
     launch_setup(c->a, rgb, rs, cp, cs, c->p.storage, plane, c->st);
-    launch_accumulate(c->a, c->st, true);
     launch_update(c->a, 1, c->st, true);
     launch_project(c->a, 1, c->st, true);
     launch_lists(c->a, c->st, true);

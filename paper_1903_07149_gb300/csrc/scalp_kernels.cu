@@ -58,37 +58,52 @@ cudaError_t srgb_table(const float **table, cudaStream_t st)
     return cudaSuccess;
 }
 
-__global__ void k_setup(SolveArgs a, const uint8_t *__restrict__ rgb, long long rgb_stride,
-                        const float *__restrict__ contour, long long contour_stride, int storage,
-                        void *plane)
+// One warp per 32-pixel segment of a row (the warp-aggregated sums need a
+// warp-uniform base): CIELab, contour factor and grid label of each pixel,
+// then the integer sums of (1, x, y, L, a, b) of the grid clusters (the
+// update's input), from the values as stored (FP16-rounded in that format).
+__global__ void __launch_bounds__(256)
+    k_setup(SolveArgs a, const uint8_t *__restrict__ rgb, long long rgb_stride,
+            const float *__restrict__ contour, long long contour_stride, int storage, void *plane)
 {
     pdl_release();  // launched after memsets: nothing to wait for
     __shared__ float lin[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) lin[i] = a.lut[i];
     __syncthreads();
     const float inv_s2 = 1.0f / (a.sigma * a.sigma);
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < a.N;
-         p += (long long)gridDim.x * blockDim.x) {
-        // N <= 2^30: 32-bit division
-        const int y = (int)((unsigned)p / (unsigned)a.W), x = (int)p - y * a.W;
-        const float3 lab = srgb_to_lab(lin, rgb + y * rgb_stride + 3 * (long long)x);
-        const float L = lab.x, A = lab.y, Bb = lab.z;
-        float c = contour ? contour[y * contour_stride + x] : 0.0f;
-        float w = -expm1f(-(c * c) * inv_s2);  // 1 - exp(-C^2/sigma^2), Eq. 2
-        const long long q = (long long)y * a.pitch + x;
-        if (storage == 0) {
-            reinterpret_cast<float4 *>(plane)[q] = make_float4(L, A, Bb, w);
-        } else {
-            __half2 lo = __floats2half2_rn(L, A), hi = __floats2half2_rn(Bb, w);
-            uint2 u;
-            u.x = *reinterpret_cast<unsigned *>(&lo);
-            u.y = *reinterpret_cast<unsigned *>(&hi);
-            reinterpret_cast<uint2 *>(plane)[q] = u;
+    const unsigned segs_per_row = (unsigned)(a.W + 31) / 32u;
+    const unsigned n_segs = segs_per_row * (unsigned)a.H;  // <= N <= 2^30
+    const unsigned warps = gridDim.x * (blockDim.x / 32);
+    for (unsigned seg = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); seg < n_segs; seg += warps) {
+        const int y = (int)(seg / segs_per_row);
+        const int bx = (int)(seg - (unsigned)y * segs_per_row) * 32;
+        const int x = bx + (int)(threadIdx.x & 31);
+        const bool valid = x < a.W;
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        int lab = 0;
+        if (valid) {
+            const float3 c3 = srgb_to_lab(lin, rgb + y * rgb_stride + 3 * (long long)x);
+            const float c = contour ? contour[y * contour_stride + x] : 0.0f;
+            const float w = -expm1f(-(c * c) * inv_s2);  // 1 - exp(-C^2/sigma^2), Eq. 2
+            const long long q = (long long)y * a.pitch + x;
+            if (storage == 0) {
+                v = make_float4(c3.x, c3.y, c3.z, w);
+                reinterpret_cast<float4 *>(plane)[q] = v;
+            } else {
+                const __half2 lo = __floats2half2_rn(c3.x, c3.y), hi = __floats2half2_rn(c3.z, w);
+                uint2 u;
+                u.x = *reinterpret_cast<const unsigned *>(&lo);
+                u.y = *reinterpret_cast<const unsigned *>(&hi);
+                reinterpret_cast<uint2 *>(plane)[q] = u;
+                v = sample_value(u);
+            }
+            // Algorithm 1 initialisation: label = cell of the regular grid
+            const int cx = (int)((long long)x * a.nx / a.W);
+            const int cy = (int)((long long)y * a.ny / a.H);
+            lab = cy * a.nx + cx;
+            a.labels[(long long)y * a.W + x] = lab;
         }
-        // Algorithm 1 initialisation: label = cell of the regular grid
-        int cx = (int)((long long)x * a.nx / a.W);
-        int cy = (int)((long long)y * a.ny / a.H);
-        a.labels[p] = cy * a.nx + cx;
+        warp_aggregate_global(valid, lab, bx, y, x - bx, 0, v, a.acc);
     }
 }
 
@@ -197,42 +212,10 @@ void launch_setup(const SolveArgs &a, const uint8_t *rgb, long long rgb_stride,
                   const float *contour, long long contour_stride, int storage, void *plane,
                   cudaStream_t st)
 {
-    int blocks = (int)std::min<long long>(ceil_div_ll(a.N, 256), 152 * 8);
+    const int blocks = (int)std::min<long long>(ceil_div_ll(a.N, 256), 152 * 16);
     k_setup<<<blocks, 256, 0, st>>>(a, rgb, rgb_stride, contour, contour_stride, storage, plane);
 }
 
-// Integer sums of (1, x, y, L, a, b) per label (the means of the update).
-// Each warp takes a 32-pixel segment of one row, whose labels are mostly
-// equal, so the warp-aggregated sums need few reductions per warp.
-template <typename T>
-__global__ void __launch_bounds__(256) k_accumulate(SolveArgs a, const T *__restrict__ plane)
-{
-    pdl_wait();  // the plane and the grid labels
-    pdl_release();
-    const long long segs_per_row = (a.W + 31) / 32;
-    const long long n_segs = segs_per_row * a.H;
-    const long long warps = (long long)gridDim.x * (blockDim.x / 32);
-    for (long long seg = blockIdx.x * (long long)(blockDim.x / 32) + (threadIdx.x >> 5); seg < n_segs;
-         seg += warps) {
-        // warp-uniform loop: every lane takes part in the reductions
-        const int y = (int)(seg / segs_per_row);
-        const int bx = (int)(seg % segs_per_row) * 32;
-        const int x = bx + (threadIdx.x & 31);
-        const bool valid = x < a.W;
-        const long long p = (long long)y * a.W + x;
-        const int lab = valid ? a.labels[p] : 0;
-        const float4 v = valid ? fetch_sample<T>(plane + (long long)y * a.pitch + x)
-                               : make_float4(0, 0, 0, 0);
-        warp_aggregate_global(valid, lab, bx, y, x - bx, 0, v, a.acc);
-    }
-}
-
-void launch_accumulate(const SolveArgs &a, cudaStream_t st, bool pdl)
-{
-    const int blocks = (int)std::min<long long>(ceil_div_ll(a.N, 256), 152 * 16);
-    if (a.plane32) pdl_launch(pdl, k_accumulate<float4>, dim3(blocks), dim3(256), 0, st, a, a.plane32);
-    else pdl_launch(pdl, k_accumulate<uint2>, dim3(blocks), dim3(256), 0, st, a, a.plane16);
-}
 
 // ---------------------------------------------------------------------------
 // Windows.  Pixel p is a candidate of cluster k iff |x_p - x_k| <= r and

@@ -32,7 +32,9 @@ cudaError_t pdl_launch(bool pdl, void (*kernel)(Params...), dim3 grid, dim3 bloc
 void set_last_error(const char *msg);
 
 // Per-pixel set-up: CIELab (Sec. II-A), contour factor 1-exp(-C^2/sigma^2)
-// of Eq. 2, grid label.  rgb/contour are device pointers with row strides.
+// of Eq. 2, grid label, and the grid clusters' integer sums of (1, x, y, L,
+// a, b) into a.acc (zeroed by the caller).  rgb/contour are device pointers
+// with row strides.
 void launch_setup(const SolveArgs &a, const uint8_t *rgb, long long rgb_stride,
                   const float *contour, long long contour_stride, int storage,
                   void *plane, cudaStream_t st);
@@ -44,9 +46,6 @@ cudaError_t srgb_table(const float **table, cudaStream_t st);
 // one word of scratch.  rgb and out are device pointers.
 void launch_gradient_prior(const uint8_t *rgb, long long rgb_stride, int H, int W, const float *lut,
                            float *out, long long out_stride, unsigned *gmax, cudaStream_t st);
-// Integer sums of (1, x, y, L, a, b) by label into a.acc (initialisation and
-// every update).
-void launch_accumulate(const SolveArgs &a, cudaStream_t st, bool pdl = false);
 // Cluster update (Algorithm 1) from a.acc when from_acc (queueing projections,
 // Eq. 4), then windows, the cluster records and the tile counts.  The tile
 // counts and list cursors must be zero on entry.
