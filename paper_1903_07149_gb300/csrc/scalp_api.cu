@@ -130,6 +130,8 @@ struct scalp_ctx {
     bool graph_prof;       // graph records the profiling events
     bool profiling;
     std::vector<cudaEvent_t> ev_pool;  // pairs around each assignment launch
+    cudaStream_t side;     // captured iterations: the lists beside the projection
+    cudaEvent_t fork_ev, join_ev;
     int prof_pending;      // event pairs recorded and not yet read
     double prof_ms;
     long long prof_launches;
@@ -283,8 +285,56 @@ void enqueue_iteration(scalp_ctx *c, int slot, bool capturing)
     launch_assign(c->a, c->p.storage, c->smem, c->st, pdl);
     if (c->profiling) cudaEventRecordWithFlags(c->ev_pool[2 * slot + 1], c->st, flags);
     launch_update(c->a, 1, c->st, pdl);
-    launch_project(c->a, 0, c->st, pdl);
-    launch_lists(c->a, c->st, pdl);
+    if (capturing && c->side) {
+        // the candidate lists need only the windows the update wrote, not the
+        // projected endpoints: a second branch of the graph runs them beside
+        // the projection, and the next assignment waits for both
+        cudaEventRecord(c->fork_ev, c->st);
+        cudaStreamWaitEvent(c->side, c->fork_ev, 0);
+        launch_lists(c->a, c->side, false);
+        cudaEventRecord(c->join_ev, c->side);
+        launch_project(c->a, 0, c->st, pdl);
+        cudaStreamWaitEvent(c->st, c->join_ev, 0);
+    } else {
+        launch_project(c->a, 0, c->st, pdl);
+        launch_lists(c->a, c->st, pdl);
+    }
+}
+
+// The second stream and the fork/join events of captured iterations, made
+// before a capture begins (none: the iterations stay in one stream).
+void ensure_side_stream(scalp_ctx *c)
+{
+    if (c->side) return;
+    int prio = 0;
+    cudaStream_t t = nullptr;
+    cudaEvent_t f = nullptr, j = nullptr;
+    if (cudaStreamGetPriority(c->st, &prio) == cudaSuccess &&
+        cudaStreamCreateWithPriority(&t, cudaStreamNonBlocking, prio) == cudaSuccess &&
+        cudaEventCreateWithFlags(&f, cudaEventDisableTiming) == cudaSuccess &&
+        cudaEventCreateWithFlags(&j, cudaEventDisableTiming) == cudaSuccess) {
+        c->side = t;
+        c->fork_ev = f;
+        c->join_ev = j;
+        return;
+    }
+    if (t) cudaStreamDestroy(t);
+    if (f) cudaEventDestroy(f);
+    if (j) cudaEventDestroy(j);
+    cudaGetLastError();  // not sticky: the iterations run in one stream
+}
+
+// Host-side resources of a context (its enqueued work has completed).
+void free_ctx(scalp_ctx *c)
+{
+    if (c->graph_valid) cudaGraphExecDestroy(c->gexec);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->side) {
+        cudaStreamDestroy(c->side);
+        cudaEventDestroy(c->fork_ev);
+        cudaEventDestroy(c->join_ev);
+    }
+    delete c;
 }
 
 }  // namespace
@@ -435,6 +485,7 @@ int scalp_iterate(scalp_ctx *c, int32_t n)
             cudaGraphExecDestroy(c->gexec);
             c->graph_valid = false;
         }
+        ensure_side_stream(c);
         cudaGraph_t g;
         rc = cuda_check(c, cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal),
                         "begin capture");
@@ -700,10 +751,8 @@ const char *scalp_last_error(const scalp_ctx *c)
 void scalp_destroy(scalp_ctx *c)
 {
     if (!c) return;
-    cudaStreamSynchronize(c->st);
-    if (c->graph_valid) cudaGraphExecDestroy(c->gexec);
-    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
-    delete c;
+    cudaStreamSynchronize(c->st);  // a side branch joins back into this stream
+    free_ctx(c);
 }
 
 
@@ -827,9 +876,7 @@ int scalp_ctx_finish_labels(scalp_ctx *c, const CtxStatus *status, int32_t *n_la
 void scalp_ctx_release(scalp_ctx *c)
 {
     if (!c) return;
-    if (c->graph_valid) cudaGraphExecDestroy(c->gexec);
-    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
-    delete c;
+    free_ctx(c);
 }
 
 }  // namespace scalp

@@ -278,6 +278,9 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
     if (tid == 0) {  // this tile's list is read: ready the counts for the next update
         a.tile_count[tile] = 0;
         a.tile_cursor[tile] = 0;
+        // the last projection (and lists) completed before this launch: its
+        // queue starts again for the next update
+        if (tile == 0) a.ctr->nproj = 0;
     }
 
     // candidates sorted by cluster index (ranks of distinct ids); the id

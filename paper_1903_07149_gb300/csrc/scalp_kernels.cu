@@ -338,6 +338,11 @@ __device__ __forceinline__ void update_cluster(const SolveArgs &a, int k, int fr
     int2 e = a.st_end[k];
     bool check_projection = false;
     int label_at_end = k;
+    if (from_acc && k == 0) {
+        // the orphans of the assignment just finished decide the projection's
+        // region; the count starts again for the next assignment
+        a.ctr->proj_all = atomicExch(&a.ctr->orphans, 0) > 0;
+    }
     if (from_acc) {
         const ClusterAcc c = a.acc[k];
         a.acc[k] = ClusterAcc{};
@@ -417,7 +422,7 @@ __device__ __forceinline__ void project_cta(const SolveArgs &a, int whole_image,
 {
     __shared__ ProjBest s_best[PROJ_THREADS / 32];
     const int nproj = a.ctr->nproj;
-    const bool all = whole_image || a.ctr->orphans > 0;
+    const bool all = whole_image || a.ctr->proj_all;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double bound = (double)max(a.W, a.H);
     for (int j = j0; j < nproj; j += stride) {
@@ -507,8 +512,9 @@ void launch_project(const SolveArgs &a, int whole_image, cudaStream_t st, bool p
 // per (cluster, tile) slot files the cluster into each tile its window
 // overlaps, at tile_off[t] + (a per-tile cursor).  The assignment CTA of tile
 // t zeroes tile_count[t] and tile_cursor[t] once it has read its list (set-up
-// and set_state zero them on the host side).  The CTA that writes tile_off
-// also resets the per-iteration counters.
+// and set_state zero them on the host side).  The lists touch no other
+// counter, so they can run beside the projection: the update restarts the
+// orphan count and the assignment the projection queue.
 // ---------------------------------------------------------------------------
 // Exclusive scan of in[0, n) into out[0, n] (out[n] = total) by one CTA of
 // `threads` threads, each a contiguous chunk; s_warp holds 32 ints.
@@ -545,16 +551,12 @@ __device__ __forceinline__ void cta_scan(const int *in, int *out, int n, int thr
     __syncthreads();
 }
 
-// tile_off from the counts, the overflow check and the counter resets.
+// tile_off from the counts and the overflow check.
 __device__ __forceinline__ void publish_offsets(const SolveArgs &a, const int *off)
 {
     const int n = a.n_tx * a.n_ty;
     for (int i = threadIdx.x; i <= n; i += blockDim.x) a.tile_off[i] = off[i];
-    if (threadIdx.x == 0) {
-        if (off[n] > a.tile_cap) atomicExch(&a.ctr->error, ERR_TILE_LIST_OVERFLOW);
-        a.ctr->nproj = 0;
-        a.ctr->orphans = 0;
-    }
+    if (threadIdx.x == 0 && off[n] > a.tile_cap) atomicExch(&a.ctr->error, ERR_TILE_LIST_OVERFLOW);
 }
 
 constexpr int SCAN1_THREADS = 1024;
@@ -566,8 +568,6 @@ __device__ __forceinline__ void scan_tiles_cta(const SolveArgs &a)
     if (threadIdx.x == 0) {
         const int n = a.n_tx * a.n_ty;
         if (a.tile_off[n] > a.tile_cap) atomicExch(&a.ctr->error, ERR_TILE_LIST_OVERFLOW);
-        a.ctr->nproj = 0;
-        a.ctr->orphans = 0;
     }
 }
 

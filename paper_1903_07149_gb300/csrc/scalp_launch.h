@@ -52,7 +52,7 @@ void launch_gradient_prior(const uint8_t *rgb, long long rgb_stride, int H, int 
 void launch_update(const SolveArgs &a, int from_acc, cudaStream_t st, bool pdl = false);
 // Eq. 4 for the queued clusters; whole_image=1 searches every pixel.
 void launch_project(const SolveArgs &a, int whole_image, cudaStream_t st, bool pdl = false);
-// Per-tile candidate lists from the tile counts; resets per-iteration counters.
+// Per-tile candidate lists from the tile counts (no other state is touched).
 void launch_lists(const SolveArgs &a, cudaStream_t st, bool pdl = false);
 // Batch: the assignment of every tile of every image in one launch, and one
 // iteration's update, projection and candidate lists for every image.
