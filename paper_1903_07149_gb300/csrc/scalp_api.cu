@@ -907,6 +907,9 @@ struct scalp_batch {
     static constexpr int BATCH_STREAMS = 8;
     cudaStream_t sub[BATCH_STREAMS] = {};
     cudaEvent_t fork = nullptr, join[BATCH_STREAMS] = {};
+    // captured iterations: the candidate lists on a second branch
+    cudaStream_t it_side = nullptr;
+    cudaEvent_t it_fork = nullptr, it_join = nullptr;
 };
 
 namespace {
@@ -994,6 +997,12 @@ void scalp_batch_destroy(scalp_batch *b)
         if (b->join[s]) cudaEventDestroy(b->join[s]);
     }
     if (b->fork) cudaEventDestroy(b->fork);
+    if (b->it_side) {
+        cudaStreamSynchronize(b->it_side);
+        cudaStreamDestroy(b->it_side);
+        cudaEventDestroy(b->it_fork);
+        cudaEventDestroy(b->it_join);
+    }
     if (b->graph_valid) cudaGraphExecDestroy(b->gexec);
     for (scalp_ctx *c : b->ctx) scalp_destroy(c);
     delete b;
@@ -1108,10 +1117,12 @@ int scalp_batch_iterate(scalp_batch *b, int32_t n)
     if (!b) return batch_fail(SCALP_E_ARG, "batch is NULL");
     if (n < 0) return batch_fail(SCALP_E_ARG, "n must be >= 0");
     if (n == 0) return SCALP_OK;
+    bool capturing = false;
     auto enqueue = [&](int iters) {
         for (int i = 0; i < iters; ++i) {
             launch_assign_batch(b->bargs, b->storage, b->total_tiles, b->smem, b->st, true);
-            launch_batch_update(b->bargs, b->total_clusters, b->total_fill, b->st, true);
+            launch_batch_update(b->bargs, b->total_clusters, b->total_fill, b->st, true,
+                                capturing ? b->it_side : nullptr, b->it_fork, b->it_join);
         }
     };
     const bool graphs = b->use_graph && b->st != nullptr;
@@ -1121,10 +1132,30 @@ int scalp_batch_iterate(scalp_batch *b, int32_t n)
             cudaGraphExecDestroy(b->gexec);
             b->graph_valid = false;
         }
+        if (!b->it_side) {  // made before the capture; without it, one stream
+            int prio = 0;
+            cudaStream_t t = nullptr;
+            cudaEvent_t f = nullptr, j = nullptr;
+            if (cudaStreamGetPriority(b->st, &prio) == cudaSuccess &&
+                cudaStreamCreateWithPriority(&t, cudaStreamNonBlocking, prio) == cudaSuccess &&
+                cudaEventCreateWithFlags(&f, cudaEventDisableTiming) == cudaSuccess &&
+                cudaEventCreateWithFlags(&j, cudaEventDisableTiming) == cudaSuccess) {
+                b->it_side = t;
+                b->it_fork = f;
+                b->it_join = j;
+            } else {
+                if (t) cudaStreamDestroy(t);
+                if (f) cudaEventDestroy(f);
+                if (j) cudaEventDestroy(j);
+                cudaGetLastError();
+            }
+        }
         cudaGraph_t g;
         e = cudaStreamBeginCapture(b->st, cudaStreamCaptureModeThreadLocal);
         if (e != cudaSuccess) return batch_fail(SCALP_E_CUDA, "begin capture: %s", cudaGetErrorString(e));
+        capturing = true;
         enqueue(n);
+        capturing = false;
         const cudaError_t le = cudaGetLastError();
         e = cudaStreamEndCapture(b->st, &g);
         if (e == cudaSuccess && le != cudaSuccess) {

@@ -641,10 +641,21 @@ __global__ void k_fill_tiles_batch(BatchArgs b)
 }
 
 // One iteration's update, projection and list kernels for a whole batch.
-void launch_batch_update(const BatchArgs &b, int total_clusters, int total_fill, cudaStream_t st, bool pdl)
+void launch_batch_update(const BatchArgs &b, int total_clusters, int total_fill, cudaStream_t st, bool pdl,
+                         cudaStream_t side, cudaEvent_t fork, cudaEvent_t join)
 {
     if (b.count <= 0) return;
     pdl_launch(pdl, k_update_batch, dim3((total_clusters + 63) / 64), dim3(64), 0, st, b, 1);
+    if (side) {  // the lists on a second branch, beside the projection
+        cudaEventRecord(fork, st);
+        cudaStreamWaitEvent(side, fork, 0);
+        pdl_launch(false, k_scan_tiles_batch, dim3(b.count), dim3(SCAN1_THREADS), 0, side, b);
+        pdl_launch(true, k_fill_tiles_batch, dim3((total_fill + 255) / 256), dim3(256), 0, side, b);
+        cudaEventRecord(join, side);
+        pdl_launch(pdl, k_project_batch, dim3(b.count * PROJ_CTAS_PER_IMAGE), dim3(PROJ_THREADS), 0, st, b, 0);
+        cudaStreamWaitEvent(st, join, 0);
+        return;
+    }
     pdl_launch(pdl, k_project_batch, dim3(b.count * PROJ_CTAS_PER_IMAGE), dim3(PROJ_THREADS), 0, st, b, 0);
     pdl_launch(pdl, k_scan_tiles_batch, dim3(b.count), dim3(SCAN1_THREADS), 0, st, b);
     pdl_launch(pdl, k_fill_tiles_batch, dim3((total_fill + 255) / 256), dim3(256), 0, st, b);

@@ -60,7 +60,8 @@ void launch_assign_batch(const BatchArgs &b, int storage, int total_tiles, size_
                          cudaStream_t st, bool pdl = false);
 cudaError_t assign_batch_configure(int storage);
 void launch_batch_update(const BatchArgs &b, int total_clusters, int total_fill, cudaStream_t st,
-                         bool pdl = false);
+                         bool pdl = false, cudaStream_t side = nullptr, cudaEvent_t fork = nullptr,
+                         cudaEvent_t join = nullptr);
 // Assignment (Algorithm 1 inner loops, Eq. 1-3) with a.map_cap distance-map
 // pairs per CTA; smem_bytes = assign_smem_bytes(a.map_cap).
 void launch_assign(const SolveArgs &a, int storage, size_t smem_bytes, cudaStream_t st, bool pdl = false);
