@@ -1,6 +1,7 @@
 // scalp_api.cu -- the C ABI of libscalp (declared in include/scalp.h):
 // argument checks, workspace carving, kernel configuration, CUDA-graph replay
 // of one iteration, state I/O.  All device work is in the kernel files.
+#include <climits>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -177,6 +178,19 @@ int device_status(scalp_ctx *c)
 
 // Tile counts and list cursors start at zero before an update (the
 // assignment kernel re-zeroes each tile's pair after reading its list).
+// floor(v * cells / len) for 0 <= v < len equals the high word of
+// (v * cells) * ceil(2^32 / len) when (len - 1) * cells * len < 2^32: with
+// m = ceil(2^32 / len) = (2^32 + e) / len, 0 <= e < len, the product exceeds
+// v * cells / len by (v * cells) * e / (len * 2^32) < 1 / len, less than the
+// distance of v * cells / len to the next integer.  0 where that does not hold.
+unsigned grid_reciprocal(long long len, long long cells)
+{
+    if (len < 2) return 0;
+    const unsigned long long num = (unsigned long long)(len - 1) * (unsigned long long)cells;
+    if (num > 0xffffffffULL / (unsigned long long)len) return 0;
+    return (unsigned)((0x100000000ULL + (unsigned long long)len - 1) / (unsigned long long)len);
+}
+
 int zero_tile_counts(scalp_ctx *c)
 {
     const size_t bytes = sizeof(int) * (size_t)c->L.n_tx * c->L.n_ty;
@@ -184,7 +198,10 @@ int zero_tile_counts(scalp_ctx *c)
     return rc ? rc : cuda_check(c, cudaMemsetAsync(c->a.tile_cursor, 0, bytes, c->st), "memset");
 }
 
-int load_inputs(scalp_ctx *c, const scalp_image *img, const scalp_contour *con)
+// The inputs of the set-up on the device: the image (and contour) copied into
+// the workspace when they are on the host; the gradient prior computed from
+// the image when the context uses it.
+int stage_inputs(scalp_ctx *c, const scalp_image *img, const scalp_contour *con, SetupInput *in)
 {
     const uint8_t *rgb = img->rgb;
     long long rs = img->rgb_stride ? img->rgb_stride : 3LL * c->W;
@@ -209,24 +226,35 @@ int load_inputs(scalp_ctx *c, const scalp_image *img, const scalp_contour *con)
             cs = c->W;
         }
     }
+    if (c->p.prior == SCALP_PRIOR_GRADIENT) {
+        // the prior computed from the image, into the contour staging area
+        float *d_c = reinterpret_cast<float *>(c->ws + c->L.contour);
+        launch_gradient_prior(rgb, rs, c->H, c->W, c->a.lut, d_c, c->W, &c->a.ctr->prior_max, c->st);
+        rc = launch_check(c, "gradient prior");
+        if (rc) return rc;
+        cp = d_c;
+        cs = c->W;
+    }
+    *in = SetupInput{rgb, cp, rs, cs};
+    return SCALP_OK;
+}
+
+int load_inputs(scalp_ctx *c, const scalp_image *img, const scalp_contour *con)
+{
+    SetupInput in;
+    int rc = stage_inputs(c, img, con, &in);
+    if (rc) return rc;
     rc = cuda_check(c, cudaMemsetAsync(c->a.acc, 0, sizeof(ClusterAcc) * c->Keff, c->st), "memset");
     if (rc) return rc;
     rc = zero_tile_counts(c);
     if (rc) return rc;
     rc = cuda_check(c, cudaMemsetAsync(c->a.ctr, 0, sizeof(DevCounters), c->st), "memset");
     if (rc) return rc;
-    if (c->p.prior == SCALP_PRIOR_GRADIENT) {
-        // the prior computed from the image, into the contour staging area
-        float *d_c = reinterpret_cast<float *>(c->ws + c->L.contour);
-        launch_gradient_prior(rgb, rs, c->H, c->W, c->a.lut, d_c, c->W, &c->a.ctr->prior_max, c->st);
-        cp = d_c;
-        cs = c->W;
-    }
     void *plane = c->ws + c->L.plane;
     // set-up (with the grid clusters' sums), then the initial update,
     // projection and lists as programmatic launches (each waits for its
     // predecessor before its first read)
-    launch_setup(c->a, rgb, rs, cp, cs, c->p.storage, plane, c->st);
+    launch_setup(c->a, in.rgb, in.rgb_stride, in.contour, in.contour_stride, c->p.storage, plane, c->st);
     launch_update(c->a, 1, c->st, true);
     launch_project(c->a, 1, c->st, true);
     launch_lists(c->a, c->st, true);
@@ -241,6 +269,19 @@ int validate_image(const scalp_image *img, const scalp_contour *con, const char 
     if (img->rgb_stride != 0 && img->rgb_stride < 3LL * img->W) { *why = "rgb_stride < 3*W"; return 0; }
     if (con && con->data && con->stride != 0 && con->stride < img->W) { *why = "contour stride < W"; return 0; }
     return 1;
+}
+
+// The checks of a reload: a valid image of the context's size, and no
+// contour where the context computes its own prior.
+int check_reload(scalp_ctx *c, const scalp_image *image, const scalp_contour *contour)
+{
+    const char *why = nullptr;
+    if (!validate_image(image, contour, &why)) return fail(c, SCALP_E_ARG, "%s", why);
+    if (c->p.prior == SCALP_PRIOR_GRADIENT && contour && contour->data)
+        return fail(c, SCALP_E_ARG, "a contour was given with SCALP_PRIOR_GRADIENT");
+    if (image->H != c->H || image->W != c->W)
+        return fail(c, SCALP_E_ARG, "reload needs the same image size");
+    return SCALP_OK;
 }
 
 int ensure_events(scalp_ctx *c, size_t pairs)
@@ -412,6 +453,8 @@ int scalp_init(scalp_ctx **out, const scalp_image *image, const scalp_contour *c
     a.ms2 = (float)((double)m * (double)m * (double)K / (double)c->N);  // m^2 / r^2
     a.n_tx = L.n_tx; a.n_ty = L.n_ty;
     a.pitch = L.pitch;
+    a.grid_rcp_x = grid_reciprocal(W, c->nx);
+    a.grid_rcp_y = grid_reciprocal(H, c->ny);
     a.plane32 = params->storage == 0 ? reinterpret_cast<const float4 *>(c->ws + L.plane) : nullptr;
     a.plane16 = params->storage == 1 ? reinterpret_cast<const uint2 *>(c->ws + L.plane) : nullptr;
     a.labels = reinterpret_cast<int *>(c->ws + L.labels);
@@ -457,14 +500,9 @@ int scalp_init(scalp_ctx **out, const scalp_image *image, const scalp_contour *c
 
 int scalp_reload(scalp_ctx *c, const scalp_image *image, const scalp_contour *contour)
 {
-    const char *why = nullptr;
     if (!c) return fail(nullptr, SCALP_E_ARG, "ctx is NULL");
-    if (!validate_image(image, contour, &why)) return fail(c, SCALP_E_ARG, "%s", why);
-    if (c->p.prior == SCALP_PRIOR_GRADIENT && contour && contour->data)
-        return fail(c, SCALP_E_ARG, "a contour was given with SCALP_PRIOR_GRADIENT");
-    if (image->H != c->H || image->W != c->W)
-        return fail(c, SCALP_E_ARG, "reload needs the same image size");
-    return load_inputs(c, image, contour);
+    const int rc = check_reload(c, image, contour);
+    return rc ? rc : load_inputs(c, image, contour);
 }
 
 int scalp_iterate(scalp_ctx *c, int32_t n)
@@ -883,10 +921,57 @@ void scalp_ctx_release(scalp_ctx *c)
 
 // ---------------------------------------------------------------------------
 // Batches: many images of uneven size and K solved together.  Each image is an
-// ordinary context carved from the batch workspace; the iteration kernels of
-// all images run as one launch each (tiles, clusters and list slots of all
-// images in one flat index space), and n iterations replay as one CUDA graph.
+// ordinary context carved from the batch workspace; the set-up, the iteration
+// and the connectivity kernels of all images run as one launch each (tiles,
+// clusters, pixels and list slots of all images in one flat index space), and
+// n iterations replay as one CUDA graph.
 // ---------------------------------------------------------------------------
+
+// A small per-image table in device memory that the host rewrites between
+// calls (input or output pointers): uploaded through pinned staging, and only
+// when its contents changed.
+struct PinnedTable {
+    void *host = nullptr;  // pinned staging
+    void *dev = nullptr;
+    size_t bytes = 0;
+    cudaEvent_t ev = nullptr;  // the last upload has left the staging buffer
+    std::vector<unsigned char> last;
+    bool valid = false;
+
+    cudaError_t init(void *d, size_t n)
+    {
+        dev = d;
+        bytes = n;
+        cudaError_t e = cudaMallocHost(&host, n);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+        return e;
+    }
+    cudaError_t upload(const void *src, cudaStream_t st)
+    {
+        if (valid && std::memcmp(last.data(), src, bytes) == 0) return cudaSuccess;
+        valid = false;
+        cudaError_t e = cudaEventSynchronize(ev);
+        if (e != cudaSuccess) return e;
+        std::memcpy(host, src, bytes);
+        e = cudaMemcpyAsync(dev, host, bytes, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess) e = cudaEventRecord(ev, st);
+        if (e != cudaSuccess) return e;
+        last.assign(static_cast<const unsigned char *>(src), static_cast<const unsigned char *>(src) + bytes);
+        valid = true;
+        return cudaSuccess;
+    }
+    void release()
+    {
+        if (ev) {
+            cudaEventSynchronize(ev);
+            cudaEventDestroy(ev);
+        }
+        if (host) cudaFreeHost(host);
+        host = nullptr;
+        ev = nullptr;
+    }
+};
+
 struct scalp_batch {
     int count = 0;
     std::vector<scalp_ctx *> ctx;
@@ -895,15 +980,22 @@ struct scalp_batch {
     int use_graph = 1;
     unsigned char *ws = nullptr;
     BatchArgs bargs{};
-    int *d_gather = nullptr;     // count label counts + count x DevCounters, gathered
+    int *d_nlab = nullptr;          // per image: labels after the connectivity
+    DevCounters *d_ctr = nullptr;   // per image: counters, gathered for one read
     int total_tiles = 0, total_clusters = 0, total_fill = 0;
     size_t smem = 0;
     cudaGraphExec_t gexec{};
     bool graph_valid = false;
     int graph_n = 0;
-    // the per-image work of a reload or of the labels (set-up, connectivity,
-    // copies) fans out over BATCH_STREAMS streams: images are independent, and
-    // their small kernels would otherwise run one after another
+    // flat set-up and connectivity
+    const int *setup_base = nullptr;
+    int setup_total = 0;
+    CclBatch cb{};
+    int ccl_total[CCL_KINDS] = {};
+    PinnedTable in_table;   // SetupInput per image
+    PinnedTable out_table;  // int* per image
+    // the per-image copies of a reload or of the labels fan out over
+    // BATCH_STREAMS streams, and so does the gradient prior
     static constexpr int BATCH_STREAMS = 8;
     cudaStream_t sub[BATCH_STREAMS] = {};
     cudaEvent_t fork = nullptr, join[BATCH_STREAMS] = {};
@@ -948,14 +1040,32 @@ cudaError_t batch_fan_out(scalp_batch *b, F &&per_image)
     return e;
 }
 
-size_t batch_head_bytes(int count)
+// The batch's own head of the workspace, in carve order.
+struct BatchHead {
+    size_t args, tile, clus, fill, nlab, ctr, ccl_img, ccl_base[CCL_KINDS], setup_base, in, out, bytes;
+};
+
+BatchHead batch_head(int count)
 {
+    BatchHead h;
     size_t cur = 0;
-    carve(cur, (size_t)count * sizeof(SolveArgs));
-    for (int i = 0; i < 3; ++i) carve(cur, (size_t)(count + 1) * sizeof(int));
-    carve(cur, (size_t)count * (sizeof(int) + sizeof(DevCounters)));
-    return (cur + ALIGN - 1) & ~(ALIGN - 1);
+    const size_t prefix = (size_t)(count + 1) * sizeof(int);
+    h.args = carve(cur, (size_t)count * sizeof(SolveArgs));
+    h.tile = carve(cur, prefix);
+    h.clus = carve(cur, prefix);
+    h.fill = carve(cur, prefix);
+    h.nlab = carve(cur, (size_t)count * sizeof(int));
+    h.ctr = carve(cur, (size_t)count * sizeof(DevCounters));
+    h.ccl_img = carve(cur, (size_t)count * sizeof(CclImage));
+    for (int k = 0; k < CCL_KINDS; ++k) h.ccl_base[k] = carve(cur, prefix);
+    h.setup_base = carve(cur, prefix);
+    h.in = carve(cur, (size_t)count * sizeof(SetupInput));
+    h.out = carve(cur, (size_t)count * sizeof(int *));
+    h.bytes = (cur + ALIGN - 1) & ~(ALIGN - 1);
+    return h;
 }
+
+size_t batch_head_bytes(int count) { return batch_head(count).bytes; }
 
 int batch_fail(int code, const char *fmt, ...)
 {
@@ -1004,6 +1114,8 @@ void scalp_batch_destroy(scalp_batch *b)
         cudaEventDestroy(b->it_join);
     }
     if (b->graph_valid) cudaGraphExecDestroy(b->gexec);
+    b->in_table.release();
+    b->out_table.release();
     for (scalp_ctx *c : b->ctx) scalp_destroy(c);
     delete b;
 }
@@ -1035,15 +1147,21 @@ int scalp_batch_init(scalp_batch **out, int32_t count, const scalp_image *images
     b->storage = params->storage;
     b->use_graph = params->use_graph;
     b->ws = reinterpret_cast<unsigned char *>(params->workspace);
-    size_t cur = 0;
-    const size_t o_args = carve(cur, (size_t)count * sizeof(SolveArgs));
-    const size_t o_tile = carve(cur, (size_t)(count + 1) * sizeof(int));
-    const size_t o_clus = carve(cur, (size_t)(count + 1) * sizeof(int));
-    const size_t o_fill = carve(cur, (size_t)(count + 1) * sizeof(int));
-    const size_t o_gather = carve(cur, (size_t)count * (sizeof(int) + sizeof(DevCounters)));
-    size_t off = batch_head_bytes(count);
+    const BatchHead h = batch_head(count);
+    size_t off = h.bytes;
     std::vector<SolveArgs> args(count);
     std::vector<int> tile_base(count + 1, 0), clus_base(count + 1, 0), fill_base(count + 1, 0);
+    std::vector<int> setup_base(count + 1, 0);
+    std::vector<std::vector<int>> ccl_base(CCL_KINDS, std::vector<int>(count + 1, 0));
+    std::vector<CclImage> ccl_img(count);
+    b->d_nlab = reinterpret_cast<int *>(b->ws + h.nlab);
+    b->d_ctr = reinterpret_cast<DevCounters *>(b->ws + h.ctr);
+    bool too_large = false;
+    auto add = [&](std::vector<int> &base, int i, long long n) {
+        const long long v = base[i] + n;
+        too_large |= v > INT_MAX;
+        base[i + 1] = (int)std::min<long long>(v, INT_MAX);
+    };
     for (int i = 0; i < count; ++i) {
         scalp_params p = *params;
         p.use_graph = 0;
@@ -1060,32 +1178,68 @@ int scalp_batch_init(scalp_batch **out, int32_t count, const scalp_image *images
         }
         b->ctx.push_back(c);
         args[i] = c->a;
-        tile_base[i + 1] = tile_base[i] + c->a.n_tx * c->a.n_ty;
-        clus_base[i + 1] = clus_base[i] + c->Keff;
-        fill_base[i + 1] = fill_base[i] + c->Keff * c->a.tpw_x * c->a.tpw_y;
+        add(tile_base, i, (long long)c->a.n_tx * c->a.n_ty);
+        add(clus_base, i, c->Keff);
+        add(fill_base, i, (long long)c->Keff * c->a.tpw_x * c->a.tpw_y);
+        add(setup_base, i, setup_blocks(c->H, c->W));
+        long long blocks[CCL_KINDS];
+        ccl_batch_blocks(c->H, c->W, blocks);
+        for (int k = 0; k < CCL_KINDS; ++k) add(ccl_base[k], i, blocks[k]);
+        CclImage &m = ccl_img[i];
+        m.labels = c->a.labels;
+        m.parent = c->ccl.parent;
+        m.size = c->ccl.size;
+        m.link = c->ccl.link;
+        m.scan = c->ccl.scan;
+        m.scan_tmp = c->ccl.scan_tmp;
+        m.nlab = b->d_nlab + i;
+        m.ctr = c->a.ctr;
+        m.ctr_out = b->d_ctr + i;
+        m.N = c->N;
+        m.T = c->N / (4LL * c->K);
+        m.H = c->H;
+        m.W = c->W;
+        m.n_tx = (c->W + 31) / 32;
+        m.n_ty = (c->H + 31) / 32;
         b->smem = std::max(b->smem, c->smem);
+    }
+    if (too_large) {
+        scalp_batch_destroy(b);
+        return batch_fail(SCALP_E_ARG, "the batch has more than 2^31-1 blocks in one launch");
     }
     b->total_tiles = tile_base[count];
     b->total_clusters = clus_base[count];
     b->total_fill = fill_base[count];
-    b->bargs.args = reinterpret_cast<const SolveArgs *>(b->ws + o_args);
-    b->bargs.tile_base = reinterpret_cast<const int *>(b->ws + o_tile);
-    b->bargs.clus_base = reinterpret_cast<const int *>(b->ws + o_clus);
-    b->bargs.fill_base = reinterpret_cast<const int *>(b->ws + o_fill);
+    b->setup_total = setup_base[count];
+    b->bargs.args = reinterpret_cast<const SolveArgs *>(b->ws + h.args);
+    b->bargs.tile_base = reinterpret_cast<const int *>(b->ws + h.tile);
+    b->bargs.clus_base = reinterpret_cast<const int *>(b->ws + h.clus);
+    b->bargs.fill_base = reinterpret_cast<const int *>(b->ws + h.fill);
     b->bargs.count = count;
-    b->d_gather = reinterpret_cast<int *>(b->ws + o_gather);
-    cudaError_t e = cudaMemcpyAsync(b->ws + o_args, args.data(), count * sizeof(SolveArgs),
-                                    cudaMemcpyHostToDevice, b->st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->ws + o_tile, tile_base.data(), (count + 1) * sizeof(int),
-                            cudaMemcpyHostToDevice, b->st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->ws + o_clus, clus_base.data(), (count + 1) * sizeof(int),
-                            cudaMemcpyHostToDevice, b->st);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(b->ws + o_fill, fill_base.data(), (count + 1) * sizeof(int),
-                            cudaMemcpyHostToDevice, b->st);
+    b->setup_base = reinterpret_cast<const int *>(b->ws + h.setup_base);
+    b->cb.img = reinterpret_cast<const CclImage *>(b->ws + h.ccl_img);
+    b->cb.out = reinterpret_cast<int *const *>(b->ws + h.out);
+    for (int k = 0; k < CCL_KINDS; ++k) {
+        b->cb.base[k] = reinterpret_cast<const int *>(b->ws + h.ccl_base[k]);
+        b->ccl_total[k] = ccl_base[k][count];
+    }
+    b->cb.count = count;
+    const size_t prefix = (count + 1) * sizeof(int);
+    std::vector<std::pair<size_t, std::pair<const void *, size_t>>> copies = {
+        {h.args, {args.data(), count * sizeof(SolveArgs)}},
+        {h.tile, {tile_base.data(), prefix}},
+        {h.clus, {clus_base.data(), prefix}},
+        {h.fill, {fill_base.data(), prefix}},
+        {h.setup_base, {setup_base.data(), prefix}},
+        {h.ccl_img, {ccl_img.data(), count * sizeof(CclImage)}}};
+    for (int k = 0; k < CCL_KINDS; ++k) copies.push_back({h.ccl_base[k], {ccl_base[k].data(), prefix}});
+    cudaError_t e = cudaSuccess;
+    for (const auto &cp : copies)
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(b->ws + cp.first, cp.second.first, cp.second.second, cudaMemcpyHostToDevice, b->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);  // host vectors go out of scope
+    if (e == cudaSuccess) e = b->in_table.init(b->ws + h.in, count * sizeof(SetupInput));
+    if (e == cudaSuccess) e = b->out_table.init(b->ws + h.out, count * sizeof(int *));
     if (e == cudaSuccess) e = assign_batch_configure(b->storage);
     if (e != cudaSuccess) {
         scalp_batch_destroy(b);
@@ -1098,17 +1252,38 @@ int scalp_batch_init(scalp_batch **out, int32_t count, const scalp_image *images
 int scalp_batch_reload(scalp_batch *b, const scalp_image *images, const scalp_contour *contours)
 {
     if (!b || !images) return batch_fail(SCALP_E_ARG, "batch or images is NULL");
+    for (int i = 0; i < b->count; ++i) {
+        const int rc = check_reload(b->ctx[i], &images[i], contours ? &contours[i] : nullptr);
+        if (rc != SCALP_OK) return batch_fail(rc, "image %d: %s", i, b->ctx[i]->err.c_str());
+    }
+    // the inputs on the device (copies, gradient priors), per image
+    std::vector<SetupInput> in(b->count);
     int bad = -1, bad_rc = SCALP_OK;
-    const cudaError_t e = batch_fan_out(b, [&](int i) {
-        const int rc = scalp_reload(b->ctx[i], &images[i], contours ? &contours[i] : nullptr);
+    auto stage = [&](int i) {
+        const int rc = stage_inputs(b->ctx[i], &images[i], contours ? &contours[i] : nullptr, &in[i]);
         if (rc != SCALP_OK) {
             bad = i;
             bad_rc = rc;
         }
         return rc;
-    });
+    };
+    cudaError_t e = cudaSuccess;
+    if (b->ctx[0]->p.prior == SCALP_PRIOR_GRADIENT) {
+        e = batch_fan_out(b, stage);
+    } else {
+        for (int i = 0; i < b->count && bad < 0; ++i) stage(i);
+    }
     if (bad >= 0) return batch_fail(bad_rc, "image %d: %s", bad, b->ctx[bad]->err.c_str());
+    // then the set-up and the first update, projection and lists of all images
+    if (e == cudaSuccess) e = b->in_table.upload(in.data(), b->st);
+    if (e == cudaSuccess) {
+        launch_setup_batch(b->bargs, static_cast<const SetupInput *>(b->in_table.dev), b->setup_base,
+                           b->setup_total, b->storage, b->st);
+        launch_batch_update(b->bargs, b->total_clusters, b->total_fill, b->st, true, nullptr, nullptr, nullptr, 1);
+        e = cudaGetLastError();
+    }
     if (e != cudaSuccess) return batch_fail(SCALP_E_CUDA, "batch reload: %s", cudaGetErrorString(e));
+    for (scalp_ctx *c : b->ctx) c->iterations = 0;
     return SCALP_OK;
 }
 
@@ -1186,32 +1361,35 @@ int scalp_batch_labels(scalp_batch *b, int32_t *const *outs, int32_t out_on_devi
     if (!b || !outs) return batch_fail(SCALP_E_ARG, "batch or outs is NULL");
     for (int i = 0; i < b->count; ++i)
         if (!outs[i]) return batch_fail(SCALP_E_ARG, "outs[%d] is NULL", i);
-    int *d_nlab = b->d_gather;
-    DevCounters *d_ctr = reinterpret_cast<DevCounters *>(b->d_gather + b->count);
-    cudaError_t ce = cudaSuccess;
-    cudaError_t e = batch_fan_out(b, [&](int i) {
-        scalp_ctx *c = b->ctx[i];
-        const size_t bytes = sizeof(int) * (size_t)c->N;
-        cudaError_t r = cudaSuccess;
-        if (enforce) {
-            int *dst = out_on_device ? outs[i] : c->ccl.link;
-            int *c_nlab = reinterpret_cast<int *>(c->ws + c->L.nlab);
-            launch_ccl(c->a.labels, c->H, c->W, c->K, dst, c->ccl, c_nlab, c->a.ctr, c->st);
-            r = cudaGetLastError();
-            if (r == cudaSuccess && !out_on_device)
-                r = cudaMemcpyAsync(outs[i], dst, bytes, cudaMemcpyDeviceToHost, c->st);
-            if (r == cudaSuccess)
-                r = cudaMemcpyAsync(d_nlab + i, c_nlab, sizeof(int), cudaMemcpyDeviceToDevice, c->st);
-        } else {
-            r = cudaMemcpyAsync(outs[i], c->a.labels, bytes,
-                                out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st);
+    int *d_nlab = b->d_nlab;
+    DevCounters *d_ctr = b->d_ctr;
+    cudaError_t e = cudaSuccess;
+    if (enforce) {
+        // the connectivity of all images, one launch per pass, into the
+        // caller's buffers or the images' staging; the passes also gather
+        // the label counts and the counters
+        std::vector<int *> dst(b->count);
+        for (int i = 0; i < b->count; ++i) dst[i] = out_on_device ? outs[i] : b->ctx[i]->ccl.link;
+        e = b->out_table.upload(dst.data(), b->st);
+        if (e == cudaSuccess) {
+            launch_ccl_batch(b->cb, b->ccl_total, b->st);
+            e = cudaGetLastError();
         }
-        if (r == cudaSuccess)
-            r = cudaMemcpyAsync(d_ctr + i, c->a.ctr, sizeof(DevCounters), cudaMemcpyDeviceToDevice, c->st);
-        ce = r;
-        return r == cudaSuccess ? SCALP_OK : SCALP_E_CUDA;
-    });
-    if (ce != cudaSuccess) e = ce;
+        for (int i = 0; i < b->count && e == cudaSuccess && !out_on_device; ++i)
+            e = cudaMemcpyAsync(outs[i], dst[i], sizeof(int) * (size_t)b->ctx[i]->N, cudaMemcpyDeviceToHost, b->st);
+    } else {
+        cudaError_t ce = cudaSuccess;
+        e = batch_fan_out(b, [&](int i) {
+            scalp_ctx *c = b->ctx[i];
+            cudaError_t r = cudaMemcpyAsync(outs[i], c->a.labels, sizeof(int) * (size_t)c->N,
+                                            out_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->st);
+            if (r == cudaSuccess)
+                r = cudaMemcpyAsync(d_ctr + i, c->a.ctr, sizeof(DevCounters), cudaMemcpyDeviceToDevice, c->st);
+            ce = r;
+            return r == cudaSuccess ? SCALP_OK : SCALP_E_CUDA;
+        });
+        if (ce != cudaSuccess) e = ce;
+    }
     if (e != cudaSuccess) return batch_fail(SCALP_E_CUDA, "batch labels: %s", cudaGetErrorString(e));
     std::vector<int> nlab(b->count);
     std::vector<DevCounters> ctr(b->count);

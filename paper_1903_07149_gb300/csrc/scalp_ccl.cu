@@ -106,16 +106,14 @@ __device__ __forceinline__ void unite_local(int *sp, int a, int b)
 constexpr int CCL_LOCAL_THREADS = 256;
 constexpr int CCL_ROWS = CCL_TILE / (CCL_LOCAL_THREADS / 32);  // rows per warp
 
-__global__ void __launch_bounds__(CCL_LOCAL_THREADS)
-    k_ccl_local(const int *__restrict__ labels, int *parent, int *size, int H, int W, int n_tx)
+__device__ __forceinline__ void ccl_local(const int *__restrict__ labels, int *parent, int *size, int H, int W,
+                                          int n_tx, int tile)
 {
-    pdl_wait();  // the previous pass (or the labels) complete
-    pdl_release();
     __shared__ int sp[CCL_TILE * CCL_TILE];
     __shared__ int sl[CCL_TILE * CCL_TILE];
     __shared__ unsigned srun[CCL_TILE];  // per row: bit x set where a run starts
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int x0 = (blockIdx.x % n_tx) * CCL_TILE, y0 = (blockIdx.x / n_tx) * CCL_TILE;
+    const int x0 = (tile % n_tx) * CCL_TILE, y0 = (tile / n_tx) * CCL_TILE;
     const int x = x0 + lane;
     int lab[CCL_ROWS];
     bool valid[CCL_ROWS];
@@ -171,15 +169,14 @@ __global__ void __launch_bounds__(CCL_LOCAL_THREADS)
 }
 
 // Pass 2: unions across tile borders (left edge and top edge of each tile).
-__global__ void k_ccl_border(const int *__restrict__ labels, int *parent, int H, int W, int n_tx,
-                             int n_ty)
+// The passes from here on take their block index and block count as blk and
+// nblk (a batch gives each image its own range of blocks).
+__device__ __forceinline__ void ccl_border(const int *__restrict__ labels, int *parent, int H, int W, int n_tx,
+                                           int n_ty, unsigned blk, unsigned nblk)
 {
-    pdl_wait();  // the previous pass (or the labels) complete
-    pdl_release();
     const long long nv = (long long)(n_tx - 1) * H;  // vertical border pixels
     const long long nh = (long long)(n_ty - 1) * W;  // horizontal border pixels
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < nv + nh;
-         i += (long long)gridDim.x * blockDim.x) {
+    for (long long i = blk * (long long)blockDim.x + threadIdx.x; i < nv + nh; i += (long long)nblk * blockDim.x) {
         long long p, q;
         if (i < nv) {
             const int y = (int)(i / (n_tx - 1)), bx = (int)(i % (n_tx - 1)) + 1;
@@ -197,13 +194,11 @@ __global__ void k_ccl_border(const int *__restrict__ labels, int *parent, int H,
 
 // Roots and component sizes; the lanes of a warp (32 consecutive pixels, most
 // of them in one component) add their counts once per distinct root.
-__global__ void k_ccl_flatten_count(int *parent, int *size, long long N)
+__device__ __forceinline__ void ccl_flatten_count(int *parent, int *size, long long N, unsigned blk, unsigned nblk)
 {
-    pdl_wait();  // the previous pass (or the labels) complete
-    pdl_release();
     const int lane = threadIdx.x & 31;
-    const long long warps = (long long)gridDim.x * (blockDim.x / 32);
-    for (long long w = blockIdx.x * (long long)(blockDim.x / 32) + (threadIdx.x >> 5); w * 32 < N;
+    const long long warps = (long long)nblk * (blockDim.x / 32);
+    for (long long w = blk * (long long)(blockDim.x / 32) + (threadIdx.x >> 5); w * 32 < N;
          w += warps) {
         const long long p = w * 32 + lane;
         const bool valid = p < N;
@@ -222,14 +217,11 @@ __global__ void k_ccl_flatten_count(int *parent, int *size, long long N)
 
 // Four consecutive pixels per thread (one 16-byte load of their parents; the
 // buffers are 256-byte aligned).
-__global__ void k_ccl_link(const int *__restrict__ parent, const int *__restrict__ size, int *link,
-                           int W, long long N, long long T)
+__device__ __forceinline__ void ccl_link(const int *__restrict__ parent, const int *__restrict__ size, int *link,
+                                         int W, long long N, long long T, unsigned blk, unsigned nblk)
 {
-    pdl_wait();  // the previous pass (or the labels) complete
-    pdl_release();
     const long long quads = (N + 3) / 4;
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < quads;
-         g += (long long)gridDim.x * blockDim.x) {
+    for (long long g = blk * (long long)blockDim.x + threadIdx.x; g < quads; g += (long long)nblk * blockDim.x) {
         const long long s0 = 4 * g;
         int pv[4];
         if (s0 + 4 <= N) {
@@ -287,15 +279,13 @@ __device__ __forceinline__ int cta_sum(int v, int *s_warp)
 
 // final[s] = first non-small ancestor of seed s (written over size[]), and
 // per chunk the number of surviving components (seeds with final[s] == s).
-__global__ void __launch_bounds__(CCL_CHUNK_THREADS)
-    k_ccl_resolve_count(const int *__restrict__ parent, const int *__restrict__ link, int *final_id,
-                        long long N, DevCounters *ctr, int *chunk_count)
+__device__ __forceinline__ void ccl_resolve_count(const int *__restrict__ parent, const int *__restrict__ link,
+                                                  int *final_id, long long N, DevCounters *ctr, int *chunk_count,
+                                                  unsigned chunk)
 {
-    pdl_wait();  // the previous pass (or the labels) complete
-    pdl_release();
     __shared__ int s_warp[32];
     // CCL_PER consecutive pixels per thread, their parents loaded first
-    const long long base = blockIdx.x * (long long)CCL_CHUNK + (long long)threadIdx.x * CCL_PER;
+    const long long base = chunk * (long long)CCL_CHUNK + (long long)threadIdx.x * CCL_PER;
     int par[CCL_PER];
     load_run(parent, base, N, par);
     int cnt = 0;
@@ -318,17 +308,15 @@ __global__ void __launch_bounds__(CCL_CHUNK_THREADS)
         cnt += f == s;
     }
     cnt = cta_sum(cnt, s_warp);
-    if (threadIdx.x == 0) chunk_count[blockIdx.x] = cnt;
+    if (threadIdx.x == 0) chunk_count[chunk] = cnt;
 }
 
 // Exclusive scan of the chunk counts by one CTA (each thread a contiguous
 // run); *total receives the number of labels.
 constexpr int CCL_SCAN_THREADS = 1024;
 
-__global__ void __launch_bounds__(CCL_SCAN_THREADS) k_ccl_chunk_scan(int *counts, long long n, int *total)
+__device__ __forceinline__ void ccl_chunk_scan(int *counts, long long n, int *total)
 {
-    pdl_wait();  // the previous pass (or the labels) complete
-    pdl_release();
     __shared__ int s_warp[32];
     const long long per = (n + CCL_SCAN_THREADS - 1) / CCL_SCAN_THREADS;
     const long long b = threadIdx.x * per, e = min(n, b + per);
@@ -362,14 +350,12 @@ __global__ void __launch_bounds__(CCL_SCAN_THREADS) k_ccl_chunk_scan(int *counts
 
 // number[s] for each surviving seed s: its rank in raster order (the chunk's
 // offset plus the rank inside the chunk); only seeds are written.
-__global__ void __launch_bounds__(CCL_CHUNK_THREADS)
-    k_ccl_number(const int *__restrict__ parent, const int *__restrict__ final_id,
-                 const int *__restrict__ chunk_off, int *number, long long N)
+__device__ __forceinline__ void ccl_number(const int *__restrict__ parent, const int *__restrict__ final_id,
+                                           const int *__restrict__ chunk_off, int *number, long long N,
+                                           unsigned chunk)
 {
-    pdl_wait();  // the previous pass (or the labels) complete
-    pdl_release();
     __shared__ int s_warp[32];
-    const long long base = blockIdx.x * (long long)CCL_CHUNK + (long long)threadIdx.x * CCL_PER;
+    const long long base = chunk * (long long)CCL_CHUNK + (long long)threadIdx.x * CCL_PER;
     int par[CCL_PER];
     load_run(parent, base, N, par);
     unsigned flags = 0;
@@ -396,7 +382,7 @@ __global__ void __launch_bounds__(CCL_CHUNK_THREADS)
         s_warp[lane] = w;
     }
     __syncthreads();
-    int rank = chunk_off[blockIdx.x] + (wid ? s_warp[wid - 1] : 0) + incl - mine;
+    int rank = chunk_off[chunk] + (wid ? s_warp[wid - 1] : 0) + incl - mine;
     while (flags) {
         const int i = __ffs(flags) - 1;
         number[base + i] = rank++;
@@ -406,15 +392,13 @@ __global__ void __launch_bounds__(CCL_CHUNK_THREADS)
 
 // Four consecutive pixels per thread; the output is written as one 16-byte
 // store when the caller's buffer is 16-byte aligned.
-__global__ void k_ccl_out(const int *__restrict__ parent, const int *__restrict__ final_id,
-                          const int *__restrict__ number, int *out, long long N)
+__device__ __forceinline__ void ccl_out(const int *__restrict__ parent, const int *__restrict__ final_id,
+                                        const int *__restrict__ number, int *out, long long N, unsigned blk,
+                                        unsigned nblk)
 {
-    pdl_wait();  // the previous pass (or the labels) complete
-    pdl_release();
     const bool vec_out = (reinterpret_cast<uintptr_t>(out) & 15) == 0;
     const long long quads = (N + 3) / 4;
-    for (long long g = blockIdx.x * (long long)blockDim.x + threadIdx.x; g < quads;
-         g += (long long)gridDim.x * blockDim.x) {
+    for (long long g = blk * (long long)blockDim.x + threadIdx.x; g < quads; g += (long long)nblk * blockDim.x) {
         const long long s0 = 4 * g;
         if (s0 + 4 <= N) {
             const int4 q = reinterpret_cast<const int4 *>(parent)[g];
@@ -431,6 +415,169 @@ __global__ void k_ccl_out(const int *__restrict__ parent, const int *__restrict_
     }
 }
 
+// ---------------------------------------------------------------------------
+// Kernels: one image (block index and grid as above), or a batch, where each
+// pass gives every image its own range of blocks and a block finds its image
+// in the prefix of the per-image block counts.  Every pass is a programmatic
+// launch: its CTAs are placed while the previous pass drains and wait for it
+// before their first read.
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(CCL_LOCAL_THREADS)
+    k_ccl_local(const int *__restrict__ labels, int *parent, int *size, int H, int W, int n_tx)
+{
+    pdl_wait();
+    pdl_release();
+    ccl_local(labels, parent, size, H, W, n_tx, blockIdx.x);
+}
+
+__global__ void k_ccl_border(const int *__restrict__ labels, int *parent, int H, int W, int n_tx, int n_ty)
+{
+    pdl_wait();
+    pdl_release();
+    ccl_border(labels, parent, H, W, n_tx, n_ty, blockIdx.x, gridDim.x);
+}
+
+__global__ void k_ccl_flatten_count(int *parent, int *size, long long N)
+{
+    pdl_wait();
+    pdl_release();
+    ccl_flatten_count(parent, size, N, blockIdx.x, gridDim.x);
+}
+
+__global__ void k_ccl_link(const int *__restrict__ parent, const int *__restrict__ size, int *link, int W,
+                           long long N, long long T)
+{
+    pdl_wait();
+    pdl_release();
+    ccl_link(parent, size, link, W, N, T, blockIdx.x, gridDim.x);
+}
+
+__global__ void __launch_bounds__(CCL_CHUNK_THREADS)
+    k_ccl_resolve_count(const int *__restrict__ parent, const int *__restrict__ link, int *final_id,
+                        long long N, DevCounters *ctr, int *chunk_count)
+{
+    pdl_wait();
+    pdl_release();
+    ccl_resolve_count(parent, link, final_id, N, ctr, chunk_count, blockIdx.x);
+}
+
+__global__ void __launch_bounds__(CCL_SCAN_THREADS) k_ccl_chunk_scan(int *counts, long long n, int *total)
+{
+    pdl_wait();
+    pdl_release();
+    ccl_chunk_scan(counts, n, total);
+}
+
+__global__ void __launch_bounds__(CCL_CHUNK_THREADS)
+    k_ccl_number(const int *__restrict__ parent, const int *__restrict__ final_id,
+                 const int *__restrict__ chunk_off, int *number, long long N)
+{
+    pdl_wait();
+    pdl_release();
+    ccl_number(parent, final_id, chunk_off, number, N, blockIdx.x);
+}
+
+__global__ void k_ccl_out(const int *__restrict__ parent, const int *__restrict__ final_id,
+                          const int *__restrict__ number, int *out, long long N)
+{
+    pdl_wait();
+    pdl_release();
+    ccl_out(parent, final_id, number, out, N, blockIdx.x, gridDim.x);
+}
+
+// The image of this block in pass `kind`, and the block's place in its range.
+struct CclBlock {
+    int i;
+    unsigned blk, nblk;
+};
+
+__device__ __forceinline__ CclBlock ccl_block(const CclBatch &cb, int kind)
+{
+    const int *base = cb.base[kind];
+    const int g = (int)blockIdx.x;
+    const int i = batch_find(base, cb.count, g);
+    return {i, (unsigned)(g - base[i]), (unsigned)(base[i + 1] - base[i])};
+}
+
+__global__ void __launch_bounds__(CCL_LOCAL_THREADS) k_ccl_local_batch(CclBatch cb)
+{
+    pdl_wait();
+    pdl_release();
+    const CclBlock b = ccl_block(cb, CCL_KIND_TILES);
+    const CclImage &m = cb.img[b.i];
+    const unsigned tiles = (unsigned)(m.n_tx * m.n_ty);
+    for (unsigned t = b.blk; t < tiles; t += b.nblk) {
+        ccl_local(m.labels, m.parent, m.size, m.H, m.W, m.n_tx, (int)t);
+        __syncthreads();  // the shared arrays are reused by the next tile
+    }
+}
+
+__global__ void k_ccl_border_batch(CclBatch cb)
+{
+    pdl_wait();
+    pdl_release();
+    const CclBlock b = ccl_block(cb, CCL_KIND_BORDER);
+    const CclImage &m = cb.img[b.i];
+    ccl_border(m.labels, m.parent, m.H, m.W, m.n_tx, m.n_ty, b.blk, b.nblk);
+}
+
+__global__ void k_ccl_flatten_count_batch(CclBatch cb)
+{
+    pdl_wait();
+    pdl_release();
+    const CclBlock b = ccl_block(cb, CCL_KIND_PIXELS);
+    const CclImage &m = cb.img[b.i];
+    ccl_flatten_count(m.parent, m.size, m.N, b.blk, b.nblk);
+}
+
+__global__ void k_ccl_link_batch(CclBatch cb)
+{
+    pdl_wait();
+    pdl_release();
+    const CclBlock b = ccl_block(cb, CCL_KIND_QUADS);
+    const CclImage &m = cb.img[b.i];
+    ccl_link(m.parent, m.size, m.link, m.W, m.N, m.T, b.blk, b.nblk);
+}
+
+__global__ void __launch_bounds__(CCL_CHUNK_THREADS) k_ccl_resolve_count_batch(CclBatch cb)
+{
+    pdl_wait();
+    pdl_release();
+    const CclBlock b = ccl_block(cb, CCL_KIND_CHUNKS);
+    const CclImage &m = cb.img[b.i];
+    ccl_resolve_count(m.parent, m.link, m.size, m.N, m.ctr, m.scan_tmp, b.blk);
+}
+
+// One CTA per image; it also copies the image's counters (no later pass
+// writes them) to where the host gathers them.
+__global__ void __launch_bounds__(CCL_SCAN_THREADS) k_ccl_chunk_scan_batch(CclBatch cb)
+{
+    pdl_wait();
+    pdl_release();
+    const int i = blockIdx.x;
+    const CclImage &m = cb.img[i];
+    ccl_chunk_scan(m.scan_tmp, ceil_div_ll(m.N, CCL_CHUNK), m.nlab);
+    if (threadIdx.x == 0) *m.ctr_out = *m.ctr;
+}
+
+__global__ void __launch_bounds__(CCL_CHUNK_THREADS) k_ccl_number_batch(CclBatch cb)
+{
+    pdl_wait();
+    pdl_release();
+    const CclBlock b = ccl_block(cb, CCL_KIND_CHUNKS);
+    const CclImage &m = cb.img[b.i];
+    ccl_number(m.parent, m.size, m.scan_tmp, m.scan, m.N, b.blk);
+}
+
+__global__ void k_ccl_out_batch(CclBatch cb)
+{
+    pdl_wait();
+    pdl_release();
+    const CclBlock b = ccl_block(cb, CCL_KIND_QUADS);
+    const CclImage &m = cb.img[b.i];
+    ccl_out(m.parent, m.size, m.scan, cb.out[b.i], m.N, b.blk, b.nblk);
+}
+
 long long ccl_scan_tmp_len(long long N) { return ceil_div_ll(N, CCL_CHUNK) + 64; }
 
 void launch_ccl(const int *labels, int H, int W, int K, int *out, const CclBuffers &b, int *d_nlab,
@@ -441,8 +588,6 @@ void launch_ccl(const int *labels, int H, int W, int K, int *out, const CclBuffe
     const int blocks = (int)std::min<long long>(ceil_div_ll(N, CCL_THREADS), 152 * 16);
     const int qblocks = (int)std::min<long long>(ceil_div_ll((N + 3) / 4, CCL_THREADS), 152 * 16);
     const int n_tx = (W + CCL_TILE - 1) / CCL_TILE, n_ty = (H + CCL_TILE - 1) / CCL_TILE;
-    // eight passes, each a programmatic launch: its CTAs are placed while the
-    // previous pass drains and wait for it before their first read
     pdl_launch(true, k_ccl_local, dim3(n_tx * n_ty), dim3(CCL_LOCAL_THREADS), 0, st, labels, b.parent, b.size,
                H, W, n_tx);
     const long long nb = (long long)(n_tx - 1) * H + (long long)(n_ty - 1) * W;
@@ -460,6 +605,36 @@ void launch_ccl(const int *labels, int H, int W, int K, int *out, const CclBuffe
                (const int *)b.size, (const int *)b.scan_tmp, b.scan, N);
     pdl_launch(true, k_ccl_out, dim3(qblocks), dim3(CCL_THREADS), 0, st, (const int *)b.parent,
                (const int *)b.size, (const int *)b.scan, out, N);
+}
+
+// Blocks of one image per pass in a batch.  A block first finds its image, so
+// each takes several units (tiles, border pixels, 32-pixel runs, quads) to
+// pay for that lookup; chunks are large enough alone.
+constexpr int CCL_BATCH_TILES = 4, CCL_BATCH_BORDER = 4, CCL_BATCH_RUNS = 8, CCL_BATCH_QUADS = 8;
+
+void ccl_batch_blocks(int H, int W, long long blocks[CCL_KINDS])
+{
+    const long long N = (long long)H * W;
+    const long long n_tx = (W + CCL_TILE - 1) / CCL_TILE, n_ty = (H + CCL_TILE - 1) / CCL_TILE;
+    blocks[CCL_KIND_TILES] = ceil_div_ll(n_tx * n_ty, CCL_BATCH_TILES);
+    blocks[CCL_KIND_BORDER] = ceil_div_ll((n_tx - 1) * H + (n_ty - 1) * W, (long long)CCL_THREADS * CCL_BATCH_BORDER);
+    blocks[CCL_KIND_PIXELS] = ceil_div_ll(N, (long long)CCL_THREADS * CCL_BATCH_RUNS);  // warps of 32 pixels
+    blocks[CCL_KIND_QUADS] = ceil_div_ll((N + 3) / 4, (long long)CCL_THREADS * CCL_BATCH_QUADS);
+    blocks[CCL_KIND_CHUNKS] = ceil_div_ll(N, CCL_CHUNK);
+}
+
+void launch_ccl_batch(const CclBatch &cb, const int total[CCL_KINDS], cudaStream_t st)
+{
+    if (cb.count <= 0) return;
+    pdl_launch(true, k_ccl_local_batch, dim3(total[CCL_KIND_TILES]), dim3(CCL_LOCAL_THREADS), 0, st, cb);
+    if (total[CCL_KIND_BORDER] > 0)
+        pdl_launch(true, k_ccl_border_batch, dim3(total[CCL_KIND_BORDER]), dim3(CCL_THREADS), 0, st, cb);
+    pdl_launch(true, k_ccl_flatten_count_batch, dim3(total[CCL_KIND_PIXELS]), dim3(CCL_THREADS), 0, st, cb);
+    pdl_launch(true, k_ccl_link_batch, dim3(total[CCL_KIND_QUADS]), dim3(CCL_THREADS), 0, st, cb);
+    pdl_launch(true, k_ccl_resolve_count_batch, dim3(total[CCL_KIND_CHUNKS]), dim3(CCL_CHUNK_THREADS), 0, st, cb);
+    pdl_launch(true, k_ccl_chunk_scan_batch, dim3(cb.count), dim3(CCL_SCAN_THREADS), 0, st, cb);
+    pdl_launch(true, k_ccl_number_batch, dim3(total[CCL_KIND_CHUNKS]), dim3(CCL_CHUNK_THREADS), 0, st, cb);
+    pdl_launch(true, k_ccl_out_batch, dim3(total[CCL_KIND_QUADS]), dim3(CCL_THREADS), 0, st, cb);
 }
 
 }  // namespace scalp

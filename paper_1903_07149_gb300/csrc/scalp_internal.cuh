@@ -108,6 +108,10 @@ struct SolveArgs {
     int n_tx, n_ty;    // tiles
     int map_cap;       // distance-map pairs per assignment CTA (0: every path on the plane)
     int pitch;         // plane row pitch in pixels (>= W, multiple of 4)
+    // grid cell of the set-up, floor(x * nx / W) and floor(y * ny / H), as
+    // multiply-highs by these (ceil(2^32 / W), ceil(2^32 / H)) where that is
+    // exact; 0: divide
+    unsigned grid_rcp_x, grid_rcp_y;
     int count_samples;
     const float4 *plane32;   // (L, a, b, w) per pixel, row pitch `pitch` [FP32 storage]
     const uint2 *plane16;    // the same as 4 x fp16                   [FP16 storage]

@@ -62,19 +62,24 @@ cudaError_t srgb_table(const float **table, cudaStream_t st)
 // warp-uniform base): CIELab, contour factor and grid label of each pixel,
 // then the integer sums of (1, x, y, L, a, b) of the grid clusters (the
 // update's input), from the values as stored (FP16-rounded in that format).
-__global__ void __launch_bounds__(256)
-    k_setup(SolveArgs a, const uint8_t *__restrict__ rgb, long long rgb_stride,
-            const float *__restrict__ contour, long long contour_stride, int storage, void *plane)
+// Block blk of nblk; with wait_sums the block waits for its predecessor
+// launch (which zeroes the sums) only before its first addition.
+constexpr int SETUP_THREADS = 256;
+constexpr int SETUP_SEGS_PER_WARP = 16;  // batch form: the image lookup is paid once per block
+
+__device__ __forceinline__ void setup_pixels(const SolveArgs &a, const uint8_t *__restrict__ rgb,
+                                             long long rgb_stride, const float *__restrict__ contour,
+                                             long long contour_stride, int storage, void *plane, unsigned blk,
+                                             unsigned nblk, bool wait_sums)
 {
-    pdl_release();  // launched after memsets: nothing to wait for
     __shared__ float lin[256];
     for (int i = threadIdx.x; i < 256; i += blockDim.x) lin[i] = a.lut[i];
     __syncthreads();
     const float inv_s2 = 1.0f / (a.sigma * a.sigma);
     const unsigned segs_per_row = (unsigned)(a.W + 31) / 32u;
     const unsigned n_segs = segs_per_row * (unsigned)a.H;  // <= N <= 2^30
-    const unsigned warps = gridDim.x * (blockDim.x / 32);
-    for (unsigned seg = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5); seg < n_segs; seg += warps) {
+    const unsigned warps = nblk * (blockDim.x / 32);
+    for (unsigned seg = blk * (blockDim.x / 32) + (threadIdx.x >> 5); seg < n_segs; seg += warps) {
         const int y = (int)(seg / segs_per_row);
         const int bx = (int)(seg - (unsigned)y * segs_per_row) * 32;
         const int x = bx + (int)(threadIdx.x & 31);
@@ -98,13 +103,65 @@ __global__ void __launch_bounds__(256)
                 v = sample_value(u);
             }
             // Algorithm 1 initialisation: label = cell of the regular grid
-            const int cx = (int)((long long)x * a.nx / a.W);
-            const int cy = (int)((long long)y * a.ny / a.H);
+            const int cx = a.grid_rcp_x ? (int)__umulhi((unsigned)x * (unsigned)a.nx, a.grid_rcp_x)
+                                        : (int)((long long)x * a.nx / a.W);
+            const int cy = a.grid_rcp_y ? (int)__umulhi((unsigned)y * (unsigned)a.ny, a.grid_rcp_y)
+                                        : (int)((long long)y * a.ny / a.H);
             lab = cy * a.nx + cx;
             a.labels[(long long)y * a.W + x] = lab;
         }
+        if (wait_sums) {
+            pdl_wait();
+            wait_sums = false;
+        }
         warp_aggregate_global(valid, lab, bx, y, x - bx, 0, v, a.acc);
     }
+}
+
+__global__ void __launch_bounds__(SETUP_THREADS)
+    k_setup(SolveArgs a, const uint8_t *__restrict__ rgb, long long rgb_stride,
+            const float *__restrict__ contour, long long contour_stride, int storage, void *plane)
+{
+    pdl_release();  // launched after memsets: nothing to wait for
+    setup_pixels(a, rgb, rgb_stride, contour, contour_stride, storage, plane, blockIdx.x, gridDim.x, false);
+}
+
+// Batch: first every image's counters, cluster sums, tile counts and list
+// cursors zeroed (ZERO_BLOCKS CTAs per image), then the set-up with each image
+// in its own range of blocks.  The set-up is placed once the zeroing has waited
+// for the work before it (the zeroing waits before it releases), converts its
+// pixels meanwhile and waits for the zeroing before its first addition.
+constexpr int ZERO_BLOCKS = 4;
+
+__global__ void k_zero_batch(BatchArgs b)
+{
+    pdl_wait();
+    pdl_release();
+    const SolveArgs a = b.args[blockIdx.x / ZERO_BLOCKS];
+    const int t0 = (int)(blockIdx.x % ZERO_BLOCKS) * blockDim.x + threadIdx.x;
+    const int step = ZERO_BLOCKS * blockDim.x;
+    static_assert(sizeof(ClusterAcc) % sizeof(int4) == 0, "cluster sums are cleared as int4");
+    const int acc4 = a.Keff * (int)(sizeof(ClusterAcc) / sizeof(int4));
+    for (int j = t0; j < acc4; j += step) reinterpret_cast<int4 *>(a.acc)[j] = make_int4(0, 0, 0, 0);
+    const int tiles = a.n_tx * a.n_ty;
+    for (int j = t0; j < tiles; j += step) {
+        a.tile_count[j] = 0;
+        a.tile_cursor[j] = 0;
+    }
+    for (int j = t0; j < (int)(sizeof(DevCounters) / sizeof(int)); j += step) reinterpret_cast<int *>(a.ctr)[j] = 0;
+}
+
+__global__ void __launch_bounds__(SETUP_THREADS)
+    k_setup_batch(BatchArgs b, const SetupInput *__restrict__ in, const int *__restrict__ setup_base, int storage)
+{
+    pdl_release();
+    const int g = (int)blockIdx.x;
+    const int i = batch_find(setup_base, b.count, g);
+    const SolveArgs a = b.args[i];
+    const SetupInput u = in[i];
+    void *plane = storage == 0 ? (void *)a.plane32 : (void *)a.plane16;
+    setup_pixels(a, u.rgb, u.rgb_stride, u.contour, u.contour_stride, storage, plane,
+                 (unsigned)(g - setup_base[i]), (unsigned)(setup_base[i + 1] - setup_base[i]), true);
 }
 
 
@@ -212,8 +269,23 @@ void launch_setup(const SolveArgs &a, const uint8_t *rgb, long long rgb_stride,
                   const float *contour, long long contour_stride, int storage, void *plane,
                   cudaStream_t st)
 {
-    const int blocks = (int)std::min<long long>(ceil_div_ll(a.N, 256), 152 * 16);
-    k_setup<<<blocks, 256, 0, st>>>(a, rgb, rgb_stride, contour, contour_stride, storage, plane);
+    const int blocks = (int)std::min<long long>(ceil_div_ll(a.N, SETUP_THREADS), 152 * 16);
+    k_setup<<<blocks, SETUP_THREADS, 0, st>>>(a, rgb, rgb_stride, contour, contour_stride, storage, plane);
+}
+
+long long setup_blocks(int H, int W)
+{
+    const long long segs = (long long)((W + 31) / 32) * H;
+    return ceil_div_ll(segs, (long long)(SETUP_THREADS / 32) * SETUP_SEGS_PER_WARP);
+}
+
+void launch_setup_batch(const BatchArgs &b, const SetupInput *in, const int *setup_base, int total_blocks,
+                        int storage, cudaStream_t st)
+{
+    if (b.count <= 0) return;
+    pdl_launch(true, k_zero_batch, dim3((unsigned)(b.count * ZERO_BLOCKS)), dim3(256), 0, st, b);
+    pdl_launch(true, k_setup_batch, dim3((unsigned)total_blocks), dim3(SETUP_THREADS), 0, st, b, in, setup_base,
+               storage);
 }
 
 
@@ -642,7 +714,7 @@ __global__ void k_fill_tiles_batch(BatchArgs b)
 
 // One iteration's update, projection and list kernels for a whole batch.
 void launch_batch_update(const BatchArgs &b, int total_clusters, int total_fill, cudaStream_t st, bool pdl,
-                         cudaStream_t side, cudaEvent_t fork, cudaEvent_t join)
+                         cudaStream_t side, cudaEvent_t fork, cudaEvent_t join, int whole_image)
 {
     if (b.count <= 0) return;
     pdl_launch(pdl, k_update_batch, dim3((total_clusters + 63) / 64), dim3(64), 0, st, b, 1);
@@ -652,11 +724,13 @@ void launch_batch_update(const BatchArgs &b, int total_clusters, int total_fill,
         pdl_launch(false, k_scan_tiles_batch, dim3(b.count), dim3(SCAN1_THREADS), 0, side, b);
         pdl_launch(true, k_fill_tiles_batch, dim3((total_fill + 255) / 256), dim3(256), 0, side, b);
         cudaEventRecord(join, side);
-        pdl_launch(pdl, k_project_batch, dim3(b.count * PROJ_CTAS_PER_IMAGE), dim3(PROJ_THREADS), 0, st, b, 0);
+        pdl_launch(pdl, k_project_batch, dim3(b.count * PROJ_CTAS_PER_IMAGE), dim3(PROJ_THREADS), 0, st, b,
+                   whole_image);
         cudaStreamWaitEvent(st, join, 0);
         return;
     }
-    pdl_launch(pdl, k_project_batch, dim3(b.count * PROJ_CTAS_PER_IMAGE), dim3(PROJ_THREADS), 0, st, b, 0);
+    pdl_launch(pdl, k_project_batch, dim3(b.count * PROJ_CTAS_PER_IMAGE), dim3(PROJ_THREADS), 0, st, b,
+               whole_image);
     pdl_launch(pdl, k_scan_tiles_batch, dim3(b.count), dim3(SCAN1_THREADS), 0, st, b);
     pdl_launch(pdl, k_fill_tiles_batch, dim3((total_fill + 255) / 256), dim3(256), 0, st, b);
 }

@@ -61,7 +61,7 @@ void launch_assign_batch(const BatchArgs &b, int storage, int total_tiles, size_
 cudaError_t assign_batch_configure(int storage);
 void launch_batch_update(const BatchArgs &b, int total_clusters, int total_fill, cudaStream_t st,
                          bool pdl = false, cudaStream_t side = nullptr, cudaEvent_t fork = nullptr,
-                         cudaEvent_t join = nullptr);
+                         cudaEvent_t join = nullptr, int whole_image = 0);
 // Assignment (Algorithm 1 inner loops, Eq. 1-3) with a.map_cap distance-map
 // pairs per CTA; smem_bytes = assign_smem_bytes(a.map_cap).
 void launch_assign(const SolveArgs &a, int storage, size_t smem_bytes, cudaStream_t st, bool pdl = false);
@@ -82,6 +82,41 @@ struct CclBuffers {
 long long ccl_scan_tmp_len(long long N);
 void launch_ccl(const int *labels, int H, int W, int K, int *out, const CclBuffers &b,
                 int *d_nlab, DevCounters *ctr, cudaStream_t st);
+
+// Connectivity of a whole batch, one launch per pass.  Each pass gives every
+// image a range of blocks; base[kind] (count+1 ints) is the prefix of the
+// per-image block counts ccl_batch_blocks() returns.
+enum { CCL_KIND_TILES, CCL_KIND_BORDER, CCL_KIND_PIXELS, CCL_KIND_QUADS, CCL_KIND_CHUNKS, CCL_KINDS };
+struct CclImage {
+    const int *labels;
+    int *parent, *size, *link, *scan, *scan_tmp;  // the image's CclBuffers
+    int *nlab;                 // receives the number of labels
+    DevCounters *ctr;          // the image's counters (error flags are raised here)
+    DevCounters *ctr_out;      // a copy of them once the connectivity has run
+    long long N, T;            // pixels, small-component bound floor(N / (4K))
+    int H, W, n_tx, n_ty;      // n_tx, n_ty: 32 x 32 tiles
+};
+struct CclBatch {
+    const CclImage *img;
+    int *const *out;           // per image: where its final labels go
+    const int *base[CCL_KINDS];
+    int count;
+};
+void ccl_batch_blocks(int H, int W, long long blocks[CCL_KINDS]);
+void launch_ccl_batch(const CclBatch &cb, const int total[CCL_KINDS], cudaStream_t st);
+
+// Set-up of a whole batch (device-side inputs of each image; contour NULL for
+// none): the image's counters, cluster sums, tile counts and list cursors
+// zeroed, then the per-pixel set-up of launch_setup, one launch each.
+// setup_base (count+1 ints) is the prefix of setup_blocks() per image.
+struct SetupInput {
+    const uint8_t *rgb;
+    const float *contour;
+    long long rgb_stride, contour_stride;
+};
+long long setup_blocks(int H, int W);
+void launch_setup_batch(const BatchArgs &b, const SetupInput *in, const int *setup_base, int total_blocks,
+                        int storage, cudaStream_t st);
 
 // Per-context accessors used by the serving loop.
 SolveArgs scalp_ctx_args(const scalp_ctx *c);

@@ -469,8 +469,9 @@ def scalp_batch_destroy(batch):
 class Batch:
     """Many SCALP solves of uneven size on the current CUDA device.
 
-    rgbs: list of (H_i, W_i, 3) uint8 CUDA tensors; contours: list of (H_i, W_i)
-    float32 CUDA tensors or None; Ks: list of K_i.
+    rgbs: list of (H_i, W_i, 3) uint8 CUDA tensors (or numpy arrays in host
+    memory, copied in by the library); contours: list of (H_i, W_i) float32
+    arrays on the same side, or None; Ks: list of K_i.
     """
 
     def __init__(self, rgbs, contours, Ks, m: float = 10.0, lam: float = 0.5, sigma: float = 0.25,
@@ -506,10 +507,19 @@ class Batch:
         torch = self._torch
         keep, imgs, cons = [], [], []
         for i, r in enumerate(rgbs):
+            c = None if contours is None else contours[i]
+            if isinstance(r, np.ndarray):
+                r = np.ascontiguousarray(r, dtype=np.uint8)
+                keep.append(r)
+                imgs.append(scalp_image(r.shape[0], r.shape[1], r.ctypes.data, 0, 0))
+                if c is not None:
+                    c = np.ascontiguousarray(c, dtype=np.float32)
+                    keep.append(c)
+                cons.append(scalp_contour(None if c is None else c.ctypes.data, 0))
+                continue
             r = r.contiguous()
             keep.append(r)
             imgs.append(scalp_image(r.shape[0], r.shape[1], r.data_ptr(), 0, 1))
-            c = None if contours is None else contours[i]
             if c is None:
                 cons.append(scalp_contour(None, 0))
             else:

@@ -27,12 +27,12 @@ def S():
     return scalp
 
 
-def _inputs():
+def _inputs(seed=500):
     import torch
 
     rgbs, cons = [], []
     for i, (H, W, K) in enumerate(SIZES):
-        rgb, con, _ = synth.small_image(H, W, seed=500 + i, n_cells=max(2, H * W // 3000))
+        rgb, con, _ = synth.small_image(H, W, seed=seed + i, n_cells=max(2, H * W // 3000))
         rgbs.append(torch.from_numpy(rgb).cuda())
         cons.append(torch.from_numpy(con).cuda())
     return rgbs, cons
@@ -83,4 +83,76 @@ def test_batch_reload_and_device_outputs(S):
         assert np.array_equal(n1, n2)
         for a_, b_ in zip(first, second):
             assert np.array_equal(a_, b_.cpu().numpy())
+        b.close()
+
+
+def test_batch_reload_new_and_host_inputs(S):
+    """A batch set up on one set of images and reloaded with another of the
+    same sizes gives what each new image gives alone, into device buffers that
+    change between calls and into host memory; reloaded from host copies of
+    the first set, it gives the first result again."""
+    import torch
+
+    rgbs_a, cons_a = _inputs(500)
+    rgbs_b, cons_b = _inputs(900)
+    Ks = [k for _, _, k in SIZES]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = S.Batch(rgbs_a, cons_a, Ks, stream=stream)
+        b.iterate(3)
+        first, n_first = b.labels(enforce=True)
+        b.reload(rgbs_b, cons_b)
+        b.iterate(3)
+        raw, _ = b.labels(enforce=False)
+        outs1 = [torch.full(r.shape[:2], -7, dtype=torch.int32, device="cuda") for r in rgbs_b]
+        outs2 = [torch.full(r.shape[:2], -7, dtype=torch.int32, device="cuda") for r in rgbs_b]
+        _, n1 = b.labels(enforce=True, outs=outs1)
+        _, n2 = b.labels(enforce=True, outs=outs2)
+        host, n3 = b.labels(enforce=True)
+        for i, (H, W, K) in enumerate(SIZES):
+            s = S.Segmenter(rgbs_b[i], cons_b[i], K, stream=stream)
+            s.iterate(3)
+            lab, _ = s.labels(enforce=False)
+            assert np.array_equal(raw[i], lab), i
+            out, n = s.labels(enforce=True)
+            assert n == n1[i] == n2[i] == n3[i], i
+            assert np.array_equal(outs1[i].cpu().numpy(), out), i
+            assert np.array_equal(outs2[i].cpu().numpy(), out), i
+            assert np.array_equal(host[i], out), i
+            s.close()
+        b.reload([r.cpu().numpy() for r in rgbs_a], [c.cpu().numpy() for c in cons_a])
+        b.iterate(3)
+        again, n_again = b.labels(enforce=True)
+        assert np.array_equal(n_first, n_again)
+        for x, y in zip(first, again):
+            assert np.array_equal(x, y)
+        b.close()
+
+
+def test_batch_gradient_prior(S):
+    """With the prior computed from each image (an odd number of images), a
+    batch gives what each image gives alone, also after a reload."""
+    import torch
+
+    rgbs, _ = _inputs(700)
+    sizes = SIZES[:5]
+    rgbs = rgbs[:5]
+    Ks = [k for _, _, k in sizes]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = S.Batch(rgbs, None, Ks, stream=stream, prior="gradient")
+        b.iterate(4)
+        first, n_first = b.labels(enforce=True)
+        b.reload(rgbs, None)
+        b.iterate(4)
+        again, n_again = b.labels(enforce=True)
+        assert np.array_equal(n_first, n_again)
+        for i, (H, W, K) in enumerate(sizes):
+            s = S.Segmenter(rgbs[i], None, K, stream=stream, prior="gradient")
+            s.iterate(4)
+            out, n = s.labels(enforce=True)
+            assert n == n_first[i], i
+            assert np.array_equal(first[i], out), i
+            assert np.array_equal(again[i], out), i
+            s.close()
         b.close()
