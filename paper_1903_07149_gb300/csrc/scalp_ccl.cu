@@ -193,51 +193,104 @@ __device__ __forceinline__ void ccl_border(const int *__restrict__ labels, int *
 }
 
 // Roots and component sizes; the lanes of a warp (32 consecutive pixels, most
-// of them in one component) add their counts once per distinct root.
+// of them in one component) add their counts once per distinct root.  A warp
+// takes CCL_FLAT_RUNS runs of 32 pixels at once and follows their parent
+// pointers in lockstep, so that many loads are in flight.  No union happens
+// any more: the forest is fixed and the writes here only shorten paths, so
+// any pointer value read leads to the same root.
+constexpr int CCL_FLAT_RUNS = 4;
+
 __device__ __forceinline__ void ccl_flatten_count(int *parent, int *size, long long N, unsigned blk, unsigned nblk)
 {
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)nblk * (blockDim.x / 32);
-    for (long long w = blk * (long long)(blockDim.x / 32) + (threadIdx.x >> 5); w * 32 < N;
-         w += warps) {
-        const long long p = w * 32 + lane;
-        const bool valid = p < N;
-        int r = -1;
-        if (valid) {
-            r = find_root(parent, (int)p);
-            parent[p] = r;
+    for (long long w0 = blk * (long long)(blockDim.x / 32) + (threadIdx.x >> 5); w0 * 32 < N;
+         w0 += warps * CCL_FLAT_RUNS) {
+        int x[CCL_FLAT_RUNS];
+#pragma unroll
+        for (int u = 0; u < CCL_FLAT_RUNS; ++u) {
+            const long long p = (w0 + u * warps) * 32 + lane;
+            x[u] = p < N ? parent[p] : -1;
         }
-        const unsigned act = __ballot_sync(0xffffffffu, valid);
-        if (valid) {
-            const unsigned grp = __match_any_sync(act, r);
-            if (lane == __ffs(grp) - 1) atomicAdd(&size[r], __popc(grp));
+        bool more = true;
+        while (more) {
+            int nx[CCL_FLAT_RUNS];
+#pragma unroll
+            for (int u = 0; u < CCL_FLAT_RUNS; ++u) nx[u] = x[u] >= 0 ? parent[x[u]] : -1;
+            more = false;
+#pragma unroll
+            for (int u = 0; u < CCL_FLAT_RUNS; ++u) {
+                more |= nx[u] != x[u];
+                x[u] = nx[u];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < CCL_FLAT_RUNS; ++u) {
+            const long long p = (w0 + u * warps) * 32 + lane;
+            const bool valid = p < N;
+            if (valid) parent[p] = x[u];
+            const unsigned act = __ballot_sync(0xffffffffu, valid);
+            if (valid) {
+                const unsigned grp = __match_any_sync(act, x[u]);
+                if (lane == __ffs(grp) - 1) atomicAdd(&size[x[u]], __popc(grp));
+            }
         }
     }
 }
 
 // Four consecutive pixels per thread (one 16-byte load of their parents; the
 // buffers are 256-byte aligned).
+// The four parents from quad g (16-byte aligned buffers); -1 past N.
+__device__ __forceinline__ int4 load_quad(const int *__restrict__ a, long long g, long long N)
+{
+    const long long s0 = 4 * g;
+    if (s0 + 4 <= N) return reinterpret_cast<const int4 *>(a)[g];
+    return make_int4(s0 < N ? a[s0] : -1, s0 + 1 < N ? a[s0 + 1] : -1, s0 + 2 < N ? a[s0 + 2] : -1,
+                     s0 + 3 < N ? a[s0 + 3] : -1);
+}
+
+// Quads per thread and round in the passes below: their loads are issued
+// together before any is used.
+constexpr int CCL_QUAD_ROUND = 4;
+
 __device__ __forceinline__ void ccl_link(const int *__restrict__ parent, const int *__restrict__ size, int *link,
                                          int W, long long N, long long T, unsigned blk, unsigned nblk)
 {
-    const long long quads = (N + 3) / 4;
-    for (long long g = blk * (long long)blockDim.x + threadIdx.x; g < quads; g += (long long)nblk * blockDim.x) {
-        const long long s0 = 4 * g;
-        int pv[4];
-        if (s0 + 4 <= N) {
-            const int4 q = reinterpret_cast<const int4 *>(parent)[g];
-            pv[0] = q.x; pv[1] = q.y; pv[2] = q.z; pv[3] = q.w;
-        } else {
+    const long long quads = (N + 3) / 4, stride = (long long)nblk * blockDim.x;
+    for (long long g0 = blk * (long long)blockDim.x + threadIdx.x; g0 < quads; g0 += stride * CCL_QUAD_ROUND) {
+        int4 q[CCL_QUAD_ROUND];
 #pragma unroll
-            for (int i = 0; i < 4; ++i) pv[i] = s0 + i < N ? parent[s0 + i] : -1;
+        for (int u = 0; u < CCL_QUAD_ROUND; ++u) {
+            const long long g = g0 + u * stride;
+            q[u] = g < quads ? load_quad(parent, g, N) : make_int4(-1, -1, -1, -1);
+        }
+        // the sizes of the same quads, streamed alike (only seeds' entries
+        // are meaningful)
+        int4 z[CCL_QUAD_ROUND];
+#pragma unroll
+        for (int u = 0; u < CCL_QUAD_ROUND; ++u) {
+            const long long g = g0 + u * stride;
+            z[u] = g < quads ? load_quad(size, g, N) : make_int4(0, 0, 0, 0);
         }
 #pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            const long long s = s0 + i;
-            if (pv[i] != s) continue;
-            const bool small = size[s] <= T && s != 0;
-            const long long nb = ((int)s % W) > 0 ? s - 1 : s - W;  // N <= 2^30
-            link[s] = small ? parent[nb] : (int)s;
+        for (int u = 0; u < CCL_QUAD_ROUND; ++u) {
+            const long long s0 = 4 * (g0 + u * stride);
+            const int pv[4] = {q[u].x, q[u].y, q[u].z, q[u].w};
+            const int zv[4] = {z[u].x, z[u].y, z[u].z, z[u].w};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const long long s = s0 + i;
+                if (pv[i] != s) continue;
+                const bool small = zv[i] <= T && s != 0;
+                int to = (int)s;
+                if (small) {
+                    // the pixel before s (in this quad unless i = 0), else
+                    // the one above for column 0; N <= 2^30
+                    if (((int)s % W) > 0) to = i > 0 ? pv[i - 1] : parent[s - 1];
+                    else to = parent[s - W];
+                }
+                link[s] = to;
+            }
         }
     }
 }
@@ -284,25 +337,26 @@ __device__ __forceinline__ void ccl_resolve_count(const int *__restrict__ parent
                                                   unsigned chunk)
 {
     __shared__ int s_warp[32];
-    // CCL_PER consecutive pixels per thread, their parents loaded first
+    // CCL_PER consecutive pixels per thread, their parents and links loaded
+    // first (a seed's link sits at its own index; other entries are unused)
     const long long base = chunk * (long long)CCL_CHUNK + (long long)threadIdx.x * CCL_PER;
-    int par[CCL_PER];
+    int par[CCL_PER], lk[CCL_PER];
     load_run(parent, base, N, par);
+    load_run(link, base, N, lk);
     int cnt = 0;
 #pragma unroll
     for (int i = 0; i < CCL_PER; ++i) {
         const long long s = base + i;
         if (par[i] != s) continue;
-        int f = (int)s;
+        int f = (int)s, nf = lk[i];
         long long guard = 0;
-        while (true) {
-            const int nf = link[f];
-            if (nf == f) break;
+        while (nf != f) {
             f = nf;
             if (++guard > N) {
                 atomicExch(&ctr->error, ERR_CCL_CHAIN);
                 break;
             }
+            nf = link[f];
         }
         final_id[s] = f;
         cnt += f == s;
@@ -610,7 +664,7 @@ void launch_ccl(const int *labels, int H, int W, int K, int *out, const CclBuffe
 // Blocks of one image per pass in a batch.  A block first finds its image, so
 // each takes several units (tiles, border pixels, 32-pixel runs, quads) to
 // pay for that lookup; chunks are large enough alone.
-constexpr int CCL_BATCH_TILES = 4, CCL_BATCH_BORDER = 4, CCL_BATCH_RUNS = 8, CCL_BATCH_QUADS = 8;
+constexpr int CCL_BATCH_TILES = 4, CCL_BATCH_BORDER = 1, CCL_BATCH_RUNS = 8, CCL_BATCH_QUADS = 8;
 
 void ccl_batch_blocks(int H, int W, long long blocks[CCL_KINDS])
 {
