@@ -454,7 +454,6 @@ int scalp_init(scalp_ctx **out, const scalp_image *image, const scalp_contour *c
     a.n_tx = L.n_tx; a.n_ty = L.n_ty;
     a.pitch = L.pitch;
     a.grid_rcp_x = grid_reciprocal(W, c->nx);
-    a.grid_rcp_y = grid_reciprocal(H, c->ny);
     a.plane32 = params->storage == 0 ? reinterpret_cast<const float4 *>(c->ws + L.plane) : nullptr;
     a.plane16 = params->storage == 1 ? reinterpret_cast<const uint2 *>(c->ws + L.plane) : nullptr;
     a.labels = reinterpret_cast<int *>(c->ws + L.labels);
@@ -1181,7 +1180,7 @@ int scalp_batch_init(scalp_batch **out, int32_t count, const scalp_image *images
         add(tile_base, i, (long long)c->a.n_tx * c->a.n_ty);
         add(clus_base, i, c->Keff);
         add(fill_base, i, (long long)c->Keff * c->a.tpw_x * c->a.tpw_y);
-        add(setup_base, i, setup_blocks(c->H, c->W));
+        add(setup_base, i, setup_blocks(c->H, c->W, c->ny));
         long long blocks[CCL_KINDS];
         ccl_batch_blocks(c->H, c->W, blocks);
         for (int k = 0; k < CCL_KINDS; ++k) add(ccl_base[k], i, blocks[k]);

@@ -32,27 +32,52 @@ constexpr int COLOR_FRAC_BITS = 19;
 // table `lin`), the D65 sRGB->XYZ matrix, normalisation by the XYZ of sRGB
 // white (the matrix row sums), then CIE 1976 companding with the linear
 // segment below (6/29)^3.
-static __constant__ float c_rgb2xyz[9] = {0.4124564f, 0.3575761f, 0.1804375f,
-                                   0.2126729f, 0.7151522f, 0.0721750f,
-                                   0.0193339f, 0.1191920f, 0.9503041f};
+__host__ __device__ constexpr float rgb2xyz(int i)
+{
+    constexpr float m[9] = {0.4124564f, 0.3575761f, 0.1804375f,
+                            0.2126729f, 0.7151522f, 0.0721750f,
+                            0.0193339f, 0.1191920f, 0.9503041f};
+    return m[i];
+}
+
+// Cube root on [(6/29)^3, 1], the range the companding takes it on (a
+// normalised XYZ value is at most 1 up to rounding).  Newton-Raphson on the
+// reciprocal cube root, y <- y (4 - t y^3) / 3, which needs no division,
+// from a start that divides the float's bit pattern by three (the pattern
+// is a piecewise-linear log2); 0x54A232A0 minimises the start's largest
+// relative error over the range (3.4%).  Two steps, then c = t y^2 corrected
+// once by (t - c^3) y^2 / 3, leave less than one ulp against the exact root
+// (0.75 ulp at most over the floats of the range in an FP32 emulation).
+__device__ __forceinline__ float cube_root(float t)
+{
+    const float third = 1.0f / 3.0f;
+    float y = __uint_as_float(0x54A232A0u - __float_as_uint(t) / 3u);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) y = (y * fmaf(-t, (y * y) * y, 4.0f)) * third;
+    const float y2 = y * y;
+    const float c = t * y2;
+    return fmaf(fmaf(-c, c * c, t), y2 * third, c);
+}
 
 __device__ __forceinline__ float lab_f(float t)
 {
     const float d3 = (6.0f / 29.0f) * (6.0f / 29.0f) * (6.0f / 29.0f);
-    return t > d3 ? cbrtf(t) : t * (841.0f / 108.0f) + (4.0f / 29.0f);
+    return t > d3 ? cube_root(t) : t * (841.0f / 108.0f) + (4.0f / 29.0f);
 }
 
 // CIELab of one sRGB pixel; lin = the 256-entry inverse transfer function.
+// Each matrix row is divided by its sum at compile time, so the products are
+// the normalised X/Xw, Y/Yw, Z/Zw.
 __device__ __forceinline__ float3 srgb_to_lab(const float *lin, const uint8_t *px)
 {
-    const float wx = c_rgb2xyz[0] + c_rgb2xyz[1] + c_rgb2xyz[2];
-    const float wy = c_rgb2xyz[3] + c_rgb2xyz[4] + c_rgb2xyz[5];
-    const float wz = c_rgb2xyz[6] + c_rgb2xyz[7] + c_rgb2xyz[8];
-    float R = lin[px[0]], G = lin[px[1]], B = lin[px[2]];
-    float X = c_rgb2xyz[0] * R + c_rgb2xyz[1] * G + c_rgb2xyz[2] * B;
-    float Y = c_rgb2xyz[3] * R + c_rgb2xyz[4] * G + c_rgb2xyz[5] * B;
-    float Z = c_rgb2xyz[6] * R + c_rgb2xyz[7] * G + c_rgb2xyz[8] * B;
-    float fx = lab_f(X / wx), fy = lab_f(Y / wy), fz = lab_f(Z / wz);
+    constexpr float wx = rgb2xyz(0) + rgb2xyz(1) + rgb2xyz(2);
+    constexpr float wy = rgb2xyz(3) + rgb2xyz(4) + rgb2xyz(5);
+    constexpr float wz = rgb2xyz(6) + rgb2xyz(7) + rgb2xyz(8);
+    const float R = lin[px[0]], G = lin[px[1]], B = lin[px[2]];
+    const float tx = (rgb2xyz(0) / wx) * R + (rgb2xyz(1) / wx) * G + (rgb2xyz(2) / wx) * B;
+    const float ty = (rgb2xyz(3) / wy) * R + (rgb2xyz(4) / wy) * G + (rgb2xyz(5) / wy) * B;
+    const float tz = (rgb2xyz(6) / wz) * R + (rgb2xyz(7) / wz) * G + (rgb2xyz(8) / wz) * B;
+    const float fx = lab_f(tx), fy = lab_f(ty), fz = lab_f(tz);
     return make_float3(116.0f * fy - 16.0f, 500.0f * (fx - fy), 200.0f * (fy - fz));
 }
 
@@ -108,10 +133,9 @@ struct SolveArgs {
     int n_tx, n_ty;    // tiles
     int map_cap;       // distance-map pairs per assignment CTA (0: every path on the plane)
     int pitch;         // plane row pitch in pixels (>= W, multiple of 4)
-    // grid cell of the set-up, floor(x * nx / W) and floor(y * ny / H), as
-    // multiply-highs by these (ceil(2^32 / W), ceil(2^32 / H)) where that is
-    // exact; 0: divide
-    unsigned grid_rcp_x, grid_rcp_y;
+    // grid column of the set-up, floor(x * nx / W), as a multiply-high by
+    // ceil(2^32 / W) where that is exact; 0: divide
+    unsigned grid_rcp_x;
     int count_samples;
     const float4 *plane32;   // (L, a, b, w) per pixel, row pitch `pitch` [FP32 storage]
     const uint2 *plane16;    // the same as 4 x fp16                   [FP16 storage]

@@ -58,39 +58,70 @@ cudaError_t srgb_table(const float **table, cudaStream_t st)
     return cudaSuccess;
 }
 
-// One warp per 32-pixel segment of a row (the warp-aggregated sums need a
-// warp-uniform base): CIELab, contour factor and grid label of each pixel,
-// then the integer sums of (1, x, y, L, a, b) of the grid clusters (the
-// update's input), from the values as stored (FP16-rounded in that format).
-// Block blk of nblk; with wait_sums the block waits for its predecessor
-// launch (which zeroes the sums) only before its first addition.
+// The set-up in warp tasks.  A task is a strip of 32 columns over at most
+// SETUP_ROWS rows of one row of grid cells; along those rows the strip's
+// pixels keep their grid cells (Algorithm 1 initialisation: the label of a
+// pixel is its cell of the regular grid).  Per pixel: CIELab, contour factor,
+// plane sample and label; each lane sums the colour of its pixels (fixed
+// point, from the values as stored: FP16-rounded in that format).  Once per
+// task the lanes of each cell add the integer sums of (1, x, y, L, a, b) of
+// their pixels to the cell, counts and coordinates in closed form.  With
+// wait_sums the warp waits for its predecessor launch (which zeroes the sums)
+// only before that addition.
 constexpr int SETUP_THREADS = 256;
-constexpr int SETUP_SEGS_PER_WARP = 16;  // batch form: the image lookup is paid once per block
+constexpr int SETUP_ROWS = 8;
 
-__device__ __forceinline__ void setup_pixels(const SolveArgs &a, const uint8_t *__restrict__ rgb,
-                                             long long rgb_stride, const float *__restrict__ contour,
-                                             long long contour_stride, int storage, void *plane, unsigned blk,
-                                             unsigned nblk, bool wait_sums)
+// Warp tasks of one image: strips x cell rows x chunks of SETUP_ROWS rows (a
+// cell row is at most ceil(H/ny) rows high; shorter ones leave tasks empty).
+__host__ __device__ inline long long setup_task_count(int H, int W, int ny, int &strips, int &chunks)
 {
-    __shared__ float lin[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) lin[i] = a.lut[i];
-    __syncthreads();
+    strips = (W + 31) / 32;
+    chunks = ((H + ny - 1) / ny + SETUP_ROWS - 1) / SETUP_ROWS;
+    return (long long)strips * ny * chunks;
+}
+
+// Exact sum over the warp of per-lane values below 2^31 in magnitude: the
+// high and low 16-bit halves are reduced apart (neither sum can overflow).
+__device__ __forceinline__ long long warp_sum_wide(int v)
+{
+    const int hi = __reduce_add_sync(0xffffffffu, v >> 16);
+    const unsigned lo = __reduce_add_sync(0xffffffffu, (unsigned)v & 0xffffu);
+    return (long long)hi * 65536 + (long long)lo;
+}
+
+__device__ __forceinline__ void setup_task(const SolveArgs &a, const float *lin, const uint8_t *__restrict__ rgb,
+                                           long long rgb_stride, const float *__restrict__ contour,
+                                           long long contour_stride, int storage, void *plane, long long task,
+                                           bool wait_sums)
+{
+    int strips, chunks;
+    setup_task_count(a.H, a.W, a.ny, strips, chunks);
+    const int strip = (int)(task % strips);
+    const long long rest = task / strips;
+    const int chunk = (int)(rest % chunks), cy = (int)(rest / chunks);
+    // the rows of cell row cy are those with floor(y * ny / H) = cy
+    const int ylo = (int)(((long long)cy * a.H + a.ny - 1) / a.ny);
+    const int yend = (int)(((long long)(cy + 1) * a.H + a.ny - 1) / a.ny);
+    const int y0 = ylo + chunk * SETUP_ROWS, y1 = min(y0 + SETUP_ROWS, yend);
+    if (y0 >= y1) return;  // warp-uniform
+    const int lane = threadIdx.x & 31, bx = strip * 32, x = bx + lane;
+    const bool valid = x < a.W;
+    const int cx = a.grid_rcp_x ? (int)__umulhi((unsigned)x * (unsigned)a.nx, a.grid_rcp_x)
+                                : (int)((long long)x * a.nx / a.W);
+    const int key = cy * a.nx + cx;
     const float inv_s2 = 1.0f / (a.sigma * a.sigma);
-    const unsigned segs_per_row = (unsigned)(a.W + 31) / 32u;
-    const unsigned n_segs = segs_per_row * (unsigned)a.H;  // <= N <= 2^30
-    const unsigned warps = nblk * (blockDim.x / 32);
-    for (unsigned seg = blk * (blockDim.x / 32) + (threadIdx.x >> 5); seg < n_segs; seg += warps) {
-        const int y = (int)(seg / segs_per_row);
-        const int bx = (int)(seg - (unsigned)y * segs_per_row) * 32;
-        const int x = bx + (int)(threadIdx.x & 31);
-        const bool valid = x < a.W;
-        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-        int lab = 0;
-        if (valid) {
+    const float scale = (float)(1 << COLOR_FRAC_BITS);
+    // per lane: SETUP_ROWS * 108 * 2^COLOR_FRAC_BITS < 2^31
+    static_assert((long long)SETUP_ROWS * 108 * (1LL << COLOR_FRAC_BITS) < (1LL << 31), "lane colour sums");
+    int sL = 0, sa = 0, sb = 0;
+    if (valid) {
+#pragma unroll 4
+        for (int y = y0; y < y1; ++y) {
             const float3 c3 = srgb_to_lab(lin, rgb + y * rgb_stride + 3 * (long long)x);
             const float c = contour ? contour[y * contour_stride + x] : 0.0f;
             const float w = -expm1f(-(c * c) * inv_s2);  // 1 - exp(-C^2/sigma^2), Eq. 2
             const long long q = (long long)y * a.pitch + x;
+            float4 v;
             if (storage == 0) {
                 v = make_float4(c3.x, c3.y, c3.z, w);
                 reinterpret_cast<float4 *>(plane)[q] = v;
@@ -102,20 +133,42 @@ __device__ __forceinline__ void setup_pixels(const SolveArgs &a, const uint8_t *
                 reinterpret_cast<uint2 *>(plane)[q] = u;
                 v = sample_value(u);
             }
-            // Algorithm 1 initialisation: label = cell of the regular grid
-            const int cx = a.grid_rcp_x ? (int)__umulhi((unsigned)x * (unsigned)a.nx, a.grid_rcp_x)
-                                        : (int)((long long)x * a.nx / a.W);
-            const int cy = a.grid_rcp_y ? (int)__umulhi((unsigned)y * (unsigned)a.ny, a.grid_rcp_y)
-                                        : (int)((long long)y * a.ny / a.H);
-            lab = cy * a.nx + cx;
-            a.labels[(long long)y * a.W + x] = lab;
+            a.labels[(long long)y * a.W + x] = key;
+            sL += __float2int_rn(v.x * scale);
+            sa += __float2int_rn(v.y * scale);
+            sb += __float2int_rn(v.z * scale);
         }
-        if (wait_sums) {
-            pdl_wait();
-            wait_sums = false;
-        }
-        warp_aggregate_global(valid, lab, bx, y, x - bx, 0, v, a.acc);
     }
+    if (wait_sums) pdl_wait();
+    const long long rows = y1 - y0, row_sum = (long long)(y0 + y1 - 1) * rows / 2;
+    unsigned pending = __ballot_sync(0xffffffffu, valid);
+    while (pending) {
+        const int leader = __ffs(pending) - 1;
+        const int k = __shfl_sync(0xffffffffu, key, leader);
+        const bool mine = valid && key == k;
+        const unsigned grp = __ballot_sync(0xffffffffu, mine);
+        const long long n = __popc(grp);
+        const unsigned lanes = __reduce_add_sync(0xffffffffu, mine ? (unsigned)lane : 0u);
+        const long long tL = warp_sum_wide(mine ? sL : 0), ta = warp_sum_wide(mine ? sa : 0),
+                        tb = warp_sum_wide(mine ? sb : 0);
+        if (lane == leader) acc_add(&a.acc[k], n * rows, rows * (n * bx + lanes), n * row_sum, tL, ta, tb);
+        pending &= ~grp;
+    }
+}
+
+// The block's warps take tasks task0, task0 + 1, ...; lin is loaded first.
+__device__ __forceinline__ void setup_block(const SolveArgs &a, const uint8_t *__restrict__ rgb, long long rgb_stride,
+                                            const float *__restrict__ contour, long long contour_stride, int storage,
+                                            void *plane, long long task0, bool wait_sums)
+{
+    __shared__ float lin[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) lin[i] = a.lut[i];
+    __syncthreads();
+    int strips, chunks;
+    const long long tasks = setup_task_count(a.H, a.W, a.ny, strips, chunks);
+    const long long task = task0 + (threadIdx.x >> 5);
+    if (task < tasks)
+        setup_task(a, lin, rgb, rgb_stride, contour, contour_stride, storage, plane, task, wait_sums);
 }
 
 __global__ void __launch_bounds__(SETUP_THREADS)
@@ -123,7 +176,8 @@ __global__ void __launch_bounds__(SETUP_THREADS)
             const float *__restrict__ contour, long long contour_stride, int storage, void *plane)
 {
     pdl_release();  // launched after memsets: nothing to wait for
-    setup_pixels(a, rgb, rgb_stride, contour, contour_stride, storage, plane, blockIdx.x, gridDim.x, false);
+    setup_block(a, rgb, rgb_stride, contour, contour_stride, storage, plane,
+                (long long)blockIdx.x * (SETUP_THREADS / 32), false);
 }
 
 // Batch: first every image's counters, cluster sums, tile counts and list
@@ -160,8 +214,8 @@ __global__ void __launch_bounds__(SETUP_THREADS)
     const SolveArgs a = b.args[i];
     const SetupInput u = in[i];
     void *plane = storage == 0 ? (void *)a.plane32 : (void *)a.plane16;
-    setup_pixels(a, u.rgb, u.rgb_stride, u.contour, u.contour_stride, storage, plane,
-                 (unsigned)(g - setup_base[i]), (unsigned)(setup_base[i + 1] - setup_base[i]), true);
+    setup_block(a, u.rgb, u.rgb_stride, u.contour, u.contour_stride, storage, plane,
+                (long long)(g - setup_base[i]) * (SETUP_THREADS / 32), true);
 }
 
 
@@ -269,14 +323,14 @@ void launch_setup(const SolveArgs &a, const uint8_t *rgb, long long rgb_stride,
                   const float *contour, long long contour_stride, int storage, void *plane,
                   cudaStream_t st)
 {
-    const int blocks = (int)std::min<long long>(ceil_div_ll(a.N, SETUP_THREADS), 152 * 16);
-    k_setup<<<blocks, SETUP_THREADS, 0, st>>>(a, rgb, rgb_stride, contour, contour_stride, storage, plane);
+    const long long blocks = setup_blocks(a.H, a.W, a.ny);
+    k_setup<<<(unsigned)blocks, SETUP_THREADS, 0, st>>>(a, rgb, rgb_stride, contour, contour_stride, storage, plane);
 }
 
-long long setup_blocks(int H, int W)
+long long setup_blocks(int H, int W, int ny)
 {
-    const long long segs = (long long)((W + 31) / 32) * H;
-    return ceil_div_ll(segs, (long long)(SETUP_THREADS / 32) * SETUP_SEGS_PER_WARP);
+    int strips, chunks;
+    return ceil_div_ll(setup_task_count(H, W, ny, strips, chunks), SETUP_THREADS / 32);
 }
 
 void launch_setup_batch(const BatchArgs &b, const SetupInput *in, const int *setup_base, int total_blocks,

@@ -114,7 +114,7 @@ struct SetupInput {
     const float *contour;
     long long rgb_stride, contour_stride;
 };
-long long setup_blocks(int H, int W);
+long long setup_blocks(int H, int W, int ny);
 void launch_setup_batch(const BatchArgs &b, const SetupInput *in, const int *setup_base, int total_blocks,
                         int storage, cudaStream_t st);
 
