@@ -207,7 +207,12 @@ int scalp_batch_init(scalp_batch **out, int32_t count, const scalp_image *images
                      const scalp_contour *contours, const int32_t *K, const float *m,
                      const scalp_params *params);
 
-/* New images and contours of the same sizes; clusters re-initialised. */
+/* New images and contours of the same sizes; clusters re-initialised
+ * (asynchronous).  The set-up of all images runs as one launch (after one that
+ * clears every image's sums and counters).  Device-side inputs are read in
+ * place; host inputs are copied into the workspace first, so they must stay
+ * valid until the call returns.  The input pointers are kept in device memory
+ * and uploaded (from pinned staging the batch owns) only when they change. */
 int scalp_batch_reload(scalp_batch *b, const scalp_image *images, const scalp_contour *contours);
 
 /* n iterations for every image (asynchronous). */
@@ -215,9 +220,12 @@ int scalp_batch_iterate(scalp_batch *b, int32_t n);
 
 /* Labels of every image into outs[i] (H_i*W_i int32, host or device memory per
  * out_on_device), connectivity enforced when enforce != 0; n_labels[i] gets
- * the count.  Synchronises the stream once.  The per-image work of this call
- * and of scalp_batch_reload runs on streams of the batch's own, forked from
- * and joined back to params->stream; host outputs should be pinned for their
+ * the count.  Synchronises the stream once.  With enforce, each connectivity
+ * pass runs once for all images and writes device outputs directly (host
+ * outputs are copied out afterwards, one copy per image on params->stream);
+ * without it the label copies, and in scalp_batch_reload the gradient priors
+ * and host-input copies, run on streams of the batch's own, forked from and
+ * joined back to params->stream.  Host outputs should be pinned for their
  * copies to overlap. */
 int scalp_batch_labels(scalp_batch *b, int32_t *const *outs, int32_t out_on_device,
                        int32_t enforce, int32_t *n_labels);
