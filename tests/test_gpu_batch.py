@@ -156,3 +156,47 @@ def test_batch_gradient_prior(S):
             assert np.array_equal(again[i], out), i
             s.close()
         b.close()
+
+
+def _alone_vs_batch(S, sizes, Ks, seed, iters=3):
+    import torch
+
+    rgbs, cons = [], []
+    for i, (H, W) in enumerate(sizes):
+        rgb, con, _ = synth.small_image(H, W, seed=seed + i, n_cells=max(2, H * W // 600))
+        rgbs.append(torch.from_numpy(rgb).cuda())
+        cons.append(torch.from_numpy(con).cuda())
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = S.Batch(rgbs, cons, Ks, stream=stream)
+        b.iterate(iters)
+        raw, _ = b.labels(enforce=False)
+        final, nfinal = b.labels(enforce=True)
+        for i, K in enumerate(Ks):
+            s = S.Segmenter(rgbs[i], cons[i], K, stream=stream)
+            s.iterate(iters)
+            lab, _ = s.labels(enforce=False)
+            assert np.array_equal(raw[i], lab), (i, sizes[i], K)
+            out, n = s.labels(enforce=True)
+            assert n == nfinal[i] and np.array_equal(final[i], out), (i, sizes[i], K)
+            s.close()
+        b.close()
+
+
+def test_many_small_images(S):
+    """48 images of random size from 1x1 to 89x89 (many without tile borders in
+    one or both directions) and random K: every flat launch maps its blocks to
+    the right image."""
+    rng = np.random.default_rng(123)
+    sizes = [(int(rng.integers(1, 90)), int(rng.integers(1, 90))) for _ in range(48)]
+    Ks = [int(rng.integers(1, min(H * W, 40) + 1)) for H, W in sizes]
+    _alone_vs_batch(S, sizes, Ks, seed=1200)
+
+
+def test_batch_of_single_tiles(S):
+    """Every image fits in one 32x32 tile, so the border pass of the batch has
+    no work at all and is not launched."""
+    rng = np.random.default_rng(321)
+    sizes = [(int(rng.integers(1, 33)), int(rng.integers(1, 33))) for _ in range(20)]
+    Ks = [int(rng.integers(1, min(H * W, 12) + 1)) for H, W in sizes]
+    _alone_vs_batch(S, sizes, Ks, seed=1300)
