@@ -244,16 +244,10 @@ int load_inputs(scalp_ctx *c, const scalp_image *img, const scalp_contour *con)
     SetupInput in;
     int rc = stage_inputs(c, img, con, &in);
     if (rc) return rc;
-    rc = cuda_check(c, cudaMemsetAsync(c->a.acc, 0, sizeof(ClusterAcc) * c->Keff, c->st), "memset");
-    if (rc) return rc;
-    rc = zero_tile_counts(c);
-    if (rc) return rc;
-    rc = cuda_check(c, cudaMemsetAsync(c->a.ctr, 0, sizeof(DevCounters), c->st), "memset");
-    if (rc) return rc;
     void *plane = c->ws + c->L.plane;
-    // set-up (with the grid clusters' sums), then the initial update,
-    // projection and lists as programmatic launches (each waits for its
-    // predecessor before its first read)
+    // zeroing of the sums and counters, set-up (with the grid clusters'
+    // sums), then the initial update, projection and lists, as programmatic
+    // launches (each waits for its predecessor before its first read)
     launch_setup(c->a, in.rgb, in.rgb_stride, in.contour, in.contour_stride, c->p.storage, plane, c->st);
     launch_update(c->a, 1, c->st, true);
     launch_project(c->a, 1, c->st, true);
@@ -988,7 +982,7 @@ struct scalp_batch {
     int graph_n = 0;
     // flat set-up and connectivity
     const int *setup_base = nullptr;
-    int setup_total = 0;
+    int setup_total = 0, zero_parts = 1;
     CclBatch cb{};
     int ccl_total[CCL_KINDS] = {};
     PinnedTable in_table;   // SetupInput per image
@@ -1181,6 +1175,7 @@ int scalp_batch_init(scalp_batch **out, int32_t count, const scalp_image *images
         add(clus_base, i, c->Keff);
         add(fill_base, i, (long long)c->Keff * c->a.tpw_x * c->a.tpw_y);
         add(setup_base, i, setup_blocks(c->H, c->W, c->ny));
+        b->zero_parts = std::max(b->zero_parts, zero_blocks(c->Keff, c->a.n_tx * c->a.n_ty));
         long long blocks[CCL_KINDS];
         ccl_batch_blocks(c->H, c->W, blocks);
         for (int k = 0; k < CCL_KINDS; ++k) add(ccl_base[k], i, blocks[k]);
@@ -1277,7 +1272,7 @@ int scalp_batch_reload(scalp_batch *b, const scalp_image *images, const scalp_co
     if (e == cudaSuccess) e = b->in_table.upload(in.data(), b->st);
     if (e == cudaSuccess) {
         launch_setup_batch(b->bargs, static_cast<const SetupInput *>(b->in_table.dev), b->setup_base,
-                           b->setup_total, b->storage, b->st);
+                           b->setup_total, b->zero_parts, b->storage, b->st);
         launch_batch_update(b->bargs, b->total_clusters, b->total_fill, b->st, true, nullptr, nullptr, nullptr, 1);
         e = cudaGetLastError();
     }

@@ -171,29 +171,24 @@ __device__ __forceinline__ void setup_block(const SolveArgs &a, const uint8_t *_
         setup_task(a, lin, rgb, rgb_stride, contour, contour_stride, storage, plane, task, wait_sums);
 }
 
-__global__ void __launch_bounds__(SETUP_THREADS)
-    k_setup(SolveArgs a, const uint8_t *__restrict__ rgb, long long rgb_stride,
-            const float *__restrict__ contour, long long contour_stride, int storage, void *plane)
+// First the counters, cluster sums, tile counts and list cursors are zeroed
+// (zero_blocks() CTAs per image), then the set-up runs as a programmatic launch:
+// it is placed once the zeroing has waited for the work before it (the zeroing
+// waits before it releases), converts its pixels meanwhile and waits for the
+// zeroing before its first addition.  A batch gives each image its own range
+// of set-up blocks.
+constexpr int ZERO_THREADS = 256, ZERO_PER_THREAD = 8;
+
+int zero_blocks(int Keff, int tiles)
 {
-    pdl_release();  // launched after memsets: nothing to wait for
-    setup_block(a, rgb, rgb_stride, contour, contour_stride, storage, plane,
-                (long long)blockIdx.x * (SETUP_THREADS / 32), false);
+    const long long words = std::max<long long>((long long)Keff * (long long)(sizeof(ClusterAcc) / sizeof(int4)), tiles);
+    return (int)std::max<long long>(1, ceil_div_ll(words, (long long)ZERO_THREADS * ZERO_PER_THREAD));
 }
 
-// Batch: first every image's counters, cluster sums, tile counts and list
-// cursors zeroed (ZERO_BLOCKS CTAs per image), then the set-up with each image
-// in its own range of blocks.  The set-up is placed once the zeroing has waited
-// for the work before it (the zeroing waits before it releases), converts its
-// pixels meanwhile and waits for the zeroing before its first addition.
-constexpr int ZERO_BLOCKS = 4;
-
-__global__ void k_zero_batch(BatchArgs b)
+__device__ __forceinline__ void zero_solver(const SolveArgs &a, int part, int parts)
 {
-    pdl_wait();
-    pdl_release();
-    const SolveArgs a = b.args[blockIdx.x / ZERO_BLOCKS];
-    const int t0 = (int)(blockIdx.x % ZERO_BLOCKS) * blockDim.x + threadIdx.x;
-    const int step = ZERO_BLOCKS * blockDim.x;
+    const int t0 = part * blockDim.x + threadIdx.x;
+    const int step = parts * blockDim.x;
     static_assert(sizeof(ClusterAcc) % sizeof(int4) == 0, "cluster sums are cleared as int4");
     const int acc4 = a.Keff * (int)(sizeof(ClusterAcc) / sizeof(int4));
     for (int j = t0; j < acc4; j += step) reinterpret_cast<int4 *>(a.acc)[j] = make_int4(0, 0, 0, 0);
@@ -203,6 +198,30 @@ __global__ void k_zero_batch(BatchArgs b)
         a.tile_cursor[j] = 0;
     }
     for (int j = t0; j < (int)(sizeof(DevCounters) / sizeof(int)); j += step) reinterpret_cast<int *>(a.ctr)[j] = 0;
+}
+
+__global__ void k_zero(SolveArgs a)
+{
+    pdl_wait();
+    pdl_release();
+    zero_solver(a, blockIdx.x, gridDim.x);
+}
+
+__global__ void k_zero_batch(BatchArgs b, int parts)
+{
+    pdl_wait();
+    pdl_release();
+    const SolveArgs a = b.args[blockIdx.x / parts];
+    zero_solver(a, blockIdx.x % parts, parts);
+}
+
+__global__ void __launch_bounds__(SETUP_THREADS)
+    k_setup(SolveArgs a, const uint8_t *__restrict__ rgb, long long rgb_stride,
+            const float *__restrict__ contour, long long contour_stride, int storage, void *plane)
+{
+    pdl_release();
+    setup_block(a, rgb, rgb_stride, contour, contour_stride, storage, plane,
+                (long long)blockIdx.x * (SETUP_THREADS / 32), true);
 }
 
 __global__ void __launch_bounds__(SETUP_THREADS)
@@ -324,7 +343,9 @@ void launch_setup(const SolveArgs &a, const uint8_t *rgb, long long rgb_stride,
                   cudaStream_t st)
 {
     const long long blocks = setup_blocks(a.H, a.W, a.ny);
-    k_setup<<<(unsigned)blocks, SETUP_THREADS, 0, st>>>(a, rgb, rgb_stride, contour, contour_stride, storage, plane);
+    pdl_launch(false, k_zero, dim3(zero_blocks(a.Keff, a.n_tx * a.n_ty)), dim3(ZERO_THREADS), 0, st, a);
+    pdl_launch(true, k_setup, dim3((unsigned)blocks), dim3(SETUP_THREADS), 0, st, a, rgb, rgb_stride, contour,
+               contour_stride, storage, plane);
 }
 
 long long setup_blocks(int H, int W, int ny)
@@ -334,10 +355,11 @@ long long setup_blocks(int H, int W, int ny)
 }
 
 void launch_setup_batch(const BatchArgs &b, const SetupInput *in, const int *setup_base, int total_blocks,
-                        int storage, cudaStream_t st)
+                        int zero_parts, int storage, cudaStream_t st)
 {
     if (b.count <= 0) return;
-    pdl_launch(true, k_zero_batch, dim3((unsigned)(b.count * ZERO_BLOCKS)), dim3(256), 0, st, b);
+    pdl_launch(true, k_zero_batch, dim3((unsigned)(b.count * zero_parts)), dim3(ZERO_THREADS), 0, st, b,
+               zero_parts);
     pdl_launch(true, k_setup_batch, dim3((unsigned)total_blocks), dim3(SETUP_THREADS), 0, st, b, in, setup_base,
                storage);
 }

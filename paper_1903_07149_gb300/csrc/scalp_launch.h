@@ -33,8 +33,8 @@ void set_last_error(const char *msg);
 
 // Per-pixel set-up: CIELab (Sec. II-A), contour factor 1-exp(-C^2/sigma^2)
 // of Eq. 2, grid label, and the grid clusters' integer sums of (1, x, y, L,
-// a, b) into a.acc (zeroed by the caller).  rgb/contour are device pointers
-// with row strides.
+// a, b) into a.acc.  It first zeroes the sums, the counters, the tile counts
+// and the list cursors.  rgb/contour are device pointers with row strides.
 void launch_setup(const SolveArgs &a, const uint8_t *rgb, long long rgb_stride,
                   const float *contour, long long contour_stride, int storage,
                   void *plane, cudaStream_t st);
@@ -108,15 +108,17 @@ void launch_ccl_batch(const CclBatch &cb, const int total[CCL_KINDS], cudaStream
 // Set-up of a whole batch (device-side inputs of each image; contour NULL for
 // none): the image's counters, cluster sums, tile counts and list cursors
 // zeroed, then the per-pixel set-up of launch_setup, one launch each.
-// setup_base (count+1 ints) is the prefix of setup_blocks() per image.
+// setup_base (count+1 ints) is the prefix of setup_blocks() per image;
+// zero_parts CTAs zero each image (the largest zero_blocks() of the batch).
 struct SetupInput {
     const uint8_t *rgb;
     const float *contour;
     long long rgb_stride, contour_stride;
 };
 long long setup_blocks(int H, int W, int ny);
+int zero_blocks(int Keff, int tiles);
 void launch_setup_batch(const BatchArgs &b, const SetupInput *in, const int *setup_base, int total_blocks,
-                        int storage, cudaStream_t st);
+                        int zero_parts, int storage, cudaStream_t st);
 
 // Per-context accessors used by the serving loop.
 SolveArgs scalp_ctx_args(const scalp_ctx *c);
