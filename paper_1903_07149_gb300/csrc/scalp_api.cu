@@ -137,6 +137,7 @@ struct scalp_ctx {
     double prof_ms;
     long long prof_launches;
     int iterations;
+    DevCounters *pin = nullptr;  // pinned host copy of the counters (made on first use)
     std::string err;
 };
 
@@ -163,14 +164,24 @@ int cuda_check(scalp_ctx *c, cudaError_t e, const char *what)
 int launch_check(scalp_ctx *c, const char *what) { return cuda_check(c, cudaGetLastError(), what); }
 
 // Reads the device counters after a synchronisation; reports device-side failures.
+// The copy goes to pinned host memory, so it is one asynchronous copy and one
+// synchronisation (a pageable destination would cost a round trip of its own).
 int device_status(scalp_ctx *c)
 {
-    DevCounters h;
-    int rc = cuda_check(c, cudaMemcpyAsync(&h, c->a.ctr, sizeof h, cudaMemcpyDeviceToHost, c->st),
-                        "read device counters");
+    int rc;
+    if (!c->pin) {
+        rc = cuda_check(c, cudaMallocHost(&c->pin, sizeof(DevCounters)), "pinned status buffer");
+        if (rc) {
+            c->pin = nullptr;
+            return rc;
+        }
+    }
+    rc = cuda_check(c, cudaMemcpyAsync(c->pin, c->a.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, c->st),
+                    "read device counters");
     if (rc) return rc;
     rc = cuda_check(c, cudaStreamSynchronize(c->st), "synchronise");
     if (rc) return rc;
+    const DevCounters &h = *c->pin;
     if (h.timeout) return fail(c, SCALP_E_TIMEOUT, "a bounded device-side wait gave up");
     if (h.error) return fail(c, SCALP_E_INTERNAL, "device-side check failed (code %d)", h.error);
     return SCALP_OK;
@@ -364,6 +375,7 @@ void free_ctx(scalp_ctx *c)
 {
     if (c->graph_valid) cudaGraphExecDestroy(c->gexec);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    if (c->pin) cudaFreeHost(c->pin);
     if (c->side) {
         cudaStreamDestroy(c->side);
         cudaEventDestroy(c->fork_ev);
@@ -559,7 +571,7 @@ int scalp_labels(scalp_ctx *c, int32_t *out, int32_t out_on_device, int32_t enfo
     size_t bytes = sizeof(int) * (size_t)c->N;
     if (enforce) {
         int *dst = out_on_device ? out : c->ccl.link;  // link is free once resolved
-        int *d_nlab = reinterpret_cast<int *>(c->ws + c->L.nlab);
+        int *d_nlab = &c->a.ctr->n_labels;  // read back with the counters
         if (out_on_device) {
             // the output must not alias a buffer the enforcement still reads
             launch_ccl(c->a.labels, c->H, c->W, c->K, dst, c->ccl, d_nlab, c->a.ctr, c->st);
@@ -571,9 +583,6 @@ int scalp_labels(scalp_ctx *c, int32_t *out, int32_t out_on_device, int32_t enfo
         }
         rc = launch_check(c, "connectivity kernels");
         if (rc) return rc;
-        rc = cuda_check(c, cudaMemcpyAsync(&nlab, d_nlab, sizeof(int), cudaMemcpyDeviceToHost, c->st),
-                        "copy label count");
-        if (rc) return rc;
     } else {
         rc = cuda_check(c, cudaMemcpyAsync(out, c->a.labels, bytes,
                                            out_on_device ? cudaMemcpyDeviceToDevice
@@ -584,6 +593,7 @@ int scalp_labels(scalp_ctx *c, int32_t *out, int32_t out_on_device, int32_t enfo
     }
     rc = device_status(c);
     if (rc) return rc;
+    if (enforce) nlab = c->pin->n_labels;
     if (n_labels) *n_labels = nlab;
     return SCALP_OK;
 }

@@ -119,6 +119,7 @@ struct DevCounters {
     unsigned long long plane_rects;  // optional: ... walked on the plane in global memory
     unsigned prior_max;  // scratch: maximum of the gradient prior (float bits)
     int proj_all;        // the update saw orphans: the projection searches the image
+    int n_labels;        // labels after the last connectivity enforcement
 };
 constexpr int ERR_TILE_LIST_OVERFLOW = 1;
 constexpr int ERR_BAD_LABEL = 2;
