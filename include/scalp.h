@@ -25,9 +25,10 @@
  *   - The library allocates no device memory: all device buffers are carved
  *     from params->workspace (caller-allocated, at least
  *     scalp_workspace_bytes() bytes, 256-byte aligned), which must stay valid
- *     until scalp_destroy().  The context itself is host memory; a batch
- *     also holds 40 bytes of pinned host memory per image (staging for its
- *     per-call pointer tables).
+ *     until scalp_destroy().  The context itself is host memory (plus 64
+ *     bytes of pinned host memory once it first reads its device status); a
+ *     batch also holds about 110 bytes of pinned host memory per image
+ *     (staging for its per-call pointer tables and its gathered status).
  *   - Images are row-major, pixel (x, y) at row y, column x, with integer
  *     coordinates at pixel centres.  Labels are int32, row-major H x W.
  *   - One context, or one batch, is used by one host thread at a time.

@@ -997,6 +997,8 @@ struct scalp_batch {
     int ccl_total[CCL_KINDS] = {};
     PinnedTable in_table;   // SetupInput per image
     PinnedTable out_table;  // int* per image
+    DevCounters *pin_ctr = nullptr;  // pinned: the gathered counters, then the label counts
+    int *pin_nlab = nullptr;
     // the per-image copies of a reload or of the labels fan out over
     // BATCH_STREAMS streams, and so does the gradient prior
     static constexpr int BATCH_STREAMS = 8;
@@ -1119,6 +1121,7 @@ void scalp_batch_destroy(scalp_batch *b)
     if (b->graph_valid) cudaGraphExecDestroy(b->gexec);
     b->in_table.release();
     b->out_table.release();
+    if (b->pin_ctr) cudaFreeHost(b->pin_ctr);
     for (scalp_ctx *c : b->ctx) scalp_destroy(c);
     delete b;
 }
@@ -1244,6 +1247,14 @@ int scalp_batch_init(scalp_batch **out, int32_t count, const scalp_image *images
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);  // host vectors go out of scope
     if (e == cudaSuccess) e = b->in_table.init(b->ws + h.in, count * sizeof(SetupInput));
     if (e == cudaSuccess) e = b->out_table.init(b->ws + h.out, count * sizeof(int *));
+    if (e == cudaSuccess) {
+        void *pin = nullptr;
+        e = cudaMallocHost(&pin, count * (sizeof(DevCounters) + sizeof(int)));
+        if (e == cudaSuccess) {
+            b->pin_ctr = static_cast<DevCounters *>(pin);
+            b->pin_nlab = reinterpret_cast<int *>(b->pin_ctr + count);
+        }
+    }
     if (e == cudaSuccess) e = assign_batch_configure(b->storage);
     if (e != cudaSuccess) {
         scalp_batch_destroy(b);
@@ -1395,11 +1406,12 @@ int scalp_batch_labels(scalp_batch *b, int32_t *const *outs, int32_t out_on_devi
         if (ce != cudaSuccess) e = ce;
     }
     if (e != cudaSuccess) return batch_fail(SCALP_E_CUDA, "batch labels: %s", cudaGetErrorString(e));
-    std::vector<int> nlab(b->count);
-    std::vector<DevCounters> ctr(b->count);
-    e = cudaMemcpyAsync(nlab.data(), d_nlab, sizeof(int) * b->count, cudaMemcpyDeviceToHost, b->st);
+    // both gathers into pinned memory: two asynchronous copies, one synchronisation
+    const int *nlab = b->pin_nlab;
+    const DevCounters *ctr = b->pin_ctr;
+    e = cudaMemcpyAsync(b->pin_nlab, d_nlab, sizeof(int) * b->count, cudaMemcpyDeviceToHost, b->st);
     if (e == cudaSuccess)
-        e = cudaMemcpyAsync(ctr.data(), d_ctr, sizeof(DevCounters) * b->count, cudaMemcpyDeviceToHost, b->st);
+        e = cudaMemcpyAsync(b->pin_ctr, d_ctr, sizeof(DevCounters) * b->count, cudaMemcpyDeviceToHost, b->st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
     if (e != cudaSuccess) return batch_fail(SCALP_E_CUDA, "batch labels: %s", cudaGetErrorString(e));
     for (int i = 0; i < b->count; ++i) {
