@@ -25,9 +25,10 @@
  *   - The library allocates no device memory: all device buffers are carved
  *     from params->workspace (caller-allocated, at least
  *     scalp_workspace_bytes() bytes, 256-byte aligned), which must stay valid
- *     until scalp_destroy().  The context itself is host memory (plus 64
- *     bytes of pinned host memory once it first reads its device status); a
- *     batch also holds about 110 bytes of pinned host memory per image
+ *     until scalp_destroy().  The context itself is host memory.  A host
+ *     thread that reads a context's status (scalp_labels and other calls that
+ *     synchronise) keeps 64 bytes of pinned host memory for the process's
+ *     life; a batch holds about 110 bytes of pinned host memory per image
  *     (staging for its per-call pointer tables and its gathered status).
  *   - Images are row-major, pixel (x, y) at row y, column x, with integer
  *     coordinates at pixel centres.  Labels are int32, row-major H x W.

@@ -110,6 +110,24 @@ Layout make_layout(int H, int W, int K, int storage)
 namespace scalp {
 // Sets the text scalp_last_error(NULL) returns on this thread.
 void set_last_error(const char *msg) { g_last_error = msg; }
+
+// One pinned buffer per host thread for status reads: a read is a copy and a
+// synchronisation inside one call, and a context is used by one thread at a
+// time.  Made on the thread's first read and kept for the process's life, so
+// that contexts made for one image each allocate nothing.
+DevCounters *pinned_status_buffer()
+{
+    thread_local DevCounters *buf = nullptr;
+    thread_local bool tried = false;
+    if (!buf && !tried) {
+        tried = true;
+        if (cudaMallocHost(&buf, sizeof(DevCounters)) != cudaSuccess) {
+            buf = nullptr;
+            cudaGetLastError();
+        }
+    }
+    return buf;
+}
 }  // namespace scalp
 
 struct scalp_ctx {
@@ -137,7 +155,6 @@ struct scalp_ctx {
     double prof_ms;
     long long prof_launches;
     int iterations;
-    DevCounters *pin = nullptr;  // pinned host copy of the counters (made on first use)
     std::string err;
 };
 
@@ -164,26 +181,23 @@ int cuda_check(scalp_ctx *c, cudaError_t e, const char *what)
 int launch_check(scalp_ctx *c, const char *what) { return cuda_check(c, cudaGetLastError(), what); }
 
 // Reads the device counters after a synchronisation; reports device-side failures.
-// The copy goes to pinned host memory, so it is one asynchronous copy and one
-// synchronisation (a pageable destination would cost a round trip of its own).
-int device_status(scalp_ctx *c)
+// The counters go to the thread's pinned status buffer (a pageable copy when
+// there is none): one asynchronous copy and one synchronisation, where a
+// pageable destination would cost a round trip of its own.  n_labels (if not
+// NULL) receives the label count the last connectivity enforcement wrote.
+int device_status(scalp_ctx *c, int *n_labels = nullptr)
 {
-    int rc;
-    if (!c->pin) {
-        rc = cuda_check(c, cudaMallocHost(&c->pin, sizeof(DevCounters)), "pinned status buffer");
-        if (rc) {
-            c->pin = nullptr;
-            return rc;
-        }
-    }
-    rc = cuda_check(c, cudaMemcpyAsync(c->pin, c->a.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, c->st),
-                    "read device counters");
+    DevCounters local;
+    DevCounters *h = pinned_status_buffer();
+    if (!h) h = &local;
+    int rc = cuda_check(c, cudaMemcpyAsync(h, c->a.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, c->st),
+                        "read device counters");
     if (rc) return rc;
     rc = cuda_check(c, cudaStreamSynchronize(c->st), "synchronise");
     if (rc) return rc;
-    const DevCounters &h = *c->pin;
-    if (h.timeout) return fail(c, SCALP_E_TIMEOUT, "a bounded device-side wait gave up");
-    if (h.error) return fail(c, SCALP_E_INTERNAL, "device-side check failed (code %d)", h.error);
+    if (h->timeout) return fail(c, SCALP_E_TIMEOUT, "a bounded device-side wait gave up");
+    if (h->error) return fail(c, SCALP_E_INTERNAL, "device-side check failed (code %d)", h->error);
+    if (n_labels) *n_labels = h->n_labels;
     return SCALP_OK;
 }
 
@@ -375,7 +389,6 @@ void free_ctx(scalp_ctx *c)
 {
     if (c->graph_valid) cudaGraphExecDestroy(c->gexec);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
-    if (c->pin) cudaFreeHost(c->pin);
     if (c->side) {
         cudaStreamDestroy(c->side);
         cudaEventDestroy(c->fork_ev);
@@ -591,9 +604,8 @@ int scalp_labels(scalp_ctx *c, int32_t *out, int32_t out_on_device, int32_t enfo
                         "copy labels");
         if (rc) return rc;
     }
-    rc = device_status(c);
+    rc = device_status(c, enforce ? &nlab : nullptr);
     if (rc) return rc;
-    if (enforce) nlab = c->pin->n_labels;
     if (n_labels) *n_labels = nlab;
     return SCALP_OK;
 }

@@ -30,6 +30,9 @@ cudaError_t pdl_launch(bool pdl, void (*kernel)(Params...), dim3 grid, dim3 bloc
 
 // Sets the text scalp_last_error(NULL) returns on this thread.
 void set_last_error(const char *msg);
+// This thread's pinned buffer for reading device counters (NULL if pinned
+// memory could not be had; the caller then copies to pageable memory).
+DevCounters *pinned_status_buffer();
 
 // Per-pixel set-up: CIELab (Sec. II-A), contour factor 1-exp(-C^2/sigma^2)
 // of Eq. 2, grid label, and the grid clusters' integer sums of (1, x, y, L,

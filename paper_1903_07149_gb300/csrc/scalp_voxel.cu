@@ -713,7 +713,6 @@ struct scalp_vctx {
     VLayout L;
     VoxArgs a;
     int iterations;
-    DevCounters *pin = nullptr;  // pinned host copy of the counters (made on first use)
 };
 
 namespace {
@@ -751,24 +750,19 @@ void venqueue_update(scalp_vctx *c, int from_acc, int whole)
     venqueue_lists(c);
 }
 
-// The counters go to pinned host memory behind the stream's work: one
-// asynchronous copy and one synchronisation.
+// The counters go to the thread's pinned status buffer behind the stream's
+// work: one asynchronous copy and one synchronisation.
 int vdevice_status(scalp_vctx *c)
 {
-    int rc;
-    if (!c->pin) {
-        rc = vcheck(cudaMallocHost(&c->pin, sizeof(DevCounters)), "pinned status buffer");
-        if (rc) {
-            c->pin = nullptr;
-            return rc;
-        }
-    }
-    rc = vcheck(cudaMemcpyAsync(c->pin, c->a.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, c->st),
-                "read counters");
+    DevCounters local;
+    DevCounters *h = pinned_status_buffer();
+    if (!h) h = &local;
+    int rc = vcheck(cudaMemcpyAsync(h, c->a.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, c->st),
+                    "read counters");
     if (rc) return rc;
     rc = vcheck(cudaStreamSynchronize(c->st), "synchronise");
     if (rc) return rc;
-    if (c->pin->error) return vfail(SCALP_E_INTERNAL, "device-side check failed (code %d)", c->pin->error);
+    if (h->error) return vfail(SCALP_E_INTERNAL, "device-side check failed (code %d)", h->error);
     return SCALP_OK;
 }
 
@@ -996,7 +990,6 @@ void scalp_voxel_destroy(scalp_vctx *c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->st);
-    if (c->pin) cudaFreeHost(c->pin);
     delete c;
 }
 
