@@ -267,8 +267,8 @@ int scalp_gradient_prior(const scalp_image *image, float *out, int64_t out_strid
  * SCALP on a video volume, the extension the paper's conclusion names as
  * future work.  Every rule is the 2-D one taken axis by axis: r = cbrt(N/K)
  * (N = T*H*W voxels) and a 3-D regular grid of step r; cluster k's candidates
- * are the voxels with |v - v_k| <= r on each axis, decided as
- * d*d <= (n*n)*r^2 in double with d = n*v - S_v exact; the linear path is the
+ * are the voxels with |v - v_k| <= r on each axis (r the real cube root, so
+ * K*|n*v - S_v|^3 <= N*n^3, decided exactly); the linear path is the
  * 3-D digital segment traced from the lexicographically smaller end
  * (x, then y, then t), the axis with the largest |delta| stepping by one and
  * each other axis by round-half-up(i*|delta_j|/|delta_major|); D is Eq. 3
@@ -312,6 +312,10 @@ int scalp_voxel_iterate(scalp_vctx *ctx, int32_t n);
 int scalp_voxel_labels(scalp_vctx *ctx, int32_t *out, int32_t out_on_device);
 int scalp_voxel_get_info(const scalp_vctx *ctx, scalp_voxel_info *info);
 int scalp_voxel_get_state(scalp_vctx *ctx, const scalp_voxel_state *state);
+/* Loads a state (synchronises).  Each cluster needs 1 <= n <= 2^30 (the
+ * bound of the exact window arithmetic), a barycenter inside the volume
+ * (0 <= S_v <= n*(dim - 1) on each axis) and an endpoint inside it; labels in
+ * [0, Keff).  The sums need not be those of the labels (test states). */
 int scalp_voxel_set_state(scalp_vctx *ctx, const scalp_voxel_state *state);
 /* As scalp_count_samples, for the supervoxel assignment. */
 int scalp_voxel_count_samples(scalp_vctx *ctx, int32_t enable, int64_t *samples, int64_t *pairs);

@@ -26,7 +26,8 @@ _lib = None
 
 # -ffp-contract=off: no fused multiply-add, so x86-64 and aarch64 hosts give
 # the same bits.
-CFLAGS = ["-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off"]
+# -fopenmp: the row-parallel iterations of the CPU baseline (orc_iterate_rows).
+CFLAGS = ["-O2", "-std=gnu11", "-fPIC", "-shared", "-ffp-contract=off", "-fopenmp"]
 
 
 def build(force: bool = False) -> str:
@@ -63,7 +64,7 @@ class _VCtx(ctypes.Structure):
         ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nt", ctypes.c_int32),
         ("Keff", ctypes.c_int32),
         ("m", ctypes.c_double), ("lam", ctypes.c_double), ("sigma", ctypes.c_double),
-        ("gamma", ctypes.c_double), ("r", ctypes.c_double), ("r2", ctypes.c_double),
+        ("gamma", ctypes.c_double), ("r", ctypes.c_double),
         ("L", ctypes.c_void_p), ("A", ctypes.c_void_p), ("B", ctypes.c_void_p),
         ("C", ctypes.c_void_p),
         ("labels", ctypes.c_void_p),
@@ -97,6 +98,9 @@ def lib():
             L.orc_assign.argtypes = [ctypes.POINTER(_Ctx), P]
             L.orc_assign.restype = ctypes.c_int64
             L.orc_iterate.argtypes = [ctypes.POINTER(_Ctx), ctypes.c_int]
+            L.orc_iterate_rows.argtypes = [ctypes.POINTER(_Ctx), ctypes.c_int, ctypes.c_int]
+            L.orc_assign_rows.argtypes = [ctypes.POINTER(_Ctx), ctypes.c_int]
+            L.orc_assign_rows.restype = ctypes.c_int64
             L.orc_assign_pixels.argtypes = [ctypes.POINTER(_Ctx), P, ctypes.c_int64, P, P]
             L.orc_connectivity.argtypes = [P, ctypes.c_int, ctypes.c_int, ctypes.c_int, P]
             L.orc_connectivity.restype = ctypes.c_int32
@@ -107,7 +111,7 @@ def lib():
             L.orc_vgrid_dims.argtypes = [ctypes.c_int] * 4 + [P, P, P, P]
             L.orc_vpath.argtypes = [ctypes.c_int] * 6 + [P]
             L.orc_vpath.restype = ctypes.c_int
-            L.orc_vin_window.argtypes = [ctypes.c_int64] * 3 + [ctypes.c_double]
+            L.orc_vin_window.argtypes = [ctypes.c_int64] * 5
             L.orc_vin_window.restype = ctypes.c_int
             L.orc_vdistance.argtypes = [ctypes.POINTER(_VCtx)] + [ctypes.c_int] * 4 + [P]
             L.orc_vdistance.restype = ctypes.c_double
@@ -290,6 +294,14 @@ class Solver:
     def iterate(self, iters: int = 1):
         lib().orc_iterate(ctypes.byref(self._c), int(iters))
 
+    def iterate_rows(self, iters: int = 1, threads: int = 0):
+        """The same iterations with the assignment pixel by pixel over rows on
+        `threads` OpenMP threads (0: every host core)."""
+        lib().orc_iterate_rows(ctypes.byref(self._c), int(iters), int(threads or os.cpu_count()))
+
+    def assign_rows(self, threads: int = 0):
+        lib().orc_assign_rows(ctypes.byref(self._c), int(threads or os.cpu_count()))
+
     def distance(self, x: int, y: int, k: int):
         """D(p, C_k) of Eq. 3 for p=(x, y); returns (D, |P|)."""
         n = ctypes.c_int32()
@@ -337,8 +349,9 @@ def vpath(p, e):
     return xyz.reshape(n, 3)
 
 
-def vin_window(v: int, n: int, s: int, r2: float) -> bool:
-    return bool(lib().orc_vin_window(v, n, s, r2))
+def vin_window(v: int, n: int, s: int, N: int, K: int) -> bool:
+    """|v - s/n| <= cbrt(N/K), the supervoxel window along one axis."""
+    return bool(lib().orc_vin_window(v, n, s, N, K))
 
 
 class VSolver:
@@ -376,10 +389,6 @@ class VSolver:
     @property
     def r(self) -> float:
         return self._c.r
-
-    @property
-    def r2(self) -> float:
-        return self._c.r2
 
     @property
     def gamma(self) -> float:

@@ -36,6 +36,7 @@
 #include <string.h>
 
 typedef __int128 i128;
+typedef unsigned __int128 u128;
 
 /* ------------------------------------------------------------------------ */
 /* CIELab conversion (Sec. II-A: clustering runs in the CIELab space).       */
@@ -337,6 +338,98 @@ int orc_iterate(orc_ctx *c, int iters)
     return 0;
 }
 
+/* The same iterations with the assignment taken pixel by pixel, rows shared
+ * out over `threads` OpenMP threads (the CPU baseline on all host cores).
+ * For each pixel the clusters whose window holds it are visited in ascending
+ * k with the strict '<' of Algorithm 1, so every label and distance equals
+ * orc_assign's; the update is orc_update's, with the projections (each reads
+ * the labels and writes only its own cluster's endpoint) run in parallel. */
+static void update_parallel(orc_ctx *c, int threads)
+{
+    int64_t N = (int64_t)c->H * c->W;
+    int K = c->Keff;
+    int64_t *n = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    int64_t *sx = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    int64_t *sy = (int64_t *)calloc((size_t)K, sizeof(int64_t));
+    double *sl = (double *)calloc((size_t)K, sizeof(double));
+    double *sa = (double *)calloc((size_t)K, sizeof(double));
+    double *sb = (double *)calloc((size_t)K, sizeof(double));
+    int *proj = (int *)malloc(sizeof(int) * (size_t)K);
+    int nproj = 0;
+    for (int64_t p = 0; p < N; p++) { /* raster order, as orc_update */
+        int k = c->labels[p];
+        n[k] += 1;
+        sx[k] += p % c->W;
+        sy[k] += p / c->W;
+        sl[k] += c->L[p];
+        sa[k] += c->A[p];
+        sb[k] += c->B[p];
+    }
+    for (int k = 0; k < K; k++) {
+        if (n[k] == 0) continue;
+        c->n[k] = n[k];
+        c->sx[k] = sx[k];
+        c->sy[k] = sy[k];
+        c->cL[k] = sl[k] / (double)n[k];
+        c->cA[k] = sa[k] / (double)n[k];
+        c->cB[k] = sb[k] / (double)n[k];
+        c->ex[k] = (int32_t)((2 * sx[k] + n[k]) / (2 * n[k]));
+        c->ey[k] = (int32_t)((2 * sy[k] + n[k]) / (2 * n[k]));
+        if (c->labels[(int64_t)c->ey[k] * c->W + c->ex[k]] != k) proj[nproj++] = k;
+    }
+#pragma omp parallel for schedule(dynamic) num_threads(threads)
+    for (int i = 0; i < nproj; i++) project_center(c, proj[i]);
+    c->projections = nproj;
+    free(n); free(sx); free(sy); free(sl); free(sa); free(sb); free(proj);
+}
+
+int64_t orc_assign_rows(orc_ctx *c, int threads)
+{
+    int64_t N = (int64_t)c->H * c->W;
+    int32_t *out = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    int64_t orphans = 0;
+#pragma omp parallel num_threads(threads) reduction(+ : orphans)
+    {
+        int *cand = (int *)malloc(sizeof(int) * (size_t)c->Keff);
+#pragma omp for schedule(dynamic)
+        for (int y = 0; y < c->H; y++) {
+            int nc = 0; /* clusters whose window holds row y, ascending k */
+            for (int k = 0; k < c->Keff; k++)
+                if (in_window(y, c->n[k], c->sy[k], N, c->K)) cand[nc++] = k;
+            for (int x = 0; x < c->W; x++) {
+                int64_t p = (int64_t)y * c->W + x;
+                double best = INFINITY;
+                int lab = c->labels[p];
+                for (int i = 0; i < nc; i++) {
+                    int k = cand[i];
+                    if (!in_window(x, c->n[k], c->sx[k], N, c->K)) continue;
+                    double D = orc_distance(c, x, y, k, NULL);
+                    if (D < best) {
+                        best = D;
+                        lab = k;
+                    }
+                }
+                if (best == INFINITY) orphans++;
+                out[p] = lab;
+            }
+        }
+        free(cand);
+    }
+    memcpy(c->labels, out, sizeof(int32_t) * (size_t)N);
+    free(out);
+    c->orphans = orphans;
+    return orphans;
+}
+
+int orc_iterate_rows(orc_ctx *c, int iters, int threads)
+{
+    for (int it = 0; it < iters; it++) {
+        orc_assign_rows(c, threads);
+        update_parallel(c, threads);
+    }
+    return 0;
+}
+
 /* Label of each listed pixel as the assignment would give it, found by
  * testing every cluster's window (pixel-centric); used to check single pixels
  * of large images.  out_label gets the argmin (smallest k on ties, previous
@@ -592,8 +685,8 @@ void orc_gradient_prior(const double *L, const double *A, const double *B, int H
 /*   - r = cbrt(N/K) (host C library); grid nx = max(1, round(W/r)),         */
 /*     ny = max(1, round(H/r)), nt = max(1, round(T/r)); voxel starts in     */
 /*     cell floor(t*nt/T)*ny*nx + floor(y*ny/H)*nx + floor(x*nx/W);          */
-/*   - window: |v - s/n| <= r per axis, decided as d*d <= (n*n)*r2 in double */
-/*     with d = n*v - s exact, r2 = r*r, each product rounded once;          */
+/*   - window: |v - s/n| <= r per axis with r the real cube root of N/K,    */
+/*     i.e. K*|n*v - s|^3 <= N*n^3, decided exactly in 128-bit integers;     */
 /*   - path: 3-D digital segment, traced from the lexicographically smaller  */
 /*     end (x, then y, then t); the major axis is the one with the largest   */
 /*     |delta| (ties: x, then y, then t); step i moves each other axis by    */
@@ -605,7 +698,7 @@ typedef struct {
     int32_t T, H, W, K;
     int32_t nx, ny, nt, Keff;
     double m, lambda, sigma, gamma; /* gamma < 0 selects 2r */
-    double r, r2;                   /* filled by orc_vinit */
+    double r;                       /* filled by orc_vinit: cbrt(N/K) */
     const double *L, *A, *B, *C;    /* N each */
     int32_t *labels;                /* N */
     int64_t *n, *sx, *sy, *st;      /* Keff */
@@ -654,14 +747,24 @@ int orc_vpath(int px, int py, int pt, int ex, int ey, int et, int32_t *xyz)
     return ns + 1;
 }
 
-static int vin_window(int64_t v, int64_t n, int64_t s, double r2)
+/* |v - s/n| <= r with r^3 = N/K, i.e. K*|n*v - s|^3 <= N*n^3, exactly.  A
+ * volume holds at most 2^30 voxels, so r <= 2^10 and n, N <= 2^30: a distance
+ * |n*v - s| above 2^10*n is outside, and below it both q^3 and N*n^3 are at
+ * most 2^120; K*q^3 <= N*n^3 holds iff q^3 <= floor(N*n^3 / K) (q^3 is an
+ * integer). */
+static int vin_window(int64_t v, int64_t n, int64_t s, int64_t N, int64_t K)
 {
-    double d = (double)(n * v - s);
-    double nn = (double)n * (double)n;
-    return d * d <= nn * r2;
+    i128 d = (i128)n * v - (i128)s;
+    u128 q = (u128)(d < 0 ? -d : d);
+    if (q > (u128)n * 1024u) return 0;
+    u128 rhs = (u128)N * (u128)n * (u128)n * (u128)n / (u128)K;
+    return q * q * q <= rhs;
 }
 
-int orc_vin_window(int64_t v, int64_t n, int64_t s, double r2) { return vin_window(v, n, s, r2); }
+int orc_vin_window(int64_t v, int64_t n, int64_t s, int64_t N, int64_t K)
+{
+    return vin_window(v, n, s, N, K);
+}
 
 static double vdc_at(const orc_vctx *c, int64_t q, int k)
 {
@@ -765,8 +868,8 @@ int orc_vinit(orc_vctx *c)
 {
     int64_t N = (int64_t)c->T * c->H * c->W, HW = (int64_t)c->H * c->W;
     if (c->T < 1 || c->H < 1 || c->W < 1 || c->K < 1 || c->K > N) return -1;
+    if (N > ((int64_t)1 << 30)) return -1; /* the window test's 128-bit bound */
     orc_vgrid_dims(c->T, c->H, c->W, c->K, &c->nx, &c->ny, &c->nt, &c->r);
-    c->r2 = c->r * c->r;
     if (c->gamma < 0) c->gamma = 2.0 * c->r;
     c->Keff = c->nx * c->ny * c->nt;
     for (int64_t p = 0; p < N; p++) {
@@ -781,15 +884,17 @@ int orc_vinit(orc_vctx *c)
     return 0;
 }
 
-/* Window bounds along one axis: every v in [lo, hi] of [0, lim) passes. */
-static void vwindow(int64_t n, int64_t s, double r, double r2, int lim, int *lo, int *hi)
+/* Window bounds along one axis: every v in [lo, hi] of [0, lim) passes (the
+ * window is an interval; the double bounds only seed the exact search). */
+static void vwindow(const orc_vctx *c, int64_t n, int64_t s, int lim, int *lo, int *hi)
 {
-    double c = (double)s / (double)n;
-    int a = (int)floor(c - r) - 1, b = (int)ceil(c + r) + 1;
+    int64_t N = (int64_t)c->T * c->H * c->W;
+    double ctr = (double)s / (double)n;
+    int a = (int)floor(ctr - c->r) - 1, b = (int)ceil(ctr + c->r) + 1;
     if (a < 0) a = 0;
     if (b > lim - 1) b = lim - 1;
-    while (a <= b && !vin_window(a, n, s, r2)) a++;
-    while (b >= a && !vin_window(b, n, s, r2)) b--;
+    while (a <= b && !vin_window(a, n, s, N, c->K)) a++;
+    while (b >= a && !vin_window(b, n, s, N, c->K)) b--;
     *lo = a;
     *hi = b;
 }
@@ -801,9 +906,9 @@ int64_t orc_vassign(orc_vctx *c, double *dbest)
     for (int64_t p = 0; p < N; p++) d[p] = INFINITY;
     for (int k = 0; k < c->Keff; k++) {
         int x0, x1, y0, y1, t0, t1;
-        vwindow(c->n[k], c->sx[k], c->r, c->r2, c->W, &x0, &x1);
-        vwindow(c->n[k], c->sy[k], c->r, c->r2, c->H, &y0, &y1);
-        vwindow(c->n[k], c->st[k], c->r, c->r2, c->T, &t0, &t1);
+        vwindow(c, c->n[k], c->sx[k], c->W, &x0, &x1);
+        vwindow(c, c->n[k], c->sy[k], c->H, &y0, &y1);
+        vwindow(c, c->n[k], c->st[k], c->T, &t0, &t1);
         for (int t = t0; t <= t1; t++)
             for (int y = y0; y <= y1; y++)
                 for (int x = x0; x <= x1; x++) {

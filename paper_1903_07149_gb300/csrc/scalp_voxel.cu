@@ -2,9 +2,9 @@
 // the extension the paper's conclusion names as future work.  Each rule is the
 // 2-D one taken axis by axis:
 //   * r = cbrt(N/K) (computed on the host); a 3-D regular grid of step r;
-//   * candidates of cluster k: |v - s_v/n| <= r on each axis, decided as
-//     d*d <= (n*n)*r^2 in double with d = n*v - s_v exact (each product
-//     rounded once), kept as integer bounds per axis;
+//   * candidates of cluster k: |v - s_v/n| <= r on each axis, r the real
+//     cube root of N/K, i.e. K*|n*v - s_v|^3 <= N*n^3 decided exactly, kept
+//     as integer bounds per axis;
 //   * the linear path is a 3-D digital segment traced from the
 //     lexicographically smaller end (x, then y, then t); the axis with the
 //     largest |delta| (ties: x, y, t) steps by one, each other axis by
@@ -55,7 +55,7 @@ struct VoxAcc {  // 64 bytes: integer sums of one assignment
 struct VoxArgs {
     int T, H, W, K, Keff, nx, ny, nt;
     long long N, HW;
-    double r, r2;
+    double r;
     float lam, gamma, ms2;
     int n_tx, n_ty, n_tt;
     int tpw_x, tpw_y, tpw_t;  // bound on the tiles one window spans, per axis
@@ -76,24 +76,36 @@ struct VoxArgs {
 };
 
 // ---------------------------------------------------------------------------
-// Windows: exact integer n*v - s, then d*d <= (n*n)*r^2 in double, each
-// product rounded once (__dmul_rn: no contraction).
+// Windows: |v - s/n| <= r with r^3 = N/K, i.e. K*q^3 <= N*n^3 for
+// q = |n*v - s|.  A double comparison of q/n with r (r = cbrt(N/K) within two
+// ulps, q/n within one) decides every value farther than 1e-9 relative from
+// the edge; the rest are decided in 128-bit integers.  There q <= (1 + 1e-9)
+// n r, and a volume holds at most 2^30 voxels (n, N <= 2^30), so K*q^3 and
+// N*n^3 both stay below 2^121.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool vin_window(long long v, long long n, long long s, double r2)
+__device__ __forceinline__ bool vin_window(long long v, long long n, long long s, long long N, long long K,
+                                           double r)
 {
-    const double d = (double)(n * v - s);
-    return __dmul_rn(d, d) <= __dmul_rn(__dmul_rn((double)n, (double)n), r2);
+    const long long d = n * v - s;
+    const unsigned long long q = (unsigned long long)(d < 0 ? -d : d);
+    const double x = (double)q / (double)n;
+    if (x < r * (1.0 - 1e-9)) return true;
+    if (x > r * (1.0 + 1e-9)) return false;
+    const unsigned __int128 lhs = (unsigned __int128)q * q * q * (unsigned long long)K;
+    const unsigned __int128 rhs =
+        (unsigned __int128)((unsigned long long)N * (unsigned long long)n) * ((unsigned long long)n * (unsigned long long)n);
+    return lhs <= rhs;
 }
 
-__device__ __forceinline__ void vwindow(long long n, long long s, double r, double r2, int lim, int &lo,
-                                        int &hi)
+__device__ __forceinline__ void vwindow(long long n, long long s, long long N, long long K, double r, int lim,
+                                        int &lo, int &hi)
 {
     const double c = (double)s / (double)n;
     int a = (int)floor(c - r) - 1, b = (int)ceil(c + r) + 1;
     a = max(a, 0);
     b = min(b, lim - 1);
-    while (a <= b && !vin_window(a, n, s, r2)) ++a;
-    while (b >= a && !vin_window(b, n, s, r2)) --b;
+    while (a <= b && !vin_window(a, n, s, N, K, r)) ++a;
+    while (b >= a && !vin_window(b, n, s, N, K, r)) --b;
     lo = a;
     hi = b;
 }
@@ -226,9 +238,9 @@ __global__ void k_vupdate(VoxArgs a, int from_acc)
     cd.tk = (float)((double)st / (double)n);
     cd.ex = e.x; cd.ey = e.y; cd.et = e.z;
     cd.pad = k;
-    vwindow(n, sx, a.r, a.r2, a.W, cd.xlo, cd.xhi);
-    vwindow(n, sy, a.r, a.r2, a.H, cd.ylo, cd.yhi);
-    vwindow(n, st, a.r, a.r2, a.T, cd.tlo, cd.thi);
+    vwindow(n, sx, a.N, a.K, a.r, a.W, cd.xlo, cd.xhi);
+    vwindow(n, sy, a.N, a.K, a.r, a.H, cd.ylo, cd.yhi);
+    vwindow(n, st, a.N, a.K, a.r, a.T, cd.tlo, cd.thi);
     a.cdev[k] = cd;
     if (cd.xlo > cd.xhi || cd.ylo > cd.yhi || cd.tlo > cd.thi) return;
     for (int tt = cd.tlo / VTT; tt <= cd.thi / VTT; ++tt)
@@ -810,7 +822,7 @@ int scalp_voxel_init(scalp_vctx **out, const scalp_volume *vol, int32_t K, float
     a.T = c->T; a.H = c->H; a.W = c->W; a.K = K; a.Keff = c->Keff;
     a.nx = c->nx; a.ny = c->ny; a.nt = c->nt;
     a.N = c->N; a.HW = (long long)c->H * c->W;
-    a.r = c->r; a.r2 = c->r * c->r;
+    a.r = c->r;
     a.lam = params->lambda;
     a.gamma = (float)c->gamma;
     a.ms2 = (float)((double)m * (double)m / (c->r * c->r));
@@ -936,7 +948,12 @@ int scalp_voxel_set_state(scalp_vctx *c, const scalp_voxel_state *s)
         return vfail(SCALP_E_ARG, "ctx and every state array are required");
     const size_t K = (size_t)c->Keff;
     for (size_t k = 0; k < K; ++k) {
-        if (s->n[k] < 1) return vfail(SCALP_E_ARG, "cluster %zu has n < 1", k);
+        if (s->n[k] < 1 || s->n[k] > (1LL << 30))
+            return vfail(SCALP_E_ARG, "cluster %zu has n outside [1, 2^30]", k);
+        const long long n = s->n[k];
+        if (s->sx[k] < 0 || s->sx[k] > n * (c->W - 1) || s->sy[k] < 0 || s->sy[k] > n * (c->H - 1) ||
+            s->st[k] < 0 || s->st[k] > n * (c->T - 1))
+            return vfail(SCALP_E_ARG, "barycenter of cluster %zu is outside the volume", k);
         const int32_t *e = s->endpoint + 3 * k;
         if (e[0] < 0 || e[0] >= c->W || e[1] < 0 || e[1] >= c->H || e[2] < 0 || e[2] >= c->T)
             return vfail(SCALP_E_ARG, "endpoint of cluster %zu is outside the volume", k);

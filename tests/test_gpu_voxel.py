@@ -9,6 +9,7 @@ import numpy as np
 import pytest
 
 import oracle
+from exact_rationals import cube_root_convergents
 from paper_1903_07149_gb300 import build as scalp_build
 from paper_1903_07149_gb300 import synth
 
@@ -79,6 +80,65 @@ def test_voxel_one_step_parity(S, T, H, W, K, t):
     assert np.array_equal(g["endpoint"][same], np.stack([orc.ex, orc.ey, orc.et], axis=1)[same])
     ref = np.stack([orc.cL, orc.cA, orc.cB], axis=1)[same]
     assert np.all(np.abs(g["color"][same] - ref) <= COLOR_RTOL * np.maximum(np.abs(ref), 1))
+    seg.close()
+
+
+@pytest.mark.parametrize("a", [2, 5, 8, 10, 100])
+def test_voxel_window_edges_exact(S, a):
+    """Window edges decided exactly: a 1 x 1 x 4000 volume with N/K = a, so
+    r = cbrt(a).  Cluster i sits alone with |v_i - X_i| = p/q at a voxel v_i,
+    p/q a convergent of cbrt(a) (within 1/q^2 of r, q up to 2^29, closer than
+    double rounding resolves), or p/q +- 1/q (just outside/inside); every
+    other cluster is far off.  v_i has no other candidate, so it takes label i
+    iff (p/q)^3 <= a, else keeps its label: GPU and oracle both match the
+    rational answer at every voxel."""
+    from fractions import Fraction
+
+    T, H, W = 1, 1, 4000
+    K = W // a
+    rng = np.random.default_rng(7700 + a)
+    rgb = rng.integers(0, 256, (T, H, W, 3), dtype=np.uint8)
+    con = rng.uniform(size=(T, H, W)).astype(np.float32)
+    orc = oracle.VSolver(oracle.lab_from_rgb(rgb), con, K)
+    Keff = orc.Keff
+    cases = []
+    for p, q in cube_root_convergents(a, 60):
+        if q > (1 << 29):
+            break
+        for num in (p, p - 1, p + 1):
+            if 0 < num <= 6 * q:
+                cases += [(num, q, +1), (num, q, -1)]
+    cases = cases[:min(len(cases), (W - 40) // 30, Keff - 1)]
+    st = orc.state()
+    st["labels"][...] = Keff - 1
+    st["n"][:] = 1
+    st["sx"][:] = W - 1
+    st["sy"][:] = 0
+    st["st"][:] = 0
+    st["ex"][:], st["ey"][:], st["et"][:] = W - 1, 0, 0
+    st["cL"][:], st["cA"][:], st["cB"][:] = 50.0, 0.0, 0.0
+    edge = []
+    for i, (num, q, sgn) in enumerate(cases):
+        v = 30 * i + 20 + 5 * sgn  # n*v - s = sgn*num: |v - X_i| = num/q
+        s_ = q * v - sgn * num
+        st["n"][i], st["sx"][i] = q, s_
+        st["ex"][i] = int((2 * s_ + q) // (2 * q))
+        edge.append((v, i, Fraction(num, q) ** 3 <= a))
+    orc.set_state(st)
+    seg = _seg(S, rgb, con, K)
+    assert seg.info.Keff == Keff and seg.info.r == orc.r
+    seg.set_state(_to_gpu_state(st))
+    seg.iterate(1)
+    g = seg.get_state()["labels"][0, 0]
+    orc.assign()
+    o = orc.labels[0, 0]
+    inside = 0
+    for v, i, want in edge:
+        assert (g[v] == i) == want, (a, v, i, want)
+        assert (o[v] == i) == want, (a, v, i, want)
+        inside += want
+    assert 0 < inside < len(edge)
+    assert np.array_equal(g, o)
     seg.close()
 
 

@@ -13,6 +13,7 @@ import numpy as np
 import pytest
 
 import oracle
+from exact_rationals import cube_root_convergents
 from paper_1903_07149_gb300 import synth
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
@@ -301,6 +302,108 @@ def test_bruteforce_tiny(seed):
                 assert s.labels[y, x] == kbest
                 checked += 1
     assert checked > 0.6 * N
+
+
+# --------------------------------------------------------------------------
+# The pixel-centric assignment (used to check single pixels of large images)
+# against the cluster-centric loop of Algorithm 1, on every pixel.
+# --------------------------------------------------------------------------
+def _assign_both(s):
+    """(labels, d) of the whole-image assignment and of assign_pixels over
+    every pixel, both from the solver's current state (left unchanged)."""
+    st = s.state()
+    lab_px, d_px = s.assign_pixels(np.arange(s.N))
+    d = s.assign(return_d=True)
+    lab = s.labels.copy()
+    s.set_state(st)
+    return lab.ravel(), d.ravel(), lab_px, d_px
+
+
+def test_assign_pixels_equals_assign_random_states():
+    for seed, (H, W, K, iters) in enumerate([(24, 32, 8, 2), (37, 29, 15, 1), (16, 50, 40, 3)]):
+        rgb, C, _ = synth.small_image(H, W, seed=140 + seed, n_cells=6)
+        s = oracle.Solver(oracle.lab_from_rgb(rgb), C, K)
+        s.iterate(iters)
+        lab, d, lab_px, d_px = _assign_both(s)
+        assert np.array_equal(lab, lab_px)
+        assert np.array_equal(d, d_px)  # the same D(p, C_k), bit for bit
+        assert np.all(np.isfinite(d))
+
+
+def test_assign_pixels_orphans_keep_label():
+    # every barycenter moved into the top-left quarter: the pixels of the other
+    # corner lie in no window and keep their previous label, with d = inf
+    H, W, K = 40, 40, 16
+    rgb, C, _ = synth.small_image(H, W, seed=150, n_cells=6)
+    s = oracle.Solver(oracle.lab_from_rgb(rgb), C, K)
+    st = s.state()
+    rng = np.random.default_rng(151)
+    for k in range(s.Keff):
+        x, y = (int(v) for v in rng.integers(0, 10, 2))
+        n = int(st["n"][k])
+        st["sx"][k], st["sy"][k] = n * x, n * y
+        st["ex"][k], st["ey"][k] = x, y
+    st["labels"] = rng.integers(0, s.Keff, (H, W)).astype(np.int32)
+    s.set_state(st)
+    lab, d, lab_px, d_px = _assign_both(s)
+    orphan = np.isinf(d)
+    assert orphan.sum() > 100 and (~orphan).sum() > 100
+    assert np.array_equal(lab, lab_px) and np.array_equal(np.isinf(d_px), orphan)
+    assert np.array_equal(d[~orphan], d_px[~orphan])
+    assert np.array_equal(lab[orphan], st["labels"].ravel()[orphan])
+
+
+def test_assign_pixels_exact_ties_go_to_smallest_k():
+    # constant colour equal to every cluster's, no contour: D is m^2/r^2 d_s
+    # plus path terms that vanish.  Clusters 1 and 2 sit at (10 - 3, 10) and
+    # (10 + 3, 10): the pixels of column 10 are at equal distance from both
+    # (exact ties); cluster 0 and the rest are far off.  The strict '<' in
+    # ascending k gives every tie to cluster 1.
+    H, W, K = 30, 40, 12
+    lab3 = (np.full((H, W), 40.0), np.full((H, W), 5.0), np.full((H, W), -7.0))
+    s = oracle.Solver(lab3, np.zeros((H, W)), K)
+    st = s.state()
+    where = {1: (7, 10), 2: (13, 10)}
+    for k in range(s.Keff):
+        x, y = where.get(k, (39 - (k % 3), 29 - (k % 2)))
+        n = 50
+        st["n"][k], st["sx"][k], st["sy"][k] = n, n * x, n * y
+        st["ex"][k], st["ey"][k] = x, y
+    st["cL"][:], st["cA"][:], st["cB"][:] = 40.0, 5.0, -7.0
+    s.set_state(st)
+    lab, d, lab_px, d_px = _assign_both(s)
+    assert np.array_equal(lab, lab_px) and np.array_equal(d, d_px)
+    ties = 0
+    for y in range(H):
+        D1, _ = s.distance(10, y, 1)
+        D2, _ = s.distance(10, y, 2)
+        assert D1 == D2
+        p = y * W + 10
+        if np.isfinite(d[p]) and d[p] == D1:
+            assert lab[p] == 1
+            ties += 1
+    assert ties >= 10
+
+
+@pytest.mark.parametrize("threads", [1, 3, 8])
+def test_iterate_rows_equals_iterate(threads):
+    # the CPU baseline's row-parallel iterations give Algorithm 1's state, bit
+    # for bit, on any number of threads (projections included)
+    H, W, K = 45, 61, 20
+    rgb, C, _ = synth.small_image(H, W, seed=160, n_cells=7)
+    lab = oracle.lab_from_rgb(rgb)
+    a = oracle.Solver(lab, C, K)
+    b = oracle.Solver(lab, C, K)
+    projected = 0
+    for _ in range(4):
+        a.iterate(1)
+        b.iterate_rows(1, threads)
+        projected += a.projections
+        assert b.projections == a.projections and b.orphans == a.orphans
+        sa, sb = a.state(), b.state()
+        for key in sa:
+            assert np.array_equal(sa[key], sb[key]), key
+    assert projected > 0
 
 
 # --------------------------------------------------------------------------
@@ -651,15 +754,74 @@ def test_vconstant_volume_fixed_point():
     assert s.projections == 0
 
 
+def _vaxis_in_window(v, n, sv, N, K):
+    """|v - sv/n| <= r with r^3 = N/K, in rational arithmetic (cubing both
+    non-negative sides): |v - sv/n|^3 <= N/K."""
+    return abs(Fraction(v) - Fraction(sv, n)) ** 3 <= Fraction(N, K)
+
+
 def _vwindow_mask(s, k, T, H, W):
-    """Voxels of cluster k's window, by the per-axis reading (double, as stated)."""
-    def axis(v, n, sv):
-        d = (n * v - sv).astype(np.float64)
-        return d * d <= (float(n) * float(n)) * s.r2
-    t, y, x = np.arange(T), np.arange(H), np.arange(W)
-    n = int(s.n[k])
-    return (axis(t, n, int(s.st[k]))[:, None, None] & axis(y, n, int(s.sy[k]))[None, :, None]
-            & axis(x, n, int(s.sx[k]))[None, None, :])
+    """Voxels of cluster k's window: per axis |v - X_k| <= cbrt(N/K), exactly."""
+    n, N = int(s.n[k]), T * H * W
+    def axis(length, sv):
+        return np.array([_vaxis_in_window(v, n, sv, N, s.K) for v in range(length)])
+    return (axis(T, int(s.st[k]))[:, None, None] & axis(H, int(s.sy[k]))[None, :, None]
+            & axis(W, int(s.sx[k]))[None, None, :])
+
+
+def test_cube_root_convergents_helper():
+    # the helper's first convergents of 2^(1/3) = [1; 3, 1, 5, 1, 1, 4, 1, 1, 8, ...]
+    conv = cube_root_convergents(2, 6)
+    assert conv[:6] == [(1, 1), (4, 3), (5, 4), (29, 23), (34, 27), (63, 50)]
+    for p, q in conv:
+        assert abs(p / q - 2 ** (1 / 3)) < 1 / q ** 2
+    assert cube_root_convergents(27, 3)[0] == (3, 1)
+
+
+def test_vwindow_predicate_exact():
+    """The supervoxel window |v - s/n| <= r, r^3 = N/K, against rational
+    arithmetic: random values, exact edges (N/K a perfect cube), values within
+    1e-12 of an irrational edge (convergents of the cube root), huge clusters."""
+    rng = np.random.default_rng(31)
+    for _ in range(3000):
+        N = int(rng.integers(10, 1 << 30))
+        K = int(rng.integers(1, min(N, 200000) + 1))
+        n = int(rng.integers(1, 1 << 20))
+        s = int(rng.integers(0, n * 4000))
+        r = (N / K) ** (1 / 3)
+        xk = s / n
+        for v in {math.floor(xk - r) - 1, math.floor(xk - r), math.ceil(xk - r),
+                  math.floor(xk + r), math.ceil(xk + r), math.ceil(xk + r) + 1}:
+            assert oracle.vin_window(v, n, s, N, K) == _vaxis_in_window(v, n, s, N, K)
+    # N/K a perfect cube: r = 3 exactly, and |v - s/n| = 3 is inside, 3 + 1/n not
+    for n in (1, 7, 1000, 1 << 29):
+        for v in (10, 100):
+            assert oracle.vin_window(v, n, n * (v - 3), 27 * 5, 5)
+            assert oracle.vin_window(v, n, n * (v + 3), 27 * 5, 5)
+            assert not oracle.vin_window(v, n, n * (v - 3) - 1, 27 * 5, 5)
+            assert not oracle.vin_window(v, n, n * (v + 3) + 1, 27 * 5, 5)
+    # |v - s/n| = p/q, a convergent of cbrt(a): alternately just inside and
+    # just outside the edge, closer than double rounding of r can resolve
+    checked_close = 0
+    for a in (2, 3, 5, 7, 10, 100, 999):
+        for p, q in cube_root_convergents(a, 40):
+            if q > (1 << 29) or p > 1024 * q:
+                break
+            N, K = a * 1000, 1000
+            n = q
+            for v, s in ((5, 5 * q - p), (5, 5 * q + p)):  # n*v - s = +p and -p
+                want = Fraction(p, q) ** 3 <= a
+                assert oracle.vin_window(v, n, s, N, K) == want
+                assert _vaxis_in_window(v, n, s, N, K) == want
+            if abs(p / q - a ** (1 / 3)) < 1e-12 * a ** (1 / 3):
+                checked_close += 1
+    assert checked_close >= 10
+    # huge clusters: n = 2^30 voxels, K = 1 (r = 2^10): the window's extreme
+    # values and one past them, without overflow
+    N, K, n = 1 << 30, 1, 1 << 30
+    assert oracle.vin_window(1024, n, 0, N, K) and not oracle.vin_window(1025, n, 0, N, K)
+    assert oracle.vin_window(0, n, 1024 * n, N, K) and not oracle.vin_window(0, n, 1025 * n, N, K)
+    assert not oracle.vin_window(65535, n, 0, N, K)
 
 
 def test_vslic_special_case():
