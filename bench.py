@@ -31,12 +31,20 @@ UNIT = "Mpix*iter/s"
 DEFAULT_WORKLOAD = "hd_1080x1920_k2000"
 SMS = 152
 FP32_LANES_PER_SM = 128
+SMEM_BYTES_PER_CLK_PER_SM = 128  # 32 banks x 4 bytes
 FALLBACK_SM_MHZ = 2070.0
-# FP32 operations the method needs: per path sample 3 sub + 3 mul-add + 1 add,
-# per evaluated (pixel, cluster) pair 20 (own colour distance, spatial
-# distance, Eq. 1-3 assembly, comparison).
-FLOPS_PER_SAMPLE = 7
-FLOPS_PER_PAIR = 20
+# Algorithmic work of the assignment, as the method states it:
+#  * each path sample gathers one (L, a, b, w) pixel: 16 bytes stored in FP32,
+#    8 in FP16 (the binding roof: on-chip load bandwidth);
+#  * FP32 flops: per sample 3 sub, 3 mul-add (counted as 6) and 2 adds, about
+#    10 counted conservatively; per evaluated (pixel, cluster) pair about 30
+#    (own colour distance, spatial distance, Eq. 1-3 assembly, comparison).
+FLOPS_PER_SAMPLE = 10
+FLOPS_PER_PAIR = 30
+# The FP32 lane operations counted per sample / pair in the earlier line
+# (kept as a secondary figure): 7 and 20.
+LANE_OPS_PER_SAMPLE = 7
+LANE_OPS_PER_PAIR = 20
 
 
 def parse():
@@ -198,46 +206,172 @@ def measured_peaks():
         return None
 
 
+def assign_roofline(samples, pairs, pixels, launch_s, storage, sm_mhz, clk_measured=True, traffic=None):
+    """Roofline of one assignment launch from its algorithmic work: the path
+    samples' gathered bytes against the shared-memory load peak (the binding
+    roof), FP32 flops against the FMA peak, and the compulsory HBM bytes
+    against the measured copy bandwidth.  Peaks other than HBM are derived
+    from unit counts and the SM clock (no measured figure exists for them)."""
+    bps = 16 if storage == "f32" else 8
+    clk = f"{sm_mhz:.0f} MHz ({'nvidia-smi clocks.max.sm' if clk_measured else 'fallback'})"
+    smem_peak = SMEM_BYTES_PER_CLK_PER_SM * SMS * sm_mhz * 1e6 / 1e9
+    fma_peak = SMS * FP32_LANES_PER_SM * 2 * sm_mhz * 1e6 / 1e12
+    lane_peak = SMS * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
+    ok = launch_s and launch_s > 0
+    smem = samples * bps / launch_s / 1e9 if ok else None
+    flops = (FLOPS_PER_SAMPLE * samples + FLOPS_PER_PAIR * pairs) / launch_s / 1e12 if ok else None
+    lane = (LANE_OPS_PER_SAMPLE * samples + LANE_OPS_PER_PAIR * pairs) / launch_s / 1e12 if ok else None
+    peaks = measured_peaks() or {}
+    hbm_peak = peaks.get("hbm_gbs") or FALLBACK_HBM_GBS
+    hbm = pixels * (bps + 8) / launch_s / 1e9 if ok else None
+    return {
+        "bound": "smem", "kernel": "k_assign", "achieved": smem, "peak": smem_peak, "unit": "GB/s",
+        "frac": smem / smem_peak if ok else None, "traffic": traffic,
+        "peak_source": f"derived: {SMEM_BYTES_PER_CLK_PER_SM} B/clk/SM shared-memory loads x {SMS} SMs x {clk}",
+        "algorithmic": {"samples_per_launch": samples, "pairs_per_launch": pairs,
+                        "bytes_per_sample": bps, "flops_per_sample": FLOPS_PER_SAMPLE,
+                        "flops_per_pair": FLOPS_PER_PAIR},
+        "launch_ms": launch_s * 1e3 if ok else None,
+        "alu": {"achieved": flops, "peak": fma_peak, "unit": "TFLOP/s",
+                "frac": flops / fma_peak if ok else None,
+                "peak_source": f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 (FMA) x {clk}"},
+        "alu_lane_ops": {"achieved": lane, "peak": lane_peak, "unit": "T op/s",
+                         "frac": lane / lane_peak if ok else None,
+                         "ops_per_sample": LANE_OPS_PER_SAMPLE, "ops_per_pair": LANE_OPS_PER_PAIR},
+        "hbm_compulsory": {"achieved": hbm, "peak": hbm_peak, "unit": "GB/s",
+                           "frac": hbm / hbm_peak if ok else None,
+                           "bytes_per_pixel": bps + 8,
+                           "peak_source": "measured (MEASURED_PEAKS.json)" if peaks.get("hbm_gbs")
+                           else "fallback 6.8 TB/s"},
+    }
+
+
 # ---------------------------------------------------------------------------
-def cpu_baseline_oracle(w, rgb, con, budget_s: float = 20.0):
-    """The FP64 oracle as it stands, single-threaded, on a bounded sample:
-    grid initialisation then as many whole-image iterations as fit the budget
-    (at least one)."""
+# CPU legs: the only place bench.py runs the oracle (the CPU baseline, the
+# reference arm and the FP64 labels the precision statement compares with).
+# ---------------------------------------------------------------------------
+def host_cpu():
+    """(threads the oracle uses, CPU model) of this host."""
+    n = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Model"):
+                model = line.split(":", 1)[1].strip()
+                if line.startswith("Model name"):
+                    break
+    except Exception:
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for line in f:
+                    if line.lower().startswith(("model name", "cpu part")):
+                        model = line.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    import platform
+
+    return n, f"{model or 'unknown'} ({platform.machine()})"
+
+
+def cpu_baseline_oracle(w, rgb, con, budget_s: float = 20.0, runs: int = 3):
+    """The FP64 oracle as it stands on every host core (its row-parallel
+    iterations, bit-identical to Algorithm 1's loop), on a bounded sample:
+    grid initialisation then as many whole-image iterations as fit about
+    budget_s / runs seconds; the median of `runs` such runs."""
+    import statistics
+
     import oracle
 
+    cores, model = host_cpu()
     lab = oracle.lab_from_rgb(rgb)
-    s = oracle.Solver(lab, con, w.K)
-    done, t_iter = 0, 0.0
-    while True:
-        t0 = time.perf_counter()
-        s.iterate(1)
-        t_iter += time.perf_counter() - t0
-        done += 1
-        if t_iter * (done + 1) / done > budget_s or done >= w.iters:
-            break
     N = w.H * w.W
-    return {"value": N * done / t_iter / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{done} whole-image iteration(s) of {w.name} from the grid state "
-                      f"({t_iter:.1f} s, FP64 C oracle, 1 thread)"}
+    vals, iters = [], []
+    for _ in range(runs):
+        s = oracle.Solver(lab, con, w.K)
+        done, t_iter = 0, 0.0
+        while True:
+            t0 = time.perf_counter()
+            s.iterate_rows(1, cores)
+            t_iter += time.perf_counter() - t0
+            done += 1
+            if t_iter * (done + 1) / done > budget_s / runs or done >= w.iters:
+                break
+        vals.append(N * done / t_iter / 1e6)
+        iters.append(done)
+    return {"value": statistics.median(vals), "unit": UNIT, "cores": cores, "cpu": model,
+            "kind": "oracle", "runs": vals,
+            "sample": f"median of {runs} runs, each {iters[0]} whole-image iteration(s) of {w.name} "
+                      f"from the grid state (FP64 C oracle, rows over {cores} OpenMP threads)"}
+
+
+def cpu_precision_statement(gpu_states, cores):
+    """Label agreement and centre / colour errors of GPU solves against the
+    FP64 oracle run the same way (10 iterations from the grid, free-running).
+    gpu_states: {key: (workload, rgb, contour, {storage: state})}."""
+    import numpy as np
+
+    import oracle
+
+    out = {}
+    for key, (w, rgb, con, states) in gpu_states.items():
+        orc = oracle.Solver(oracle.lab_from_rgb(rgb), con, w.K)
+        t0 = time.perf_counter()
+        orc.iterate_rows(w.iters, cores)
+        t_orc = time.perf_counter() - t0
+        co, ref = orc.centers(), orc.colors()
+        row = {"H": w.H, "W": w.W, "K": w.K, "Keff": int(orc.Keff), "iters": w.iters,
+               "oracle_s": t_orc}
+        for storage, g in states.items():
+            diff = g["labels"] != orc.labels
+            bad = np.unique(np.concatenate([g["labels"][diff], orc.labels[diff]]))
+            same = np.setdiff1d(np.arange(orc.Keff), bad)
+            cg = np.stack([g["sx"] / g["n"], g["sy"] / g["n"]], axis=1)
+            dcen = np.hypot(*(cg - co).T)
+            dcol = np.max(np.abs(g["color"] - ref) / np.maximum(np.abs(ref), 1), axis=1)
+            row[storage] = {
+                "label_agreement": float(1.0 - diff.mean()),
+                "meets_99_9": bool(1.0 - diff.mean() >= 0.999),
+                "clusters_same_pixels": int(len(same)),
+                "centre_err_max_px": float(dcen.max()),
+                "centre_err_p99_px": float(np.percentile(dcen, 99)),
+                "centre_err_max_px_same_pixels": float(dcen[same].max()) if len(same) else None,
+                "colour_rel_err_max_same_pixels": float(dcol[same].max()) if len(same) else None,
+            }
+        out[key] = row
+    return out
+
+
+def line_config(w, world: int) -> dict:
+    """The workload both arms name (same keys and values in both lines)."""
+    return {"workload": w.name, "H": w.H, "W": w.W, "K": w.K, "iters": w.iters,
+            "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"}
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle (there is no reference code), on
+    every host core, on the same workload; each step is one whole-image
+    iteration (a bounded sample of the workload's 10-iteration solve)."""
     world, rank, local = dist_env()
     if rank != 0:
         return
     from paper_1903_07149_gb300 import synth
     import oracle
 
+    cores, model = host_cpu()
     w, rgb, con = synth.single_image_config(args.workload)
     lab = oracle.lab_from_rgb(rgb)
     N = w.H * w.W
     s = oracle.Solver(lab, con, w.K)
     for _ in range(args.warmup):
-        s.iterate(1)
+        s.iterate_rows(1, cores)
     t = 0.0
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        s.iterate(1)
+        s.iterate_rows(1, cores)
         t += time.perf_counter() - t0
     value = N * args.steps / t / 1e6
     line = {
@@ -245,10 +379,12 @@ def run_reference(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": w.name, "H": w.H, "W": w.W, "K": w.K, "iters_per_step": 1,
-                   "note": "each step is one whole-image iteration of the FP64 CPU oracle"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{args.steps} single iterations of {w.name}"},
+        "config": line_config(w, world),
+        "timing": "each step is one whole-image iteration of the FP64 CPU oracle "
+                  f"(rows over {cores} OpenMP threads)",
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "cpu": model, "kind": "oracle",
+                         "sample": f"{args.steps} whole-image iterations of {w.name}, "
+                                   f"after {args.warmup} warm-up iterations"},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -618,22 +754,26 @@ def measure_voxel(args, flush):
         seg.close()
     ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)) / n_steps
     N = T * H * W
-    flops = FLOPS_PER_SAMPLE * samples + FLOPS_PER_PAIR * pairs
-    peak = SMS * FP32_LANES_PER_SM * FALLBACK_SM_MHZ * 1e6 / 1e12
+    roof = assign_roofline(samples, pairs, N, it_ms / 1e3, "f32", FALLBACK_SM_MHZ, clk_measured=False)
+    roof["kernel"] = "k_vassign"
+    roof["note"] = "whole iteration (assignment, update, projection, lists) timed, not the assignment alone"
     return {"workload": name, "T": T, "H": H, "W": W, "K": K, "Keff": keff, "iters": iters,
             "value": N * iters / (ms / 1e3) / 1e6, "unit": "Mvox*iter/s", "ms_per_solve": ms,
             "iteration_ms": it_ms, "samples_per_iteration": samples, "pairs_per_iteration": pairs,
-            "roofline": {"bound": "alu", "achieved": flops / (it_ms / 1e3) / 1e12, "unit": "TFLOP/s",
-                         "peak": peak, "frac": flops / (it_ms / 1e3) / 1e12 / peak,
-                         "note": "whole iteration (all four kernels) timed; FP32 lanes at 2070 MHz"}}
+            "roofline": roof}
 
 
-def measure_single_form(args, w, rgb, con, storage: str, flush):
-    """Plain single-image solve with the given plane storage (FP16 form)."""
+def measure_single_form(args, w, rgb, con, storage: str, flush, steps=None, sm_mhz=None):
+    """Plain single-image solves with the given plane storage: whole solves
+    (reload, 10 iterations, connectivity), then the assignment's time per
+    launch (a second pass with event records) and its path samples (counted
+    on the device), for its roofline; also returns the solver state after
+    one solve (for the precision statement)."""
     import torch
 
     from paper_1903_07149_gb300 import scalp
 
+    steps = steps or args.steps
     stream = torch.cuda.Stream()
     d_rgb = torch.from_numpy(rgb).cuda()
     d_con = torch.from_numpy(con).cuda()
@@ -648,26 +788,71 @@ def measure_single_form(args, w, rgb, con, storage: str, flush):
 
         for _ in range(args.warmup):
             step()
-        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ev0 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+        ev1 = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
         torch.cuda.synchronize()
-        for i in range(args.steps):
+        for i in range(steps):
             flush.zero_()
             ev0[i].record(stream)
             step()
             ev1[i].record(stream)
         torch.cuda.synchronize()
         seg.profile(1)  # a second pass for the assignment's time per launch
-        for i in range(args.steps):
+        for i in range(steps):
             flush.zero_()
             step()
         torch.cuda.synchronize()
         ms_assign, n_assign = seg.profile(0)
+        seg.count_samples(1)
+        seg.reload(d_rgb, d_con)
+        seg.iterate(w.iters)
+        samples, pairs = seg.count_samples(0)
+        state = seg.get_state()
         seg.close()
     total_ms = sum(a.elapsed_time(c) for a, c in zip(ev0, ev1))
-    return {"value": w.H * w.W * w.iters * args.steps / (total_ms / 1e3) / 1e6, "unit": UNIT,
-            "ms_per_step": total_ms / args.steps, "storage": storage, "workload": w.name,
-            "assign_ms_per_launch": ms_assign / max(n_assign, 1)}
+    t_launch = ms_assign / max(n_assign, 1) / 1e3
+    roof = assign_roofline(samples / w.iters, pairs / w.iters, w.H * w.W, t_launch, storage,
+                           sm_mhz or FALLBACK_SM_MHZ, clk_measured=sm_mhz is not None,
+                           traffic=traffic_per_launch(storage) if w.name == DEFAULT_WORKLOAD else None)
+    return {"value": w.H * w.W * w.iters * steps / (total_ms / 1e3) / 1e6, "unit": UNIT,
+            "ms_per_step": total_ms / steps, "storage": storage, "workload": w.name,
+            "assign_ms_per_launch": t_launch * 1e3, "roofline": roof}, state
+
+
+def measure_uhd_precision_form(args, flush, sm_mhz):
+    """The precision form's own workload: 2160x3840, K=10000, 10 iterations,
+    FP16 planes beside FP32 planes on the same input."""
+    from paper_1903_07149_gb300 import synth
+
+    w, rgb, con = synth.single_image_config("uhd_2160x3840_k10000")
+    res, states = {}, {}
+    for storage in ("f32", "f16"):
+        res[storage], states[storage] = measure_single_form(args, w, rgb, con, storage, flush,
+                                                            steps=max(args.steps // 2, 3), sm_mhz=sm_mhz)
+    res["f16_over_f32"] = res["f16"]["value"] / res["f32"]["value"]
+    return res, (w, rgb, con, states)
+
+
+def batch_sample_states(bws, rgbs, cons, count: int = 4):
+    """Solver states of the first `count` images of the batch mix, solved as
+    one batch in each storage (10 iterations, free-running)."""
+    import torch
+
+    from paper_1903_07149_gb300 import scalp
+
+    out = {}
+    ws = bws[:count]
+    d_rgb = [torch.from_numpy(r).cuda() for r in rgbs[:count]]
+    d_con = [torch.from_numpy(c).cuda() for c in cons[:count]]
+    states = {}
+    for storage in ("f32", "f16"):
+        b = scalp.Batch(d_rgb, d_con, [w.K for w in ws], storage=storage)
+        b.iterate(ws[0].iters)
+        states[storage] = [b.get_state(i) for i in range(count)]
+        b.close()
+    for i, w in enumerate(ws):
+        out[f"batch_image_{i}"] = (w, rgbs[i], cons[i], {st: states[st][i] for st in states})
+    return out
 
 
 def run_ours(args):
@@ -793,23 +978,11 @@ def run_ours(args):
 
     # roofline of the dominant kernel (the assignment)
     t_launch = ms_assign / max(assign_launches, 1) / 1e3
-    flops = (FLOPS_PER_SAMPLE * samples + FLOPS_PER_PAIR * pairs) / iters
-    sm_mhz = (clk or {}).get("sm_max_mhz") or FALLBACK_SM_MHZ
-    peak = SMS * FP32_LANES_PER_SM * sm_mhz * 1e6 / 1e12
-    achieved = flops / t_launch / 1e12 if t_launch > 0 else None
-    bytes_per_sample = 16 if args.storage == "f32" else 8
-    roofline = {
-        "bound": "alu", "kernel": "k_assign", "achieved": achieved, "peak": peak,
-        "unit": "TFLOP/s", "frac": achieved / peak if achieved else None,
-        "traffic": traffic_per_launch(args.storage),
-        "peak_source": f"derived: {SMS} SMs x {FP32_LANES_PER_SM} FP32 lanes x {sm_mhz:.0f} MHz "
-                       "(nvidia-smi clocks.max.sm)" if clk else "derived: fallback 2070 MHz",
-        "algorithmic": {"samples_per_launch": samples / iters, "pairs_per_launch": pairs / iters,
-                        "flops_per_sample": FLOPS_PER_SAMPLE, "flops_per_pair": FLOPS_PER_PAIR},
-        "launch_ms": t_launch * 1e3, "launches": assign_launches,
-        "onchip_sample_GBps": samples / iters * bytes_per_sample / t_launch / 1e9 if t_launch else None,
-        "hbm_compulsory_GBps": N * (bytes_per_sample + 8) / t_launch / 1e9 if t_launch else None,
-    }
+    sm_max = (clk or {}).get("sm_max_mhz")
+    roofline = assign_roofline(samples / iters, pairs / iters, N, t_launch, args.storage,
+                               sm_max or FALLBACK_SM_MHZ, clk_measured=sm_max is not None,
+                               traffic=traffic_per_launch(args.storage))
+    roofline["launches"] = assign_launches
     peaks = measured_peaks()
     if peaks:
         roofline["measured_peaks"] = peaks
@@ -817,27 +990,31 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": args.storage, "data": "synthetic",
-        "config": {"workload": w.name, "H": w.H, "W": w.W, "K": w.K, "iters": iters,
-                   "storage": args.storage, "form": "plain single image",
-                   "l2": "flushed (256 MB write) before each timed step",
-                   "parallelism": f"replicas x{world}" if world > 1 else "1 GPU",
-                   "n_labels": int(n_labels)},
+        "config": line_config(w, world),
+        "timing": {"form": "plain single image", "storage": args.storage,
+                   "step": "reload + 10 iterations + connectivity + labels in device memory",
+                   "l2": "flushed (256 MB write) before each timed step"},
+        "n_labels": int(n_labels),
         "clocks": clk, "e2e": e2e,
         "gpu_launches": args.steps * (reload_launches(w.H, w.W) + iter_launches(w.H, w.W) * iters
                                       + ccl_launches(w.H, w.W)),
         "roofline": roofline,
     }
+    precision_inputs = {}
     if not args.no_forms:
         from paper_1903_07149_gb300 import synth
 
         other = "f16" if args.storage == "f32" else "f32"
         bws = synth.batch_configs()
         batch_imgs = (bws, *synth.batch_images(bws))
+        single_other, st_other = measure_single_form(args, w, rgb, con, other, flush, sm_mhz=sm_max)
         line["forms"] = {
-            f"single_{other}": measure_single_form(args, w, rgb, con, other, flush),
+            f"single_{other}": single_other,
             "batched_f16": measure_batch(args, "f16", flush, batch_imgs),
             "batched_f32": measure_batch(args, "f32", flush, batch_imgs),
         }
+        uhd, uhd_states = measure_uhd_precision_form(args, flush, sm_max)
+        line["forms"]["uhd_2160x3840_k10000"] = uhd
         line["forms"]["multiscale_boundary_map"] = measure_multiscale(args, flush)
         _, _, cells = synth.voronoi_image(w.H, w.W, w.n_cells, gradient=w.gradient,
                                           noise_sigma=w.noise_sigma, seed=w.seed)
@@ -846,8 +1023,27 @@ def run_ours(args):
         line["forms"]["supervoxels"] = measure_voxel(args, flush)
         if not args.no_serving:
             line["forms"]["serving"] = measure_serving(args, batch_imgs)
+        # GPU states for the precision statement (computed in the CPU leg)
+        seg.reload(d_rgb, d_con)
+        seg.iterate(iters)
+        st_main = seg.get_state()
+        w0, rgb0, con0 = synth.single_image_config("bsd_321x481_k400")
+        st0 = {}
+        for storage in ("f32", "f16"):
+            s0 = scalp.Segmenter(torch.from_numpy(rgb0).cuda(), torch.from_numpy(con0).cuda(), w0.K,
+                                 storage=storage)
+            s0.iterate(w0.iters)
+            st0[storage] = s0.get_state()
+            s0.close()
+        precision_inputs = {w0.name: (w0, rgb0, con0, st0),
+                            w.name: (w, rgb, con, {args.storage: st_main, other: st_other}),
+                            "uhd_2160x3840_k10000": uhd_states}
+        precision_inputs.update(batch_sample_states(*batch_imgs))
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline_oracle(w, rgb, con)
+        if precision_inputs:
+            line["precision_vs_fp64_oracle"] = cpu_precision_statement(
+                precision_inputs, line["cpu_baseline"]["cores"])
     print(json.dumps(line), flush=True)
     seg.close()
     if dist:

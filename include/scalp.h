@@ -27,8 +27,8 @@
  *     scalp_workspace_bytes() bytes, 256-byte aligned), which must stay valid
  *     until scalp_destroy().  The context itself is host memory.  A host
  *     thread that reads a context's status (scalp_labels and other calls that
- *     synchronise) keeps 64 bytes of pinned host memory for the process's
- *     life; a batch holds about 110 bytes of pinned host memory per image
+ *     synchronise) keeps 64 bytes of pinned host memory until it exits; a
+ *     batch holds about 110 bytes of pinned host memory per image
  *     (staging for its per-call pointer tables and its gathered status).
  *   - Images are row-major, pixel (x, y) at row y, column x, with integer
  *     coordinates at pixel centres.  Labels are int32, row-major H x W.
@@ -149,6 +149,15 @@ int scalp_get_info(const scalp_ctx *ctx, scalp_info *info);
 
 /* Copies the state to host memory (synchronises). */
 int scalp_get_state(scalp_ctx *ctx, const scalp_state *state);
+
+/* The cluster descriptors C_k = [l_k, a_k, b_k, X_k] of Sec. II-A, as
+ * Algorithm 1's last update left them: out (host memory, Keff x 5 floats,
+ * caller-owned) receives per cluster k the mean CIELab colour (l_k, a_k, b_k)
+ * and the barycenter X_k = (x_k, y_k) in pixel coordinates (the exact integer
+ * coordinate sums divided by |S_k|, rounded once to float); *K_eff receives
+ * Keff.  A cluster that has lost every pixel keeps its last descriptor.
+ * Synchronises the stream; out must hold scalp_get_info()'s Keff x 5 floats. */
+int scalp_clusters(scalp_ctx *ctx, float *out, int32_t *K_eff);
 
 /* Replaces the state (checkpoint restore, or injecting a state to compute one
  * assignment from).  Labels must be in [0, Keff), n >= 1, 0 <= sx/n <= W-1,
@@ -363,7 +372,16 @@ int scalp_server_step(scalp_server *s, int32_t *n_running);
  * 0 (the default) iterates every request in flight.  *n_running of
  * scalp_server_step counts those iterated. */
 int scalp_server_set_step_budget(scalp_server *s, int64_t max_pixels);
+/* *done = 1 once request id has been delivered or has failed; its memory is
+ * then released and the id is forgotten.  A device-side check or bounded wait
+ * that failed in the request's own work returns SCALP_E_INTERNAL or
+ * SCALP_E_TIMEOUT with *done = 1 (its labels are not valid). */
 int scalp_server_poll(scalp_server *s, uint64_t id, int32_t *done, int32_t *n_labels);
+/* Fault injection for tests of the error path, on the host: when request id
+ * completes, its status reads as if a device-side check had failed with
+ * `error` (nonzero), or a bounded wait had given up (timeout nonzero).  No
+ * GPU work is changed. */
+int scalp_server_inject_status(scalp_server *s, uint64_t id, int32_t error, int32_t timeout);
 int scalp_server_stats(const scalp_server *s, int32_t *in_flight, size_t *pool_free_bytes);
 void scalp_server_destroy(scalp_server *s);
 

@@ -113,20 +113,31 @@ void set_last_error(const char *msg) { g_last_error = msg; }
 
 // One pinned buffer per host thread for status reads: a read is a copy and a
 // synchronisation inside one call, and a context is used by one thread at a
-// time.  Made on the thread's first read and kept for the process's life, so
+// time.  Made on the thread's first read and freed when the thread exits, so
 // that contexts made for one image each allocate nothing.
+struct PinnedStatus {
+    DevCounters *buf = nullptr;
+    bool tried = false;
+    ~PinnedStatus()
+    {
+        // at thread (or process) exit; a runtime already torn down is no error here
+        if (buf) cudaFreeHost(buf);
+    }
+};
+
 DevCounters *pinned_status_buffer()
 {
-    thread_local DevCounters *buf = nullptr;
-    thread_local bool tried = false;
-    if (!buf && !tried) {
-        tried = true;
-        if (cudaMallocHost(&buf, sizeof(DevCounters)) != cudaSuccess) {
-            buf = nullptr;
-            cudaGetLastError();
+    thread_local PinnedStatus t;
+    if (!t.buf && !t.tried) {
+        t.tried = true;
+        const cudaError_t pending = cudaPeekAtLastError();
+        if (cudaMallocHost(&t.buf, sizeof(DevCounters)) != cudaSuccess) {
+            t.buf = nullptr;
+            // clear only the error this allocation raised, not one pending before it
+            if (pending == cudaSuccess) cudaGetLastError();
         }
     }
-    return buf;
+    return t.buf;
 }
 }  // namespace scalp
 
@@ -583,19 +594,19 @@ int scalp_labels(scalp_ctx *c, int32_t *out, int32_t out_on_device, int32_t enfo
     int nlab = c->Keff;
     size_t bytes = sizeof(int) * (size_t)c->N;
     if (enforce) {
-        int *dst = out_on_device ? out : c->ccl.link;  // link is free once resolved
+        // the final labels go straight to a device output (which must not alias
+        // the workspace), else to the link buffer, free once the links are
+        // resolved, and from there to the host
+        int *dst = out_on_device ? out : c->ccl.link;
         int *d_nlab = &c->a.ctr->n_labels;  // read back with the counters
-        if (out_on_device) {
-            // the output must not alias a buffer the enforcement still reads
-            launch_ccl(c->a.labels, c->H, c->W, c->K, dst, c->ccl, d_nlab, c->a.ctr, c->st);
-        } else {
-            launch_ccl(c->a.labels, c->H, c->W, c->K, dst, c->ccl, d_nlab, c->a.ctr, c->st);
+        launch_ccl(c->a.labels, c->H, c->W, c->K, dst, c->ccl, d_nlab, c->a.ctr, c->st);
+        rc = launch_check(c, "connectivity kernels");
+        if (rc) return rc;
+        if (!out_on_device) {
             rc = cuda_check(c, cudaMemcpyAsync(out, dst, bytes, cudaMemcpyDeviceToHost, c->st),
                             "copy labels");
             if (rc) return rc;
         }
-        rc = launch_check(c, "connectivity kernels");
-        if (rc) return rc;
     } else {
         rc = cuda_check(c, cudaMemcpyAsync(out, c->a.labels, bytes,
                                            out_on_device ? cudaMemcpyDeviceToDevice
@@ -647,6 +658,33 @@ int scalp_get_state(scalp_ctx *c, const scalp_state *s)
         s->endpoint[2 * k] = end[k].x;
         s->endpoint[2 * k + 1] = end[k].y;
     }
+    return SCALP_OK;
+}
+
+int scalp_clusters(scalp_ctx *c, float *out, int32_t *K_eff)
+{
+    if (!c || !out || !K_eff) return fail(c, SCALP_E_ARG, "ctx, out and K_eff are required");
+    const size_t K = c->Keff;
+    std::vector<float4> col(K);
+    std::vector<long long> n(K), sx(K), sy(K);
+    int rc = 0;
+    rc = rc ? rc : cuda_check(c, cudaMemcpyAsync(col.data(), c->a.st_col, 16 * K, cudaMemcpyDeviceToHost, c->st), "copy clusters");
+    rc = rc ? rc : cuda_check(c, cudaMemcpyAsync(n.data(), c->a.st_n, 8 * K, cudaMemcpyDeviceToHost, c->st), "copy clusters");
+    rc = rc ? rc : cuda_check(c, cudaMemcpyAsync(sx.data(), c->a.st_sx, 8 * K, cudaMemcpyDeviceToHost, c->st), "copy clusters");
+    rc = rc ? rc : cuda_check(c, cudaMemcpyAsync(sy.data(), c->a.st_sy, 8 * K, cudaMemcpyDeviceToHost, c->st), "copy clusters");
+    if (rc) return rc;
+    rc = device_status(c);
+    if (rc) return rc;
+    for (size_t k = 0; k < K; ++k) {
+        float *o = out + 5 * k;
+        o[0] = col[k].x;
+        o[1] = col[k].y;
+        o[2] = col[k].z;
+        // X_k = (Sx/n, Sy/n) from the exact integer sums, rounded once
+        o[3] = (float)((double)sx[k] / (double)n[k]);
+        o[4] = (float)((double)sy[k] / (double)n[k]);
+    }
+    *K_eff = c->Keff;
     return SCALP_OK;
 }
 

@@ -53,6 +53,7 @@ struct Solve {
     int status_slot = -1;         // its entry in the pinned status array
     bool joined = false;          // the step stream has waited for `ready`
     bool retired = false;
+    int32_t inject_error = 0, inject_timeout = 0;  // host-side fault injection (tests)
 };
 
 int server_fail(int code, const char *fmt, ...)
@@ -436,10 +437,15 @@ int scalp_server_poll(scalp_server *s, uint64_t id, int32_t *done, int32_t *n_la
     if (q == cudaErrorNotReady) return SCALP_OK;
     if (q != cudaSuccess) return server_fail(SCALP_E_CUDA, "request %llu: %s", (unsigned long long)id, cudaGetErrorString(q));
     int32_t nl = 0;
-    int rc = scalp_ctx_finish_labels(v->ctx, &s->status[v->status_slot], &nl);
-    if (rc) return rc;
+    CtxStatus &status = s->status[v->status_slot];
+    if (v->inject_error) status.error = v->inject_error;
+    if (v->inject_timeout) status.timeout = v->inject_timeout;
+    // the request's work is complete either way: a failed request is released
+    // too, so that it neither holds its pool region nor counts against
+    // max_slots
+    const int rc = scalp_ctx_finish_labels(v->ctx, &status, &nl);
     *done = 1;
-    if (n_labels) *n_labels = nl;
+    if (n_labels) *n_labels = rc ? 0 : nl;
     // release: the state leaves the pool.  Its done event covers every step
     // that read it (later argument blocks leave it out), so no stream wait.
     scalp_ctx_release(v->ctx);
@@ -450,6 +456,16 @@ int scalp_server_poll(scalp_server *s, uint64_t id, int32_t *done, int32_t *n_la
     s->active.erase(std::find(s->active.begin(), s->active.end(), v));
     s->by_id.erase(it);
     delete v;
+    return rc;
+}
+
+int scalp_server_inject_status(scalp_server *s, uint64_t id, int32_t error, int32_t timeout)
+{
+    if (!s) return server_fail(SCALP_E_ARG, "server is NULL");
+    auto it = s->by_id.find(id);
+    if (it == s->by_id.end()) return server_fail(SCALP_E_ARG, "unknown or already delivered request");
+    it->second->inject_error = error;
+    it->second->inject_timeout = timeout;
     return SCALP_OK;
 }
 

@@ -75,15 +75,15 @@ __global__ void __launch_bounds__(256)
         const int bx = (int)(seg % segs_per_row) * 32;
         const int x = bx + (threadIdx.x & 31);
         bool valid = x < W;
-        int lab = 0;
+        int label = 0;
         float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
         if (valid) {
-            lab = labels[(long long)y * W + x];
-            valid = lab >= 0 && lab < n_labels;
-            const float3 lab = srgb_to_lab(lin, rgb + y * rgb_stride + 3 * (long long)x);
-            v = make_float4(lab.x, lab.y, lab.z, 0.f);
+            label = labels[(long long)y * W + x];
+            valid = label >= 0 && label < n_labels;
+            const float3 c = srgb_to_lab(lin, rgb + y * rgb_stride + 3 * (long long)x);
+            v = make_float4(c.x, c.y, c.z, 0.f);
         }
-        warp_aggregate_global(valid, valid ? lab : 0, bx, y, x - bx, 0, v, s->sums);
+        warp_aggregate_global(valid, valid ? label : 0, bx, y, x - bx, 0, v, s->sums);
     }
 }
 

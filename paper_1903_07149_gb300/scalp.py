@@ -88,6 +88,7 @@ class scalp_state(ctypes.Structure):
 EXPORTS = (
     "scalp_default_params", "scalp_workspace_bytes", "scalp_init", "scalp_reload",
     "scalp_iterate", "scalp_labels", "scalp_get_info", "scalp_get_state", "scalp_set_state",
+    "scalp_clusters", "scalp_server_inject_status",
     "scalp_debug_paths", "scalp_profile", "scalp_count_samples", "scalp_sync",
     "scalp_last_error", "scalp_destroy", "scalp_label_means_static",
     "scalp_batch_workspace_bytes", "scalp_batch_init", "scalp_batch_reload", "scalp_batch_iterate",
@@ -129,6 +130,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "scalp_labels": (ctypes.c_int, [P, P, I32, I32, ctypes.POINTER(I32)]),
             "scalp_get_info": (ctypes.c_int, [P, ctypes.POINTER(scalp_info)]),
             "scalp_get_state": (ctypes.c_int, [P, ctypes.POINTER(scalp_state)]),
+            "scalp_clusters": (ctypes.c_int, [P, P, ctypes.POINTER(I32)]),
             "scalp_set_state": (ctypes.c_int, [P, ctypes.POINTER(scalp_state)]),
             "scalp_debug_paths": (ctypes.c_int, [P, P, I32, P, I32, P]),
             "scalp_profile": (ctypes.c_int, [P, I32, ctypes.POINTER(ctypes.c_double),
@@ -160,6 +162,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "scalp_server_poll": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.POINTER(I32),
                                                  ctypes.POINTER(I32)]),
             "scalp_server_stats": (ctypes.c_int, [P, ctypes.POINTER(I32), ctypes.POINTER(ctypes.c_size_t)]),
+            "scalp_server_inject_status": (ctypes.c_int, [P, ctypes.c_uint64, I32, I32]),
             "scalp_server_destroy": (None, [P]),
             "scalp_boundary_map": (ctypes.c_int, [P, I32, I32, I32, P, P]),
             "scalp_quality_workspace_bytes": (ctypes.c_size_t, [I32, I32, I32, I32]),
@@ -239,6 +242,15 @@ def scalp_get_state(ctx, state: scalp_state):
 
 def scalp_set_state(ctx, state: scalp_state):
     _check(load().scalp_set_state(ctx, ctypes.byref(state)), ctx)
+
+
+def scalp_clusters(ctx, Keff: int) -> np.ndarray:
+    """(Keff, 5) float32 cluster descriptors (l, a, b, x, y) of Sec. II-A."""
+    out = np.empty((Keff, 5), np.float32)
+    k = ctypes.c_int32()
+    _check(load().scalp_clusters(ctx, out.ctypes.data, ctypes.byref(k)), ctx)
+    assert k.value == Keff
+    return out
 
 
 def scalp_debug_paths(ctx, pairs: np.ndarray, stride_xy: int):
@@ -383,6 +395,10 @@ class Segmenter:
                     endpoint=np.ascontiguousarray(st["endpoint"], np.int32))
         scalp_set_state(self.ctx, scalp_state(*(arrs[k].ctypes.data for k in
                                                 ("labels", "n", "sx", "sy", "color", "endpoint"))))
+
+    def clusters(self):
+        """(Keff, 5) float32: per cluster (l_k, a_k, b_k, x_k, y_k), Sec. II-A."""
+        return scalp_clusters(self.ctx, self.info.Keff)
 
     def debug_paths(self, pairs, stride_xy: int | None = None):
         if stride_xy is None:
@@ -601,10 +617,20 @@ def scalp_server_step(server) -> int:
 
 
 def scalp_server_poll(server, rid: int):
+    """(done, n_labels).  A request that failed raises ScalpError with
+    .done = True (it has been released)."""
     done = ctypes.c_int32()
     nl = ctypes.c_int32()
-    _check(load().scalp_server_poll(server, ctypes.c_uint64(rid), ctypes.byref(done), ctypes.byref(nl)))
+    rc = load().scalp_server_poll(server, ctypes.c_uint64(rid), ctypes.byref(done), ctypes.byref(nl))
+    if rc != SCALP_OK:
+        err = ScalpError(rc, load().scalp_last_error(None).decode(errors="replace"))
+        err.done = bool(done.value)
+        raise err
     return bool(done.value), nl.value
+
+
+def scalp_server_inject_status(server, rid: int, error: int = 0, timeout: int = 0):
+    _check(load().scalp_server_inject_status(server, ctypes.c_uint64(rid), int(error), int(timeout)))
 
 
 def scalp_server_stats(server):
@@ -664,10 +690,19 @@ class Server:
         return scalp_server_step(self.server)
 
     def poll(self, rid: int):
-        done, n = scalp_server_poll(self.server, rid)
+        try:
+            done, n = scalp_server_poll(self.server, rid)
+        except ScalpError as e:
+            if getattr(e, "done", False):
+                self._keep.pop(rid, None)
+            raise
         if done:
             self._keep.pop(rid, None)
         return done, n
+
+    def inject_status(self, rid: int, error: int = 0, timeout: int = 0):
+        """Test hook: request rid completes as if a device-side check failed."""
+        scalp_server_inject_status(self.server, rid, error, timeout)
 
     def stats(self):
         return scalp_server_stats(self.server)

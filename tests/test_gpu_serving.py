@@ -181,3 +181,58 @@ def test_two_servers_two_threads(S):
             s.close()
     for srv, _ in lanes:
         srv.close()
+
+
+def test_serving_failed_request_is_released(S):
+    """A request whose device-side status reports a failure (injected on the
+    host: no GPU fault is made) is delivered as failed, with its pool region
+    and slot released: the server then admits as many requests as before and
+    their results are unaffected."""
+    import torch
+
+    H, W, K = 150, 230, 120
+    rgb, con, _ = synth.small_image(H, W, seed=950)
+    img = (torch.from_numpy(rgb).cuda(), torch.from_numpy(con).cuda(), K)
+    p = S.scalp_default_params()
+    need = S.scalp_workspace_bytes(H, W, K, p)
+    budget = S.scalp_server_reserve_bytes(2) + 2 * need + (1 << 20)
+    stream = torch.cuda.Stream()
+    srv = S.Server(budget, max_slots=2, iters=3, stream=stream)
+    _, free0 = srv.stats()
+
+    def run(inject):
+        ids = [srv.submit(*img)[0] for _ in range(2)]
+        assert srv.submit(*img) is None  # both slots taken
+        for rid, (err, tmo) in zip(ids, inject):
+            if err or tmo:
+                srv.inject_status(rid, err, tmo)
+        out = {}
+        for _ in range(200):
+            srv.step()
+            for rid in ids:
+                if rid in out:
+                    continue
+                try:
+                    done, n = srv.poll(rid)
+                except S.ScalpError as e:
+                    assert e.done
+                    out[rid] = e.code
+                    continue
+                if done:
+                    out[rid] = n
+            if len(out) == 2:
+                break
+        return [out[r] for r in ids]
+
+    res = run([(7, 0), (0, 1)])
+    assert res == [S.SCALP_E_INTERNAL, S.SCALP_E_TIMEOUT]
+    in_flight, free1 = srv.stats()
+    assert in_flight == 0 and free1 == free0
+    res = run([(0, 0), (0, 0)])  # slots and memory are back; results are right
+    with torch.cuda.stream(stream):
+        s = S.Segmenter(*img, stream=stream)
+        s.iterate(3)
+        _, nref = s.labels(enforce=True)
+        s.close()
+    assert res == [nref, nref]
+    srv.close()
