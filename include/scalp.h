@@ -207,8 +207,9 @@ void scalp_destroy(scalp_ctx *ctx);
  * it) inside one caller-owned workspace of scalp_batch_workspace_bytes()
  * bytes; each iteration of Algorithm 1 then runs as one launch per kernel for
  * all images together, and n iterations replay as one CUDA graph (non-NULL
- * stream, params->use_graph).  Results are identical to solving each image
- * alone with the same parameters. */
+ * stream, params->use_graph), or all n iterations run as one persistent
+ * launch (scalp_batch_set_launch).  Results are identical to solving each
+ * image alone with the same parameters. */
 typedef struct scalp_batch scalp_batch;
 
 size_t scalp_batch_workspace_bytes(int32_t count, const int32_t *H, const int32_t *W,
@@ -228,8 +229,60 @@ int scalp_batch_init(scalp_batch **out, int32_t count, const scalp_image *images
  * and uploaded (from pinned staging the batch owns) only when they change. */
 int scalp_batch_reload(scalp_batch *b, const scalp_image *images, const scalp_contour *contours);
 
-/* n iterations for every image (asynchronous). */
+/* n iterations for every image (asynchronous).  In the flat launch mode (the
+ * default) each iteration is one launch per kernel for all images and the n
+ * iterations replay as one CUDA graph; in a persistent mode all n iterations
+ * are one cooperative launch (see scalp_batch_set_launch).  The results are
+ * the same bits in every mode. */
 int scalp_batch_iterate(scalp_batch *b, int32_t n);
+
+/* Launch modes of scalp_batch_iterate (Algorithm 1's iteration loop for every
+ * image of the batch):
+ *   SCALP_BATCH_FLAT: per iteration one launch each for the assignment, the
+ *     update, the projection and the candidate lists of all images;
+ *   SCALP_BATCH_PERSISTENT: one cooperative launch of one CTA per resident
+ *     slot (two per SM) for all n iterations; per iteration the CTAs take the
+ *     tiles of all images from a queue in batch order, then update,
+ *     project and rebuild the lists, with grid-wide barriers between the
+ *     phases;
+ *   SCALP_BATCH_PERSISTENT_COST: the same, the queue taking the images by
+ *     descending grid step r (longest paths first; ties in batch order).
+ * Every barrier wait of a persistent launch is bounded (scalp_batch_set_wait;
+ * 2 s by default): a CTA that waits longer abandons the launch, every CTA
+ * returns, and the next call that reads the status (scalp_batch_labels)
+ * returns SCALP_E_TIMEOUT.  The images' state is then undefined until
+ * scalp_batch_reload, after which the batch works as before.  A persistent
+ * mode needs cooperative launch support and two resident CTAs per SM:
+ * otherwise SCALP_E_STATE (the mode is unchanged).  Synchronises the stream. */
+#define SCALP_BATCH_FLAT 0
+#define SCALP_BATCH_PERSISTENT 1
+#define SCALP_BATCH_PERSISTENT_COST 2
+int scalp_batch_set_launch(scalp_batch *b, int32_t mode);
+/* The current mode and the persistent grid (CTAs; -1 until a persistent mode
+ * was first asked for, 0 if none fits). */
+int scalp_batch_get_launch(const scalp_batch *b, int32_t *mode, int32_t *grid);
+/* Bound on each barrier wait of a persistent launch, 1 ms <= limit_ns <= 60 s.
+ * hold > 0 is a fault-injection hook for tests: every barrier then waits for
+ * `hold` arrivals that never come, so the first one runs out (no GPU fault is
+ * made; the CTAs return).  Applies from the next scalp_batch_iterate. */
+int scalp_batch_set_wait(scalp_batch *b, int64_t limit_ns, int32_t hold);
+/* As scalp_count_samples, summed over the images: the path samples and the
+ * (pixel, cluster) pairs the assignments evaluated since counting was
+ * enabled (enable 1 resets and counts, 0 stops, -1 only reads).  Synchronises. */
+int scalp_batch_count_samples(scalp_batch *b, int32_t enable, int64_t *samples, int64_t *pairs);
+/* Autotuner (not part of the paper): times `iters` iterations of the batch in
+ * each launch mode this device supports (the faster of two runs after a
+ * warm-up, each from a fresh scalp_batch_reload of images/contours), keeps
+ * the fastest and leaves the batch freshly reloaded in it.  *mode receives
+ * the choice, trial_ms[3] (may be NULL) the time of each mode (-1: not run).
+ * With cache_path (a JSON file, may be NULL) the choice is looked up first
+ * under a key of the device's SM count, the storage and the batch's shape
+ * class (images, total tiles to two significant digits, mean grid step); a
+ * hit (*from_cache = 1) skips the trials; a new choice is written back.
+ * Synchronises the stream. */
+int scalp_batch_autotune(scalp_batch *b, const scalp_image *images, const scalp_contour *contours,
+                         int32_t iters, const char *cache_path, int32_t *mode, float *trial_ms,
+                         int32_t *from_cache);
 
 /* Labels of every image into outs[i] (H_i*W_i int32, host or device memory per
  * out_on_device), connectivity enforced when enforce != 0; n_labels[i] gets

@@ -10,6 +10,7 @@
 #include <cstddef>
 #include <cstring>
 #include <new>
+#include <map>
 #include <string>
 #include <vector>
 
@@ -1057,6 +1058,16 @@ struct scalp_batch {
     // captured iterations: the candidate lists on a second branch
     cudaStream_t it_side = nullptr;
     cudaEvent_t it_fork = nullptr, it_join = nullptr;
+    // persistent launches (scalp_batch_set_launch): the queue orders, the
+    // cooperative grid (-1: not asked yet) and the bounded-wait settings
+    int launch_mode = SCALP_BATCH_FLAT;
+    int persist_grid = -1;
+    PersistSync *d_sync = nullptr;
+    int *d_order = nullptr, *d_order_base = nullptr;
+    std::vector<int> tiles;       // per image
+    std::vector<double> r;        // per image: the grid step
+    long long wait_ns = 2000000000LL;
+    int hold = 0;
 };
 
 namespace {
@@ -1097,7 +1108,8 @@ cudaError_t batch_fan_out(scalp_batch *b, F &&per_image)
 
 // The batch's own head of the workspace, in carve order.
 struct BatchHead {
-    size_t args, tile, clus, fill, nlab, ctr, ccl_img, ccl_base[CCL_KINDS], setup_base, in, out, bytes;
+    size_t args, tile, clus, fill, nlab, ctr, ccl_img, ccl_base[CCL_KINDS], setup_base, in, out, sync, order,
+        order_base, bytes;
 };
 
 BatchHead batch_head(int count)
@@ -1116,6 +1128,9 @@ BatchHead batch_head(int count)
     h.setup_base = carve(cur, prefix);
     h.in = carve(cur, (size_t)count * sizeof(SetupInput));
     h.out = carve(cur, (size_t)count * sizeof(int *));
+    h.sync = carve(cur, sizeof(PersistSync));
+    h.order = carve(cur, (size_t)count * sizeof(int));
+    h.order_base = carve(cur, prefix);
     h.bytes = (cur + ALIGN - 1) & ~(ALIGN - 1);
     return h;
 }
@@ -1259,6 +1274,8 @@ int scalp_batch_init(scalp_batch **out, int32_t count, const scalp_image *images
         m.n_tx = (c->W + 31) / 32;
         m.n_ty = (c->H + 31) / 32;
         b->smem = std::max(b->smem, c->smem);
+        b->tiles.push_back(c->a.n_tx * c->a.n_ty);
+        b->r.push_back(c->r);
     }
     if (too_large) {
         scalp_batch_destroy(b);
@@ -1281,6 +1298,9 @@ int scalp_batch_init(scalp_batch **out, int32_t count, const scalp_image *images
         b->ccl_total[k] = ccl_base[k][count];
     }
     b->cb.count = count;
+    b->d_sync = reinterpret_cast<PersistSync *>(b->ws + h.sync);
+    b->d_order = reinterpret_cast<int *>(b->ws + h.order);
+    b->d_order_base = reinterpret_cast<int *>(b->ws + h.order_base);
     const size_t prefix = (count + 1) * sizeof(int);
     std::vector<std::pair<size_t, std::pair<const void *, size_t>>> copies = {
         {h.args, {args.data(), count * sizeof(SolveArgs)}},
@@ -1357,6 +1377,25 @@ int scalp_batch_iterate(scalp_batch *b, int32_t n)
     if (!b) return batch_fail(SCALP_E_ARG, "batch is NULL");
     if (n < 0) return batch_fail(SCALP_E_ARG, "n must be >= 0");
     if (n == 0) return SCALP_OK;
+    if (b->launch_mode != SCALP_BATCH_FLAT) {
+        // all n iterations in one cooperative launch; its barrier words start at zero
+        PersistArgs q{};
+        q.b = b->bargs;
+        q.order = b->d_order;
+        q.order_base = b->d_order_base;
+        q.sync = b->d_sync;
+        q.total_tiles = b->total_tiles;
+        q.total_clusters = b->total_clusters;
+        q.total_fill = b->total_fill;
+        q.iters = n;
+        q.wait_ns = b->wait_ns;
+        q.hold = b->hold;
+        cudaError_t e = cudaMemsetAsync(b->d_sync, 0, sizeof(PersistSync), b->st);
+        if (e == cudaSuccess) e = launch_batch_persistent(q, b->storage, b->smem, b->persist_grid, b->st);
+        if (e != cudaSuccess) return batch_fail(SCALP_E_CUDA, "persistent batch launch: %s", cudaGetErrorString(e));
+        for (scalp_ctx *c : b->ctx) c->iterations += n;
+        return SCALP_OK;
+    }
     bool capturing = false;
     auto enqueue = [&](int iters) {
         for (int i = 0; i < iters; ++i) {
@@ -1482,6 +1521,229 @@ int scalp_batch_get_info(const scalp_batch *b, int32_t index, scalp_info *info)
 {
     if (!b || index < 0 || index >= b->count) return batch_fail(SCALP_E_ARG, "bad batch or index");
     return scalp_get_info(b->ctx[index], info);
+}
+
+int scalp_batch_set_launch(scalp_batch *b, int32_t mode)
+{
+    if (!b) return batch_fail(SCALP_E_ARG, "batch is NULL");
+    if (mode != SCALP_BATCH_FLAT && mode != SCALP_BATCH_PERSISTENT && mode != SCALP_BATCH_PERSISTENT_COST)
+        return batch_fail(SCALP_E_ARG, "unknown launch mode %d", mode);
+    if (mode == SCALP_BATCH_FLAT) {
+        b->launch_mode = mode;
+        return SCALP_OK;
+    }
+    if (b->persist_grid < 0) {
+        int grid = 0;
+        const cudaError_t e = batch_persistent_grid(b->storage, b->smem, &grid);
+        if (e != cudaSuccess) return batch_fail(SCALP_E_CUDA, "persistent launch set-up: %s", cudaGetErrorString(e));
+        b->persist_grid = grid;
+    }
+    if (b->persist_grid <= 0)
+        return batch_fail(SCALP_E_STATE, "no cooperative persistent launch fits this device");
+    // the queue's image order: batch order, or by descending grid step r
+    // (the images whose tiles walk the longest paths first; ties in batch order)
+    std::vector<int> order(b->count), base(b->count + 1, 0);
+    for (int i = 0; i < b->count; ++i) order[i] = i;
+    if (mode == SCALP_BATCH_PERSISTENT_COST)
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return b->r[x] > b->r[y]; });
+    for (int j = 0; j < b->count; ++j) base[j + 1] = base[j] + b->tiles[order[j]];
+    cudaError_t e = cudaMemcpyAsync(b->d_order, order.data(), b->count * sizeof(int), cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_order_base, base.data(), (b->count + 1) * sizeof(int), cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);  // the host vectors go out of scope
+    if (e != cudaSuccess) return batch_fail(SCALP_E_CUDA, "queue order: %s", cudaGetErrorString(e));
+    b->launch_mode = mode;
+    return SCALP_OK;
+}
+
+int scalp_batch_get_launch(const scalp_batch *b, int32_t *mode, int32_t *grid)
+{
+    if (!b) return batch_fail(SCALP_E_ARG, "batch is NULL");
+    if (mode) *mode = b->launch_mode;
+    if (grid) *grid = b->persist_grid;
+    return SCALP_OK;
+}
+
+int scalp_batch_set_wait(scalp_batch *b, int64_t limit_ns, int32_t hold)
+{
+    if (!b) return batch_fail(SCALP_E_ARG, "batch is NULL");
+    if (limit_ns < 1000000LL || limit_ns > 60000000000LL || hold < 0 || hold > 1024)
+        return batch_fail(SCALP_E_ARG, "need 1 ms <= limit_ns <= 60 s and 0 <= hold <= 1024");
+    b->wait_ns = limit_ns;
+    b->hold = hold;
+    return SCALP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+// The autotuner's key: the device (SM count), the storage and the batch's
+// shape class (images, total tiles to two significant digits, mean grid step).
+std::string autotune_key(const scalp_batch *b)
+{
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    double rsum = 0.0;
+    for (double r : b->r) rsum += r;
+    long long t = b->total_tiles, scale = 1;
+    while (t >= 100) {
+        t = (t + 5) / 10;
+        scale *= 10;
+    }
+    char key[160];
+    snprintf(key, sizeof key, "scalp-batch/sm%d/%s/n%d/tiles%lld/r%d", sms, b->storage ? "f16" : "f32", b->count,
+             t * scale, (int)std::lround(rsum / b->count));
+    return key;
+}
+
+// The cache: a JSON object, one entry per line, "key": {"mode": M, "ms": [...]}.
+std::map<std::string, std::string> read_cache(const char *path)
+{
+    std::map<std::string, std::string> out;
+    FILE *f = path ? fopen(path, "r") : nullptr;
+    if (!f) return out;
+    char line[1024];
+    while (fgets(line, sizeof line, f)) {
+        const char *q0 = strchr(line, '"');
+        const char *q1 = q0 ? strchr(q0 + 1, '"') : nullptr;
+        const char *brace = q1 ? strchr(q1, '{') : nullptr;
+        const char *end = brace ? strrchr(brace, '}') : nullptr;
+        if (!end) continue;
+        out[std::string(q0 + 1, q1)] = std::string(brace, end + 1);
+    }
+    fclose(f);
+    return out;
+}
+
+int cached_mode(const std::map<std::string, std::string> &cache, const std::string &key)
+{
+    const auto it = cache.find(key);
+    int mode = -1;
+    if (it != cache.end() && sscanf(it->second.c_str(), "{\"mode\": %d", &mode) != 1) mode = -1;
+    return mode;
+}
+
+bool write_cache(const char *path, const std::map<std::string, std::string> &cache)
+{
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "w");
+    if (!f) return false;
+    fprintf(f, "{\n");
+    size_t i = 0;
+    for (const auto &kv : cache)
+        fprintf(f, "  \"%s\": %s%s\n", kv.first.c_str(), kv.second.c_str(), ++i < cache.size() ? "," : "");
+    fprintf(f, "}\n");
+    const bool ok = fclose(f) == 0;
+    return ok && rename(tmp.c_str(), path) == 0;
+}
+
+}  // namespace
+
+extern "C" {
+
+int scalp_batch_autotune(scalp_batch *b, const scalp_image *images, const scalp_contour *contours, int32_t iters,
+                         const char *cache_path, int32_t *mode, float *trial_ms, int32_t *from_cache)
+{
+    if (!b || !images || iters < 1) return batch_fail(SCALP_E_ARG, "need a batch, its images and iters >= 1");
+    const std::string key = autotune_key(b);
+    std::map<std::string, std::string> cache = read_cache(cache_path);
+    if (trial_ms)
+        for (int m = 0; m < 3; ++m) trial_ms[m] = -1.f;
+    if (from_cache) *from_cache = 0;
+    int best = cached_mode(cache, key);
+    if (best >= SCALP_BATCH_FLAT && best <= SCALP_BATCH_PERSISTENT_COST) {
+        int rc = scalp_batch_set_launch(b, best);
+        if (rc == SCALP_OK) {
+            if (from_cache) *from_cache = 1;
+            if (mode) *mode = best;
+            return scalp_batch_reload(b, images, contours);
+        }
+    }
+    // trials: each mode once to warm up (graph capture, module load), then
+    // the faster of two timed runs of `iters` iterations from a fresh reload
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+        if (e0) cudaEventDestroy(e0);
+        return batch_fail(SCALP_E_CUDA, "autotune events");
+    }
+    float ms[3] = {-1.f, -1.f, -1.f};
+    int rc = SCALP_OK;
+    for (int m = SCALP_BATCH_FLAT; m <= SCALP_BATCH_PERSISTENT_COST && rc == SCALP_OK; ++m) {
+        if (scalp_batch_set_launch(b, m) != SCALP_OK) continue;  // not available here
+        for (int rep = 0; rep < 3 && rc == SCALP_OK; ++rep) {
+            rc = scalp_batch_reload(b, images, contours);
+            if (rc == SCALP_OK && rep > 0 && cudaEventRecord(e0, b->st) != cudaSuccess) rc = SCALP_E_CUDA;
+            if (rc == SCALP_OK) rc = scalp_batch_iterate(b, iters);
+            if (rc == SCALP_OK && rep > 0) {
+                float t = 0.f;
+                if (cudaEventRecord(e1, b->st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+                    cudaEventElapsedTime(&t, e0, e1) != cudaSuccess)
+                    rc = batch_fail(SCALP_E_CUDA, "autotune timing");
+                else if (ms[m] < 0.f || t < ms[m])
+                    ms[m] = t;
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc != SCALP_OK) return rc;
+    best = SCALP_BATCH_FLAT;
+    for (int m = 0; m < 3; ++m)
+        if (ms[m] >= 0.f && ms[m] < ms[best]) best = m;
+    if (trial_ms)
+        for (int m = 0; m < 3; ++m) trial_ms[m] = ms[m];
+    rc = scalp_batch_set_launch(b, best);
+    if (rc == SCALP_OK) rc = scalp_batch_reload(b, images, contours);
+    if (rc != SCALP_OK) return rc;
+    if (mode) *mode = best;
+    if (cache_path) {
+        char entry[256];
+        snprintf(entry, sizeof entry, "{\"mode\": %d, \"iters\": %d, \"ms\": [%.4f, %.4f, %.4f]}", best, iters,
+                 ms[0], ms[1], ms[2]);
+        cache[key] = entry;
+        if (!write_cache(cache_path, cache)) return batch_fail(SCALP_E_ARG, "cannot write the cache %s", cache_path);
+    }
+    return SCALP_OK;
+}
+
+int scalp_batch_count_samples(scalp_batch *b, int32_t enable, int64_t *samples, int64_t *pairs)
+{
+    if (!b) return batch_fail(SCALP_E_ARG, "batch is NULL");
+    std::vector<DevCounters> h(b->count);
+    cudaError_t e = cudaSuccess;
+    for (int i = 0; i < b->count && e == cudaSuccess; ++i)
+        e = cudaMemcpyAsync(&h[i], b->ctx[i]->a.ctr, sizeof(DevCounters), cudaMemcpyDeviceToHost, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return batch_fail(SCALP_E_CUDA, "read counters: %s", cudaGetErrorString(e));
+    long long ns = 0, np = 0;
+    for (const DevCounters &c : h) {
+        ns += (long long)c.samples;
+        np += (long long)c.pairs;
+    }
+    if (samples) *samples = ns;
+    if (pairs) *pairs = np;
+    if (enable < 0) return SCALP_OK;
+    const int on = enable != 0;
+    std::vector<SolveArgs> args(b->count);
+    for (int i = 0; i < b->count && e == cudaSuccess; ++i) {
+        scalp_ctx *c = b->ctx[i];
+        c->a.count_samples = on;
+        args[i] = c->a;
+        if (on) e = cudaMemsetAsync(&c->a.ctr->samples, 0, 4 * sizeof(unsigned long long), b->st);
+    }
+    // the argument blocks the kernels read, then the replayed graph, change
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(const_cast<SolveArgs *>(b->bargs.args), args.data(), b->count * sizeof(SolveArgs),
+                            cudaMemcpyHostToDevice, b->st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return batch_fail(SCALP_E_CUDA, "count samples: %s", cudaGetErrorString(e));
+    if (b->graph_valid) {
+        cudaGraphExecDestroy(b->gexec);
+        b->graph_valid = false;
+    }
+    return SCALP_OK;
 }
 
 }  // extern "C"

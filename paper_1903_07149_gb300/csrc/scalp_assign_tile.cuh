@@ -1,0 +1,495 @@
+// scalp_assign_tile.cuh -- the assignment of one 32 x 32 tile (Algorithm 1's
+// inner loops restated per tile, with the fused partial sums of the update):
+// the body shared by the per-iteration assignment kernels (scalp_assign.cu)
+// and the persistent batched kernel (scalp_persistent.cu).
+#pragma once
+
+#include <cfloat>
+#include <climits>
+
+#include "scalp_internal.cuh"
+
+namespace scalp {
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// One FP32 pair of a distance map, by 32-bit shared-memory byte address.
+__device__ __forceinline__ float2 lds_pair(uint32_t addr)
+{
+    float2 v;
+    asm volatile("ld.shared.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "r"(addr));
+    return v;
+}
+
+// Path sums of Eq. 1 and Eq. 2 over a distance map (row pitch `bw` pairs,
+// pair (0,0) = image pixel (bx0, by0)).  The same samples, in the same order
+// and with the same FP32 additions, as path_sums over the plane.
+__device__ __forceinline__ int path_sums_map(uint32_t map, int bw, int bx0, int by0,
+                                             const PathSetup &s, float &sum_dc, float &sum_w)
+{
+    int smaj, smin;
+    path_strides(s, bw, smaj, smin);
+    const uint32_t q0 = map + (uint32_t)(((s.ay - by0) * bw + (s.ax - bx0)) * 8);
+    float dc = 0.f, w = 0.f;
+    const auto visit = [&](uint32_t q) {
+        const float2 v = lds_pair(q);
+        dc += v.x;
+        w += v.y;
+    };
+    // the fixed-point form of the steps (fewer instructions per sample)
+    // covers every path of up to FIXED_STEP_MAX_NS steps
+    const int len = s.ns <= FIXED_STEP_MAX_NS
+                        ? walk_with<FixedPointStep>(q0, smaj * 8, smin * 8, s, visit)
+                        : walk_with<ErrorTermStep>(q0, smaj * 8, smin * 8, s, visit);
+    sum_dc = dc;
+    sum_w = w;
+    return len;
+}
+
+// Shared-memory layout; every section starts on a 16-byte boundary (int4
+// loads and 8-byte atomics need it); the distance maps fill the rest.
+constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+constexpr int STRIP = 4;  // items run along strips STRIP pixels wide
+constexpr int MAX_ITEMS = MAX_TILE_CANDIDATES * (TILE_PIXELS / 32);
+constexpr int STRIP_RCP_BITS = 20;
+// the strip index j / (STRIP * len) by a STRIP_RCP_BITS-bit reciprocal is exact
+// when the rounding error j / 2^STRIP_RCP_BITS stays below 1 / (STRIP * len)
+static_assert((long long)TILE_PIXELS * STRIP * (TILE_X > TILE_Y ? TILE_X : TILE_Y) <
+                  (1LL << STRIP_RCP_BITS),
+              "exact strip index");
+// Per candidate (rank c): three 16-byte records the walk reads,
+//   rec0 = (xa, ya, w | h << 8 | vert << 16, strip reciprocal)  its rectangle
+//   rec1 = (ex, ey, xk bits, yk bits)                           endpoint, X_k
+//   rec2 = (bx0, by0, pitch, map byte offset, or -1: walk the plane)
+// the map box for the build, box = (bx0, by0, pitch, 32-bit reciprocal of
+// the pitch), and the colour C_k, col = (l_k, a_k, b_k, 0).
+struct AssignSmem {
+    static constexpr size_t rec0 = 0;
+    static constexpr size_t rec1 = align16(rec0 + MAX_TILE_CANDIDATES * sizeof(int4));
+    static constexpr size_t rec2 = align16(rec1 + MAX_TILE_CANDIDATES * sizeof(int4));
+    static constexpr size_t box = align16(rec2 + MAX_TILE_CANDIDATES * sizeof(int4));
+    static constexpr size_t col = align16(box + MAX_TILE_CANDIDATES * sizeof(int4));
+    static constexpr size_t cid = align16(col + MAX_TILE_CANDIDATES * sizeof(float4));
+    static constexpr size_t nit = align16(cid + MAX_TILE_CANDIDATES * sizeof(int));
+    static constexpr size_t area = align16(nit + MAX_TILE_CANDIDATES * sizeof(int));
+    static constexpr size_t best = align16(area + MAX_TILE_CANDIDATES * sizeof(int));
+    static constexpr size_t first = align16(best + TILE_PIXELS * sizeof(unsigned long long));
+    static constexpr size_t mfirst = align16(first + (MAX_TILE_CANDIDATES + 1) * sizeof(int));
+    static constexpr size_t cfirst = align16(mfirst + (MAX_TILE_CANDIDATES + 1) * sizeof(int));
+    static constexpr size_t owner = align16(cfirst + (MAX_TILE_CANDIDATES + 1) * sizeof(int));
+    static constexpr size_t misc = align16(owner + MAX_ITEMS);
+    static constexpr size_t maps = align16(misc + 64);
+};
+static_assert(AssignSmem::rec1 % 16 == 0 && AssignSmem::rec2 % 16 == 0 && AssignSmem::col % 16 == 0 &&
+                  AssignSmem::cid % 16 == 0 && AssignSmem::nit % 16 == 0 && AssignSmem::box % 16 == 0 &&
+                  AssignSmem::area % 16 == 0 && AssignSmem::best % 16 == 0 &&
+                  AssignSmem::first % 16 == 0 && AssignSmem::mfirst % 16 == 0 &&
+                  AssignSmem::cfirst % 16 == 0 &&
+                  AssignSmem::owner % 16 == 0 && AssignSmem::misc % 16 == 0 &&
+                  AssignSmem::maps % 16 == 0,
+              "shared-memory sections aligned");
+static_assert(MAX_TILE_CANDIDATES <= 256, "item owners are bytes");
+static_assert(MAX_TILE_CANDIDATES % 32 == 0, "the scans give each lane whole candidates");
+
+__device__ __forceinline__ unsigned long long pack_best(float D, int slot)
+{
+    // D >= 0, so its IEEE bits order like the value; ties fall to the slot
+    return ((unsigned long long)__float_as_uint(D) << 32) | (unsigned)slot;
+}
+
+// Exclusive prefix of cnt <= MAX_TILE_CANDIDATES counts in(c) by one warp:
+// out[c] for c < cnt and the total in out[cnt].  Returns the largest prefix
+// end that stays <= cap (the leading candidates that fit a buffer of cap).
+template <typename In>
+__device__ __forceinline__ int warp_scan_counts(In in, int *out, int cnt, int cap, int lane)
+{
+    constexpr int PER = MAX_TILE_CANDIDATES / 32;
+    int v[PER], sum = 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int c = lane * PER + i;
+        v[i] = c < cnt ? in(c) : 0;
+        sum += v[i];
+    }
+    int incl = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    int run = incl - sum, fit = 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int c = lane * PER + i;
+        if (c < cnt) out[c] = run;
+        run += v[i];
+        if (c < cnt && run <= cap) fit = run;
+    }
+    if (lane == 31) out[cnt] = incl;
+    return (int)__reduce_max_sync(0xffffffffu, (unsigned)fit);
+}
+
+// The map layout by one warp: mfirst = exclusive prefix of the box areas
+// (cnt + 1 entries); the leading candidates whose boxes end within cap get a
+// map, of CHUNK-entry chunks whose prefix goes to cfirst (cnt + 1 entries;
+// none for the others).  Returns the map entries used.
+template <int CHUNK>
+__device__ __forceinline__ int warp_scan_maps(const int *area, int *mfirst, int *cfirst, int cnt, int cap,
+                                              int lane)
+{
+    constexpr int PER = MAX_TILE_CANDIDATES / 32;
+    int v[PER], ch[PER], sum = 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int c = lane * PER + i;
+        v[i] = c < cnt ? area[c] : 0;
+        sum += v[i];
+    }
+    int incl = sum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    // a box fits when its prefix end is within cap (the ends only grow)
+    int run = incl - sum, fit = 0, csum = 0;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int c = lane * PER + i;
+        if (c < cnt) mfirst[c] = run;
+        run += v[i];
+        const bool mapped = c < cnt && v[i] > 0 && run <= cap;
+        if (c < cnt && run <= cap) fit = run;
+        ch[i] = mapped ? (v[i] + CHUNK - 1) / CHUNK : 0;
+        csum += ch[i];
+    }
+    if (lane == 31) mfirst[cnt] = incl;
+    int cincl = csum;
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, cincl, o);
+        if (lane >= o) cincl += t;
+    }
+    int crun = cincl - csum;
+#pragma unroll
+    for (int i = 0; i < PER; ++i) {
+        const int c = lane * PER + i;
+        if (c < cnt) cfirst[c] = crun;
+        crun += ch[i];
+    }
+    if (lane == 31) cfirst[cnt] = cincl;
+    return (int)__reduce_max_sync(0xffffffffu, (unsigned)fit);
+}
+
+// Items: the pixels of a candidate's window that lie in the tile form a
+// rectangle.  When the rectangle lies mostly left or right of the path
+// endpoint (paths mostly along x, |P| set by the column) it is cut into
+// vertical strips STRIP columns wide, otherwise into horizontal strips STRIP
+// rows high.  The strips are read one after the other, each across its width
+// first, and every 32 consecutive pixels of that order form one warp's item.
+// So a warp's pixels lie in a few neighbouring columns (rows), where the path
+// lengths differ little, and only the last item of a rectangle has idle lanes.
+// One tile of one image (the body shared by the single-image and the batched
+// kernels).
+template <typename T>
+__device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsigned char *smem)
+{
+    constexpr int THREADS = ASSIGN_THREADS;
+    constexpr int PIX_PER_THREAD = TILE_PIXELS / THREADS;
+    constexpr int WARPS = THREADS / 32;
+    constexpr int BUILD_UNROLL = 4;
+    constexpr int BUILD_CHUNK = BUILD_UNROLL * 32;  // map entries per warp task
+    const T *__restrict__ plane = reinterpret_cast<const T *>(
+        sizeof(T) == 16 ? (const void *)a.plane32 : (const void *)a.plane16);
+    const int tx = tile % a.n_tx, ty = tile / a.n_tx;
+    const int x0 = tx * TILE_X, y0 = ty * TILE_Y;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+
+    int4 *rec0 = reinterpret_cast<int4 *>(smem + AssignSmem::rec0);
+    int4 *rec1 = reinterpret_cast<int4 *>(smem + AssignSmem::rec1);
+    int4 *rec2 = reinterpret_cast<int4 *>(smem + AssignSmem::rec2);
+    int4 *box = reinterpret_cast<int4 *>(smem + AssignSmem::box);
+    float4 *col = reinterpret_cast<float4 *>(smem + AssignSmem::col);
+    int *cid = reinterpret_cast<int *>(smem + AssignSmem::cid);
+    int *nit = reinterpret_cast<int *>(smem + AssignSmem::nit);
+    int *area = reinterpret_cast<int *>(smem + AssignSmem::area);
+    unsigned long long *best = reinterpret_cast<unsigned long long *>(smem + AssignSmem::best);
+    int *first = reinterpret_cast<int *>(smem + AssignSmem::first);
+    int *mfirst = reinterpret_cast<int *>(smem + AssignSmem::mfirst);
+    int *cfirst = reinterpret_cast<int *>(smem + AssignSmem::cfirst);
+    unsigned char *owner = smem + AssignSmem::owner;
+    int *misc = reinterpret_cast<int *>(smem + AssignSmem::misc);
+    float2 *maps = reinterpret_cast<float2 *>(smem + AssignSmem::maps);
+    const uint32_t maps_u32 = smem_u32(maps);
+
+    const int off = a.tile_off[tile];
+    // the list capacity is a proven bound; the clamp only guards memory if the
+    // device-side overflow check (reported as an error) ever fired
+    const int cnt = (int)max(0LL, min((long long)a.tile_off[tile + 1], a.tile_cap) - off);
+    const bool fast = cnt <= MAX_TILE_CANDIDATES;
+    if (tid == 0) {  // this tile's list is read: ready the counts for the next update
+        a.tile_count[tile] = 0;
+        a.tile_cursor[tile] = 0;
+        // the last projection (and lists) completed before this launch: its
+        // queue starts again for the next update
+        if (tile == 0) a.ctr->nproj = 0;
+    }
+
+    // candidates sorted by cluster index (ranks of distinct ids); the id
+    // staging reuses the `best` words before they are initialised
+    int *ids = reinterpret_cast<int *>(best);
+    int myid = INT_MAX;
+    ClusterDev cd;  // this thread's candidate: its load overlaps the barrier
+    if (fast && tid < cnt) {
+        myid = a.tile_list[off + tid];
+        ids[tid] = myid;
+        cd = a.cdev[myid];
+    }
+    if (tid == 0) misc[1] = 0;  // work counter
+    __syncthreads();
+    if (fast && tid < cnt) {
+        int rank = 0;
+        for (int j = 0; j < cnt; ++j) rank += ids[j] < myid;
+        cid[rank] = myid;
+        // window x tile (clipped to the image), cut into strips
+        const int xa = max(cd.xlo, x0), xb = min(min(cd.xhi, x0 + TILE_X - 1), a.W - 1);
+        const int ya = max(cd.ylo, y0), yb = min(min(cd.yhi, y0 + TILE_Y - 1), a.H - 1);
+        const int w = max(xb - xa + 1, 0), h = max(yb - ya + 1, 0);
+        const bool vert = abs(xa + xb - 2 * cd.ex) >= abs(ya + yb - 2 * cd.ey);
+        const int slen = max(vert ? h : w, 1);  // pixels along one strip
+        rec0[rank] = make_int4(xa, ya, w | (h << 8) | ((int)vert << 16),
+                               ((1 << STRIP_RCP_BITS) + STRIP * slen - 1) / (STRIP * slen));
+        rec1[rank] = make_int4(cd.ex, cd.ey, __float_as_int(cd.xk), __float_as_int(cd.yk));
+        col[rank] = make_float4(cd.L, cd.a, cd.b, 0.f);
+        nit[rank] = (w * h + 31) >> 5;
+        // map box: the rectangle and the endpoint (both inside the image).
+        // Rows are padded to a pitch = 4 (mod 8) pairs: the walks of a warp
+        // then spread over the shared-memory banks (neighbouring rows start
+        // 8 banks apart); 32-bit reciprocal of the pitch for the build.
+        int bx0 = 0, by0 = 0, pitch = 1;
+        long long n = 0;
+        if (w > 0 && h > 0) {
+            bx0 = min(xa, cd.ex);
+            by0 = min(ya, cd.ey);
+            const int bw = max(xb, cd.ex) - bx0 + 1;
+            pitch = bw + ((4 - bw) & 7);
+            n = (long long)pitch * (max(yb, cd.ey) - by0 + 1);
+        }
+        // ceil(2^32 / pitch) = floor((2^32 - 1) / pitch) + 1 for pitch >= 2
+        // (an empty box has pitch 1 and no map)
+        const unsigned rcp = pitch > 1 ? 0xffffffffu / (unsigned)pitch + 1u : 0u;
+        box[rank] = make_int4(bx0, by0, pitch, (int)rcp);
+        // a box larger than the whole buffer never fits: clamp it so that the
+        // prefix sums stay small
+        area[rank] = a.map_cap > 0 ? (int)min(n, (long long)a.map_cap + 1) : 0;
+    }
+    __syncthreads();
+    for (int i = tid; i < TILE_PIXELS; i += THREADS) best[i] = ~0ull;
+    if (warp == 0 && fast) warp_scan_counts([&](int c) { return nit[c]; }, first, cnt, INT_MAX, lane);
+    if (warp == 1 && fast) {
+        const int used = warp_scan_maps<BUILD_CHUNK>(area, mfirst, cfirst, cnt, a.map_cap, lane);
+        if (lane == 0) misc[2] = used;
+    }
+    __syncthreads();
+
+    // the distance maps of the candidates whose boxes fit: entries [0, used)
+    // hold the leading candidates' boxes back to back, row-major; the
+    // padding columns of a row are left unwritten (no walk reads them)
+    const int used = fast ? misc[2] : 0;
+    if (fast) {
+        if (tid < cnt) {
+            const int f = first[tid], n = nit[tid];
+            for (int j = 0; j < n; ++j) owner[f + j] = (unsigned char)tid;
+            const int4 b = box[tid];
+            const bool mapped = area[tid] > 0 && mfirst[tid + 1] <= used;
+            rec2[tid] = make_int4(b.x, b.y, b.z, mapped ? mfirst[tid] * (int)sizeof(float2) : -1);
+        }
+        // warps take the chunks in turn; within one the candidate is uniform
+        // and the lanes read consecutive entries (coalesced plane rows)
+        const int n_chunks = cfirst[cnt];
+        int c = 0;
+        for (int g = warp; g < n_chunks; g += WARPS) {
+            while (g >= cfirst[c + 1]) ++c;
+            const int4 b = box[c];
+            // unpadded width: from the rectangle's right edge and e_k
+            const int4 r0 = rec0[c];
+            const int bw = max(r0.x + (r0.z & 0xff) - 1, rec1[c].x) - b.x + 1;
+            const float4 ck = col[c];
+            const int m0 = mfirst[c];
+            const int n_le = mfirst[c + 1] - m0;
+            const int le0 = (g - cfirst[c]) * BUILD_CHUNK + lane;
+            // the box's first pixel; offsets within the box fit 32 bits: a
+            // box of at most map_cap pairs has row < min(H, map_cap / 4) and
+            // the plane pitch is at most W + 3, so row * pitch + column < 2^31
+            const T *__restrict__ pbox = plane + (long long)b.y * a.pitch + b.x;
+            float2 *mrow = maps + (m0 + le0);
+            T v[BUILD_UNROLL];  // raw samples: all loads issue before any use
+            bool ok[BUILD_UNROLL];
+#pragma unroll
+            for (int u = 0; u < BUILD_UNROLL; ++u) {
+                const int le = le0 + u * 32;
+                // a mapped box has pitch >= 4 and le * pitch < 2^32, so the
+                // 32-bit reciprocal gives the exact row
+                const int row = (int)__umulhi((unsigned)le, (unsigned)b.w);
+                const int cx = le - row * b.z;
+                ok[u] = le < n_le && cx < bw;
+                if (ok[u]) v[u] = __ldg(pbox + (row * a.pitch + cx));
+            }
+#pragma unroll
+            for (int u = 0; u < BUILD_UNROLL; ++u) {
+                if (ok[u]) {
+                    const float4 q = sample_value(v[u]);
+                    mrow[u * 32] = make_float2(colour_dist(q, ck.x, ck.y, ck.z), q.w);
+                }
+            }
+        }
+    }
+    __syncthreads();
+
+    unsigned my_samples = 0, my_pairs = 0;  // per thread: far below 2^32
+    int bestk[PIX_PER_THREAD];  // per-pixel path only
+#pragma unroll
+    for (int j = 0; j < PIX_PER_THREAD; ++j) bestk[j] = INT_MAX;
+
+    // this thread's pixels: block (warp + j*WARPS) of the tile, lane within it
+    auto my_pixel = [&](int j, int &qx, int &qy) {
+        const int blk = warp + j * WARPS;
+        qx = x0 + (blk % (TILE_X / WARP_BLOCK_X)) * WARP_BLOCK_X + (lane % WARP_BLOCK_X);
+        qy = y0 + (blk / (TILE_X / WARP_BLOCK_X)) * WARP_BLOCK_Y + (lane / WARP_BLOCK_X);
+    };
+
+    if (fast) {
+        const int n_items = first[cnt];
+        while (true) {
+            int item = 0;
+            if (lane == 0) item = atomicAdd(&misc[1], 1);
+            item = __shfl_sync(0xffffffffu, item, 0);
+            if (item >= n_items) break;
+            const int c = owner[item];
+            const int4 r0 = rec0[c];
+            const int rw = r0.z & 0xff, rh = (r0.z >> 8) & 0xff;
+            const int j = ((item - first[c]) << 5) + lane;  // pixel of the rectangle
+            if (j >= rw * rh) continue;
+            const bool vert = (r0.z >> 16) != 0;
+            const int slen = vert ? rh : rw, across = vert ? rw : rh;
+            const int strip = (j * r0.w) >> STRIP_RCP_BITS;
+            const int t = j - strip * STRIP * slen;
+            // t / width for a strip 1..4 wide: exact 16-bit reciprocals
+            const int width = min(STRIP, across - strip * STRIP);
+            const int along = (t * (width == 3 ? 21846 : 65536 >> (width >> 1))) >> 16;
+            const int offs = strip * STRIP + (t - along * width);
+            const int qx = r0.x + (vert ? offs : along);
+            const int qy = r0.y + (vert ? along : offs);
+            const int4 r1 = rec1[c];
+            const int4 r2 = rec2[c];
+            const PathSetup s = path_setup(qx, qy, r1.x, r1.y);
+            float sdc, sw, dcp;
+            int len;
+            if (r2.w >= 0) {
+                const uint32_t map = maps_u32 + (uint32_t)r2.w;
+                len = path_sums_map(map, r2.z, r2.x, r2.y, s, sdc, sw);
+                dcp = lds_pair(map + (uint32_t)(((qy - r2.y) * r2.z + (qx - r2.x)) * 8)).x;
+            } else {
+                const float4 ck = col[c];
+                len = path_sums<T>(plane, a.pitch, 0, 0, s, ck.x, ck.y, ck.z, sdc, sw);
+                dcp = colour_dist(fetch_sample<T>(plane + (long long)qy * a.pitch + qx), ck.x, ck.y,
+                                  ck.z);
+            }
+            const float ddx = (float)qx - __int_as_float(r1.z), ddy = (float)qy - __int_as_float(r1.w);
+            const float ds = fmaf(ddx, ddx, ddy * ddy);
+            const float D = scalp_distance(dcp, sdc, sw, len, a.lam, a.gamma, a.ms2, ds);
+            atomicMin(&best[(qy - y0) * TILE_X + (qx - x0)], pack_best(D, c));
+            my_samples += len;
+            my_pairs += 1;
+        }
+    } else {
+        // per-pixel path: every candidate straight from the global list
+#pragma unroll 1
+        for (int j = 0; j < PIX_PER_THREAD; ++j) {
+            int px, py;
+            my_pixel(j, px, py);
+            if (px >= a.W || py >= a.H) continue;
+            const float4 own = fetch_sample<T>(plane + (long long)py * a.pitch + px);
+            float bestD = FLT_MAX;
+            for (int i = 0; i < cnt; ++i) {
+                const int k = a.tile_list[off + i];
+                const ClusterDev cd = a.cdev[k];
+                if (px < cd.xlo || px > cd.xhi || py < cd.ylo || py > cd.yhi) continue;
+                const PathSetup s = path_setup(px, py, cd.ex, cd.ey);
+                float sdc, sw;
+                const int len = path_sums<T>(plane, a.pitch, 0, 0, s, cd.L, cd.a, cd.b, sdc, sw);
+                const float dcp = colour_dist(own, cd.L, cd.a, cd.b);
+                const float ddx = (float)px - cd.xk, ddy = (float)py - cd.yk;
+                const float ds = fmaf(ddx, ddx, ddy * ddy);
+                const float D = scalp_distance(dcp, sdc, sw, len, a.lam, a.gamma, a.ms2, ds);
+                if (D < bestD || (D == bestD && k < bestk[j])) {
+                    bestD = D;
+                    bestk[j] = k;
+                }
+                my_samples += len;
+                my_pairs += 1;
+            }
+        }
+    }
+    __syncthreads();
+
+    // labels and the warp-aggregated integer sums of the update; the
+    // pixels' own samples are all requested first
+    float4 owns[PIX_PER_THREAD];
+#pragma unroll
+    for (int j = 0; j < PIX_PER_THREAD; ++j) {
+        int px, py;
+        my_pixel(j, px, py);
+        owns[j] = px < a.W && py < a.H ? fetch_sample<T>(plane + (long long)py * a.pitch + px)
+                                       : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+#pragma unroll
+    for (int j = 0; j < PIX_PER_THREAD; ++j) {
+        int px, py;
+        my_pixel(j, px, py);
+        const bool valid = px < a.W && py < a.H;
+        const long long p = (long long)py * a.W + px;
+        const float4 own = owns[j];
+        int lab = -1;
+        if (valid) {
+            if (fast) {
+                const unsigned long long b = best[(py - y0) * TILE_X + (px - x0)];
+                if (b != ~0ull) lab = cid[(int)(b & 0xffffffffu)];
+            } else if (bestk[j] != INT_MAX) {
+                lab = bestk[j];
+            }
+            if (lab >= 0) {
+                a.labels[p] = lab;
+            } else {
+                lab = a.labels[p];  // no window reaches p: keep its label
+                atomicAdd(&a.ctr->orphans, 1);
+            }
+        }
+        // fire-and-forget reductions into the global cluster sums, one set
+        // per label group of the warp (offsets within the tile)
+        warp_aggregate_global(valid, lab, x0, y0, px - x0, py - y0, own, a.acc);
+    }
+    if (a.count_samples) {
+        for (int o = 16; o > 0; o >>= 1) {
+            my_samples += __shfl_down_sync(0xffffffffu, my_samples, o);
+            my_pairs += __shfl_down_sync(0xffffffffu, my_pairs, o);
+        }
+        if (lane == 0) {
+            atomicAdd(&a.ctr->samples, (unsigned long long)my_samples);
+            atomicAdd(&a.ctr->pairs, (unsigned long long)my_pairs);
+        }
+        // (candidate, tile) rectangles walked on a map and on the plane
+        if (tid == 0) {
+            unsigned long long on_map = 0, on_plane = 0;
+            for (int c = 0; c < cnt; ++c) {
+                if (fast && nit[c] == 0) continue;
+                if (fast && rec2[c].w >= 0) ++on_map;
+                else ++on_plane;
+            }
+            atomicAdd(&a.ctr->map_rects, on_map);
+            atomicAdd(&a.ctr->plane_rects, on_plane);
+        }
+    }
+}
+
+}  // namespace scalp

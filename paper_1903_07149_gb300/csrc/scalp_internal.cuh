@@ -165,6 +165,29 @@ struct BatchArgs {
     int count;
 };
 
+// Synchronisation words of a persistent batched launch (zeroed before each).
+struct PersistSync {
+    unsigned arrive;  // CTAs arrived at the current barrier
+    unsigned gen;     // barriers completed
+    unsigned queue;   // next tile of the assignment queue
+    unsigned abort;   // a wait gave up: every CTA returns
+};
+
+// A persistent batched launch: n iterations of the batch in one launch.
+struct PersistArgs {
+    BatchArgs b;
+    const int *order;       // count: the images in queue order
+    const int *order_base;  // count+1: prefix of their tile counts, in that order
+    PersistSync *sync;
+    int total_tiles, total_clusters, total_fill, iters;
+    long long wait_ns;      // bound on each barrier wait
+    int hold;               // test hook: extra arrivals a barrier waits for (0)
+};
+
+// Static shared memory a persistent batched CTA may use beside the
+// assignment's dynamic buffer (the map capacity leaves this much free).
+constexpr int PERSIST_STATIC_SMEM = 1024;
+
 // Image of flat index g: the last i with base[i] <= g (base[0] = 0).
 __device__ __forceinline__ int batch_find(const int *base, int count, int g)
 {

@@ -62,6 +62,10 @@ void launch_lists(const SolveArgs &a, cudaStream_t st, bool pdl = false);
 void launch_assign_batch(const BatchArgs &b, int storage, int total_tiles, size_t smem_bytes,
                          cudaStream_t st, bool pdl = false);
 cudaError_t assign_batch_configure(int storage);
+// The persistent batched iterations (scalp_persistent.cu): the cooperative
+// grid that fits (*grid = 0: not available on this device), and the launch.
+cudaError_t batch_persistent_grid(int storage, size_t smem, int *grid);
+cudaError_t launch_batch_persistent(const PersistArgs &q, int storage, size_t smem, int grid, cudaStream_t st);
 void launch_batch_update(const BatchArgs &b, int total_clusters, int total_fill, cudaStream_t st,
                          bool pdl = false, cudaStream_t side = nullptr, cudaEvent_t fork = nullptr,
                          cudaEvent_t join = nullptr, int whole_image = 0);

@@ -24,6 +24,7 @@ SCALP_E_TIMEOUT = -4
 SCALP_E_STATE = -5
 SCALP_E_INTERNAL = -6
 STORAGE = {"f32": 0, "f16": 1}
+BATCH_LAUNCH = {"flat": 0, "persistent": 1, "persistent_cost": 2}
 PRIOR = {"input": 0, "gradient": 1}
 
 
@@ -93,6 +94,8 @@ EXPORTS = (
     "scalp_last_error", "scalp_destroy", "scalp_label_means_static",
     "scalp_batch_workspace_bytes", "scalp_batch_init", "scalp_batch_reload", "scalp_batch_iterate",
     "scalp_batch_labels", "scalp_batch_get_state", "scalp_batch_get_info", "scalp_batch_destroy",
+    "scalp_batch_set_launch", "scalp_batch_get_launch", "scalp_batch_set_wait",
+    "scalp_batch_count_samples", "scalp_batch_autotune",
     "scalp_server_reserve_bytes", "scalp_server_create", "scalp_server_submit", "scalp_server_step",
     "scalp_server_poll", "scalp_server_stats", "scalp_server_destroy", "scalp_boundary_map",
     "scalp_server_set_step_budget",
@@ -151,6 +154,12 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "scalp_batch_get_state": (ctypes.c_int, [P, I32, ctypes.POINTER(scalp_state)]),
             "scalp_batch_get_info": (ctypes.c_int, [P, I32, ctypes.POINTER(scalp_info)]),
             "scalp_batch_destroy": (None, [P]),
+            "scalp_batch_set_launch": (ctypes.c_int, [P, I32]),
+            "scalp_batch_get_launch": (ctypes.c_int, [P, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
+            "scalp_batch_set_wait": (ctypes.c_int, [P, I64, I32]),
+            "scalp_batch_count_samples": (ctypes.c_int, [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+            "scalp_batch_autotune": (ctypes.c_int, [P, P, P, I32, ctypes.c_char_p, ctypes.POINTER(I32),
+                                                    P, ctypes.POINTER(I32)]),
             "scalp_server_reserve_bytes": (ctypes.c_size_t, [I32]),
             "scalp_server_create": (ctypes.c_int, [ctypes.POINTER(P), P, ctypes.c_size_t, I32,
                                                    ctypes.POINTER(scalp_params)]),
@@ -561,6 +570,40 @@ class Batch:
         ptrs = [o.data_ptr() if on_dev else o.ctypes.data for o in outs]
         n = scalp_batch_labels(self.batch, ptrs, on_dev, enforce)
         return outs, n
+
+    def set_launch(self, mode: str):
+        """'flat', 'persistent' or 'persistent_cost' (scalp_batch_set_launch)."""
+        _check(load().scalp_batch_set_launch(self.batch, BATCH_LAUNCH[mode]))
+
+    def get_launch(self):
+        m, g = ctypes.c_int32(), ctypes.c_int32()
+        _check(load().scalp_batch_get_launch(self.batch, ctypes.byref(m), ctypes.byref(g)))
+        return {v: k for k, v in BATCH_LAUNCH.items()}[m.value], g.value
+
+    def set_wait(self, limit_ns: int = 2_000_000_000, hold: int = 0):
+        _check(load().scalp_batch_set_wait(self.batch, int(limit_ns), int(hold)))
+
+    def count_samples(self, enable: int):
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(load().scalp_batch_count_samples(self.batch, int(enable), ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
+
+    def autotune(self, rgbs, contours, iters: int = 10, cache_path=None):
+        """Times each launch mode and keeps the fastest (the batch is left
+        freshly reloaded).  Returns (mode, {mode: ms}, from_cache)."""
+        imgs, cons, keep = self._marshal(rgbs, contours)
+        arr_i = (scalp_image * self.count)(*imgs)
+        arr_c = (scalp_contour * self.count)(*cons)
+        m, hit = ctypes.c_int32(), ctypes.c_int32()
+        ms = (ctypes.c_float * 3)()
+        path = cache_path.encode() if cache_path else None
+        _check(load().scalp_batch_autotune(self.batch, ctypes.cast(arr_i, ctypes.c_void_p),
+                                           ctypes.cast(arr_c, ctypes.c_void_p), int(iters), path,
+                                           ctypes.byref(m), ctypes.cast(ms, ctypes.c_void_p),
+                                           ctypes.byref(hit)))
+        self._keep = keep
+        names = {v: k for k, v in BATCH_LAUNCH.items()}
+        return names[m.value], {names[i]: ms[i] for i in range(3) if ms[i] >= 0}, bool(hit.value)
 
     def get_state(self, index: int):
         info = self.infos[index]

@@ -200,3 +200,127 @@ def test_batch_of_single_tiles(S):
     sizes = [(int(rng.integers(1, 33)), int(rng.integers(1, 33))) for _ in range(20)]
     Ks = [int(rng.integers(1, min(H * W, 12) + 1)) for H, W in sizes]
     _alone_vs_batch(S, sizes, Ks, seed=1300)
+
+
+def _batch_result(b):
+    raw, _ = b.labels(enforce=False)
+    final, n = b.labels(enforce=True)
+    states = [b.get_state(i) for i in range(b.count)]
+    return raw, final, n, states
+
+
+def _assert_same(r1, r2):
+    raw1, fin1, n1, st1 = r1
+    raw2, fin2, n2, st2 = r2
+    assert np.array_equal(n1, n2)
+    for i in range(len(raw1)):
+        assert np.array_equal(raw1[i], raw2[i]), i
+        assert np.array_equal(fin1[i], fin2[i]), i
+        for k in ("n", "sx", "sy", "color", "endpoint"):
+            assert np.array_equal(st1[i][k], st2[i][k]), (i, k)
+
+
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_persistent_launch_equals_flat(S, storage):
+    """All iterations of the batch in one cooperative launch (tiles from a
+    queue, grid-wide barriers between the phases), the queue in batch order
+    and by descending grid step: bit-identical to the per-kernel launches,
+    also after a reload and across two calls of different lengths; the
+    device-counted path samples agree too."""
+    import torch
+
+    rgbs, cons = _inputs()
+    Ks = [k for _, _, k in SIZES]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = S.Batch(rgbs, cons, Ks, storage=storage, stream=stream)
+        b.count_samples(1)
+        b.iterate(4)
+        b.iterate(3)
+        ref_samples = b.count_samples(0)
+        ref = _batch_result(b)
+        for mode in ("persistent", "persistent_cost"):
+            b.set_launch(mode)
+            m, grid = b.get_launch()
+            assert m == mode and grid >= torch.cuda.get_device_properties(0).multi_processor_count
+            b.reload(rgbs, cons)
+            b.count_samples(1)
+            b.iterate(4)
+            b.iterate(3)
+            assert b.count_samples(0) == ref_samples
+            _assert_same(ref, _batch_result(b))
+        b.set_launch("flat")
+        b.reload(rgbs, cons)
+        b.iterate(7)
+        _assert_same(ref, _batch_result(b))
+        b.close()
+
+
+def test_persistent_wait_runs_out_and_batch_recovers(S):
+    """A barrier wait that can never complete (the test hold: one more arrival
+    than there are CTAs, nothing faulted) runs out after its 20 ms limit:
+    every CTA returns, the labels call reports SCALP_E_TIMEOUT, and after a
+    reload the batch gives the right result again."""
+    import time
+
+    import torch
+
+    rgbs, cons = _inputs()
+    Ks = [k for _, _, k in SIZES]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ref_b = S.Batch(rgbs, cons, Ks, stream=stream)
+        ref_b.iterate(3)
+        ref = _batch_result(ref_b)
+        ref_b.close()
+        b = S.Batch(rgbs, cons, Ks, stream=stream)
+        b.set_launch("persistent")
+        b.set_wait(20_000_000, hold=1)
+        t0 = time.perf_counter()
+        b.iterate(3)
+        with pytest.raises(S.ScalpError) as e:
+            b.labels(enforce=True)
+        assert e.value.code == S.SCALP_E_TIMEOUT
+        assert time.perf_counter() - t0 < 30.0
+        b.set_wait()  # default limit, no hold
+        b.reload(rgbs, cons)
+        b.iterate(3)
+        _assert_same(ref, _batch_result(b))
+        b.close()
+
+
+def test_autotune_chooses_and_caches(S, tmp_path):
+    """The autotuner times every launch mode, keeps the fastest, leaves the
+    batch freshly reloaded (its solve then equals the flat one) and writes
+    its choice to the JSON cache, which a second batch of the same shape
+    class then reads without trials."""
+    import json
+
+    import torch
+
+    rgbs, cons = _inputs()
+    Ks = [k for _, _, k in SIZES]
+    cache = str(tmp_path / "autotune.json")
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        ref_b = S.Batch(rgbs, cons, Ks, stream=stream)
+        ref_b.iterate(5)
+        ref = _batch_result(ref_b)
+        ref_b.close()
+        b = S.Batch(rgbs, cons, Ks, stream=stream)
+        mode, ms, hit = b.autotune(rgbs, cons, iters=5, cache_path=cache)
+        assert not hit and set(ms) == {"flat", "persistent", "persistent_cost"}
+        assert ms[mode] == min(ms.values())
+        assert b.get_launch()[0] == mode
+        b.iterate(5)
+        _assert_same(ref, _batch_result(b))
+        b.close()
+        with open(cache) as f:
+            entries = json.load(f)
+        assert len(entries) == 1 and list(entries.values())[0]["mode"] == S.BATCH_LAUNCH[mode]
+        b2 = S.Batch(rgbs, cons, Ks, stream=stream)
+        mode2, ms2, hit2 = b2.autotune(rgbs, cons, iters=5, cache_path=cache)
+        assert hit2 and mode2 == mode and ms2 == {}
+        b2.iterate(5)
+        _assert_same(ref, _batch_result(b2))
+        b2.close()

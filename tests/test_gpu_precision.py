@@ -50,7 +50,10 @@ def precision_stats(g, orc):
     """Agreement and errors of a GPU state g against the oracle solver orc."""
     diff = g["labels"] != orc.labels
     bad = np.unique(np.concatenate([g["labels"][diff], orc.labels[diff]]))
-    same = np.setdiff1d(np.arange(orc.Keff), bad)
+    # clusters holding pixels whose pixel set is the same on both sides (an
+    # empty cluster keeps whatever state its history left it)
+    present = np.unique(orc.labels)
+    same = np.setdiff1d(present, bad)
     cg = np.stack([g["sx"] / g["n"], g["sy"] / g["n"]], axis=1)
     co = orc.centers()
     dcen = np.hypot(*(cg - co).T)
