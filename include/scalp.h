@@ -252,7 +252,8 @@ int scalp_batch_iterate(scalp_batch *b, int32_t n);
  * returns, and the next call that reads the status (scalp_batch_labels)
  * returns SCALP_E_TIMEOUT.  The images' state is then undefined until
  * scalp_batch_reload, after which the batch works as before.  A persistent
- * mode needs cooperative launch support and two resident CTAs per SM:
+ * mode needs cooperative launch support, two resident CTAs per SM and a batch
+ * of at most about 14,000 images:
  * otherwise SCALP_E_STATE (the mode is unchanged).  Synchronises the stream. */
 #define SCALP_BATCH_FLAT 0
 #define SCALP_BATCH_PERSISTENT 1

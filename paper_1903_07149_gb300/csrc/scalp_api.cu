@@ -1540,6 +1540,10 @@ int scalp_batch_set_launch(scalp_batch *b, int32_t mode)
     }
     if (b->persist_grid <= 0)
         return batch_fail(SCALP_E_STATE, "no cooperative persistent launch fits this device");
+    // the projection phase lays out the images' queue lengths and their
+    // prefix in the dynamic shared memory
+    if ((size_t)(2 * b->count + 1) * sizeof(int) > b->smem)
+        return batch_fail(SCALP_E_STATE, "too many images (%d) for the persistent launch's work list", b->count);
     // the queue's image order: batch order, or by descending grid step r
     // (the images whose tiles walk the longest paths first; ties in batch order)
     std::vector<int> order(b->count), base(b->count + 1, 0);

@@ -245,7 +245,11 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
         ids[tid] = myid;
         cd = a.cdev[myid];
     }
-    if (tid == 0) misc[1] = 0;  // work counter
+    if (tid == 0) {
+        misc[1] = 0;  // work counter
+        misc[4] = 0;  // path samples and pairs (counting on)
+        misc[5] = 0;
+    }
     __syncthreads();
     if (fast && tid < cnt) {
         int rank = 0;
@@ -346,7 +350,9 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
     }
     __syncthreads();
 
-    unsigned my_samples = 0, my_pairs = 0;  // per thread: far below 2^32
+    // with counting on, the tile's path samples and pairs are summed in
+    // misc[4], misc[5] (zeroed at the start; far below 2^32 per tile)
+    unsigned *tile_samples = reinterpret_cast<unsigned *>(misc + 4);
     int bestk[PIX_PER_THREAD];  // per-pixel path only
 #pragma unroll
     for (int j = 0; j < PIX_PER_THREAD; ++j) bestk[j] = INT_MAX;
@@ -399,8 +405,10 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
             const float ds = fmaf(ddx, ddx, ddy * ddy);
             const float D = scalp_distance(dcp, sdc, sw, len, a.lam, a.gamma, a.ms2, ds);
             atomicMin(&best[(qy - y0) * TILE_X + (qx - x0)], pack_best(D, c));
-            my_samples += len;
-            my_pairs += 1;
+            if (a.count_samples) {
+                atomicAdd(tile_samples, (unsigned)len);
+                atomicAdd(tile_samples + 1, 1u);
+            }
         }
     } else {
         // per-pixel path: every candidate straight from the global list
@@ -426,8 +434,10 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
                     bestD = D;
                     bestk[j] = k;
                 }
-                my_samples += len;
-                my_pairs += 1;
+                if (a.count_samples) {
+                    atomicAdd(tile_samples, (unsigned)len);
+                    atomicAdd(tile_samples + 1, 1u);
+                }
             }
         }
     }
@@ -470,13 +480,10 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
         warp_aggregate_global(valid, lab, x0, y0, px - x0, py - y0, own, a.acc);
     }
     if (a.count_samples) {
-        for (int o = 16; o > 0; o >>= 1) {
-            my_samples += __shfl_down_sync(0xffffffffu, my_samples, o);
-            my_pairs += __shfl_down_sync(0xffffffffu, my_pairs, o);
-        }
-        if (lane == 0) {
-            atomicAdd(&a.ctr->samples, (unsigned long long)my_samples);
-            atomicAdd(&a.ctr->pairs, (unsigned long long)my_pairs);
+        // (the walks ended before the barrier above the labels)
+        if (tid == 0) {
+            atomicAdd(&a.ctr->samples, (unsigned long long)tile_samples[0]);
+            atomicAdd(&a.ctr->pairs, (unsigned long long)tile_samples[1]);
         }
         // (candidate, tile) rectangles walked on a map and on the plane
         if (tid == 0) {

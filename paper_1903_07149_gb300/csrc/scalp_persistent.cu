@@ -100,25 +100,109 @@ __device__ __noinline__ bool grid_wait(PersistSync *y, unsigned target, long lon
 
 // Phases 2-4 out of line: their registers (128-bit projection arithmetic)
 // stay out of the assignment's allocation.
+//
+// The update of one cluster is a chain of dependent loads and 128-bit window
+// arithmetic: every CTA takes an equal run of consecutive clusters, so that
+// the chains spread over all SMs (a grid-stride loop would leave most CTAs
+// idle: a batch has far fewer clusters than the grid has threads).
 __device__ __noinline__ void phase_update(const BatchArgs &b, int total_clusters)
 {
-    const long long stride = (long long)gridDim.x * blockDim.x;
-    for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < total_clusters; g += stride) {
-        const int i = batch_find(b.clus_base, b.count, (int)g);
-        update_cluster(b.args[i], (int)g - b.clus_base[i], 1);
+    const int chunk = (total_clusters + gridDim.x - 1) / gridDim.x;
+    const int end = min(total_clusters, (int)(blockIdx.x + 1) * chunk);
+    for (int g = blockIdx.x * chunk + threadIdx.x; g < end; g += blockDim.x) {
+        const int i = batch_find(b.clus_base, b.count, g);
+        update_cluster(b.args[i], g - b.clus_base[i], 1);
     }
 }
 
-// Tile-count scans, then the projections: image i's queue entries start at
-// a CTA that moves with i, so the first entries of the images do not all
-// fall on the same CTAs.
-__device__ __noinline__ void phase_project(const BatchArgs &b)
+// Eq. 4 for queued cluster j of one image by one warp, over the window the
+// last assignment used (which holds S_k): the same argmin, with the same
+// exact comparison and tie rule, as the CTA-wide search.
+__device__ __forceinline__ void project_warp(const SolveArgs &a, int j)
 {
-    const int G = gridDim.x;
-    for (int i = blockIdx.x; i < b.count; i += G) scan_tiles_cta<ASSIGN_THREADS>(b.args[i]);
-    for (int i = 0; i < b.count; ++i) {
-        const int j0 = (int)((blockIdx.x + (long long)i * (G - 97 % G)) % G);
-        project_cta(b.args[i], 0, j0, G);
+    constexpr int BATCH = 4;
+    const int lane = threadIdx.x & 31;
+    const int k = a.proj_list[j];
+    const long long n = a.st_n[k], sx = a.st_sx[k], sy = a.st_sy[k];
+    const int4 w4 = a.prev_win[k];
+    const int xlo = w4.x, ylo = w4.z;
+    const int w = w4.y - w4.x + 1;
+    const long long area = (long long)w * (w4.w - w4.z + 1);
+    const RowDiv div(w, area);
+    const double bound = (double)max(a.W, a.H);
+    const bool small = 2.0 * (n * bound) * (n * bound) < 4.0e18;
+    ProjBest b = {~0ull, ~0ull, LLONG_MAX};
+    for (long long base = 0; base < area; base += 32 * BATCH) {
+        int lab[BATCH];
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            const long long i = base + u * 32 + lane;
+            lab[u] = -1;
+            if (i < area) {
+                const long long r = div.row(i);
+                lab[u] = a.labels[(long long)(ylo + (int)r) * a.W + xlo + (int)(i - r * w)];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            if (lab[u] != k) continue;
+            const long long i = base + u * 32 + lane;
+            const long long r = div.row(i);
+            const int y = ylo + (int)r, x = xlo + (int)(i - r * w);
+            const ProjBest c = proj_candidate((long long)y * a.W + x, x, y, n, sx, sy, small);
+            if (proj_less(c, b)) b = c;
+        }
+    }
+    proj_shfl_min(b);
+    if (lane == 0) {
+        if (b.p == LLONG_MAX) {
+            atomicExch(&a.ctr->error, ERR_BAD_LABEL);
+        } else {
+            const int ex = (int)(b.p % a.W), ey = (int)(b.p / a.W);
+            a.st_end[k] = make_int2(ex, ey);
+            a.cdev[k].ex = ex;
+            a.cdev[k].ey = ey;
+        }
+    }
+}
+
+// The whole-image searches (an image whose last assignment left pixels with
+// no candidate), one CTA per queued cluster: out of line, so that their
+// registers stay out of the other phases' allocation.
+__device__ __noinline__ void project_whole_image(const SolveArgs &a, int j)
+{
+    project_cta(a, 0, j, INT_MAX);
+}
+
+// Tile-count scans (one CTA per image), then the projections: every CTA
+// lays out the same list of all queued clusters of all images (a prefix over
+// the images' queue lengths, in the dynamic shared memory the assignment
+// phase has finished with) and its warps take entries in turn, a warp per
+// cluster; the clusters of images that need a whole-image search are taken
+// by whole CTAs afterwards.  Needs 2 * count + 1 ints of shared memory
+// (checked on the host).
+__device__ __noinline__ void phase_project(const BatchArgs &b, unsigned char *smem)
+{
+    __shared__ int s_warp[32];
+    const int G = gridDim.x, count = b.count;
+    for (int i = blockIdx.x; i < count; i += G) scan_tiles_cta<ASSIGN_THREADS>(b.args[i]);
+    int *s_cnt = reinterpret_cast<int *>(smem);  // per image: queue length, 0 for whole-image
+    int *s_pref = s_cnt + count;                 // count + 1: its prefix
+    for (int i = threadIdx.x; i < count; i += blockDim.x)
+        s_cnt[i] = b.args[i].ctr->proj_all ? 0 : b.args[i].ctr->nproj;
+    __syncthreads();
+    cta_scan(s_cnt, s_pref, count, ASSIGN_THREADS, s_warp);
+    const int total = s_pref[count];
+    const int warps = blockDim.x / 32;
+    for (int t = blockIdx.x * warps + (int)(threadIdx.x >> 5); t < total; t += G * warps) {
+        const int i = batch_find(s_pref, count, t);
+        project_warp(b.args[i], t - s_pref[i]);
+    }
+    // whole-image searches: image by image, entry j on CTA (j mod G)
+    for (int i = 0; i < count; ++i) {
+        if (s_cnt[i] != 0 || !b.args[i].ctr->proj_all) continue;
+        const int nproj = b.args[i].ctr->nproj;
+        for (int j = blockIdx.x; j < nproj; j += G) project_whole_image(b.args[i], j);
     }
 }
 
@@ -131,20 +215,23 @@ __device__ __noinline__ void phase_lists(const BatchArgs &b, int total_fill)
     }
 }
 
-// The assignment phase: tiles from the queue until it runs dry.
+// The assignment phase: tiles from the queue until it runs dry.  The next
+// tile's index is fetched while the current tile is labelled, so the queue's
+// round trip is off the critical path.
 template <typename T>
-__device__ __noinline__ void phase_assign(const BatchArgs &b, const int *order, const int *order_base,
-                                          unsigned *queue, int total_tiles, unsigned char *smem)
+__device__ __forceinline__ void phase_assign(const BatchArgs &b, const int *order, const int *order_base,
+                                             unsigned *queue, int total_tiles, unsigned char *smem)
 {
-    __shared__ int s_tile;
-    while (true) {
-        if (threadIdx.x == 0) s_tile = (int)atomicAdd(queue, 1u);
-        __syncthreads();
-        const int g = s_tile;
-        if (g >= total_tiles) break;
+    __shared__ int s_tile[2];
+    if (threadIdx.x == 0) s_tile[0] = (int)atomicAdd(queue, 1u);
+    __syncthreads();
+    int slot = 0;
+    for (int g = s_tile[0]; g < total_tiles; g = s_tile[slot]) {
+        if (threadIdx.x == 0) s_tile[slot ^ 1] = (int)atomicAdd(queue, 1u);
         const int j = batch_find(order_base, b.count, g);
         assign_tile<T>(b.args[order[j]], g - order_base[j], smem);
-        __syncthreads();  // the tile's shared memory and s_tile are reused
+        __syncthreads();  // the tile's shared memory is reused; the next index is visible
+        slot ^= 1;
     }
 }
 
@@ -164,7 +251,7 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, ASSIGN_CTAS_PER_SM) k_batch_pe
         phase_update(q.b, q.total_clusters);
         if (!SCALP_GRID_WAIT()) return;
         // 3. scans and projections
-        phase_project(q.b);
+        phase_project(q.b, smem);
         if (!SCALP_GRID_WAIT()) return;
         // 4. candidate lists
         phase_lists(q.b, q.total_fill);
