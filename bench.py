@@ -177,7 +177,7 @@ def ccl_launches(H: int, W: int) -> int:
 
 def kernel_hash() -> str:
     h = hashlib.sha256()
-    for f in ("scalp_assign.cu", "scalp_internal.cuh"):
+    for f in ("scalp_assign.cu", "scalp_assign_tile.cuh", "scalp_internal.cuh"):
         with open(os.path.join(ROOT, "paper_1903_07149_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]

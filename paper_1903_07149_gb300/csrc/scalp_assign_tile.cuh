@@ -80,7 +80,9 @@ struct AssignSmem {
     static constexpr size_t mfirst = align16(first + (MAX_TILE_CANDIDATES + 1) * sizeof(int));
     static constexpr size_t cfirst = align16(mfirst + (MAX_TILE_CANDIDATES + 1) * sizeof(int));
     static constexpr size_t owner = align16(cfirst + (MAX_TILE_CANDIDATES + 1) * sizeof(int));
-    static constexpr size_t misc = align16(owner + MAX_ITEMS);
+    static constexpr size_t prev = align16(owner + MAX_ITEMS);
+    static constexpr size_t queue = align16(prev + TILE_PIXELS);
+    static constexpr size_t misc = align16(queue + (ASSIGN_THREADS / 32) * 64 * sizeof(uint32_t));
     static constexpr size_t maps = align16(misc + 64);
 };
 static_assert(AssignSmem::rec1 % 16 == 0 && AssignSmem::rec2 % 16 == 0 && AssignSmem::col % 16 == 0 &&
@@ -88,11 +90,35 @@ static_assert(AssignSmem::rec1 % 16 == 0 && AssignSmem::rec2 % 16 == 0 && Assign
                   AssignSmem::area % 16 == 0 && AssignSmem::best % 16 == 0 &&
                   AssignSmem::first % 16 == 0 && AssignSmem::mfirst % 16 == 0 &&
                   AssignSmem::cfirst % 16 == 0 &&
-                  AssignSmem::owner % 16 == 0 && AssignSmem::misc % 16 == 0 &&
+                  AssignSmem::owner % 16 == 0 && AssignSmem::prev % 16 == 0 && AssignSmem::queue % 16 == 0 &&
+                  AssignSmem::misc % 16 == 0 &&
                   AssignSmem::maps % 16 == 0,
               "shared-memory sections aligned");
 static_assert(MAX_TILE_CANDIDATES <= 256, "item owners are bytes");
 static_assert(MAX_TILE_CANDIDATES % 32 == 0, "the scans give each lane whole candidates");
+
+// Rank of cluster k among the tile's candidates (cid sorted ascending), or -1.
+__device__ __forceinline__ int find_slot(const int *cid, int cnt, int k)
+{
+    int lo = 0, hi = cnt;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (cid[mid] < k) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < cnt && cid[lo] == k ? lo : -1;
+}
+
+// A lower bound of D (Eq. 3) from the pixel's own colour distance and the
+// spatial term, in FP32 such that it never exceeds the D scalp_distance()
+// computes from the same dcp and ds: there dcol = lam*dcp + (1-lam)*avg is a
+// rounded sum of non-negative terms, so dcol >= fl(lam*dcp); dcon =
+// 1 + gamma*avg_w >= 1; D = fl(dcol*dcon + fl(ms2*ds)) >= fl(fl(lam*dcp) +
+// fl(ms2*ds)), rounding being monotone.  (lam in [0, 1], gamma >= 0.)
+__device__ __forceinline__ float distance_lower_bound(float dcp, float lam, float ms2, float ds)
+{
+    return __fadd_rn(__fmul_rn(lam, dcp), __fmul_rn(ms2, ds));
+}
 
 __device__ __forceinline__ unsigned long long pack_best(float D, int slot)
 {
@@ -218,9 +244,17 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
     int *mfirst = reinterpret_cast<int *>(smem + AssignSmem::mfirst);
     int *cfirst = reinterpret_cast<int *>(smem + AssignSmem::cfirst);
     unsigned char *owner = smem + AssignSmem::owner;
+    unsigned char *prev_slot = smem + AssignSmem::prev;
     int *misc = reinterpret_cast<int *>(smem + AssignSmem::misc);
     float2 *maps = reinterpret_cast<float2 *>(smem + AssignSmem::maps);
     const uint32_t maps_u32 = smem_u32(maps);
+
+    // this thread's pixels: block (warp + j*WARPS) of the tile, lane within it
+    auto my_pixel = [&](int j, int &qx, int &qy) {
+        const int blk = warp + j * WARPS;
+        qx = x0 + (blk % (TILE_X / WARP_BLOCK_X)) * WARP_BLOCK_X + (lane % WARP_BLOCK_X);
+        qy = y0 + (blk / (TILE_X / WARP_BLOCK_X)) * WARP_BLOCK_Y + (lane / WARP_BLOCK_X);
+    };
 
     const int off = a.tile_off[tile];
     // the list capacity is a proven bound; the clamp only guards memory if the
@@ -238,6 +272,14 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
     // candidates sorted by cluster index (ranks of distinct ids); the id
     // staging reuses the `best` words before they are initialised
     int *ids = reinterpret_cast<int *>(best);
+    // this thread's pixels' previous labels (their loads overlap the set-up)
+    int prev_lab[PIX_PER_THREAD];
+#pragma unroll
+    for (int j = 0; j < PIX_PER_THREAD; ++j) {
+        int px, py;
+        my_pixel(j, px, py);
+        prev_lab[j] = fast && px < a.W && py < a.H ? a.labels[(long long)py * a.W + px] : -1;
+    }
     int myid = INT_MAX;
     ClusterDev cd;  // this thread's candidate: its load overlaps the barrier
     if (fast && tid < cnt) {
@@ -295,6 +337,24 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
         if (lane == 0) misc[2] = used;
     }
     __syncthreads();
+
+    // each pixel's previous label, as a candidate slot when the pixel lies in
+    // that candidate's rectangle (0xff otherwise): pass 1 below evaluates it
+    // first, pass 2 skips it
+    if (fast) {
+#pragma unroll
+        for (int j = 0; j < PIX_PER_THREAD; ++j) {
+            int px, py;
+            my_pixel(j, px, py);
+            int c = prev_lab[j] >= 0 ? find_slot(cid, cnt, prev_lab[j]) : -1;
+            if (c >= 0) {
+                const int4 r0 = rec0[c];
+                if (px < r0.x || px >= r0.x + (r0.z & 0xff) || py < r0.y || py >= r0.y + ((r0.z >> 8) & 0xff))
+                    c = -1;
+            }
+            prev_slot[(py - y0) * TILE_X + (px - x0)] = (unsigned char)(c >= 0 ? c : 0xff);
+        }
+    }
 
     // the distance maps of the candidates whose boxes fit: entries [0, used)
     // hold the leading candidates' boxes back to back, row-major; the
@@ -357,14 +417,78 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
 #pragma unroll
     for (int j = 0; j < PIX_PER_THREAD; ++j) bestk[j] = INT_MAX;
 
-    // this thread's pixels: block (warp + j*WARPS) of the tile, lane within it
-    auto my_pixel = [&](int j, int &qx, int &qy) {
-        const int blk = warp + j * WARPS;
-        qx = x0 + (blk % (TILE_X / WARP_BLOCK_X)) * WARP_BLOCK_X + (lane % WARP_BLOCK_X);
-        qy = y0 + (blk / (TILE_X / WARP_BLOCK_X)) * WARP_BLOCK_Y + (lane / WARP_BLOCK_X);
+    // D of pixel (qx, qy) for candidate slot c (Eq. 1-3), its path length in
+    // *len; on a map when the candidate has one, else on the plane
+    auto pair_distance = [&](int qx, int qy, int c, int4 r1, int4 r2, float dcp, float ds, int *len) {
+        const PathSetup s = path_setup(qx, qy, r1.x, r1.y);
+        float sdc, sw;
+        if (r2.w >= 0) {
+            *len = path_sums_map(maps_u32 + (uint32_t)r2.w, r2.z, r2.x, r2.y, s, sdc, sw);
+        } else {
+            const float4 ck = col[c];
+            *len = path_sums<T>(plane, a.pitch, 0, 0, s, ck.x, ck.y, ck.z, sdc, sw);
+        }
+        return scalp_distance(dcp, sdc, sw, *len, a.lam, a.gamma, a.ms2, ds);
+    };
+    // the pixel's own colour distance d_c(p, C_c) (map entry, else the plane)
+    auto own_distance = [&](int qx, int qy, int c, int4 r2) {
+        if (r2.w >= 0)
+            return lds_pair(maps_u32 + (uint32_t)r2.w + (uint32_t)(((qy - r2.y) * r2.z + (qx - r2.x)) * 8)).x;
+        const float4 ck = col[c];
+        return colour_dist(fetch_sample<T>(plane + (long long)qy * a.pitch + qx), ck.x, ck.y, ck.z);
+    };
+    auto spatial = [&](int qx, int qy, int4 r1) {
+        const float ddx = (float)qx - __int_as_float(r1.z), ddy = (float)qy - __int_as_float(r1.w);
+        return fmaf(ddx, ddx, ddy * ddy);
+    };
+    auto count_pair = [&](int len) {
+        if (a.count_samples) {
+            atomicAdd(tile_samples, (unsigned)len);
+            atomicAdd(tile_samples + 1, 1u);
+        }
     };
 
     if (fast) {
+        // Pass 1: each pixel's previous label first, when it is a candidate
+        // of the pixel (it usually wins again).  Its D bounds the minimum, so
+        // pass 2 can skip every candidate whose lower bound exceeds the
+        // pixel's best D so far: such a candidate's D is larger than the
+        // minimum and cannot win or tie.  The argmin is unchanged.  A warp
+        // goes on to pass 2 when its own pixels are done (a pixel whose pass 1
+        // is still running elsewhere is simply not pruned yet).
+#pragma unroll 1
+        for (int j = 0; j < PIX_PER_THREAD; ++j) {
+            int px, py;
+            my_pixel(j, px, py);
+            const int pix = (py - y0) * TILE_X + (px - x0);
+            const int c = prev_slot[pix];
+            if (c != 0xff) {
+                const int4 r1 = rec1[c], r2 = rec2[c];
+                int len;
+                const float D = pair_distance(px, py, c, r1, r2, own_distance(px, py, c, r2), spatial(px, py, r1),
+                                              &len);
+                atomicMin(&best[pix], pack_best(D, c));
+                count_pair(len);
+            }
+        }
+
+        // Pass 2: the candidates' rectangles, cut into items.  A lane whose
+        // pair survives the bound queues it in its warp's queue in shared
+        // memory; each time 32 pairs are queued the warp walks them, one per
+        // lane, so the walks run on full warps however many pairs the bound
+        // removed from an item.  A queued pair is (slot << 10 | tile pixel).
+        uint32_t *wq = reinterpret_cast<uint32_t *>(smem + AssignSmem::queue) + warp * 64;
+        const unsigned lanes_below = (1u << lane) - 1u;
+        auto walk_queued = [&](uint32_t e) {
+            const int pix = (int)(e & 1023u), c = (int)(e >> 10);
+            const int qx = x0 + (pix & (TILE_X - 1)), qy = y0 + (pix / TILE_X);
+            const int4 r1 = rec1[c], r2 = rec2[c];
+            int len;
+            const float D = pair_distance(qx, qy, c, r1, r2, own_distance(qx, qy, c, r2), spatial(qx, qy, r1), &len);
+            atomicMin(&best[pix], pack_best(D, c));
+            count_pair(len);
+        };
+        int queued = 0;  // warp-uniform
         const int n_items = first[cnt];
         while (true) {
             int item = 0;
@@ -375,41 +499,44 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
             const int4 r0 = rec0[c];
             const int rw = r0.z & 0xff, rh = (r0.z >> 8) & 0xff;
             const int j = ((item - first[c]) << 5) + lane;  // pixel of the rectangle
-            if (j >= rw * rh) continue;
-            const bool vert = (r0.z >> 16) != 0;
-            const int slen = vert ? rh : rw, across = vert ? rw : rh;
-            const int strip = (j * r0.w) >> STRIP_RCP_BITS;
-            const int t = j - strip * STRIP * slen;
-            // t / width for a strip 1..4 wide: exact 16-bit reciprocals
-            const int width = min(STRIP, across - strip * STRIP);
-            const int along = (t * (width == 3 ? 21846 : 65536 >> (width >> 1))) >> 16;
-            const int offs = strip * STRIP + (t - along * width);
-            const int qx = r0.x + (vert ? offs : along);
-            const int qy = r0.y + (vert ? along : offs);
-            const int4 r1 = rec1[c];
-            const int4 r2 = rec2[c];
-            const PathSetup s = path_setup(qx, qy, r1.x, r1.y);
-            float sdc, sw, dcp;
-            int len;
-            if (r2.w >= 0) {
-                const uint32_t map = maps_u32 + (uint32_t)r2.w;
-                len = path_sums_map(map, r2.z, r2.x, r2.y, s, sdc, sw);
-                dcp = lds_pair(map + (uint32_t)(((qy - r2.y) * r2.z + (qx - r2.x)) * 8)).x;
-            } else {
-                const float4 ck = col[c];
-                len = path_sums<T>(plane, a.pitch, 0, 0, s, ck.x, ck.y, ck.z, sdc, sw);
-                dcp = colour_dist(fetch_sample<T>(plane + (long long)qy * a.pitch + qx), ck.x, ck.y,
-                                  ck.z);
+            bool keep = false;
+            int pix = 0;
+            if (j < rw * rh) {
+                const bool vert = (r0.z >> 16) != 0;
+                const int slen = vert ? rh : rw, across = vert ? rw : rh;
+                const int strip = (j * r0.w) >> STRIP_RCP_BITS;
+                const int t = j - strip * STRIP * slen;
+                // t / width for a strip 1..4 wide: exact 16-bit reciprocals
+                const int width = min(STRIP, across - strip * STRIP);
+                const int along = (t * (width == 3 ? 21846 : 65536 >> (width >> 1))) >> 16;
+                const int offs = strip * STRIP + (t - along * width);
+                const int qx = r0.x + (vert ? offs : along);
+                const int qy = r0.y + (vert ? along : offs);
+                pix = (qy - y0) * TILE_X + (qx - x0);
+                if (prev_slot[pix] != c) {  // else evaluated in pass 1
+                    const int4 r1 = rec1[c];
+                    const float dcp = own_distance(qx, qy, c, rec2[c]);
+                    // best holds (D bits, slot); all ones (a NaN) until a D arrives
+                    const float dbest = __uint_as_float((unsigned)(best[pix] >> 32));
+                    keep = !(distance_lower_bound(dcp, a.lam, a.ms2, spatial(qx, qy, r1)) > dbest);
+                    // a pair that cannot win is not walked (counted as the method's work)
+                    if (!keep) count_pair(max(abs(qx - r1.x), abs(qy - r1.y)) + 1);
+                }
             }
-            const float ddx = (float)qx - __int_as_float(r1.z), ddy = (float)qy - __int_as_float(r1.w);
-            const float ds = fmaf(ddx, ddx, ddy * ddy);
-            const float D = scalp_distance(dcp, sdc, sw, len, a.lam, a.gamma, a.ms2, ds);
-            atomicMin(&best[(qy - y0) * TILE_X + (qx - x0)], pack_best(D, c));
-            if (a.count_samples) {
-                atomicAdd(tile_samples, (unsigned)len);
-                atomicAdd(tile_samples + 1, 1u);
+            const unsigned kept = __ballot_sync(0xffffffffu, keep);
+            if (keep) wq[queued + __popc(kept & lanes_below)] = ((uint32_t)c << 10) | (uint32_t)pix;
+            queued += __popc(kept);
+            __syncwarp();
+            if (queued >= 32) {
+                const uint32_t e = wq[lane];
+                __syncwarp();
+                if (lane < queued - 32) wq[lane] = wq[32 + lane];
+                queued -= 32;
+                __syncwarp();
+                walk_queued(e);
             }
         }
+        if (lane < queued) walk_queued(wq[lane]);
     } else {
         // per-pixel path: every candidate straight from the global list
 #pragma unroll 1

@@ -267,6 +267,36 @@ def test_end_to_end_bsd_shape(S):
     seg.close()
 
 
+def test_sample_count_equals_method_work(S):
+    """The device's count of path samples and (pixel, cluster) pairs of one
+    assignment (what the benchmark's roofline divides by) equals the method's
+    work computed here from the same state: every pixel of every cluster's
+    window (exact integer test), |P| = max(|dx|, |dy|) + 1 samples each.  It
+    holds whether a pair's path was walked or skipped by the lower bound."""
+    H, W, K = 150, 230, 120
+    rgb, con, _ = synth.small_image(H, W, seed=33)
+    orc = oracle.Solver(oracle.lab_from_rgb(rgb), con, K)
+    orc.iterate(2)
+    st = orc.state()
+    seg = make_seg(S, rgb, con, K)
+    seg.set_state(to_gpu_state(st))
+    seg.count_samples(1)
+    seg.iterate(1)
+    samples, pairs = seg.count_samples(0)
+    N = H * W
+    ys, xs = np.mgrid[0:H, 0:W]
+    ref_s = ref_p = 0
+    for k in range(orc.Keff):
+        n, sx, sy = int(st["n"][k]), int(st["sx"][k]), int(st["sy"][k])
+        win = ((K * (n * xs.astype(object) - sx) ** 2 <= N * n * n) &
+               (K * (n * ys.astype(object) - sy) ** 2 <= N * n * n)).astype(bool)
+        ex, ey = int(st["ex"][k]), int(st["ey"][k])
+        ref_p += int(win.sum())
+        ref_s += int((np.maximum(np.abs(xs - ex), np.abs(ys - ey)) + 1)[win].sum())
+    assert (samples, pairs) == (ref_s, ref_p)
+    seg.close()
+
+
 def test_clusters_export(S):
     """scalp_clusters: the descriptors C_k = [l_k, a_k, b_k, X_k] (Sec. II-A)
     after one iteration from the oracle's state, against the oracle's colours
