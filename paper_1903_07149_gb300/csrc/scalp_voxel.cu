@@ -455,9 +455,31 @@ __device__ __forceinline__ unsigned long long vpack_best(float D, int slot)
     return ((unsigned long long)__float_as_uint(D) << 32) | (unsigned)slot;  // D >= 0
 }
 
+// Rank of cluster k among the sorted candidate ids, or -1.
+__device__ __forceinline__ int vfind_slot(const int *ids, int cnt, int k)
+{
+    int lo = 0, hi = cnt;
+    while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (ids[mid] < k) lo = mid + 1;
+        else hi = mid;
+    }
+    return lo < cnt && ids[lo] == k ? lo : -1;
+}
+
+// The pruning of the 2-D assignment, in 3-D.  Pass 1 evaluates each voxel's
+// previous label (when it is a candidate of the voxel); pass 2 skips every
+// other candidate whose FP32 lower bound fl(fl(lam*d_c(p)) + fl(m^2/r^2*d_s))
+// exceeds the voxel's best D so far (the computed D is never below that
+// bound: dcol >= fl(lam*dcp), dcon >= 1, and rounding is monotone), so the
+// argmin is unchanged; the surviving pairs are queued per warp and walked 32
+// at a time.
 __global__ void __launch_bounds__(VTILE) k_vassign(VoxArgs a)
 {
     __shared__ VoxCluster cand[VITEM_CAND];
+    __shared__ int s_sorted[VITEM_CAND];   // candidate ids in slot order
+    __shared__ unsigned char s_prev[VTILE];  // each voxel's previous label as a slot, 0xff if none
+    __shared__ unsigned s_queue[VTILE / 32][64];
     __shared__ int4 s_box[VITEM_CAND];     // (xa, ya, ta, w | h << 8 | d << 16)
     __shared__ int2 s_rcp[VITEM_CAND];     // 16-bit reciprocals of w and h
     __shared__ int s_ids[VITEM_CAND];
@@ -479,6 +501,7 @@ __global__ void __launch_bounds__(VTILE) k_vassign(VoxArgs a)
     const long long p = ((long long)t * a.H + y) * a.W + x;
     unsigned my_samples = 0, my_pairs = 0;
     int lab = -1;
+    const int prev = fast && valid ? a.labels[p] : -1;  // overlaps the set-up
 
     if (fast) {
         // candidates sorted by cluster index (ranks of distinct ids)
@@ -495,6 +518,7 @@ __global__ void __launch_bounds__(VTILE) k_vassign(VoxArgs a)
             for (int j = 0; j < cnt; ++j) rank += s_ids[j] < myid;
             const VoxCluster cd = a.cdev[myid];
             cand[rank] = cd;
+            s_sorted[rank] = myid;
             const int xa = max(cd.xlo, x0), xb = min(min(cd.xhi, x0 + VTX - 1), a.W - 1);
             const int ya = max(cd.ylo, y0), yb = min(min(cd.yhi, y0 + VTY - 1), a.H - 1);
             const int ta = max(cd.tlo, t0), tb = min(min(cd.thi, t0 + VTT - 1), a.T - 1);
@@ -532,7 +556,47 @@ __global__ void __launch_bounds__(VTILE) k_vassign(VoxArgs a)
             const int f = s_first[tid], n = s_nit[tid];
             for (int j = 0; j < n; ++j) s_owner[f + j] = (unsigned char)tid;
         }
+        // this voxel's previous label as a slot when the voxel is in that box
+        int pslot = prev >= 0 ? vfind_slot(s_sorted, cnt, prev) : -1;
+        if (pslot >= 0) {
+            const int4 b = s_box[pslot];
+            if (x < b.x || x >= b.x + (b.w & 0xff) || y < b.y || y >= b.y + ((b.w >> 8) & 0xff) || t < b.z ||
+                t >= b.z + (b.w >> 16))
+                pslot = -1;
+        }
+        s_prev[tid] = (unsigned char)(pslot >= 0 ? pslot : 0xff);
         __syncthreads();
+        // D of voxel (qx, qy, qt) for candidate slot c, from its own sample
+        auto own_dc = [&](int qx, int qy, int qt, const VoxCluster &cd) {
+            return colour_dist(__ldg(a.plane + ((long long)qt * a.H + qy) * a.W + qx), cd.L, cd.a, cd.b);
+        };
+        auto vspatial = [&](int qx, int qy, int qt, const VoxCluster &cd) {
+            const float ddx = (float)qx - cd.xk, ddy = (float)qy - cd.yk, ddt = (float)qt - cd.tk;
+            return fmaf(ddx, ddx, fmaf(ddy, ddy, ddt * ddt));
+        };
+        auto evaluate = [&](int qx, int qy, int qt, int c) {
+            const VoxCluster &cd = cand[c];
+            float sdc, sw;
+            const int len = vpath_sums(a.plane, a.W, a.HW, qx, qy, qt, cd.ex, cd.ey, cd.et, cd.L, cd.a, cd.b,
+                                       sdc, sw);
+            const float D = scalp_distance(own_dc(qx, qy, qt, cd), sdc, sw, len, a.lam, a.gamma, a.ms2,
+                                           vspatial(qx, qy, qt, cd));
+            atomicMin(&s_best[((qt - t0) * VTY + (qy - y0)) * VTX + (qx - x0)], vpack_best(D, c));
+            my_samples += len;
+            my_pairs += 1;
+        };
+        // pass 1: the previous label (no barrier before pass 2: a voxel whose
+        // pass 1 is still running elsewhere is simply not pruned yet)
+        if (pslot >= 0) evaluate(x, y, t, pslot);
+        // pass 2: the candidates' boxes, cut into items; survivors queued
+        unsigned *wq = s_queue[tid >> 5];
+        const unsigned lanes_below = (1u << lane) - 1u;
+        int queued = 0;
+        auto walk_queued = [&](unsigned e) {
+            const int v = (int)(e & (VTILE - 1)), c = (int)(e >> 9);
+            evaluate(x0 + v % VTX, y0 + (v / VTX) % VTY, t0 + v / (VTX * VTY), c);
+        };
+        static_assert(VTILE == 512, "queued pairs are (slot << 9 | voxel)");
         const int n_items = s_first[cnt];
         while (true) {
             int item = 0;
@@ -543,27 +607,43 @@ __global__ void __launch_bounds__(VTILE) k_vassign(VoxArgs a)
             const int4 b = s_box[c];
             const int w = b.w & 0xff, h = (b.w >> 8) & 0xff, d = b.w >> 16;
             const int j = ((item - s_first[c]) << 5) + lane;
-            if (j >= w * h * d) continue;
-            const int2 r = s_rcp[c];
-            // exact: j < 512 and w, h <= 16, so the 16-bit reciprocals give floor
-            const int q = (j * r.x) >> 16;  // j / w
-            const int qx = b.x + (j - q * w);
-            const int qt = (q * r.y) >> 16;  // q / h
-            const int qy = b.y + (q - qt * h);
-            const int qtt = b.z + qt;
-            const VoxCluster &cd = cand[c];
-            float sdc, sw;
-            const int len = vpath_sums(a.plane, a.W, a.HW, qx, qy, qtt, cd.ex, cd.ey, cd.et, cd.L, cd.a, cd.b,
-                                       sdc, sw);
-            const float4 v = __ldg(a.plane + ((long long)qtt * a.H + qy) * a.W + qx);
-            const float dcp = colour_dist(v, cd.L, cd.a, cd.b);
-            const float ddx = (float)qx - cd.xk, ddy = (float)qy - cd.yk, ddt = (float)qtt - cd.tk;
-            const float ds = fmaf(ddx, ddx, fmaf(ddy, ddy, ddt * ddt));
-            const float D = scalp_distance(dcp, sdc, sw, len, a.lam, a.gamma, a.ms2, ds);
-            atomicMin(&s_best[((qtt - t0) * VTY + (qy - y0)) * VTX + (qx - x0)], vpack_best(D, c));
-            my_samples += len;
-            my_pairs += 1;
+            bool keep = false;
+            int vox = 0;
+            if (j < w * h * d) {
+                const int2 r = s_rcp[c];
+                // exact: j < 512 and w, h <= 16, so the 16-bit reciprocals give floor
+                const int q = (j * r.x) >> 16;  // j / w
+                const int qx = b.x + (j - q * w);
+                const int qt = (q * r.y) >> 16;  // q / h
+                const int qy = b.y + (q - qt * h);
+                const int qtt = b.z + qt;
+                vox = ((qtt - t0) * VTY + (qy - y0)) * VTX + (qx - x0);
+                if (s_prev[vox] != c) {  // else evaluated in pass 1
+                    const VoxCluster &cd = cand[c];
+                    const float lb = __fadd_rn(__fmul_rn(a.lam, own_dc(qx, qy, qtt, cd)),
+                                               __fmul_rn(a.ms2, vspatial(qx, qy, qtt, cd)));
+                    // s_best holds (D bits, slot); all ones (a NaN) until a D arrives
+                    keep = !(lb > __uint_as_float((unsigned)(s_best[vox] >> 32)));
+                    if (!keep) {  // cannot win: not walked (counted as the method's work)
+                        my_samples += max(abs(qx - cd.ex), max(abs(qy - cd.ey), abs(qtt - cd.et))) + 1;
+                        my_pairs += 1;
+                    }
+                }
+            }
+            const unsigned kept = __ballot_sync(0xffffffffu, keep);
+            if (keep) wq[queued + __popc(kept & lanes_below)] = ((unsigned)c << 9) | (unsigned)vox;
+            queued += __popc(kept);
+            __syncwarp();
+            if (queued >= 32) {
+                const unsigned e = wq[lane];
+                __syncwarp();
+                if (lane < queued - 32) wq[lane] = wq[32 + lane];
+                queued -= 32;
+                __syncwarp();
+                walk_queued(e);
+            }
         }
+        if (lane < queued) walk_queued(wq[lane]);
         __syncthreads();
         if (valid) {
             const unsigned long long bb = s_best[tid];
