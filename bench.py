@@ -461,7 +461,7 @@ def measure_batch(args, storage: str, flush, batch_imgs, sm_mhz=None):
 
 def measure_serving(args, batch_imgs, n_requests: int = 2000, rate_hz: float = 500.0,
                     budget_gb: float = 40.0, storage: str = "f16", step_mpix: float = 4.0,
-                    split_mpix: float = 4.0):
+                    split_mpix: float = 4.0, large_first: bool = True, serial: bool = True):
     """The serving form: Poisson arrivals at rate_hz over the batch size mix
     plus 10% 2160x3840 images, admitted into servers with a device memory
     budget; each request gets 10 iterations and connectivity enforcement.
@@ -499,7 +499,11 @@ def measure_serving(args, batch_imgs, n_requests: int = 2000, rate_hz: float = 5
     # lanes: (server, stream, queue); a request goes to the first lane whose
     # size bound holds it
     if split_mpix > 0:
-        specs = [(split_mpix * 1e6, -5, 0.25), (float("inf"), 0, 0.75)]  # bound, priority, pool share
+        # bound, stream priority, pool share; with large_first the rare large
+        # requests (which set the tail) get the high-priority stream
+        hi, lo = -5, 0
+        specs = [(split_mpix * 1e6, lo if large_first else hi, 0.25),
+                 (float("inf"), hi if large_first else lo, 0.75)]
     else:
         specs = [(float("inf"), 0, 1.0)]
     lanes = []
@@ -565,6 +569,22 @@ def measure_serving(args, batch_imgs, n_requests: int = 2000, rate_hz: float = 5
     for _, srv, _, _ in lanes:
         srv.close()
     stream = lanes[0][2]
+    tot = sum(pix) * iters / 1e6
+    res = {
+        "requests": n_requests, "rate_hz": rate_hz, "budget_gb": budget_gb, "storage": storage,
+        "step": (f"least remaining work first, at most {step_mpix:g} Mpix per step" if step_mpix
+                 else "every request in flight each step"),
+        "lanes": (f"requests <= {split_mpix:g} Mpix on one server, larger ones on another, one host thread "
+                  f"each; the {'larger' if large_first else 'smaller'} requests' stream has the higher priority"
+                  if split_mpix else "one server"),
+        "mix": "64 sizes of the batch mix + 10% 2160x3840", "iters": iters,
+        "value": tot / wall, "unit": UNIT, "wall_s": wall,
+        "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+        "p99_small_ms": float(np.percentile(lat[np.array(pix) <= 4e6], 99) * 1e3),
+        "p99_large_ms": float(np.percentile(lat[np.array(pix) > 4e6], 99) * 1e3),
+    }
+    if not serial:
+        return res
 
     # serial plain-FP32 solves of the same stream
     lat_s = np.zeros(n_requests)
@@ -587,20 +607,23 @@ def measure_serving(args, batch_imgs, n_requests: int = 2000, rate_hz: float = 5
     wall_s = time.perf_counter() - t0
     for s in segs.values():
         s.close()
-    tot = sum(pix) * iters / 1e6
-    return {
-        "requests": n_requests, "rate_hz": rate_hz, "budget_gb": budget_gb, "storage": storage,
-        "step": (f"least remaining work first, at most {step_mpix:g} Mpix per step" if step_mpix
-                 else "every request in flight each step"),
-        "lanes": (f"requests <= {split_mpix:g} Mpix on a high-priority server, larger ones on a "
-                  "low-priority one, one host thread each" if split_mpix else "one server"),
-        "mix": "64 sizes of the batch mix + 10% 2160x3840", "iters": iters,
-        "value": tot / wall, "unit": UNIT, "wall_s": wall,
-        "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
-        "serial_f32": {"value": tot / wall_s, "unit": UNIT, "wall_s": wall_s,
-                       "p50_ms": float(np.percentile(lat_s, 50) * 1e3),
-                       "p99_ms": float(np.percentile(lat_s, 99) * 1e3)},
-    }
+    res["serial_f32"] = {"value": tot / wall_s, "unit": UNIT, "wall_s": wall_s,
+                         "p50_ms": float(np.percentile(lat_s, 50) * 1e3),
+                         "p99_ms": float(np.percentile(lat_s, 99) * 1e3)}
+    return res
+
+
+def measure_serving_sweep(args, batch_imgs, rates=(500.0, 1000.0, 1500.0, 2000.0), n_requests: int = 1000):
+    """The serving form at rising Poisson rates (same size mix): delivered
+    Mpix*iter/s and latency per rate; where the delivered rate stops
+    following the offered one, the form is at capacity."""
+    out = []
+    for rate in rates:
+        r = measure_serving(args, batch_imgs, n_requests=n_requests, rate_hz=rate, serial=False)
+        offered = r["value"] * r["wall_s"] / (n_requests / rate)
+        out.append({"rate_hz": rate, "offered_mpix_iter_s": offered, "delivered_mpix_iter_s": r["value"],
+                    "p50_ms": r["p50_ms"], "p99_ms": r["p99_ms"], "wall_s": r["wall_s"]})
+    return out
 
 
 def measure_multiscale(args, flush, storage: str = "f32"):
@@ -759,7 +782,8 @@ def measure_voxel(args, flush):
             step().close()
             ev1[i].record(stream)
         torch.cuda.synchronize()
-        # work of one iteration, counted on the device, and the iteration time
+        # work of one iteration, counted on the device, the iteration time,
+        # and the assignment's own time per launch (event pairs around it)
         seg = step()
         seg.count_samples(1)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -769,17 +793,21 @@ def measure_voxel(args, flush):
         samples, pairs = seg.count_samples(0)
         torch.cuda.synchronize()
         it_ms = e0.elapsed_time(e1)
+        seg.profile(1)
+        seg.iterate(iters)
+        a_ms, a_n = seg.profile(0)
         keff = seg.Keff
         seg.close()
     ms = sum(a.elapsed_time(b) for a, b in zip(ev0, ev1)) / n_steps
     N = T * H * W
-    roof = assign_roofline(samples, pairs, N, it_ms / 1e3, "f32", FALLBACK_SM_MHZ, clk_measured=False)
+    launch_s = a_ms / max(a_n, 1) / 1e3
+    roof = assign_roofline(samples, pairs, N, launch_s, "f32", FALLBACK_SM_MHZ, clk_measured=False)
     roof["kernel"] = "k_vassign"
-    roof["note"] = "whole iteration (assignment, update, projection, lists) timed, not the assignment alone"
+    roof["note"] = "the assignment launch alone (CUDA events around it); samples gathered from global memory"
     return {"workload": name, "T": T, "H": H, "W": W, "K": K, "Keff": keff, "iters": iters,
             "value": N * iters / (ms / 1e3) / 1e6, "unit": "Mvox*iter/s", "ms_per_solve": ms,
-            "iteration_ms": it_ms, "samples_per_iteration": samples, "pairs_per_iteration": pairs,
-            "roofline": roof}
+            "iteration_ms": it_ms, "assign_ms_per_launch": launch_s * 1e3,
+            "samples_per_iteration": samples, "pairs_per_iteration": pairs, "roofline": roof}
 
 
 def measure_single_form(args, w, rgb, con, storage: str, flush, steps=None, sm_mhz=None):
@@ -1042,6 +1070,7 @@ def run_ours(args):
         line["forms"]["supervoxels"] = measure_voxel(args, flush)
         if not args.no_serving:
             line["forms"]["serving"] = measure_serving(args, batch_imgs)
+            line["forms"]["serving"]["rate_sweep"] = measure_serving_sweep(args, batch_imgs)
         # GPU states for the precision statement (computed in the CPU leg)
         seg.reload(d_rgb, d_con)
         seg.iterate(iters)
@@ -1082,9 +1111,10 @@ def run_form(args):
     elif args.only_form == "serving":
         bws = synth.batch_configs()
         imgs = (bws, *synth.batch_images(bws))
-        res = {"one_server": measure_serving(args, imgs, step_mpix=0.0, split_mpix=0.0),
-               "two_lanes": measure_serving(args, imgs, step_mpix=0.0, split_mpix=4.0),
-               "two_lanes_step_budget": measure_serving(args, imgs)}
+        res = {"large_first": measure_serving(args, imgs),
+               "small_first": measure_serving(args, imgs, large_first=False, serial=False),
+               "one_server": measure_serving(args, imgs, step_mpix=0.0, split_mpix=0.0, serial=False),
+               "sweep": measure_serving_sweep(args, imgs)}
     elif args.only_form == "batched":
         bws = synth.batch_configs()
         imgs = (bws, *synth.batch_images(bws))

@@ -382,6 +382,11 @@ int scalp_voxel_get_state(scalp_vctx *ctx, const scalp_voxel_state *state);
 int scalp_voxel_set_state(scalp_vctx *ctx, const scalp_voxel_state *state);
 /* As scalp_count_samples, for the supervoxel assignment. */
 int scalp_voxel_count_samples(scalp_vctx *ctx, int32_t enable, int64_t *samples, int64_t *pairs);
+/* As scalp_profile, for the supervoxel assignment: with enable = 1 each
+ * assignment launch of scalp_voxel_iterate is bracketed by CUDA events;
+ * *ms and *launches receive the accumulated time and count (synchronises
+ * when events are pending; 1 resets, 0 stops, -1 only reads). */
+int scalp_voxel_profile(scalp_vctx *ctx, int32_t enable, double *ms, int64_t *launches);
 void scalp_voxel_destroy(scalp_vctx *ctx);
 
 /* ---- Serving: continuous batching of solves in flight ------------------------

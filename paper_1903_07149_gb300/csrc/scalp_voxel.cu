@@ -805,6 +805,12 @@ struct scalp_vctx {
     VLayout L;
     VoxArgs a;
     int iterations;
+    // profiling: an event pair around each assignment launch
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev;
+    int ev_pending = 0;  // pairs recorded and not yet read
+    double prof_ms = 0.0;
+    long long prof_launches = 0;
 };
 
 namespace {
@@ -969,7 +975,18 @@ int scalp_voxel_iterate(scalp_vctx *c, int32_t n)
     if (!c || n < 0) return vfail(SCALP_E_ARG, "ctx is NULL or n < 0");
     for (int i = 0; i < n; ++i) {
         const unsigned tiles = (unsigned)(c->a.n_tx * c->a.n_ty * c->a.n_tt);
+        const bool prof = c->profiling;
+        if (prof) {
+            while ((int)c->ev.size() < 2 * (c->ev_pending + 1)) {
+                cudaEvent_t e;
+                const int rc = vcheck(cudaEventCreate(&e), "profiling event");
+                if (rc) return rc;
+                c->ev.push_back(e);
+            }
+            cudaEventRecord(c->ev[2 * c->ev_pending], c->st);
+        }
         k_vassign<<<tiles, VTILE, 0, c->st>>>(c->a);
+        if (prof) cudaEventRecord(c->ev[2 * c->ev_pending++ + 1], c->st);
         venqueue_update(c, 1, 0);
         ++c->iterations;
     }
@@ -1083,10 +1100,38 @@ int scalp_voxel_count_samples(scalp_vctx *c, int32_t enable, int64_t *samples, i
     return SCALP_OK;
 }
 
+int scalp_voxel_profile(scalp_vctx *c, int32_t enable, double *ms, int64_t *launches)
+{
+    if (!c) return vfail(SCALP_E_ARG, "ctx is NULL");
+    if (c->ev_pending) {
+        const int rc = vcheck(cudaStreamSynchronize(c->st), "synchronise");
+        if (rc) return rc;
+        for (int i = 0; i < c->ev_pending; ++i) {
+            float t = 0.f;
+            const int r2 = vcheck(cudaEventElapsedTime(&t, c->ev[2 * i], c->ev[2 * i + 1]), "event time");
+            if (r2) return r2;
+            c->prof_ms += t;
+            c->prof_launches += 1;
+        }
+        c->ev_pending = 0;
+    }
+    if (ms) *ms = c->prof_ms;
+    if (launches) *launches = c->prof_launches;
+    if (enable >= 0) {
+        if (enable) {
+            c->prof_ms = 0.0;
+            c->prof_launches = 0;
+        }
+        c->profiling = enable != 0;
+    }
+    return SCALP_OK;
+}
+
 void scalp_voxel_destroy(scalp_vctx *c)
 {
     if (!c) return;
     cudaStreamSynchronize(c->st);
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     delete c;
 }
 

@@ -103,7 +103,7 @@ EXPORTS = (
     "scalp_gradient_prior_workspace_bytes", "scalp_gradient_prior",
     "scalp_voxel_workspace_bytes", "scalp_voxel_init", "scalp_voxel_iterate", "scalp_voxel_labels",
     "scalp_voxel_get_info", "scalp_voxel_get_state", "scalp_voxel_set_state",
-    "scalp_voxel_count_samples", "scalp_voxel_destroy",
+    "scalp_voxel_count_samples", "scalp_voxel_profile", "scalp_voxel_destroy",
 )
 
 _lib = None
@@ -185,6 +185,7 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "scalp_voxel_get_state": (ctypes.c_int, [P, ctypes.POINTER(scalp_voxel_state)]),
             "scalp_voxel_set_state": (ctypes.c_int, [P, ctypes.POINTER(scalp_voxel_state)]),
             "scalp_voxel_count_samples": (ctypes.c_int, [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+            "scalp_voxel_profile": (ctypes.c_int, [P, I32, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(I64)]),
             "scalp_voxel_destroy": (None, [P]),
             "scalp_gradient_prior": (ctypes.c_int, [ctypes.POINTER(scalp_image), P, I64, I32, P, P,
                                                     ctypes.c_size_t]),
@@ -925,6 +926,12 @@ class VoxelSegmenter:
         a, b = ctypes.c_int64(), ctypes.c_int64()
         _check(load().scalp_voxel_count_samples(self.ctx, int(enable), ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def profile(self, enable: int):
+        """(ms, launches) of the assignment launches since profiling was enabled."""
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        _check(load().scalp_voxel_profile(self.ctx, int(enable), ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
 
     def close(self):
         if getattr(self, "ctx", None):
