@@ -79,7 +79,10 @@ typedef struct {
     float gamma;           /* Eq. 2 contour weight, >= 0; < 0 selects 2r */
     int32_t storage;       /* SCALP_STORAGE_F32 or SCALP_STORAGE_F16 */
     int32_t use_graph;     /* 1: replay each iteration as a CUDA graph (non-NULL stream) */
-    int32_t global_walk;   /* 1: walk every path on the plane in global memory (no distance maps) */
+    int32_t global_walk;   /* bit 0: walk every path on the plane in global memory (no distance
+                              maps); bit 1: evaluate every (pixel, candidate) pair, without the
+                              lower bound that skips pairs which cannot win (the same labels and
+                              state, slower: for tests) */
     int32_t prior;         /* SCALP_PRIOR_INPUT (default) or SCALP_PRIOR_GRADIENT; with the
                               latter the contour argument must be NULL or have NULL data */
     void *stream;          /* cudaStream_t for all device work */

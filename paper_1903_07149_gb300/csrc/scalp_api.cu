@@ -515,7 +515,8 @@ int scalp_init(scalp_ctx **out, const scalp_image *image, const scalp_contour *c
     // distance maps of the assignment CTAs (none: every path walks the plane)
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
-    a.map_cap = params->global_walk ? 0 : assign_map_capacity(dev);
+    a.map_cap = (params->global_walk & 1) ? 0 : assign_map_capacity(dev);
+    a.prune = (params->global_walk & 2) ? 0 : 1;
     c->smem = assign_smem_bytes(a.map_cap);
     int rc = cuda_check(c, assign_configure(params->storage), "configure kernel");
     if (rc == SCALP_OK) rc = cuda_check(c, srgb_table(&a.lut, c->st), "transfer-function table");

@@ -518,7 +518,7 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
                     const float dcp = own_distance(qx, qy, c, rec2[c]);
                     // best holds (D bits, slot); all ones (a NaN) until a D arrives
                     const float dbest = __uint_as_float((unsigned)(best[pix] >> 32));
-                    keep = !(distance_lower_bound(dcp, a.lam, a.ms2, spatial(qx, qy, r1)) > dbest);
+                    keep = !a.prune || !(distance_lower_bound(dcp, a.lam, a.ms2, spatial(qx, qy, r1)) > dbest);
                     // a pair that cannot win is not walked (counted as the method's work)
                     if (!keep) count_pair(max(abs(qx - r1.x), abs(qy - r1.y)) + 1);
                 }

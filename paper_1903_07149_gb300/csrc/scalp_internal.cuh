@@ -138,6 +138,7 @@ struct SolveArgs {
     // ceil(2^32 / W) where that is exact; 0: divide
     unsigned grid_rcp_x;
     int count_samples;
+    int prune;         // 1: skip pairs whose lower bound exceeds the pixel's best D (0: evaluate all)
     const float4 *plane32;   // (L, a, b, w) per pixel, row pitch `pitch` [FP32 storage]
     const uint2 *plane16;    // the same as 4 x fp16                   [FP16 storage]
     int *labels;

@@ -317,7 +317,7 @@ class Segmenter:
 
     def __init__(self, rgb, contour, K: int, m: float = 10.0, lam: float = 0.5,
                  sigma: float = 0.25, gamma: float = -1.0, storage: str = "f32",
-                 use_graph: bool = True, global_walk: bool = False, stream=None,
+                 use_graph: bool = True, global_walk: bool = False, stream=None, prune: bool = True,
                  prior: str = "input"):
         import torch
 
@@ -328,7 +328,7 @@ class Segmenter:
         p.lambda_, p.sigma, p.gamma = lam, sigma, gamma
         p.storage = STORAGE[storage]
         p.use_graph = int(use_graph)
-        p.global_walk = int(global_walk)
+        p.global_walk = int(global_walk) | (0 if prune else 2)
         p.prior = PRIOR[prior]
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         p.stream = self.stream.cuda_stream

@@ -297,6 +297,27 @@ def test_sample_count_equals_method_work(S):
     seg.close()
 
 
+@pytest.mark.parametrize("name", ["bsd_321x481_k400", "hd_1080x1920_k2000"])
+def test_pruning_is_exact(S, name):
+    """The assignment skips pairs whose lower bound exceeds the pixel's best D;
+    the same solve evaluating every pair gives the same bits: labels, state
+    and the counted work, over ten iterations."""
+    w, rgb, con = synth.single_image_config(name)
+    a = make_seg(S, rgb, con, w.K)
+    b = make_seg(S, rgb, con, w.K, prune=False)
+    a.count_samples(1)
+    b.count_samples(1)
+    a.iterate(w.iters)
+    b.iterate(w.iters)
+    assert a.count_samples(0) == b.count_samples(0)
+    la, lb = a.labels(enforce=False)[0], b.labels(enforce=False)[0]
+    assert np.array_equal(la, lb)
+    sa, sb = a.get_state(), b.get_state()
+    for k in ("n", "sx", "sy", "color", "endpoint"):
+        assert np.array_equal(sa[k], sb[k]), k
+    a.close(); b.close()
+
+
 def test_clusters_export(S):
     """scalp_clusters: the descriptors C_k = [l_k, a_k, b_k, X_k] (Sec. II-A)
     after one iteration from the oracle's state, against the oracle's colours
