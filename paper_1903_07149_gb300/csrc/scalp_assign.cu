@@ -18,17 +18,25 @@
 //      The boxes of the candidates are packed in candidate order into the map
 //      buffer; a candidate whose box no longer fits walks the plane in global
 //      memory instead, with the same per-sample arithmetic and order.
-//   3. The pixels of the tile inside a candidate's window form a rectangle,
-//      cut into strips; each 32 consecutive pixels of a candidate are one
-//      work item, and warps take items from a shared-memory counter until
-//      none are left.
-//   4. Each lane walks its pixel's path to the candidate's endpoint (one
+//   3. Pass 1: each thread evaluates its pixels' previous labels (when they
+//      are candidates of the pixel); the previous label usually wins again.
+//   4. Pass 2: the pixels of the tile inside a candidate's window form a
+//      rectangle, cut into strips; each 32 consecutive pixels of a candidate
+//      are one work item, and warps take items from a shared-memory counter
+//      until none are left.  A pair whose lower bound
+//      fl(fl(lam*d_c(p)) + fl(m^2/r^2*d_s)) exceeds the pixel's best D so far
+//      cannot win or tie (its computed D is never below the bound) and is not
+//      walked; the others are queued per warp and walked 32 at a time.
+//   5. Each walk follows the pixel's path to the candidate's endpoint (one
 //      8-byte map load and two adds per sample), forms D (Eq. 1-3) and takes
 //      a 64-bit shared-memory atomicMin of (D bits, candidate slot) for its
-//      pixel; slots are in cluster order, so ties go to the smallest k.
-//   5. Each thread writes its pixels' labels; warp-aggregated integer sums of
+//      pixel; slots are in cluster order, so ties go to the smallest k.  The
+//      argmin is that of evaluating every pair.
+//   6. Each thread writes its pixels' labels; warp-aggregated integer sums of
 //      (1, x, y, L, a, b) per label go to the global cluster sums as
 //      fire-and-forget reductions.
+// The tile body is in scalp_assign_tile.cuh (shared with the persistent
+// batched kernel).
 // A tile with more candidates than shared memory holds evaluates its pixels
 // one by one from the global candidate list instead.
 #include <algorithm>
