@@ -461,17 +461,20 @@ def measure_batch(args, storage: str, flush, batch_imgs, sm_mhz=None):
 
 def measure_serving(args, batch_imgs, n_requests: int = 2000, rate_hz: float = 500.0,
                     budget_gb: float = 40.0, storage: str = "f16", step_mpix: float = 4.0,
-                    split_mpix: float = 4.0, large_first: bool = True, serial: bool = True):
+                    split_mpix: float = 4.0, large_first: bool = False, serial: bool = True,
+                    large_step_mpix: float | None = None, equal_priority: bool = False,
+                    large_solo: bool = True, age_ms: float | None = 5.0):
     """The serving form: Poisson arrivals at rate_hz over the batch size mix
     plus 10% 2160x3840 images, admitted into servers with a device memory
     budget; each request gets 10 iterations and connectivity enforcement.
-    With split_mpix > 0 two servers share the GPU: requests of at most
-    split_mpix Mpix go to one on a high-priority stream, larger ones to one on
-    a low-priority stream, each driven by its own host thread (the library's
-    blocking calls release the interpreter lock), so long steps of large
-    images neither share a step with small requests nor hold up their
-    admission.  step_mpix > 0 sets each server's step budget (least remaining
-    work first).  Latency = delivery of its labels (host, pinned) - arrival.
+    With split_mpix > 0 two lanes share the GPU: requests of at most
+    split_mpix Mpix go to a continuous-batching server, larger ones (with
+    large_solo) are solved whole, one at a time, each as reload + graph-replayed
+    iterations + connectivity on a context of their own, or (without) go to a
+    second server.  Each lane has its own host thread (the library's blocking
+    calls release the interpreter lock) and stream; the small requests' stream
+    has the higher priority unless large_first (or equal_priority).  step_mpix
+    > 0 sets each server's step budget (least remaining work first).  Latency = delivery of its labels (host, pinned) - arrival.
     Compared with serial plain-FP32 solves of the same request stream (first
     come, first served, one at a time)."""
     import collections
@@ -501,7 +504,7 @@ def measure_serving(args, batch_imgs, n_requests: int = 2000, rate_hz: float = 5
     if split_mpix > 0:
         # bound, stream priority, pool share; with large_first the rare large
         # requests (which set the tail) get the high-priority stream
-        hi, lo = -5, 0
+        hi, lo = (0, 0) if equal_priority else (-5, 0)
         specs = [(split_mpix * 1e6, lo if large_first else hi, 0.25),
                  (float("inf"), hi if large_first else lo, 0.75)]
     else:
@@ -509,15 +512,39 @@ def measure_serving(args, batch_imgs, n_requests: int = 2000, rate_hz: float = 5
     lanes = []
     for bound, prio, share in specs:
         st = torch.cuda.Stream(priority=prio)
-        srv = scalp.Server(int(budget_gb * share * (1 << 30)), max_slots=1024, storage=storage, iters=iters,
-                           stream=st, step_pixels=int(step_mpix * 1e6))
+        budget = step_mpix if (bound != float("inf") or large_step_mpix is None) else large_step_mpix
+        if large_solo and bound == float("inf"):
+            srv = None  # whole solves one at a time (below)
+        else:
+            srv = scalp.Server(int(budget_gb * share * (1 << 30)), max_slots=1024, storage=storage,
+                               iters=iters, stream=st, step_pixels=int(budget * 1e6))
         lanes.append((bound, srv, st, collections.deque()))
+    # the solo lane: each large request is one whole solve (reload, graph-replayed
+    # iterations, connectivity) on its own stream, in arrival order; one
+    # context per distinct image size and K, made up front
+    # With age_ms, a large request that has waited longer than that runs on a
+    # high-priority stream of its own (aging), so a burst of large requests
+    # cannot be held back indefinitely by the small ones.
+    solo = {}
+    st_boost = torch.cuda.Stream(priority=-5) if (large_solo and age_ms is not None) else None
+    if large_solo:
+        st_solo = lanes[-1][2]
+        for st_k in [st_solo] + ([st_boost] if st_boost is not None else []):
+            with torch.cuda.stream(st_k):
+                for rgb, con, K in uhd:
+                    seg = scalp.Segmenter(rgb, con, K, storage=storage, stream=st_k)
+                    out = torch.empty((rgb.shape[0], rgb.shape[1]), dtype=torch.int32, pin_memory=True)
+                    seg.iterate(iters)
+                    seg.labels(enforce=True, out=out.numpy())
+                    solo[(rgb.data_ptr(), K, st_k is st_boost)] = (seg, out)
 
     def lane_of(i):
         return next(k for k, l in enumerate(lanes) if pix[i] <= l[0])
 
     # warm the pinned-memory cache and the kernels with a few requests per lane
     for k, (_, srv, _, _) in enumerate(lanes):
+        if srv is None:
+            continue
         mine = [i for i in range(n_requests) if lane_of(i) == k][:8]
         warm = {r[0] for r in (srv.submit(*reqs[i]) for i in mine) if r}
         while warm:
@@ -552,7 +579,27 @@ def measure_serving(args, batch_imgs, n_requests: int = 2000, rate_hz: float = 5
         except Exception as exc:  # reported after the join
             errors.append(exc)
 
-    threads = [threading.Thread(target=drive, args=(srv, q)) for _, srv, _, q in lanes]
+    def drive_solo(st, queue):
+        try:
+            torch.cuda.set_device(device)
+            while not (finished.is_set() and not queue):
+                if not queue:
+                    time.sleep(20e-6)
+                    continue
+                i = queue.popleft()
+                rgb, con, K = reqs[i]
+                boost = age_ms is not None and (time.perf_counter() - t0 - arrivals[i]) * 1e3 > age_ms
+                seg, out = solo[(rgb.data_ptr(), K, boost)]
+                with torch.cuda.stream(st_boost if boost else st):
+                    seg.reload(rgb, con)
+                    seg.iterate(iters)
+                    seg.labels(enforce=True, out=out.numpy())
+                lat[i] = time.perf_counter() - t0 - arrivals[i]
+        except Exception as exc:  # reported after the join
+            errors.append(exc)
+
+    threads = [threading.Thread(target=drive, args=(srv, q)) if srv is not None
+               else threading.Thread(target=drive_solo, args=(st, q)) for _, srv, st, q in lanes]
     for t in threads:
         t.start()
     for i in range(n_requests):  # dispatch at the arrival times
@@ -567,15 +614,23 @@ def measure_serving(args, batch_imgs, n_requests: int = 2000, rate_hz: float = 5
     if errors:
         raise errors[0]
     for _, srv, _, _ in lanes:
-        srv.close()
+        if srv is not None:
+            srv.close()
+    for seg, _ in solo.values():
+        seg.close()
     stream = lanes[0][2]
     tot = sum(pix) * iters / 1e6
     res = {
         "requests": n_requests, "rate_hz": rate_hz, "budget_gb": budget_gb, "storage": storage,
         "step": (f"least remaining work first, at most {step_mpix:g} Mpix per step" if step_mpix
                  else "every request in flight each step"),
-        "lanes": (f"requests <= {split_mpix:g} Mpix on one server, larger ones on another, one host thread "
-                  f"each; the {'larger' if large_first else 'smaller'} requests' stream has the higher priority"
+        "lanes": (("requests <= %g Mpix on a continuous-batching server, larger ones solved whole one at a "
+                   "time (graph-replayed iterations) on a %s-priority stream%s, one host thread each"
+                   % (split_mpix, "higher" if large_first else "lower",
+                      "" if age_ms is None else f"; a large request waiting over {age_ms:g} ms runs on a "
+                      "high-priority stream")) if (split_mpix and large_solo) else
+                  (f"requests <= {split_mpix:g} Mpix on one server, larger ones on another, one host thread "
+                   f"each; the {'larger' if large_first else 'smaller'} requests' stream has the higher priority")
                   if split_mpix else "one server"),
         "mix": "64 sizes of the batch mix + 10% 2160x3840", "iters": iters,
         "value": tot / wall, "unit": UNIT, "wall_s": wall,
@@ -1111,9 +1166,14 @@ def run_form(args):
     elif args.only_form == "serving":
         bws = synth.batch_configs()
         imgs = (bws, *synth.batch_images(bws))
-        res = {"large_first": measure_serving(args, imgs),
-               "small_first": measure_serving(args, imgs, large_first=False, serial=False),
-               "one_server": measure_serving(args, imgs, step_mpix=0.0, split_mpix=0.0, serial=False),
+        res = {"default": measure_serving(args, imgs),
+               "default_4000": measure_serving(args, imgs, n_requests=4000),
+               "no_aging": measure_serving(args, imgs, age_ms=None, serial=False),
+               "solo_equal_priority": measure_serving(args, imgs, equal_priority=True, age_ms=None, serial=False),
+               "two_servers_large_first": measure_serving(args, imgs, large_solo=False, large_first=True,
+                                                          age_ms=None, serial=False),
+               "one_server": measure_serving(args, imgs, step_mpix=0.0, split_mpix=0.0, large_solo=False,
+                                             age_ms=None, serial=False),
                "sweep": measure_serving_sweep(args, imgs)}
     elif args.only_form == "batched":
         bws = synth.batch_configs()
