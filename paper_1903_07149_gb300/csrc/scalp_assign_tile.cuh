@@ -24,6 +24,21 @@ __device__ __forceinline__ float2 lds_pair(uint32_t addr)
     return v;
 }
 
+// The same pair as the two floats' bits in one 64-bit word (d_c low).
+__device__ __forceinline__ unsigned long long lds_pair_bits(uint32_t addr)
+{
+    unsigned long long v;
+    asm volatile("ld.shared.b64 %0, [%1];" : "=l"(v) : "r"(addr));
+    return v;
+}
+
+// Both running sums of a walk advanced at once: (d_c, w) += pair, each half
+// an FP32 addition rounded to nearest (the same result as two scalar adds).
+__device__ __forceinline__ void add_pair(unsigned long long &acc, unsigned long long v)
+{
+    asm("add.rn.f32x2 %0, %0, %1;" : "+l"(acc) : "l"(v));
+}
+
 // Path sums of Eq. 1 and Eq. 2 over a distance map (row pitch `bw` pairs,
 // pair (0,0) = image pixel (bx0, by0)).  The same samples, in the same order
 // and with the same FP32 additions, as path_sums over the plane.
@@ -33,19 +48,14 @@ __device__ __forceinline__ int path_sums_map(uint32_t map, int bw, int bx0, int 
     int smaj, smin;
     path_strides(s, bw, smaj, smin);
     const uint32_t q0 = map + (uint32_t)(((s.ay - by0) * bw + (s.ax - bx0)) * 8);
-    float dc = 0.f, w = 0.f;
-    const auto visit = [&](uint32_t q) {
-        const float2 v = lds_pair(q);
-        dc += v.x;
-        w += v.y;
-    };
-    // the fixed-point form of the steps (fewer instructions per sample)
-    // covers every path of up to FIXED_STEP_MAX_NS steps
-    const int len = s.ns <= FIXED_STEP_MAX_NS
-                        ? walk_with<FixedPointStep>(q0, smaj * 8, smin * 8, s, visit)
-                        : walk_with<ErrorTermStep>(q0, smaj * 8, smin * 8, s, visit);
-    sum_dc = dc;
-    sum_w = w;
+    unsigned long long acc = 0;  // (+0.0f, +0.0f)
+    const auto visit = [&](uint32_t q) { add_pair(acc, lds_pair_bits(q)); };
+    // the fixed-point forms of the steps (fewer instructions per sample)
+    // cover every path of up to FIXED_STEP_MAX_NS steps
+    const int len = s.ns <= FIXED_STEP_MAX_NS ? walk_grouped<4>(q0, smaj * 8, smin * 8, s, visit)
+                                              : walk_with<ErrorTermStep>(q0, smaj * 8, smin * 8, s, visit);
+    sum_dc = __uint_as_float((unsigned)acc);
+    sum_w = __uint_as_float((unsigned)(acc >> 32));
     return len;
 }
 

@@ -331,6 +331,38 @@ __device__ __forceinline__ int walk_with(Addr q, int smaj, int smin, const PathS
     return s.ns + 1;
 }
 
+// The fixed-point rule in closed form: the carries after i steps are
+// m_i = floor((2^31 + i S) / 2^32), so sample i lies at q + i smaj + m_i smin.
+// The walk takes U samples at a time from the accumulator at the group's
+// start (m of sample k of the group = the high word of acc + k S, one wide
+// multiply-add each; the samples' addresses do not depend on one another) and
+// then moves the start and the accumulator on by U steps.  Same samples, in
+// the same order, as walk_with<FixedPointStep>; for ns <= FIXED_STEP_MAX_NS.
+template <int U, typename Addr, typename Visit>
+__device__ __forceinline__ int walk_grouped(Addr q, int smaj, int smin, const PathSetup &s, Visit &&visit)
+{
+    const uint32_t S = fixed_step_slope(s.dmin, s.ns);
+    uint32_t acc = 0x80000000u;
+    const int n = s.ns + 1;
+    const auto at = [&](int k) {
+        const uint32_t m = k == 0 ? 0u : (uint32_t)(((unsigned long long)S * (unsigned)k + acc) >> 32);
+        return q + (Addr)(k * smaj) + (Addr)((int)m * smin);
+    };
+    int i = 0;
+#pragma unroll 1
+    for (; i + U <= n; i += U) {
+#pragma unroll
+        for (int k = 0; k < U; ++k) visit(at(k));
+        const unsigned long long t = (unsigned long long)S * (unsigned)U + acc;
+        acc = (uint32_t)t;
+        q += (Addr)(U * smaj) + (Addr)((int)(t >> 32) * smin);
+    }
+#pragma unroll
+    for (int k = 0; k < U - 1; ++k)
+        if (i + k < n) visit(at(k));
+    return n;
+}
+
 template <typename Addr, typename Visit>
 __device__ __forceinline__ int walk_steps(Addr q, int smaj, int smin, const PathSetup &s,
                                           Visit &&visit)
@@ -359,9 +391,17 @@ __device__ __forceinline__ int walk_path(const T *__restrict__ base, int pitch, 
 
 // Squared CIELab distance d_c(q, C_k) of Eq. 1 between a sample and a
 // cluster colour, in one fixed FP32 order (every walker and map uses it).
+// The L and a differences are one packed FP32x2 subtraction (each half
+// rounded to nearest, as two scalar subtractions would be).
 __device__ __forceinline__ float colour_dist(float4 v, float cL, float ca, float cb)
 {
-    const float dl = v.x - cL, da = v.y - ca, db = v.z - cb;
+    unsigned long long xy, cxy, d;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(xy) : "f"(v.x), "f"(v.y));
+    asm("mov.b64 %0, {%1, %2};" : "=l"(cxy) : "f"(cL), "f"(ca));
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(xy), "l"(cxy));
+    float dl, da;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(dl), "=f"(da) : "l"(d));
+    const float db = v.z - cb;
     return fmaf(dl, dl, fmaf(da, da, db * db));
 }
 

@@ -509,8 +509,9 @@ void launch_lists(const SolveArgs &a, cudaStream_t st, bool pdl)
 // Debug: the path pixels exactly as the assignment kernel steps through them.
 // ---------------------------------------------------------------------------
 // One path per thread, pixels in walking order.  The error-term steps give
-// the pixels; paths short enough for the fixed-point form are walked with it
-// in lockstep, and a disagreement on any sample reports length -1.
+// the pixels; paths short enough for the fixed-point forms are walked with
+// the step form in lockstep and with the grouped closed form after it, and a
+// disagreement on any sample reports length -1.
 __global__ void k_debug_paths(const int *pairs, int M, int *out_xy, int stride_xy, int *out_len,
                               int W)
 {
@@ -536,6 +537,14 @@ __global__ void k_debug_paths(const int *pairs, int M, int *out_xy, int stride_x
         same = same && (!check || qf == qe);
         qe += e.next();
         if (check) qf += f.next();
+    }
+    if (check) {  // the grouped closed form, sample by sample against the error term
+        long long qg = start;
+        ErrorTermStep g(s, smaj, smin);
+        walk_grouped<4>(start, smaj, smin, s, [&](long long q) {
+            same = same && q == qg;
+            qg += g.next();
+        });
     }
     out_len[i] = same ? s.ns + 1 : -1;
 }
