@@ -48,7 +48,10 @@
 
 namespace scalp {
 
-size_t assign_smem_bytes(int map_cap) { return AssignSmem::maps + (size_t)map_cap * sizeof(float2); }
+size_t assign_smem_bytes(int map_cap)
+{
+    return tile_layout(MAX_TILE_CANDIDATES).maps + (size_t)map_cap * sizeof(float2);
+}
 
 // Map capacity (pairs) when ASSIGN_CTAS_PER_SM CTAs share an SM's shared memory.
 int assign_map_capacity(int device)
@@ -66,7 +69,7 @@ int assign_map_capacity(int device)
     long long per_cta = std::min((long long)per_cta_max,
                                  (long long)per_sm / ASSIGN_CTAS_PER_SM - reserved) - PERSIST_STATIC_SMEM;
     per_cta &= ~15LL;
-    const long long cap = (per_cta - (long long)AssignSmem::maps) / (long long)sizeof(float2);
+    const long long cap = (per_cta - (long long)tile_layout(MAX_TILE_CANDIDATES).maps) / (long long)sizeof(float2);
     return cap > 0 ? (int)cap : 0;
 }
 

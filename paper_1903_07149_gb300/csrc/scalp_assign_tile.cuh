@@ -60,51 +60,56 @@ __device__ __forceinline__ int path_sums_map(uint32_t map, int bw, int bx0, int 
 }
 
 // Shared-memory layout; every section starts on a 16-byte boundary (int4
-// loads and 8-byte atomics need it); the distance maps fill the rest.
-constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
-constexpr int STRIP = 4;  // items run along strips STRIP pixels wide
-constexpr int MAX_ITEMS = MAX_TILE_CANDIDATES * (TILE_PIXELS / 32);
-constexpr int STRIP_RCP_BITS = 20;
-// the strip index j / (STRIP * len) by a STRIP_RCP_BITS-bit reciprocal is exact
-// when the rounding error j / 2^STRIP_RCP_BITS stays below 1 / (STRIP * len)
-static_assert((long long)TILE_PIXELS * STRIP * (TILE_X > TILE_Y ? TILE_X : TILE_Y) <
-                  (1LL << STRIP_RCP_BITS),
-              "exact strip index");
-// Per candidate (rank c): three 16-byte records the walk reads,
-//   rec0 = (xa, ya, w | h << 8 | vert << 16, strip reciprocal)  its rectangle
-//   rec1 = (ex, ey, xk bits, yk bits)                           endpoint, X_k
-//   rec2 = (bx0, by0, pitch, map byte offset, or -1: walk the plane)
-// the map box for the build, box = (bx0, by0, pitch, 32-bit reciprocal of
-// the pitch), and the colour C_k, col = (l_k, a_k, b_k, 0).
+// loads and 8-byte atomics need it).  The fixed sections come first; the
+// per-candidate records follow, sized for the tile's own candidate count, and
+// the distance maps fill the rest (a tile with few candidates has more room).
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+// The tile's queue of pairs that survive the bound (slot << 10 | tile pixel).
+constexpr int TILE_QUEUE_ENTRIES = 1024;
 struct AssignSmem {
-    static constexpr size_t rec0 = 0;
-    static constexpr size_t rec1 = align16(rec0 + MAX_TILE_CANDIDATES * sizeof(int4));
-    static constexpr size_t rec2 = align16(rec1 + MAX_TILE_CANDIDATES * sizeof(int4));
-    static constexpr size_t box = align16(rec2 + MAX_TILE_CANDIDATES * sizeof(int4));
-    static constexpr size_t col = align16(box + MAX_TILE_CANDIDATES * sizeof(int4));
-    static constexpr size_t cid = align16(col + MAX_TILE_CANDIDATES * sizeof(float4));
-    static constexpr size_t nit = align16(cid + MAX_TILE_CANDIDATES * sizeof(int));
-    static constexpr size_t area = align16(nit + MAX_TILE_CANDIDATES * sizeof(int));
-    static constexpr size_t best = align16(area + MAX_TILE_CANDIDATES * sizeof(int));
-    static constexpr size_t first = align16(best + TILE_PIXELS * sizeof(unsigned long long));
-    static constexpr size_t mfirst = align16(first + (MAX_TILE_CANDIDATES + 1) * sizeof(int));
-    static constexpr size_t cfirst = align16(mfirst + (MAX_TILE_CANDIDATES + 1) * sizeof(int));
-    static constexpr size_t owner = align16(cfirst + (MAX_TILE_CANDIDATES + 1) * sizeof(int));
-    static constexpr size_t prev = align16(owner + MAX_ITEMS);
+    static constexpr size_t best = 0;
+    static constexpr size_t tileq = align16(best + TILE_PIXELS * sizeof(unsigned long long));
+    static constexpr size_t prev = align16(tileq + TILE_QUEUE_ENTRIES * sizeof(uint32_t));
     static constexpr size_t queue = align16(prev + TILE_PIXELS);
     static constexpr size_t misc = align16(queue + (ASSIGN_THREADS / 32) * 64 * sizeof(uint32_t));
-    static constexpr size_t maps = align16(misc + 64);
+    static constexpr size_t records = align16(misc + 64);
 };
-static_assert(AssignSmem::rec1 % 16 == 0 && AssignSmem::rec2 % 16 == 0 && AssignSmem::col % 16 == 0 &&
-                  AssignSmem::cid % 16 == 0 && AssignSmem::nit % 16 == 0 && AssignSmem::box % 16 == 0 &&
-                  AssignSmem::area % 16 == 0 && AssignSmem::best % 16 == 0 &&
-                  AssignSmem::first % 16 == 0 && AssignSmem::mfirst % 16 == 0 &&
-                  AssignSmem::cfirst % 16 == 0 &&
-                  AssignSmem::owner % 16 == 0 && AssignSmem::prev % 16 == 0 && AssignSmem::queue % 16 == 0 &&
-                  AssignSmem::misc % 16 == 0 &&
-                  AssignSmem::maps % 16 == 0,
+static_assert(AssignSmem::tileq % 16 == 0 && AssignSmem::prev % 16 == 0 && AssignSmem::queue % 16 == 0 &&
+                  AssignSmem::misc % 16 == 0 && AssignSmem::records % 16 == 0,
               "shared-memory sections aligned");
-static_assert(MAX_TILE_CANDIDATES <= 256, "item owners are bytes");
+// Per candidate (rank c): three 16-byte records the walk reads,
+//   rec0 = (xa, ya, w | h << 8, 0)                   its rectangle
+//   rec1 = (ex, ey, xk bits, yk bits)                endpoint, X_k
+//   rec2 = (bx0, by0, pitch, map byte offset, or -1: walk the plane)
+// the map box for the build, box = (bx0, by0, pitch, 32-bit reciprocal of
+// the pitch), the colour C_k, col = (l_k, a_k, b_k, 0), the cluster index
+// cid, the box area and the prefixes mfirst and cfirst of the map layout.
+struct TileLayout {
+    uint32_t rec0, rec1, rec2, box, col, cid, area, mfirst, cfirst, maps;
+};
+__host__ __device__ constexpr TileLayout tile_layout(int n)
+{
+    TileLayout t{};
+    t.rec0 = (uint32_t)AssignSmem::records;
+    t.rec1 = t.rec0 + (uint32_t)n * 16u;
+    t.rec2 = t.rec1 + (uint32_t)n * 16u;
+    t.box = t.rec2 + (uint32_t)n * 16u;
+    t.col = t.box + (uint32_t)n * 16u;
+    t.cid = t.col + (uint32_t)n * 16u;
+    t.area = (uint32_t)align16(t.cid + (size_t)n * 4);
+    t.mfirst = (uint32_t)align16(t.area + (size_t)n * 4);
+    t.cfirst = (uint32_t)align16(t.mfirst + (size_t)(n + 1) * 4);
+    t.maps = (uint32_t)align16(t.cfirst + (size_t)(n + 1) * 4);
+    return t;
+}
+// The map pairs a tile of n candidates has beyond the capacity sized for
+// MAX_TILE_CANDIDATES.
+__host__ __device__ constexpr int extra_map_pairs(int n)
+{
+    return (int)((tile_layout(MAX_TILE_CANDIDATES).maps - tile_layout(n).maps) / 8u);
+}
+static_assert(MAX_TILE_CANDIDATES < 255, "slots are bytes; 0xff is none");
+static_assert(TILE_PIXELS <= 1024 && MAX_TILE_CANDIDATES < (1 << 21), "queued pairs pack into 32 bits");
 static_assert(MAX_TILE_CANDIDATES % 32 == 0, "the scans give each lane whole candidates");
 
 // Rank of cluster k among the tile's candidates (cid sorted ascending), or -1.
@@ -134,37 +139,6 @@ __device__ __forceinline__ unsigned long long pack_best(float D, int slot)
 {
     // D >= 0, so its IEEE bits order like the value; ties fall to the slot
     return ((unsigned long long)__float_as_uint(D) << 32) | (unsigned)slot;
-}
-
-// Exclusive prefix of cnt <= MAX_TILE_CANDIDATES counts in(c) by one warp:
-// out[c] for c < cnt and the total in out[cnt].  Returns the largest prefix
-// end that stays <= cap (the leading candidates that fit a buffer of cap).
-template <typename In>
-__device__ __forceinline__ int warp_scan_counts(In in, int *out, int cnt, int cap, int lane)
-{
-    constexpr int PER = MAX_TILE_CANDIDATES / 32;
-    int v[PER], sum = 0;
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int c = lane * PER + i;
-        v[i] = c < cnt ? in(c) : 0;
-        sum += v[i];
-    }
-    int incl = sum;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    int run = incl - sum, fit = 0;
-#pragma unroll
-    for (int i = 0; i < PER; ++i) {
-        const int c = lane * PER + i;
-        if (c < cnt) out[c] = run;
-        run += v[i];
-        if (c < cnt && run <= cap) fit = run;
-    }
-    if (lane == 31) out[cnt] = incl;
-    return (int)__reduce_max_sync(0xffffffffu, (unsigned)fit);
 }
 
 // The map layout by one warp: mfirst = exclusive prefix of the box areas
@@ -217,16 +191,9 @@ __device__ __forceinline__ int warp_scan_maps(const int *area, int *mfirst, int 
     return (int)__reduce_max_sync(0xffffffffu, (unsigned)fit);
 }
 
-// Items: the pixels of a candidate's window that lie in the tile form a
-// rectangle.  When the rectangle lies mostly left or right of the path
-// endpoint (paths mostly along x, |P| set by the column) it is cut into
-// vertical strips STRIP columns wide, otherwise into horizontal strips STRIP
-// rows high.  The strips are read one after the other, each across its width
-// first, and every 32 consecutive pixels of that order form one warp's item.
-// So a warp's pixels lie in a few neighbouring columns (rows), where the path
-// lengths differ little, and only the last item of a rectangle has idle lanes.
 // One tile of one image (the body shared by the single-image and the batched
-// kernels).
+// kernels).  The pixels of a candidate's window that lie in the tile form a
+// rectangle; each warp owns 64 pixels of the tile (two blocks of 8 x 4).
 template <typename T>
 __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsigned char *smem)
 {
@@ -241,25 +208,13 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
     const int x0 = tx * TILE_X, y0 = ty * TILE_Y;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
-    int4 *rec0 = reinterpret_cast<int4 *>(smem + AssignSmem::rec0);
-    int4 *rec1 = reinterpret_cast<int4 *>(smem + AssignSmem::rec1);
-    int4 *rec2 = reinterpret_cast<int4 *>(smem + AssignSmem::rec2);
-    int4 *box = reinterpret_cast<int4 *>(smem + AssignSmem::box);
-    float4 *col = reinterpret_cast<float4 *>(smem + AssignSmem::col);
-    int *cid = reinterpret_cast<int *>(smem + AssignSmem::cid);
-    int *nit = reinterpret_cast<int *>(smem + AssignSmem::nit);
-    int *area = reinterpret_cast<int *>(smem + AssignSmem::area);
     unsigned long long *best = reinterpret_cast<unsigned long long *>(smem + AssignSmem::best);
-    int *first = reinterpret_cast<int *>(smem + AssignSmem::first);
-    int *mfirst = reinterpret_cast<int *>(smem + AssignSmem::mfirst);
-    int *cfirst = reinterpret_cast<int *>(smem + AssignSmem::cfirst);
-    unsigned char *owner = smem + AssignSmem::owner;
+    uint32_t *tileq = reinterpret_cast<uint32_t *>(smem + AssignSmem::tileq);
     unsigned char *prev_slot = smem + AssignSmem::prev;
     int *misc = reinterpret_cast<int *>(smem + AssignSmem::misc);
-    float2 *maps = reinterpret_cast<float2 *>(smem + AssignSmem::maps);
-    const uint32_t maps_u32 = smem_u32(maps);
 
-    // this thread's pixels: block (warp + j*WARPS) of the tile, lane within it
+    // this thread's pixels: block (warp * PIX_PER_THREAD + j) of the tile
+    // (a warp's blocks lie side by side), lane within it
     auto my_pixel = [&](int j, int &qx, int &qy) {
         const int blk = warp + j * WARPS;
         qx = x0 + (blk % (TILE_X / WARP_BLOCK_X)) * WARP_BLOCK_X + (lane % WARP_BLOCK_X);
@@ -271,6 +226,20 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
     // device-side overflow check (reported as an error) ever fired
     const int cnt = (int)max(0LL, min((long long)a.tile_off[tile + 1], a.tile_cap) - off);
     const bool fast = cnt <= MAX_TILE_CANDIDATES;
+    // the records for this tile's candidates, then its maps
+    const TileLayout lay = tile_layout(fast ? cnt : 0);
+    int4 *rec0 = reinterpret_cast<int4 *>(smem + lay.rec0);
+    int4 *rec1 = reinterpret_cast<int4 *>(smem + lay.rec1);
+    int4 *rec2 = reinterpret_cast<int4 *>(smem + lay.rec2);
+    int4 *box = reinterpret_cast<int4 *>(smem + lay.box);
+    float4 *col = reinterpret_cast<float4 *>(smem + lay.col);
+    int *cid = reinterpret_cast<int *>(smem + lay.cid);
+    int *area = reinterpret_cast<int *>(smem + lay.area);
+    int *mfirst = reinterpret_cast<int *>(smem + lay.mfirst);
+    int *cfirst = reinterpret_cast<int *>(smem + lay.cfirst);
+    const uint32_t maps_u32 = smem_u32(smem + lay.maps);
+    float2 *maps = reinterpret_cast<float2 *>(smem + lay.maps);
+    const int map_cap = a.map_cap > 0 ? a.map_cap + extra_map_pairs(fast ? cnt : 0) : 0;
     if (tid == 0) {  // this tile's list is read: ready the counts for the next update
         a.tile_count[tile] = 0;
         a.tile_cursor[tile] = 0;
@@ -298,7 +267,8 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
         cd = a.cdev[myid];
     }
     if (tid == 0) {
-        misc[1] = 0;  // work counter
+        misc[1] = 0;  // batches of the tile queue taken
+        misc[6] = 0;  // tile queue entries reserved
         misc[4] = 0;  // path samples and pairs (counting on)
         misc[5] = 0;
     }
@@ -307,17 +277,13 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
         int rank = 0;
         for (int j = 0; j < cnt; ++j) rank += ids[j] < myid;
         cid[rank] = myid;
-        // window x tile (clipped to the image), cut into strips
+        // window x tile (clipped to the image)
         const int xa = max(cd.xlo, x0), xb = min(min(cd.xhi, x0 + TILE_X - 1), a.W - 1);
         const int ya = max(cd.ylo, y0), yb = min(min(cd.yhi, y0 + TILE_Y - 1), a.H - 1);
         const int w = max(xb - xa + 1, 0), h = max(yb - ya + 1, 0);
-        const bool vert = abs(xa + xb - 2 * cd.ex) >= abs(ya + yb - 2 * cd.ey);
-        const int slen = max(vert ? h : w, 1);  // pixels along one strip
-        rec0[rank] = make_int4(xa, ya, w | (h << 8) | ((int)vert << 16),
-                               ((1 << STRIP_RCP_BITS) + STRIP * slen - 1) / (STRIP * slen));
+        rec0[rank] = make_int4(xa, ya, w | (h << 8), 0);
         rec1[rank] = make_int4(cd.ex, cd.ey, __float_as_int(cd.xk), __float_as_int(cd.yk));
         col[rank] = make_float4(cd.L, cd.a, cd.b, 0.f);
-        nit[rank] = (w * h + 31) >> 5;
         // map box: the rectangle and the endpoint (both inside the image).
         // Rows are padded to a pitch = 4 (mod 8) pairs: the walks of a warp
         // then spread over the shared-memory banks (neighbouring rows start
@@ -337,13 +303,12 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
         box[rank] = make_int4(bx0, by0, pitch, (int)rcp);
         // a box larger than the whole buffer never fits: clamp it so that the
         // prefix sums stay small
-        area[rank] = a.map_cap > 0 ? (int)min(n, (long long)a.map_cap + 1) : 0;
+        area[rank] = map_cap > 0 ? (int)min(n, (long long)map_cap + 1) : 0;
     }
     __syncthreads();
     for (int i = tid; i < TILE_PIXELS; i += THREADS) best[i] = ~0ull;
-    if (warp == 0 && fast) warp_scan_counts([&](int c) { return nit[c]; }, first, cnt, INT_MAX, lane);
-    if (warp == 1 && fast) {
-        const int used = warp_scan_maps<BUILD_CHUNK>(area, mfirst, cfirst, cnt, a.map_cap, lane);
+    if (warp == 0 && fast) {
+        const int used = warp_scan_maps<BUILD_CHUNK>(area, mfirst, cfirst, cnt, map_cap, lane);
         if (lane == 0) misc[2] = used;
     }
     __syncthreads();
@@ -372,8 +337,6 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
     const int used = fast ? misc[2] : 0;
     if (fast) {
         if (tid < cnt) {
-            const int f = first[tid], n = nit[tid];
-            for (int j = 0; j < n; ++j) owner[f + j] = (unsigned char)tid;
             const int4 b = box[tid];
             const bool mapped = area[tid] > 0 && mfirst[tid + 1] <= used;
             rec2[tid] = make_int4(b.x, b.y, b.z, mapped ? mfirst[tid] * (int)sizeof(float2) : -1);
@@ -461,11 +424,12 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
     if (fast) {
         // Pass 1: each pixel's previous label first, when it is a candidate
         // of the pixel (it usually wins again).  Its D bounds the minimum, so
-        // pass 2 can skip every candidate whose lower bound exceeds the
-        // pixel's best D so far: such a candidate's D is larger than the
-        // minimum and cannot win or tie.  The argmin is unchanged.  A warp
-        // goes on to pass 2 when its own pixels are done (a pixel whose pass 1
-        // is still running elsewhere is simply not pruned yet).
+        // pass 2 can skip every candidate whose lower bound exceeds it: such
+        // a candidate's D is larger than the minimum and cannot win or tie.
+        // The argmin is unchanged.  Each warp walks its own pixels here.
+        float dprev[PIX_PER_THREAD];  // D of the previous label; NaN: none
+#pragma unroll
+        for (int j = 0; j < PIX_PER_THREAD; ++j) dprev[j] = __int_as_float(0x7fffffff);
 #pragma unroll 1
         for (int j = 0; j < PIX_PER_THREAD; ++j) {
             int px, py;
@@ -478,18 +442,19 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
                 const float D = pair_distance(px, py, c, r1, r2, own_distance(px, py, c, r2), spatial(px, py, r1),
                                               &len);
                 atomicMin(&best[pix], pack_best(D, c));
+#pragma unroll
+                for (int i = 0; i < PIX_PER_THREAD; ++i)  // (registers: constant indices)
+                    if (i == j) dprev[i] = D;
                 count_pair(len);
             }
         }
 
-        // Pass 2: the candidates' rectangles, cut into items.  A lane whose
-        // pair survives the bound queues it in its warp's queue in shared
-        // memory; each time 32 pairs are queued the warp walks them, one per
-        // lane, so the walks run on full warps however many pairs the bound
-        // removed from an item.  A queued pair is (slot << 10 | tile pixel).
-        uint32_t *wq = reinterpret_cast<uint32_t *>(smem + AssignSmem::queue) + warp * 64;
-        const unsigned lanes_below = (1u << lane) - 1u;
-        auto walk_queued = [&](uint32_t e) {
+        // Pass 2, bound: each warp checks its own pixels against every other
+        // candidate whose rectangle holds them.  A surviving pair goes to the
+        // warp's queue (slot << 10 | tile pixel); each 32 queued pairs move
+        // on as one batch to the tile queue, or are walked at once when the
+        // tile queue is full.
+        const auto walk_queued = [&](uint32_t e) {
             const int pix = (int)(e & 1023u), c = (int)(e >> 10);
             const int qx = x0 + (pix & (TILE_X - 1)), qy = y0 + (pix / TILE_X);
             const int4 r1 = rec1[c], r2 = rec2[c];
@@ -498,55 +463,76 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
             atomicMin(&best[pix], pack_best(D, c));
             count_pair(len);
         };
+        uint32_t *wq = reinterpret_cast<uint32_t *>(smem + AssignSmem::queue) + warp * 64;
+        const unsigned lanes_below = (1u << lane) - 1u;
         int queued = 0;  // warp-uniform
-        const int n_items = first[cnt];
-        while (true) {
-            int item = 0;
-            if (lane == 0) item = atomicAdd(&misc[1], 1);
-            item = __shfl_sync(0xffffffffu, item, 0);
-            if (item >= n_items) break;
-            const int c = owner[item];
+        // the n <= 32 pairs at the head of the warp queue, appended to the
+        // tile queue (the part past its end is walked at once): the queue's
+        // entries [0, min(reserved, capacity)) are all written
+        const auto hand_off = [&](int n) {
+            int at = 0;
+            if (lane == 0) at = atomicAdd(&misc[6], n);
+            at = __shfl_sync(0xffffffffu, at, 0);
+            if (lane < n) {
+                const uint32_t e = wq[lane];
+                if (at + lane < TILE_QUEUE_ENTRIES) tileq[at + lane] = e;
+                else walk_queued(e);
+            }
+        };
+        for (int c = 0; c < cnt; ++c) {
             const int4 r0 = rec0[c];
-            const int rw = r0.z & 0xff, rh = (r0.z >> 8) & 0xff;
-            const int j = ((item - first[c]) << 5) + lane;  // pixel of the rectangle
-            bool keep = false;
-            int pix = 0;
-            if (j < rw * rh) {
-                const bool vert = (r0.z >> 16) != 0;
-                const int slen = vert ? rh : rw, across = vert ? rw : rh;
-                const int strip = (j * r0.w) >> STRIP_RCP_BITS;
-                const int t = j - strip * STRIP * slen;
-                // t / width for a strip 1..4 wide: exact 16-bit reciprocals
-                const int width = min(STRIP, across - strip * STRIP);
-                const int along = (t * (width == 3 ? 21846 : 65536 >> (width >> 1))) >> 16;
-                const int offs = strip * STRIP + (t - along * width);
-                const int qx = r0.x + (vert ? offs : along);
-                const int qy = r0.y + (vert ? along : offs);
-                pix = (qy - y0) * TILE_X + (qx - x0);
-                if (prev_slot[pix] != c) {  // else evaluated in pass 1
-                    const int4 r1 = rec1[c];
-                    const float dcp = own_distance(qx, qy, c, rec2[c]);
-                    // best holds (D bits, slot); all ones (a NaN) until a D arrives
-                    const float dbest = __uint_as_float((unsigned)(best[pix] >> 32));
-                    keep = !a.prune || !(distance_lower_bound(dcp, a.lam, a.ms2, spatial(qx, qy, r1)) > dbest);
+            const unsigned rw = (unsigned)(r0.z & 0xff), rh = (unsigned)((r0.z >> 8) & 0xff);
+            bool in[PIX_PER_THREAD];
+            bool any = false;
+#pragma unroll
+            for (int j = 0; j < PIX_PER_THREAD; ++j) {
+                int px, py;
+                my_pixel(j, px, py);
+                // (a pixel of the rectangle lies in the image)
+                in[j] = (unsigned)(px - r0.x) < rw && (unsigned)(py - r0.y) < rh &&
+                        prev_slot[(py - y0) * TILE_X + (px - x0)] != c;
+                any = any || in[j];
+            }
+            if (!__any_sync(0xffffffffu, any)) continue;
+            const int4 r1 = rec1[c], r2 = rec2[c];
+#pragma unroll
+            for (int j = 0; j < PIX_PER_THREAD; ++j) {
+                int px, py;
+                my_pixel(j, px, py);
+                bool keep = false;
+                if (in[j]) {
+                    const float dcp = own_distance(px, py, c, r2);
+                    keep = !a.prune || !(distance_lower_bound(dcp, a.lam, a.ms2, spatial(px, py, r1)) > dprev[j]);
                     // a pair that cannot win is not walked (counted as the method's work)
-                    if (!keep) count_pair(max(abs(qx - r1.x), abs(qy - r1.y)) + 1);
+                    if (!keep) count_pair(max(abs(px - r1.x), abs(py - r1.y)) + 1);
+                }
+                const unsigned kept = __ballot_sync(0xffffffffu, keep);
+                if (keep)
+                    wq[queued + __popc(kept & lanes_below)] =
+                        ((uint32_t)c << 10) | (uint32_t)((py - y0) * TILE_X + (px - x0));
+                queued += __popc(kept);
+                __syncwarp();
+                if (queued >= 32) {
+                    hand_off(32);
+                    __syncwarp();
+                    if (lane < queued - 32) wq[lane] = wq[32 + lane];
+                    queued -= 32;
+                    __syncwarp();
                 }
             }
-            const unsigned kept = __ballot_sync(0xffffffffu, keep);
-            if (keep) wq[queued + __popc(kept & lanes_below)] = ((uint32_t)c << 10) | (uint32_t)pix;
-            queued += __popc(kept);
-            __syncwarp();
-            if (queued >= 32) {
-                const uint32_t e = wq[lane];
-                __syncwarp();
-                if (lane < queued - 32) wq[lane] = wq[32 + lane];
-                queued -= 32;
-                __syncwarp();
-                walk_queued(e);
-            }
         }
-        if (lane < queued) walk_queued(wq[lane]);
+        if (queued > 0) hand_off(queued);
+        __syncthreads();
+
+        // Pass 2, walks: the warps take the tile queue 32 entries at a time
+        const int total = min(misc[6], TILE_QUEUE_ENTRIES);
+        while (true) {
+            int b = 0;
+            if (lane == 0) b = atomicAdd(&misc[1], 32);
+            b = __shfl_sync(0xffffffffu, b, 0);
+            if (b >= total) break;
+            if (b + lane < total) walk_queued(tileq[b + lane]);
+        }
     } else {
         // per-pixel path: every candidate straight from the global list
 #pragma unroll 1
@@ -626,7 +612,7 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
         if (tid == 0) {
             unsigned long long on_map = 0, on_plane = 0;
             for (int c = 0; c < cnt; ++c) {
-                if (fast && nit[c] == 0) continue;
+                if (fast && (rec0[c].z & 0xff) * ((rec0[c].z >> 8) & 0xff) == 0) continue;  // no pixel
                 if (fast && rec2[c].w >= 0) ++on_map;
                 else ++on_plane;
             }
