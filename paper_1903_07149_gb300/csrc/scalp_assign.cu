@@ -21,19 +21,17 @@
 //   3. Pass 1: each warp evaluates its own 64 pixels' previous labels (when
 //      they are candidates of the pixel); the previous label usually wins
 //      again, and its D stays in the thread's registers.
-//   4. Pass 2, bound: each warp checks its pixels against the other
-//      candidates whose rectangle (the tile's pixels inside the window) holds
-//      them.  A pair whose lower bound fl(fl(lam*d_c(p)) + fl(m^2/r^2*d_s))
-//      exceeds the pixel's pass-1 D cannot win or tie (its computed D is never
-//      below the bound) and is not walked; the others are queued per warp and
-//      handed on, 32 at a time, to a tile-wide queue in shared memory.
-//   5. Pass 2, walks: after a barrier all warps take the tile queue 32 pairs
-//      at a time.  Each walk follows the pixel's path to the candidate's
-//      endpoint (one 8-byte map load and one packed two-float add per
-//      sample), forms D (Eq. 1-3) and takes a 64-bit shared-memory atomicMin
-//      of (D bits, candidate slot) for its pixel; slots are in cluster order,
-//      so ties go to the smallest k.  The argmin is that of evaluating every
-//      pair.
+//   4. Pass 2: each warp checks its pixels against the other candidates
+//      whose rectangle (the tile's pixels inside the window) holds them.  A
+//      pair whose lower bound fl(fl(lam*d_c(p)) + fl(m^2/r^2*d_s)) exceeds
+//      the pixel's pass-1 D cannot win or tie (its computed D is never below
+//      the bound) and is not walked; the others are queued per warp and
+//      walked 32 at a time by that warp.
+//   5. Each walk follows the pixel's path to the candidate's endpoint (one
+//      8-byte map load and one packed two-float add per sample), forms D
+//      (Eq. 1-3) and takes a 64-bit shared-memory atomicMin of (D bits,
+//      candidate slot) for its pixel; slots are in cluster order, so ties go
+//      to the smallest k.  The argmin is that of evaluating every pair.
 //   6. Each thread writes its pixels' labels; warp-aggregated integer sums of
 //      (1, x, y, L, a, b) per label go to the global cluster sums as
 //      fire-and-forget reductions.

@@ -64,17 +64,14 @@ __device__ __forceinline__ int path_sums_map(uint32_t map, int bw, int bx0, int 
 // per-candidate records follow, sized for the tile's own candidate count, and
 // the distance maps fill the rest (a tile with few candidates has more room).
 __host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
-// The tile's queue of pairs that survive the bound (slot << 10 | tile pixel).
-constexpr int TILE_QUEUE_ENTRIES = 1024;
 struct AssignSmem {
     static constexpr size_t best = 0;
-    static constexpr size_t tileq = align16(best + TILE_PIXELS * sizeof(unsigned long long));
-    static constexpr size_t prev = align16(tileq + TILE_QUEUE_ENTRIES * sizeof(uint32_t));
+    static constexpr size_t prev = align16(best + TILE_PIXELS * sizeof(unsigned long long));
     static constexpr size_t queue = align16(prev + TILE_PIXELS);
     static constexpr size_t misc = align16(queue + (ASSIGN_THREADS / 32) * 64 * sizeof(uint32_t));
     static constexpr size_t records = align16(misc + 64);
 };
-static_assert(AssignSmem::tileq % 16 == 0 && AssignSmem::prev % 16 == 0 && AssignSmem::queue % 16 == 0 &&
+static_assert(AssignSmem::prev % 16 == 0 && AssignSmem::queue % 16 == 0 &&
                   AssignSmem::misc % 16 == 0 && AssignSmem::records % 16 == 0,
               "shared-memory sections aligned");
 // Per candidate (rank c): three 16-byte records the walk reads,
@@ -209,7 +206,6 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
 
     unsigned long long *best = reinterpret_cast<unsigned long long *>(smem + AssignSmem::best);
-    uint32_t *tileq = reinterpret_cast<uint32_t *>(smem + AssignSmem::tileq);
     unsigned char *prev_slot = smem + AssignSmem::prev;
     int *misc = reinterpret_cast<int *>(smem + AssignSmem::misc);
 
@@ -267,8 +263,6 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
         cd = a.cdev[myid];
     }
     if (tid == 0) {
-        misc[1] = 0;  // batches of the tile queue taken
-        misc[6] = 0;  // tile queue entries reserved
         misc[4] = 0;  // path samples and pairs (counting on)
         misc[5] = 0;
     }
@@ -449,11 +443,12 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
             }
         }
 
-        // Pass 2, bound: each warp checks its own pixels against every other
+        // Pass 2: each warp checks its own pixels against every other
         // candidate whose rectangle holds them.  A surviving pair goes to the
-        // warp's queue (slot << 10 | tile pixel); each 32 queued pairs move
-        // on as one batch to the tile queue, or are walked at once when the
-        // tile queue is full.
+        // warp's queue (slot << 10 | tile pixel); each time 32 are queued the
+        // warp walks them, one per lane, and the last few at the end.  (A
+        // barrier before the walks, to share them among the warps, cost more
+        // than the uneven loads it evens out.)
         const auto walk_queued = [&](uint32_t e) {
             const int pix = (int)(e & 1023u), c = (int)(e >> 10);
             const int qx = x0 + (pix & (TILE_X - 1)), qy = y0 + (pix / TILE_X);
@@ -466,19 +461,6 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
         uint32_t *wq = reinterpret_cast<uint32_t *>(smem + AssignSmem::queue) + warp * 64;
         const unsigned lanes_below = (1u << lane) - 1u;
         int queued = 0;  // warp-uniform
-        // the n <= 32 pairs at the head of the warp queue, appended to the
-        // tile queue (the part past its end is walked at once): the queue's
-        // entries [0, min(reserved, capacity)) are all written
-        const auto hand_off = [&](int n) {
-            int at = 0;
-            if (lane == 0) at = atomicAdd(&misc[6], n);
-            at = __shfl_sync(0xffffffffu, at, 0);
-            if (lane < n) {
-                const uint32_t e = wq[lane];
-                if (at + lane < TILE_QUEUE_ENTRIES) tileq[at + lane] = e;
-                else walk_queued(e);
-            }
-        };
         for (int c = 0; c < cnt; ++c) {
             const int4 r0 = rec0[c];
             const unsigned rw = (unsigned)(r0.z & 0xff), rh = (unsigned)((r0.z >> 8) & 0xff);
@@ -513,26 +495,16 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
                 queued += __popc(kept);
                 __syncwarp();
                 if (queued >= 32) {
-                    hand_off(32);
+                    const uint32_t e = wq[lane];
                     __syncwarp();
                     if (lane < queued - 32) wq[lane] = wq[32 + lane];
                     queued -= 32;
                     __syncwarp();
+                    walk_queued(e);
                 }
             }
         }
-        if (queued > 0) hand_off(queued);
-        __syncthreads();
-
-        // Pass 2, walks: the warps take the tile queue 32 entries at a time
-        const int total = min(misc[6], TILE_QUEUE_ENTRIES);
-        while (true) {
-            int b = 0;
-            if (lane == 0) b = atomicAdd(&misc[1], 32);
-            b = __shfl_sync(0xffffffffu, b, 0);
-            if (b >= total) break;
-            if (b + lane < total) walk_queued(tileq[b + lane]);
-        }
+        if (lane < queued) walk_queued(wq[lane]);
     } else {
         // per-pixel path: every candidate straight from the global list
 #pragma unroll 1
