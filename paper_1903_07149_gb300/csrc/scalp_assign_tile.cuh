@@ -536,7 +536,9 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
             }
         }
     }
-    __syncthreads();
+    // a warp's pixels were walked by that warp alone (both passes, or the
+    // per-pixel path), so its lanes' writes to them need only a warp barrier
+    __syncwarp();
 
     // labels and the warp-aggregated integer sums of the update; the
     // pixels' own samples are all requested first
@@ -575,7 +577,7 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
         warp_aggregate_global(valid, lab, x0, y0, px - x0, py - y0, own, a.acc);
     }
     if (a.count_samples) {
-        // (the walks ended before the barrier above the labels)
+        __syncthreads();  // every warp's counts are in (a CTA-uniform branch)
         if (tid == 0) {
             atomicAdd(&a.ctr->samples, (unsigned long long)tile_samples[0]);
             atomicAdd(&a.ctr->pairs, (unsigned long long)tile_samples[1]);
