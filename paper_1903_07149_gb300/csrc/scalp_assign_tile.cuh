@@ -244,9 +244,6 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
         if (tile == 0) a.ctr->nproj = 0;
     }
 
-    // candidates sorted by cluster index (ranks of distinct ids); the id
-    // staging reuses the `best` words before they are initialised
-    int *ids = reinterpret_cast<int *>(best);
     // this thread's pixels' previous labels (their loads overlap the set-up)
     int prev_lab[PIX_PER_THREAD];
 #pragma unroll
@@ -255,22 +252,13 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
         my_pixel(j, px, py);
         prev_lab[j] = fast && px < a.W && py < a.H ? a.labels[(long long)py * a.W + px] : -1;
     }
-    int myid = INT_MAX;
-    ClusterDev cd;  // this thread's candidate: its load overlaps the barrier
-    if (fast && tid < cnt) {
-        myid = a.tile_list[off + tid];
-        ids[tid] = myid;
-        cd = a.cdev[myid];
-    }
     if (tid == 0) {
         misc[4] = 0;  // path samples and pairs (counting on)
         misc[5] = 0;
     }
-    __syncthreads();
-    if (fast && tid < cnt) {
-        int rank = 0;
-        for (int j = 0; j < cnt; ++j) rank += ids[j] < myid;
-        cid[rank] = myid;
+    // the records of candidate id (rank among the tile's sorted ids)
+    const auto write_records = [&](int rank, int id, const ClusterDev &cd) {
+        cid[rank] = id;
         // window x tile (clipped to the image)
         const int xa = max(cd.xlo, x0), xb = min(min(cd.xhi, x0 + TILE_X - 1), a.W - 1);
         const int ya = max(cd.ylo, y0), yb = min(min(cd.yhi, y0 + TILE_Y - 1), a.H - 1);
@@ -298,12 +286,53 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
         // a box larger than the whole buffer never fits: clamp it so that the
         // prefix sums stay small
         area[rank] = map_cap > 0 ? (int)min(n, (long long)map_cap + 1) : 0;
-    }
-    __syncthreads();
-    for (int i = tid; i < TILE_PIXELS; i += THREADS) best[i] = ~0ull;
-    if (warp == 0 && fast) {
-        const int used = warp_scan_maps<BUILD_CHUNK>(area, mfirst, cfirst, cnt, map_cap, lane);
-        if (lane == 0) misc[2] = used;
+    };
+    // the candidates sorted by cluster index (ranks of distinct ids), their
+    // records and the map layout; each warp readies its own pixels' best words
+    if (fast && cnt <= 32) {
+        // one warp: ranks by shuffles, no block barrier until the layout is done
+        if (warp == 0) {
+            int myid = INT_MAX;
+            ClusterDev cd;
+            if (lane < cnt) {
+                myid = a.tile_list[off + lane];
+                cd = a.cdev[myid];
+            }
+            int rank = 0;
+            for (int j = 0; j < 32; ++j) rank += __shfl_sync(0xffffffffu, myid, j) < myid;
+            if (lane < cnt) write_records(rank, myid, cd);
+            __syncwarp();
+            const int used = warp_scan_maps<BUILD_CHUNK>(area, mfirst, cfirst, cnt, map_cap, lane);
+            if (lane == 0) misc[2] = used;
+        }
+#pragma unroll
+        for (int j = 0; j < PIX_PER_THREAD; ++j) {
+            int px, py;
+            my_pixel(j, px, py);
+            best[(py - y0) * TILE_X + (px - x0)] = ~0ull;
+        }
+    } else {
+        // the id staging reuses the `best` words before they are initialised
+        int *ids = reinterpret_cast<int *>(best);
+        int myid = INT_MAX;
+        ClusterDev cd;  // this thread's candidate: its load overlaps the barrier
+        if (fast && tid < cnt) {
+            myid = a.tile_list[off + tid];
+            ids[tid] = myid;
+            cd = a.cdev[myid];
+        }
+        __syncthreads();
+        if (fast && tid < cnt) {
+            int rank = 0;
+            for (int j = 0; j < cnt; ++j) rank += ids[j] < myid;
+            write_records(rank, myid, cd);
+        }
+        __syncthreads();
+        for (int i = tid; i < TILE_PIXELS; i += THREADS) best[i] = ~0ull;
+        if (warp == 0 && fast) {
+            const int used = warp_scan_maps<BUILD_CHUNK>(area, mfirst, cfirst, cnt, map_cap, lane);
+            if (lane == 0) misc[2] = used;
+        }
     }
     __syncthreads();
 
