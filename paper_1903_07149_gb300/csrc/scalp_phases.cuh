@@ -263,37 +263,44 @@ __device__ __forceinline__ void project_cta(const SolveArgs &a, int whole_image,
 // orphan count and the assignment the projection queue.
 // ---------------------------------------------------------------------------
 // Exclusive scan of in[0, n) into out[0, n] (out[n] = total) by one CTA of
-// `threads` threads, each a contiguous chunk; s_warp holds 32 ints.
+// `threads` threads (a multiple of 32, at most 1024).  Each warp scans a
+// contiguous segment 32 consecutive entries at a time (coalesced loads,
+// conflict-free stores), carrying its running sum; the warps' totals are
+// then scanned and each warp adds its offset.  s_warp holds 32 ints.
 __device__ __forceinline__ void cta_scan(const int *in, int *out, int n, int threads, int *s_warp)
 {
-    const int per = (n + threads - 1) / threads;
-    const int b = threadIdx.x * per, e = min(n, b + per);
-    int tsum = 0;
-    for (int i = b; i < e; ++i) tsum += in[i];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int incl = tsum;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) s_warp[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-        int w = lane < threads / 32 ? s_warp[lane] : 0;
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = threads / 32;
+    const int seg = (n + nw - 1) / nw;
+    const int b = min(n, wid * seg), e = min(n, b + seg);
+    int carry = 0;
+#pragma unroll 4
+    for (int base = b; base < e; base += 32) {
+        const int i = base + lane;
+        const int v = i < e ? in[i] : 0;
+        int incl = v;
         for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, w, o);
+            const int t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (i < e) out[i] = carry + incl - v;
+        carry += __shfl_sync(FULL, incl, 31);
+    }
+    if (lane == 0) s_warp[wid] = carry;
+    __syncthreads();
+    if (wid == 0) {  // inclusive scan of the warp totals
+        int w = lane < nw ? s_warp[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, w, o);
             if (lane >= o) w += t;
         }
         s_warp[lane] = w;
     }
     __syncthreads();
-    int run = (wid ? s_warp[wid - 1] : 0) + incl - tsum;
-    for (int i = b; i < e; ++i) {
-        const int v = in[i];
-        out[i] = run;
-        run += v;
-    }
-    if (threadIdx.x == threads - 1) out[n] = s_warp[31];
+    const int off = wid ? s_warp[wid - 1] : 0;
+    if (off)
+        for (int i = b + lane; i < e; i += 32) out[i] += off;  // (each entry its own lane's)
+    if (threadIdx.x == 0) out[n] = s_warp[31];
     __syncthreads();
 }
 
