@@ -357,7 +357,10 @@ void enqueue_iteration(scalp_ctx *c, int slot, bool capturing)
     launch_assign(c->a, c->p.storage, c->smem, c->st, pdl);
     if (c->profiling) cudaEventRecordWithFlags(c->ev_pool[2 * slot + 1], c->st, flags);
     launch_update(c->a, 1, c->st, pdl);
-    if (capturing && c->side) {
+    if (project_lists_fused(c->a)) {
+        // the projection and the candidate lists in one launch
+        launch_project_lists(c->a, c->st, pdl);
+    } else if (capturing && c->side) {
         // the candidate lists need only the windows the update wrote, not the
         // projected endpoints: a second branch of the graph runs them beside
         // the projection, and the next assignment waits for both

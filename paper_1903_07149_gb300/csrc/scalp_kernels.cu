@@ -428,19 +428,16 @@ __global__ void __launch_bounds__(SCAN1_THREADS) k_scan_tiles_batch(BatchArgs b)
 constexpr int LISTS_THREADS = 256;
 constexpr int LISTS_MAX_TILES = 12287;  // (n + 1) ints of shared memory <= 48 KB
 
-__global__ void __launch_bounds__(LISTS_THREADS) k_lists(SolveArgs a)
+// The scan and fill by CTA blk of nblk (blockDim.x threads); s_off holds
+// n + 1 ints of dynamic shared memory.
+__device__ __forceinline__ void lists_cta(const SolveArgs &a, int blk, int nblk, int *s_off, int *s_warp)
 {
-    pdl_wait();
-    pdl_release();
-    extern __shared__ int s_off[];
-    __shared__ int s_warp[32];
     const int n = a.n_tx * a.n_ty;
-    cta_scan(a.tile_count, s_off, n, LISTS_THREADS, s_warp);
-    if (blockIdx.x == 0) publish_offsets(a, s_off);
+    cta_scan(a.tile_count, s_off, n, blockDim.x, s_warp);
+    if (blk == 0) publish_offsets(a, s_off);
     const long long slots = (long long)a.Keff * a.tpw_x * a.tpw_y;
     const int tpw = a.tpw_x * a.tpw_y;
-    for (long long i = blockIdx.x * (long long)LISTS_THREADS + threadIdx.x; i < slots;
-         i += (long long)gridDim.x * LISTS_THREADS) {
+    for (long long i = blk * (long long)blockDim.x + threadIdx.x; i < slots; i += (long long)nblk * blockDim.x) {
         const int k = slots < (1LL << 32) ? (int)((unsigned)i / (unsigned)tpw) : (int)(i / tpw);
         const int j = (int)(i - (long long)k * tpw);
         const ClusterDev cd = a.cdev[k];
@@ -451,6 +448,28 @@ __global__ void __launch_bounds__(LISTS_THREADS) k_lists(SolveArgs a)
         const int pos = s_off[t] + atomicAdd(&a.tile_cursor[t], 1);
         if (pos < a.tile_cap) a.tile_list[pos] = k;
     }
+}
+
+__global__ void __launch_bounds__(LISTS_THREADS) k_lists(SolveArgs a)
+{
+    pdl_wait();
+    pdl_release();
+    extern __shared__ int s_off[];
+    __shared__ int s_warp[32];
+    lists_cta(a, blockIdx.x, gridDim.x, s_off, s_warp);
+}
+
+// The candidate lists (CTAs [0, n_lists), placed first) and the projection
+// (the others) in one launch: both need only the update's output, so the
+// iteration stays one chain of programmatic launches.
+__global__ void __launch_bounds__(PROJ_THREADS) k_project_lists(SolveArgs a, int n_lists)
+{
+    pdl_wait();
+    pdl_release();
+    extern __shared__ int s_off[];
+    __shared__ int s_warp[32];
+    if ((int)blockIdx.x < n_lists) lists_cta(a, blockIdx.x, n_lists, s_off, s_warp);
+    else project_cta(a, 0, blockIdx.x - n_lists, gridDim.x - n_lists);
 }
 
 __global__ void k_fill_tiles(SolveArgs a)
@@ -489,6 +508,21 @@ void launch_batch_update(const BatchArgs &b, int total_clusters, int total_fill,
                whole_image);
     pdl_launch(pdl, k_scan_tiles_batch, dim3(b.count), dim3(SCAN1_THREADS), 0, st, b);
     pdl_launch(pdl, k_fill_tiles_batch, dim3((total_fill + 255) / 256), dim3(256), 0, st, b);
+}
+
+bool project_lists_fused(const SolveArgs &a) { return a.n_tx * a.n_ty <= LISTS_MAX_TILES; }
+
+void launch_project_lists(const SolveArgs &a, cudaStream_t st, bool pdl)
+{
+    const int n = a.n_tx * a.n_ty;
+    const long long slots = (long long)a.Keff * a.tpw_x * a.tpw_y;
+    // one resident wave (two 512-thread CTAs per SM): a few list CTAs, four
+    // slots per thread, and the projection in the rest
+    const int slots_per_cta = 4 * PROJ_THREADS;
+    const int n_lists = (int)std::max(std::min(ceil_div_ll(slots, slots_per_cta), 64LL), 1LL);
+    const int n_proj = std::max(std::min(a.Keff, 2 * 152 - n_lists), 1);
+    pdl_launch(pdl, k_project_lists, dim3((unsigned)(n_lists + n_proj)), dim3(PROJ_THREADS),
+               (size_t)(n + 1) * sizeof(int), st, a, n_lists);
 }
 
 void launch_lists(const SolveArgs &a, cudaStream_t st, bool pdl)

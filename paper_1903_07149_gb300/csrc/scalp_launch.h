@@ -57,6 +57,10 @@ void launch_update(const SolveArgs &a, int from_acc, cudaStream_t st, bool pdl =
 void launch_project(const SolveArgs &a, int whole_image, cudaStream_t st, bool pdl = false);
 // Per-tile candidate lists from the tile counts (no other state is touched).
 void launch_lists(const SolveArgs &a, cudaStream_t st, bool pdl = false);
+// The projection and the candidate lists as one launch (when the lists'
+// scan fits shared memory, project_lists_fused()).
+bool project_lists_fused(const SolveArgs &a);
+void launch_project_lists(const SolveArgs &a, cudaStream_t st, bool pdl = false);
 // Batch: the assignment of every tile of every image in one launch, and one
 // iteration's update, projection and candidate lists for every image.
 void launch_assign_batch(const BatchArgs &b, int storage, int total_tiles, size_t smem_bytes,
