@@ -81,6 +81,48 @@ __device__ __forceinline__ float3 srgb_to_lab(const float *lin, const uint8_t *p
     return make_float3(116.0f * fy - 16.0f, 500.0f * (fx - fy), 200.0f * (fy - fz));
 }
 
+// Exclusive scan of in[0, n) into out[0, n] (out[n] = total) by one CTA of
+// `threads` threads (a multiple of 32, at most 1024).  Each warp scans a
+// contiguous segment 32 consecutive entries at a time (coalesced loads,
+// conflict-free stores), carrying its running sum; the warps' totals are
+// then scanned and each warp adds its offset.  s_warp holds 32 ints.
+__device__ __forceinline__ void cta_scan(const int *in, int *out, int n, int threads, int *s_warp)
+{
+    const unsigned FULL = 0xffffffffu;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = threads / 32;
+    const int seg = (n + nw - 1) / nw;
+    const int b = min(n, wid * seg), e = min(n, b + seg);
+    int carry = 0;
+#pragma unroll 4
+    for (int base = b; base < e; base += 32) {
+        const int i = base + lane;
+        const int v = i < e ? in[i] : 0;
+        int incl = v;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (i < e) out[i] = carry + incl - v;
+        carry += __shfl_sync(FULL, incl, 31);
+    }
+    if (lane == 0) s_warp[wid] = carry;
+    __syncthreads();
+    if (wid == 0) {  // inclusive scan of the warp totals
+        int w = lane < nw ? s_warp[lane] : 0;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(FULL, w, o);
+            if (lane >= o) w += t;
+        }
+        s_warp[lane] = w;
+    }
+    __syncthreads();
+    const int off = wid ? s_warp[wid - 1] : 0;
+    if (off)
+        for (int i = b + lane; i < e; i += 32) out[i] += off;  // (each entry its own lane's)
+    if (threadIdx.x == 0) out[n] = s_warp[31];
+    __syncthreads();
+}
+
 // Programmatic dependent launch: a kernel launched with pdl_launch() may be
 // placed on the GPU while its predecessor in the stream is still draining.
 // It calls pdl_wait() before it reads anything the predecessor wrote (the wait

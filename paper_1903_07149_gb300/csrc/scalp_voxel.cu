@@ -201,6 +201,8 @@ __global__ void __launch_bounds__(256) k_vaccumulate(VoxArgs a)
 // ---------------------------------------------------------------------------
 __global__ void k_vupdate(VoxArgs a, int from_acc)
 {
+    pdl_wait();
+    pdl_release();
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= a.Keff) return;
     if (from_acc) {
@@ -279,6 +281,8 @@ __device__ __forceinline__ void vshfl_min(VBest &b)
 
 __global__ void __launch_bounds__(VPROJ_THREADS) k_vproject(VoxArgs a, int whole)
 {
+    pdl_wait();
+    pdl_release();
     __shared__ VBest s_best[VPROJ_THREADS / 32];
     const int nproj = a.ctr->nproj;
     const bool all = whole || a.ctr->orphans > 0;
@@ -338,40 +342,17 @@ constexpr int VSCAN_THREADS = 1024;
 
 __global__ void __launch_bounds__(VSCAN_THREADS) k_vscan(VoxArgs a)
 {
+    pdl_wait();
+    pdl_release();
     __shared__ int s_warp[32];
     const int n = a.n_tx * a.n_ty * a.n_tt;
-    const int per = (n + VSCAN_THREADS - 1) / VSCAN_THREADS;
-    const int b = threadIdx.x * per, e = min(n, b + per);
-    int tsum = 0;
-    for (int i = b; i < e; ++i) tsum += a.tile_count[i];
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    int incl = tsum;
-    for (int o = 1; o < 32; o <<= 1) {
-        const int t = __shfl_up_sync(0xffffffffu, incl, o);
-        if (lane >= o) incl += t;
-    }
-    if (lane == 31) s_warp[wid] = incl;
-    __syncthreads();
-    if (wid == 0) {
-        int v = s_warp[lane];
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(0xffffffffu, v, o);
-            if (lane >= o) v += t;
-        }
-        s_warp[lane] = v;
-    }
-    __syncthreads();
-    int run = (wid ? s_warp[wid - 1] : 0) + incl - tsum;
-    for (int i = b; i < e; ++i) {
-        const int v = a.tile_count[i];
-        a.tile_off[i] = run;
+    cta_scan(a.tile_count, a.tile_off, n, VSCAN_THREADS, s_warp);  // (ends with a barrier)
+    for (int i = threadIdx.x; i < n; i += VSCAN_THREADS) {
         a.tile_cursor[i] = 0;
         a.tile_count[i] = 0;
-        run += v;
     }
-    if (threadIdx.x == VSCAN_THREADS - 1) {
-        a.tile_off[n] = s_warp[31];
-        if (s_warp[31] > a.tile_cap) atomicExch(&a.ctr->error, ERR_TILE_LIST_OVERFLOW);
+    if (threadIdx.x == 0) {  // (tile_off[n] is this thread's own write)
+        if (a.tile_off[n] > a.tile_cap) atomicExch(&a.ctr->error, ERR_TILE_LIST_OVERFLOW);
         a.ctr->nproj = 0;
         a.ctr->orphans = 0;
     }
@@ -379,6 +360,8 @@ __global__ void __launch_bounds__(VSCAN_THREADS) k_vscan(VoxArgs a)
 
 __global__ void k_vfill(VoxArgs a)
 {
+    pdl_wait();
+    pdl_release();
     const long long slots = (long long)a.tpw_x * a.tpw_y * a.tpw_t;
     const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     if (i >= (long long)a.Keff * slots) return;
@@ -488,6 +471,8 @@ __global__ void __launch_bounds__(VTILE) k_vassign(VoxArgs a)
     __shared__ unsigned char s_owner[VMAX_ITEMS];
     __shared__ unsigned long long s_best[VTILE];
     __shared__ int s_counter;
+    pdl_wait();
+    pdl_release();
     const int tile = blockIdx.x;
     const int tx = tile % a.n_tx, ty = (tile / a.n_tx) % a.n_ty, tt = tile / (a.n_tx * a.n_ty);
     const int x0 = tx * VTX, y0 = ty * VTY, t0 = tt * VTT;
@@ -834,17 +819,23 @@ int vcheck(cudaError_t e, const char *what)
     return e == cudaSuccess ? SCALP_OK : vfail(SCALP_E_CUDA, "%s: %s", what, cudaGetErrorString(e));
 }
 
+// Programmatic launches (each kernel placed while the one before drains),
+// except around the profiling event records.
 void venqueue_lists(scalp_vctx *c)
 {
-    k_vscan<<<1, VSCAN_THREADS, 0, c->st>>>(c->a);
+    const bool pdl = !c->profiling;
+    pdl_launch(pdl, k_vscan, dim3(1), dim3(VSCAN_THREADS), 0, c->st, c->a);
     const long long slots = (long long)c->Keff * c->a.tpw_x * c->a.tpw_y * c->a.tpw_t;
-    k_vfill<<<(unsigned)((slots + 255) / 256), 256, 0, c->st>>>(c->a);
+    pdl_launch(pdl, k_vfill, dim3((unsigned)((slots + 255) / 256)), dim3(256), 0, c->st, c->a);
 }
 
 void venqueue_update(scalp_vctx *c, int from_acc, int whole)
 {
-    k_vupdate<<<(c->Keff + 63) / 64, 64, 0, c->st>>>(c->a, from_acc);
-    if (from_acc) k_vproject<<<std::min(c->Keff, 2 * 152), VPROJ_THREADS, 0, c->st>>>(c->a, whole);
+    const bool pdl = !c->profiling;
+    pdl_launch(pdl, k_vupdate, dim3((c->Keff + 63) / 64), dim3(64), 0, c->st, c->a, from_acc);
+    if (from_acc)
+        pdl_launch(pdl, k_vproject, dim3(std::min(c->Keff, 2 * 152)), dim3(VPROJ_THREADS), 0, c->st, c->a,
+                   whole);
     venqueue_lists(c);
 }
 
@@ -985,7 +976,7 @@ int scalp_voxel_iterate(scalp_vctx *c, int32_t n)
             }
             cudaEventRecord(c->ev[2 * c->ev_pending], c->st);
         }
-        k_vassign<<<tiles, VTILE, 0, c->st>>>(c->a);
+        pdl_launch(!prof, k_vassign, dim3(tiles), dim3(VTILE), 0, c->st, c->a);
         if (prof) cudaEventRecord(c->ev[2 * c->ev_pending++ + 1], c->st);
         venqueue_update(c, 1, 0);
         ++c->iterations;
