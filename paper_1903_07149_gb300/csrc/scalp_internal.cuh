@@ -123,6 +123,26 @@ __device__ __forceinline__ void cta_scan(const int *in, int *out, int n, int thr
     __syncthreads();
 }
 
+// The start of an exact window search, floor(s/n - r) - 1 and ceil(s/n + r)
+// + 1 for a coordinate in [0, lim): the searches then move inward with the
+// exact integer test, so the start needs only an error below one.  For lim
+// <= 2^20 it is taken in FP32 (s, n and the quotient each rounded: relative
+// error below 4e-7, so below 0.42 in absolute terms, r below 2^-4 too),
+// without FP64 divisions, which are slow on this part; else in FP64.
+__device__ __forceinline__ void window_start(long long s, long long n, double r, int lim, long long &lo,
+                                             long long &hi)
+{
+    if (lim <= (1 << 20)) {
+        const float c = __fdividef((float)s, (float)n), rf = (float)r;
+        lo = (long long)floorf(c - rf) - 1;
+        hi = (long long)ceilf(c + rf) + 1;
+    } else {
+        const double c = (double)s / (double)n;
+        lo = (long long)floor(c - r) - 1;
+        hi = (long long)ceil(c + r) + 1;
+    }
+}
+
 // Programmatic dependent launch: a kernel launched with pdl_launch() may be
 // placed on the GPU while its predecessor in the stream is still draining.
 // It calls pdl_wait() before it reads anything the predecessor wrote (the wait

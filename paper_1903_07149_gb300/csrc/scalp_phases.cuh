@@ -28,8 +28,8 @@ __device__ __forceinline__ bool in_window(long long v, long long n, long long s,
 __device__ inline bool window_range(long long n, long long s, long long N, long long K, double r,
                              int limit, int &lo, int &hi)
 {
-    double c = (double)s / (double)n;
-    long long l = (long long)floor(c - r) - 1, h = (long long)ceil(c + r) + 1;
+    long long l, h;
+    window_start(s, n, r, limit, l, h);
     int guard = 0;
     while (!in_window(l, n, s, N, K) && guard++ < 64) ++l;
     guard = 0;

@@ -77,20 +77,22 @@ struct VoxArgs {
 
 // ---------------------------------------------------------------------------
 // Windows: |v - s/n| <= r with r^3 = N/K, i.e. K*q^3 <= N*n^3 for
-// q = |n*v - s|.  A double comparison of q/n with r (r = cbrt(N/K) within two
-// ulps, q/n within one) decides every value farther than 1e-9 relative from
-// the edge; the rest are decided in 128-bit integers.  There q <= (1 + 1e-9)
-// n r, and a volume holds at most 2^30 voxels (n, N <= 2^30), so K*q^3 and
-// N*n^3 both stay below 2^121.
+// q = |n*v - s|.  An FP32 comparison of q/n with r (each within 4e-7
+// relative of exact) decides every value farther than 1e-5 relative from the
+// edge; the rest are decided in 128-bit integers.  There q <= (1 + 1e-5) n r,
+// and a volume holds at most 2^30 voxels (n, N <= 2^30), so K*q^3 and N*n^3
+// both stay below 2^121.
 // ---------------------------------------------------------------------------
 __device__ __forceinline__ bool vin_window(long long v, long long n, long long s, long long N, long long K,
                                            double r)
 {
     const long long d = n * v - s;
     const unsigned long long q = (unsigned long long)(d < 0 ? -d : d);
-    const double x = (double)q / (double)n;
-    if (x < r * (1.0 - 1e-9)) return true;
-    if (x > r * (1.0 + 1e-9)) return false;
+    // FP32 filter: q/n and r each within 4e-7 relative of exact, so outside
+    // a 1e-5 band the FP32 comparison is the exact one
+    const float x = __fdividef((float)q, (float)n), rf = (float)r;
+    if (x < rf * (1.0f - 1e-5f)) return true;
+    if (x > rf * (1.0f + 1e-5f)) return false;
     const unsigned __int128 lhs = (unsigned __int128)q * q * q * (unsigned long long)K;
     const unsigned __int128 rhs =
         (unsigned __int128)((unsigned long long)N * (unsigned long long)n) * ((unsigned long long)n * (unsigned long long)n);
@@ -100,10 +102,9 @@ __device__ __forceinline__ bool vin_window(long long v, long long n, long long s
 __device__ __forceinline__ void vwindow(long long n, long long s, long long N, long long K, double r, int lim,
                                         int &lo, int &hi)
 {
-    const double c = (double)s / (double)n;
-    int a = (int)floor(c - r) - 1, b = (int)ceil(c + r) + 1;
-    a = max(a, 0);
-    b = min(b, lim - 1);
+    long long a0, b0;
+    window_start(s, n, r, lim, a0, b0);
+    int a = (int)max(a0, 0LL), b = (int)min(b0, (long long)lim - 1);
     while (a <= b && !vin_window(a, n, s, N, K, r)) ++a;
     while (b >= a && !vin_window(b, n, s, N, K, r)) --b;
     lo = a;
