@@ -123,12 +123,32 @@ __device__ __forceinline__ void cta_scan(const int *in, int *out, int n, int thr
     __syncthreads();
 }
 
+// Row of index i in rows of w pixels: i / w by a 32-bit reciprocal
+// (rcp = ceil(2^32 / w), exact while i * w < 2^32; the caller checks), else by
+// a 64-bit division.
+struct RowDiv {
+    long long w;
+    unsigned rcp;
+    bool fast;
+    __device__ __forceinline__ RowDiv(long long w_, long long area) : w(w_)
+    {
+        fast = w_ > 1 && (unsigned long long)area * (unsigned long long)w_ < (1ULL << 32);
+        rcp = fast ? (unsigned)((0x100000000ULL + w_ - 1) / w_) : 0u;
+    }
+    __device__ __forceinline__ long long row(long long i) const
+    {
+        if (w == 1) return i;
+        return fast ? (long long)__umulhi((unsigned)i, rcp) : i / w;
+    }
+};
+
 // The start of an exact window search, floor(s/n - r) - 1 and ceil(s/n + r)
 // + 1 for a coordinate in [0, lim): the searches then move inward with the
 // exact integer test, so the start needs only an error below one.  For lim
-// <= 2^20 it is taken in FP32 (s, n and the quotient each rounded: relative
-// error below 4e-7, so below 0.42 in absolute terms, r below 2^-4 too),
-// without FP64 divisions, which are slow on this part; else in FP64.
+// <= 2^20 it is taken in FP32, without FP64 divisions (slow on this part):
+// s, n and their quotient each rounded leave at most 4e-7 relative, 0.42
+// absolute; rounding r adds at most 0.07 and the subtraction 0.13, 0.62 in
+// all.  Larger dimensions take FP64.
 __device__ __forceinline__ void window_start(long long s, long long n, double r, int lim, long long &lo,
                                              long long &hi)
 {

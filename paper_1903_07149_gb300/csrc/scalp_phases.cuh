@@ -72,24 +72,6 @@ __device__ __forceinline__ void proj_shfl_min(ProjBest &b)
 }
 
 
-// Row of index i in rows of w pixels: i / w by a 32-bit reciprocal
-// (rcp = ceil(2^32 / w), exact while i * w < 2^32; the caller checks), else by
-// a 64-bit division.
-struct RowDiv {
-    long long w;
-    unsigned rcp;
-    bool fast;
-    __device__ __forceinline__ RowDiv(long long w_, long long area) : w(w_)
-    {
-        fast = w_ > 1 && (unsigned long long)area * (unsigned long long)w_ < (1ULL << 32);
-        rcp = fast ? (unsigned)((0x100000000ULL + w_ - 1) / w_) : 0u;
-    }
-    __device__ __forceinline__ long long row(long long i) const
-    {
-        if (w == 1) return i;
-        return fast ? (long long)__umulhi((unsigned)i, rcp) : i / w;
-    }
-};
 
 // Candidate p (raster index, pixel (x, y)) for X_k^* of cluster (n, sx, sy).
 __device__ __forceinline__ ProjBest proj_candidate(long long p, int x, int y, long long n,

@@ -298,18 +298,48 @@ __global__ void __launch_bounds__(VPROJ_THREADS) k_vproject(VoxArgs a, int whole
         }
         const long long w = xhi - xlo + 1, h = yhi - ylo + 1;
         const long long vol = max(0LL, w) * max(0LL, h) * max(0LL, (long long)(thi - tlo + 1));
+        // voxel i of the box: row i / w, frame row / h, by reciprocals
+        const RowDiv div_w(w, vol), div_h(h, w > 0 ? vol / w : 0);
+        // 64-bit squared distances when 3 (n * largest dimension)^2 < 2^62
+        const double bound = (double)max(a.W, max(a.H, a.T));
+        const bool small = 3.0 * ((double)n * bound) * ((double)n * bound) < 4.0e18;
         VBest b = {~0ull, ~0ull, LLONG_MAX};
-        for (long long i = tid; i < vol; i += VPROJ_THREADS) {
-            const long long plane_i = i / w;
-            const int x = xlo + (int)(i - plane_i * w);
-            const int t = tlo + (int)(plane_i / h), y = ylo + (int)(plane_i - (plane_i / h) * h);
-            const long long p = ((long long)t * a.H + y) * a.W + x;
-            if (a.labels[p] != k) continue;
-            const __int128 dx = (__int128)n * x - sx, dy = (__int128)n * y - sy, dt = (__int128)n * t - st;
-            const unsigned __int128 d2 = (unsigned __int128)(dx * dx) + (unsigned __int128)(dy * dy) +
-                                         (unsigned __int128)(dt * dt);
-            const VBest c = {(unsigned long long)(d2 >> 64), (unsigned long long)d2, p};
-            if (vless(c, b)) b = c;
+        constexpr int VB = 8;  // label loads issued before any comparison
+        for (long long base = 0; base < vol; base += (long long)VPROJ_THREADS * VB) {
+            int lab[VB];
+#pragma unroll
+            for (int u = 0; u < VB; ++u) {
+                const long long i = base + (long long)u * VPROJ_THREADS + tid;
+                lab[u] = -1;
+                if (i < vol) {
+                    const long long row = div_w.row(i), fr = div_h.row(row);
+                    const int x = xlo + (int)(i - row * w), y = ylo + (int)(row - fr * h), t = tlo + (int)fr;
+                    lab[u] = a.labels[((long long)t * a.H + y) * a.W + x];
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < VB; ++u) {
+                if (lab[u] != k) continue;
+                const long long i = base + (long long)u * VPROJ_THREADS + tid;
+                const long long row = div_w.row(i), fr = div_h.row(row);
+                const int x = xlo + (int)(i - row * w), y = ylo + (int)(row - fr * h), t = tlo + (int)fr;
+                const long long p = ((long long)t * a.H + y) * a.W + x;
+                VBest c;
+                c.p = p;
+                if (small) {
+                    const long long dx = n * x - sx, dy = n * y - sy, dt = n * t - st;
+                    c.hi = 0;
+                    c.lo = (unsigned long long)(dx * dx) + (unsigned long long)(dy * dy) +
+                           (unsigned long long)(dt * dt);
+                } else {
+                    const __int128 dx = (__int128)n * x - sx, dy = (__int128)n * y - sy, dt = (__int128)n * t - st;
+                    const unsigned __int128 d2 = (unsigned __int128)(dx * dx) + (unsigned __int128)(dy * dy) +
+                                                 (unsigned __int128)(dt * dt);
+                    c.hi = (unsigned long long)(d2 >> 64);
+                    c.lo = (unsigned long long)d2;
+                }
+                if (vless(c, b)) b = c;
+            }
         }
         vshfl_min(b);
         if (lane == 0) s_best[warp] = b;
