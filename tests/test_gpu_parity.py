@@ -451,10 +451,14 @@ def test_constant_image_fixed_point(S):
 
 
 @pytest.mark.parametrize("H,W,K", [(1, 1, 1), (1, 37, 5), (37, 1, 4), (7, 9, 63), (33, 33, 1),
-                                   (16, 32, 2), (65, 97, 30)])
+                                   (16, 32, 2), (65, 97, 30), (64, 96, 300), (16, 16, 256)])
 def test_edge_sizes(S, H, W, K):
     """Degenerate sizes (one pixel, one row or column, K = N, K = 1, one
-    tile): each of three iterations from the oracle's state gives labels whose
+    tile) and the assignment's three set-up forms: tiles of at most 32
+    candidates (one warp ranks them), of 33 to 128 (7x9 with K = 63 on one
+    tile; 64x96 with K = 300, about 80 on each of six tiles: the whole CTA
+    ranks them) and of more than 128 (16x16 with K = N = 256: the per-pixel
+    path).  Each of three iterations from the oracle's state gives labels whose
     every disagreement is a near-tie, with exact sums and endpoints where a
     cluster's pixel set agrees; three free-running iterations equal the oracle
     unless such a near-tie flip occurred; the enforcement of the GPU's labels
