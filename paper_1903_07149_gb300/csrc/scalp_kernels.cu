@@ -397,15 +397,49 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(SolveArgs a, int whole
     project_cta(a, whole_image, blockIdx.x, gridDim.x);
 }
 
-// Batch: PROJ_CTAS_PER_IMAGE CTAs per image.
+// Batch of more images than the work list's shared memory holds:
+// PROJ_CTAS_PER_IMAGE CTAs per image, each cluster searched by a whole CTA.
 constexpr int PROJ_CTAS_PER_IMAGE = 16;
+constexpr int PROJ_LIST_MAX_IMAGES = 4095;  // (3 * count + 1) ints <= 48 KB
 
-__global__ void __launch_bounds__(PROJ_THREADS) k_project_batch(BatchArgs b, int whole_image)
+__global__ void __launch_bounds__(PROJ_THREADS) k_project_batch_images(BatchArgs b, int whole_image)
 {
     pdl_wait();
     pdl_release();
     const int i = blockIdx.x / PROJ_CTAS_PER_IMAGE;
     project_cta(b.args[i], whole_image, blockIdx.x % PROJ_CTAS_PER_IMAGE, PROJ_CTAS_PER_IMAGE);
+}
+
+// Batch: every image's queued clusters as one work list over the warps of
+// the grid (one warp per cluster, prefix of the queue lengths in shared
+// memory); an image whose projection searches the whole image (at set-up,
+// or after orphans) takes its clusters one per CTA instead.  Dynamic shared
+// memory: 3 * count + 1 ints.
+__global__ void __launch_bounds__(PROJ_THREADS) k_project_batch(BatchArgs b, int whole_image)
+{
+    pdl_wait();
+    pdl_release();
+    extern __shared__ int s_cnt[];
+    __shared__ int s_warp[32];
+    const int count = b.count;
+    int *s_pref = s_cnt + count, *s_all = s_pref + count + 1;
+    for (int i = threadIdx.x; i < count; i += blockDim.x) {
+        const bool all = whole_image || b.args[i].ctr->proj_all;
+        s_all[i] = all;
+        s_cnt[i] = all ? 0 : b.args[i].ctr->nproj;
+    }
+    __syncthreads();
+    cta_scan(s_cnt, s_pref, count, PROJ_THREADS, s_warp);
+    const int total = s_pref[count], warps = PROJ_THREADS / 32, G = gridDim.x;
+    for (int t = blockIdx.x * warps + (int)(threadIdx.x >> 5); t < total; t += G * warps) {
+        const int i = batch_find(s_pref, count, t);
+        project_warp(b.args[i], t - s_pref[i]);
+    }
+    for (int i = 0; i < count; ++i) {  // (s_all[i] is CTA-uniform: the barriers inside are safe)
+        if (!s_all[i]) continue;
+        const int nproj = b.args[i].ctr->nproj;
+        for (int j = blockIdx.x; j < nproj; j += G) project_cta(b.args[i], whole_image, j, INT_MAX);
+    }
 }
 
 void launch_project(const SolveArgs &a, int whole_image, cudaStream_t st, bool pdl)
@@ -488,6 +522,16 @@ __global__ void k_fill_tiles_batch(BatchArgs b)
 }
 
 // One iteration's update, projection and list kernels for a whole batch.
+static void launch_project_batch(const BatchArgs &b, cudaStream_t st, bool pdl, int whole_image)
+{
+    if (b.count <= PROJ_LIST_MAX_IMAGES)
+        pdl_launch(pdl, k_project_batch, dim3(2 * 152), dim3(PROJ_THREADS), (size_t)(3 * b.count + 1) * sizeof(int),
+                   st, b, whole_image);
+    else
+        pdl_launch(pdl, k_project_batch_images, dim3(b.count * PROJ_CTAS_PER_IMAGE), dim3(PROJ_THREADS), 0, st, b,
+                   whole_image);
+}
+
 void launch_batch_update(const BatchArgs &b, int total_clusters, int total_fill, cudaStream_t st, bool pdl,
                          cudaStream_t side, cudaEvent_t fork, cudaEvent_t join, int whole_image)
 {
@@ -499,13 +543,11 @@ void launch_batch_update(const BatchArgs &b, int total_clusters, int total_fill,
         pdl_launch(false, k_scan_tiles_batch, dim3(b.count), dim3(SCAN1_THREADS), 0, side, b);
         pdl_launch(true, k_fill_tiles_batch, dim3((total_fill + 255) / 256), dim3(256), 0, side, b);
         cudaEventRecord(join, side);
-        pdl_launch(pdl, k_project_batch, dim3(b.count * PROJ_CTAS_PER_IMAGE), dim3(PROJ_THREADS), 0, st, b,
-                   whole_image);
+        launch_project_batch(b, st, pdl, whole_image);
         cudaStreamWaitEvent(st, join, 0);
         return;
     }
-    pdl_launch(pdl, k_project_batch, dim3(b.count * PROJ_CTAS_PER_IMAGE), dim3(PROJ_THREADS), 0, st, b,
-               whole_image);
+    launch_project_batch(b, st, pdl, whole_image);
     pdl_launch(pdl, k_scan_tiles_batch, dim3(b.count), dim3(SCAN1_THREADS), 0, st, b);
     pdl_launch(pdl, k_fill_tiles_batch, dim3((total_fill + 255) / 256), dim3(256), 0, st, b);
 }

@@ -165,6 +165,57 @@ __device__ __forceinline__ void update_cluster(const SolveArgs &a, int k, int fr
     }
 }
 
+// Eq. 4 for queued cluster j of one image by one warp, over the window the
+// last assignment used (which holds S_k): the same argmin, with the same
+// exact comparison and tie rule, as the CTA-wide search.
+__device__ __forceinline__ void project_warp(const SolveArgs &a, int j)
+{
+    constexpr int BATCH = 4;
+    const int lane = threadIdx.x & 31;
+    const int k = a.proj_list[j];
+    const long long n = a.st_n[k], sx = a.st_sx[k], sy = a.st_sy[k];
+    const int4 w4 = a.prev_win[k];
+    const int xlo = w4.x, ylo = w4.z;
+    const int w = w4.y - w4.x + 1;
+    const long long area = (long long)w * (w4.w - w4.z + 1);
+    const RowDiv div(w, area);
+    const double bound = (double)max(a.W, a.H);
+    const bool small = 2.0 * (n * bound) * (n * bound) < 4.0e18;
+    ProjBest b = {~0ull, ~0ull, LLONG_MAX};
+    for (long long base = 0; base < area; base += 32 * BATCH) {
+        int lab[BATCH];
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            const long long i = base + u * 32 + lane;
+            lab[u] = -1;
+            if (i < area) {
+                const long long r = div.row(i);
+                lab[u] = a.labels[(long long)(ylo + (int)r) * a.W + xlo + (int)(i - r * w)];
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < BATCH; ++u) {
+            if (lab[u] != k) continue;
+            const long long i = base + u * 32 + lane;
+            const long long r = div.row(i);
+            const int y = ylo + (int)r, x = xlo + (int)(i - r * w);
+            const ProjBest c = proj_candidate((long long)y * a.W + x, x, y, n, sx, sy, small);
+            if (proj_less(c, b)) b = c;
+        }
+    }
+    proj_shfl_min(b);
+    if (lane == 0) {
+        if (b.p == LLONG_MAX) {
+            atomicExch(&a.ctr->error, ERR_BAD_LABEL);
+        } else {
+            const int ex = (int)(b.p % a.W), ey = (int)(b.p / a.W);
+            a.st_end[k] = make_int2(ex, ey);
+            a.cdev[k].ex = ex;
+            a.cdev[k].ey = ey;
+        }
+    }
+}
+
 // Queued projections: S_k lies inside the window the last assignment used for
 // cluster k, unless some pixel kept its old label for lack of any candidate;
 // then (or with whole_image, at set-up) the whole image is searched.  One CTA
@@ -176,7 +227,8 @@ __device__ __forceinline__ void project_cta(const SolveArgs &a, int whole_image,
     const bool all = whole_image || a.ctr->proj_all;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const double bound = (double)max(a.W, a.H);
-    for (int j = j0; j < nproj; j += stride) {
+    // (the step cannot overflow: a stride past the queue's end ends the loop)
+    for (int j = j0; j < nproj; j = stride < nproj - j ? j + stride : nproj) {
         const int k = a.proj_list[j];
         const long long n = a.st_n[k], sx = a.st_sx[k], sy = a.st_sy[k];
         int xlo = 0, xhi = a.W - 1, ylo = 0, yhi = a.H - 1;
