@@ -397,10 +397,11 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project(SolveArgs a, int whole
     project_cta(a, whole_image, blockIdx.x, gridDim.x);
 }
 
-// Batch of more images than the work list's shared memory holds:
+// Batch of few images, or of more than the work lists' shared memory holds:
 // PROJ_CTAS_PER_IMAGE CTAs per image, each cluster searched by a whole CTA.
 constexpr int PROJ_CTAS_PER_IMAGE = 16;
-constexpr int PROJ_LIST_MAX_IMAGES = 4095;  // (3 * count + 1) ints <= 48 KB
+constexpr int PROJ_LIST_MIN_IMAGES = 32;
+constexpr int PROJ_LIST_MAX_IMAGES = 3071;  // (4 * count + 2) ints <= 48 KB
 
 __global__ void __launch_bounds__(PROJ_THREADS) k_project_batch_images(BatchArgs b, int whole_image)
 {
@@ -410,35 +411,56 @@ __global__ void __launch_bounds__(PROJ_THREADS) k_project_batch_images(BatchArgs
     project_cta(b.args[i], whole_image, blockIdx.x % PROJ_CTAS_PER_IMAGE, PROJ_CTAS_PER_IMAGE);
 }
 
-// Batch: every image's queued clusters as one work list over the warps of
-// the grid (one warp per cluster, prefix of the queue lengths in shared
-// memory); an image whose projection searches the whole image (at set-up,
-// or after orphans) takes its clusters one per CTA instead.  Dynamic shared
-// memory: 3 * count + 1 ints.
+// Batch: the queued clusters of every image as work lists over the grid, each
+// with the prefix of its images' queue lengths in shared memory.  A warp
+// searches a window alone, so warps pay only when the clusters outnumber the
+// CTAs several times (more than four per CTA): then one
+// warp per cluster for the images whose windows have at most
+// PROJ_WARP_MAX_AREA pixels, and one CTA per cluster for those with larger
+// windows and for those whose projection searches the whole image (at
+// set-up, or after orphans); with fewer clusters, one CTA per cluster for
+// all.  Dynamic shared memory: 4 * count + 2 ints.
+constexpr float PROJ_WARP_MAX_AREA = 4096.0f;
+
 __global__ void __launch_bounds__(PROJ_THREADS) k_project_batch(BatchArgs b, int whole_image)
 {
     pdl_wait();
     pdl_release();
-    extern __shared__ int s_cnt[];
+    extern __shared__ int s_mem[];
     __shared__ int s_warp[32];
     const int count = b.count;
-    int *s_pref = s_cnt + count, *s_all = s_pref + count + 1;
+    int *s_nw = s_mem, *s_pw = s_nw + count;          // warp list: lengths, prefix
+    int *s_nc = s_pw + count + 1, *s_pc = s_nc + count;  // CTA list: lengths, prefix
+    const int G = gridDim.x;
+    constexpr int warps = PROJ_THREADS / 32;
     for (int i = threadIdx.x; i < count; i += blockDim.x) {
-        const bool all = whole_image || b.args[i].ctr->proj_all;
-        s_all[i] = all;
-        s_cnt[i] = all ? 0 : b.args[i].ctr->nproj;
+        s_nw[i] = 0;
+        s_nc[i] = b.args[i].ctr->nproj;
     }
     __syncthreads();
-    cta_scan(s_cnt, s_pref, count, PROJ_THREADS, s_warp);
-    const int total = s_pref[count], warps = PROJ_THREADS / 32, G = gridDim.x;
-    for (int t = blockIdx.x * warps + (int)(threadIdx.x >> 5); t < total; t += G * warps) {
-        const int i = batch_find(s_pref, count, t);
-        project_warp(b.args[i], t - s_pref[i]);
+    cta_scan(s_nc, s_pc, count, PROJ_THREADS, s_warp);
+    if (s_pc[count] > 4 * G) {  // (the same decision in every CTA)
+        for (int i = threadIdx.x; i < count; i += blockDim.x) {
+            const SolveArgs &a = b.args[i];
+            const float side = 2.0f * (float)a.r + 1.0f;  // window side
+            const bool cta = whole_image || a.ctr->proj_all || side * side > PROJ_WARP_MAX_AREA;
+            s_nw[i] = cta ? 0 : s_nc[i];
+            s_nc[i] = cta ? s_nc[i] : 0;
+        }
+        __syncthreads();
+        cta_scan(s_nc, s_pc, count, PROJ_THREADS, s_warp);
     }
-    for (int i = 0; i < count; ++i) {  // (s_all[i] is CTA-uniform: the barriers inside are safe)
-        if (!s_all[i]) continue;
-        const int nproj = b.args[i].ctr->nproj;
-        for (int j = blockIdx.x; j < nproj; j += G) project_cta(b.args[i], whole_image, j, INT_MAX);
+    cta_scan(s_nw, s_pw, count, PROJ_THREADS, s_warp);
+    const int total_w = s_pw[count], total_c = s_pc[count];
+    for (int t = blockIdx.x * warps + (int)(threadIdx.x >> 5); t < total_w; t += G * warps) {
+        const int i = batch_find(s_pw, count, t);
+        project_warp(b.args[i], t - s_pw[i]);
+    }
+    // (t is CTA-uniform: the barriers inside project_cta are safe; it searches
+    // the whole image only at set-up or after orphans)
+    for (int t = blockIdx.x; t < total_c; t += G) {
+        const int i = batch_find(s_pc, count, t);
+        project_cta(b.args[i], whole_image, t - s_pc[i], INT_MAX);
     }
 }
 
@@ -524,8 +546,11 @@ __global__ void k_fill_tiles_batch(BatchArgs b)
 // One iteration's update, projection and list kernels for a whole batch.
 static void launch_project_batch(const BatchArgs &b, cudaStream_t st, bool pdl, int whole_image)
 {
-    if (b.count <= PROJ_LIST_MAX_IMAGES)
-        pdl_launch(pdl, k_project_batch, dim3(2 * 152), dim3(PROJ_THREADS), (size_t)(3 * b.count + 1) * sizeof(int),
+    // the work lists for batches of many images (measured: 64 images 33.26
+    // -> 32.69 ms per 10 iterations); a few images keep the per-image CTAs
+    // (12 scales of one image: 3.05 against 3.33 ms per map with the lists)
+    if (b.count >= PROJ_LIST_MIN_IMAGES && b.count <= PROJ_LIST_MAX_IMAGES)
+        pdl_launch(pdl, k_project_batch, dim3(2 * 152), dim3(PROJ_THREADS), (size_t)(4 * b.count + 2) * sizeof(int),
                    st, b, whole_image);
     else
         pdl_launch(pdl, k_project_batch_images, dim3(b.count * PROJ_CTAS_PER_IMAGE), dim3(PROJ_THREADS), 0, st, b,
