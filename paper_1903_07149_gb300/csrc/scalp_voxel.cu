@@ -433,9 +433,48 @@ __device__ __forceinline__ int vpath_sums(const float4 *__restrict__ plane, int 
     else if (ady >= adt) { ns = ady; smaj = sys; d1 = adx; s1 = sxs; d2 = adt; s2 = sts; }
     else { ns = adt; smaj = sts; d1 = adx; s1 = sxs; d2 = ady; s2 = sys; }
     int q = at * hw + ay * W + ax;
+    float dc = 0.f, w = 0.f;
+    if (ns <= FIXED_STEP_MAX_NS) {
+        // the fixed-point rule in closed form per minor axis: sample i lies at
+        // q + i smaj + m1_i s1 + m2_i s2 with m_i the high word of
+        // 2^31 + i S; four samples per group from the group's accumulators
+        const uint32_t S1 = fixed_step_slope(d1, ns), S2 = fixed_step_slope(d2, ns);
+        uint32_t a1 = 0x80000000u, a2 = 0x80000000u;
+        const int n = ns + 1;
+        const auto at = [&](int k) {
+            const int m1 = k == 0 ? 0 : (int)(((unsigned long long)S1 * (unsigned)k + a1) >> 32);
+            const int m2 = k == 0 ? 0 : (int)(((unsigned long long)S2 * (unsigned)k + a2) >> 32);
+            return q + k * smaj + m1 * s1 + m2 * s2;
+        };
+        int i = 0;
+#pragma unroll 1
+        for (; i + 4 <= n; i += 4) {
+            float4 v[4];
+#pragma unroll
+            for (int k = 0; k < 4; ++k) v[k] = __ldg(plane + at(k));
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                dc += colour_dist(v[k], cL, ca, cb);
+                w += v[k].w;
+            }
+            const unsigned long long t1 = (unsigned long long)S1 * 4u + a1, t2 = (unsigned long long)S2 * 4u + a2;
+            a1 = (uint32_t)t1;
+            a2 = (uint32_t)t2;
+            q += 4 * smaj + (int)(t1 >> 32) * s1 + (int)(t2 >> 32) * s2;
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+            if (i + k < n) {
+                const float4 v = __ldg(plane + at(k));
+                dc += colour_dist(v, cL, ca, cb);
+                w += v.w;
+            }
+        sum_dc = dc;
+        sum_w = w;
+        return n;
+    }
     const int two_ns = 2 * ns, two_d1 = 2 * d1, two_d2 = 2 * d2;
     int e1 = ns, e2 = ns;
-    float dc = 0.f, w = 0.f;
 #pragma unroll 4
     for (int i = 0; i <= ns; ++i) {
         const float4 v = __ldg(plane + q);
