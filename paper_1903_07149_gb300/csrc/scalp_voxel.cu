@@ -112,31 +112,6 @@ __device__ __forceinline__ void vwindow(long long n, long long s, long long N, l
 }
 
 // ---------------------------------------------------------------------------
-// Set-up: CIELab, contour factor, grid label.
-// ---------------------------------------------------------------------------
-__global__ void k_vsetup(VoxArgs a, const uint8_t *__restrict__ rgb, const float *__restrict__ contour,
-                         float sigma, float4 *plane)
-{
-    __shared__ float lin[256];
-    for (int i = threadIdx.x; i < 256; i += blockDim.x) lin[i] = a.lut[i];
-    __syncthreads();
-    const float inv_s2 = 1.0f / (sigma * sigma);
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < a.N;
-         p += (long long)gridDim.x * blockDim.x) {
-        const int t = (int)(p / a.HW);
-        const long long q = p - (long long)t * a.HW;
-        const int y = (int)(q / a.W), x = (int)(q - (long long)y * a.W);
-        const float3 lab = srgb_to_lab(lin, rgb + 3 * p);
-        const float c = contour ? contour[p] : 0.0f;
-        plane[p] = make_float4(lab.x, lab.y, lab.z, -expm1f(-(c * c) * inv_s2));
-        const int cx = (int)((long long)x * a.nx / a.W);
-        const int cy = (int)((long long)y * a.ny / a.H);
-        const int ct = (int)((long long)t * a.nt / a.T);
-        a.labels[p] = (ct * a.ny + cy) * a.nx + cx;
-    }
-}
-
-// ---------------------------------------------------------------------------
 // Integer sums of (1, x, y, t, L, a, b) per label; colour fixed point
 // 2^COLOR_FRAC_BITS.  A warp's 32 voxels share a frame and lie within 32
 // columns and 2 rows of a base, so the three offsets pack into one 32-bit
@@ -177,13 +152,26 @@ __device__ __forceinline__ void vaggregate(const VoxArgs &a, bool valid, int lab
     }
 }
 
-__global__ void __launch_bounds__(256) k_vaccumulate(VoxArgs a)
+// ---------------------------------------------------------------------------
+// Set-up: CIELab, contour factor, grid label, initial sums.
+// ---------------------------------------------------------------------------
+// One warp per 32-voxel row segment: CIELab, contour factor, plane sample
+// and grid label of each voxel, then the warp-aggregated integer sums of the
+// initial clusters from the values just stored (the sums start at zero).
+// The frame and row come once per segment; the cell column by a 32-bit
+// division when W * nx < 2^32.
+__global__ void __launch_bounds__(256) k_vsetup(VoxArgs a, const uint8_t *__restrict__ rgb,
+                                               const float *__restrict__ contour, float sigma, float4 *plane)
 {
-    // 32-voxel row segments
+    __shared__ float lin[256];
+    for (int i = threadIdx.x; i < 256; i += blockDim.x) lin[i] = a.lut[i];
+    __syncthreads();
+    const float inv_s2 = 1.0f / (sigma * sigma);
     const long long segs_per_row = (a.W + 31) / 32;
     const long long n_segs = segs_per_row * a.H * a.T;
     const long long warps = (long long)gridDim.x * (blockDim.x / 32);
     const int lane = threadIdx.x & 31;
+    const bool narrow = (unsigned long long)a.W * (unsigned long long)a.nx < (1ULL << 32);
     for (long long s = blockIdx.x * (long long)(blockDim.x / 32) + (threadIdx.x >> 5); s < n_segs; s += warps) {
         const long long row = s / segs_per_row;
         const int x0 = (int)(s - row * segs_per_row) * 32;
@@ -191,8 +179,19 @@ __global__ void __launch_bounds__(256) k_vaccumulate(VoxArgs a)
         const int x = x0 + lane;
         const bool valid = x < a.W;
         const long long p = ((long long)t * a.H + y) * a.W + x;
-        const float4 v = valid ? __ldg(a.plane + p) : make_float4(0.f, 0.f, 0.f, 0.f);
-        const int lab = valid ? a.labels[p] : -1;
+        const int cy = (int)((long long)y * a.ny / a.H), ct = (int)((long long)t * a.nt / a.T);
+        float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+        int lab = -1;
+        if (valid) {
+            const float3 c3 = srgb_to_lab(lin, rgb + 3 * p);
+            const float c = contour ? contour[p] : 0.0f;
+            v = make_float4(c3.x, c3.y, c3.z, -expm1f(-(c * c) * inv_s2));
+            plane[p] = v;
+            const int cx = narrow ? (int)((unsigned)x * (unsigned)a.nx / (unsigned)a.W)
+                                  : (int)((long long)x * a.nx / a.W);
+            lab = (ct * a.ny + cy) * a.nx + cx;
+            a.labels[p] = lab;
+        }
         vaggregate(a, valid, lab, x0, y, t, lane, 0, 0, v);
     }
 }
@@ -1016,9 +1015,7 @@ int scalp_voxel_init(scalp_vctx **out, const scalp_volume *vol, int32_t K, float
         delete c;
         return rc;
     }
-    const int blocks = (int)std::min<long long>((c->N + 255) / 256, 152 * 8);
-    k_vsetup<<<blocks, 256, 0, c->st>>>(a, rgb, con, params->sigma, reinterpret_cast<float4 *>(c->ws + L.plane));
-    k_vaccumulate<<<152 * 8, 256, 0, c->st>>>(a);
+    k_vsetup<<<152 * 8, 256, 0, c->st>>>(a, rgb, con, params->sigma, reinterpret_cast<float4 *>(c->ws + L.plane));
     venqueue_update(c, 1, 1);
     rc = vcheck(cudaGetLastError(), "initialisation kernels");
     if (!rc) rc = vcheck(cudaStreamSynchronize(c->st), "initialisation");  // host staging is released
