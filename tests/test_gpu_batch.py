@@ -193,6 +193,46 @@ def test_many_small_images(S):
     _alone_vs_batch(S, sizes, Ks, seed=1200)
 
 
+def test_projection_work_lists(S):
+    """A batch that takes both of the projection's work lists: 40 images of
+    256x256 with K = 1024 (grid step 8, 17x17 windows: thousands of queued
+    clusters, one warp each) and 4 of 480x640 with K = 20 (windows far above
+    4096 pixels: one CTA each).  Labels, counts, sums, colours and endpoints
+    equal each image solved alone."""
+    import torch
+
+    sizes = [(256, 256)] * 40 + [(480, 640)] * 4
+    Ks = [1024] * 40 + [20] * 4
+    rgbs, cons = [], []
+    for i, (H, W) in enumerate(sizes):
+        rgb, con, _ = synth.small_image(H, W, seed=1400 + i, n_cells=max(2, H * W // 600))
+        rgbs.append(torch.from_numpy(rgb).cuda())
+        cons.append(torch.from_numpy(con).cuda())
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = S.Batch(rgbs, cons, Ks, stream=stream)
+        b.iterate(4)
+        raw, _ = b.labels(enforce=False)
+        projected = 0
+        for i, K in enumerate(Ks):
+            s = S.Segmenter(rgbs[i], cons[i], K, stream=stream)
+            s.iterate(4)
+            lab, _ = s.labels(enforce=False)
+            assert np.array_equal(raw[i], lab), (i, sizes[i], K)
+            sa, sb = s.get_state(), b.get_state(i)
+            for k in ("n", "sx", "sy", "color", "endpoint"):
+                assert np.array_equal(sa[k], sb[k]), (i, k)
+            if i < 40:  # clusters the last update queued: endpoint != rounded barycenter
+                n = sb["n"]
+                half_up = (2 * sb["sx"] + n) // np.maximum(2 * n, 1), (2 * sb["sy"] + n) // np.maximum(2 * n, 1)
+                projected += int(((n > 0) & ((sb["endpoint"][:, 0] != half_up[0]) |
+                                             (sb["endpoint"][:, 1] != half_up[1]))).sum())
+            s.close()
+        b.close()
+    # the warp list needs more queued clusters than four per CTA (304 CTAs)
+    assert projected > 4 * 2 * 152, projected
+
+
 def test_batch_of_single_tiles(S):
     """Every image fits in one 32x32 tile, so the border pass of the batch has
     no work at all and is not launched."""
