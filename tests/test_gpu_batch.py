@@ -233,6 +233,32 @@ def test_projection_work_lists(S):
     assert projected > 4 * 2 * 152, projected
 
 
+def test_more_tiles_than_the_lists_scan_holds(S):
+    """A 3008x4224 image has 12,408 tiles, more than the single-image list
+    kernel scans in shared memory (12,287): its lists come from the separate
+    scan and fill kernels beside the projection.  Solved alone it equals the
+    same image in a batch of one, whose lists a batch builds per image."""
+    import torch
+
+    H, W, K = 3008, 4224, 3000
+    rgb, con, _ = synth.small_image(H, W, seed=1500, n_cells=400)
+    d_rgb, d_con = torch.from_numpy(rgb).cuda(), torch.from_numpy(con).cuda()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        s = S.Segmenter(d_rgb, d_con, K, stream=stream)
+        s.iterate(3)
+        lab, _ = s.labels(enforce=False)
+        b = S.Batch([d_rgb], [d_con], [K], stream=stream)
+        b.iterate(3)
+        raw, _ = b.labels(enforce=False)
+        assert np.array_equal(raw[0], lab)
+        sa, sb = s.get_state(), b.get_state(0)
+        for k in ("n", "sx", "sy", "color", "endpoint"):
+            assert np.array_equal(sa[k], sb[k]), k
+        s.close()
+        b.close()
+
+
 def test_batch_of_single_tiles(S):
     """Every image fits in one 32x32 tile, so the border pass of the batch has
     no work at all and is not launched."""
