@@ -274,6 +274,16 @@ int scalp_batch_set_wait(scalp_batch *b, int64_t limit_ns, int32_t hold);
  * (pixel, cluster) pairs the assignments evaluated since counting was
  * enabled (enable 1 resets and counts, 0 stops, -1 only reads).  Synchronises. */
 int scalp_batch_count_samples(scalp_batch *b, int32_t enable, int64_t *samples, int64_t *pairs);
+/* As scalp_profile, for the batched assignment (every tile of every image in
+ * one launch per iteration, the inner loops of Algorithm 1 with Eq. 1-3):
+ * enable != 0 starts timing each assignment launch with CUDA events on the
+ * batch's stream (and resets the totals), 0 stops, -1 only reads; *ms and
+ * *launches receive the totals so far (synchronises).  While timing, the
+ * iteration's launches are not programmatically overlapped.  The persistent
+ * launch modes run the assignment inside one launch: nothing is timed there
+ * and *launches stays 0.  Errors: SCALP_E_ARG for a NULL batch, SCALP_E_CUDA
+ * if an event cannot be made or read. */
+int scalp_batch_profile(scalp_batch *b, int32_t enable, double *ms, int64_t *launches);
 /* Autotuner (not part of the paper): times `iters` iterations of the batch in
  * each launch mode this device supports (the faster of two runs after a
  * warm-up, each from a fresh scalp_batch_reload of images/contours), keeps

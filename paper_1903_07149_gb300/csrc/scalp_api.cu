@@ -1072,6 +1072,13 @@ struct scalp_batch {
     std::vector<double> r;        // per image: the grid step
     long long wait_ns = 2000000000LL;
     int hold = 0;
+    // per-launch timing of the batched assignment (scalp_batch_profile):
+    // event pair i brackets iteration i's assignment launch
+    bool profiling = false, graph_prof = false;
+    std::vector<cudaEvent_t> ev;
+    int prof_pending = 0;
+    double prof_ms = 0.0;
+    long long prof_launches = 0;
 };
 
 namespace {
@@ -1152,6 +1159,34 @@ int batch_fail(int code, const char *fmt, ...)
     return code;
 }
 
+int batch_ensure_events(scalp_batch *b, size_t pairs)
+{
+    while (b->ev.size() < 2 * pairs) {
+        cudaEvent_t e;
+        const cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return batch_fail(SCALP_E_CUDA, "create event: %s", cudaGetErrorString(r));
+        b->ev.push_back(e);
+    }
+    return SCALP_OK;
+}
+
+// Adds the durations of the recorded assignment launches to the totals.
+int batch_harvest_profile(scalp_batch *b)
+{
+    if (b->prof_pending == 0) return SCALP_OK;
+    cudaError_t e = cudaStreamSynchronize(b->st);
+    if (e != cudaSuccess) return batch_fail(SCALP_E_CUDA, "synchronise: %s", cudaGetErrorString(e));
+    for (int i = 0; i < b->prof_pending; ++i) {
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, b->ev[2 * i], b->ev[2 * i + 1]);
+        if (e != cudaSuccess) return batch_fail(SCALP_E_CUDA, "event time: %s", cudaGetErrorString(e));
+        b->prof_ms += t;
+        b->prof_launches += 1;
+    }
+    b->prof_pending = 0;
+    return SCALP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1188,6 +1223,7 @@ void scalp_batch_destroy(scalp_batch *b)
         cudaEventDestroy(b->it_join);
     }
     if (b->graph_valid) cudaGraphExecDestroy(b->gexec);
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
     b->in_table.release();
     b->out_table.release();
     if (b->pin_ctr) cudaFreeHost(b->pin_ctr);
@@ -1400,17 +1436,30 @@ int scalp_batch_iterate(scalp_batch *b, int32_t n)
         for (scalp_ctx *c : b->ctx) c->iterations += n;
         return SCALP_OK;
     }
+    if (b->profiling) {
+        int rc = batch_harvest_profile(b);  // the events are about to be re-recorded
+        if (rc) return rc;
+        rc = batch_ensure_events(b, (size_t)n);
+        if (rc) return rc;
+    }
     bool capturing = false;
+    // programmatic launches overlap each kernel's placement with the drain of
+    // the one before (not across the profiling event records)
+    const bool pdl = !b->profiling;
     auto enqueue = [&](int iters) {
+        // under stream capture the records become event-record nodes
+        const unsigned flags = capturing ? cudaEventRecordExternal : cudaEventRecordDefault;
         for (int i = 0; i < iters; ++i) {
-            launch_assign_batch(b->bargs, b->storage, b->total_tiles, b->smem, b->st, true);
-            launch_batch_update(b->bargs, b->total_clusters, b->total_fill, b->st, true,
+            if (b->profiling) cudaEventRecordWithFlags(b->ev[2 * i], b->st, flags);
+            launch_assign_batch(b->bargs, b->storage, b->total_tiles, b->smem, b->st, pdl);
+            if (b->profiling) cudaEventRecordWithFlags(b->ev[2 * i + 1], b->st, flags);
+            launch_batch_update(b->bargs, b->total_clusters, b->total_fill, b->st, pdl,
                                 capturing ? b->it_side : nullptr, b->it_fork, b->it_join);
         }
     };
     const bool graphs = b->use_graph && b->st != nullptr;
     cudaError_t e = cudaSuccess;
-    if (graphs && !(b->graph_valid && b->graph_n == n)) {
+    if (graphs && !(b->graph_valid && b->graph_n == n && b->graph_prof == b->profiling)) {
         if (b->graph_valid) {
             cudaGraphExecDestroy(b->gexec);
             b->graph_valid = false;
@@ -1451,6 +1500,7 @@ int scalp_batch_iterate(scalp_batch *b, int32_t n)
         if (e != cudaSuccess) return batch_fail(SCALP_E_CUDA, "instantiate: %s", cudaGetErrorString(e));
         b->graph_valid = true;
         b->graph_n = n;
+        b->graph_prof = b->profiling;
     }
     if (graphs) {
         e = cudaGraphLaunch(b->gexec, b->st);
@@ -1459,6 +1509,7 @@ int scalp_batch_iterate(scalp_batch *b, int32_t n)
         e = cudaGetLastError();
     }
     if (e != cudaSuccess) return batch_fail(SCALP_E_CUDA, "batch iteration: %s", cudaGetErrorString(e));
+    if (b->profiling) b->prof_pending = n;
     for (scalp_ctx *c : b->ctx) c->iterations += n;
     return SCALP_OK;
 }
@@ -1712,6 +1763,24 @@ int scalp_batch_autotune(scalp_batch *b, const scalp_image *images, const scalp_
                  ms[0], ms[1], ms[2]);
         cache[key] = entry;
         if (!write_cache(cache_path, cache)) return batch_fail(SCALP_E_ARG, "cannot write the cache %s", cache_path);
+    }
+    return SCALP_OK;
+}
+
+int scalp_batch_profile(scalp_batch *b, int32_t enable, double *ms, int64_t *launches)
+{
+    if (!b) return batch_fail(SCALP_E_ARG, "batch is NULL");
+    const int rc = batch_harvest_profile(b);
+    if (rc) return rc;
+    if (ms) *ms = b->prof_ms;
+    if (launches) *launches = b->prof_launches;
+    if (enable >= 0) {
+        const bool on = enable != 0;
+        if (on) {
+            b->prof_ms = 0.0;
+            b->prof_launches = 0;
+        }
+        b->profiling = on;
     }
     return SCALP_OK;
 }

@@ -95,7 +95,7 @@ EXPORTS = (
     "scalp_batch_workspace_bytes", "scalp_batch_init", "scalp_batch_reload", "scalp_batch_iterate",
     "scalp_batch_labels", "scalp_batch_get_state", "scalp_batch_get_info", "scalp_batch_destroy",
     "scalp_batch_set_launch", "scalp_batch_get_launch", "scalp_batch_set_wait",
-    "scalp_batch_count_samples", "scalp_batch_autotune",
+    "scalp_batch_count_samples", "scalp_batch_profile", "scalp_batch_autotune",
     "scalp_server_reserve_bytes", "scalp_server_create", "scalp_server_submit", "scalp_server_step",
     "scalp_server_poll", "scalp_server_stats", "scalp_server_destroy", "scalp_boundary_map",
     "scalp_server_set_step_budget",
@@ -158,6 +158,8 @@ def load(path: str = LIB_PATH) -> ctypes.CDLL:
             "scalp_batch_get_launch": (ctypes.c_int, [P, ctypes.POINTER(I32), ctypes.POINTER(I32)]),
             "scalp_batch_set_wait": (ctypes.c_int, [P, I64, I32]),
             "scalp_batch_count_samples": (ctypes.c_int, [P, I32, ctypes.POINTER(I64), ctypes.POINTER(I64)]),
+            "scalp_batch_profile": (ctypes.c_int, [P, I32, ctypes.POINTER(ctypes.c_double),
+                                                   ctypes.POINTER(I64)]),
             "scalp_batch_autotune": (ctypes.c_int, [P, P, P, I32, ctypes.c_char_p, ctypes.POINTER(I32),
                                                     P, ctypes.POINTER(I32)]),
             "scalp_server_reserve_bytes": (ctypes.c_size_t, [I32]),
@@ -588,6 +590,13 @@ class Batch:
         a, b = ctypes.c_int64(), ctypes.c_int64()
         _check(load().scalp_batch_count_samples(self.batch, int(enable), ctypes.byref(a), ctypes.byref(b)))
         return a.value, b.value
+
+    def profile(self, enable: int):
+        """(ms, launches) of the batched assignment launches since timing was
+        enabled (none in a persistent launch mode)."""
+        ms, n = ctypes.c_double(), ctypes.c_int64()
+        _check(load().scalp_batch_profile(self.batch, int(enable), ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
 
     def autotune(self, rgbs, contours, iters: int = 10, cache_path=None):
         """Times each launch mode and keeps the fastest (the batch is left

@@ -286,6 +286,47 @@ def _assert_same(r1, r2):
             assert np.array_equal(st1[i][k], st2[i][k]), (i, k)
 
 
+def test_batch_profile_times_each_assignment(S):
+    """Timing the batched assignment launches (events around each one, the
+    programmatic overlap off meanwhile) counts one launch per iteration,
+    also across graph replays of two lengths, changes no result, and times
+    nothing in a persistent launch mode, whose assignment runs inside one
+    kernel."""
+    import torch
+
+    rgbs, cons = _inputs()
+    Ks = [k for _, _, k in SIZES]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        b = S.Batch(rgbs, cons, Ks, stream=stream)
+        b.iterate(4)
+        b.iterate(3)
+        ref = _batch_result(b)
+        b.reload(rgbs, cons)
+        assert b.profile(1) == (0.0, 0)
+        b.iterate(4)
+        b.iterate(3)
+        ms, n = b.profile(-1)  # read, keep timing
+        assert n == 7 and ms > 0.0
+        _assert_same(ref, _batch_result(b))
+        b.reload(rgbs, cons)
+        b.iterate(7)
+        ms2, n2 = b.profile(0)
+        assert n2 == 14 and ms2 > ms
+        assert b.profile(-1) == (ms2, n2)  # stopped: nothing more is added
+        b.reload(rgbs, cons)
+        b.iterate(7)
+        assert b.profile(-1) == (ms2, n2)
+        _assert_same(ref, _batch_result(b))
+        b.set_launch("persistent")
+        b.reload(rgbs, cons)
+        b.profile(1)
+        b.iterate(7)
+        assert b.profile(0) == (0.0, 0)
+        _assert_same(ref, _batch_result(b))
+        b.close()
+
+
 @pytest.mark.parametrize("storage", ["f32", "f16"])
 def test_persistent_launch_equals_flat(S, storage):
     """All iterations of the batch in one cooperative launch (tiles from a
