@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(ASSIGN_THREADS, ASSIGN_CTAS_PER_SM) k_assign_b
     extern __shared__ __align__(16) unsigned char smem[];
     const int g = blockIdx.x;
     const int i = batch_find(b.tile_base, b.count, g);
-    assign_tile<T>(b.args[i], g - b.tile_base[i], smem);
+    assign_tile<T, true>(b.args[i], g - b.tile_base[i], smem);
 }
 
 void launch_assign(const SolveArgs &a, int storage, size_t smem_bytes, cudaStream_t st, bool pdl)

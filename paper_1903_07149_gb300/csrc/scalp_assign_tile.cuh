@@ -191,7 +191,9 @@ __device__ __forceinline__ int warp_scan_maps(const int *area, int *mfirst, int 
 // One tile of one image (the body shared by the single-image and the batched
 // kernels).  The pixels of a candidate's window that lie in the tile form a
 // rectangle; each warp owns 64 pixels of the tile (two blocks of 8 x 4).
-template <typename T>
+// PREFETCH_TILE: the tile's plane rows are first asked into L2 (for batches,
+// whose planes outgrow L2; an image whose plane stays in L2 only pays for it).
+template <typename T, bool PREFETCH_TILE = false>
 __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsigned char *smem)
 {
     constexpr int THREADS = ASSIGN_THREADS;
@@ -242,6 +244,19 @@ __device__ __forceinline__ void assign_tile(const SolveArgs &a, int tile, unsign
         // the last projection (and lists) completed before this launch: its
         // queue starts again for the next update
         if (tile == 0) a.ctr->nproj = 0;
+    }
+
+    // the tile's plane rows into L2 while the set-up runs, so that the map
+    // build finds them there (x0 * sizeof(T) and the row pitch are multiples
+    // of 16 bytes, and so is every row's length: the bulk prefetch's rules)
+    static_assert(TILE_Y <= 32, "one row per lane");
+    if (PREFETCH_TILE && warp == WARPS - 1) {
+        const int rows = min(a.H - y0, TILE_Y);
+        const uint32_t bytes = (uint32_t)(min(TILE_X, a.pitch - x0) * (int)sizeof(T));
+        if (lane < rows) {
+            const T *p = plane + (long long)(y0 + lane) * a.pitch + x0;
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+        }
     }
 
     // this thread's pixels' previous labels (their loads overlap the set-up)
