@@ -90,4 +90,14 @@ def test_init_rejects_bad_arguments_on_host(lib):
 def test_null_context_calls(lib):
     assert lib.scalp_iterate(None, 1) == scalp.SCALP_E_ARG
     assert lib.scalp_sync(None) == scalp.SCALP_E_ARG
+    ms, n = ctypes.c_double(-1.0), ctypes.c_int64(-1)
+    assert lib.scalp_profile(None, 1, ctypes.byref(ms), ctypes.byref(n)) == scalp.SCALP_E_ARG
+    # a NULL batch is refused before anything is read or written
+    assert lib.scalp_batch_iterate(None, 1) == scalp.SCALP_E_ARG
+    assert lib.scalp_batch_profile(None, 1, ctypes.byref(ms), ctypes.byref(n)) == scalp.SCALP_E_ARG
+    assert (ms.value, n.value) == (-1.0, -1)
+    a, b = ctypes.c_int64(-1), ctypes.c_int64(-1)
+    assert lib.scalp_batch_count_samples(None, 1, ctypes.byref(a), ctypes.byref(b)) == scalp.SCALP_E_ARG
+    assert (a.value, b.value) == (-1, -1)
     lib.scalp_destroy(None)  # no-op
+    lib.scalp_batch_destroy(None)  # no-op
